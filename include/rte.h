@@ -1,0 +1,213 @@
+/*
+ * rte.h -- C ABI of the GB300 (sm_103a) FGMRES-ROMSAD solver for the steady
+ * one-group parametric radiative transfer equation (arXiv 2410.08735).
+ *
+ * Method (paper sections cited per call):
+ *   Sec. 2    S_N discrete ordinates (Chebyshev-Legendre product rule in 2D,
+ *             Gauss-Legendre in the 1D slab) and upwind DG with the orthonormal
+ *             Q^1 basis (P^1 in 1D): (D_j + Sigma_t) psi_j = Sigma_s phi + G + g_j^bc.
+ *   Sec. 3    memory-efficient form: A~ phi = (I - T Sigma_s) phi = b~,
+ *             T = sum_j omega_j (D_j + Sigma_t)^{-1}, b~ = sum_j omega_j (D_j + Sigma_t)^{-1} G~_j.
+ *   Sec. 4    ROMSAD preconditioner M_ROM^{-1} = I + W (U_r^T A U_r)^{-1} P^T Sigma_s,
+ *             P = sum_j U_{r,j}, W = sum_j omega_j U_{r,j}; FGMRES (Alg. 1); greedy
+ *             ROM construction (Sec. 4.4.2) with MGS truncation (appendix B).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an int status (RTE_OK = 0 or one of RTE_ERR_*);
+ *     rte_status_string() names it and rte_last_error() gives a thread-local
+ *     detail message for the last failing call of the calling thread.
+ *   - A problem holds B parameter instances, each on its own uniform Cartesian
+ *     mesh.  A "scalar vector" concatenates the instances: instance b occupies
+ *     [off_b, off_b + N_b) with N_b = nx_b*ny_b*nd (nd = 4 in 2D, 2 in 1D); the
+ *     offsets are returned by rte_problem_offsets().  Inside an instance the
+ *     layout is cell-major, cells row-major (c = iy*nx + ix), local dof
+ *     k = a + 2b for the basis p_a(x) q_b(y) (orthonormal Legendre).
+ *   - An "angular vector" (rte_sweep output) holds, per instance, N_Omega
+ *     consecutive scalar vectors: instance b occupies [N_Omega*off_b, N_Omega*off_{b+1}),
+ *     direction j at N_Omega*off_b + j*N_b, directions in the paper's index
+ *     order j = (j2-1) N_theta + j1.
+ *   - Data pointers are caller-owned.  Unless a call says otherwise they are
+ *     DEVICE pointers (e.g. torch CUDA tensors, contiguous), of the type given
+ *     by the dtype argument (RTE_F64: double, RTE_F32: float).  Host arrays
+ *     in descriptors and parameter setters are copied before the call returns.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that return results to the host synchronise that stream.
+ *   - Handles (rte_problem_t, romsad_t, rte_mlp_t) own their device memory;
+ *     destroy them once no call on them is in flight.  A handle is not
+ *     thread-safe: serialise calls on the same handle.
+ */
+#ifndef RTE_GB300_H
+#define RTE_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define RTE_OK 0
+#define RTE_ERR_INVALID_ARG 1   /* bad pointer, size, enum or mesh mismatch          */
+#define RTE_ERR_CUDA 2          /* a CUDA runtime call failed (detail in last_error) */
+#define RTE_ERR_OOM 3           /* device allocation failed                           */
+#define RTE_ERR_NOT_CONVERGED 4 /* solver hit max_iter; outputs and stats written     */
+#define RTE_ERR_NUMERIC 5       /* NaN/Inf met (e.g. in beta or a Hessenberg column)   */
+#define RTE_ERR_TIMEOUT 6       /* a bounded device wait gave up                      */
+#define RTE_ERR_UNSUPPORTED 7   /* valid request this build does not implement        */
+#define RTE_ERR_IO 8            /* checkpoint file could not be read or written       */
+
+/* arithmetic type of the vectors handed to a call */
+#define RTE_F64 0
+#define RTE_F32 1
+
+const char* rte_status_string(int status);
+const char* rte_last_error(void);
+/* Library version and the CUDA device it would run on; safe without a GPU (returns the version). */
+int rte_version(int* major, int* minor);
+
+/* ----------------------------------------------------------------- problem */
+typedef struct rte_problem_desc {
+    int dim;               /* 1 (slab, Sec. appendix A geometry) or 2 (X-Y, Sec. 2)        */
+    int n_instances;       /* B >= 1                                                        */
+    const int* nx;         /* [B] cells in x, host                                          */
+    const int* ny;         /* [B] cells in y, host (ignored in 1D)                          */
+    double box[4];         /* domain x0, x1, y0, y1 (y ignored in 1D)                       */
+    int n_polar;           /* 1D: Gauss-Legendre points in mu; 2D: GL points in Omega_z     */
+    int n_azim;            /* 2D: Chebyshev azimuthal points N_theta (even); 1D: ignored    */
+    int rx, ry;            /* region grid, R = rx*ry equal blocks (ry = 1 in 1D)            */
+    const double* sigma_s; /* [B][R] host: scattering cross section per region (>= 0)       */
+    const double* sigma_a; /* [B][R] host: absorption cross section per region (>= 0)       */
+    double src_q;          /* isotropic source value inside src_box, 0 outside (eq. 1 G)    */
+    double src_box[4];     /* xa, xb, ya, yb                                                */
+    double inflow_g;       /* isotropic inflow value g on all inflow boundaries (eq. 1c)    */
+} rte_problem_desc;
+
+typedef struct rte_problem* rte_problem_t;
+
+typedef struct rte_problem_info {
+    int dim, n_instances, n_directions, n_unique_directions, dofs_per_cell, n_regions;
+    long long n_dof_total;     /* sum_b N_b                                       */
+    long long n_angular_total; /* N_Omega * n_dof_total (rte_sweep output length) */
+} rte_problem_info;
+
+/* Build quadrature, geometry, region maps and the per-instance source on the device
+ * (Sec. 2.1-2.3).  Returns RTE_ERR_INVALID_ARG for dim not in {1,2}, B < 1, a mesh
+ * with fewer than 1 cell, a region grid that does not divide every mesh, an odd
+ * n_azim, or negative cross sections. */
+int rte_problem_create(const rte_problem_desc* desc, rte_problem_t* out);
+int rte_problem_destroy(rte_problem_t p);
+int rte_problem_get_info(rte_problem_t p, rte_problem_info* info);
+/* offsets: host array [B+1], off_0 = 0, off_B = n_dof_total. */
+int rte_problem_offsets(rte_problem_t p, long long* offsets);
+/* New material parameters mu = (sigma_s, sigma_a) per instance without rebuilding
+ * (Sec. 4.1 parametric problem).  Host arrays [B][R], copied. */
+int rte_problem_set_params(rte_problem_t p, const double* sigma_s, const double* sigma_a);
+
+/* --------------------------------------------------------- transport (Sec. 3) */
+/* Angular-output sweep (Sec. 3.1, eq. SI-equation): for every direction j,
+ * psi_j = (D_j + Sigma_t)^{-1} (src + with_bc * g_j^bc).  src: scalar vector;
+ * psi: angular vector (see conventions).  Directions with the same (Omega_x,
+ * Omega_y) give identical psi_j and are computed once. */
+int rte_sweep(rte_problem_t p, int dtype, const void* src, int with_bc, void* psi, void* stream);
+/* phi = Q psi = sum_j omega_j psi_j (Sec. 2.3). psi: angular vector, phi: scalar vector. */
+int rte_scalar_flux(rte_problem_t p, int dtype, const void* psi, void* phi, void* stream);
+/* phi = T s = sum_j omega_j (D_j + Sigma_t)^{-1} s (eq. memory-efficient-SI), fused, psi never stored. */
+int rte_apply_T(rte_problem_t p, int dtype, const void* s, void* phi, void* stream);
+/* w = A~ z = z - T (Sigma_s z) (eq. memory-efficient-rte), fused. */
+int rte_apply_op(rte_problem_t p, int dtype, const void* z, void* w, void* stream);
+/* btilde = sum_j omega_j (D_j + Sigma_t)^{-1} (G + g_j^bc) (eq. memory-efficient-SI). */
+int rte_rhs(rte_problem_t p, int dtype, void* btilde, void* stream);
+
+/* ----------------------------------------------------------- ROMSAD (Sec. 4) */
+typedef struct romsad* romsad_t;
+
+/* ROM from an orthonormal basis U_r given on the HOST as [r][N_Omega][N_b] doubles
+ * for the mesh of instance `instance` of tmpl.  The library forms P, W and the
+ * affine reduced operators A_D, T_R, S_R (Sec. 4.1):
+ *   U^T A_mu U = A_D + sum_R (sigma_a,R + sigma_s,R) T_R - sum_R sigma_s,R S_R. */
+int romsad_create_from_basis(rte_problem_t tmpl, int instance, int r, const double* U_host, romsad_t* out);
+
+typedef struct romsad_greedy_opts {
+    int window;           /* w: FGMRES iterations whose corrections enter the ROM (Sec. 4.3)  */
+    int max_greedy_iter;  /* N_g-iter                                                         */
+    int max_rank;         /* cap on r                                                         */
+    double eps_rom;       /* stop when max relative indicator R_mu/||eta_mu^(0)|| < eps_rom   */
+    double eps_qr;        /* appendix B truncation, relative to the snapshot norm (1e-13)     */
+    int mu1;              /* index of the first sample, or -1: nearest the centroid of
+                             (log sigma_s, sigma_a) over the training set                    */
+    double hf_rtol;       /* relative residual of the high-fidelity FGMRES of step 2(a)      */
+    int hf_restart;       /* restart length of that solve                                    */
+    int hf_max_iter;
+} romsad_greedy_opts;
+
+typedef struct romsad_report {
+    int n_sampled;
+    int* sampled;          /* caller array [max_greedy_iter] or NULL: training indices in order */
+    double* max_indicator; /* caller array [max_greedy_iter] or NULL                           */
+    int rank;
+    double* labels;        /* caller array [n_train][max_rank] or NULL: Galerkin coefficients
+                              c_mu of eq. greedy-rom on the final basis (MLP labels)           */
+} romsad_report;
+
+/* Greedy ROM construction (Sec. 4.4.2) on the GPU for the mesh of instance 0 of
+ * tmpl, over n_train parameter points (host arrays [n_train][R]).  tmpl's own
+ * parameters are left unchanged. */
+int romsad_build_greedy(rte_problem_t tmpl, int n_train, const double* train_sigma_s,
+                        const double* train_sigma_a, const romsad_greedy_opts* opts,
+                        romsad_t* out, romsad_report* report);
+int romsad_rank(romsad_t rom, int* r);
+/* Copy the basis to the host as [r][N_Omega][N] doubles. */
+int romsad_get_basis(romsad_t rom, double* U_host);
+/* Reduced operator U^T A_mu U (affine assembly) for per-region sigma (host [R]) -> host [r][r]. */
+int romsad_reduced_operator(romsad_t rom, const double* sigma_s, const double* sigma_a, double* A_host);
+/* z = M_ROM^{-1} v for every instance of p (all instances must use the ROM's mesh),
+ * eq. rom-sa-preconditioner, with the instance's own sigma.  v, z: scalar vectors. */
+int romsad_apply(romsad_t rom, rte_problem_t p, int dtype, const void* v, void* z, void* stream);
+int romsad_save(romsad_t rom, const char* path);
+int romsad_load(const char* path, romsad_t* out);
+int romsad_destroy(romsad_t rom);
+
+/* ------------------------------------------------------------ FGMRES (Alg. 1) */
+#define RTE_POST_ROM 0       /* keep M_ROM after the window (a fixed linear operator) */
+#define RTE_POST_IDENTITY 1  /* z = v after the window                                */
+#define RTE_MODE_FP64 0      /* every sweep, MGS and least squares in FP64             */
+#define RTE_MODE_MIXED 1     /* FP64 iterative refinement around an FGMRES whose sweeps
+                                and ROM products run in FP32; MGS/Givens in FP64       */
+
+typedef struct fgmres_opts {
+    int restart;             /* m of Alg. 1 (Krylov vectors per cycle)                */
+    double rtol;             /* FP64 mode: ||r||/||b~|| target; mixed: FP64 true residual target */
+    int max_iter;            /* cap on Arnoldi iterations (summed over restarts / outer steps) */
+    int window;              /* w of eq. ROMSAD-preconditioner                        */
+    int post_mode;           /* RTE_POST_ROM or RTE_POST_IDENTITY                      */
+    int mode;                /* RTE_MODE_FP64 or RTE_MODE_MIXED                        */
+    double inner_rtol;       /* mixed: relative target of each inner solve             */
+    int max_outer;           /* mixed: cap on refinement steps                         */
+    int true_residual_check; /* FP64 mode: recompute b~ - A~ phi after convergence     */
+    int warm_start;          /* 1: phi0 is used as the initial guess                   */
+} fgmres_opts;
+
+typedef struct fgmres_stats {
+    int status;              /* RTE_OK or RTE_ERR_NOT_CONVERGED / RTE_ERR_NUMERIC      */
+    int iterations;          /* Arnoldi iterations (all cycles and outer steps)        */
+    int sweeps;              /* operator applies counted as in Sec. 5 (1 + iterations
+                                with a zero guess; +1 per restart / nonzero guess)   */
+    int sweeps_fp64;         /* of which in FP64                                       */
+    int restarts;
+    int outer;               /* mixed: refinement steps                                */
+    double est_rel_residual; /* last Givens estimate |g_{j+1}| / ||b~||                */
+    double true_rel_residual;/* ||b~ - A~ phi||_2 / ||b~||_2 in FP64 (NaN if not computed) */
+    double true_linf_residual;
+} fgmres_stats;
+
+/* Solve A~_b phi_b = b~_b for every instance b (Alg. 1, restarted).  roms: NULL (no
+ * preconditioner, M_j = I) or an array [B] of ROM handles (NULL entries allowed),
+ * roms[b] built on instance b's mesh.  phi0: scalar vector (FP64, device) or NULL.
+ * phi: scalar vector, FP64; may be a DEVICE or HOST pointer (detected): with a host
+ * pointer the result is copied back and the stream synchronised.  stats: host [B].
+ * Returns RTE_ERR_NOT_CONVERGED if any instance missed its target. */
+int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_opts* opts, const void* phi0,
+                 void* phi, fgmres_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTE_GB300_H */

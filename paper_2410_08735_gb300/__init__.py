@@ -1,0 +1,7 @@
+"""GB300 (sm_103a) FGMRES-ROMSAD solver for the parametric radiative transfer equation.
+
+The compute path is librte_gb300.so (hand-written CUDA kernels behind the C ABI
+of include/rte.h); this package only builds and binds it.
+"""
+from .binding import (Problem, Rom, RteError, fgmres_solve, load, RTE_F32, RTE_F64,  # noqa: F401
+                      RTE_MODE_FP64, RTE_MODE_MIXED, RTE_POST_IDENTITY, RTE_POST_ROM)

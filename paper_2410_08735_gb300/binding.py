@@ -1,0 +1,356 @@
+"""Thin ctypes binding of include/rte.h (argument marshalling only).
+
+Every computation runs in librte_gb300.so (hand-written CUDA for sm_103a).
+Tensors are torch CUDA tensors (contiguous); their data pointers are handed to
+the C ABI unchanged.  A missing or unloadable library raises immediately:
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build_lib
+
+RTE_OK = 0
+RTE_ERR_NOT_CONVERGED = 4
+RTE_F64, RTE_F32 = 0, 1
+RTE_POST_ROM, RTE_POST_IDENTITY = 0, 1
+RTE_MODE_FP64, RTE_MODE_MIXED = 0, 1
+
+_lib = None
+
+
+class RteError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: {detail} ({status})")
+        self.status = status
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n_instances", ctypes.c_int),
+                ("nx", ctypes.POINTER(ctypes.c_int)), ("ny", ctypes.POINTER(ctypes.c_int)),
+                ("box", ctypes.c_double * 4), ("n_polar", ctypes.c_int), ("n_azim", ctypes.c_int),
+                ("rx", ctypes.c_int), ("ry", ctypes.c_int),
+                ("sigma_s", ctypes.POINTER(ctypes.c_double)), ("sigma_a", ctypes.POINTER(ctypes.c_double)),
+                ("src_q", ctypes.c_double), ("src_box", ctypes.c_double * 4), ("inflow_g", ctypes.c_double)]
+
+
+class ProblemInfo(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n_instances", ctypes.c_int), ("n_directions", ctypes.c_int),
+                ("n_unique_directions", ctypes.c_int), ("dofs_per_cell", ctypes.c_int),
+                ("n_regions", ctypes.c_int), ("n_dof_total", ctypes.c_longlong),
+                ("n_angular_total", ctypes.c_longlong)]
+
+
+class GreedyOpts(ctypes.Structure):
+    _fields_ = [("window", ctypes.c_int), ("max_greedy_iter", ctypes.c_int), ("max_rank", ctypes.c_int),
+                ("eps_rom", ctypes.c_double), ("eps_qr", ctypes.c_double), ("mu1", ctypes.c_int),
+                ("hf_rtol", ctypes.c_double), ("hf_restart", ctypes.c_int), ("hf_max_iter", ctypes.c_int)]
+
+
+class GreedyReport(ctypes.Structure):
+    _fields_ = [("n_sampled", ctypes.c_int), ("sampled", ctypes.POINTER(ctypes.c_int)),
+                ("max_indicator", ctypes.POINTER(ctypes.c_double)), ("rank", ctypes.c_int),
+                ("labels", ctypes.POINTER(ctypes.c_double))]
+
+
+class FgmresOpts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("window", ctypes.c_int), ("post_mode", ctypes.c_int), ("mode", ctypes.c_int),
+                ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int),
+                ("true_residual_check", ctypes.c_int), ("warm_start", ctypes.c_int)]
+
+
+class FgmresStats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("sweeps", ctypes.c_int),
+                ("sweeps_fp64", ctypes.c_int), ("restarts", ctypes.c_int), ("outer", ctypes.c_int),
+                ("est_rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
+                ("true_linf_residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_SIGS = {
+    "rte_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rte_last_error": (ctypes.c_char_p, []),
+    "rte_version": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "rte_problem_create": (ctypes.c_int, [ctypes.POINTER(ProblemDesc), ctypes.POINTER(ctypes.c_void_p)]),
+    "rte_problem_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "rte_problem_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ProblemInfo)]),
+    "rte_problem_offsets": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "rte_problem_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]),
+    "rte_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                 ctypes.c_void_p]),
+    "rte_scalar_flux": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "rte_apply_T": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]),
+    "rte_apply_op": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
+    "rte_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "romsad_create_from_basis": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p)]),
+    "romsad_build_greedy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(GreedyOpts),
+                                           ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(GreedyReport)]),
+    "romsad_rank": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "romsad_get_basis": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "romsad_reduced_operator": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+    "romsad_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
+    "romsad_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
+    "romsad_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "romsad_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fgmres_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(FgmresOpts),
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(FgmresStats),
+                                    ctypes.c_void_p]),
+}
+
+
+def lib_path() -> str:
+    return build_lib.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load librte_gb300.so (building it first only when asked)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = build_lib.build() if build_if_missing else build_lib.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"librte_gb300.so not built ({path}); run paper_2410_08735_gb300.build_lib.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status: int, where: str):
+    if status != RTE_OK:
+        lib = load()
+        raise RteError(status, where, lib.rte_last_error().decode() or lib.rte_status_string(status).decode())
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _dtype_code(t) -> int:
+    import torch
+    if t.dtype == torch.float64:
+        return RTE_F64
+    if t.dtype == torch.float32:
+        return RTE_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class Problem:
+    """Owns an rte_problem_t.  spec: a workloads.ProblemSpec; sigma_s/sigma_a: [B][R] arrays."""
+
+    def __init__(self, spec, sigma_s, sigma_a):
+        lib = load()
+        B = spec.n_instances
+        self.spec = spec
+        ss = np.ascontiguousarray(np.asarray(sigma_s, dtype=np.float64).reshape(B, -1))
+        sa = np.ascontiguousarray(np.asarray(sigma_a, dtype=np.float64).reshape(B, -1))
+        nx = (ctypes.c_int * B)(*spec.nx)
+        ny = (ctypes.c_int * B)(*spec.ny)
+        d = ProblemDesc()
+        d.dim = spec.dim
+        d.n_instances = B
+        d.nx = nx
+        d.ny = ny
+        d.box = (ctypes.c_double * 4)(*spec.box)
+        d.n_polar = spec.n_polar
+        d.n_azim = spec.n_azim
+        d.rx = spec.rx
+        d.ry = spec.ry if spec.dim == 2 else 1
+        d.sigma_s = _dptr(ss)
+        d.sigma_a = _dptr(sa)
+        d.src_q = spec.src_q
+        d.src_box = (ctypes.c_double * 4)(*spec.src_box)
+        d.inflow_g = spec.inflow_g
+        h = ctypes.c_void_p()
+        _check(lib.rte_problem_create(ctypes.byref(d), ctypes.byref(h)), "rte_problem_create")
+        self.h = h
+        info = ProblemInfo()
+        _check(lib.rte_problem_get_info(h, ctypes.byref(info)), "rte_problem_get_info")
+        self.info = info
+        offs = (ctypes.c_longlong * (B + 1))()
+        _check(lib.rte_problem_offsets(h, offs), "rte_problem_offsets")
+        self.offsets = np.array(list(offs), dtype=np.int64)
+
+    @property
+    def n_dof(self) -> int:
+        return int(self.info.n_dof_total)
+
+    @property
+    def n_directions(self) -> int:
+        return int(self.info.n_directions)
+
+    def set_params(self, sigma_s, sigma_a):
+        ss = np.ascontiguousarray(np.asarray(sigma_s, dtype=np.float64))
+        sa = np.ascontiguousarray(np.asarray(sigma_a, dtype=np.float64))
+        _check(load().rte_problem_set_params(self.h, _dptr(ss), _dptr(sa)), "rte_problem_set_params")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rte_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # transport ------------------------------------------------------------
+    def sweep(self, src, psi, with_bc: bool = False, stream=None):
+        _check(load().rte_sweep(self.h, _dtype_code(src), _ptr(src), int(with_bc), _ptr(psi), _stream(stream)),
+               "rte_sweep")
+
+    def scalar_flux(self, psi, phi, stream=None):
+        _check(load().rte_scalar_flux(self.h, _dtype_code(psi), _ptr(psi), _ptr(phi), _stream(stream)),
+               "rte_scalar_flux")
+
+    def apply_T(self, s, phi, stream=None):
+        _check(load().rte_apply_T(self.h, _dtype_code(s), _ptr(s), _ptr(phi), _stream(stream)), "rte_apply_T")
+
+    def apply_op(self, z, w, stream=None):
+        _check(load().rte_apply_op(self.h, _dtype_code(z), _ptr(z), _ptr(w), _stream(stream)), "rte_apply_op")
+
+    def rhs(self, out, stream=None):
+        _check(load().rte_rhs(self.h, _dtype_code(out), _ptr(out), _stream(stream)), "rte_rhs")
+
+
+class Rom:
+    """Owns a romsad_t."""
+
+    def __init__(self, handle):
+        self.h = handle
+
+    @classmethod
+    def from_basis(cls, problem: Problem, U: np.ndarray, instance: int = 0):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(load().romsad_create_from_basis(problem.h, instance, U.shape[0], _dptr(U), ctypes.byref(h)),
+               "romsad_create_from_basis")
+        return cls(h)
+
+    @classmethod
+    def greedy(cls, problem: Problem, train_ss, train_sa, window=2, max_greedy_iter=10, max_rank=32,
+               eps_rom=1e-8, eps_qr=1e-13, mu1=-1, hf_rtol=1e-12, hf_restart=30, hf_max_iter=2000,
+               want_labels=False):
+        ss = np.ascontiguousarray(train_ss, dtype=np.float64)
+        sa = np.ascontiguousarray(train_sa, dtype=np.float64)
+        n_train = ss.shape[0]
+        o = GreedyOpts(window, max_greedy_iter, max_rank, eps_rom, eps_qr, mu1, hf_rtol, hf_restart, hf_max_iter)
+        sampled = (ctypes.c_int * max_greedy_iter)()
+        ind = (ctypes.c_double * max_greedy_iter)()
+        labels = np.zeros((n_train, max_rank)) if want_labels else None
+        rep = GreedyReport(0, sampled, ind, 0, _dptr(labels) if labels is not None else None)
+        h = ctypes.c_void_p()
+        _check(load().romsad_build_greedy(problem.h, n_train, _dptr(ss), _dptr(sa), ctypes.byref(o), ctypes.byref(h),
+                                          ctypes.byref(rep)), "romsad_build_greedy")
+        rom = cls(h)
+        r = rep.rank
+        report = {"sampled": [sampled[i] for i in range(rep.n_sampled)],
+                  "max_indicator": [ind[i] for i in range(max(0, rep.n_sampled - 1))],
+                  "rank": r, "labels": labels[:, :r] if labels is not None else None}
+        return rom, report
+
+    @classmethod
+    def load_file(cls, path: str):
+        h = ctypes.c_void_p()
+        _check(load().romsad_load(path.encode(), ctypes.byref(h)), "romsad_load")
+        return cls(h)
+
+    @property
+    def rank(self) -> int:
+        r = ctypes.c_int()
+        _check(load().romsad_rank(self.h, ctypes.byref(r)), "romsad_rank")
+        return r.value
+
+    def basis(self, n_dir: int, n_dof: int) -> np.ndarray:
+        U = np.zeros((self.rank, n_dir, n_dof))
+        _check(load().romsad_get_basis(self.h, _dptr(U)), "romsad_get_basis")
+        return U
+
+    def reduced_operator(self, sigma_s, sigma_a) -> np.ndarray:
+        r = self.rank
+        A = np.zeros((r, r))
+        ss = np.ascontiguousarray(sigma_s, dtype=np.float64)
+        sa = np.ascontiguousarray(sigma_a, dtype=np.float64)
+        _check(load().romsad_reduced_operator(self.h, _dptr(ss), _dptr(sa), _dptr(A)), "romsad_reduced_operator")
+        return A
+
+    def apply(self, problem: Problem, v, z, stream=None):
+        _check(load().romsad_apply(self.h, problem.h, _dtype_code(v), _ptr(v), _ptr(z), _stream(stream)),
+               "romsad_apply")
+
+    def save(self, path: str):
+        _check(load().romsad_save(self.h, path.encode()), "romsad_save")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().romsad_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fgmres_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi, phi0=None, restart=30,
+                 rtol=1e-10, max_iter=1000, window=2, post_mode=RTE_POST_ROM, mode=RTE_MODE_FP64,
+                 inner_rtol=1e-5, max_outer=20, true_residual_check=True, stream=None, raise_on_fail=True):
+    """FGMRES-ROMSAD for all instances; phi: FP64 device tensor or host (numpy/pinned) buffer.
+
+    Returns the list of per-instance stats dicts.
+    """
+    B = problem.spec.n_instances
+    o = FgmresOpts(restart, rtol, max_iter, window, post_mode, mode, inner_rtol, max_outer,
+                   int(true_residual_check), int(phi0 is not None))
+    st = (FgmresStats * B)()
+    if roms is None:
+        rarr = None
+    else:
+        rarr = (ctypes.c_void_p * B)(*[(r.h.value if r is not None else None) for r in roms])
+    if isinstance(phi, np.ndarray):
+        assert phi.dtype == np.float64 and phi.flags["C_CONTIGUOUS"]
+        phi_ptr = ctypes.c_void_p(phi.ctypes.data)
+    else:
+        phi_ptr = _ptr(phi)
+    s = load().fgmres_solve(problem.h, rarr, ctypes.byref(o), _ptr(phi0), phi_ptr, st, _stream(stream))
+    stats = [st[b].as_dict() for b in range(B)]
+    if s != RTE_OK and (raise_on_fail or s != RTE_ERR_NOT_CONVERGED):
+        _check(s, "fgmres_solve")
+    return stats

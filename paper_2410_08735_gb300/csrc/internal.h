@@ -1,0 +1,142 @@
+// Internal declarations shared by the translation units of librte_gb300.
+// Everything here is host C++ / CUDA for sm_103a; the public surface is include/rte.h.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/rte.h"
+
+namespace rte {
+
+// ----------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+struct Status {
+  int code = RTE_OK;
+};
+#define RTE_CHECK_CUDA(expr)                                                                 \
+  do {                                                                                       \
+    cudaError_t _e = (expr);                                                                 \
+    if (_e != cudaSuccess) {                                                                 \
+      ::rte::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));                  \
+      return _e == cudaErrorMemoryAllocation ? RTE_ERR_OOM : RTE_ERR_CUDA;                   \
+    }                                                                                        \
+  } while (0)
+#define RTE_TRY(expr)                \
+  do {                               \
+    int _s = (expr);                 \
+    if (_s != RTE_OK) return _s;     \
+  } while (0)
+#define RTE_ARG(cond, msg)                                 \
+  do {                                                     \
+    if (!(cond)) {                                         \
+      ::rte::set_error(std::string("invalid argument: ") + (msg)); \
+      return RTE_ERR_INVALID_ARG;                          \
+    }                                                      \
+  } while (0)
+
+// Device buffer owned by a handle.
+template <typename T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  int alloc(size_t count) {
+    release();
+    if (count == 0) return RTE_OK;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+      return RTE_ERR_OOM;
+    }
+    n = count;
+    return RTE_OK;
+  }
+  int ensure(size_t count) { return count <= n && p ? RTE_OK : alloc(count); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  ~DevBuf() { release(); }
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+};
+
+// Per-instance geometry as seen by the kernels.
+struct InstInfo {
+  int nx, ny;          // cells
+  long long off;       // dof offset in a scalar vector
+  int ndof;            // nx*ny*nd
+  double hx, hy;       // cell sizes
+};
+
+// A unique in-plane direction (duplicates over +-Omega_z merged, weights summed).
+struct UDir {
+  double ax, ay;       // |Omega_x|, |Omega_y| (2D); |mu| in ax (1D)
+  double w;            // merged weight
+  int sx, sy;          // signs of Omega_x, Omega_y (+1/-1)
+  int quadrant;        // 2D: 0 (+,+), 1 (-,+), 2 (+,-), 3 (-,-); 1D: 0 (mu>0), 1 (mu<0)
+  int ndup;            // number of original directions mapped here
+  int dup[4];          // their original indices (ndup <= 4)
+};
+
+// Sweep task: one warp sweeps D unique directions of one quadrant of one instance.
+struct SweepTask {
+  int b;       // instance
+  int u0;      // first unique direction (directions u0..u0+D-1 share a quadrant)
+  int t;       // task index within the instance (partial-sum slot)
+  int pad;
+};
+
+}  // namespace rte
+
+struct rte_problem {
+  int dim = 2, B = 0, nd = 4, ndir = 0, nu = 0, R = 1, rx = 1, ry = 1;
+  std::vector<int> nx, ny;
+  std::vector<long long> off;        // [B+1]
+  long long ntot = 0;
+  double box[4] = {0, 1, 0, 1};
+  double g = 0.0, src_q = 0.0, src_box[4] = {0, 0, 0, 0};
+  std::vector<double> ss, sa;        // [B][R] host copies
+  std::vector<double> om_x, om_y, om_z, w;  // [ndir] quadrature (paper order)
+  std::vector<int> uniq_of_dir;      // [ndir]
+  std::vector<rte::UDir> udir;       // [nu], grouped by quadrant, quadrant-major
+  std::vector<int> quad_start;       // [nquad+1] first unique dir of each quadrant
+  std::vector<rte::InstInfo> inst;   // [B]
+  // device state
+  rte::DevBuf<rte::InstInfo> d_inst;
+  rte::DevBuf<rte::UDir> d_udir;
+  rte::DevBuf<double> d_sig_s, d_sig_t;       // [B][R]
+  rte::DevBuf<float> d_sig_s32;               // [B][R]
+  rte::DevBuf<double> d_G;                    // [ntot] source moments
+  rte::DevBuf<double> d_linv64;               // [B][nu][R][nd*nd]
+  rte::DevBuf<float> d_linv32;
+  // sweep scratch (grown on demand)
+  rte::DevBuf<unsigned char> d_partial;       // partial scalar fluxes per task
+  rte::DevBuf<rte::SweepTask> d_tasks;
+  int tasks_D = -1;                           // directions per task of the cached task list
+  int ntasks = 0, tasks_per_inst = 0;
+  rte::DevBuf<int> d_active;                  // [B] instance mask (1 = active), all 1 by default
+  rte::DevBuf<double> d_tmp64;                // [ntot] temporaries
+  rte::DevBuf<double> d_wq;                   // [ndir] quadrature weights (paper order)
+};
+
+namespace rte {
+// problem.cu
+int upload_params(rte_problem* p);
+// sweep.cu: generic launcher.
+//   src:  input vector (dtype in_f64 ? double : float)
+//   mode: 0 phi = T s ; 1 w = z - T(Sigma_s z) ; 2 r = b - (z - T(Sigma_s z)) ; 3 b~ (src = G, bc)
+//   compute_f64: arithmetic of the sweep; out_f64: type of out and b
+enum SweepMode { MODE_T = 0, MODE_OP = 1, MODE_RES = 2, MODE_RHS = 3 };
+int launch_T(rte_problem* p, int mode, bool compute_f64, const void* src, bool in_f64, const void* bvec,
+             void* out, bool out_f64, const int* d_active, cudaStream_t st);
+int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st);
+int launch_scalar_flux(rte_problem* p, bool f64, const void* psi, void* phi, cudaStream_t st);
+// forward operator (D_u + Sigma_t) x for unique direction u of instance b (FP64), used offline
+int launch_forward(rte_problem* p, int b, int u, const double* x, double* y, const double* sig_t_override,
+                   cudaStream_t st);
+}  // namespace rte

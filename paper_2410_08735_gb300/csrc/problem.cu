@@ -1,0 +1,367 @@
+// Problem setup (paper Sec. 2): quadrature, mesh/region maps, source moments and
+// the per-(instance, direction, region) inverses of the cell blocks of D_j + Sigma_t.
+//
+// With the orthonormal tensor-Legendre basis eta_ab = p_a(x) q_b(y) on a uniform
+// Cartesian cell, every cell block of the upwind DG operator (eq. DG, eq. upwind)
+// is the Kronecker sum
+//     L = alpha K (x) I + beta I (x) K + sigma_t I,  K = [[1, sqrt3], [-sqrt3, 3]],
+// alpha = |Omega_x|/h_x, beta = |Omega_y|/h_y, written in the frame reflected so
+// that both direction components are positive (odd modes change sign).  In 1D
+// (P1, Sec. appendix A slab) L = alpha K + sigma_t I.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace rte {
+
+// n-point Gauss-Legendre nodes (ascending) and weights by Newton's method on P_n.
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 1; k < n; ++k) {
+        double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p0 = 1.0; p1 = z; }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 1; k < n; ++k) {
+      double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0);
+      p0 = p1;
+      p1 = p2;
+    }
+    if (n == 1) { p0 = 1.0; p1 = z; }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return x[a] < x[b]; });
+  std::vector<double> xs(n), ws(n);
+  for (int i = 0; i < n; ++i) { xs[i] = x[idx[i]]; ws[i] = w[idx[i]]; }
+  x = xs;
+  w = ws;
+}
+
+// Integrals of the two orthonormal Legendre modes of a cell [xl, xl+h] over [lo, hi] (inside the cell).
+static void mode_integrals(double xl, double h, double lo, double hi, double* I) {
+  double xc = xl + 0.5 * h;
+  double a = 2.0 * (lo - xc) / h, b = 2.0 * (hi - xc) / h;
+  I[0] = (hi - lo) / std::sqrt(h);
+  I[1] = std::sqrt(3.0 / h) * (h / 4.0) * (b * b - a * a);
+}
+
+__global__ void k_linv(int B, int nu, int R, int dim, const InstInfo* inst, const UDir* ud,
+                       const double* sig_t, double* out64, float* out32) {
+  long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long total = (long long)B * nu * R;
+  if (tid >= total) return;
+  int r = (int)(tid % R);
+  int u = (int)((tid / R) % nu);
+  int b = (int)(tid / ((long long)R * nu));
+  const double s3 = 1.7320508075688772;
+  const double K[4] = {1.0, s3, -s3, 3.0};
+  double sg = sig_t[(size_t)b * R + r];
+  int nd = dim == 2 ? 4 : 2;
+  double A[16], X[16];
+  if (dim == 2) {
+    double al = ud[u].ax / inst[b].hx, be = ud[u].ay / inst[b].hy;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) {
+        int a = i & 1, bb = i >> 1, c = j & 1, d = j >> 1;
+        double v = 0.0;
+        if (bb == d) v += al * K[a * 2 + c];
+        if (a == c) v += be * K[bb * 2 + d];
+        if (i == j) v += sg;
+        A[i * 4 + j] = v;
+      }
+  } else {
+    double al = ud[u].ax / inst[b].hx;
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j) A[i * 2 + j] = al * K[i * 2 + j] + (i == j ? sg : 0.0);
+  }
+  // Gauss-Jordan with partial pivoting
+  for (int i = 0; i < nd * nd; ++i) X[i] = (i / nd == i % nd) ? 1.0 : 0.0;
+  for (int c = 0; c < nd; ++c) {
+    int piv = c;
+    double best = fabs(A[c * nd + c]);
+    for (int i = c + 1; i < nd; ++i)
+      if (fabs(A[i * nd + c]) > best) { best = fabs(A[i * nd + c]); piv = i; }
+    if (piv != c)
+      for (int j = 0; j < nd; ++j) {
+        double t = A[c * nd + j]; A[c * nd + j] = A[piv * nd + j]; A[piv * nd + j] = t;
+        t = X[c * nd + j]; X[c * nd + j] = X[piv * nd + j]; X[piv * nd + j] = t;
+      }
+    double inv = 1.0 / A[c * nd + c];
+    for (int j = 0; j < nd; ++j) { A[c * nd + j] *= inv; X[c * nd + j] *= inv; }
+    for (int i = 0; i < nd; ++i) {
+      if (i == c) continue;
+      double f = A[i * nd + c];
+      for (int j = 0; j < nd; ++j) { A[i * nd + j] -= f * A[c * nd + j]; X[i * nd + j] -= f * X[c * nd + j]; }
+    }
+  }
+  size_t base = (size_t)tid * nd * nd;
+  for (int i = 0; i < nd * nd; ++i) {
+    out64[base + i] = X[i];
+    out32[base + i] = (float)X[i];
+  }
+}
+
+int upload_params(rte_problem* p) {
+  std::vector<double> st(p->ss.size());
+  std::vector<float> s32(p->ss.size());
+  for (size_t i = 0; i < st.size(); ++i) {
+    st[i] = p->ss[i] + p->sa[i];
+    s32[i] = (float)p->ss[i];
+  }
+  RTE_CHECK_CUDA(cudaMemcpy(p->d_sig_s.p, p->ss.data(), st.size() * 8, cudaMemcpyHostToDevice));
+  RTE_CHECK_CUDA(cudaMemcpy(p->d_sig_t.p, st.data(), st.size() * 8, cudaMemcpyHostToDevice));
+  RTE_CHECK_CUDA(cudaMemcpy(p->d_sig_s32.p, s32.data(), s32.size() * 4, cudaMemcpyHostToDevice));
+  long long total = (long long)p->B * p->nu * p->R;
+  int threads = 128;
+  k_linv<<<(unsigned)((total + threads - 1) / threads), threads>>>(p->B, p->nu, p->R, p->dim, p->d_inst.p,
+                                                                  p->d_udir.p, p->d_sig_t.p, p->d_linv64.p,
+                                                                  p->d_linv32.p);
+  RTE_CHECK_CUDA(cudaGetLastError());
+  RTE_CHECK_CUDA(cudaDeviceSynchronize());
+  return RTE_OK;
+}
+
+static int create_impl(const rte_problem_desc* d, rte_problem* p) {
+  RTE_ARG(d->dim == 1 || d->dim == 2, "dim must be 1 or 2");
+  RTE_ARG(d->n_instances >= 1, "n_instances must be >= 1");
+  RTE_ARG(d->nx != nullptr && (d->dim == 1 || d->ny != nullptr), "nx/ny arrays required");
+  RTE_ARG(d->sigma_s != nullptr && d->sigma_a != nullptr, "sigma_s/sigma_a arrays required");
+  RTE_ARG(d->n_polar >= 1 && d->n_polar <= 64, "n_polar must be in [1, 64]");
+  RTE_ARG(d->rx >= 1 && (d->dim == 1 || d->ry >= 1), "region grid must be positive");
+  RTE_ARG(d->box[1] > d->box[0] && (d->dim == 1 || d->box[3] > d->box[2]), "empty domain box");
+  if (d->dim == 2) RTE_ARG(d->n_azim >= 4 && d->n_azim % 4 == 0 && d->n_azim <= 256,
+                           "n_azim must be a positive multiple of 4 (no axis-parallel directions)");
+  if (d->dim == 1) RTE_ARG(d->n_polar % 2 == 0, "1D n_polar must be even");
+  p->dim = d->dim;
+  p->B = d->n_instances;
+  p->nd = d->dim == 2 ? 4 : 2;
+  p->rx = d->rx;
+  p->ry = d->dim == 2 ? d->ry : 1;
+  p->R = p->rx * p->ry;
+  std::memcpy(p->box, d->box, sizeof(p->box));
+  p->g = d->inflow_g;
+  p->src_q = d->src_q;
+  std::memcpy(p->src_box, d->src_box, sizeof(p->src_box));
+  p->nx.resize(p->B);
+  p->ny.resize(p->B);
+  p->off.assign(p->B + 1, 0);
+  p->inst.resize(p->B);
+  for (int b = 0; b < p->B; ++b) {
+    p->nx[b] = d->nx[b];
+    p->ny[b] = d->dim == 2 ? d->ny[b] : 1;
+    RTE_ARG(p->nx[b] >= 1 && p->ny[b] >= 1 && p->nx[b] <= 8192 && p->ny[b] <= 8192, "mesh size out of range");
+    RTE_ARG(p->nx[b] % p->rx == 0 && p->ny[b] % p->ry == 0, "region grid must divide every mesh");
+    long long nb = (long long)p->nx[b] * p->ny[b] * p->nd;
+    p->off[b + 1] = p->off[b] + nb;
+    InstInfo& in = p->inst[b];
+    in.nx = p->nx[b];
+    in.ny = p->ny[b];
+    in.off = p->off[b];
+    in.ndof = (int)nb;
+    in.hx = (d->box[1] - d->box[0]) / p->nx[b];
+    in.hy = d->dim == 2 ? (d->box[3] - d->box[2]) / p->ny[b] : 1.0;
+  }
+  p->ntot = p->off[p->B];
+  size_t nR = (size_t)p->B * p->R;
+  p->ss.assign(d->sigma_s, d->sigma_s + nR);
+  p->sa.assign(d->sigma_a, d->sigma_a + nR);
+  for (size_t i = 0; i < nR; ++i)
+    RTE_ARG(p->ss[i] >= 0.0 && p->sa[i] >= 0.0 && std::isfinite(p->ss[i]) && std::isfinite(p->sa[i]),
+            "cross sections must be finite and non-negative");
+  // quadrature (Sec. 2.1) and unique in-plane directions
+  std::vector<double> zx, zw;
+  gauss_legendre(d->n_polar, zx, zw);
+  if (p->dim == 1) {
+    p->ndir = d->n_polar;
+    for (int j = 0; j < p->ndir; ++j) {
+      p->om_x.push_back(zx[j]);
+      p->om_y.push_back(0.0);
+      p->om_z.push_back(0.0);
+      p->w.push_back(zw[j] / 2.0);
+    }
+    // unique = all; quadrant 0: mu > 0 (ascending index), quadrant 1: mu < 0
+    p->uniq_of_dir.assign(p->ndir, -1);
+    p->quad_start.assign(3, 0);
+    for (int q = 0; q < 2; ++q) {
+      p->quad_start[q] = (int)p->udir.size();
+      for (int j = 0; j < p->ndir; ++j) {
+        bool pos = p->om_x[j] > 0;
+        if ((q == 0) != pos) continue;
+        UDir u{};
+        u.ax = std::fabs(p->om_x[j]);
+        u.ay = 0.0;
+        u.w = p->w[j];
+        u.sx = pos ? 1 : -1;
+        u.sy = 1;
+        u.quadrant = q;
+        u.ndup = 1;
+        u.dup[0] = j;
+        p->uniq_of_dir[j] = (int)p->udir.size();
+        p->udir.push_back(u);
+      }
+    }
+    p->quad_start[2] = (int)p->udir.size();
+  } else {
+    int nt = d->n_azim, nz = d->n_polar;
+    p->ndir = nt * nz;
+    for (int j2 = 0; j2 < nz; ++j2)
+      for (int j1 = 0; j1 < nt; ++j1) {
+        double th = (2.0 * (j1 + 1) - 1.0) * M_PI / nt;
+        double s = std::sqrt(1.0 - zx[j2] * zx[j2]);
+        p->om_x.push_back(std::cos(th) * s);
+        p->om_y.push_back(std::sin(th) * s);
+        p->om_z.push_back(zx[j2]);
+        p->w.push_back(zw[j2] / 2.0 / nt);
+      }
+    // +-Omega_z pairs (j2, nz-1-j2) share (Omega_x, Omega_y): merge them
+    p->uniq_of_dir.assign(p->ndir, -1);
+    std::vector<UDir> all;
+    std::vector<std::vector<int>> members;
+    for (int j2 = 0; j2 < (nz + 1) / 2; ++j2)
+      for (int j1 = 0; j1 < nt; ++j1) {
+        int ja = j2 * nt + j1, jb = (nz - 1 - j2) * nt + j1;
+        UDir u{};
+        u.ax = std::fabs(p->om_x[ja]);
+        u.ay = std::fabs(p->om_y[ja]);
+        u.sx = p->om_x[ja] > 0 ? 1 : -1;
+        u.sy = p->om_y[ja] > 0 ? 1 : -1;
+        u.quadrant = (u.sx < 0 ? 1 : 0) + (u.sy < 0 ? 2 : 0);
+        u.ndup = (ja == jb) ? 1 : 2;
+        u.dup[0] = ja;
+        u.dup[1] = jb;
+        u.w = p->w[ja] + (ja == jb ? 0.0 : p->w[jb]);
+        all.push_back(u);
+      }
+    p->quad_start.assign(5, 0);
+    for (int q = 0; q < 4; ++q) {
+      p->quad_start[q] = (int)p->udir.size();
+      for (auto& u : all)
+        if (u.quadrant == q) {
+          for (int k = 0; k < u.ndup; ++k) p->uniq_of_dir[u.dup[k]] = (int)p->udir.size();
+          p->udir.push_back(u);
+        }
+    }
+    p->quad_start[4] = (int)p->udir.size();
+  }
+  p->nu = (int)p->udir.size();
+  // source moments G_k = int_T G eta_k (closed form, exact for the box source)
+  std::vector<double> G(p->ntot, 0.0);
+  for (int b = 0; b < p->B; ++b) {
+    const InstInfo& in = p->inst[b];
+    for (int iy = 0; iy < in.ny; ++iy)
+      for (int ix = 0; ix < in.nx; ++ix) {
+        double xl = p->box[0] + ix * in.hx;
+        double lo = std::max(xl, p->src_box[0]), hi = std::min(xl + in.hx, p->src_box[1]);
+        if (hi <= lo) continue;
+        double Ix[2];
+        mode_integrals(xl, in.hx, lo, hi, Ix);
+        long long c = (long long)iy * in.nx + ix;
+        if (p->dim == 1) {
+          G[in.off + 2 * c] = p->src_q * Ix[0];
+          G[in.off + 2 * c + 1] = p->src_q * Ix[1];
+          continue;
+        }
+        double yl = p->box[2] + iy * in.hy;
+        double ylo = std::max(yl, p->src_box[2]), yhi = std::min(yl + in.hy, p->src_box[3]);
+        if (yhi <= ylo) continue;
+        double Iy[2];
+        mode_integrals(yl, in.hy, ylo, yhi, Iy);
+        for (int k = 0; k < 4; ++k) G[in.off + 4 * c + k] = p->src_q * Ix[k & 1] * Iy[k >> 1];
+      }
+  }
+  // device buffers
+  RTE_TRY(p->d_inst.alloc(p->B));
+  RTE_TRY(p->d_udir.alloc(p->nu));
+  RTE_TRY(p->d_sig_s.alloc(nR));
+  RTE_TRY(p->d_sig_t.alloc(nR));
+  RTE_TRY(p->d_sig_s32.alloc(nR));
+  RTE_TRY(p->d_G.alloc(p->ntot));
+  size_t nl = (size_t)p->B * p->nu * p->R * p->nd * p->nd;
+  RTE_TRY(p->d_linv64.alloc(nl));
+  RTE_TRY(p->d_linv32.alloc(nl));
+  RTE_TRY(p->d_active.alloc(p->B));
+  RTE_TRY(p->d_wq.alloc(p->ndir));
+  RTE_CHECK_CUDA(cudaMemcpy(p->d_inst.p, p->inst.data(), p->B * sizeof(InstInfo), cudaMemcpyHostToDevice));
+  RTE_CHECK_CUDA(cudaMemcpy(p->d_udir.p, p->udir.data(), p->nu * sizeof(UDir), cudaMemcpyHostToDevice));
+  RTE_CHECK_CUDA(cudaMemcpy(p->d_G.p, G.data(), p->ntot * 8, cudaMemcpyHostToDevice));
+  RTE_CHECK_CUDA(cudaMemcpy(p->d_wq.p, p->w.data(), p->ndir * 8, cudaMemcpyHostToDevice));
+  std::vector<int> ones(p->B, 1);
+  RTE_CHECK_CUDA(cudaMemcpy(p->d_active.p, ones.data(), p->B * sizeof(int), cudaMemcpyHostToDevice));
+  return upload_params(p);
+}
+
+}  // namespace rte
+
+extern "C" {
+
+int rte_problem_create(const rte_problem_desc* desc, rte_problem_t* out) {
+  RTE_ARG(desc != nullptr && out != nullptr, "null descriptor or output handle");
+  *out = nullptr;
+  rte_problem* p = new rte_problem();
+  int s = rte::create_impl(desc, p);
+  if (s != RTE_OK) {
+    delete p;
+    return s;
+  }
+  *out = p;
+  return RTE_OK;
+}
+
+int rte_problem_destroy(rte_problem_t p) {
+  if (p) {
+    cudaDeviceSynchronize();
+    delete p;
+  }
+  return RTE_OK;
+}
+
+int rte_problem_get_info(rte_problem_t p, rte_problem_info* info) {
+  RTE_ARG(p != nullptr && info != nullptr, "null handle or info");
+  info->dim = p->dim;
+  info->n_instances = p->B;
+  info->n_directions = p->ndir;
+  info->n_unique_directions = p->nu;
+  info->dofs_per_cell = p->nd;
+  info->n_regions = p->R;
+  info->n_dof_total = p->ntot;
+  info->n_angular_total = (long long)p->ndir * p->ntot;
+  return RTE_OK;
+}
+
+int rte_problem_offsets(rte_problem_t p, long long* offsets) {
+  RTE_ARG(p != nullptr && offsets != nullptr, "null handle or offsets");
+  for (int b = 0; b <= p->B; ++b) offsets[b] = p->off[b];
+  return RTE_OK;
+}
+
+int rte_problem_set_params(rte_problem_t p, const double* sigma_s, const double* sigma_a) {
+  RTE_ARG(p != nullptr && sigma_s != nullptr && sigma_a != nullptr, "null handle or parameter array");
+  size_t nR = (size_t)p->B * p->R;
+  for (size_t i = 0; i < nR; ++i)
+    RTE_ARG(sigma_s[i] >= 0.0 && sigma_a[i] >= 0.0 && std::isfinite(sigma_s[i]) && std::isfinite(sigma_a[i]),
+            "cross sections must be finite and non-negative");
+  p->ss.assign(sigma_s, sigma_s + nR);
+  p->sa.assign(sigma_a, sigma_a + nR);
+  return rte::upload_params(p);
+}
+
+}  // extern "C"

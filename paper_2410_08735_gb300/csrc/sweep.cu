@@ -1,0 +1,502 @@
+// Transport sweep kernels (paper Sec. 3.1 eq. SI-equation and Sec. 3.2 eq. memory-efficient-SI /
+// memory-efficient-rte):
+//
+//   psi_j = (D_j + Sigma_t)^{-1} s        one block Gauss-Seidel pass in upwind order per direction
+//   T s   = sum_j omega_j psi_j            fused: psi is never stored
+//   A~ z  = z - T (Sigma_s z)              fused Sigma_s scaling on load, subtraction in the reduce
+//
+// 2D work decomposition.  A task is (instance, quadrant, chunk of D unique directions); one warp
+// runs one task.  Lane l owns mesh rows l, l+32, l+64, ... (rows counted in the upwind y order) and
+// marches along its row in the upwind x order.  The 32 rows of a band form a diagonal wavefront:
+// lane l handles column i of band k at step k*P + l + i (P = max(nx, 32)), so the y-inflow of a cell
+// is the y-outflow its lower neighbour produced one step earlier, received with one warp shuffle;
+// the x-inflow is the lane's own previous cell (registers).  Band k+1's first row takes its y-inflow
+// from band k's last row through a per-column buffer in shared memory.  Each lane keeps D directions
+// in flight per cell (independent dependency chains: instruction-level parallelism), shares the
+// cell's source load between them, and accumulates omega_j psi_j in registers.  Every task writes one
+// partial scalar flux; a second kernel sums the partials of an instance in a fixed order, so results
+// are deterministic and independent of scheduling.
+//
+// Cell solve.  In the frame reflected so that Omega_x, Omega_y > 0 (odd Legendre modes change
+// sign), the cell block is L = alpha K(x)I + beta I(x)K + sigma_t I with K = [[1, sqrt3], [-sqrt3, 3]];
+// the right-hand side gets alpha phat_a tx_b + beta phat_b ty_a from the upwind traces, phat =
+// (1, -sqrt3), tx_b = psi_0b + sqrt3 psi_1b (x-outflow trace), ty_a = psi_a0 + sqrt3 psi_a1; L^{-1}
+// per (instance, direction, region) is precomputed (problem.cu) and staged in shared memory.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace rte {
+
+struct SweepArgs {
+  const InstInfo* inst;
+  const UDir* udir;
+  const SweepTask* tasks;
+  int ntasks;
+  const void* linv;     // compute type, [B][nu][R][nd*nd]
+  const void* sig_s;    // compute type, [B][R]; null: no Sigma_s scaling of the input
+  const void* src;      // input type, scalar vector
+  int with_bc;
+  double g;
+  void* partial;        // compute type, [tasks_per_inst * off_b + t * N_b + i]
+  int tasks_per_inst;
+  void* psi;            // compute type, angular vector, or null
+  int ndir, nu, R, rx, ry;
+  const int* active;    // [B] or null
+  int smem_per_warp;    // elements of the compute type
+};
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  __device__ static void load(const float* p, float& a, float& b, float& c, float& d) {
+    float4 v = *reinterpret_cast<const float4*>(p);
+    a = v.x; b = v.y; c = v.z; d = v.w;
+  }
+  __device__ static void store(float* p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+  }
+};
+template <>
+struct Vec4<double> {
+  __device__ static void load(const double* p, double& a, double& b, double& c, double& d) {
+    double2 v0 = reinterpret_cast<const double2*>(p)[0];
+    double2 v1 = reinterpret_cast<const double2*>(p)[1];
+    a = v0.x; b = v0.y; c = v1.x; d = v1.y;
+  }
+  __device__ static void store(double* p, double a, double b, double c, double d) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+  }
+};
+
+template <typename T, typename TI, int D, bool ANG>
+__global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int tid = blockIdx.x * wpb + warp;
+  if (tid >= a.ntasks) return;
+  const SweepTask tk = a.tasks[tid];
+  if (a.active && !a.active[tk.b]) return;
+  const InstInfo in = a.inst[tk.b];
+  const int nx = in.nx, ny = in.ny, R = a.R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tab = reinterpret_cast<T*>(smem_raw) + (size_t)warp * a.smem_per_warp;
+  T* ybuf = tab + D * R * 16;
+  const T* linv = reinterpret_cast<const T*>(a.linv) + ((size_t)tk.b * a.nu + tk.u0) * R * 16;
+  for (int e = lane; e < D * R * 16; e += 32) tab[e] = linv[e];
+  T al[D], be[D], wg[D];
+  const int sx = a.udir[tk.u0].sx, sy = a.udir[tk.u0].sy;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const UDir u = a.udir[tk.u0 + d];
+    al[d] = (T)(u.ax / in.hx);
+    be[d] = (T)(u.ay / in.hy);
+    wg[d] = (T)u.w;
+  }
+  const T bnd = a.with_bc ? (T)(a.g * sqrt(in.hx * in.hy)) : (T)0;
+  const T* sig_s = a.sig_s ? reinterpret_cast<const T*>(a.sig_s) + (size_t)tk.b * R : nullptr;
+  const TI* src = reinterpret_cast<const TI*>(a.src) + in.off;
+  T* part = reinterpret_cast<T*>(a.partial) + (size_t)a.tasks_per_inst * in.off + (size_t)tk.t * in.ndof;
+  T* psi = ANG ? reinterpret_cast<T*>(a.psi) + (size_t)a.ndir * in.off : nullptr;
+  const T S3 = (T)1.7320508075688772;
+  const int P = nx > 32 ? nx : 32;
+  const int nbands = (ny + 31) >> 5;
+  const int nsteps = (nbands - 1) * P + 31 + nx;
+  const int cx = nx / a.rx, cy = ny / a.ry;
+  T tx0[D], tx1[D], ty0[D], ty1[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) { tx0[d] = tx1[d] = ty0[d] = ty1[d] = (T)0; }
+  __syncwarp();
+  for (int s = 0; s < nsteps; ++s) {
+    const int rel = s - lane;
+    const int band = rel >= 0 ? rel / P : -1;
+    const int col = rel - band * P;
+    const int row = band * 32 + lane;
+    const bool act = rel >= 0 && band < nbands && col < nx && row < ny;
+    T yi0[D], yi1[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      yi0[d] = __shfl_up_sync(0xffffffffu, ty0[d], 1);
+      yi1[d] = __shfl_up_sync(0xffffffffu, ty1[d], 1);
+    }
+    if (act) {
+      if (lane == 0) {
+        if (band == 0) {
+#pragma unroll
+          for (int d = 0; d < D; ++d) { yi0[d] = bnd; yi1[d] = (T)0; }
+        } else {
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            yi0[d] = ybuf[(d * nx + col) * 2];
+            yi1[d] = ybuf[(d * nx + col) * 2 + 1];
+          }
+        }
+      }
+      if (col == 0) {
+#pragma unroll
+        for (int d = 0; d < D; ++d) { tx0[d] = bnd; tx1[d] = (T)0; }
+      }
+      const int ix = sx > 0 ? col : nx - 1 - col;
+      const int iy = sy > 0 ? row : ny - 1 - row;
+      const long long c = (long long)iy * nx + ix;
+      const int reg = (iy / cy) * a.rx + ix / cx;
+      T s0, s1, s2, s3;
+      {
+        TI v0, v1, v2, v3;
+        Vec4<TI>::load(src + 4 * c, v0, v1, v2, v3);
+        s0 = (T)v0; s1 = (T)v1; s2 = (T)v2; s3 = (T)v3;
+      }
+      if (sig_s) {
+        const T sg = sig_s[reg];
+        s0 *= sg; s1 *= sg; s2 *= sg; s3 *= sg;
+      }
+      s1 = sx > 0 ? s1 : -s1;
+      s2 = sy > 0 ? s2 : -s2;
+      s3 = (sx * sy) > 0 ? s3 : -s3;
+      T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const T ax = al[d], by = be[d];
+        const T r0 = s0 + ax * tx0[d] + by * yi0[d];
+        const T r1 = s1 - S3 * ax * tx0[d] + by * yi1[d];
+        const T r2 = s2 + ax * tx1[d] - S3 * by * yi0[d];
+        const T r3 = s3 - S3 * (ax * tx1[d] + by * yi1[d]);
+        const T* L = tab + (d * R + reg) * 16;
+        const T p0 = L[0] * r0 + L[1] * r1 + L[2] * r2 + L[3] * r3;
+        const T p1 = L[4] * r0 + L[5] * r1 + L[6] * r2 + L[7] * r3;
+        const T p2 = L[8] * r0 + L[9] * r1 + L[10] * r2 + L[11] * r3;
+        const T p3 = L[12] * r0 + L[13] * r1 + L[14] * r2 + L[15] * r3;
+        tx0[d] = p0 + S3 * p1;
+        tx1[d] = p2 + S3 * p3;
+        ty0[d] = p0 + S3 * p2;
+        ty1[d] = p1 + S3 * p3;
+        acc0 += wg[d] * p0;
+        acc1 += wg[d] * p1;
+        acc2 += wg[d] * p2;
+        acc3 += wg[d] * p3;
+        if (lane == 31 && band + 1 < nbands) {
+          ybuf[(d * nx + col) * 2] = ty0[d];
+          ybuf[(d * nx + col) * 2 + 1] = ty1[d];
+        }
+        if (ANG) {
+          const UDir u = a.udir[tk.u0 + d];
+          const T q1 = sx > 0 ? p1 : -p1, q2 = sy > 0 ? p2 : -p2, q3 = (sx * sy) > 0 ? p3 : -p3;
+          for (int k = 0; k < u.ndup; ++k)
+            Vec4<T>::store(psi + (size_t)u.dup[k] * in.ndof + 4 * c, p0, q1, q2, q3);
+        }
+      }
+      acc1 = sx > 0 ? acc1 : -acc1;
+      acc2 = sy > 0 ? acc2 : -acc2;
+      acc3 = (sx * sy) > 0 ? acc3 : -acc3;
+      Vec4<T>::store(part + 4 * c, acc0, acc1, acc2, acc3);
+    }
+    __syncwarp();
+  }
+}
+
+// 1D slab (P1, 2 dofs per cell): one thread per (instance, direction) marches its chain.
+template <typename T, typename TI, bool ANG>
+__global__ void k_sweep1d(SweepArgs a) {
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= a.ntasks) return;
+  const SweepTask tk = a.tasks[tid];
+  if (a.active && !a.active[tk.b]) return;
+  const InstInfo in = a.inst[tk.b];
+  const UDir u = a.udir[tk.u0];
+  const int nx = in.nx, R = a.R, cx = nx / a.rx;
+  const T al = (T)(u.ax / in.hx), wg = (T)u.w;
+  const T S3 = (T)1.7320508075688772;
+  const T* linv = reinterpret_cast<const T*>(a.linv) + ((size_t)tk.b * a.nu + tk.u0) * R * 4;
+  const T* sig_s = a.sig_s ? reinterpret_cast<const T*>(a.sig_s) + (size_t)tk.b * R : nullptr;
+  const TI* src = reinterpret_cast<const TI*>(a.src) + in.off;
+  T* part = reinterpret_cast<T*>(a.partial) + (size_t)a.tasks_per_inst * in.off + (size_t)tk.t * in.ndof;
+  T* psi = ANG ? reinterpret_cast<T*>(a.psi) + (size_t)a.ndir * in.off + (size_t)u.dup[0] * in.ndof : nullptr;
+  T tx = a.with_bc ? (T)(a.g * sqrt(in.hx)) : (T)0;
+  for (int col = 0; col < nx; ++col) {
+    const int ix = u.sx > 0 ? col : nx - 1 - col;
+    const int reg = ix / cx;
+    T s0 = (T)src[2 * ix], s1 = (T)src[2 * ix + 1];
+    if (sig_s) { s0 *= sig_s[reg]; s1 *= sig_s[reg]; }
+    s1 = u.sx > 0 ? s1 : -s1;
+    const T r0 = s0 + al * tx, r1 = s1 - S3 * al * tx;
+    const T* L = linv + reg * 4;
+    const T p0 = L[0] * r0 + L[1] * r1, p1 = L[2] * r0 + L[3] * r1;
+    tx = p0 + S3 * p1;
+    const T q1 = u.sx > 0 ? p1 : -p1;
+    part[2 * ix] = wg * p0;
+    part[2 * ix + 1] = wg * q1;
+    if (ANG) { psi[2 * ix] = p0; psi[2 * ix + 1] = q1; }
+  }
+}
+
+// out = sum_t partial[t]  (mode T),  z - sum (mode OP),  b - (z - sum) (mode RES); one instance per blockIdx.y.
+template <typename TP, typename TZ, typename TO>
+__global__ void k_reduce(const TP* partial, int ntask, const InstInfo* inst, int mode, const TZ* z, const TO* bvec,
+                         TO* out, const int* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const InstInfo in = inst[b];
+  const TP* pp = partial + (size_t)ntask * in.off;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) {
+    TP s = 0;
+    for (int t = 0; t < ntask; ++t) s += pp[(size_t)t * in.ndof + i];
+    TO v = (TO)s;
+    if (mode == MODE_OP) v = (TO)z[in.off + i] - v;
+    if (mode == MODE_RES) v = bvec[in.off + i] - ((TO)z[in.off + i] - v);
+    out[in.off + i] = v;
+  }
+}
+
+// phi = sum_j omega_j psi_j from an angular vector (K3).
+template <typename T>
+__global__ void k_scalar_flux(const T* psi, const double* w, int ndir, const InstInfo* inst, T* phi) {
+  const int b = blockIdx.y;
+  const InstInfo in = inst[b];
+  const T* pb = psi + (size_t)ndir * in.off;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) {
+    T s = 0;
+    for (int j = 0; j < ndir; ++j) s += (T)w[j] * pb[(size_t)j * in.ndof + i];
+    phi[in.off + i] = s;
+  }
+}
+
+// ----------------------------------------------------------------- host side
+static int pick_D(const rte_problem* p, bool f64) {
+  if (p->dim == 1) return 1;
+  int nq = p->quad_start[1] - p->quad_start[0];
+  // directions per warp: enough independent chains to hide latency, few enough for registers
+  const int cands64[] = {4, 2, 1};
+  const int cands32[] = {8, 4, 2, 1};
+  long long cells = 0;
+  for (int b = 0; b < p->B; ++b) cells += (long long)p->nx[b] * p->ny[b];
+  if (f64) {
+    for (int d : cands64)
+      if (nq % d == 0) return d;
+  } else {
+    for (int d : cands32)
+      if (nq % d == 0) return d;
+  }
+  return 1;
+}
+
+static int ensure_tasks(rte_problem* p, int D) {
+  if (p->tasks_D == D && p->d_tasks.p) return RTE_OK;
+  std::vector<SweepTask> tasks;
+  int per_inst = 0;
+  if (p->dim == 1) {
+    per_inst = p->nu;
+    for (int b = 0; b < p->B; ++b)
+      for (int u = 0; u < p->nu; ++u) tasks.push_back(SweepTask{b, u, u, 0});
+  } else {
+    int nquad = 4;
+    for (int q = 0; q < nquad; ++q) {
+      int nq = p->quad_start[q + 1] - p->quad_start[q];
+      per_inst += nq / D;
+    }
+    for (int b = 0; b < p->B; ++b) {
+      int t = 0;
+      for (int q = 0; q < nquad; ++q)
+        for (int u0 = p->quad_start[q]; u0 < p->quad_start[q + 1]; u0 += D) tasks.push_back(SweepTask{b, u0, t++, 0});
+    }
+    // longest tasks first (instances with the most cells): a static longest-processing-time order
+    std::stable_sort(tasks.begin(), tasks.end(), [&](const SweepTask& x, const SweepTask& y) {
+      return (long long)p->nx[x.b] * p->ny[x.b] > (long long)p->nx[y.b] * p->ny[y.b];
+    });
+  }
+  RTE_TRY(p->d_tasks.alloc(tasks.size()));
+  RTE_CHECK_CUDA(cudaMemcpy(p->d_tasks.p, tasks.data(), tasks.size() * sizeof(SweepTask), cudaMemcpyHostToDevice));
+  p->ntasks = (int)tasks.size();
+  p->tasks_per_inst = per_inst;
+  p->tasks_D = D;
+  return RTE_OK;
+}
+
+template <typename T, typename TI, bool ANG>
+static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) {
+  if (p->dim == 1) {
+    int threads = 128;
+    k_sweep1d<T, TI, ANG><<<(a.ntasks + threads - 1) / threads, threads, 0, st>>>(a);
+    RTE_CHECK_CUDA(cudaGetLastError());
+    return RTE_OK;
+  }
+  int maxnx = 0;
+  for (int b = 0; b < p->B; ++b) maxnx = std::max(maxnx, p->nx[b]);
+  a.smem_per_warp = D * p->R * 16 + D * maxnx * 2;
+  a.smem_per_warp = (a.smem_per_warp + 3) & ~3;
+  size_t per_warp = (size_t)a.smem_per_warp * sizeof(T);
+  int wpb = 4;
+  while (wpb > 1 && per_warp * wpb > 96 * 1024) --wpb;
+  size_t smem = per_warp * wpb;
+  if (smem > 227 * 1024) {
+    set_error("sweep: shared-memory table too large for this mesh/region count");
+    return RTE_ERR_UNSUPPORTED;
+  }
+  int blocks = (a.ntasks + wpb - 1) / wpb;
+#define RTE_SWEEP_CASE(DD)                                                                                  \
+  case DD: {                                                                                                \
+    auto kern = k_sweep2d<T, TI, DD, ANG>;                                                                  \
+    static size_t smem_set = 48 * 1024;                                                                     \
+    if (smem > smem_set) {                                                                                  \
+      RTE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));   \
+      smem_set = smem;                                                                                      \
+    }                                                                                                       \
+    kern<<<blocks, wpb * 32, smem, st>>>(a);                                                                \
+    break;                                                                                                  \
+  }
+  switch (D) {
+    RTE_SWEEP_CASE(1)
+    RTE_SWEEP_CASE(2)
+    RTE_SWEEP_CASE(4)
+    RTE_SWEEP_CASE(8)
+    default:
+      set_error("sweep: unsupported directions-per-warp");
+      return RTE_ERR_UNSUPPORTED;
+  }
+#undef RTE_SWEEP_CASE
+  RTE_CHECK_CUDA(cudaGetLastError());
+  return RTE_OK;
+}
+
+static void fill_args(rte_problem* p, SweepArgs& a, bool f64) {
+  std::memset(&a, 0, sizeof(a));
+  a.inst = p->d_inst.p;
+  a.udir = p->d_udir.p;
+  a.tasks = p->d_tasks.p;
+  a.ntasks = p->ntasks;
+  a.linv = f64 ? (const void*)p->d_linv64.p : (const void*)p->d_linv32.p;
+  a.g = p->g;
+  a.tasks_per_inst = p->tasks_per_inst;
+  a.ndir = p->ndir;
+  a.nu = p->nu;
+  a.R = p->R;
+  a.rx = p->rx;
+  a.ry = p->ry;
+}
+
+static int ensure_partial(rte_problem* p, bool f64) {
+  size_t bytes = (size_t)p->tasks_per_inst * p->ntot * (f64 ? 8 : 4);
+  return p->d_partial.ensure(bytes);
+}
+
+int launch_T(rte_problem* p, int mode, bool f64, const void* src, bool in_f64, const void* bvec, void* out,
+             bool out_f64, const int* d_active, cudaStream_t st) {
+  int D = pick_D(p, f64);
+  RTE_TRY(ensure_tasks(p, D));
+  RTE_TRY(ensure_partial(p, f64));
+  SweepArgs a;
+  fill_args(p, a, f64);
+  a.src = mode == MODE_RHS ? (const void*)p->d_G.p : src;
+  bool src64 = mode == MODE_RHS ? true : in_f64;
+  a.with_bc = mode == MODE_RHS ? 1 : 0;
+  a.sig_s = (mode == MODE_OP || mode == MODE_RES) ? (f64 ? (const void*)p->d_sig_s.p : (const void*)p->d_sig_s32.p)
+                                                   : nullptr;
+  a.partial = p->d_partial.p;
+  a.active = d_active;
+  if (f64) {
+    if (src64) RTE_TRY((launch_sweep_t<double, double, false>(p, D, a, st)));
+    else RTE_TRY((launch_sweep_t<double, float, false>(p, D, a, st)));
+  } else {
+    if (src64) RTE_TRY((launch_sweep_t<float, double, false>(p, D, a, st)));
+    else RTE_TRY((launch_sweep_t<float, float, false>(p, D, a, st)));
+  }
+  int maxn = 0;
+  for (int b = 0; b < p->B; ++b) maxn = std::max(maxn, (int)(p->off[b + 1] - p->off[b]));
+  dim3 grid((maxn + 255) / 256, p->B);
+  int rmode = mode == MODE_RHS ? MODE_T : mode;
+  if (rmode != MODE_T && !in_f64 && out_f64) {
+    set_error("launch_T: FP32 operator input with FP64 output is not supported");
+    return RTE_ERR_UNSUPPORTED;
+  }
+#define RTE_RED(TP, TZ, TO)                                                                                   \
+  k_reduce<TP, TZ, TO><<<grid, 256, 0, st>>>(reinterpret_cast<const TP*>(p->d_partial.p), p->tasks_per_inst,    \
+                                             p->d_inst.p, rmode, reinterpret_cast<const TZ*>(src),              \
+                                             reinterpret_cast<const TO*>(bvec), reinterpret_cast<TO*>(out), d_active)
+  if (f64) {
+    if (out_f64) RTE_RED(double, double, double);
+    else RTE_RED(double, float, float);
+  } else {
+    if (out_f64) RTE_RED(float, double, double);
+    else RTE_RED(float, float, float);
+  }
+#undef RTE_RED
+  RTE_CHECK_CUDA(cudaGetLastError());
+  return RTE_OK;
+}
+
+int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st) {
+  int D = pick_D(p, f64);
+  RTE_TRY(ensure_tasks(p, D));
+  RTE_TRY(ensure_partial(p, f64));
+  SweepArgs a;
+  fill_args(p, a, f64);
+  a.src = src;
+  a.with_bc = with_bc ? 1 : 0;
+  a.partial = p->d_partial.p;
+  a.psi = psi;
+  if (f64) RTE_TRY((launch_sweep_t<double, double, true>(p, D, a, st)));
+  else RTE_TRY((launch_sweep_t<float, float, true>(p, D, a, st)));
+  return RTE_OK;
+}
+
+int launch_scalar_flux(rte_problem* p, bool f64, const void* psi, void* phi, cudaStream_t st) {
+  DevBuf<double>* wdev = &p->d_wq;
+  int maxn = 0;
+  for (int b = 0; b < p->B; ++b) maxn = std::max(maxn, (int)(p->off[b + 1] - p->off[b]));
+  dim3 grid((maxn + 255) / 256, p->B);
+  if (f64)
+    k_scalar_flux<double><<<grid, 256, 0, st>>>(reinterpret_cast<const double*>(psi), wdev->p, p->ndir, p->d_inst.p,
+                                                 reinterpret_cast<double*>(phi));
+  else
+    k_scalar_flux<float><<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(psi), wdev->p, p->ndir, p->d_inst.p,
+                                                reinterpret_cast<float*>(phi));
+  RTE_CHECK_CUDA(cudaGetLastError());
+  return RTE_OK;
+}
+
+}  // namespace rte
+
+extern "C" {
+
+static int check_dtype(int dtype) {
+  RTE_ARG(dtype == RTE_F64 || dtype == RTE_F32, "dtype must be RTE_F64 or RTE_F32");
+  return RTE_OK;
+}
+
+int rte_sweep(rte_problem_t p, int dtype, const void* src, int with_bc, void* psi, void* stream) {
+  RTE_ARG(p && src && psi, "null handle or pointer");
+  RTE_TRY(check_dtype(dtype));
+  return rte::launch_angular(p, dtype == RTE_F64, src, with_bc, psi, (cudaStream_t)stream);
+}
+
+int rte_scalar_flux(rte_problem_t p, int dtype, const void* psi, void* phi, void* stream) {
+  RTE_ARG(p && psi && phi, "null handle or pointer");
+  RTE_TRY(check_dtype(dtype));
+  return rte::launch_scalar_flux(p, dtype == RTE_F64, psi, phi, (cudaStream_t)stream);
+}
+
+int rte_apply_T(rte_problem_t p, int dtype, const void* s, void* phi, void* stream) {
+  RTE_ARG(p && s && phi, "null handle or pointer");
+  RTE_TRY(check_dtype(dtype));
+  bool f = dtype == RTE_F64;
+  return rte::launch_T(p, rte::MODE_T, f, s, f, nullptr, phi, f, nullptr, (cudaStream_t)stream);
+}
+
+int rte_apply_op(rte_problem_t p, int dtype, const void* z, void* w, void* stream) {
+  RTE_ARG(p && z && w, "null handle or pointer");
+  RTE_TRY(check_dtype(dtype));
+  bool f = dtype == RTE_F64;
+  return rte::launch_T(p, rte::MODE_OP, f, z, f, nullptr, w, f, nullptr, (cudaStream_t)stream);
+}
+
+int rte_rhs(rte_problem_t p, int dtype, void* btilde, void* stream) {
+  RTE_ARG(p && btilde, "null handle or pointer");
+  RTE_TRY(check_dtype(dtype));
+  bool f = dtype == RTE_F64;
+  return rte::launch_T(p, rte::MODE_RHS, f, nullptr, true, nullptr, btilde, f, nullptr, (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+"""GPU parity of the transport kernels (sweep, quadrature, T, A~, b~) against the oracle."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import transport as OT
+
+from gpu_common import lib, oracle_problems, rel, spec1d, spec2d, split, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+# meshes spanning several 32-row bands with ragged tails, nx both below and above the warp width
+MESHES_2D = [(38, 46), (12, 70), (64, 64), (8, 8), (96, 34)]
+
+
+def _params(spec, seed):
+    return wl.draw_params(spec, spec.n_instances, seed)
+
+
+@pytest.mark.parametrize("mesh", MESHES_2D)
+def test_apply_op_fp64_matches_oracle(mesh):
+    torch = torch_cuda()
+    B = lib()
+    spec = spec2d([mesh[0]], [mesh[1]], n_polar=4, n_azim=8)
+    ss, sa = _params(spec, 11)
+    gp = B.Problem(spec, ss, sa)
+    ops = oracle_problems(spec, ss, sa)
+    rng = np.random.default_rng(5)
+    z = rng.standard_normal(gp.n_dof)
+    w = torch.empty(gp.n_dof, dtype=torch.float64, device="cuda")
+    gp.apply_op(to_dev(z), w)
+    ref = OT.Atilde_apply(ops[0], z)
+    assert rel(w.cpu().numpy(), ref) < 1e-13
+    # T itself
+    gp.apply_T(to_dev(z), w)
+    assert rel(w.cpu().numpy(), OT.T_apply(ops[0], z)) < 1e-13
+
+
+def test_batched_uneven_instances_match_oracle_per_instance():
+    torch = torch_cuda()
+    B = lib()
+    spec = spec2d([32, 64, 40, 16], [32, 64, 24, 48], n_polar=4, n_azim=8, inflow_g=0.3)
+    ss, sa = _params(spec, 12)
+    gp = B.Problem(spec, ss, sa)
+    ops = oracle_problems(spec, ss, sa)
+    rng = np.random.default_rng(6)
+    z = rng.standard_normal(gp.n_dof)
+    w = torch.empty(gp.n_dof, dtype=torch.float64, device="cuda")
+    gp.apply_op(to_dev(z), w)
+    bt = torch.empty_like(w)
+    gp.rhs(bt)
+    for b, (wb, zb, bb) in enumerate(zip(split(w.cpu().numpy(), gp.offsets), split(z, gp.offsets),
+                                         split(bt.cpu().numpy(), gp.offsets))):
+        assert rel(wb, OT.Atilde_apply(ops[b], zb)) < 1e-13
+        assert rel(bb, OT.rhs_btilde(ops[b])) < 1e-13
+
+
+@pytest.mark.parametrize("g", [0.0, 0.7])
+def test_rhs_fp64_matches_oracle(g):
+    torch = torch_cuda()
+    B = lib()
+    spec = spec2d([40], [36], n_polar=4, n_azim=8, inflow_g=g)
+    ss, sa = _params(spec, 13)
+    gp = B.Problem(spec, ss, sa)
+    op = oracle_problems(spec, ss, sa)[0]
+    bt = torch.empty(gp.n_dof, dtype=torch.float64, device="cuda")
+    gp.rhs(bt)
+    assert rel(bt.cpu().numpy(), OT.rhs_btilde(op)) < 1e-13
+
+
+def test_angular_sweep_and_scalar_flux_match_oracle():
+    torch = torch_cuda()
+    B = lib()
+    spec = spec2d([34], [40], n_polar=4, n_azim=8, inflow_g=0.25)
+    ss, sa = _params(spec, 14)
+    gp = B.Problem(spec, ss, sa)
+    op = oracle_problems(spec, ss, sa)[0]
+    rng = np.random.default_rng(7)
+    s = rng.standard_normal(gp.n_dof)
+    psi = torch.empty(gp.n_directions * gp.n_dof, dtype=torch.float64, device="cuda")
+    gp.sweep(to_dev(s), psi, with_bc=True)
+    ref = np.stack([op.sweep(j, s + op.gbc(j)) for j in range(op.ndir)])
+    got = psi.cpu().numpy().reshape(op.ndir, op.ndof)
+    for j in range(op.ndir):
+        assert rel(got[j], ref[j]) < 1e-13, j
+    phi = torch.empty(gp.n_dof, dtype=torch.float64, device="cuda")
+    gp.scalar_flux(psi, phi)
+    assert rel(phi.cpu().numpy(), OT.scalar_flux(op, ref)) < 1e-13
+
+
+def test_fp32_kernels_close_to_oracle():
+    torch = torch_cuda()
+    B = lib()
+    spec = spec2d([48], [40], n_polar=4, n_azim=8, inflow_g=0.5)
+    ss, sa = _params(spec, 15)
+    gp = B.Problem(spec, ss, sa)
+    op = oracle_problems(spec, ss, sa)[0]
+    rng = np.random.default_rng(8)
+    z = rng.standard_normal(gp.n_dof)
+    w = torch.empty(gp.n_dof, dtype=torch.float32, device="cuda")
+    gp.apply_op(to_dev(z, torch.float32), w)
+    assert rel(w.cpu().numpy(), OT.Atilde_apply(op, z.astype(np.float32).astype(np.float64))) < 2e-5
+    bt = torch.empty(gp.n_dof, dtype=torch.float32, device="cuda")
+    gp.rhs(bt)
+    assert rel(bt.cpu().numpy(), OT.rhs_btilde(op)) < 2e-5
+    psi = torch.empty(gp.n_directions * gp.n_dof, dtype=torch.float32, device="cuda")
+    gp.sweep(to_dev(z, torch.float32), psi, with_bc=False)
+    ref = np.stack([op.sweep(j, z.astype(np.float32).astype(np.float64)) for j in range(op.ndir)])
+    assert rel(psi.cpu().numpy().reshape(op.ndir, -1), ref) < 2e-5
+
+
+def test_slab_1d_matches_oracle():
+    torch = torch_cuda()
+    B = lib()
+    spec = spec1d([128, 64, 20], n_polar=16, inflow_g=0.4)
+    ss, sa = _params(spec, 16)
+    gp = B.Problem(spec, ss, sa)
+    ops = oracle_problems(spec, ss, sa)
+    rng = np.random.default_rng(9)
+    z = rng.standard_normal(gp.n_dof)
+    w = torch.empty(gp.n_dof, dtype=torch.float64, device="cuda")
+    gp.apply_op(to_dev(z), w)
+    bt = torch.empty_like(w)
+    gp.rhs(bt)
+    psi = torch.empty(gp.n_directions * gp.n_dof, dtype=torch.float64, device="cuda")
+    gp.sweep(to_dev(z), psi, with_bc=True)
+    psi_h = psi.cpu().numpy()
+    for b, op in enumerate(ops):
+        o = gp.offsets
+        assert rel(w.cpu().numpy()[o[b]:o[b + 1]], OT.Atilde_apply(op, z[o[b]:o[b + 1]])) < 1e-13
+        assert rel(bt.cpu().numpy()[o[b]:o[b + 1]], OT.rhs_btilde(op)) < 1e-13
+        pb = psi_h[op.ndir * o[b]:op.ndir * o[b + 1]].reshape(op.ndir, -1)
+        for j in range(op.ndir):
+            assert rel(pb[j], op.sweep(j, z[o[b]:o[b + 1]] + op.gbc(j))) < 1e-13
+
+
+def test_results_are_deterministic():
+    torch = torch_cuda()
+    B = lib()
+    spec = spec2d([64, 32], [64, 32], n_polar=4, n_azim=16)
+    ss, sa = _params(spec, 17)
+    gp = B.Problem(spec, ss, sa)
+    z = to_dev(np.random.default_rng(1).standard_normal(gp.n_dof))
+    w1 = torch.empty_like(z)
+    w2 = torch.empty_like(z)
+    gp.apply_op(z, w1)
+    gp.apply_op(z, w2)
+    assert torch.equal(w1, w2)
+
+
+def test_full_size_square_64_matches_oracle():
+    """The 64x64, 8x16-direction workload at full size: one A~ apply and b~ against the oracle."""
+    torch = torch_cuda()
+    B = lib()
+    spec = wl.config(2)
+    ss, sa = wl.draw_params(spec, 1, wl.seed_for(2, 1))
+    gp = B.Problem(spec, ss, sa)
+    op = oracle_problems(spec, ss, sa)[0]
+    z = np.random.default_rng(2).standard_normal(gp.n_dof)
+    w = torch.empty(gp.n_dof, dtype=torch.float64, device="cuda")
+    gp.apply_op(to_dev(z), w)
+    assert rel(w.cpu().numpy(), OT.Atilde_apply(op, z)) < 1e-13
+    gp.rhs(w)
+    assert rel(w.cpu().numpy(), OT.rhs_btilde(op)) < 1e-13
