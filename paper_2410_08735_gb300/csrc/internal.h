@@ -3,6 +3,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -122,6 +123,7 @@ struct rte_problem {
   rte::DevBuf<int> d_active;                  // [B] instance mask (1 = active), all 1 by default
   rte::DevBuf<double> d_tmp64;                // [ntot] temporaries
   rte::DevBuf<double> d_wq;                   // [ndir] quadrature weights (paper order)
+  std::shared_ptr<void> krylov_ws;            // FGMRES workspace (krylov.cu), grown on demand
 };
 
 namespace rte {
@@ -136,7 +138,8 @@ int launch_T(rte_problem* p, int mode, bool compute_f64, const void* src, bool i
              void* out, bool out_f64, const int* d_active, cudaStream_t st);
 int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st);
 int launch_scalar_flux(rte_problem* p, bool f64, const void* psi, void* phi, cudaStream_t st);
-// forward operator (D_u + Sigma_t) x for unique direction u of instance b (FP64), used offline
-int launch_forward(rte_problem* p, int b, int u, const double* x, double* y, const double* sig_t_override,
-                   cudaStream_t st);
+// forward operator y = (D_u + sigma_t) x (FP64) for ncol columns on one mesh; used offline
+int launch_forward_cols(int dim, int nx, int ny, double hx, double hy, const UDir& u, int rx, int ry,
+                        const double* sig_t_reg, const double* x, long long ldx, double* y, long long ldy, int ncol,
+                        cudaStream_t st);
 }  // namespace rte

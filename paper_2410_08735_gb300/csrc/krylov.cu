@@ -1,0 +1,616 @@
+// Flexible GMRES (paper Sec. 4.2, Alg. 1) for A~ phi = b~, batched over parameter instances.
+//
+// All instances of a problem advance in lock step: one launch per step covers every instance that
+// is still active in the current cycle.  Per iteration j (0-based):
+//   z_j = M_j^{-1} v_j              ROMSAD (romsad.cu) for j < window, then the post-window operator
+//   w   = A~ z_j                    fused sweep (sweep.cu), written straight into v_{j+1}
+//   MGS: h_ij = w . v_i, w -= h_ij v_i (i = 0..j, sequentially), h_{j+1,j} = ||w||, v_{j+1} = w / h
+//   Givens: rotate column j of H, new rotation, |g_{j+1}| = residual estimate
+// At the end of a cycle y = R^{-1} g and phi += Z y.  MGS, Givens and all Krylov vectors are FP64.
+//
+// Readings where Alg. 1 is silent: stop when |g_{j+1}| / ||b~|| <= rtol; happy breakdown when
+// h_{j+1,j} <= 1e-14 ||w|| (before orthogonalisation); restart: phi0 <- phi, r0 = b~ - A~ phi0
+// (one sweep); after convergence the true residual is recomputed once (optional) and the solve
+// restarts from it if it exceeds 2 rtol.  The window counts iterations from the start of the solve.
+//
+// Mixed mode: FP64 iterative refinement.  r_k = b~ - A~ phi_k in FP64 (FP64 sweep), inner FGMRES on
+// A~ d = r_k with FP32 sweeps and FP32 ROM products (MGS/Givens FP64) to inner_rtol, phi += d.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "romsad.h"
+
+namespace rte {
+
+enum CycleFlag { RUN = 0, STOP_CONV = 1, STOP_BREAK = 2, STOP_RESTART = 3, STOP_NUMERIC = 4 };
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum (deterministic: fixed tree), result broadcast to all threads.
+__device__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < nw ? sh[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) sh[32] = t;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+__global__ void k_norm(const double* x, const InstInfo* inst, const int* active, double* out) {
+  __shared__ double sh[33];
+  const int b = blockIdx.x;
+  if (active && !active[b]) return;
+  const InstInfo in = inst[b];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) {
+    double v = x[in.off + i];
+    s += v * v;
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[b] = sqrt(s);
+}
+
+__global__ void k_linf(const double* x, const InstInfo* inst, double* out) {
+  __shared__ double sh[33];
+  const int b = blockIdx.x;
+  const InstInfo in = inst[b];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) s = fmax(s, fabs(x[in.off + i]));
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+    out[b] = m;
+  }
+}
+
+// dst = src * (1/scale_b) on active instances; grid (chunks, B)
+__global__ void k_scale(double* dst, const double* src, const double* scale, const InstInfo* inst,
+                        const int* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const InstInfo in = inst[b];
+  const double s = 1.0 / scale[b];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x)
+    dst[in.off + i] = src[in.off + i] * s;
+}
+
+__global__ void k_copy_active(double* dst, const double* src, const InstInfo* inst, const int* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const InstInfo in = inst[b];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x)
+    dst[in.off + i] = src[in.off + i];
+}
+
+// Modified Gram-Schmidt of w = V[j+1] against V[0..j] (Alg. 1), one block per active instance.
+// Writes H[b][:, j] (column-major, ld m+1) and a breakdown flag; normalises V[j+1].
+__global__ void k_mgs(double* V, long long ntot, int j, int m, const InstInfo* inst, const int* active, double* H,
+                      int* brk) {
+  __shared__ double sh[33];
+  const int b = blockIdx.x;
+  if (!active[b]) return;
+  const InstInfo in = inst[b];
+  double* w = V + (size_t)(j + 1) * ntot + in.off;
+  double* h = H + ((size_t)b * m + j) * (m + 1);
+  double s = 0.0;
+  for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) s += w[i] * w[i];
+  const double w0 = sqrt(block_sum(s, sh));
+  for (int q = 0; q <= j; ++q) {
+    const double* vq = V + (size_t)q * ntot + in.off;
+    s = 0.0;
+    for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) s += w[i] * vq[i];
+    const double hq = block_sum(s, sh);
+    for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) w[i] -= hq * vq[i];
+    if (threadIdx.x == 0) h[q] = hq;
+  }
+  s = 0.0;
+  for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) s += w[i] * w[i];
+  const double hn = sqrt(block_sum(s, sh));
+  const bool breakdown = !(hn > 1e-14 * w0);
+  if (threadIdx.x == 0) {
+    h[j + 1] = hn;
+    brk[b] = breakdown ? 1 : 0;
+  }
+  if (!breakdown) {
+    const double inv = 1.0 / hn;
+    for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) w[i] *= inv;
+  }
+}
+
+// Givens update of column j for every active instance (thread per instance).
+__global__ void k_givens(double* H, double* cs, double* sn, double* g, int j, int m, int B, const int* active,
+                         const int* brk, const double* bnorm, double rtol, const int* iters_left, double* est,
+                         int* flag, int* kcols) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !active[b]) return;
+  double* h = H + ((size_t)b * m + j) * (m + 1);
+  double* c = cs + (size_t)b * m;
+  double* s = sn + (size_t)b * m;
+  double* gg = g + (size_t)b * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    const double t = c[i] * h[i] + s[i] * h[i + 1];
+    h[i + 1] = -s[i] * h[i] + c[i] * h[i + 1];
+    h[i] = t;
+  }
+  const double den = hypot(h[j], h[j + 1]);
+  double cj = 1.0, sj = 0.0;
+  if (den > 0.0) { cj = h[j] / den; sj = h[j + 1] / den; }
+  c[j] = cj;
+  s[j] = sj;
+  h[j] = den;
+  h[j + 1] = 0.0;
+  gg[j + 1] = -sj * gg[j];
+  gg[j] = cj * gg[j];
+  const double e = fabs(gg[j + 1]);
+  est[b] = e;
+  kcols[b] = j + 1;
+  int f = RUN;
+  if (!isfinite(e) || !isfinite(den)) f = STOP_NUMERIC;
+  else if (e <= rtol * bnorm[b]) f = STOP_CONV;
+  else if (brk[b]) f = STOP_BREAK;
+  else if (j + 1 == m || iters_left[b] <= 1) f = STOP_RESTART;
+  flag[b] = f;
+}
+
+// y = R^{-1} g (R: rotated H, upper triangular k x k), thread per instance with k > 0.
+__global__ void k_backsolve(const double* H, const double* g, int m, int B, const int* kcols, double* y) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const int k = kcols[b];
+  const double* Hb = H + (size_t)b * m * (m + 1);
+  const double* gg = g + (size_t)b * (m + 1);
+  double* yb = y + (size_t)b * m;
+  for (int i = k - 1; i >= 0; --i) {
+    double t = gg[i];
+    for (int q = i + 1; q < k; ++q) t -= Hb[(size_t)q * (m + 1) + i] * yb[q];
+    const double d = Hb[(size_t)i * (m + 1) + i];
+    yb[i] = d != 0.0 ? t / d : 0.0;
+  }
+}
+
+// phi += sum_c y_c Z_c for instances with k > 0; grid (chunks, B)
+__global__ void k_update(double* phi, const double* Z, long long ntot, int m, const InstInfo* inst, const int* kcols,
+                         const double* y) {
+  const int b = blockIdx.y;
+  const int k = kcols[b];
+  if (k <= 0) return;
+  const InstInfo in = inst[b];
+  __shared__ double ys[128];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) ys[q] = y[(size_t)b * m + q];
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) {
+    double s = phi[in.off + i];
+    for (int q = 0; q < k; ++q) s += ys[q] * Z[(size_t)q * ntot + in.off + i];
+    phi[in.off + i] = s;
+  }
+}
+
+// phi += d (FP64), all instances in mask
+__global__ void k_axpy_active(double* phi, const double* d, const InstInfo* inst, const int* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const InstInfo in = inst[b];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x)
+    phi[in.off + i] += d[in.off + i];
+}
+
+__global__ void k_zero_active(double* x, const InstInfo* inst, const int* active) {
+  const int b = blockIdx.y;
+  if (active && !active[b]) return;
+  const InstInfo in = inst[b];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) x[in.off + i] = 0.0;
+}
+
+// ----------------------------------------------------------------- host driver
+struct Ws {
+  int B = 0, m = 0;
+  long long ntot = 0;
+  bool withZ = false;
+  DevBuf<double> V, Z, H, cs, sn, g, y, bt, r, d, phi_in;
+  DevBuf<double> bnorm, beta, est, nrm;
+  DevBuf<int> active, brk, flag, kcols, iters_left, list;
+  DevBuf<double> rom_y, rom_c;
+  int alloc(rte_problem* p, int m_, bool withZ_) {
+    if (B == p->B && m == m_ && ntot == p->ntot && (withZ == withZ_ || !withZ_)) return RTE_OK;
+    B = p->B;
+    m = m_;
+    ntot = p->ntot;
+    withZ = withZ_ || withZ;
+    RTE_TRY(V.alloc((size_t)(m + 1) * ntot));
+    if (withZ) RTE_TRY(Z.alloc((size_t)m * ntot));
+    RTE_TRY(H.alloc((size_t)B * m * (m + 1)));
+    RTE_TRY(cs.alloc((size_t)B * m));
+    RTE_TRY(sn.alloc((size_t)B * m));
+    RTE_TRY(g.alloc((size_t)B * (m + 1)));
+    RTE_TRY(y.alloc((size_t)B * m));
+    RTE_TRY(bt.alloc(ntot));
+    RTE_TRY(r.alloc(ntot));
+    RTE_TRY(d.alloc(ntot));
+    RTE_TRY(bnorm.alloc(B));
+    RTE_TRY(beta.alloc(B));
+    RTE_TRY(est.alloc(B));
+    RTE_TRY(nrm.alloc(B));
+    RTE_TRY(active.alloc(B));
+    RTE_TRY(brk.alloc(B));
+    RTE_TRY(flag.alloc(B));
+    RTE_TRY(kcols.alloc(B));
+    RTE_TRY(iters_left.alloc(B));
+    RTE_TRY(list.alloc(B));
+    RTE_TRY(rom_y.alloc((size_t)B * 64));
+    RTE_TRY(rom_c.alloc((size_t)B * 64));
+    return RTE_OK;
+  }
+};
+
+struct SolveCtx {
+  rte_problem* p;
+  const romsad_t* roms;  // [B] or null
+  int m, window, post;
+  cudaStream_t st;
+  Ws* ws;
+};
+
+static dim3 vec_grid(rte_problem* p) {
+  int maxn = 0;
+  for (int b = 0; b < p->B; ++b) maxn = std::max(maxn, (int)(p->off[b + 1] - p->off[b]));
+  return dim3((maxn + 255) / 256, p->B);
+}
+
+// Per-instance outcome of one inner (or FP64) FGMRES run.
+struct RunStats {
+  std::vector<int> iterations, sweeps, restarts, status;
+  std::vector<double> est;
+};
+
+// Restarted FGMRES on A~ x = rhs for the instances with want[b] = 1.  x: initial guess (zero if
+// zero_guess) and result.  f64: sweep arithmetic.  true_check: recompute the residual after
+// convergence (FP64 sweep if f64).  it_base: iterations already done per instance (window count).
+static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess, const std::vector<int>& want,
+                      double rtol, int max_iter, bool f64, bool true_check, const std::vector<int>& it_base,
+                      RunStats& rs) {
+  rte_problem* p = C.p;
+  Ws& W = *C.ws;
+  const int B = p->B, m = C.m;
+  const long long ntot = p->ntot;
+  cudaStream_t st = C.st;
+  const dim3 vg = vec_grid(p);
+  rs.iterations.assign(B, 0);
+  rs.sweeps.assign(B, 0);
+  rs.restarts.assign(B, 0);
+  rs.status.assign(B, RTE_OK);
+  rs.est.assign(B, 0.0);
+  std::vector<int> act(want), hflag(B), hk(B);
+  std::vector<double> hb(B), hbn(B);
+  // ||rhs||
+  RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+  k_norm<<<B, 512, 0, st>>>(rhs, p->d_inst.p, W.active.p, W.bnorm.p);
+  // r0
+  if (zero_guess) {
+    k_copy_active<<<vg, 256, 0, st>>>(W.r.p, rhs, p->d_inst.p, W.active.p);
+    k_zero_active<<<vg, 256, 0, st>>>(x, p->d_inst.p, W.active.p);
+  } else {
+    RTE_TRY(launch_T(p, MODE_RES, f64, x, true, rhs, W.r.p, true, W.active.p, st));
+    for (int b = 0; b < B; ++b) rs.sweeps[b] += act[b];
+  }
+  RTE_CHECK_CUDA(cudaGetLastError());
+  RTE_CHECK_CUDA(cudaMemcpyAsync(hbn.data(), W.bnorm.p, B * 8, cudaMemcpyDeviceToHost, st));
+  RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+  for (int b = 0; b < B; ++b)
+    if (act[b] && hbn[b] == 0.0) { act[b] = 0; rs.est[b] = 0.0; }
+  double* Zbase = W.withZ ? W.Z.p : W.V.p;
+  while (true) {
+    // beta = ||r||
+    RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_norm<<<B, 512, 0, st>>>(W.r.p, p->d_inst.p, W.active.p, W.beta.p);
+    RTE_CHECK_CUDA(cudaMemcpyAsync(hb.data(), W.beta.p, B * 8, cudaMemcpyDeviceToHost, st));
+    RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+    int nact = 0;
+    for (int b = 0; b < B; ++b) {
+      if (!act[b]) continue;
+      if (!std::isfinite(hb[b])) { act[b] = 0; rs.status[b] = RTE_ERR_NUMERIC; continue; }
+      rs.est[b] = hb[b] / hbn[b];
+      if (hb[b] <= rtol * hbn[b]) { act[b] = 0; continue; }
+      if (rs.iterations[b] >= max_iter) { act[b] = 0; rs.status[b] = RTE_ERR_NOT_CONVERGED; continue; }
+      ++nact;
+    }
+    if (nact == 0) break;
+    // v_0 = r / beta, g = beta e_1
+    RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_scale<<<vg, 256, 0, st>>>(W.V.p, W.r.p, W.beta.p, p->d_inst.p, W.active.p);
+    {
+      std::vector<double> g0((size_t)B * (m + 1), 0.0);
+      std::vector<int> left(B, 0);
+      for (int b = 0; b < B; ++b) {
+        g0[(size_t)b * (m + 1)] = hb[b];
+        left[b] = max_iter - rs.iterations[b];
+      }
+      RTE_CHECK_CUDA(cudaMemcpyAsync(W.g.p, g0.data(), g0.size() * 8, cudaMemcpyHostToDevice, st));
+      RTE_CHECK_CUDA(cudaMemcpyAsync(W.iters_left.p, left.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+      RTE_CHECK_CUDA(cudaMemsetAsync(W.kcols.p, 0, B * sizeof(int), st));
+    }
+    std::vector<int> incycle(act);
+    std::vector<int> outcome(B, RUN);
+    for (int j = 0; j < m; ++j) {
+      // preconditioner
+      double* vj = W.V.p + (size_t)j * ntot;
+      double* zj = Zbase + (size_t)j * ntot;
+      if (W.withZ) {
+        // instances without ROM (or past the window with identity): copy; with ROM: apply per ROM group
+        std::vector<int> ident(B, 0);
+        std::vector<std::pair<romsad_t, int>> romlist;
+        for (int b = 0; b < B; ++b) {
+          if (!act[b]) continue;
+          romsad_t rb = C.roms ? C.roms[b] : nullptr;
+          const int jg = it_base[b] + rs.iterations[b] + 1;  // 1-based global iteration index
+          if (rb && (jg <= C.window || C.post == RTE_POST_ROM)) romlist.push_back({rb, b});
+          else ident[b] = 1;
+        }
+        RTE_CHECK_CUDA(cudaMemcpyAsync(W.brk.p, ident.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+        k_copy_active<<<vg, 256, 0, st>>>(zj, vj, p->d_inst.p, W.brk.p);
+        std::sort(romlist.begin(), romlist.end());
+        size_t s0 = 0;
+        while (s0 < romlist.size()) {
+          size_t s1 = s0;
+          std::vector<int> ids;
+          while (s1 < romlist.size() && romlist[s1].first == romlist[s0].first) ids.push_back(romlist[s1++].second);
+          RTE_CHECK_CUDA(cudaMemcpyAsync(W.list.p, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+          RTE_TRY(rom_apply_list(romlist[s0].first, p, W.list.p, (int)ids.size(), vj, zj, f64, W.rom_y.p, W.rom_c.p,
+                                 st));
+          s0 = s1;
+        }
+        RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+      }
+      // w = A~ z_j into V[j+1]
+      RTE_TRY(launch_T(p, MODE_OP, f64, zj, true, nullptr, W.V.p + (size_t)(j + 1) * ntot, true, W.active.p, st));
+      k_mgs<<<B, 1024, 0, st>>>(W.V.p, ntot, j, m, p->d_inst.p, W.active.p, W.H.p, W.brk.p);
+      k_givens<<<(B + 127) / 128, 128, 0, st>>>(W.H.p, W.cs.p, W.sn.p, W.g.p, j, m, B, W.active.p, W.brk.p,
+                                                W.bnorm.p, rtol, W.iters_left.p, W.est.p, W.flag.p, W.kcols.p);
+      RTE_CHECK_CUDA(cudaGetLastError());
+      RTE_CHECK_CUDA(cudaMemcpyAsync(hflag.data(), W.flag.p, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+      RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+      int still = 0;
+      std::vector<int> left(B, 0);
+      for (int b = 0; b < B; ++b) {
+        if (!act[b]) continue;
+        rs.iterations[b] += 1;
+        rs.sweeps[b] += 1;
+        if (hflag[b] != RUN) {
+          outcome[b] = hflag[b];
+          act[b] = 0;
+        } else {
+          ++still;
+        }
+        left[b] = max_iter - rs.iterations[b];
+      }
+      if (still == 0) break;
+      RTE_CHECK_CUDA(cudaMemcpyAsync(W.iters_left.p, left.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+      RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    // end of cycle: phi += Z y for the instances of this cycle
+    k_backsolve<<<(B + 127) / 128, 128, 0, st>>>(W.H.p, W.g.p, m, B, W.kcols.p, W.y.p);
+    k_update<<<vg, 256, 0, st>>>(x, Zbase, ntot, m, p->d_inst.p, W.kcols.p, W.y.p);
+    RTE_CHECK_CUDA(cudaGetLastError());
+    std::vector<double> hest(B);
+    RTE_CHECK_CUDA(cudaMemcpyAsync(hest.data(), W.est.p, B * 8, cudaMemcpyDeviceToHost, st));
+    RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+    // decide per instance: finished, check residual, or restart
+    std::vector<int> resid(B, 0);
+    for (int b = 0; b < B; ++b) {
+      if (!incycle[b]) continue;
+      rs.est[b] = hest[b] / hbn[b];
+      const int o = outcome[b];
+      if (o == STOP_NUMERIC) { rs.status[b] = RTE_ERR_NUMERIC; continue; }
+      if (o == STOP_CONV || o == STOP_BREAK) {
+        if (true_check) resid[b] = 1;  // verified below (uncounted check sweep)
+        continue;
+      }
+      // restart or iteration cap
+      if (rs.iterations[b] >= max_iter) { rs.status[b] = RTE_ERR_NOT_CONVERGED; continue; }
+      resid[b] = 2;
+    }
+    bool any = false;
+    for (int b = 0; b < B; ++b) any = any || resid[b];
+    if (!any) break;
+    std::vector<int> mask(B);
+    for (int b = 0; b < B; ++b) mask[b] = resid[b] ? 1 : 0;
+    RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, mask.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    RTE_TRY(launch_T(p, MODE_RES, f64, x, true, rhs, W.r.p, true, W.active.p, st));
+    for (int b = 0; b < B; ++b)
+      if (resid[b] == 2) { rs.sweeps[b] += 1; rs.restarts[b] += 1; }
+    for (int b = 0; b < B; ++b) act[b] = mask[b];
+    // check-sweep instances: the loop head computes beta and stops them if within 2 rtol
+    if (true_check) {
+      k_norm<<<B, 512, 0, st>>>(W.r.p, p->d_inst.p, W.active.p, W.nrm.p);
+      std::vector<double> hn(B);
+      RTE_CHECK_CUDA(cudaMemcpyAsync(hn.data(), W.nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
+      RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+      for (int b = 0; b < B; ++b) {
+        if (resid[b] != 1) continue;
+        if (hn[b] <= 2.0 * rtol * hbn[b] || rs.iterations[b] >= max_iter) {
+          act[b] = 0;
+          if (!(hn[b] <= 2.0 * rtol * hbn[b])) rs.status[b] = RTE_ERR_NOT_CONVERGED;
+        } else {
+          rs.restarts[b] += 1;
+        }
+      }
+    }
+  }
+  return RTE_OK;
+}
+
+static Ws* get_ws(rte_problem* p) {
+  if (!p->krylov_ws) p->krylov_ws = std::shared_ptr<void>(new Ws(), [](void* q) { delete static_cast<Ws*>(q); });
+  return static_cast<Ws*>(p->krylov_ws.get());
+}
+
+}  // namespace rte
+
+using namespace rte;
+
+extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_opts* o, const void* phi0, void* phi,
+                            fgmres_stats* stats, void* stream) {
+  RTE_ARG(p && o && phi && stats, "null handle or pointer");
+  RTE_ARG(o->restart >= 1 && o->restart <= 128, "restart must be in [1, 128]");
+  RTE_ARG(o->rtol > 0.0 && o->max_iter >= 1, "rtol must be > 0 and max_iter >= 1");
+  RTE_ARG(o->mode == RTE_MODE_FP64 || o->mode == RTE_MODE_MIXED, "unknown mode");
+  RTE_ARG(o->post_mode == RTE_POST_ROM || o->post_mode == RTE_POST_IDENTITY, "unknown post_mode");
+  if (roms)
+    for (int b = 0; b < p->B; ++b)
+      if (roms[b]) RTE_TRY(rom_check_mesh(roms[b], p, b));
+  cudaStream_t st = (cudaStream_t)stream;
+  bool any_rom = false;
+  if (roms)
+    for (int b = 0; b < p->B; ++b) any_rom = any_rom || roms[b] != nullptr;
+  Ws* ws = get_ws(p);
+  RTE_TRY(ws->alloc(p, o->restart, any_rom));
+  // output location: device pointer, or host pointer (solve into a device buffer, copy back)
+  cudaPointerAttributes attr;
+  bool host_out = false;
+  if (cudaPointerGetAttributes(&attr, phi) != cudaSuccess || attr.type == cudaMemoryTypeHost ||
+      attr.type == cudaMemoryTypeUnregistered) {
+    cudaGetLastError();
+    host_out = true;
+  }
+  double* x;
+  if (host_out) {
+    RTE_TRY(ws->phi_in.ensure(p->ntot));
+    x = ws->phi_in.p;
+  } else {
+    x = (double*)phi;
+  }
+  const int B = p->B;
+  SolveCtx C{p, roms, o->restart, o->window, o->post_mode, st, ws};
+  std::vector<int> all(B, 1), zero(B, 0);
+  // b~ (FP64 sweep, counted)
+  RTE_TRY(launch_T(p, MODE_RHS, true, nullptr, true, nullptr, ws->bt.p, true, nullptr, st));
+  const bool warm = o->warm_start && phi0 != nullptr;
+  if (warm) RTE_CHECK_CUDA(cudaMemcpyAsync(x, phi0, p->ntot * 8, cudaMemcpyDeviceToDevice, st));
+  std::vector<fgmres_stats> S(B);
+  for (int b = 0; b < B; ++b) {
+    std::memset(&S[b], 0, sizeof(fgmres_stats));
+    S[b].sweeps = 1;
+    S[b].sweeps_fp64 = 1;
+    S[b].true_rel_residual = NAN;
+    S[b].true_linf_residual = NAN;
+  }
+  if (o->mode == RTE_MODE_FP64) {
+    RunStats rs;
+    RTE_TRY(run_fgmres(C, ws->bt.p, x, !warm, all, o->rtol, o->max_iter, true, o->true_residual_check != 0, zero, rs));
+    for (int b = 0; b < B; ++b) {
+      S[b].iterations = rs.iterations[b];
+      S[b].sweeps += rs.sweeps[b];
+      S[b].sweeps_fp64 += rs.sweeps[b];
+      S[b].restarts = rs.restarts[b];
+      S[b].est_rel_residual = rs.est[b];
+      S[b].status = rs.status[b];
+    }
+  } else {
+    // FP64 iterative refinement around the FP32-sweep inner FGMRES
+    const dim3 vg = vec_grid(p);
+    std::vector<int> act(B, 1), it_done(B, 0);
+    if (warm) {
+      RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ws->r.p, true, nullptr, st));
+      for (int b = 0; b < B; ++b) { S[b].sweeps += 1; S[b].sweeps_fp64 += 1; }
+    } else {
+      RTE_CHECK_CUDA(cudaMemsetAsync(x, 0, p->ntot * 8, st));
+      RTE_CHECK_CUDA(cudaMemcpyAsync(ws->r.p, ws->bt.p, p->ntot * 8, cudaMemcpyDeviceToDevice, st));
+    }
+    std::vector<double> hb(B), hr(B);
+    RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_norm<<<B, 512, 0, st>>>(ws->bt.p, p->d_inst.p, ws->active.p, ws->nrm.p);
+    RTE_CHECK_CUDA(cudaMemcpyAsync(hb.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
+    RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+    for (int outer = 0; outer <= o->max_outer; ++outer) {
+      RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+      k_norm<<<B, 512, 0, st>>>(ws->r.p, p->d_inst.p, ws->active.p, ws->nrm.p);
+      RTE_CHECK_CUDA(cudaMemcpyAsync(hr.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
+      RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+      int nact = 0;
+      for (int b = 0; b < B; ++b) {
+        if (!act[b]) continue;
+        double rel = hb[b] > 0 ? hr[b] / hb[b] : 0.0;
+        S[b].true_rel_residual = rel;
+        S[b].est_rel_residual = rel;
+        if (!std::isfinite(rel)) { act[b] = 0; S[b].status = RTE_ERR_NUMERIC; continue; }
+        if (rel <= o->rtol) { act[b] = 0; continue; }
+        if (outer == o->max_outer || S[b].iterations >= o->max_iter) {
+          act[b] = 0;
+          S[b].status = RTE_ERR_NOT_CONVERGED;
+          continue;
+        }
+        ++nact;
+      }
+      if (nact == 0) break;
+      // inner solve A~ d = r (FP32 sweeps), zero guess
+      RunStats rs;
+      RTE_TRY(run_fgmres(C, ws->r.p, ws->d.p, true, act, o->inner_rtol, o->max_iter, false, false, zero, rs));
+      RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+      k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d.p, p->d_inst.p, ws->active.p);
+      // r = b~ - A~ x in FP64
+      RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ws->r.p, true, ws->active.p, st));
+      for (int b = 0; b < B; ++b) {
+        if (!act[b]) continue;
+        S[b].iterations += rs.iterations[b];
+        S[b].sweeps += rs.sweeps[b] + 1;
+        S[b].sweeps_fp64 += 1;
+        S[b].restarts += rs.restarts[b];
+        S[b].outer += 1;
+        if (rs.status[b] == RTE_ERR_NUMERIC) { act[b] = 0; S[b].status = RTE_ERR_NUMERIC; }
+      }
+    }
+  }
+  // FP64 true residual (l2, linf) for reporting; not counted as a solver sweep
+  if (o->mode == RTE_MODE_FP64 && o->true_residual_check) {
+    // the residual buffer already holds b~ - A~ phi for every instance that finished through the
+    // check; recompute it for the others (not converged / numeric)
+    std::vector<int> redo(B, 0);
+    bool any = false;
+    for (int b = 0; b < B; ++b) { redo[b] = S[b].status != RTE_OK; any = any || redo[b]; }
+    if (any) {
+      RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, redo.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+      RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ws->r.p, true, ws->active.p, st));
+    }
+  }
+  if (o->mode == RTE_MODE_MIXED || o->true_residual_check) {
+    std::vector<int> all1(B, 1);
+    RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, all1.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_norm<<<B, 512, 0, st>>>(ws->r.p, p->d_inst.p, ws->active.p, ws->nrm.p);
+    k_norm<<<B, 512, 0, st>>>(ws->bt.p, p->d_inst.p, ws->active.p, ws->beta.p);
+    k_linf<<<B, 512, 0, st>>>(ws->r.p, p->d_inst.p, ws->est.p);
+    std::vector<double> hn(B), hb(B), hl(B);
+    RTE_CHECK_CUDA(cudaMemcpyAsync(hn.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
+    RTE_CHECK_CUDA(cudaMemcpyAsync(hb.data(), ws->beta.p, B * 8, cudaMemcpyDeviceToHost, st));
+    RTE_CHECK_CUDA(cudaMemcpyAsync(hl.data(), ws->est.p, B * 8, cudaMemcpyDeviceToHost, st));
+    RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+    for (int b = 0; b < B; ++b) {
+      S[b].true_rel_residual = hb[b] > 0 ? hn[b] / hb[b] : 0.0;
+      S[b].true_linf_residual = hl[b];
+    }
+  }
+  if (host_out) {
+    RTE_CHECK_CUDA(cudaMemcpyAsync(phi, x, p->ntot * 8, cudaMemcpyDeviceToHost, st));
+    RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+  }
+  int ret = RTE_OK;
+  for (int b = 0; b < B; ++b) {
+    stats[b] = S[b];
+    if (S[b].status != RTE_OK && ret == RTE_OK) ret = S[b].status;
+  }
+  if (ret == RTE_ERR_NOT_CONVERGED) set_error("fgmres_solve: at least one instance missed its tolerance");
+  if (ret == RTE_ERR_NUMERIC) set_error("fgmres_solve: NaN/Inf met");
+  return ret;
+}

@@ -1,0 +1,42 @@
+// ROMSAD data structures shared by romsad.cu, greedy.cu and krylov.cu.
+#pragma once
+#include "internal.h"
+
+struct romsad {
+  // mesh the ROM belongs to (must match every instance it is applied to)
+  int dim = 2, nx = 0, ny = 0, nd = 4, ndir = 0, nu = 0, R = 1, rx = 1, ry = 1;
+  double box[4] = {0, 1, 0, 1};
+  int N = 0;        // dofs of the mesh
+  int r = 0;        // rank
+  int rmax = 0;     // capacity of the device arrays (columns)
+  // stored direction blocks of U: a = 0..nA-1 (all N_Omega directions, or the unique in-plane ones
+  // with multiplicity); P = sum_a mult_a U_a, W = sum_a wA_a U_a
+  int nA = 0;
+  std::vector<int> uidx;       // [nA] unique direction of block a
+  std::vector<double> mult;    // [nA]
+  std::vector<double> wA;      // [nA]
+  // device arrays
+  rte::DevBuf<double> P, W;    // [N][rmax] (dof-major, rank contiguous)
+  rte::DevBuf<float> P32, W32;
+  rte::DevBuf<double> U;       // [rmax][nA][N] (greedy / create_from_basis; may be empty after load)
+  rte::DevBuf<double> Y;       // [rmax][nA][N]: D_u U_a (transport without collision), greedy only
+  // affine reduced operators, host, row-major [r][r]
+  std::vector<double> A_D;     // sum_a mult_a U_a^T D_u U_a
+  std::vector<double> T_R;     // [R][r][r] sum_a mult_a U_a^T chi_R U_a
+  std::vector<double> S_R;     // [R][r][r] P^T chi_R W
+  rte::DevBuf<double> d_aff;   // [(1 + 2R)][r][r] device copy: A_D, T_R..., S_R...
+};
+
+namespace rte {
+// Assemble and LU-factor U^T A_mu U for the listed instances of p (device), then
+// c = A_r^{-1} y per instance: y [ninst][r] in, c [ninst][r] out (FP64).
+int rom_small_solve(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* y, double* c,
+                    cudaStream_t st);
+// z_b = v_b + W (U^T A_mu U)^{-1} P^T Sigma_s v_b for the listed instances (all on the ROM's mesh).
+// f64: FP64 P/W and vectors; otherwise FP32 P/W products with FP64 vectors in and out.
+int rom_apply_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* v, double* z,
+                   bool f64, double* scratch_y, double* scratch_c, cudaStream_t st);
+int rom_check_mesh(const romsad* rom, const rte_problem* p, int b);
+int rom_upload_affine(romsad* rom);
+int rom_build_operators_from_U(romsad* rom, rte_problem* tmpl, int inst, cudaStream_t st);
+}  // namespace rte

@@ -264,6 +264,79 @@ __global__ void k_scalar_flux(const T* psi, const double* w, int ndir, const Ins
   }
 }
 
+
+// Forward operator y = (D_u + sigma_t) x for one unique direction u (no inflow-boundary term, as in
+// the definition of D_j, Sec. 2.3): in the reflected frame y' = L0 x' - alpha phat_a tx_b(x'_up)
+// - beta phat_b ty_a(x'_down) + sigma_t x', L0 = alpha K(x)I + beta I(x)K.  One thread per
+// (cell, column); columns x[col*ldx + i], y[col*ldy + i].  sig_t: per-region array or null (= 0).
+__global__ void k_forward(int dim, int nx, int ny, double hx, double hy, UDir u, int rx, int ry,
+                          const double* sig_t, const double* x, long long ldx, double* y, long long ldy, int ncol) {
+  const long long ncell = (long long)nx * ny;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (tid >= ncell * ncol) return;
+  const int col = (int)(tid / ncell);
+  const long long c = tid % ncell;
+  const int ix = (int)(c % nx), iy = (int)(c / nx);
+  const double S3 = 1.7320508075688772;
+  const int reg = (iy / (ny / ry)) * rx + ix / (nx / rx);
+  const double sg = sig_t ? sig_t[reg] : 0.0;
+  const double* xc = x + col * ldx;
+  double* yc = y + col * ldy;
+  if (dim == 1) {
+    const double al = u.ax / hx;
+    const double f1 = u.sx > 0 ? 1.0 : -1.0;
+    double x0 = xc[2 * c], x1 = f1 * xc[2 * c + 1];
+    double y0 = al * (x0 + S3 * x1), y1 = al * (-S3 * x0 + 3.0 * x1);
+    const int iup = ix - u.sx;
+    if (iup >= 0 && iup < nx) {
+      double t = xc[2 * iup] + S3 * f1 * xc[2 * iup + 1];
+      y0 -= al * t;
+      y1 += S3 * al * t;
+    }
+    yc[2 * c] = y0 + sg * xc[2 * c];
+    yc[2 * c + 1] = f1 * y1 + sg * xc[2 * c + 1];
+    return;
+  }
+  const double al = u.ax / hx, be = u.ay / hy;
+  const double fx = u.sx > 0 ? 1.0 : -1.0, fy = u.sy > 0 ? 1.0 : -1.0;
+  double v[4] = {xc[4 * c], fx * xc[4 * c + 1], fy * xc[4 * c + 2], fx * fy * xc[4 * c + 3]};
+  const double K[4] = {1.0, S3, -S3, 3.0};
+  double o[4];
+  for (int k = 0; k < 4; ++k) {
+    int a = k & 1, b = k >> 1;
+    double s = 0.0;
+    for (int cc = 0; cc < 2; ++cc) s += al * K[a * 2 + cc] * v[cc + 2 * b];
+    for (int d = 0; d < 2; ++d) s += be * K[b * 2 + d] * v[a + 2 * d];
+    o[k] = s;
+  }
+  const int ixu = ix - u.sx, iyu = iy - u.sy;
+  if (ixu >= 0 && ixu < nx) {
+    const double* n = xc + 4 * ((long long)iy * nx + ixu);
+    double t0 = n[0] + S3 * fx * n[1], t1 = fy * n[2] + S3 * fx * fy * n[3];
+    o[0] -= al * t0; o[1] += S3 * al * t0; o[2] -= al * t1; o[3] += S3 * al * t1;
+  }
+  if (iyu >= 0 && iyu < ny) {
+    const double* n = xc + 4 * ((long long)iyu * nx + ix);
+    double t0 = n[0] + S3 * fy * n[2], t1 = fx * n[1] + S3 * fx * fy * n[3];
+    o[0] -= be * t0; o[2] += S3 * be * t0; o[1] -= be * t1; o[3] += S3 * be * t1;
+  }
+  yc[4 * c] = o[0] + sg * xc[4 * c];
+  yc[4 * c + 1] = fx * o[1] + sg * xc[4 * c + 1];
+  yc[4 * c + 2] = fy * o[2] + sg * xc[4 * c + 2];
+  yc[4 * c + 3] = fx * fy * o[3] + sg * xc[4 * c + 3];
+}
+
+int launch_forward_cols(int dim, int nx, int ny, double hx, double hy, const UDir& u, int rx, int ry,
+                        const double* sig_t_reg, const double* x, long long ldx, double* y, long long ldy, int ncol,
+                        cudaStream_t st) {
+  long long total = (long long)nx * ny * ncol;
+  if (total == 0) return RTE_OK;
+  k_forward<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(dim, nx, ny, hx, hy, u, rx, ry, sig_t_reg, x, ldx, y,
+                                                             ldy, ncol);
+  RTE_CHECK_CUDA(cudaGetLastError());
+  return RTE_OK;
+}
+
 // ----------------------------------------------------------------- host side
 static int pick_D(const rte_problem* p, bool f64) {
   if (p->dim == 1) return 1;
