@@ -1,0 +1,342 @@
+"""Benchmark: parameter solves/s of FGMRES-ROMSAD for the parametric RTE on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+A step solves one batch of seeded parameter instances of the workload to FP64 true residual
+1e-8 (relative l2 of b~ - A~ phi).  `value` is the mixed-precision path (FP32 sweeps, FP64
+Arnoldi/Givens/residual); `fp64` beside it is the plain FP64 path on the same GPU.  Inputs are
+resident in HBM when the timed region starts; L2 is flushed (a 256 MiB write) before every
+timed step.  `e2e` repeats the mixed measurement through the C ABI with host buffers: each step
+copies its parameters host->device and the scalar flux device->host inside the timed region.
+Under torchrun every rank solves its own instances (no collective on the data path): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as wl  # noqa: E402
+
+# Arithmetic per cell and unique direction of the fused sweep (rhs assembly 8 FMA, 4x4 solve 16 FMA,
+# outflow traces 4 FMA, quadrature 4 FMA).
+SWEEP_FLOPS_PER_CELL_DIR = 64
+# ALU peaks from the unit counts and the maximum SM clock (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz);
+# FP64: GB300 nominal 1.25 TFLOP/s.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def workload_spec(name: str):
+    if name == "square2d_64":
+        return wl.config(2), 1
+    if name == "batch256_uneven":
+        return wl.config(3), 256
+    if name == "slab1d_128":
+        return wl.config(1), 1
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(s[1]) for s in self.samples if len(s) >= 9 and s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) >= 9 and s[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = set()
+        for s in self.samples:
+            if len(s) < 9:
+                continue
+            for k, nm in enumerate(names):
+                if s[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ oracle legs
+def oracle_sample(spec, ss, sa, iters_needed: int, sample_iters: int):
+    """Time the CPU oracle on one instance: b~ plus a bounded number of FGMRES iterations, and
+    extrapolate to one full solve (the same algorithm needs `iters_needed` iterations)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import Problem as OProblem, transport as OT
+    from oracle.krylov import fgmres
+    p = OProblem(spec, 0, ss, sa)
+    t0 = time.perf_counter()
+    bt = OT.rhs_btilde(p)
+    t1 = time.perf_counter()
+    fgmres(lambda z: OT.Atilde_apply(p, z), bt, None, restart=min(sample_iters, 128), rtol=1e-30,
+           max_iter=sample_iters, true_residual_check=False)
+    t2 = time.perf_counter()
+    per_iter = (t2 - t1) / sample_iters
+    solve_s = (t1 - t0) + iters_needed * per_iter + (t1 - t0)   # b~, iterations, final FP64 residual
+    return {"value": 1.0 / solve_s, "unit": "param solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"b~ + {sample_iters} FGMRES iterations of one {spec.name} instance on 1 host core "
+                      f"({t2 - t0:.1f} s), extrapolated to {iters_needed} iterations + 1 residual sweep"}
+
+
+def run_reference(args, spec, B, world, rank):
+    if rank != 0:
+        return
+    ss, sa = wl.draw_params(spec, max(1, B), wl.seed_for(2, 1))
+    iters = args.ref_iters
+    vals = []
+    t_start = time.perf_counter()
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    for s in range(args.steps):
+        cb = oracle_sample(spec.with_instances(spec.nx[:1], spec.ny[:1]), ss[0], sa[0], iters, args.ref_sample)
+        vals.append(1.0 / cb["value"])
+    total = sum(vals)
+    value = args.steps * B / total if B else 0.0
+    line = {"impl": "reference", "metric": "param solves/s at 1e-8 true residual", "value": value,
+            "unit": "param solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "instances_per_step": B},
+            "cpu_baseline": dict(cb, value=value),
+            "e2e": {"value": value, "unit": "param solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_start}
+    print(json.dumps(line))
+
+
+# ------------------------------------------------------------------ GPU legs
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="square2d_64")
+    ap.add_argument("--restart", type=int, default=128)
+    ap.add_argument("--max-iter", type=int, default=6000)
+    ap.add_argument("--inner-rtol", type=float, default=1e-2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=40, help="oracle FGMRES iterations per reference step")
+    ap.add_argument("--ref-iters", type=int, default=500, help="iterations of a full solve for extrapolation")
+    args = ap.parse_args()
+    spec, B = workload_spec(args.workload)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, spec, B, world, rank)
+        return
+    import torch
+    from paper_2410_08735_gb300 import binding as RB
+    RB.load()                                   # fails loudly without the built CUDA library
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    R = spec.n_regions
+    n_sets = args.warmup + args.steps
+    # parameters: distinct seeded draws per rank and step (test split)
+    ss_all, sa_all = wl.draw_params(spec, n_sets * B * world, wl.seed_for(2, 1))
+    base = rank * n_sets * B
+
+    def params(step):
+        i0 = base + step * B
+        return ss_all[i0:i0 + B], sa_all[i0:i0 + B]
+
+    ss0, sa0 = params(0)
+    prob = RB.Problem(spec, ss0, sa0)
+    n = prob.n_dof
+    phi = torch.zeros(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    common = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=2, stream=stream)
+
+    def solve(mode):
+        return RB.fgmres_solve(prob, None, phi, mode=mode, inner_rtol=args.inner_rtol, max_outer=30,
+                               true_residual_check=True, **common)
+
+    def timed_loop(mode):
+        per_step, stats_all = [], []
+        for s in range(n_sets):
+            ss, sa = params(s)
+            prob.set_params(ss, sa)
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = solve(mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if s >= args.warmup:
+                per_step.append(e0.elapsed_time(e1))
+                stats_all.extend(st)
+        return per_step, stats_all
+
+    barrier(world)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    launches0 = RB.kernel_launches()
+    t_mixed, st_mixed = timed_loop(RB.RTE_MODE_MIXED)
+    launches_mixed = RB.kernel_launches() - launches0
+    t_fp64, st_fp64 = timed_loop(RB.RTE_MODE_FP64)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = clk.stop()
+    mixed_s = max_over_ranks(world, sum(t_mixed) / 1e3)
+    fp64_s = max_over_ranks(world, sum(t_fp64) / 1e3)
+    solves = args.steps * B * world
+    value = solves / mixed_s
+    fp64_value = solves / fp64_s
+    # e2e: host parameters in, host scalar flux out, through the C ABI
+    host_phi = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+    e2e_ms = []
+    for s in range(n_sets):
+        ss, sa = params(s)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prob.set_params(ss, sa)
+        RB.fgmres_solve(prob, None, host_phi, mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol, max_outer=30,
+                        true_residual_check=True, **common)
+        t1 = time.perf_counter()
+        if s >= args.warmup:
+            e2e_ms.append(1e3 * (t1 - t0))
+    e2e_s = max_over_ranks(world, sum(e2e_ms) / 1e3)
+    # roofline of the dominant kernel: the fused sweep (A~ apply), timed alone with CUDA events
+    z64 = torch.randn(n, dtype=torch.float64, device=dev)
+    w64 = torch.empty_like(z64)
+    z32 = z64.float()
+    w32 = torch.empty_like(z32)
+
+    def time_op(z, w, reps=20):
+        for _ in range(3):
+            prob.apply_op(z, w, stream=stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            prob.apply_op(z, w, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms32 = time_op(z32, w32)
+    ms64 = time_op(z64, w64)
+    cells = sum(nx * ny for nx, ny in zip(spec.nx[:B], spec.ny[:B]))
+    nu = prob.info.n_unique_directions
+    flops = SWEEP_FLOPS_PER_CELL_DIR * cells * nu
+    sw32 = sum(s["sweeps"] - s["sweeps_fp64"] for s in st_mixed)
+    sw64 = sum(s["sweeps_fp64"] for s in st_mixed)
+    share32, share64 = sw32 * ms32, sw64 * ms64
+    if share32 >= share64:
+        roof = {"kernel": "k_sweep2d<float> (A~ apply, FP32)", "bound": "alu", "achieved": flops / (ms32 * 1e-3) / 1e12,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    else:
+        roof = {"kernel": "k_sweep2d<double> (A~ apply, FP64)", "bound": "alu",
+                "achieved": flops / (ms64 * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["ms_per_launch_fp32"] = ms32
+    roof["ms_per_launch_fp64"] = ms64
+    roof["peak_source"] = "unit counts x max SM clock (FP32); GB300 nominal (FP64)"
+    if rank != 0:
+        return
+    line = {
+        "metric": "param solves/s at 1e-8 true residual (mixed FP32-sweep/FP64-Arnoldi vs plain FP64)",
+        "value": value, "unit": "param solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * mixed_s / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "instances_per_step": B, "mesh": f"{spec.nx[0]}x{spec.ny[0]}",
+                   "directions": spec.n_directions, "restart": args.restart, "preconditioner": "none",
+                   "l2": "flushed (256 MiB write) before every timed step"},
+        "fp64": {"value": fp64_value, "unit": "param solves/s", "ms_per_step": 1e3 * fp64_s / args.steps},
+        "speedup_mixed_vs_fp64": value / fp64_value,
+        "solver": {
+            "mixed_iterations_mean": statistics.mean(s["iterations"] for s in st_mixed),
+            "mixed_fp64_sweeps_mean": statistics.mean(s["sweeps_fp64"] for s in st_mixed),
+            "mixed_true_rel_residual_max": max(s["true_rel_residual"] for s in st_mixed),
+            "fp64_iterations_mean": statistics.mean(s["iterations"] for s in st_fp64),
+            "fp64_true_rel_residual_max": max(s["true_rel_residual"] for s in st_fp64),
+            "status": sorted({s["status"] for s in st_mixed + st_fp64})},
+        "e2e": {"value": solves / e2e_s, "unit": "param solves/s", "h2d_bytes_per_step": 2 * R * 8 * B,
+                "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": int(launches_mixed * args.steps / n_sets),
+        "roofline": roof,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        ss, sa = params(args.warmup)
+        iters = int(round(statistics.mean(s["iterations"] for s in st_fp64)))
+        line["cpu_baseline"] = oracle_sample(spec.with_instances(spec.nx[:1], spec.ny[:1]), ss[0], sa[0], iters,
+                                             args.ref_sample)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -60,8 +60,10 @@ extern "C" {
 
 const char* rte_status_string(int status);
 const char* rte_last_error(void);
-/* Library version and the CUDA device it would run on; safe without a GPU (returns the version). */
+/* Library version; safe without a GPU. */
 int rte_version(int* major, int* minor);
+/* Number of CUDA kernels this library has launched in this process (monotonic counter). */
+long long rte_kernel_launches(void);
 
 /* ----------------------------------------------------------------- problem */
 typedef struct rte_problem_desc {

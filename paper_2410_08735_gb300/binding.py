@@ -79,6 +79,7 @@ _SIGS = {
     "rte_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rte_last_error": (ctypes.c_char_p, []),
     "rte_version": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "rte_kernel_launches": (ctypes.c_longlong, []),
     "rte_problem_create": (ctypes.c_int, [ctypes.POINTER(ProblemDesc), ctypes.POINTER(ctypes.c_void_p)]),
     "rte_problem_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "rte_problem_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ProblemInfo)]),
@@ -137,6 +138,11 @@ def load(build_if_missing: bool = False):
 
 def exported_symbols():
     return list(_SIGS)
+
+
+def kernel_launches() -> int:
+    """Kernels launched by librte_gb300 so far in this process."""
+    return int(load().rte_kernel_launches())
 
 
 def _check(status: int, where: str):

@@ -3,9 +3,13 @@
 
 #include "internal.h"
 
+#include <atomic>
+
 namespace rte {
 static thread_local std::string g_last_error;
+static std::atomic<long long> g_launches{0};
 void set_error(const std::string& msg) { g_last_error = msg; }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 }  // namespace rte
 
 extern "C" {
@@ -26,6 +30,8 @@ const char* rte_status_string(int status) {
 }
 
 const char* rte_last_error(void) { return rte::g_last_error.c_str(); }
+
+long long rte_kernel_launches(void) { return rte::g_launches.load(); }
 
 int rte_version(int* major, int* minor) {
   if (major) *major = 0;

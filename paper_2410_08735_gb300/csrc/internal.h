@@ -13,6 +13,8 @@ namespace rte {
 
 // ----------------------------------------------------------------- errors
 void set_error(const std::string& msg);
+// number of kernels this library has launched (reported by rte_kernel_launches)
+void count_launch();
 struct Status {
   int code = RTE_OK;
 };

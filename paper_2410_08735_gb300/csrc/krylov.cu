@@ -298,10 +298,13 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
   // ||rhs||
   RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
   k_norm<<<B, 512, 0, st>>>(rhs, p->d_inst.p, W.active.p, W.bnorm.p);
+  count_launch();
   // r0
   if (zero_guess) {
     k_copy_active<<<vg, 256, 0, st>>>(W.r.p, rhs, p->d_inst.p, W.active.p);
+    count_launch();
     k_zero_active<<<vg, 256, 0, st>>>(x, p->d_inst.p, W.active.p);
+    count_launch();
   } else {
     RTE_TRY(launch_T(p, MODE_RES, f64, x, true, rhs, W.r.p, true, W.active.p, st));
     for (int b = 0; b < B; ++b) rs.sweeps[b] += act[b];
@@ -316,6 +319,7 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
     // beta = ||r||
     RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
     k_norm<<<B, 512, 0, st>>>(W.r.p, p->d_inst.p, W.active.p, W.beta.p);
+    count_launch();
     RTE_CHECK_CUDA(cudaMemcpyAsync(hb.data(), W.beta.p, B * 8, cudaMemcpyDeviceToHost, st));
     RTE_CHECK_CUDA(cudaStreamSynchronize(st));
     int nact = 0;
@@ -331,6 +335,7 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
     // v_0 = r / beta, g = beta e_1
     RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
     k_scale<<<vg, 256, 0, st>>>(W.V.p, W.r.p, W.beta.p, p->d_inst.p, W.active.p);
+    count_launch();
     {
       std::vector<double> g0((size_t)B * (m + 1), 0.0);
       std::vector<int> left(B, 0);
@@ -361,6 +366,7 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
         }
         RTE_CHECK_CUDA(cudaMemcpyAsync(W.brk.p, ident.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
         k_copy_active<<<vg, 256, 0, st>>>(zj, vj, p->d_inst.p, W.brk.p);
+        count_launch();
         std::sort(romlist.begin(), romlist.end());
         size_t s0 = 0;
         while (s0 < romlist.size()) {
@@ -377,8 +383,10 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
       // w = A~ z_j into V[j+1]
       RTE_TRY(launch_T(p, MODE_OP, f64, zj, true, nullptr, W.V.p + (size_t)(j + 1) * ntot, true, W.active.p, st));
       k_mgs<<<B, 1024, 0, st>>>(W.V.p, ntot, j, m, p->d_inst.p, W.active.p, W.H.p, W.brk.p);
+      count_launch();
       k_givens<<<(B + 127) / 128, 128, 0, st>>>(W.H.p, W.cs.p, W.sn.p, W.g.p, j, m, B, W.active.p, W.brk.p,
                                                 W.bnorm.p, rtol, W.iters_left.p, W.est.p, W.flag.p, W.kcols.p);
+      count_launch();
       RTE_CHECK_CUDA(cudaGetLastError());
       RTE_CHECK_CUDA(cudaMemcpyAsync(hflag.data(), W.flag.p, B * sizeof(int), cudaMemcpyDeviceToHost, st));
       RTE_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -402,7 +410,9 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
     }
     // end of cycle: phi += Z y for the instances of this cycle
     k_backsolve<<<(B + 127) / 128, 128, 0, st>>>(W.H.p, W.g.p, m, B, W.kcols.p, W.y.p);
+    count_launch();
     k_update<<<vg, 256, 0, st>>>(x, Zbase, ntot, m, p->d_inst.p, W.kcols.p, W.y.p);
+    count_launch();
     RTE_CHECK_CUDA(cudaGetLastError());
     std::vector<double> hest(B);
     RTE_CHECK_CUDA(cudaMemcpyAsync(hest.data(), W.est.p, B * 8, cudaMemcpyDeviceToHost, st));
@@ -435,6 +445,7 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
     // check-sweep instances: the loop head computes beta and stops them if within 2 rtol
     if (true_check) {
       k_norm<<<B, 512, 0, st>>>(W.r.p, p->d_inst.p, W.active.p, W.nrm.p);
+      count_launch();
       std::vector<double> hn(B);
       RTE_CHECK_CUDA(cudaMemcpyAsync(hn.data(), W.nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
       RTE_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -532,11 +543,13 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     std::vector<double> hb(B), hr(B);
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
     k_norm<<<B, 512, 0, st>>>(ws->bt.p, p->d_inst.p, ws->active.p, ws->nrm.p);
+    count_launch();
     RTE_CHECK_CUDA(cudaMemcpyAsync(hb.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
     RTE_CHECK_CUDA(cudaStreamSynchronize(st));
     for (int outer = 0; outer <= o->max_outer; ++outer) {
       RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
       k_norm<<<B, 512, 0, st>>>(ws->r.p, p->d_inst.p, ws->active.p, ws->nrm.p);
+      count_launch();
       RTE_CHECK_CUDA(cudaMemcpyAsync(hr.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
       RTE_CHECK_CUDA(cudaStreamSynchronize(st));
       int nact = 0;
@@ -560,6 +573,7 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       RTE_TRY(run_fgmres(C, ws->r.p, ws->d.p, true, act, o->inner_rtol, o->max_iter, false, false, zero, rs));
       RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
       k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d.p, p->d_inst.p, ws->active.p);
+      count_launch();
       // r = b~ - A~ x in FP64
       RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ws->r.p, true, ws->active.p, st));
       for (int b = 0; b < B; ++b) {
@@ -589,8 +603,11 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     std::vector<int> all1(B, 1);
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, all1.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
     k_norm<<<B, 512, 0, st>>>(ws->r.p, p->d_inst.p, ws->active.p, ws->nrm.p);
+    count_launch();
     k_norm<<<B, 512, 0, st>>>(ws->bt.p, p->d_inst.p, ws->active.p, ws->beta.p);
+    count_launch();
     k_linf<<<B, 512, 0, st>>>(ws->r.p, p->d_inst.p, ws->est.p);
+    count_launch();
     std::vector<double> hn(B), hb(B), hl(B);
     RTE_CHECK_CUDA(cudaMemcpyAsync(hn.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
     RTE_CHECK_CUDA(cudaMemcpyAsync(hb.data(), ws->beta.p, B * 8, cudaMemcpyDeviceToHost, st));

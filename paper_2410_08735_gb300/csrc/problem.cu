@@ -135,6 +135,7 @@ int upload_params(rte_problem* p) {
   k_linv<<<(unsigned)((total + threads - 1) / threads), threads>>>(p->B, p->nu, p->R, p->dim, p->d_inst.p,
                                                                   p->d_udir.p, p->d_sig_t.p, p->d_linv64.p,
                                                                   p->d_linv32.p);
+  count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   RTE_CHECK_CUDA(cudaDeviceSynchronize());
   return RTE_OK;

@@ -140,6 +140,7 @@ int rom_add_column(romsad* rom, DevBuf<double>& d_mult, DevBuf<double>& d_wA, cu
   const int k = rom->r, N = rom->N, nA = rom->nA, R = rom->R;
   k_pw_column<<<(N + 255) / 256, 256, 0, st>>>(rom->U.p, nA, N, k, rom->rmax, d_mult.p, d_wA.p, rom->P.p, rom->W.p,
                                                rom->P32.p, rom->W32.p);
+  count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   const int achunk = std::max(1, (nA + 7) / 8);
   const int nac = (nA + achunk - 1) / achunk;
@@ -148,10 +149,12 @@ int rom_add_column(romsad* rom, DevBuf<double>& d_mult, DevBuf<double>& d_wA, cu
   dim3 g1(k + 1, R, nac);
   k_newcol_dots<<<g1, 256, 0, st>>>(rom->U.p, rom->Y.p, nA, N, k, rom->nx, rom->ny, rom->nd, rom->rx, rom->ry,
                                     d_mult.p, achunk, d_out.p);
+  count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   double* d_s = d_out.p + (size_t)(k + 1) * R * nac * 3;
   dim3 g2(k + 1, R);
   k_newcol_S<<<g2, 256, 0, st>>>(rom->P.p, rom->W.p, rom->rmax, k, rom->nx, rom->ny, rom->nd, rom->rx, rom->ry, d_s);
+  count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   std::vector<double> h(d_out.n);
   RTE_CHECK_CUDA(cudaMemcpyAsync(h.data(), d_out.p, h.size() * 8, cudaMemcpyDeviceToHost, st));
@@ -312,6 +315,7 @@ int rom_small_solve(romsad* rom, rte_problem* p, const int* d_list, int ninst, c
   const int r = rom->r;
   size_t smem = ((size_t)r * r + r) * 8;
   k_small_solve<<<ninst, 128, smem, st>>>(rom->d_aff.p, r, rom->R, p->d_sig_s.p, p->d_sig_t.p, d_list, y, c);
+  count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   return RTE_OK;
 }
@@ -326,6 +330,7 @@ int rom_apply_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, co
   else
     k_project<float><<<ninst, 256, 0, st>>>(rom->P32.p, rom->rmax, r, p->d_inst.p, d_list, p->d_sig_s.p, p->R, p->rx,
                                             p->ry, p->nd, v, scratch_y);
+    count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   RTE_TRY(rom_small_solve(rom, p, d_list, ninst, scratch_y, scratch_c, st));
   dim3 grid((rom->N + 255) / 256, ninst);
@@ -333,6 +338,7 @@ int rom_apply_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, co
     k_lift<double><<<grid, 256, 0, st>>>(rom->W.p, rom->rmax, r, p->d_inst.p, d_list, v, scratch_c, z);
   else
     k_lift<float><<<grid, 256, 0, st>>>(rom->W32.p, rom->rmax, r, p->d_inst.p, d_list, v, scratch_c, z);
+    count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   return RTE_OK;
 }

@@ -333,6 +333,7 @@ int launch_forward_cols(int dim, int nx, int ny, double hx, double hy, const UDi
   if (total == 0) return RTE_OK;
   k_forward<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(dim, nx, ny, hx, hy, u, rx, ry, sig_t_reg, x, ldx, y,
                                                              ldy, ncol);
+  count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   return RTE_OK;
 }
@@ -340,18 +341,20 @@ int launch_forward_cols(int dim, int nx, int ny, double hx, double hy, const UDi
 // ----------------------------------------------------------------- host side
 static int pick_D(const rte_problem* p, bool f64) {
   if (p->dim == 1) return 1;
-  int nq = p->quad_start[1] - p->quad_start[0];
-  // directions per warp: enough independent chains to hide latency, few enough for registers
+  const int nq = p->quad_start[1] - p->quad_start[0];
+  // Directions per warp: the largest D that still leaves at least 8 warps per SM (152 SMs) in
+  // flight; with fewer tasks (a single small instance) parallelism wins and D = 1.  FP64 keeps D
+  // small (registers; its pipe, not latency, bounds it).
   const int cands64[] = {4, 2, 1};
   const int cands32[] = {8, 4, 2, 1};
-  long long cells = 0;
-  for (int b = 0; b < p->B; ++b) cells += (long long)p->nx[b] * p->ny[b];
-  if (f64) {
-    for (int d : cands64)
-      if (nq % d == 0) return d;
-  } else {
-    for (int d : cands32)
-      if (nq % d == 0) return d;
+  const long long target = 152LL * 8;
+  const int* c = f64 ? cands64 : cands32;
+  const int nc = f64 ? 3 : 4;
+  for (int k = 0; k < nc; ++k) {
+    const int d = c[k];
+    if (nq % d) continue;
+    const long long ntasks = (long long)p->B * 4 * (nq / d);
+    if (ntasks >= target) return d;
   }
   return 1;
 }
@@ -393,6 +396,7 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
   if (p->dim == 1) {
     int threads = 128;
     k_sweep1d<T, TI, ANG><<<(a.ntasks + threads - 1) / threads, threads, 0, st>>>(a);
+    count_launch();
     RTE_CHECK_CUDA(cudaGetLastError());
     return RTE_OK;
   }
@@ -418,6 +422,7 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
       smem_set = smem;                                                                                      \
     }                                                                                                       \
     kern<<<blocks, wpb * 32, smem, st>>>(a);                                                                \
+    count_launch();                                                                                         \
     break;                                                                                                  \
   }
   switch (D) {
@@ -496,6 +501,7 @@ int launch_T(rte_problem* p, int mode, bool f64, const void* src, bool in_f64, c
     else RTE_RED(float, float, float);
   }
 #undef RTE_RED
+  count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   return RTE_OK;
 }
@@ -526,6 +532,7 @@ int launch_scalar_flux(rte_problem* p, bool f64, const void* psi, void* phi, cud
   else
     k_scalar_flux<float><<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(psi), wdev->p, p->ndir, p->d_inst.p,
                                                 reinterpret_cast<float*>(phi));
+  count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   return RTE_OK;
 }
