@@ -286,8 +286,8 @@ class Rom:
                                           ctypes.byref(rep)), "romsad_build_greedy")
         rom = cls(h)
         r = rep.rank
-        report = {"sampled": [sampled[i] for i in range(rep.n_sampled)],
-                  "max_indicator": [ind[i] for i in range(max(0, rep.n_sampled - 1))],
+        report = {"sampled": [sampled[i] for i in range(min(rep.n_sampled, max_greedy_iter))],
+                  "max_indicator": [ind[i] for i in range(min(rep.n_sampled, max_greedy_iter))],
                   "rank": r, "labels": labels[:, :r] if labels is not None else None}
         return rom, report
 

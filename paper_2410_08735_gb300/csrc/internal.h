@@ -98,6 +98,7 @@ struct SweepTask {
 
 struct rte_problem {
   int dim = 2, B = 0, nd = 4, ndir = 0, nu = 0, R = 1, rx = 1, ry = 1;
+  int n_polar = 0, n_azim = 0;       // quadrature orders as given at create
   std::vector<int> nx, ny;
   std::vector<long long> off;        // [B+1]
   long long ntot = 0;
@@ -138,7 +139,10 @@ int upload_params(rte_problem* p);
 enum SweepMode { MODE_T = 0, MODE_OP = 1, MODE_RES = 2, MODE_RHS = 3 };
 int launch_T(rte_problem* p, int mode, bool compute_f64, const void* src, bool in_f64, const void* bvec,
              void* out, bool out_f64, const int* d_active, cudaStream_t st);
-int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st);
+// Angular-output sweep; scale_sigma_s multiplies the source by sigma_s, unique_layout writes one block
+// per unique direction ([nu][N] per instance) instead of all N_Omega directions.
+int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st,
+                   bool scale_sigma_s = false, bool unique_layout = false);
 int launch_scalar_flux(rte_problem* p, bool f64, const void* psi, void* phi, cudaStream_t st);
 // forward operator y = (D_u + sigma_t) x (FP64) for ncol columns on one mesh; used offline
 int launch_forward_cols(int dim, int nx, int ny, double hx, double hy, const UDir& u, int rx, int ry,

@@ -19,6 +19,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <cooperative_groups.h>
+
 #include "romsad.h"
 
 namespace rte {
@@ -131,31 +133,148 @@ __global__ void k_mgs(double* V, long long ntot, int j, int m, const InstInfo* i
   }
 }
 
-// Givens update of column j for every active instance (thread per instance).
-__global__ void k_givens(double* H, double* cs, double* sn, double* g, int j, int m, int B, const int* active,
-                         const int* brk, const double* bnorm, double rtol, const int* iters_left, double* est,
+
+// Modified Gram-Schmidt with one thread-block cluster per instance (Alg. 1 inner loop).  The cluster's
+// CS blocks split w = V[j+1] into contiguous slices held in registers (EPT elements per thread); for
+// q = 0..j every block forms its partial w . v_q, the partials are exchanged through distributed
+// shared memory after one cluster barrier and summed in rank order (deterministic), and each block
+// updates its slice.  v_{q+1} is loaded before the barrier so the load overlaps the exchange.
+template <int EPT>
+__global__ void __launch_bounds__(512) k_mgs_cluster(double* V, long long ntot, int j, int m, const InstInfo* inst,
+                                                     const int* active, double* H, double* Hraw, int* brk) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int b = blockIdx.x / CS;
+  if (!active[b]) return;   // uniform for the whole cluster
+  const InstInfo in = inst[b];
+  const int chunk = (in.ndof + CS - 1) / CS;
+  const int i0 = rank * chunk;
+  const int i1 = min(in.ndof, i0 + chunk);
+  __shared__ double part[2][4];  // [buffer][value]: partial sums published to the cluster
+  __shared__ double wsum[16];
+  __shared__ double bcast;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* wg = V + (size_t)(j + 1) * ntot + in.off;
+  double w[EPT], v[EPT];
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = i0 + threadIdx.x + e * 512;
+    w[e] = i < i1 ? wg[i] : 0.0;
+  }
+  // cluster-wide sum of one value per thread, published in part[buf][0]; returns the total
+  auto cluster_sum = [&](double x, int buf) -> double {
+    x = warp_sum(x);
+    if (lane == 0) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      double t = lane < 16 ? wsum[lane] : 0.0;
+      t = warp_sum(t);
+      if (lane == 0) part[buf][0] = t;
+    }
+    cluster.sync();
+    if (warp == 0) {
+      double t = 0.0;
+      if (lane < CS) t = *cluster.map_shared_rank(&part[buf][0], lane);
+      // fixed-order tree over ranks 0..CS-1
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) bcast = t;
+    }
+    __syncthreads();
+    return bcast;
+  };
+  double s = 0.0;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) s += w[e] * w[e];
+  int buf = 0;
+  const double w0 = sqrt(cluster_sum(s, buf));
+  buf ^= 1;
+  double* h = H + ((size_t)b * m + j) * (m + 1);
+  const double* vq = V + in.off;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = i0 + threadIdx.x + e * 512;
+    v[e] = i < i1 ? vq[i] : 0.0;
+  }
+  for (int q = 0; q <= j; ++q) {
+    s = 0.0;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) s += w[e] * v[e];
+    double vn[EPT];
+    if (q < j) {
+      const double* vnext = V + (size_t)(q + 1) * ntot + in.off;
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) {
+        const int i = i0 + threadIdx.x + e * 512;
+        vn[e] = i < i1 ? vnext[i] : 0.0;
+      }
+    }
+    const double hq = cluster_sum(s, buf);
+    buf ^= 1;
+#pragma unroll
+    for (int e = 0; e < EPT; ++e) w[e] -= hq * v[e];
+    if (rank == 0 && threadIdx.x == 0) {
+      h[q] = hq;
+      if (Hraw) Hraw[((size_t)b * m + j) * (m + 1) + q] = hq;
+    }
+    if (q < j) {
+#pragma unroll
+      for (int e = 0; e < EPT; ++e) v[e] = vn[e];
+    }
+  }
+  s = 0.0;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) s += w[e] * w[e];
+  const double hn = sqrt(cluster_sum(s, buf));
+  const bool breakdown = !(hn > 1e-14 * w0);
+  if (rank == 0 && threadIdx.x == 0) {
+    h[j + 1] = hn;
+    if (Hraw) Hraw[((size_t)b * m + j) * (m + 1) + j + 1] = hn;
+    brk[b] = breakdown ? 1 : 0;
+  }
+  const double inv = breakdown ? 1.0 : 1.0 / hn;
+#pragma unroll
+  for (int e = 0; e < EPT; ++e) {
+    const int i = i0 + threadIdx.x + e * 512;
+    if (i < i1) wg[i] = w[e] * inv;
+  }
+  cluster.sync();  // keep this block's shared memory alive until every peer has read it
+}
+
+// Givens update of column j (one block per active instance): the column and the stored rotations are
+// staged in shared memory by all threads, then one thread applies the j previous rotations.
+__global__ void k_givens(double* H, double* cs, double* sn, double* g, int j, int m, int B, int* active,
+                         const int* brk, const double* bnorm, double rtol, int* iters_left, double* est,
                          int* flag, int* kcols) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B || !active[b]) return;
+  const int b = blockIdx.x;
+  if (!active[b]) return;
+  __shared__ double hs[130], css[128], sns[128];
   double* h = H + ((size_t)b * m + j) * (m + 1);
   double* c = cs + (size_t)b * m;
   double* s = sn + (size_t)b * m;
   double* gg = g + (size_t)b * (m + 1);
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hs[i] = h[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) { css[i] = c[i]; sns[i] = s[i]; }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   for (int i = 0; i < j; ++i) {
-    const double t = c[i] * h[i] + s[i] * h[i + 1];
-    h[i + 1] = -s[i] * h[i] + c[i] * h[i + 1];
-    h[i] = t;
+    const double t = css[i] * hs[i] + sns[i] * hs[i + 1];
+    hs[i + 1] = -sns[i] * hs[i] + css[i] * hs[i + 1];
+    hs[i] = t;
   }
-  const double den = hypot(h[j], h[j + 1]);
+  const double den = hypot(hs[j], hs[j + 1]);
   double cj = 1.0, sj = 0.0;
-  if (den > 0.0) { cj = h[j] / den; sj = h[j + 1] / den; }
+  if (den > 0.0) { cj = hs[j] / den; sj = hs[j + 1] / den; }
+  for (int i = 0; i < j; ++i) h[i] = hs[i];
   c[j] = cj;
   s[j] = sj;
   h[j] = den;
   h[j + 1] = 0.0;
-  gg[j + 1] = -sj * gg[j];
-  gg[j] = cj * gg[j];
-  const double e = fabs(gg[j + 1]);
+  const double gj = gg[j];
+  gg[j + 1] = -sj * gj;
+  gg[j] = cj * gj;
+  const double e = fabs(sj * gj);
   est[b] = e;
   kcols[b] = j + 1;
   int f = RUN;
@@ -164,21 +283,32 @@ __global__ void k_givens(double* H, double* cs, double* sn, double* g, int j, in
   else if (brk[b]) f = STOP_BREAK;
   else if (j + 1 == m || iters_left[b] <= 1) f = STOP_RESTART;
   flag[b] = f;
+  iters_left[b] -= 1;
+  if (f != RUN) active[b] = 0;   // the instance leaves this cycle; the host mirrors it from flag
 }
 
-// y = R^{-1} g (R: rotated H, upper triangular k x k), thread per instance with k > 0.
+// y = R^{-1} g (R: rotated H, upper triangular k x k), one block per instance with k > 0:
+// column-oriented back substitution, column i of R read by all threads (coalesced).
 __global__ void k_backsolve(const double* H, const double* g, int m, int B, const int* kcols, double* y) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= B) return;
+  const int b = blockIdx.x;
   const int k = kcols[b];
+  if (k <= 0) return;
+  __shared__ double rhs[129];
+  __shared__ double yi;
   const double* Hb = H + (size_t)b * m * (m + 1);
-  const double* gg = g + (size_t)b * (m + 1);
-  double* yb = y + (size_t)b * m;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = g[(size_t)b * (m + 1) + i];
+  __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
-    double t = gg[i];
-    for (int q = i + 1; q < k; ++q) t -= Hb[(size_t)q * (m + 1) + i] * yb[q];
-    const double d = Hb[(size_t)i * (m + 1) + i];
-    yb[i] = d != 0.0 ? t / d : 0.0;
+    const double* col = Hb + (size_t)i * (m + 1);
+    if (threadIdx.x == 0) {
+      const double d = col[i];
+      yi = d != 0.0 ? rhs[i] / d : 0.0;
+      y[(size_t)b * m + i] = yi;
+    }
+    __syncthreads();
+    const double v = yi;
+    for (int t = threadIdx.x; t < i; t += blockDim.x) rhs[t] -= col[t] * v;
+    __syncthreads();
   }
 }
 
@@ -215,15 +345,73 @@ __global__ void k_zero_active(double* x, const InstInfo* inst, const int* active
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) x[in.off + i] = 0.0;
 }
 
+// MGS launcher: a cluster of CS blocks (512 threads, EPT elements per thread) per instance; the
+// cluster size grows with the largest instance and, for few instances, up to 16 to spread one
+// instance's orthogonalisation over many SMs.
+template <int EPT>
+static int launch_mgs_t(rte_problem* p, int CS, double* V, long long ntot, int j, int m, const int* active, double* H,
+                        double* Hraw, int* brk, cudaStream_t st) {
+  auto kern = k_mgs_cluster<EPT>;
+  static bool attr = false;
+  if (!attr) {
+    RTE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    attr = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p->B * CS);
+  cfg.blockDim = dim3(512);
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CS;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  RTE_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, V, ntot, j, m, (const InstInfo*)p->d_inst.p, active, H, Hraw, brk));
+  count_launch();
+  return RTE_OK;
+}
+
+int launch_mgs(rte_problem* p, double* V, long long ntot, int j, int m, const int* active, double* H, double* Hraw,
+               int* brk, cudaStream_t st) {
+  int maxn = 0;
+  for (int b = 0; b < p->B; ++b) maxn = std::max(maxn, (int)(p->off[b + 1] - p->off[b]));
+  // want CS blocks per instance with CS * B near 2 x 152 (at most 16), and 512 * EPT * CS >= maxn
+  int CS = 1;
+  while (CS < 16 && (long long)CS * 2 * p->B <= 2 * 152) CS *= 2;
+  int EPT = 1;
+  while ((long long)512 * EPT * CS < maxn) {
+    if (EPT < 16) EPT *= 2;
+    else if (CS < 16) CS *= 2;
+    else break;
+  }
+  if ((long long)512 * EPT * CS < maxn) {
+    set_error("MGS: instance too large for the cluster kernel (more than 131072 dofs)");
+    return RTE_ERR_UNSUPPORTED;
+  }
+  switch (EPT) {
+    case 1: return launch_mgs_t<1>(p, CS, V, ntot, j, m, active, H, Hraw, brk, st);
+    case 2: return launch_mgs_t<2>(p, CS, V, ntot, j, m, active, H, Hraw, brk, st);
+    case 4: return launch_mgs_t<4>(p, CS, V, ntot, j, m, active, H, Hraw, brk, st);
+    case 8: return launch_mgs_t<8>(p, CS, V, ntot, j, m, active, H, Hraw, brk, st);
+    default: return launch_mgs_t<16>(p, CS, V, ntot, j, m, active, H, Hraw, brk, st);
+  }
+}
+
 // ----------------------------------------------------------------- host driver
 struct Ws {
   int B = 0, m = 0;
   long long ntot = 0;
   bool withZ = false;
-  DevBuf<double> V, Z, H, cs, sn, g, y, bt, r, d, phi_in;
+  DevBuf<double> V, Z, H, Hraw, cs, sn, g, y, bt, r, d, phi_in;
   DevBuf<double> bnorm, beta, est, nrm;
   DevBuf<int> active, brk, flag, kcols, iters_left, list;
   DevBuf<double> rom_y, rom_c;
+  int* hflag = nullptr;   // pinned host mirror of flag
+  ~Ws() {
+    if (hflag) cudaFreeHost(hflag);
+  }
   int alloc(rte_problem* p, int m_, bool withZ_) {
     if (B == p->B && m == m_ && ntot == p->ntot && (withZ == withZ_ || !withZ_)) return RTE_OK;
     B = p->B;
@@ -233,6 +421,7 @@ struct Ws {
     RTE_TRY(V.alloc((size_t)(m + 1) * ntot));
     if (withZ) RTE_TRY(Z.alloc((size_t)m * ntot));
     RTE_TRY(H.alloc((size_t)B * m * (m + 1)));
+    RTE_TRY(Hraw.alloc((size_t)B * m * (m + 1)));
     RTE_TRY(cs.alloc((size_t)B * m));
     RTE_TRY(sn.alloc((size_t)B * m));
     RTE_TRY(g.alloc((size_t)B * (m + 1)));
@@ -252,6 +441,8 @@ struct Ws {
     RTE_TRY(list.alloc(B));
     RTE_TRY(rom_y.alloc((size_t)B * 64));
     RTE_TRY(rom_c.alloc((size_t)B * 64));
+    if (hflag) cudaFreeHost(hflag);
+    RTE_CHECK_CUDA(cudaMallocHost(&hflag, B * sizeof(int)));
     return RTE_OK;
   }
 };
@@ -262,6 +453,7 @@ struct SolveCtx {
   int m, window, post;
   cudaStream_t st;
   Ws* ws;
+  FirstCycle* rec = nullptr;  // records the first cycle of instance 0 (greedy high-fidelity solve)
 };
 
 static dim3 vec_grid(rte_problem* p) {
@@ -378,38 +570,50 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
                                  st));
           s0 = s1;
         }
-        RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
       }
       // w = A~ z_j into V[j+1]
       RTE_TRY(launch_T(p, MODE_OP, f64, zj, true, nullptr, W.V.p + (size_t)(j + 1) * ntot, true, W.active.p, st));
-      k_mgs<<<B, 1024, 0, st>>>(W.V.p, ntot, j, m, p->d_inst.p, W.active.p, W.H.p, W.brk.p);
-      count_launch();
-      k_givens<<<(B + 127) / 128, 128, 0, st>>>(W.H.p, W.cs.p, W.sn.p, W.g.p, j, m, B, W.active.p, W.brk.p,
+      RTE_TRY(launch_mgs(p, W.V.p, ntot, j, m, W.active.p, W.H.p, C.rec ? W.Hraw.p : nullptr, W.brk.p, st));
+      k_givens<<<B, 128, 0, st>>>(W.H.p, W.cs.p, W.sn.p, W.g.p, j, m, B, W.active.p, W.brk.p,
                                                 W.bnorm.p, rtol, W.iters_left.p, W.est.p, W.flag.p, W.kcols.p);
       count_launch();
       RTE_CHECK_CUDA(cudaGetLastError());
-      RTE_CHECK_CUDA(cudaMemcpyAsync(hflag.data(), W.flag.p, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+      RTE_CHECK_CUDA(cudaMemcpyAsync(W.hflag, W.flag.p, B * sizeof(int), cudaMemcpyDeviceToHost, st));
       RTE_CHECK_CUDA(cudaStreamSynchronize(st));
       int still = 0;
-      std::vector<int> left(B, 0);
       for (int b = 0; b < B; ++b) {
         if (!act[b]) continue;
         rs.iterations[b] += 1;
         rs.sweeps[b] += 1;
-        if (hflag[b] != RUN) {
-          outcome[b] = hflag[b];
+        if (W.hflag[b] != RUN) {
+          outcome[b] = W.hflag[b];
           act[b] = 0;
         } else {
           ++still;
         }
-        left[b] = max_iter - rs.iterations[b];
       }
       if (still == 0) break;
-      RTE_CHECK_CUDA(cudaMemcpyAsync(W.iters_left.p, left.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-      RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    // first-cycle record for the xi recurrence: unrotated H, the Krylov basis (Z = V without a
+    // preconditioner) and beta
+    if (C.rec && !C.rec->done) {
+      int k0 = 0;
+      RTE_CHECK_CUDA(cudaMemcpyAsync(&k0, W.kcols.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+      C.rec->k = k0;
+      C.rec->beta = hb[0];
+      C.rec->m = m;
+      C.rec->H.assign((size_t)m * (m + 1), 0.0);
+      RTE_CHECK_CUDA(cudaMemcpyAsync(C.rec->H.data(), W.Hraw.p, C.rec->H.size() * 8, cudaMemcpyDeviceToHost, st));
+      const int nv = std::min(k0, C.rec->want);
+      RTE_TRY(C.rec->Z.ensure((size_t)std::max(1, nv) * ntot));
+      if (nv > 0)
+        RTE_CHECK_CUDA(cudaMemcpyAsync(C.rec->Z.p, Zbase, (size_t)nv * ntot * 8, cudaMemcpyDeviceToDevice, st));
+      C.rec->nz = nv;
+      C.rec->done = true;
     }
     // end of cycle: phi += Z y for the instances of this cycle
-    k_backsolve<<<(B + 127) / 128, 128, 0, st>>>(W.H.p, W.g.p, m, B, W.kcols.p, W.y.p);
+    k_backsolve<<<B, 128, 0, st>>>(W.H.p, W.g.p, m, B, W.kcols.p, W.y.p);
     count_launch();
     k_update<<<vg, 256, 0, st>>>(x, Zbase, ntot, m, p->d_inst.p, W.kcols.p, W.y.p);
     count_launch();
@@ -466,6 +670,22 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
 static Ws* get_ws(rte_problem* p) {
   if (!p->krylov_ws) p->krylov_ws = std::shared_ptr<void>(new Ws(), [](void* q) { delete static_cast<Ws*>(q); });
   return static_cast<Ws*>(p->krylov_ws.get());
+}
+
+// High-fidelity FP64 FGMRES (M = I, zero initial guess) on a one-instance problem, recording the first
+// cycle; used by the greedy ROM construction (step 2(a)).  x: device output [N].
+int hf_solve(rte_problem* p, double rtol, int restart, int max_iter, double* x, FirstCycle* rec, int* iterations,
+             int* status) {
+  Ws* ws = get_ws(p);
+  RTE_TRY(ws->alloc(p, restart, false));
+  SolveCtx C{p, nullptr, restart, 0, RTE_POST_IDENTITY, 0, ws, rec};
+  RTE_TRY(launch_T(p, MODE_RHS, true, nullptr, true, nullptr, ws->bt.p, true, nullptr, 0));
+  std::vector<int> all(p->B, 1), zero(p->B, 0);
+  RunStats rs;
+  RTE_TRY(run_fgmres(C, ws->bt.p, x, true, all, rtol, max_iter, true, false, zero, rs));
+  *iterations = rs.iterations[0];
+  *status = rs.status[0];
+  return RTE_OK;
 }
 
 }  // namespace rte

@@ -154,6 +154,8 @@ static int create_impl(const rte_problem_desc* d, rte_problem* p) {
   if (d->dim == 1) RTE_ARG(d->n_polar % 2 == 0, "1D n_polar must be even");
   p->dim = d->dim;
   p->B = d->n_instances;
+  p->n_polar = d->n_polar;
+  p->n_azim = d->dim == 2 ? d->n_azim : 0;
   p->nd = d->dim == 2 ? 4 : 2;
   p->rx = d->rx;
   p->ry = d->dim == 2 ? d->ry : 1;

@@ -320,6 +320,16 @@ int rom_small_solve(romsad* rom, rte_problem* p, const int* d_list, int ninst, c
   return RTE_OK;
 }
 
+int rom_project_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* v, double* y,
+                     cudaStream_t st) {
+  if (ninst == 0) return RTE_OK;
+  k_project<double><<<ninst, 256, 0, st>>>(rom->P.p, rom->rmax, rom->r, p->d_inst.p, d_list, p->d_sig_s.p, p->R, p->rx,
+                                           p->ry, p->nd, v, y);
+  count_launch();
+  RTE_CHECK_CUDA(cudaGetLastError());
+  return RTE_OK;
+}
+
 int rom_apply_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* v, double* z, bool f64,
                    double* scratch_y, double* scratch_c, cudaStream_t st) {
   if (ninst == 0) return RTE_OK;
@@ -343,7 +353,7 @@ int rom_apply_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, co
   return RTE_OK;
 }
 
-static int alloc_rom_arrays(romsad* rom, int rmax, bool withU) {
+int rom_alloc_arrays(romsad* rom, int rmax, bool withU) {
   rom->rmax = rmax;
   RTE_TRY(rom->P.alloc((size_t)rom->N * rmax));
   RTE_TRY(rom->W.alloc((size_t)rom->N * rmax));
@@ -405,9 +415,11 @@ int romsad_create_from_basis(rte_problem_t tmpl, int instance, int r, const doub
   rom_init_geometry(rom, tmpl, instance);
   rom->nA = tmpl->ndir;
   rom->uidx = tmpl->uniq_of_dir;
+  rom->dir_block.resize(tmpl->ndir);
+  for (int j = 0; j < tmpl->ndir; ++j) rom->dir_block[j] = j;
   rom->mult.assign(tmpl->ndir, 1.0);
   rom->wA = tmpl->w;
-  int s = alloc_rom_arrays(rom, r, true);
+  int s = rom_alloc_arrays(rom, r, true);
   DevBuf<double> d_mult, d_wA;
   if (s == RTE_OK) s = d_mult.alloc(rom->nA);
   if (s == RTE_OK) s = d_wA.alloc(rom->nA);
@@ -447,12 +459,8 @@ int romsad_get_basis(romsad_t rom, double* U_host) {
     RTE_CHECK_CUDA(cudaMemcpy(blk.data(), rom->U.p + (size_t)k * rom->nA * rom->N, blk.size() * 8,
                               cudaMemcpyDeviceToHost));
     double* dst = U_host + (size_t)k * rom->ndir * rom->N;
-    if (rom->nA == rom->ndir) {
-      std::memcpy(dst, blk.data(), blk.size() * 8);
-    } else {
-      return (set_error("romsad_get_basis: unique-direction storage needs the problem's duplicate map"),
-              RTE_ERR_UNSUPPORTED);
-    }
+    for (int j = 0; j < rom->ndir; ++j)
+      std::memcpy(dst + (size_t)j * rom->N, blk.data() + (size_t)rom->dir_block[j] * rom->N, (size_t)rom->N * 8);
   }
   return RTE_OK;
 }
@@ -554,7 +562,7 @@ int romsad_load(const char* path, romsad_t* out) {
     set_error(std::string("romsad_load: malformed checkpoint ") + path);
     return RTE_ERR_IO;
   }
-  int s = alloc_rom_arrays(rom, rom->r, false);
+  int s = rom_alloc_arrays(rom, rom->r, false);
   if (s == RTE_OK) {
     std::vector<float> P32(P.size()), W32(W.size());
     for (size_t i = 0; i < P.size(); ++i) { P32[i] = (float)P[i]; W32[i] = (float)W[i]; }

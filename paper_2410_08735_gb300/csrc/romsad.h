@@ -15,6 +15,7 @@ struct romsad {
   std::vector<int> uidx;       // [nA] unique direction of block a
   std::vector<double> mult;    // [nA]
   std::vector<double> wA;      // [nA]
+  std::vector<int> dir_block;  // [ndir] stored block holding direction j
   // device arrays
   rte::DevBuf<double> P, W;    // [N][rmax] (dof-major, rank contiguous)
   rte::DevBuf<float> P32, W32;
@@ -28,6 +29,24 @@ struct romsad {
 };
 
 namespace rte {
+// First FGMRES cycle of a high-fidelity solve (instance 0), for the xi recurrence (Sec. 4.4.1).
+struct FirstCycle {
+  int want = 0;              // number of preconditioned vectors z to keep (the window)
+  bool done = false;
+  int k = 0, m = 0, nz = 0;  // columns in the first cycle, restart length, vectors kept
+  double beta = 0.0;         // ||r^(0)||
+  std::vector<double> H;     // unrotated Hessenberg, column-major [m][m+1]
+  DevBuf<double> Z;          // [nz][N] z^(1..nz) (= v without a preconditioner)
+};
+int hf_solve(rte_problem* p, double rtol, int restart, int max_iter, double* x, FirstCycle* rec, int* iterations,
+             int* status);
+int rom_add_column(romsad* rom, DevBuf<double>& d_mult, DevBuf<double>& d_wA, cudaStream_t st);
+int rom_compute_Y_column(romsad* rom, const rte_problem* p, int inst, int k, cudaStream_t st);
+void rom_init_geometry(romsad* rom, const rte_problem* p, int b);
+int rom_alloc_arrays(romsad* rom, int rmax, bool withU);
+// y[b][k] = (P^T Sigma_s v_b)[k] for the listed instances (FP64), y laid out [ninst][64]
+int rom_project_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* v, double* y,
+                     cudaStream_t st);
 // Assemble and LU-factor U^T A_mu U for the listed instances of p (device), then
 // c = A_r^{-1} y per instance: y [ninst][r] in, c [ninst][r] out (FP64).
 int rom_small_solve(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* y, double* c,

@@ -46,6 +46,7 @@ struct SweepArgs {
   int ndir, nu, R, rx, ry;
   const int* active;    // [B] or null
   int smem_per_warp;    // elements of the compute type
+  int psi_unique;       // angular output: 0 = all N_Omega directions, 1 = one block per unique direction
 };
 
 template <typename T>
@@ -86,8 +87,11 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tab = reinterpret_cast<T*>(smem_raw) + (size_t)warp * a.smem_per_warp;
   T* ybuf = tab + D * R * 16;
+  T* sgs = ybuf + D * nx * 2;   // sigma_s per region
   const T* linv = reinterpret_cast<const T*>(a.linv) + ((size_t)tk.b * a.nu + tk.u0) * R * 16;
   for (int e = lane; e < D * R * 16; e += 32) tab[e] = linv[e];
+  if (a.sig_s)
+    for (int e = lane; e < R; e += 32) sgs[e] = reinterpret_cast<const T*>(a.sig_s)[(size_t)tk.b * R + e];
   T al[D], be[D], wg[D];
   const int sx = a.udir[tk.u0].sx, sy = a.udir[tk.u0].sy;
 #pragma unroll
@@ -98,10 +102,10 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
     wg[d] = (T)u.w;
   }
   const T bnd = a.with_bc ? (T)(a.g * sqrt(in.hx * in.hy)) : (T)0;
-  const T* sig_s = a.sig_s ? reinterpret_cast<const T*>(a.sig_s) + (size_t)tk.b * R : nullptr;
+  const bool sig_s = a.sig_s != nullptr;
   const TI* src = reinterpret_cast<const TI*>(a.src) + in.off;
   T* part = reinterpret_cast<T*>(a.partial) + (size_t)a.tasks_per_inst * in.off + (size_t)tk.t * in.ndof;
-  T* psi = ANG ? reinterpret_cast<T*>(a.psi) + (size_t)a.ndir * in.off : nullptr;
+  T* psi = ANG ? reinterpret_cast<T*>(a.psi) + (size_t)(a.psi_unique ? a.nu : a.ndir) * in.off : nullptr;
   const T S3 = (T)1.7320508075688772;
   const int P = nx > 32 ? nx : 32;
   const int nbands = (ny + 31) >> 5;
@@ -110,13 +114,87 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
   T tx0[D], tx1[D], ty0[D], ty1[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) { tx0[d] = tx1[d] = ty0[d] = ty1[d] = (T)0; }
+  // Cursor over this lane's cells: (band, col) advance by one column per step; the region index and
+  // the cell offset are carried along so the step loop has no integer division.
+  struct Cursor {
+    int band, col, row, iy, ryb, xr, xrc;   // xr: region column, xrc: column inside it
+    long long cell;
+  };
+  auto cur_init = [&](Cursor& c, int st) {
+    const int rel = st - lane;
+    c.band = rel >= 0 ? rel / P : 0;
+    c.col = rel >= 0 ? rel - c.band * P : rel;   // negative before the lane starts
+    c.row = c.band * 32 + lane;
+    c.iy = sy > 0 ? c.row : ny - 1 - c.row;
+    c.ryb = (c.row < ny ? c.iy / cy : 0) * a.rx;
+    const int cc = c.col >= 0 ? c.col : 0;
+    const int ix = sx > 0 ? cc : nx - 1 - cc;
+    c.xr = ix / cx;
+    c.xrc = ix - c.xr * cx;
+    c.cell = (long long)c.iy * nx + ix;
+  };
+  auto cur_valid = [&](const Cursor& c) { return c.col >= 0 && c.col < nx && c.band < nbands && c.row < ny; };
+  auto cur_next = [&](Cursor& c) {
+    ++c.col;
+    if (c.col == P) {      // next band: recompute (rare)
+      const int band = c.band + 1;
+      c.band = band;
+      c.col = 0;
+      c.row = band * 32 + lane;
+      c.iy = sy > 0 ? c.row : ny - 1 - c.row;
+      c.ryb = (c.row < ny ? c.iy / cy : 0) * a.rx;
+      const int ix = sx > 0 ? 0 : nx - 1;
+      c.xr = ix / cx;
+      c.xrc = ix - c.xr * cx;
+      c.cell = (long long)c.iy * nx + ix;
+      return;
+    }
+    if (c.col <= 0) {      // the lane has not started yet (or starts now)
+      if (c.col == 0) {
+        const int ix = sx > 0 ? 0 : nx - 1;
+        c.xr = ix / cx;
+        c.xrc = ix - c.xr * cx;
+        c.cell = (long long)c.iy * nx + ix;
+      }
+      return;
+    }
+    if (c.col >= nx) return;   // past the end of the row: idle until the next band
+    if (sx > 0) {
+      ++c.cell;
+      if (++c.xrc == cx) { c.xrc = 0; ++c.xr; }
+    } else {
+      --c.cell;
+      if (--c.xrc < 0) { c.xrc = cx - 1; --c.xr; }
+    }
+  };
+  // Sources are read PF steps ahead into a register ring (their addresses do not depend on the
+  // sweep), so the load latency overlaps PF wavefront steps instead of stalling each one.
+  constexpr int PF = 4;
+  TI q0[PF], q1[PF], q2[PF], q3[PF];
+  int qreg[PF];
+  Cursor cu, fu;   // cu: current step, fu: step s + PF (prefetch)
+  cur_init(cu, 0);
+  cur_init(fu, 0);
+#pragma unroll
+  for (int k = 0; k < PF; ++k) {
+    if (cur_valid(fu)) Vec4<TI>::load(src + 4 * fu.cell, q0[k], q1[k], q2[k], q3[k]);
+    qreg[k] = fu.ryb + fu.xr;
+    cur_next(fu);
+  }
   __syncwarp();
-  for (int s = 0; s < nsteps; ++s) {
-    const int rel = s - lane;
-    const int band = rel >= 0 ? rel / P : -1;
-    const int col = rel - band * P;
-    const int row = band * 32 + lane;
-    const bool act = rel >= 0 && band < nbands && col < nx && row < ny;
+  for (int s0 = 0; s0 < nsteps; s0 += PF) {
+#pragma unroll
+  for (int kk = 0; kk < PF; ++kk) {
+    const int s = s0 + kk;
+    const bool act = s < nsteps && cur_valid(cu);
+    const int col = cu.col, band = cu.band;
+    const long long c = cu.cell;
+    T s0v = (T)q0[kk], s1 = (T)q1[kk], s2 = (T)q2[kk], s3 = (T)q3[kk];
+    const int reg = qreg[kk];
+    if (cur_valid(fu)) Vec4<TI>::load(src + 4 * fu.cell, q0[kk], q1[kk], q2[kk], q3[kk]);
+    qreg[kk] = fu.ryb + fu.xr;
+    cur_next(fu);
+    cur_next(cu);
     T yi0[D], yi1[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -140,19 +218,9 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
 #pragma unroll
         for (int d = 0; d < D; ++d) { tx0[d] = bnd; tx1[d] = (T)0; }
       }
-      const int ix = sx > 0 ? col : nx - 1 - col;
-      const int iy = sy > 0 ? row : ny - 1 - row;
-      const long long c = (long long)iy * nx + ix;
-      const int reg = (iy / cy) * a.rx + ix / cx;
-      T s0, s1, s2, s3;
-      {
-        TI v0, v1, v2, v3;
-        Vec4<TI>::load(src + 4 * c, v0, v1, v2, v3);
-        s0 = (T)v0; s1 = (T)v1; s2 = (T)v2; s3 = (T)v3;
-      }
       if (sig_s) {
-        const T sg = sig_s[reg];
-        s0 *= sg; s1 *= sg; s2 *= sg; s3 *= sg;
+        const T sg = sgs[reg];
+        s0v *= sg; s1 *= sg; s2 *= sg; s3 *= sg;
       }
       s1 = sx > 0 ? s1 : -s1;
       s2 = sy > 0 ? s2 : -s2;
@@ -161,15 +229,20 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const T ax = al[d], by = be[d];
-        const T r0 = s0 + ax * tx0[d] + by * yi0[d];
+        const T r0 = s0v + ax * tx0[d] + by * yi0[d];
         const T r1 = s1 - S3 * ax * tx0[d] + by * yi1[d];
         const T r2 = s2 + ax * tx1[d] - S3 * by * yi0[d];
         const T r3 = s3 - S3 * (ax * tx1[d] + by * yi1[d]);
         const T* L = tab + (d * R + reg) * 16;
-        const T p0 = L[0] * r0 + L[1] * r1 + L[2] * r2 + L[3] * r3;
-        const T p1 = L[4] * r0 + L[5] * r1 + L[6] * r2 + L[7] * r3;
-        const T p2 = L[8] * r0 + L[9] * r1 + L[10] * r2 + L[11] * r3;
-        const T p3 = L[12] * r0 + L[13] * r1 + L[14] * r2 + L[15] * r3;
+        T l[16];
+        Vec4<T>::load(L, l[0], l[1], l[2], l[3]);
+        Vec4<T>::load(L + 4, l[4], l[5], l[6], l[7]);
+        Vec4<T>::load(L + 8, l[8], l[9], l[10], l[11]);
+        Vec4<T>::load(L + 12, l[12], l[13], l[14], l[15]);
+        const T p0 = l[0] * r0 + l[1] * r1 + l[2] * r2 + l[3] * r3;
+        const T p1 = l[4] * r0 + l[5] * r1 + l[6] * r2 + l[7] * r3;
+        const T p2 = l[8] * r0 + l[9] * r1 + l[10] * r2 + l[11] * r3;
+        const T p3 = l[12] * r0 + l[13] * r1 + l[14] * r2 + l[15] * r3;
         tx0[d] = p0 + S3 * p1;
         tx1[d] = p2 + S3 * p3;
         ty0[d] = p0 + S3 * p2;
@@ -183,10 +256,14 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
           ybuf[(d * nx + col) * 2 + 1] = ty1[d];
         }
         if (ANG) {
-          const UDir u = a.udir[tk.u0 + d];
           const T q1 = sx > 0 ? p1 : -p1, q2 = sy > 0 ? p2 : -p2, q3 = (sx * sy) > 0 ? p3 : -p3;
-          for (int k = 0; k < u.ndup; ++k)
-            Vec4<T>::store(psi + (size_t)u.dup[k] * in.ndof + 4 * c, p0, q1, q2, q3);
+          if (a.psi_unique) {
+            Vec4<T>::store(psi + (size_t)(tk.u0 + d) * in.ndof + 4 * c, p0, q1, q2, q3);
+          } else {
+            const UDir u = a.udir[tk.u0 + d];
+            for (int k = 0; k < u.ndup; ++k)
+              Vec4<T>::store(psi + (size_t)u.dup[k] * in.ndof + 4 * c, p0, q1, q2, q3);
+          }
         }
       }
       acc1 = sx > 0 ? acc1 : -acc1;
@@ -195,6 +272,7 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
       Vec4<T>::store(part + 4 * c, acc0, acc1, acc2, acc3);
     }
     __syncwarp();
+  }
   }
 }
 
@@ -214,7 +292,9 @@ __global__ void k_sweep1d(SweepArgs a) {
   const T* sig_s = a.sig_s ? reinterpret_cast<const T*>(a.sig_s) + (size_t)tk.b * R : nullptr;
   const TI* src = reinterpret_cast<const TI*>(a.src) + in.off;
   T* part = reinterpret_cast<T*>(a.partial) + (size_t)a.tasks_per_inst * in.off + (size_t)tk.t * in.ndof;
-  T* psi = ANG ? reinterpret_cast<T*>(a.psi) + (size_t)a.ndir * in.off + (size_t)u.dup[0] * in.ndof : nullptr;
+  T* psi = ANG ? reinterpret_cast<T*>(a.psi) + (size_t)(a.psi_unique ? a.nu : a.ndir) * in.off +
+                     (size_t)(a.psi_unique ? tk.u0 : u.dup[0]) * in.ndof
+                : nullptr;
   T tx = a.with_bc ? (T)(a.g * sqrt(in.hx)) : (T)0;
   for (int col = 0; col < nx; ++col) {
     const int ix = u.sx > 0 ? col : nx - 1 - col;
@@ -402,7 +482,7 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
   }
   int maxnx = 0;
   for (int b = 0; b < p->B; ++b) maxnx = std::max(maxnx, p->nx[b]);
-  a.smem_per_warp = D * p->R * 16 + D * maxnx * 2;
+  a.smem_per_warp = D * p->R * 16 + D * maxnx * 2 + p->R;
   a.smem_per_warp = (a.smem_per_warp + 3) & ~3;
   size_t per_warp = (size_t)a.smem_per_warp * sizeof(T);
   int wpb = 4;
@@ -506,7 +586,8 @@ int launch_T(rte_problem* p, int mode, bool f64, const void* src, bool in_f64, c
   return RTE_OK;
 }
 
-int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st) {
+int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st,
+                   bool scale_sigma_s, bool unique_layout) {
   int D = pick_D(p, f64);
   RTE_TRY(ensure_tasks(p, D));
   RTE_TRY(ensure_partial(p, f64));
@@ -516,6 +597,8 @@ int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void*
   a.with_bc = with_bc ? 1 : 0;
   a.partial = p->d_partial.p;
   a.psi = psi;
+  a.psi_unique = unique_layout ? 1 : 0;
+  if (scale_sigma_s) a.sig_s = f64 ? (const void*)p->d_sig_s.p : (const void*)p->d_sig_s32.p;
   if (f64) RTE_TRY((launch_sweep_t<double, double, true>(p, D, a, st)));
   else RTE_TRY((launch_sweep_t<float, float, true>(p, D, a, st)));
   return RTE_OK;
