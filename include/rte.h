@@ -174,6 +174,39 @@ int romsad_destroy(romsad_t rom);
 #define RTE_MODE_MIXED 1     /* FP64 iterative refinement around an FGMRES whose sweeps
                                 and ROM products run in FP32; MGS/Givens in FP64       */
 
+/* ------------------------------------------------- learned warm start (MLP) */
+/* A small MLP maps mu = (sigma_s[R], sigma_a[R]) of an instance to the r reduced-basis
+ * coefficients c of eq. greedy-rom (labels from romsad_build_greedy).  Since the first FGMRES
+ * correction satisfies delta phi = T Sigma_s xi = phi - b~ (eqs. density-relation, correction-fgmres1),
+ * phi0 = b~ + W c_hat(mu) is a warm start.  Features: standardised (log sigma_s, sigma_a); layers
+ * 2R -> hidden -> hidden -> r with the exact (erf) GELU; FP32 master weights, products with BF16-
+ * rounded weights when bf16 = 1, FP32 accumulation; loss 0.5 ||y - c||^2 / r averaged; Adam.
+ * Parameters are one flat FP32 array: W1 [hidden][2R], b1, W2 [hidden][hidden], b2, W3 [r][hidden], b3. */
+typedef struct rte_mlp* rte_mlp_t;
+typedef struct rte_mlp_train_opts {
+    int epochs;          /* passes over the training set                      */
+    int batch;           /* minibatch size (fixed order, last partial dropped) */
+    double lr, beta1, beta2, eps;   /* Adam                                  */
+    int bf16;            /* 1: BF16-rounded weights in the products           */
+} rte_mlp_train_opts;
+/* Weights uniform in +-1/sqrt(fan_in) from SplitMix64(seed), biases 0, standardisation identity. */
+int rte_mlp_create(int n_in, int hidden, int n_out, unsigned long long seed, rte_mlp_t* out);
+int rte_mlp_num_params(rte_mlp_t mlp, int* n);
+/* flat: host [n_params]; mean/stdv: host [n_in] feature standardisation (NULL keeps the current). */
+int rte_mlp_set_params(rte_mlp_t mlp, const float* flat, const float* mean, const float* stdv);
+int rte_mlp_get_params(rte_mlp_t mlp, float* flat, float* mean, float* stdv);
+/* Loss and gradient on the GPU for n samples: mu host [n][n_in], c host [n][n_out] -> loss, grad host [n_params]. */
+int rte_mlp_loss_grad(rte_mlp_t mlp, int n, const double* mu, const double* c, int bf16, double* loss, float* grad);
+/* Sets the standardisation from the training set, then Adam for the given epochs; final_loss over all n. */
+int rte_mlp_train(rte_mlp_t mlp, int n, const double* mu, const double* c, const rte_mlp_train_opts* opts,
+                  double* final_loss);
+/* c_out host [n][n_out] = network(mu host [n][n_in]) with BF16-rounded weights. */
+int rte_mlp_infer(rte_mlp_t mlp, int n, const double* mu, double* c_out);
+int rte_mlp_destroy(rte_mlp_t mlp);
+/* The ROM uses the MLP for the learned warm start (fgmres_opts.warm_start = 2); NULL detaches.
+ * The MLP must outlive the ROM's use of it. */
+int romsad_attach_mlp(romsad_t rom, rte_mlp_t mlp);
+
 typedef struct fgmres_opts {
     int restart;             /* m of Alg. 1 (Krylov vectors per cycle)                */
     double rtol;             /* FP64 mode: ||r||/||b~|| target; mixed: FP64 true residual target */
@@ -184,7 +217,8 @@ typedef struct fgmres_opts {
     double inner_rtol;       /* mixed: relative target of each inner solve             */
     int max_outer;           /* mixed: cap on refinement steps                         */
     int true_residual_check; /* FP64 mode: recompute b~ - A~ phi after convergence     */
-    int warm_start;          /* 1: phi0 is used as the initial guess                   */
+    int warm_start;          /* 0: zero initial guess; 1: phi0; 2: learned phi0 = b~ + W c_hat(mu)
+                                from each instance's ROM MLP (instances without one start at 0) */
 } fgmres_opts;
 
 typedef struct fgmres_stats {

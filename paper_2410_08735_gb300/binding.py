@@ -58,6 +58,12 @@ class GreedyReport(ctypes.Structure):
                 ("labels", ctypes.POINTER(ctypes.c_double))]
 
 
+class MlpTrainOpts(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("beta2", ctypes.c_double), ("eps", ctypes.c_double),
+                ("bf16", ctypes.c_int)]
+
+
 class FgmresOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("window", ctypes.c_int), ("post_mode", ctypes.c_int), ("mode", ctypes.c_int),
@@ -109,6 +115,23 @@ _SIGS = {
     "romsad_save": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p]),
     "romsad_load": (ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]),
     "romsad_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "rte_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "rte_mlp_num_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int)]),
+    "rte_mlp_set_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    "rte_mlp_get_params": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                                          ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float)]),
+    "rte_mlp_loss_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)]),
+    "rte_mlp_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(MlpTrainOpts),
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "rte_mlp_infer": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double)]),
+    "rte_mlp_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "romsad_attach_mlp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "fgmres_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(FgmresOpts),
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(FgmresStats),
                                     ctypes.c_void_p]),
@@ -335,16 +358,88 @@ class Rom:
             pass
 
 
+def _fptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Mlp:
+    """Owns an rte_mlp_t (learned warm start network)."""
+
+    def __init__(self, n_in: int, hidden: int, n_out: int, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().rte_mlp_create(n_in, hidden, n_out, seed, ctypes.byref(h)), "rte_mlp_create")
+        self.h = h
+        self.n_in, self.hidden, self.n_out = n_in, hidden, n_out
+        n = ctypes.c_int()
+        _check(load().rte_mlp_num_params(h, ctypes.byref(n)), "rte_mlp_num_params")
+        self.n_params = n.value
+
+    def set_params(self, flat, mean=None, stdv=None):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        m = None if mean is None else _fptr(np.ascontiguousarray(mean, dtype=np.float32))
+        s = None if stdv is None else _fptr(np.ascontiguousarray(stdv, dtype=np.float32))
+        _check(load().rte_mlp_set_params(self.h, _fptr(flat), m, s), "rte_mlp_set_params")
+
+    def get_params(self):
+        flat = np.zeros(self.n_params, dtype=np.float32)
+        mean = np.zeros(self.n_in, dtype=np.float32)
+        stdv = np.zeros(self.n_in, dtype=np.float32)
+        _check(load().rte_mlp_get_params(self.h, _fptr(flat), _fptr(mean), _fptr(stdv)), "rte_mlp_get_params")
+        return flat, mean, stdv
+
+    def loss_grad(self, mu, c, bf16=False):
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        loss = ctypes.c_double()
+        grad = np.zeros(self.n_params, dtype=np.float32)
+        _check(load().rte_mlp_loss_grad(self.h, mu.shape[0], _dptr(mu), _dptr(c), int(bf16), ctypes.byref(loss),
+                                        _fptr(grad)), "rte_mlp_loss_grad")
+        return loss.value, grad
+
+    def train(self, mu, c, epochs=200, batch=256, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, bf16=True):
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        o = MlpTrainOpts(epochs, batch, lr, beta1, beta2, eps, int(bf16))
+        loss = ctypes.c_double()
+        _check(load().rte_mlp_train(self.h, mu.shape[0], _dptr(mu), _dptr(c), ctypes.byref(o), ctypes.byref(loss)),
+               "rte_mlp_train")
+        return loss.value
+
+    def infer(self, mu):
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        out = np.zeros((mu.shape[0], self.n_out))
+        _check(load().rte_mlp_infer(self.h, mu.shape[0], _dptr(mu), _dptr(out)), "rte_mlp_infer")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().rte_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def attach_mlp(rom: "Rom", mlp: Optional[Mlp]):
+    _check(load().romsad_attach_mlp(rom.h, mlp.h if mlp is not None else None), "romsad_attach_mlp")
+    rom._mlp = mlp
+
+
 def fgmres_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi, phi0=None, restart=30,
                  rtol=1e-10, max_iter=1000, window=2, post_mode=RTE_POST_ROM, mode=RTE_MODE_FP64,
-                 inner_rtol=1e-5, max_outer=20, true_residual_check=True, stream=None, raise_on_fail=True):
+                 inner_rtol=1e-5, max_outer=20, true_residual_check=True, stream=None, raise_on_fail=True,
+                 learned_warm_start=False):
     """FGMRES-ROMSAD for all instances; phi: FP64 device tensor or host (numpy/pinned) buffer.
 
     Returns the list of per-instance stats dicts.
     """
     B = problem.spec.n_instances
+    ws = 2 if learned_warm_start else int(phi0 is not None)
     o = FgmresOpts(restart, rtol, max_iter, window, post_mode, mode, inner_rtol, max_outer,
-                   int(true_residual_check), int(phi0 is not None))
+                   int(true_residual_check), ws)
     st = (FgmresStats * B)()
     if roms is None:
         rarr = None

@@ -728,8 +728,27 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
   std::vector<int> all(B, 1), zero(B, 0);
   // b~ (FP64 sweep, counted)
   RTE_TRY(launch_T(p, MODE_RHS, true, nullptr, true, nullptr, ws->bt.p, true, nullptr, st));
-  const bool warm = o->warm_start && phi0 != nullptr;
+  bool warm = o->warm_start == 1 && phi0 != nullptr;
   if (warm) RTE_CHECK_CUDA(cudaMemcpyAsync(x, phi0, p->ntot * 8, cudaMemcpyDeviceToDevice, st));
+  if (o->warm_start == 2 && roms) {
+    // learned warm start: phi0 = b~ + W c_hat(mu) per ROM group with an MLP, zero elsewhere
+    RTE_CHECK_CUDA(cudaMemsetAsync(x, 0, p->ntot * 8, st));
+    std::vector<std::pair<romsad_t, int>> groups;
+    for (int b = 0; b < p->B; ++b)
+      if (roms[b] && roms[b]->mlp) groups.push_back({roms[b], b});
+    std::sort(groups.begin(), groups.end());
+    size_t g0 = 0;
+    while (g0 < groups.size()) {
+      size_t g1 = g0;
+      std::vector<int> ids;
+      while (g1 < groups.size() && groups[g1].first == groups[g0].first) ids.push_back(groups[g1++].second);
+      RTE_CHECK_CUDA(cudaMemcpyAsync(ws->list.p, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+      RTE_TRY(mlp_predict_instances(groups[g0].first->mlp, p, ws->list.p, ids, ws->rom_c.p, st));
+      RTE_TRY(rom_lift_list(groups[g0].first, p, ws->list.p, (int)ids.size(), ws->bt.p, ws->rom_c.p, x, st));
+      g0 = g1;
+    }
+    warm = !groups.empty();
+  }
   std::vector<fgmres_stats> S(B);
   for (int b = 0; b < B; ++b) {
     std::memset(&S[b], 0, sizeof(fgmres_stats));

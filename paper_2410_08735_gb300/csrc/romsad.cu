@@ -320,6 +320,16 @@ int rom_small_solve(romsad* rom, rte_problem* p, const int* d_list, int ninst, c
   return RTE_OK;
 }
 
+int rom_lift_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* v, const double* c,
+                  double* z, cudaStream_t st) {
+  if (ninst == 0) return RTE_OK;
+  dim3 grid((rom->N + 255) / 256, ninst);
+  k_lift<double><<<grid, 256, 0, st>>>(rom->W.p, rom->rmax, rom->r, p->d_inst.p, d_list, v, c, z);
+  count_launch();
+  RTE_CHECK_CUDA(cudaGetLastError());
+  return RTE_OK;
+}
+
 int rom_project_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* v, double* y,
                      cudaStream_t st) {
   if (ninst == 0) return RTE_OK;

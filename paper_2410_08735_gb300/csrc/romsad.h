@@ -2,6 +2,8 @@
 #pragma once
 #include "internal.h"
 
+struct rte_mlp;
+
 struct romsad {
   // mesh the ROM belongs to (must match every instance it is applied to)
   int dim = 2, nx = 0, ny = 0, nd = 4, ndir = 0, nu = 0, R = 1, rx = 1, ry = 1;
@@ -26,6 +28,7 @@ struct romsad {
   std::vector<double> T_R;     // [R][r][r] sum_a mult_a U_a^T chi_R U_a
   std::vector<double> S_R;     // [R][r][r] P^T chi_R W
   rte::DevBuf<double> d_aff;   // [(1 + 2R)][r][r] device copy: A_D, T_R..., S_R...
+  rte_mlp* mlp = nullptr;      // learned warm start (not owned)
 };
 
 namespace rte {
@@ -56,6 +59,12 @@ int rom_small_solve(romsad* rom, rte_problem* p, const int* d_list, int ninst, c
 int rom_apply_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* v, double* z,
                    bool f64, double* scratch_y, double* scratch_c, cudaStream_t st);
 int rom_check_mesh(const romsad* rom, const rte_problem* p, int b);
+// z_b = v_b + W c_b for the listed instances (c laid out [ninst][64])
+int rom_lift_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* v, const double* c,
+                  double* z, cudaStream_t st);
+// c_hat of the listed instances from the MLP (host list, device list copy), out [ninst][64]
+int mlp_predict_instances(rte_mlp* M, rte_problem* p, const int* d_list, const std::vector<int>& list, double* c_out,
+                          cudaStream_t st);
 int rom_upload_affine(romsad* rom);
 int rom_build_operators_from_U(romsad* rom, rte_problem* tmpl, int inst, cudaStream_t st);
 }  // namespace rte
