@@ -183,6 +183,7 @@ def main():
     ap.add_argument("--max-iter", type=int, default=6000)
     ap.add_argument("--inner-rtol", type=float, default=1e-2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mlp-epochs", type=int, default=300)
     ap.add_argument("--ref-sample", type=int, default=40, help="oracle FGMRES iterations per reference step")
     ap.add_argument("--ref-iters", type=int, default=500, help="iterations of a full solve for extrapolation")
     args = ap.parse_args()
@@ -212,11 +213,27 @@ def main():
     n = prob.n_dof
     phi = torch.zeros(n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    common = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=2, stream=stream)
+    # offline (untimed): greedy ROM on the training draws, MLP trained on its labels
+    t_off = time.perf_counter()
+    tr_ss, tr_sa = wl.draw_params(spec, spec.n_train, wl.seed_for(2, 0))
+    tmpl = RB.Problem(spec.with_instances(spec.nx[:1], spec.ny[:1]), tr_ss[:1], tr_sa[:1])
+    rom, rep = RB.Rom.greedy(tmpl, tr_ss, tr_sa, window=spec.window, max_greedy_iter=spec.rom_rank // spec.window,
+                             max_rank=spec.rom_rank, eps_rom=0.0, hf_rtol=1e-10, hf_restart=args.restart,
+                             hf_max_iter=args.max_iter, want_labels=True, indicator_f32=True)
+    t_greedy = time.perf_counter() - t_off
+    net = RB.Mlp(2 * R, 128, rep["rank"], seed=2410)
+    mlp_loss = net.train(np.concatenate([tr_ss, tr_sa], axis=1), rep["labels"], epochs=args.mlp_epochs,
+                         batch=min(64, spec.n_train), lr=2e-3, bf16=True)
+    RB.attach_mlp(rom, net)
+    t_offline = time.perf_counter() - t_off
+    roms = [rom] * B
+    common = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window, stream=stream)
 
     def solve(mode):
-        return RB.fgmres_solve(prob, None, phi, mode=mode, inner_rtol=args.inner_rtol, max_outer=30,
-                               true_residual_check=True, **common)
+        if mode == RB.RTE_MODE_MIXED:
+            return RB.fgmres_solve(prob, roms, phi, mode=mode, inner_rtol=args.inner_rtol, max_outer=30,
+                                   learned_warm_start=True, **common)
+        return RB.fgmres_solve(prob, roms, phi, mode=mode, true_residual_check=True, **common)
 
     def timed_loop(mode):
         per_step, stats_all = [], []
@@ -261,8 +278,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         prob.set_params(ss, sa)
-        RB.fgmres_solve(prob, None, host_phi, mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol, max_outer=30,
-                        true_residual_check=True, **common)
+        RB.fgmres_solve(prob, roms, host_phi, mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol, max_outer=30,
+                        learned_warm_start=True, **common)
         t1 = time.perf_counter()
         if s >= args.warmup:
             e2e_ms.append(1e3 * (t1 - t0))
@@ -308,15 +325,19 @@ def main():
     if rank != 0:
         return
     line = {
-        "metric": "param solves/s at 1e-8 true residual (mixed FP32-sweep/FP64-Arnoldi vs plain FP64)",
+        "metric": "param solves/s at 1e-8 true residual (mixed+MLP FGMRES-ROMSAD vs plain FP64 FGMRES-ROMSAD)",
         "value": value, "unit": "param solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * mixed_s / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "instances_per_step": B, "mesh": f"{spec.nx[0]}x{spec.ny[0]}",
-                   "directions": spec.n_directions, "restart": args.restart, "preconditioner": "none",
+                   "directions": spec.n_directions, "restart": args.restart,
+                   "preconditioner": f"ROMSAD rank {rep['rank']} (window {spec.window}, kept after the window)",
+                   "warm_start": "MLP 8-128-128-r (mixed path only)",
                    "l2": "flushed (256 MiB write) before every timed step"},
         "fp64": {"value": fp64_value, "unit": "param solves/s", "ms_per_step": 1e3 * fp64_s / args.steps},
         "speedup_mixed_vs_fp64": value / fp64_value,
+        "offline": {"greedy_s": t_greedy, "total_s": t_offline, "rank": rep["rank"], "sampled": len(rep["sampled"]),
+                    "mlp_final_loss": mlp_loss},
         "solver": {
             "mixed_iterations_mean": statistics.mean(s["iterations"] for s in st_mixed),
             "mixed_fp64_sweeps_mean": statistics.mean(s["sweeps_fp64"] for s in st_mixed),

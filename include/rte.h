@@ -138,6 +138,8 @@ typedef struct romsad_greedy_opts {
     double hf_rtol;       /* relative residual of the high-fidelity FGMRES of step 2(a)      */
     int hf_restart;       /* restart length of that solve                                    */
     int hf_max_iter;
+    int indicator_f32;    /* 1: evaluate the eq. rom-residual indicator in FP32 (it only decides the
+                             argmax sample); 0: FP64                                           */
 } romsad_greedy_opts;
 
 typedef struct romsad_report {

@@ -49,7 +49,8 @@ class ProblemInfo(ctypes.Structure):
 class GreedyOpts(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int), ("max_greedy_iter", ctypes.c_int), ("max_rank", ctypes.c_int),
                 ("eps_rom", ctypes.c_double), ("eps_qr", ctypes.c_double), ("mu1", ctypes.c_int),
-                ("hf_rtol", ctypes.c_double), ("hf_restart", ctypes.c_int), ("hf_max_iter", ctypes.c_int)]
+                ("hf_rtol", ctypes.c_double), ("hf_restart", ctypes.c_int), ("hf_max_iter", ctypes.c_int),
+                ("indicator_f32", ctypes.c_int)]
 
 
 class GreedyReport(ctypes.Structure):
@@ -295,11 +296,12 @@ class Rom:
     @classmethod
     def greedy(cls, problem: Problem, train_ss, train_sa, window=2, max_greedy_iter=10, max_rank=32,
                eps_rom=1e-8, eps_qr=1e-13, mu1=-1, hf_rtol=1e-12, hf_restart=30, hf_max_iter=2000,
-               want_labels=False):
+               want_labels=False, indicator_f32=False):
         ss = np.ascontiguousarray(train_ss, dtype=np.float64)
         sa = np.ascontiguousarray(train_sa, dtype=np.float64)
         n_train = ss.shape[0]
-        o = GreedyOpts(window, max_greedy_iter, max_rank, eps_rom, eps_qr, mu1, hf_rtol, hf_restart, hf_max_iter)
+        o = GreedyOpts(window, max_greedy_iter, max_rank, eps_rom, eps_qr, mu1, hf_rtol, hf_restart, hf_max_iter,
+                       int(indicator_f32))
         sampled = (ctypes.c_int * max_greedy_iter)()
         ind = (ctypes.c_double * max_greedy_iter)()
         labels = np.zeros((n_train, max_rank)) if want_labels else None

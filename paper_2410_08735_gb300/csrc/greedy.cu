@@ -74,29 +74,29 @@ __global__ void k_base(const double* W, int rmax, int r, const double* c, const 
 //   e_i = sum_k (Y[k][u][i] + sigma_t(i) U[k][u][i]) c_mu[k] - base_mu[i]
 // A block holds a chunk of 256 dofs of one direction u and a tile of MT parameters: each U/Y value
 // is read once and used for all MT parameters (accumulators in registers).
-template <int MT>
-__global__ void k_indicator(const double* U, const double* Y, int nA, int N, int r, const double* c,
+template <typename T, int MT>
+__global__ void k_indicator(const T* U, const T* Y, int nA, int N, int r, const double* c,
                             const double* base, const int* mus, int nmu, const double* sig_t, int R, int rx, int ry,
                             int nx, int ny, int nd, double* part) {
   const int u = blockIdx.y;
   const int chunk = blockIdx.x;
   const int mt0 = blockIdx.z * MT;
   const int i = chunk * 256 + threadIdx.x;
-  __shared__ double cs[64][MT];
+  __shared__ T cs[64][MT];
   __shared__ double red[8][MT];
   for (int e = threadIdx.x; e < MT * 64; e += blockDim.x) {
     const int k = e / MT, m = e % MT;
-    cs[k][m] = (mt0 + m < nmu && k < r) ? c[(size_t)mus[mt0 + m] * 64 + k] : 0.0;
+    cs[k][m] = (T)((mt0 + m < nmu && k < r) ? c[(size_t)mus[mt0 + m] * 64 + k] : 0.0);
   }
   __syncthreads();
-  double a[MT], b[MT];
+  T a[MT], b[MT];
 #pragma unroll
-  for (int m = 0; m < MT; ++m) { a[m] = 0.0; b[m] = 0.0; }
+  for (int m = 0; m < MT; ++m) { a[m] = (T)0; b[m] = (T)0; }
   int reg = 0;
   if (i < N) {
     for (int k = 0; k < r; ++k) {
-      const double yk = Y[((size_t)k * nA + u) * N + i];
-      const double uk = U[((size_t)k * nA + u) * N + i];
+      const T yk = Y[((size_t)k * nA + u) * N + i];
+      const T uk = U[((size_t)k * nA + u) * N + i];
 #pragma unroll
       for (int m = 0; m < MT; ++m) {
         a[m] += yk * cs[k][m];
@@ -113,7 +113,7 @@ __global__ void k_indicator(const double* U, const double* Y, int nA, int N, int
     double e2 = 0.0;
     if (i < N && mt0 + m < nmu) {
       const int mu = mus[mt0 + m];
-      const double e = a[m] + sig_t[(size_t)mu * R + reg] * b[m] - base[(size_t)mu * N + i];
+      const double e = (double)a[m] + sig_t[(size_t)mu * R + reg] * (double)b[m] - base[(size_t)mu * N + i];
       e2 = e * e;
     }
     for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
@@ -237,6 +237,11 @@ static int greedy_impl(rte_problem* tmpl, int n_train, const double* tss, const 
   RTE_TRY(xi.alloc((size_t)std::max(1, window) * N));
   const long long nang = (long long)rom->nA * N;
   RTE_TRY(snap.alloc(nang));
+  DevBuf<float> U32, Y32;   // FP32 copies of the basis for the FP32 indicator
+  if (o->indicator_f32) {
+    RTE_TRY(U32.alloc((size_t)rom->rmax * nang));
+    RTE_TRY(Y32.alloc((size_t)rom->rmax * nang));
+  }
   const unsigned vb = (unsigned)std::min<long long>(4096, (nang + 255) / 256);
   while (true) {
     // Step 2(a): high-fidelity solve for mu_k, first cycle recorded
@@ -293,6 +298,12 @@ static int greedy_impl(rte_problem* tmpl, int n_train, const double* tss, const 
       k_scal_copy<<<vb, 256, 0, st>>>(rom->U.p + (size_t)rom->r * nang, snap.p, 1.0 / nu, nang);
       count_launch();
       RTE_TRY(rom_compute_Y_column(rom, hp.p, 0, rom->r, st));
+      if (o->indicator_f32) {
+        k_to_f32<<<vb, 256, 0, st>>>(U32.p + (size_t)rom->r * nang, rom->U.p + (size_t)rom->r * nang, nang);
+        count_launch();
+        k_to_f32<<<vb, 256, 0, st>>>(Y32.p + (size_t)rom->r * nang, rom->Y.p + (size_t)rom->r * nang, nang);
+        count_launch();
+      }
       RTE_TRY(rom_add_column(rom, d_mult, d_wA, st));
     }
     if ((int)sampled.size() >= o->max_greedy_iter || rom->r >= o->max_rank || (int)sampled.size() == n_train ||
@@ -325,9 +336,14 @@ static int greedy_impl(rte_problem* tmpl, int n_train, const double* tss, const 
     constexpr int MT = 8;
     RTE_TRY(ipart.alloc((size_t)n_train * rom->nA * nchunk));
     dim3 gi(nchunk, rom->nA, (nmu + MT - 1) / MT);
-    k_indicator<MT><<<gi, 256, 0, st>>>(rom->U.p, rom->Y.p, rom->nA, N, rom->r, cs.p, base.p, d_mus.p, nmu,
+    if (o->indicator_f32)
+      k_indicator<float, MT><<<gi, 256, 0, st>>>(U32.p, Y32.p, rom->nA, N, rom->r, cs.p, base.p, d_mus.p, nmu,
                                                  tp.p->d_sig_t.p, R, tp.p->rx, tp.p->ry, tp.p->nx[0], tp.p->ny[0],
                                                  tp.p->nd, ipart.p);
+    else
+      k_indicator<double, MT><<<gi, 256, 0, st>>>(rom->U.p, rom->Y.p, rom->nA, N, rom->r, cs.p, base.p, d_mus.p, nmu,
+                                                  tp.p->d_sig_t.p, R, tp.p->rx, tp.p->ry, tp.p->nx[0], tp.p->ny[0],
+                                                  tp.p->nd, ipart.p);
     count_launch();
     RTE_CHECK_CUDA(cudaGetLastError());
     std::vector<double> hp_((size_t)n_train * rom->nA * nchunk);

@@ -408,9 +408,11 @@ struct Ws {
   DevBuf<double> bnorm, beta, est, nrm;
   DevBuf<int> active, brk, flag, kcols, iters_left, list;
   DevBuf<double> rom_y, rom_c;
-  int* hflag = nullptr;   // pinned host mirror of flag
+  int* hflag = nullptr;   // pinned host mirrors of flag and kcols
+  int* hk = nullptr;
   ~Ws() {
     if (hflag) cudaFreeHost(hflag);
+    if (hk) cudaFreeHost(hk);
   }
   int alloc(rte_problem* p, int m_, bool withZ_) {
     if (B == p->B && m == m_ && ntot == p->ntot && (withZ == withZ_ || !withZ_)) return RTE_OK;
@@ -442,7 +444,9 @@ struct Ws {
     RTE_TRY(rom_y.alloc((size_t)B * 64));
     RTE_TRY(rom_c.alloc((size_t)B * 64));
     if (hflag) cudaFreeHost(hflag);
+    if (hk) cudaFreeHost(hk);
     RTE_CHECK_CUDA(cudaMallocHost(&hflag, B * sizeof(int)));
+    RTE_CHECK_CUDA(cudaMallocHost(&hk, B * sizeof(int)));
     return RTE_OK;
   }
 };
@@ -453,8 +457,16 @@ struct SolveCtx {
   int m, window, post;
   cudaStream_t st;
   Ws* ws;
-  FirstCycle* rec = nullptr;  // records the first cycle of instance 0 (greedy high-fidelity solve)
+  FirstCycle* rec = nullptr;          // records the first cycle of instance 0 (greedy high-fidelity solve)
+  std::vector<RomPlan>* plans = nullptr;  // one per ROM group (factored once per solve)
+  std::vector<int> no_rom_mask;       // [B] 1 for instances without a ROM
 };
+
+// dst[b] = dst[b] && m[b]
+__global__ void k_mask_and(int* dst, const int* m, int B) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) dst[b] = dst[b] && m[b];
+}
 
 static dim3 vec_grid(rte_problem* p) {
   int maxn = 0;
@@ -541,50 +553,50 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
     }
     std::vector<int> incycle(act);
     std::vector<int> outcome(B, RUN);
+    std::vector<int> its0(rs.iterations);   // iterations before this cycle
+    int it_first = 0;
+    for (int b = 0; b < B; ++b)
+      if (act[b]) { it_first = it_base[b] + rs.iterations[b]; break; }
+    // The device drops finished instances from the active mask itself (k_givens), so the host reads
+    // the flags only every kCheck iterations: instances that stopped in between are skipped by
+    // every kernel until the host catches up.
+    const int kCheck = 8;
     for (int j = 0; j < m; ++j) {
       // preconditioner
       double* vj = W.V.p + (size_t)j * ntot;
       double* zj = Zbase + (size_t)j * ntot;
       if (W.withZ) {
-        // instances without ROM (or past the window with identity): copy; with ROM: apply per ROM group
-        std::vector<int> ident(B, 0);
-        std::vector<std::pair<romsad_t, int>> romlist;
-        for (int b = 0; b < B; ++b) {
-          if (!act[b]) continue;
-          romsad_t rb = C.roms ? C.roms[b] : nullptr;
-          const int jg = it_base[b] + rs.iterations[b] + 1;  // 1-based global iteration index
-          if (rb && (jg <= C.window || C.post == RTE_POST_ROM)) romlist.push_back({rb, b});
-          else ident[b] = 1;
-        }
-        RTE_CHECK_CUDA(cudaMemcpyAsync(W.brk.p, ident.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-        k_copy_active<<<vg, 256, 0, st>>>(zj, vj, p->d_inst.p, W.brk.p);
-        count_launch();
-        std::sort(romlist.begin(), romlist.end());
-        size_t s0 = 0;
-        while (s0 < romlist.size()) {
-          size_t s1 = s0;
-          std::vector<int> ids;
-          while (s1 < romlist.size() && romlist[s1].first == romlist[s0].first) ids.push_back(romlist[s1++].second);
-          RTE_CHECK_CUDA(cudaMemcpyAsync(W.list.p, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-          RTE_TRY(rom_apply_list(romlist[s0].first, p, W.list.p, (int)ids.size(), vj, zj, f64, W.rom_y.p, W.rom_c.p,
-                                 st));
-          s0 = s1;
+        // ROMSAD for instances with a ROM while j is inside the window (or always with POST_ROM);
+        // identity (a copy) otherwise.  Lock-step instances share the global iteration index.
+        const int jg = it_first + j + 1;
+        const bool use_rom = jg <= C.window || C.post == RTE_POST_ROM;
+        if (use_rom) {
+          RTE_CHECK_CUDA(cudaMemcpyAsync(W.brk.p, C.no_rom_mask.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+          k_mask_and<<<(B + 127) / 128, 128, 0, st>>>(W.brk.p, W.active.p, B);
+          count_launch();
+          k_copy_active<<<vg, 256, 0, st>>>(zj, vj, p->d_inst.p, W.brk.p);
+          count_launch();
+          for (auto& pl : *C.plans) RTE_TRY(pl.apply(p, W.active.p, vj, zj, f64, st));
+        } else {
+          k_copy_active<<<vg, 256, 0, st>>>(zj, vj, p->d_inst.p, W.active.p);
+          count_launch();
         }
       }
       // w = A~ z_j into V[j+1]
       RTE_TRY(launch_T(p, MODE_OP, f64, zj, true, nullptr, W.V.p + (size_t)(j + 1) * ntot, true, W.active.p, st));
       RTE_TRY(launch_mgs(p, W.V.p, ntot, j, m, W.active.p, W.H.p, C.rec ? W.Hraw.p : nullptr, W.brk.p, st));
       k_givens<<<B, 128, 0, st>>>(W.H.p, W.cs.p, W.sn.p, W.g.p, j, m, B, W.active.p, W.brk.p,
-                                                W.bnorm.p, rtol, W.iters_left.p, W.est.p, W.flag.p, W.kcols.p);
+                                  W.bnorm.p, rtol, W.iters_left.p, W.est.p, W.flag.p, W.kcols.p);
       count_launch();
       RTE_CHECK_CUDA(cudaGetLastError());
+      if ((j + 1) % kCheck != 0 && j != m - 1) continue;
       RTE_CHECK_CUDA(cudaMemcpyAsync(W.hflag, W.flag.p, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+      RTE_CHECK_CUDA(cudaMemcpyAsync(W.hk, W.kcols.p, B * sizeof(int), cudaMemcpyDeviceToHost, st));
       RTE_CHECK_CUDA(cudaStreamSynchronize(st));
       int still = 0;
       for (int b = 0; b < B; ++b) {
         if (!act[b]) continue;
-        rs.iterations[b] += 1;
-        rs.sweeps[b] += 1;
+        rs.iterations[b] = its0[b] + W.hk[b];
         if (W.hflag[b] != RUN) {
           outcome[b] = W.hflag[b];
           act[b] = 0;
@@ -594,6 +606,8 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
       }
       if (still == 0) break;
     }
+    for (int b = 0; b < B; ++b)
+      if (incycle[b]) rs.sweeps[b] += rs.iterations[b] - its0[b];   // one operator apply per iteration
     // first-cycle record for the xi recurrence: unrotated H, the Krylov basis (Z = V without a
     // preconditioner) and beta
     if (C.rec && !C.rec->done) {
@@ -725,6 +739,25 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
   }
   const int B = p->B;
   SolveCtx C{p, roms, o->restart, o->window, o->post_mode, st, ws};
+  // ROM plans: group instances by ROM handle, assemble and factor U^T A_mu U once per solve
+  std::vector<RomPlan> plans;
+  C.no_rom_mask.assign(B, 1);
+  if (roms) {
+    std::vector<std::pair<romsad_t, int>> groups;
+    for (int b = 0; b < B; ++b)
+      if (roms[b]) { groups.push_back({roms[b], b}); C.no_rom_mask[b] = 0; }
+    std::sort(groups.begin(), groups.end());
+    size_t g0 = 0;
+    while (g0 < groups.size()) {
+      size_t g1 = g0;
+      std::vector<int> ids;
+      while (g1 < groups.size() && groups[g1].first == groups[g0].first) ids.push_back(groups[g1++].second);
+      plans.emplace_back();
+      RTE_TRY(plans.back().build(groups[g0].first, p, ids, st));
+      g0 = g1;
+    }
+  }
+  C.plans = &plans;
   std::vector<int> all(B, 1), zero(B, 0);
   // b~ (FP64 sweep, counted)
   RTE_TRY(launch_T(p, MODE_RHS, true, nullptr, true, nullptr, ws->bt.p, true, nullptr, st));

@@ -310,6 +310,181 @@ __global__ void k_lift(const TP* W, int rmax, int r, const InstInfo* inst, const
   }
 }
 
+// ------------------------------------------------- factor once, apply many times (online path)
+// LU with partial pivoting of U^T A_mu U for every listed instance; one block per instance.
+__global__ void k_rom_factor(const double* aff, int r, int R, const double* sig_s, const double* sig_t, const int* list,
+                             double* lu, int* piv) {
+  extern __shared__ double sm[];
+  double* A = sm;
+  __shared__ int piv_s;
+  const int b = list[blockIdx.x];
+  const size_t rr = (size_t)r * r;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    double v = aff[e];
+    for (int q = 0; q < R; ++q)
+      v += sig_t[(size_t)b * R + q] * aff[(1 + q) * rr + e] - sig_s[(size_t)b * R + q] * aff[(1 + R + q) * rr + e];
+    A[e] = v;
+  }
+  __syncthreads();
+  int* pv = piv + (size_t)blockIdx.x * 64;
+  for (int col = 0; col < r; ++col) {
+    if (threadIdx.x == 0) {
+      int p = col;
+      double best = fabs(A[col * r + col]);
+      for (int i = col + 1; i < r; ++i)
+        if (fabs(A[i * r + col]) > best) { best = fabs(A[i * r + col]); p = i; }
+      piv_s = p;
+      pv[col] = p;
+    }
+    __syncthreads();
+    const int p = piv_s;
+    if (p != col)
+      for (int j = threadIdx.x; j < r; j += blockDim.x) {
+        double t = A[col * r + j]; A[col * r + j] = A[p * r + j]; A[p * r + j] = t;
+      }
+    __syncthreads();
+    const double d = A[col * r + col];
+    for (int i = col + 1 + threadIdx.x; i < r; i += blockDim.x) {
+      const double f = A[i * r + col] / d;
+      A[i * r + col] = f;   // L below the diagonal
+      for (int j = col + 1; j < r; ++j) A[i * r + j] -= f * A[col * r + j];
+    }
+    __syncthreads();
+  }
+  double* out = lu + (size_t)blockIdx.x * 64 * 64;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) out[e] = A[e];
+}
+
+// Partial projections: part[(inst, chunk)][k] = sum over the chunk's dofs of P[i][k] sigma_s(i) v[i].
+// grid (nchunk, ninst); 8 warps stride over the chunk, lanes over k (two columns per lane).
+template <typename TP>
+__global__ void k_project_part(const TP* P, int rmax, int r, const InstInfo* inst, const int* list, const int* active,
+                               const double* sig_s, int R, int rx, int ry, int nd, const double* v, int chunk,
+                               double* part) {
+  const int b = list[blockIdx.y];
+  if (active && !active[b]) return;
+  const InstInfo in = inst[b];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int cx = in.nx / rx, cy = in.ny / ry;
+  const int i0 = blockIdx.x * chunk, i1 = min(in.ndof, i0 + chunk);
+  double acc0 = 0.0, acc1 = 0.0;
+  const double* vb = v + in.off;
+  for (int i = i0 + warp; i < i1; i += nw) {
+    const int c = i / nd;
+    const int ix = c % in.nx, iy = c / in.nx;
+    const double sv = sig_s[(size_t)b * R + (iy / cy) * rx + ix / cx] * vb[i];
+    if (lane < r) acc0 += (double)P[(size_t)i * rmax + lane] * sv;
+    if (lane + 32 < r) acc1 += (double)P[(size_t)i * rmax + lane + 32] * sv;
+  }
+  __shared__ double red[8][64];
+  red[warp][lane] = acc0;
+  red[warp][lane + 32] = acc1;
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w][threadIdx.x];
+    part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 64 + threadIdx.x] = s;
+  }
+}
+
+// c = (LU)^{-1} y with y = sum of the partials (fixed chunk order); one block of 64 threads per instance.
+__global__ void k_rom_lu_solve(const double* part, int nchunk, int r, const double* lu, const int* piv,
+                               const int* list, const int* active, double* c) {
+  const int b = list[blockIdx.x];
+  if (active && !active[b]) return;
+  __shared__ double x[64];
+  __shared__ double xi;
+  const int t = threadIdx.x;
+  if (t < r) {
+    double s = 0.0;
+    for (int ch = 0; ch < nchunk; ++ch) s += part[((size_t)blockIdx.x * nchunk + ch) * 64 + t];
+    x[t] = s;
+  }
+  __syncthreads();
+  const int* pv = piv + (size_t)blockIdx.x * 64;
+  const double* A = lu + (size_t)blockIdx.x * 64 * 64;
+  if (t == 0)
+    for (int k = 0; k < r; ++k) {
+      const int p = pv[k];
+      if (p != k) { double tmp = x[k]; x[k] = x[p]; x[p] = tmp; }
+    }
+  __syncthreads();
+  for (int k = 0; k < r; ++k) {          // forward substitution with unit L
+    const double xk = x[k];
+    __syncthreads();
+    if (t > k && t < r) x[t] -= A[t * r + k] * xk;
+    __syncthreads();
+  }
+  for (int k = r - 1; k >= 0; --k) {     // back substitution with U
+    if (t == 0) xi = x[k] / A[k * r + k];
+    __syncthreads();
+    const double v = xi;
+    if (t == 0) x[k] = v;
+    if (t < k) x[t] -= A[t * r + k] * v;
+    __syncthreads();
+  }
+  if (t < r) c[(size_t)blockIdx.x * 64 + t] = x[t];
+}
+
+// z_b = v_b + W c_b; grid (chunks, listed instances), skipping inactive instances
+template <typename TP>
+__global__ void k_lift_masked(const TP* W, int rmax, int r, const InstInfo* inst, const int* list, const int* active,
+                              const double* v, const double* c, double* z) {
+  const int b = list[blockIdx.y];
+  if (active && !active[b]) return;
+  const InstInfo in = inst[b];
+  __shared__ double cs[64];
+  for (int k = threadIdx.x; k < r; k += blockDim.x) cs[k] = c[(size_t)blockIdx.y * 64 + k];
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) {
+    const TP* w = W + (size_t)i * rmax;
+    double s = 0.0;
+    for (int k = 0; k < r; ++k) s += (double)w[k] * cs[k];
+    z[in.off + i] = v[in.off + i] + s;
+  }
+}
+
+int RomPlan::build(romsad* rom_, rte_problem* p, const std::vector<int>& ids_, cudaStream_t st) {
+  rom = rom_;
+  ids = ids_;
+  const int n = (int)ids.size();
+  RTE_TRY(d_ids.alloc(n));
+  RTE_CHECK_CUDA(cudaMemcpyAsync(d_ids.p, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+  RTE_TRY(lu.alloc((size_t)n * 64 * 64));
+  RTE_TRY(piv.alloc((size_t)n * 64));
+  chunk = 1024;
+  nchunk = (rom->N + chunk - 1) / chunk;
+  RTE_TRY(part.alloc((size_t)n * nchunk * 64));
+  RTE_TRY(c.alloc((size_t)n * 64));
+  size_t smem = (size_t)rom->r * rom->r * 8;
+  k_rom_factor<<<n, 128, smem, st>>>(rom->d_aff.p, rom->r, rom->R, p->d_sig_s.p, p->d_sig_t.p, d_ids.p, lu.p, piv.p);
+  count_launch();
+  RTE_CHECK_CUDA(cudaGetLastError());
+  return RTE_OK;
+}
+
+int RomPlan::apply(rte_problem* p, const int* d_active, const double* v, double* z, bool f64, cudaStream_t st) {
+  const int n = (int)ids.size();
+  dim3 gp(nchunk, n);
+  if (f64)
+    k_project_part<double><<<gp, 256, 0, st>>>(rom->P.p, rom->rmax, rom->r, p->d_inst.p, d_ids.p, d_active,
+                                               p->d_sig_s.p, p->R, p->rx, p->ry, p->nd, v, chunk, part.p);
+  else
+    k_project_part<float><<<gp, 256, 0, st>>>(rom->P32.p, rom->rmax, rom->r, p->d_inst.p, d_ids.p, d_active,
+                                              p->d_sig_s.p, p->R, p->rx, p->ry, p->nd, v, chunk, part.p);
+  count_launch();
+  k_rom_lu_solve<<<n, 64, 0, st>>>(part.p, nchunk, rom->r, lu.p, piv.p, d_ids.p, d_active, c.p);
+  count_launch();
+  dim3 gl((rom->N + 255) / 256, n);
+  if (f64)
+    k_lift_masked<double><<<gl, 256, 0, st>>>(rom->W.p, rom->rmax, rom->r, p->d_inst.p, d_ids.p, d_active, v, c.p, z);
+  else
+    k_lift_masked<float><<<gl, 256, 0, st>>>(rom->W32.p, rom->rmax, rom->r, p->d_inst.p, d_ids.p, d_active, v, c.p, z);
+  count_launch();
+  RTE_CHECK_CUDA(cudaGetLastError());
+  return RTE_OK;
+}
+
 int rom_small_solve(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* y, double* c,
                     cudaStream_t st) {
   const int r = rom->r;
@@ -340,28 +515,6 @@ int rom_project_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, 
   return RTE_OK;
 }
 
-int rom_apply_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* v, double* z, bool f64,
-                   double* scratch_y, double* scratch_c, cudaStream_t st) {
-  if (ninst == 0) return RTE_OK;
-  const int r = rom->r;
-  if (f64)
-    k_project<double><<<ninst, 256, 0, st>>>(rom->P.p, rom->rmax, r, p->d_inst.p, d_list, p->d_sig_s.p, p->R, p->rx,
-                                             p->ry, p->nd, v, scratch_y);
-  else
-    k_project<float><<<ninst, 256, 0, st>>>(rom->P32.p, rom->rmax, r, p->d_inst.p, d_list, p->d_sig_s.p, p->R, p->rx,
-                                            p->ry, p->nd, v, scratch_y);
-    count_launch();
-  RTE_CHECK_CUDA(cudaGetLastError());
-  RTE_TRY(rom_small_solve(rom, p, d_list, ninst, scratch_y, scratch_c, st));
-  dim3 grid((rom->N + 255) / 256, ninst);
-  if (f64)
-    k_lift<double><<<grid, 256, 0, st>>>(rom->W.p, rom->rmax, r, p->d_inst.p, d_list, v, scratch_c, z);
-  else
-    k_lift<float><<<grid, 256, 0, st>>>(rom->W32.p, rom->rmax, r, p->d_inst.p, d_list, v, scratch_c, z);
-    count_launch();
-  RTE_CHECK_CUDA(cudaGetLastError());
-  return RTE_OK;
-}
 
 int rom_alloc_arrays(romsad* rom, int rmax, bool withU) {
   rom->rmax = rmax;
@@ -492,15 +645,11 @@ int romsad_apply(romsad_t rom, rte_problem_t p, int dtype, const void* v, void* 
   RTE_ARG(dtype == RTE_F64, "romsad_apply takes FP64 vectors");
   for (int b = 0; b < p->B; ++b) RTE_TRY(rom_check_mesh(rom, p, b));
   cudaStream_t st = (cudaStream_t)stream;
-  DevBuf<int> list;
-  DevBuf<double> ys, cs;
-  RTE_TRY(list.alloc(p->B));
-  RTE_TRY(ys.alloc((size_t)p->B * 64));
-  RTE_TRY(cs.alloc((size_t)p->B * 64));
-  std::vector<int> h(p->B);
-  for (int b = 0; b < p->B; ++b) h[b] = b;
-  RTE_CHECK_CUDA(cudaMemcpyAsync(list.p, h.data(), p->B * sizeof(int), cudaMemcpyHostToDevice, st));
-  RTE_TRY(rom_apply_list(rom, p, list.p, p->B, (const double*)v, (double*)z, true, ys.p, cs.p, st));
+  std::vector<int> ids(p->B);
+  for (int b = 0; b < p->B; ++b) ids[b] = b;
+  RomPlan plan;
+  RTE_TRY(plan.build(rom, p, ids, st));
+  RTE_TRY(plan.apply(p, nullptr, (const double*)v, (double*)z, true, st));
   RTE_CHECK_CUDA(cudaStreamSynchronize(st));
   return RTE_OK;
 }

@@ -50,14 +50,22 @@ int rom_alloc_arrays(romsad* rom, int rmax, bool withU);
 // y[b][k] = (P^T Sigma_s v_b)[k] for the listed instances (FP64), y laid out [ninst][64]
 int rom_project_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* v, double* y,
                      cudaStream_t st);
+// ROMSAD application plan for one ROM and the instances that use it, built once per solve: the
+// reduced operators U^T A_mu U are assembled and LU-factored at build; apply() then costs one
+// projection (multi-block partial sums), two triangular solves and one lift.
+struct RomPlan {
+  romsad* rom = nullptr;
+  std::vector<int> ids;
+  DevBuf<int> d_ids, piv;
+  DevBuf<double> lu, part, c;
+  int chunk = 1024, nchunk = 0;
+  int build(romsad* rom, rte_problem* p, const std::vector<int>& ids, cudaStream_t st);
+  int apply(rte_problem* p, const int* d_active, const double* v, double* z, bool f64, cudaStream_t st);
+};
 // Assemble and LU-factor U^T A_mu U for the listed instances of p (device), then
 // c = A_r^{-1} y per instance: y [ninst][r] in, c [ninst][r] out (FP64).
 int rom_small_solve(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* y, double* c,
                     cudaStream_t st);
-// z_b = v_b + W (U^T A_mu U)^{-1} P^T Sigma_s v_b for the listed instances (all on the ROM's mesh).
-// f64: FP64 P/W and vectors; otherwise FP32 P/W products with FP64 vectors in and out.
-int rom_apply_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* v, double* z,
-                   bool f64, double* scratch_y, double* scratch_c, cudaStream_t st);
 int rom_check_mesh(const romsad* rom, const rte_problem* p, int b);
 // z_b = v_b + W c_b for the listed instances (c laid out [ninst][64])
 int rom_lift_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, const double* v, const double* c,
