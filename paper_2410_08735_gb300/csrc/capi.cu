@@ -10,6 +10,8 @@ static thread_local std::string g_last_error;
 static std::atomic<long long> g_launches{0};
 void set_error(const std::string& msg) { g_last_error = msg; }
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(); }
 }  // namespace rte
 
 extern "C" {

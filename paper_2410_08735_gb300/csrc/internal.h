@@ -15,6 +15,8 @@ namespace rte {
 void set_error(const std::string& msg);
 // number of kernels this library has launched (reported by rte_kernel_launches)
 void count_launch();
+void add_launches(long long n);
+long long launches_so_far();
 struct Status {
   int code = RTE_OK;
 };
@@ -129,13 +131,17 @@ struct rte_problem {
   rte::DevBuf<rte::UDir> d_udir;
   rte::DevBuf<double> d_sig_s, d_sig_t;       // [B][R]
   rte::DevBuf<float> d_sig_s32;               // [B][R]
+  rte::DevBuf<double> d_sig_dof;              // [ntot] sigma_s of every dof (ROM projections)
   rte::DevBuf<double> d_G;                    // [ntot] source moments
   rte::DevBuf<double> d_linv64;               // [B][nu][R][nd*nd]
   rte::DevBuf<float> d_linv32;
   // sweep scratch (grown on demand)
   rte::DevBuf<unsigned char> d_partial;       // partial scalar fluxes per task
-  rte::DevBuf<rte::SweepTask> d_tasks;
-  int tasks_D = -1;                           // directions per task of the cached task list
+  // task lists per directions-per-warp value D (index D), built once; stable device pointers
+  rte::DevBuf<rte::SweepTask> d_tasks_by_D[17];
+  int ntasks_by_D[17] = {0};
+  int per_inst_by_D[17] = {0};
+  int tasks_D = -1;                           // D of the most recent launch
   int ntasks = 0, tasks_per_inst = 0;
   rte::DevBuf<int> d_active;                  // [B] instance mask (1 = active), all 1 by default
   rte::DevBuf<double> d_tmp64;                // [ntot] temporaries
@@ -157,6 +163,8 @@ int launch_T(rte_problem* p, int mode, bool compute_f64, const void* src, bool i
 // per unique direction ([nu][N] per instance) instead of all N_Omega directions.
 int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st,
                    bool scale_sigma_s = false, bool unique_layout = false);
+// task lists and partial buffer for both precisions (stable pointers for graph capture)
+int prepare_sweeps(rte_problem* p);
 int launch_scalar_flux(rte_problem* p, bool f64, const void* psi, void* phi, cudaStream_t st);
 // forward operator y = (D_u + sigma_t) x (FP64) for ncol columns on one mesh; used offline
 int launch_forward_cols(int dim, int nx, int ny, double hx, double hy, const UDir& u, int rx, int ry,

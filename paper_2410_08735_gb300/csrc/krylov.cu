@@ -4,7 +4,7 @@
 // is still active in the current cycle.  Per iteration j (0-based):
 //   z_j = M_j^{-1} v_j              ROMSAD (romsad.cu) for j < window, then the post-window operator
 //   w   = A~ z_j                    fused sweep (sweep.cu), written straight into v_{j+1}
-//   MGS: h_ij = w . v_i, w -= h_ij v_i (i = 0..j, sequentially), h_{j+1,j} = ||w||, v_{j+1} = w / h
+//   MGS: h_ij = w . v_i, w -= h_ij v_i (i = 0..j), h_{j+1,j} = ||w||, v_{j+1} = w / h  (compact-WY form)
 //   Givens: rotate column j of H, new rotation, |g_{j+1}| = residual estimate
 // At the end of a cycle y = R^{-1} g and phi += Z y.  MGS, Givens and all Krylov vectors are FP64.
 //
@@ -18,8 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-
-#include <cooperative_groups.h>
+#include <unordered_map>
 
 #include "romsad.h"
 
@@ -98,159 +97,187 @@ __global__ void k_copy_active(double* dst, const double* src, const InstInfo* in
     dst[in.off + i] = src[in.off + i];
 }
 
-// Modified Gram-Schmidt of w = V[j+1] against V[0..j] (Alg. 1), one block per active instance.
-// Writes H[b][:, j] (column-major, ld m+1) and a breakdown flag; normalises V[j+1].
-__global__ void k_mgs(double* V, long long ntot, int j, int m, const InstInfo* inst, const int* active, double* H,
-                      int* brk) {
-  __shared__ double sh[33];
-  const int b = blockIdx.x;
+// Modified Gram-Schmidt in compact-WY form.  The MGS recurrence h_i = v_i.w^(i-1),
+// w^(i) = w^(i-1) - h_i v_i gives h_i = v_i.w - sum_{k<i} (v_i.v_k) h_k, i.e. (I + L) h = V^T w with L
+// the strictly lower part of the Gram matrix V^T V, and w^(j) = w - V h.  The same coefficients are
+// therefore obtained from one pass of dot products (V^T w, plus the new Gram row v_j . V), a (j+1)-long
+// triangular solve and one update pass, instead of j+1 dependent reductions (Swirydowicz, Langou,
+// Ananthan, Yang, Thomas, Numer. Linear Algebra Appl. 2020).  Rounding differs from the sequential
+// loop; the projector is the MGS projector.
+//
+// Pass 1: per (instance, chunk of dofs) partials of a_k = v_k . w (k <= j), g_k = v_k . v_j (k < j)
+// and w . w.  part layout [b][chunk][slot], slots: a (0..j), g (m+1 .. m+j), ww (2m+2).
+__global__ void __launch_bounds__(256) k_cwy_dots(const double* V, long long ntot, int j, int m, const InstInfo* inst,
+                                                  const int* active, int chunk, double* part) {
+  const int b = blockIdx.y;
   if (!active[b]) return;
   const InstInfo in = inst[b];
-  double* w = V + (size_t)(j + 1) * ntot + in.off;
-  double* h = H + ((size_t)b * m + j) * (m + 1);
-  double s = 0.0;
-  for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) s += w[i] * w[i];
-  const double w0 = sqrt(block_sum(s, sh));
-  for (int q = 0; q <= j; ++q) {
-    const double* vq = V + (size_t)q * ntot + in.off;
-    s = 0.0;
-    for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) s += w[i] * vq[i];
-    const double hq = block_sum(s, sh);
-    for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) w[i] -= hq * vq[i];
-    if (threadIdx.x == 0) h[q] = hq;
+  const int i0 = blockIdx.x * chunk;
+  if (i0 >= in.ndof) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nslot = 2 * m + 3;
+  extern __shared__ double red[];   // [8][nslot]
+  const double* w = V + (size_t)(j + 1) * ntot + in.off;
+  const double* vj = V + (size_t)j * ntot + in.off;
+  const int i = i0 + threadIdx.x;
+  const bool ok = i < in.ndof && threadIdx.x < chunk;
+  const double wi = ok ? w[i] : 0.0;
+  const double vji = ok ? vj[i] : 0.0;
+  double vk = ok ? V[in.off + i] : 0.0;
+  for (int kk = 0; kk <= j; ++kk) {
+    const double vnext = (kk < j && ok) ? V[(size_t)(kk + 1) * ntot + in.off + i] : 0.0;
+    double a = vk * wi;
+    double g = vk * vji;
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      g += __shfl_xor_sync(0xffffffffu, g, o);
+    }
+    if (lane == 0) {
+      red[warp * nslot + kk] = a;
+      if (kk < j) red[warp * nslot + m + 1 + kk] = g;
+    }
+    vk = vnext;
   }
-  s = 0.0;
-  for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) s += w[i] * w[i];
-  const double hn = sqrt(block_sum(s, sh));
-  const bool breakdown = !(hn > 1e-14 * w0);
-  if (threadIdx.x == 0) {
-    h[j + 1] = hn;
-    brk[b] = breakdown ? 1 : 0;
-  }
-  if (!breakdown) {
-    const double inv = 1.0 / hn;
-    for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) w[i] *= inv;
+  double s = wi * wi;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) red[warp * nslot + 2 * m + 2] = s;
+  __syncthreads();
+  double* out = part + ((size_t)b * gridDim.x + blockIdx.x) * nslot;
+  const int nw = blockDim.x >> 5;
+  for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
+    const bool used = t <= j || (t >= m + 1 && t < m + 1 + j) || t == 2 * m + 2;
+    if (!used) continue;
+    double acc = 0.0;
+    for (int q = 0; q < nw; ++q) acc += red[q * nslot + t];
+    out[t] = acc;
   }
 }
 
-
-// Modified Gram-Schmidt with one thread-block cluster per instance (Alg. 1 inner loop).  The cluster's
-// CS blocks split w = V[j+1] into contiguous slices held in registers (EPT elements per thread); for
-// q = 0..j every block forms its partial w . v_q, the partials are exchanged through distributed
-// shared memory after one cluster barrier and summed in rank order (deterministic), and each block
-// updates its slice.  v_{q+1} is loaded before the barrier so the load overlaps the exchange.
-template <int EPT>
-__global__ void __launch_bounds__(512) k_mgs_cluster(double* V, long long ntot, int j, int m, const InstInfo* inst,
-                                                     const int* active, double* H, double* Hraw, int* brk) {
-  namespace cg = cooperative_groups;
-  cg::cluster_group cluster = cg::this_cluster();
-  const int CS = (int)cluster.num_blocks();
-  const int rank = (int)cluster.block_rank();
-  const int b = blockIdx.x / CS;
-  if (!active[b]) return;   // uniform for the whole cluster
-  const InstInfo in = inst[b];
-  const int chunk = (in.ndof + CS - 1) / CS;
-  const int i0 = rank * chunk;
-  const int i1 = min(in.ndof, i0 + chunk);
-  __shared__ double part[2][4];  // [buffer][value]: partial sums published to the cluster
-  __shared__ double wsum[16];
-  __shared__ double bcast;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* wg = V + (size_t)(j + 1) * ntot + in.off;
-  double w[EPT], v[EPT];
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) {
-    const int i = i0 + threadIdx.x + e * 512;
-    w[e] = i < i1 ? wg[i] : 0.0;
+// Pass 2 (one block per instance): sum the partials in chunk order, store the Gram row (transposed:
+// Lt[k][j] = v_k . v_j), solve (I + L) h = a by forward substitution in one warp, write H[:, j] and w0.
+__global__ void k_cwy_solve(const double* part, int nchunk, int j, int m, const int* active, double* Lt, double* H,
+                            double* Hraw, double* w0) {
+  const int b = blockIdx.x;
+  if (!active[b]) return;
+  const int nslot = 2 * m + 3;
+  __shared__ double a[130];
+  const double* pb = part + (size_t)b * nchunk * nslot;
+  double* L = Lt + (size_t)b * (m + 1) * (m + 1);
+  for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
+    const bool used = t <= j || (t >= m + 1 && t < m + 1 + j) || t == 2 * m + 2;
+    if (!used) continue;
+    double acc = 0.0;
+    for (int c = 0; c < nchunk; ++c) acc += pb[(size_t)c * nslot + t];
+    if (t <= j) a[t] = acc;
+    else if (t < m + 1 + j) L[(size_t)(t - m - 1) * (m + 1) + j] = acc;
+    else w0[b] = sqrt(acc);
   }
-  // cluster-wide sum of one value per thread, published in part[buf][0]; returns the total
-  auto cluster_sum = [&](double x, int buf) -> double {
-    x = warp_sum(x);
-    if (lane == 0) wsum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      double t = lane < 16 ? wsum[lane] : 0.0;
-      t = warp_sum(t);
-      if (lane == 0) part[buf][0] = t;
-    }
-    cluster.sync();
-    if (warp == 0) {
-      double t = 0.0;
-      if (lane < CS) t = *cluster.map_shared_rank(&part[buf][0], lane);
-      // fixed-order tree over ranks 0..CS-1
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) bcast = t;
-    }
-    __syncthreads();
-    return bcast;
-  };
-  double s = 0.0;
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) s += w[e] * w[e];
-  int buf = 0;
-  const double w0 = sqrt(cluster_sum(s, buf));
-  buf ^= 1;
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
   double* h = H + ((size_t)b * m + j) * (m + 1);
-  const double* vq = V + in.off;
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) {
-    const int i = i0 + threadIdx.x + e * 512;
-    v[e] = i < i1 ? vq[i] : 0.0;
+  double* hr = Hraw ? Hraw + ((size_t)b * m + j) * (m + 1) : nullptr;
+  // forward substitution (I + L) h = a; lane owns rows t = lane + 32 q; the Gram row of step i + 1
+  // (Lt[i+1][t] = v_{i+1} . v_t) is loaded while step i is processed
+  double at[5], lr[5];
+  for (int q = 0; q < 5; ++q) {
+    const int t = lane + 32 * q;
+    at[q] = t <= j ? a[t] : 0.0;
+    lr[q] = (t > 0 && t <= j) ? L[t] : 0.0;   // row 0
   }
-  for (int q = 0; q <= j; ++q) {
-    s = 0.0;
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) s += w[e] * v[e];
-    double vn[EPT];
-    if (q < j) {
-      const double* vnext = V + (size_t)(q + 1) * ntot + in.off;
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) {
-        const int i = i0 + threadIdx.x + e * 512;
-        vn[e] = i < i1 ? vnext[i] : 0.0;
-      }
+  for (int i = 0; i <= j; ++i) {
+    double nx[5];
+    for (int q = 0; q < 5; ++q) {
+      const int t = lane + 32 * q;
+      nx[q] = (i + 1 <= j && t > i + 1 && t <= j) ? L[(size_t)(i + 1) * (m + 1) + t] : 0.0;
     }
-    const double hq = cluster_sum(s, buf);
-    buf ^= 1;
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) w[e] -= hq * v[e];
-    if (rank == 0 && threadIdx.x == 0) {
-      h[q] = hq;
-      if (Hraw) Hraw[((size_t)b * m + j) * (m + 1) + q] = hq;
+    const int owner = i & 31, qi = i >> 5;
+    double mine = 0.0;
+    for (int q = 0; q < 5; ++q)
+      if (q == qi) mine = at[q];
+    const double hi = __shfl_sync(0xffffffffu, mine, owner);
+    if (lane == 0) {
+      h[i] = hi;
+      if (hr) hr[i] = hi;
     }
-    if (q < j) {
-#pragma unroll
-      for (int e = 0; e < EPT; ++e) v[e] = vn[e];
+    for (int q = 0; q < 5; ++q) {
+      const int t = lane + 32 * q;
+      if (t > i && t <= j) at[q] -= lr[q] * hi;
+      lr[q] = nx[q];
     }
   }
-  s = 0.0;
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) s += w[e] * w[e];
-  const double hn = sqrt(cluster_sum(s, buf));
-  const bool breakdown = !(hn > 1e-14 * w0);
-  if (rank == 0 && threadIdx.x == 0) {
-    h[j + 1] = hn;
-    if (Hraw) Hraw[((size_t)b * m + j) * (m + 1) + j + 1] = hn;
-    brk[b] = breakdown ? 1 : 0;
+}
+
+// Pass 3: w -= sum_k h_k v_k for the chunk, partial ||w||^2 per block.
+__global__ void __launch_bounds__(256) k_cwy_update(double* V, long long ntot, int j, int m, const InstInfo* inst,
+                                                    const int* active, const double* H, int chunk, double* part) {
+  const int b = blockIdx.y;
+  if (!active[b]) return;
+  const InstInfo in = inst[b];
+  const int i0 = blockIdx.x * chunk;
+  if (i0 >= in.ndof) return;
+  __shared__ double hs[130];
+  __shared__ double red[8];
+  const double* h = H + ((size_t)b * m + j) * (m + 1);
+  for (int t = threadIdx.x; t <= j; t += blockDim.x) hs[t] = h[t];
+  __syncthreads();
+  const int i = i0 + threadIdx.x;
+  const bool ok = i < in.ndof && threadIdx.x < chunk;
+  double s = 0.0;
+  if (ok) {
+    double wi = V[(size_t)(j + 1) * ntot + in.off + i];
+    for (int kk = 0; kk <= j; ++kk) wi -= hs[kk] * V[(size_t)kk * ntot + in.off + i];
+    V[(size_t)(j + 1) * ntot + in.off + i] = wi;
+    s = wi * wi;
   }
-  const double inv = breakdown ? 1.0 : 1.0 / hn;
-#pragma unroll
-  for (int e = 0; e < EPT; ++e) {
-    const int i = i0 + threadIdx.x + e * 512;
-    if (i < i1) wg[i] = w[e] * inv;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double acc = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) acc += red[q];
+    part[(size_t)b * gridDim.x + blockIdx.x] = acc;
   }
-  cluster.sync();  // keep this block's shared memory alive until every peer has read it
+}
+
+// Pass 5: v_{j+1} = w / h_{j+1,j} unless the instance broke down.
+__global__ void k_cwy_normalize(double* V, long long ntot, int j, const InstInfo* inst, const int* active0,
+                                const int* brk, const double* hnorm) {
+  const int b = blockIdx.y;
+  if (!active0[b] || brk[b]) return;
+  const InstInfo in = inst[b];
+  const double inv = 1.0 / hnorm[b];
+  double* w = V + (size_t)(j + 1) * ntot + in.off;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) w[i] *= inv;
 }
 
 // Givens update of column j (one block per active instance): the column and the stored rotations are
 // staged in shared memory by all threads, then one thread applies the j previous rotations.
 __global__ void k_givens(double* H, double* cs, double* sn, double* g, int j, int m, int B, int* active,
-                         const int* brk, const double* bnorm, double rtol, int* iters_left, double* est,
-                         int* flag, int* kcols) {
+                         int* brk, const double* bnorm, const double* rtol_p, int* iters_left, double* est,
+                         int* flag, int* kcols, const double* npart, int nchunk, const double* w0, double* hnorm,
+                         double* Hraw, int* active0) {
   const int b = blockIdx.x;
-  if (!active[b]) return;
+  if (!active[b]) {
+    if (threadIdx.x == 0) active0[b] = 0;
+    return;
+  }
   __shared__ double hs[130], css[128], sns[128];
   double* h = H + ((size_t)b * m + j) * (m + 1);
+  if (npart) {
+    // finish the orthogonalisation: h_{j+1,j} = ||w|| (partials summed in chunk order), breakdown test
+    if (threadIdx.x == 0) {
+      double acc = 0.0;
+      for (int c = 0; c < nchunk; ++c) acc += npart[(size_t)b * nchunk + c];
+      const double hn = sqrt(acc);
+      h[j + 1] = hn;
+      if (Hraw) Hraw[((size_t)b * m + j) * (m + 1) + j + 1] = hn;
+      hnorm[b] = hn;
+      brk[b] = (hn > 1e-14 * w0[b]) ? 0 : 1;
+      active0[b] = 1;
+    }
+    __syncthreads();
+  }
   double* c = cs + (size_t)b * m;
   double* s = sn + (size_t)b * m;
   double* gg = g + (size_t)b * (m + 1);
@@ -279,7 +306,7 @@ __global__ void k_givens(double* H, double* cs, double* sn, double* g, int j, in
   kcols[b] = j + 1;
   int f = RUN;
   if (!isfinite(e) || !isfinite(den)) f = STOP_NUMERIC;
-  else if (e <= rtol * bnorm[b]) f = STOP_CONV;
+  else if (e <= rtol_p[0] * bnorm[b]) f = STOP_CONV;
   else if (brk[b]) f = STOP_BREAK;
   else if (j + 1 == m || iters_left[b] <= 1) f = STOP_RESTART;
   flag[b] = f;
@@ -345,77 +372,49 @@ __global__ void k_zero_active(double* x, const InstInfo* inst, const int* active
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) x[in.off + i] = 0.0;
 }
 
-// MGS launcher: a cluster of CS blocks (512 threads, EPT elements per thread) per instance; the
-// cluster size grows with the largest instance and, for few instances, up to 16 to spread one
-// instance's orthogonalisation over many SMs.
-template <int EPT>
-static int launch_mgs_t(rte_problem* p, int CS, double* V, long long ntot, int j, int m, const int* active, double* H,
-                        double* Hraw, int* brk, cudaStream_t st) {
-  auto kern = k_mgs_cluster<EPT>;
-  static bool attr = false;
-  if (!attr) {
-    RTE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    attr = true;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(p->B * CS);
-  cfg.blockDim = dim3(512);
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CS;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  RTE_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, V, ntot, j, m, (const InstInfo*)p->d_inst.p, active, H, Hraw, brk));
-  count_launch();
-  return RTE_OK;
-}
-
-int launch_mgs(rte_problem* p, double* V, long long ntot, int j, int m, const int* active, double* H, double* Hraw,
-               int* brk, cudaStream_t st) {
-  int maxn = 0;
-  for (int b = 0; b < p->B; ++b) maxn = std::max(maxn, (int)(p->off[b + 1] - p->off[b]));
-  // want CS blocks per instance with CS * B near 2 x 152 (at most 16), and 512 * EPT * CS >= maxn
-  int CS = 1;
-  while (CS < 16 && (long long)CS * 2 * p->B <= 2 * 152) CS *= 2;
-  int EPT = 1;
-  while ((long long)512 * EPT * CS < maxn) {
-    if (EPT < 16) EPT *= 2;
-    else if (CS < 16) CS *= 2;
-    else break;
-  }
-  if ((long long)512 * EPT * CS < maxn) {
-    set_error("MGS: instance too large for the cluster kernel (more than 131072 dofs)");
-    return RTE_ERR_UNSUPPORTED;
-  }
-  switch (EPT) {
-    case 1: return launch_mgs_t<1>(p, CS, V, ntot, j, m, active, H, Hraw, brk, st);
-    case 2: return launch_mgs_t<2>(p, CS, V, ntot, j, m, active, H, Hraw, brk, st);
-    case 4: return launch_mgs_t<4>(p, CS, V, ntot, j, m, active, H, Hraw, brk, st);
-    case 8: return launch_mgs_t<8>(p, CS, V, ntot, j, m, active, H, Hraw, brk, st);
-    default: return launch_mgs_t<16>(p, CS, V, ntot, j, m, active, H, Hraw, brk, st);
-  }
-}
-
 // ----------------------------------------------------------------- host driver
 struct Ws {
   int B = 0, m = 0;
   long long ntot = 0;
   bool withZ = false;
   DevBuf<double> V, Z, H, Hraw, cs, sn, g, y, bt, r, d, phi_in;
+  DevBuf<double> Lt, part, npart, w0, hnorm;   // compact-WY MGS
+  DevBuf<int> active0;
+  int nchunk = 0;
+  bool cwy_attr = false;
+  // CUDA graphs of single iterations, keyed by (j, ROM on/off, precision, recording); they capture
+  // device pointers, so they are dropped whenever a buffer they use is reallocated
+  DevBuf<double> d_rtol;
+  DevBuf<int> norom;            // [B] 1 for instances without a ROM
+  double* h_rtol = nullptr;     // pinned
+  cudaStream_t cap = nullptr;   // capture stream
+  struct Graph {
+    cudaGraphExec_t exec;
+    int launches;
+  };
+  std::unordered_map<int, Graph> graphs;
+  std::vector<RomPlan> plans;   // persistent across solves (same ROM groups -> same buffers)
+  std::vector<romsad_t> plan_rom;
+  std::vector<std::vector<int>> plan_ids;
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.exec);
+    graphs.clear();
+  }
   DevBuf<double> bnorm, beta, est, nrm;
   DevBuf<int> active, brk, flag, kcols, iters_left, list;
   DevBuf<double> rom_y, rom_c;
   int* hflag = nullptr;   // pinned host mirrors of flag and kcols
   int* hk = nullptr;
   ~Ws() {
+    drop_graphs();
+    if (cap) cudaStreamDestroy(cap);
     if (hflag) cudaFreeHost(hflag);
     if (hk) cudaFreeHost(hk);
+    if (h_rtol) cudaFreeHost(h_rtol);
   }
   int alloc(rte_problem* p, int m_, bool withZ_) {
     if (B == p->B && m == m_ && ntot == p->ntot && (withZ == withZ_ || !withZ_)) return RTE_OK;
+    drop_graphs();
     B = p->B;
     m = m_;
     ntot = p->ntot;
@@ -424,6 +423,17 @@ struct Ws {
     if (withZ) RTE_TRY(Z.alloc((size_t)m * ntot));
     RTE_TRY(H.alloc((size_t)B * m * (m + 1)));
     RTE_TRY(Hraw.alloc((size_t)B * m * (m + 1)));
+    {
+      int maxn = 0;
+      for (int b = 0; b < p->B; ++b) maxn = std::max(maxn, (int)(p->off[b + 1] - p->off[b]));
+      nchunk = (maxn + 255) / 256;
+    }
+    RTE_TRY(Lt.alloc((size_t)B * (m + 1) * (m + 1)));
+    RTE_TRY(part.alloc((size_t)B * nchunk * (2 * m + 3)));
+    RTE_TRY(npart.alloc((size_t)B * nchunk));
+    RTE_TRY(w0.alloc(B));
+    RTE_TRY(hnorm.alloc(B));
+    RTE_TRY(active0.alloc(B));
     RTE_TRY(cs.alloc((size_t)B * m));
     RTE_TRY(sn.alloc((size_t)B * m));
     RTE_TRY(g.alloc((size_t)B * (m + 1)));
@@ -447,6 +457,10 @@ struct Ws {
     if (hk) cudaFreeHost(hk);
     RTE_CHECK_CUDA(cudaMallocHost(&hflag, B * sizeof(int)));
     RTE_CHECK_CUDA(cudaMallocHost(&hk, B * sizeof(int)));
+    RTE_TRY(d_rtol.alloc(1));
+    RTE_TRY(norom.alloc(B));
+    if (!h_rtol) RTE_CHECK_CUDA(cudaMallocHost(&h_rtol, sizeof(double)));
+    if (!cap) RTE_CHECK_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     return RTE_OK;
   }
 };
@@ -462,10 +476,10 @@ struct SolveCtx {
   std::vector<int> no_rom_mask;       // [B] 1 for instances without a ROM
 };
 
-// dst[b] = dst[b] && m[b]
-__global__ void k_mask_and(int* dst, const int* m, int B) {
+// dst[b] = a[b] && m[b]
+__global__ void k_mask_and2(int* dst, const int* a, const int* m, int B) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < B) dst[b] = dst[b] && m[b];
+  if (b < B) dst[b] = a[b] && m[b];
 }
 
 static dim3 vec_grid(rte_problem* p) {
@@ -561,34 +575,71 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
     // the flags only every kCheck iterations: instances that stopped in between are skipped by
     // every kernel until the host catches up.
     const int kCheck = 8;
+    *W.h_rtol = rtol;
+    RTE_CHECK_CUDA(cudaMemcpyAsync(W.d_rtol.p, W.h_rtol, sizeof(double), cudaMemcpyHostToDevice, st));
     for (int j = 0; j < m; ++j) {
-      // preconditioner
-      double* vj = W.V.p + (size_t)j * ntot;
-      double* zj = Zbase + (size_t)j * ntot;
-      if (W.withZ) {
-        // ROMSAD for instances with a ROM while j is inside the window (or always with POST_ROM);
-        // identity (a copy) otherwise.  Lock-step instances share the global iteration index.
-        const int jg = it_first + j + 1;
-        const bool use_rom = jg <= C.window || C.post == RTE_POST_ROM;
-        if (use_rom) {
-          RTE_CHECK_CUDA(cudaMemcpyAsync(W.brk.p, C.no_rom_mask.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-          k_mask_and<<<(B + 127) / 128, 128, 0, st>>>(W.brk.p, W.active.p, B);
-          count_launch();
-          k_copy_active<<<vg, 256, 0, st>>>(zj, vj, p->d_inst.p, W.brk.p);
-          count_launch();
-          for (auto& pl : *C.plans) RTE_TRY(pl.apply(p, W.active.p, vj, zj, f64, st));
-        } else {
-          k_copy_active<<<vg, 256, 0, st>>>(zj, vj, p->d_inst.p, W.active.p);
-          count_launch();
+      const int jg = it_first + j + 1;   // lock-step instances share the global iteration index
+      const bool use_rom = W.withZ && (jg <= C.window || C.post == RTE_POST_ROM);
+      // One Arnoldi iteration: preconditioner, w = A~ z_j into V[j+1], compact-WY MGS, Givens.
+      auto body = [&](cudaStream_t s) -> int {
+        double* vj = W.V.p + (size_t)j * ntot;
+        double* zj = Zbase + (size_t)j * ntot;
+        if (W.withZ) {
+          if (use_rom) {
+            // copy for instances without a ROM, ROMSAD for the others
+            k_mask_and2<<<(B + 127) / 128, 128, 0, s>>>(W.brk.p, W.norom.p, W.active.p, B);
+            count_launch();
+            k_copy_active<<<vg, 256, 0, s>>>(zj, vj, p->d_inst.p, W.brk.p);
+            count_launch();
+            for (auto& pl : *C.plans) RTE_TRY(pl.apply(p, W.active.p, vj, zj, f64, s));
+          } else {
+            k_copy_active<<<vg, 256, 0, s>>>(zj, vj, p->d_inst.p, W.active.p);
+            count_launch();
+          }
         }
+        RTE_TRY(launch_T(p, MODE_OP, f64, zj, true, nullptr, W.V.p + (size_t)(j + 1) * ntot, true, W.active.p, s));
+        const int chunk = 256;
+        const dim3 gch((unsigned)W.nchunk, B);
+        const size_t smem = (size_t)8 * (2 * m + 3) * sizeof(double);
+        k_cwy_dots<<<gch, 256, smem, s>>>(W.V.p, ntot, j, m, p->d_inst.p, W.active.p, chunk, W.part.p);
+        count_launch();
+        k_cwy_solve<<<B, 256, 0, s>>>(W.part.p, W.nchunk, j, m, W.active.p, W.Lt.p, W.H.p,
+                                      C.rec ? W.Hraw.p : nullptr, W.w0.p);
+        count_launch();
+        k_cwy_update<<<gch, 256, 0, s>>>(W.V.p, ntot, j, m, p->d_inst.p, W.active.p, W.H.p, chunk, W.npart.p);
+        count_launch();
+        k_givens<<<B, 128, 0, s>>>(W.H.p, W.cs.p, W.sn.p, W.g.p, j, m, B, W.active.p, W.brk.p, W.bnorm.p, W.d_rtol.p,
+                                   W.iters_left.p, W.est.p, W.flag.p, W.kcols.p, W.npart.p, W.nchunk, W.w0.p,
+                                   W.hnorm.p, C.rec ? W.Hraw.p : nullptr, W.active0.p);
+        count_launch();
+        k_cwy_normalize<<<vg, 256, 0, s>>>(W.V.p, ntot, j, p->d_inst.p, W.active0.p, W.brk.p, W.hnorm.p);
+        count_launch();
+        RTE_CHECK_CUDA(cudaGetLastError());
+        return RTE_OK;
+      };
+      const int key = j | (use_rom ? 1 << 8 : 0) | (f64 ? 1 << 9 : 0) | (C.rec ? 1 << 10 : 0);
+      auto it = W.graphs.find(key);
+      if (it == W.graphs.end()) {
+        // capture this iteration once; later iterations with the same key replay it
+        const long long n0 = launches_so_far();
+        RTE_CHECK_CUDA(cudaStreamBeginCapture(W.cap, cudaStreamCaptureModeThreadLocal));
+        const int rc = body(W.cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(W.cap, &g);
+        if (rc != RTE_OK) {
+          if (g) cudaGraphDestroy(g);
+          return rc;
+        }
+        RTE_CHECK_CUDA(ec);
+        cudaGraphExec_t ex = nullptr;
+        const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        RTE_CHECK_CUDA(ei);
+        it = W.graphs.emplace(key, Ws::Graph{ex, (int)(launches_so_far() - n0)}).first;
+        add_launches(-(long long)it->second.launches);   // counted when replayed
       }
-      // w = A~ z_j into V[j+1]
-      RTE_TRY(launch_T(p, MODE_OP, f64, zj, true, nullptr, W.V.p + (size_t)(j + 1) * ntot, true, W.active.p, st));
-      RTE_TRY(launch_mgs(p, W.V.p, ntot, j, m, W.active.p, W.H.p, C.rec ? W.Hraw.p : nullptr, W.brk.p, st));
-      k_givens<<<B, 128, 0, st>>>(W.H.p, W.cs.p, W.sn.p, W.g.p, j, m, B, W.active.p, W.brk.p,
-                                  W.bnorm.p, rtol, W.iters_left.p, W.est.p, W.flag.p, W.kcols.p);
-      count_launch();
-      RTE_CHECK_CUDA(cudaGetLastError());
+      RTE_CHECK_CUDA(cudaGraphLaunch(it->second.exec, st));
+      add_launches(it->second.launches);
       if ((j + 1) % kCheck != 0 && j != m - 1) continue;
       RTE_CHECK_CUDA(cudaMemcpyAsync(W.hflag, W.flag.p, B * sizeof(int), cudaMemcpyDeviceToHost, st));
       RTE_CHECK_CUDA(cudaMemcpyAsync(W.hk, W.kcols.p, B * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -692,7 +743,10 @@ int hf_solve(rte_problem* p, double rtol, int restart, int max_iter, double* x, 
              int* status) {
   Ws* ws = get_ws(p);
   RTE_TRY(ws->alloc(p, restart, false));
+  RTE_TRY(prepare_sweeps(p));
   SolveCtx C{p, nullptr, restart, 0, RTE_POST_IDENTITY, 0, ws, rec};
+  std::vector<RomPlan> none;
+  C.plans = &none;
   RTE_TRY(launch_T(p, MODE_RHS, true, nullptr, true, nullptr, ws->bt.p, true, nullptr, 0));
   std::vector<int> all(p->B, 1), zero(p->B, 0);
   RunStats rs;
@@ -740,24 +794,39 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
   const int B = p->B;
   SolveCtx C{p, roms, o->restart, o->window, o->post_mode, st, ws};
   // ROM plans: group instances by ROM handle, assemble and factor U^T A_mu U once per solve
-  std::vector<RomPlan> plans;
+  // ROM plans: group instances by ROM handle and factor U^T A_mu U once per solve.  The plans live in
+  // the workspace so that captured iteration graphs stay valid from one solve to the next.
   C.no_rom_mask.assign(B, 1);
-  if (roms) {
-    std::vector<std::pair<romsad_t, int>> groups;
-    for (int b = 0; b < B; ++b)
-      if (roms[b]) { groups.push_back({roms[b], b}); C.no_rom_mask[b] = 0; }
-    std::sort(groups.begin(), groups.end());
-    size_t g0 = 0;
-    while (g0 < groups.size()) {
-      size_t g1 = g0;
-      std::vector<int> ids;
-      while (g1 < groups.size() && groups[g1].first == groups[g0].first) ids.push_back(groups[g1++].second);
-      plans.emplace_back();
-      RTE_TRY(plans.back().build(groups[g0].first, p, ids, st));
-      g0 = g1;
+  {
+    std::vector<romsad_t> prom;
+    std::vector<std::vector<int>> pids;
+    if (roms) {
+      std::vector<std::pair<romsad_t, int>> groups;
+      for (int b = 0; b < B; ++b)
+        if (roms[b]) { groups.push_back({roms[b], b}); C.no_rom_mask[b] = 0; }
+      std::sort(groups.begin(), groups.end());
+      size_t g0 = 0;
+      while (g0 < groups.size()) {
+        size_t g1 = g0;
+        std::vector<int> ids;
+        while (g1 < groups.size() && groups[g1].first == groups[g0].first) ids.push_back(groups[g1++].second);
+        prom.push_back(groups[g0].first);
+        pids.push_back(ids);
+        g0 = g1;
+      }
     }
+    if (prom != ws->plan_rom || pids != ws->plan_ids) {
+      ws->drop_graphs();
+      ws->plans.clear();
+      ws->plans.resize(prom.size());
+      ws->plan_rom = prom;
+      ws->plan_ids = pids;
+    }
+    for (size_t q = 0; q < prom.size(); ++q) RTE_TRY(ws->plans[q].build(prom[q], p, pids[q], st));
+    RTE_CHECK_CUDA(cudaMemcpyAsync(ws->norom.p, C.no_rom_mask.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
   }
-  C.plans = &plans;
+  RTE_TRY(prepare_sweeps(p));
+  C.plans = &ws->plans;
   std::vector<int> all(B, 1), zero(B, 0);
   // b~ (FP64 sweep, counted)
   RTE_TRY(launch_T(p, MODE_RHS, true, nullptr, true, nullptr, ws->bt.p, true, nullptr, st));

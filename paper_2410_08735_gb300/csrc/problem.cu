@@ -120,6 +120,18 @@ __global__ void k_linv(int B, int nu, int R, int dim, const InstInfo* inst, cons
   }
 }
 
+// sigma_s of the cell of every dof (instance-major scalar-vector layout)
+__global__ void k_sig_dof(const InstInfo* inst, int B, int R, int rx, int ry, int nd, const double* sig_s, double* out) {
+  const int b = blockIdx.y;
+  const InstInfo in = inst[b];
+  const int cx = in.nx / rx, cy = in.ny / ry;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) {
+    const int c = i / nd;
+    const int ix = c % in.nx, iy = c / in.nx;
+    out[in.off + i] = sig_s[(size_t)b * R + (iy / cy) * rx + ix / cx];
+  }
+}
+
 int upload_params(rte_problem* p) {
   std::vector<double> st(p->ss.size());
   std::vector<float> s32(p->ss.size());
@@ -137,6 +149,14 @@ int upload_params(rte_problem* p) {
                                                                   p->d_linv32.p);
   count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
+  {
+    int maxn = 0;
+    for (int b = 0; b < p->B; ++b) maxn = std::max(maxn, (int)(p->off[b + 1] - p->off[b]));
+    dim3 g((maxn + 255) / 256, p->B);
+    k_sig_dof<<<g, 256>>>(p->d_inst.p, p->B, p->R, p->rx, p->ry, p->nd, p->d_sig_s.p, p->d_sig_dof.p);
+    count_launch();
+    RTE_CHECK_CUDA(cudaGetLastError());
+  }
   RTE_CHECK_CUDA(cudaDeviceSynchronize());
   return RTE_OK;
 }
@@ -298,6 +318,7 @@ static int create_impl(const rte_problem_desc* d, rte_problem* p) {
   RTE_TRY(p->d_sig_t.alloc(nR));
   RTE_TRY(p->d_sig_s32.alloc(nR));
   RTE_TRY(p->d_G.alloc(p->ntot));
+  RTE_TRY(p->d_sig_dof.alloc(p->ntot));
   size_t nl = (size_t)p->B * p->nu * p->R * p->nd * p->nd;
   RTE_TRY(p->d_linv64.alloc(nl));
   RTE_TRY(p->d_linv32.alloc(nl));

@@ -311,11 +311,13 @@ __global__ void k_lift(const TP* W, int rmax, int r, const InstInfo* inst, const
 }
 
 // ------------------------------------------------- factor once, apply many times (online path)
-// LU with partial pivoting of U^T A_mu U for every listed instance; one block per instance.
+// Inverse of U^T A_mu U (Gauss-Jordan with partial pivoting, FP64) for every listed instance, one block
+// per instance; formed once per solve so that each ROMSAD apply needs one r x r matrix-vector product.
 __global__ void k_rom_factor(const double* aff, int r, int R, const double* sig_s, const double* sig_t, const int* list,
-                             double* lu, int* piv) {
+                             double* inv, int* piv) {
   extern __shared__ double sm[];
-  double* A = sm;
+  double* A = sm;            // r x r
+  double* X = sm + r * r;    // r x r, becomes the inverse
   __shared__ int piv_s;
   const int b = list[blockIdx.x];
   const size_t rr = (size_t)r * r;
@@ -324,9 +326,9 @@ __global__ void k_rom_factor(const double* aff, int r, int R, const double* sig_
     for (int q = 0; q < R; ++q)
       v += sig_t[(size_t)b * R + q] * aff[(1 + q) * rr + e] - sig_s[(size_t)b * R + q] * aff[(1 + R + q) * rr + e];
     A[e] = v;
+    X[e] = (e / r == e % r) ? 1.0 : 0.0;
   }
   __syncthreads();
-  int* pv = piv + (size_t)blockIdx.x * 64;
   for (int col = 0; col < r; ++col) {
     if (threadIdx.x == 0) {
       int p = col;
@@ -334,45 +336,51 @@ __global__ void k_rom_factor(const double* aff, int r, int R, const double* sig_
       for (int i = col + 1; i < r; ++i)
         if (fabs(A[i * r + col]) > best) { best = fabs(A[i * r + col]); p = i; }
       piv_s = p;
-      pv[col] = p;
+      piv[(size_t)blockIdx.x * 64 + col] = p;
     }
     __syncthreads();
     const int p = piv_s;
     if (p != col)
       for (int j = threadIdx.x; j < r; j += blockDim.x) {
         double t = A[col * r + j]; A[col * r + j] = A[p * r + j]; A[p * r + j] = t;
+        t = X[col * r + j]; X[col * r + j] = X[p * r + j]; X[p * r + j] = t;
       }
     __syncthreads();
-    const double d = A[col * r + col];
-    for (int i = col + 1 + threadIdx.x; i < r; i += blockDim.x) {
-      const double f = A[i * r + col] / d;
-      A[i * r + col] = f;   // L below the diagonal
-      for (int j = col + 1; j < r; ++j) A[i * r + j] -= f * A[col * r + j];
+    const double d = 1.0 / A[col * r + col];
+    __syncthreads();
+    for (int j = threadIdx.x; j < r; j += blockDim.x) { A[col * r + j] *= d; X[col * r + j] *= d; }
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      const int i = e / r, j = e % r;
+      if (i == col) continue;
+      const double f = A[i * r + col];
+      if (j != col) A[i * r + j] -= f * A[col * r + j];
+      X[i * r + j] -= f * X[col * r + j];
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < r; i += blockDim.x)
+      if (i != col) A[i * r + col] = 0.0;
+    __syncthreads();
   }
-  double* out = lu + (size_t)blockIdx.x * 64 * 64;
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) out[e] = A[e];
+  double* out = inv + (size_t)blockIdx.x * 64 * 64;
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) out[e] = X[e];
 }
 
-// Partial projections: part[(inst, chunk)][k] = sum over the chunk's dofs of P[i][k] sigma_s(i) v[i].
-// grid (nchunk, ninst); 8 warps stride over the chunk, lanes over k (two columns per lane).
+// Partial projections: part[(inst, chunk)][k] = sum over the chunk's dofs of P[i][k] sigma_s(i) v[i]
+// (sigma_s per dof precomputed); grid (nchunk, ninst); 8 warps stride over the chunk, lanes over k.
 template <typename TP>
 __global__ void k_project_part(const TP* P, int rmax, int r, const InstInfo* inst, const int* list, const int* active,
-                               const double* sig_s, int R, int rx, int ry, int nd, const double* v, int chunk,
-                               double* part) {
+                               const double* sig_dof, const double* v, int chunk, double* part) {
   const int b = list[blockIdx.y];
   if (active && !active[b]) return;
   const InstInfo in = inst[b];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int cx = in.nx / rx, cy = in.ny / ry;
   const int i0 = blockIdx.x * chunk, i1 = min(in.ndof, i0 + chunk);
   double acc0 = 0.0, acc1 = 0.0;
   const double* vb = v + in.off;
+  const double* sb = sig_dof + in.off;
   for (int i = i0 + warp; i < i1; i += nw) {
-    const int c = i / nd;
-    const int ix = c % in.nx, iy = c / in.nx;
-    const double sv = sig_s[(size_t)b * R + (iy / cy) * rx + ix / cx] * vb[i];
+    const double sv = sb[i] * vb[i];
     if (lane < r) acc0 += (double)P[(size_t)i * rmax + lane] * sv;
     if (lane + 32 < r) acc1 += (double)P[(size_t)i * rmax + lane + 32] * sv;
   }
@@ -387,43 +395,25 @@ __global__ void k_project_part(const TP* P, int rmax, int r, const InstInfo* ins
   }
 }
 
-// c = (LU)^{-1} y with y = sum of the partials (fixed chunk order); one block of 64 threads per instance.
-__global__ void k_rom_lu_solve(const double* part, int nchunk, int r, const double* lu, const int* piv,
-                               const int* list, const int* active, double* c) {
+// c = (U^T A U)^{-1} y with y = sum of the partials (fixed chunk order); one block of 64 threads per instance.
+__global__ void k_rom_inv_apply(const double* part, int nchunk, int r, const double* inv, const int* list,
+                                const int* active, double* c) {
   const int b = list[blockIdx.x];
   if (active && !active[b]) return;
-  __shared__ double x[64];
-  __shared__ double xi;
+  __shared__ double y[64];
   const int t = threadIdx.x;
   if (t < r) {
     double s = 0.0;
     for (int ch = 0; ch < nchunk; ++ch) s += part[((size_t)blockIdx.x * nchunk + ch) * 64 + t];
-    x[t] = s;
+    y[t] = s;
   }
   __syncthreads();
-  const int* pv = piv + (size_t)blockIdx.x * 64;
-  const double* A = lu + (size_t)blockIdx.x * 64 * 64;
-  if (t == 0)
-    for (int k = 0; k < r; ++k) {
-      const int p = pv[k];
-      if (p != k) { double tmp = x[k]; x[k] = x[p]; x[p] = tmp; }
-    }
-  __syncthreads();
-  for (int k = 0; k < r; ++k) {          // forward substitution with unit L
-    const double xk = x[k];
-    __syncthreads();
-    if (t > k && t < r) x[t] -= A[t * r + k] * xk;
-    __syncthreads();
+  if (t < r) {
+    const double* row = inv + (size_t)blockIdx.x * 64 * 64 + (size_t)t * r;
+    double s = 0.0;
+    for (int k = 0; k < r; ++k) s += row[k] * y[k];
+    c[(size_t)blockIdx.x * 64 + t] = s;
   }
-  for (int k = r - 1; k >= 0; --k) {     // back substitution with U
-    if (t == 0) xi = x[k] / A[k * r + k];
-    __syncthreads();
-    const double v = xi;
-    if (t == 0) x[k] = v;
-    if (t < k) x[t] -= A[t * r + k] * v;
-    __syncthreads();
-  }
-  if (t < r) c[(size_t)blockIdx.x * 64 + t] = x[t];
 }
 
 // z_b = v_b + W c_b; grid (chunks, listed instances), skipping inactive instances
@@ -448,16 +438,17 @@ int RomPlan::build(romsad* rom_, rte_problem* p, const std::vector<int>& ids_, c
   rom = rom_;
   ids = ids_;
   const int n = (int)ids.size();
-  RTE_TRY(d_ids.alloc(n));
+  // ensure(): buffers are reused (same device pointers) when the plan is rebuilt for the same groups
+  RTE_TRY(d_ids.ensure(n));
   RTE_CHECK_CUDA(cudaMemcpyAsync(d_ids.p, ids.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
-  RTE_TRY(lu.alloc((size_t)n * 64 * 64));
-  RTE_TRY(piv.alloc((size_t)n * 64));
-  chunk = 1024;
+  RTE_TRY(lu.ensure((size_t)n * 64 * 64));
+  RTE_TRY(piv.ensure((size_t)n * 64));
+  chunk = 256;
   nchunk = (rom->N + chunk - 1) / chunk;
-  RTE_TRY(part.alloc((size_t)n * nchunk * 64));
-  RTE_TRY(c.alloc((size_t)n * 64));
-  size_t smem = (size_t)rom->r * rom->r * 8;
-  k_rom_factor<<<n, 128, smem, st>>>(rom->d_aff.p, rom->r, rom->R, p->d_sig_s.p, p->d_sig_t.p, d_ids.p, lu.p, piv.p);
+  RTE_TRY(part.ensure((size_t)n * nchunk * 64));
+  RTE_TRY(c.ensure((size_t)n * 64));
+  size_t smem = (size_t)2 * rom->r * rom->r * 8;
+  k_rom_factor<<<n, 256, smem, st>>>(rom->d_aff.p, rom->r, rom->R, p->d_sig_s.p, p->d_sig_t.p, d_ids.p, lu.p, piv.p);
   count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   return RTE_OK;
@@ -468,12 +459,12 @@ int RomPlan::apply(rte_problem* p, const int* d_active, const double* v, double*
   dim3 gp(nchunk, n);
   if (f64)
     k_project_part<double><<<gp, 256, 0, st>>>(rom->P.p, rom->rmax, rom->r, p->d_inst.p, d_ids.p, d_active,
-                                               p->d_sig_s.p, p->R, p->rx, p->ry, p->nd, v, chunk, part.p);
+                                               p->d_sig_dof.p, v, chunk, part.p);
   else
     k_project_part<float><<<gp, 256, 0, st>>>(rom->P32.p, rom->rmax, rom->r, p->d_inst.p, d_ids.p, d_active,
-                                              p->d_sig_s.p, p->R, p->rx, p->ry, p->nd, v, chunk, part.p);
+                                              p->d_sig_dof.p, v, chunk, part.p);
   count_launch();
-  k_rom_lu_solve<<<n, 64, 0, st>>>(part.p, nchunk, rom->r, lu.p, piv.p, d_ids.p, d_active, c.p);
+  k_rom_inv_apply<<<n, 64, 0, st>>>(part.p, nchunk, rom->r, lu.p, d_ids.p, d_active, c.p);
   count_launch();
   dim3 gl((rom->N + 255) / 256, n);
   if (f64)

@@ -440,34 +440,39 @@ static int pick_D(const rte_problem* p, bool f64) {
 }
 
 static int ensure_tasks(rte_problem* p, int D) {
-  if (p->tasks_D == D && p->d_tasks.p) return RTE_OK;
-  std::vector<SweepTask> tasks;
-  int per_inst = 0;
-  if (p->dim == 1) {
-    per_inst = p->nu;
-    for (int b = 0; b < p->B; ++b)
-      for (int u = 0; u < p->nu; ++u) tasks.push_back(SweepTask{b, u, u, 0});
-  } else {
-    int nquad = 4;
-    for (int q = 0; q < nquad; ++q) {
-      int nq = p->quad_start[q + 1] - p->quad_start[q];
-      per_inst += nq / D;
-    }
-    for (int b = 0; b < p->B; ++b) {
-      int t = 0;
-      for (int q = 0; q < nquad; ++q)
-        for (int u0 = p->quad_start[q]; u0 < p->quad_start[q + 1]; u0 += D) tasks.push_back(SweepTask{b, u0, t++, 0});
-    }
-    // longest tasks first (instances with the most cells): a static longest-processing-time order
-    std::stable_sort(tasks.begin(), tasks.end(), [&](const SweepTask& x, const SweepTask& y) {
-      return (long long)p->nx[x.b] * p->ny[x.b] > (long long)p->nx[y.b] * p->ny[y.b];
-    });
+  if (D < 1 || D > 16) {
+    set_error("sweep: directions per warp out of range");
+    return RTE_ERR_UNSUPPORTED;
   }
-  RTE_TRY(p->d_tasks.alloc(tasks.size()));
-  RTE_CHECK_CUDA(cudaMemcpy(p->d_tasks.p, tasks.data(), tasks.size() * sizeof(SweepTask), cudaMemcpyHostToDevice));
-  p->ntasks = (int)tasks.size();
-  p->tasks_per_inst = per_inst;
+  if (!p->d_tasks_by_D[D].p) {
+    std::vector<SweepTask> tasks;
+    int per_inst = 0;
+    if (p->dim == 1) {
+      per_inst = p->nu;
+      for (int b = 0; b < p->B; ++b)
+        for (int u = 0; u < p->nu; ++u) tasks.push_back(SweepTask{b, u, u, 0});
+    } else {
+      const int nquad = 4;
+      for (int q = 0; q < nquad; ++q) per_inst += (p->quad_start[q + 1] - p->quad_start[q]) / D;
+      for (int b = 0; b < p->B; ++b) {
+        int t = 0;
+        for (int q = 0; q < nquad; ++q)
+          for (int u0 = p->quad_start[q]; u0 < p->quad_start[q + 1]; u0 += D) tasks.push_back(SweepTask{b, u0, t++, 0});
+      }
+      // longest tasks first (instances with the most cells): a static longest-processing-time order
+      std::stable_sort(tasks.begin(), tasks.end(), [&](const SweepTask& x, const SweepTask& y) {
+        return (long long)p->nx[x.b] * p->ny[x.b] > (long long)p->nx[y.b] * p->ny[y.b];
+      });
+    }
+    RTE_TRY(p->d_tasks_by_D[D].alloc(tasks.size()));
+    RTE_CHECK_CUDA(cudaMemcpy(p->d_tasks_by_D[D].p, tasks.data(), tasks.size() * sizeof(SweepTask),
+                              cudaMemcpyHostToDevice));
+    p->ntasks_by_D[D] = (int)tasks.size();
+    p->per_inst_by_D[D] = per_inst;
+  }
   p->tasks_D = D;
+  p->ntasks = p->ntasks_by_D[D];
+  p->tasks_per_inst = p->per_inst_by_D[D];
   return RTE_OK;
 }
 
@@ -523,7 +528,7 @@ static void fill_args(rte_problem* p, SweepArgs& a, bool f64) {
   std::memset(&a, 0, sizeof(a));
   a.inst = p->d_inst.p;
   a.udir = p->d_udir.p;
-  a.tasks = p->d_tasks.p;
+  a.tasks = p->d_tasks_by_D[p->tasks_D].p;
   a.ntasks = p->ntasks;
   a.linv = f64 ? (const void*)p->d_linv64.p : (const void*)p->d_linv32.p;
   a.g = p->g;
@@ -538,6 +543,17 @@ static void fill_args(rte_problem* p, SweepArgs& a, bool f64) {
 static int ensure_partial(rte_problem* p, bool f64) {
   size_t bytes = (size_t)p->tasks_per_inst * p->ntot * (f64 ? 8 : 4);
   return p->d_partial.ensure(bytes);
+}
+
+// Build the task lists of both precisions and size the partial-sum buffer for the larger one, so
+// that later launches (including captured CUDA graphs) see stable device pointers.
+int prepare_sweeps(rte_problem* p) {
+  const int d64 = pick_D(p, true), d32 = pick_D(p, false);
+  RTE_TRY(ensure_tasks(p, d32));
+  const size_t b32 = (size_t)p->tasks_per_inst * p->ntot * 4;
+  RTE_TRY(ensure_tasks(p, d64));
+  const size_t b64 = (size_t)p->tasks_per_inst * p->ntot * 8;
+  return p->d_partial.ensure(std::max(b32, b64));
 }
 
 int launch_T(rte_problem* p, int mode, bool f64, const void* src, bool in_f64, const void* bvec, void* out,
