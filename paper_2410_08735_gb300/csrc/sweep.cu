@@ -276,6 +276,167 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
   }
 }
 
+// Band-parallel variant for meshes with ny <= 32 * 8: one CTA per task, warp w owns the 32-row band w
+// (lane l owns row 32w + l).  All bands advance in lock step, one CTA barrier per step: lane l of
+// band w handles column col = s - 32w - l at step s, so the y-inflow of a cell is the y-outflow of
+// the lane below one step earlier (warp shuffle; for lane 0 the last lane of the band below, through
+// shared memory).  The critical path is the nx + ny - 1 diagonals, and a lane's cell index moves by one
+// per step, so the step loop has no division and the source prefetch is a plain +-PF offset.
+template <typename T, typename TI, int D, bool ANG>
+__global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int tid = blockIdx.x;
+  if (tid >= a.ntasks) return;
+  const SweepTask tk = a.tasks[tid];
+  if (a.active && !a.active[tk.b]) return;   // uniform for the CTA
+  const InstInfo in = a.inst[tk.b];
+  const int nx = in.nx, ny = in.ny, R = a.R;
+  const int nb = (ny + 31) >> 5;             // bands of this instance (<= nwarps)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tab = reinterpret_cast<T*>(smem_raw);                 // [D][R][16]
+  T* sgs = tab + D * R * 16;                                // [R] (4-aligned)
+  T* ybuf = sgs + ((R + 3) & ~3);                           // [nwarps-1][D][nx][2]
+  int* xreg = reinterpret_cast<int*>(ybuf + (size_t)(nwarps > 1 ? nwarps - 1 : 1) * D * nx * 2);   // [nx]
+  const T* linv = reinterpret_cast<const T*>(a.linv) + ((size_t)tk.b * a.nu + tk.u0) * R * 16;
+  for (int e = threadIdx.x; e < D * R * 16; e += blockDim.x) tab[e] = linv[e];
+  if (a.sig_s)
+    for (int e = threadIdx.x; e < R; e += blockDim.x) sgs[e] = reinterpret_cast<const T*>(a.sig_s)[(size_t)tk.b * R + e];
+  const int cx = nx / a.rx, cy = ny / a.ry;
+  for (int e = threadIdx.x; e < nx; e += blockDim.x) xreg[e] = e / cx;
+  T al[D], be[D], wg[D];
+  const int sx = a.udir[tk.u0].sx, sy = a.udir[tk.u0].sy;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const UDir u = a.udir[tk.u0 + d];
+    al[d] = (T)(u.ax / in.hx);
+    be[d] = (T)(u.ay / in.hy);
+    wg[d] = (T)u.w;
+  }
+  const T bnd = a.with_bc ? (T)(a.g * sqrt(in.hx * in.hy)) : (T)0;
+  const bool sig_s = a.sig_s != nullptr;
+  const TI* src = reinterpret_cast<const TI*>(a.src) + in.off;
+  T* part = reinterpret_cast<T*>(a.partial) + (size_t)a.tasks_per_inst * in.off + (size_t)tk.t * in.ndof;
+  T* psi = ANG ? reinterpret_cast<T*>(a.psi) + (size_t)(a.psi_unique ? a.nu : a.ndir) * in.off : nullptr;
+  const T S3 = (T)1.7320508075688772;
+  const int band = warp;
+  const int row = band * 32 + lane;
+  const bool rowok = band < nb && row < ny;
+  const int iy = sy > 0 ? row : ny - 1 - row;
+  const long long rowbase = (long long)(rowok ? iy : 0) * nx;
+  const int rowreg = rowok ? (iy / cy) * a.rx : 0;
+  const int nsteps = 32 * (nb - 1) + 31 + nx;
+  const int col0 = -(32 * band + lane);      // column at step 0
+  auto cell_of = [&](int col) -> long long { return rowbase + (sx > 0 ? col : nx - 1 - col); };
+  T tx0[D], tx1[D], ty0[D], ty1[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) { tx0[d] = tx1[d] = ty0[d] = ty1[d] = (T)0; }
+  constexpr int PF = 4;
+  TI q0[PF], q1[PF], q2[PF], q3[PF];
+#pragma unroll
+  for (int k = 0; k < PF; ++k) {
+    const int c = col0 + k;
+    if (rowok && c >= 0 && c < nx) Vec4<TI>::load(src + 4 * cell_of(c), q0[k], q1[k], q2[k], q3[k]);
+  }
+  __syncthreads();
+  for (int s0 = 0; s0 < nsteps; s0 += PF) {
+#pragma unroll
+    for (int kk = 0; kk < PF; ++kk) {
+      const int s = s0 + kk;
+      const int col = col0 + s;
+      const bool act = rowok && s < nsteps && col >= 0 && col < nx;
+      T s0v = (T)q0[kk], s1 = (T)q1[kk], s2 = (T)q2[kk], s3 = (T)q3[kk];
+      {
+        const int cn = col + PF;
+        if (rowok && cn >= 0 && cn < nx) Vec4<TI>::load(src + 4 * cell_of(cn), q0[kk], q1[kk], q2[kk], q3[kk]);
+      }
+      T yi0[D], yi1[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        yi0[d] = __shfl_up_sync(0xffffffffu, ty0[d], 1);
+        yi1[d] = __shfl_up_sync(0xffffffffu, ty1[d], 1);
+      }
+      if (act) {
+        if (lane == 0) {
+          if (band == 0) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) { yi0[d] = bnd; yi1[d] = (T)0; }
+          } else {
+            const T* yb = ybuf + (size_t)(band - 1) * D * nx * 2;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              yi0[d] = yb[(d * nx + col) * 2];
+              yi1[d] = yb[(d * nx + col) * 2 + 1];
+            }
+          }
+        }
+        if (col == 0) {
+#pragma unroll
+          for (int d = 0; d < D; ++d) { tx0[d] = bnd; tx1[d] = (T)0; }
+        }
+        const int ix = sx > 0 ? col : nx - 1 - col;
+        const long long c = rowbase + ix;
+        const int reg = rowreg + xreg[ix];
+        if (sig_s) {
+          const T sg = sgs[reg];
+          s0v *= sg; s1 *= sg; s2 *= sg; s3 *= sg;
+        }
+        s1 = sx > 0 ? s1 : -s1;
+        s2 = sy > 0 ? s2 : -s2;
+        s3 = (sx * sy) > 0 ? s3 : -s3;
+        T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const T ax = al[d], by = be[d];
+          const T r0 = s0v + ax * tx0[d] + by * yi0[d];
+          const T r1 = s1 - S3 * ax * tx0[d] + by * yi1[d];
+          const T r2 = s2 + ax * tx1[d] - S3 * by * yi0[d];
+          const T r3 = s3 - S3 * (ax * tx1[d] + by * yi1[d]);
+          const T* L = tab + (d * R + reg) * 16;
+          T l[16];
+          Vec4<T>::load(L, l[0], l[1], l[2], l[3]);
+          Vec4<T>::load(L + 4, l[4], l[5], l[6], l[7]);
+          Vec4<T>::load(L + 8, l[8], l[9], l[10], l[11]);
+          Vec4<T>::load(L + 12, l[12], l[13], l[14], l[15]);
+          const T p0 = l[0] * r0 + l[1] * r1 + l[2] * r2 + l[3] * r3;
+          const T p1 = l[4] * r0 + l[5] * r1 + l[6] * r2 + l[7] * r3;
+          const T p2 = l[8] * r0 + l[9] * r1 + l[10] * r2 + l[11] * r3;
+          const T p3 = l[12] * r0 + l[13] * r1 + l[14] * r2 + l[15] * r3;
+          tx0[d] = p0 + S3 * p1;
+          tx1[d] = p2 + S3 * p3;
+          ty0[d] = p0 + S3 * p2;
+          ty1[d] = p1 + S3 * p3;
+          acc0 += wg[d] * p0;
+          acc1 += wg[d] * p1;
+          acc2 += wg[d] * p2;
+          acc3 += wg[d] * p3;
+          if (lane == 31 && band + 1 < nb) {
+            T* yb = ybuf + (size_t)band * D * nx * 2;
+            yb[(d * nx + col) * 2] = ty0[d];
+            yb[(d * nx + col) * 2 + 1] = ty1[d];
+          }
+          if (ANG) {
+            const T q1 = sx > 0 ? p1 : -p1, q2 = sy > 0 ? p2 : -p2, q3 = (sx * sy) > 0 ? p3 : -p3;
+            if (a.psi_unique) {
+              Vec4<T>::store(psi + (size_t)(tk.u0 + d) * in.ndof + 4 * c, p0, q1, q2, q3);
+            } else {
+              const UDir u = a.udir[tk.u0 + d];
+              for (int k = 0; k < u.ndup; ++k)
+                Vec4<T>::store(psi + (size_t)u.dup[k] * in.ndof + 4 * c, p0, q1, q2, q3);
+            }
+          }
+        }
+        acc1 = sx > 0 ? acc1 : -acc1;
+        acc2 = sy > 0 ? acc2 : -acc2;
+        acc3 = (sx * sy) > 0 ? acc3 : -acc3;
+        Vec4<T>::store(part + 4 * c, acc0, acc1, acc2, acc3);
+      }
+      if (nwarps > 1) __syncthreads();
+      else __syncwarp();
+    }
+  }
+}
+
 // 1D slab (P1, 2 dofs per cell): one thread per (instance, direction) marches its chain.
 template <typename T, typename TI, bool ANG>
 __global__ void k_sweep1d(SweepArgs a) {
@@ -485,8 +646,50 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
     RTE_CHECK_CUDA(cudaGetLastError());
     return RTE_OK;
   }
-  int maxnx = 0;
-  for (int b = 0; b < p->B; ++b) maxnx = std::max(maxnx, p->nx[b]);
+  int maxnx = 0, maxny = 0;
+  for (int b = 0; b < p->B; ++b) {
+    maxnx = std::max(maxnx, p->nx[b]);
+    maxny = std::max(maxny, p->ny[b]);
+  }
+  const int nbands = (maxny + 31) / 32;
+  // The band kernel shortens the critical path (latency-bound launches, FP32); for FP64 launches with
+  // enough tasks to fill the GPU the FP64 pipe is the limit and the warp-per-task kernel keeps more
+  // warps per SM (no idle band warps on smaller meshes of a mixed batch).
+  const bool fp64_throughput = sizeof(T) == 8 && a.ntasks >= 152 * 8;
+  if (nbands <= 8 && !fp64_throughput) {
+    // band-parallel kernel: one CTA per task, one warp per 32-row band
+    const int W = nbands;
+    size_t elems = (size_t)D * p->R * 16 + ((p->R + 3) & ~3) + (size_t)(W > 1 ? W - 1 : 1) * D * maxnx * 2;
+    size_t smem = elems * sizeof(T) + (size_t)maxnx * sizeof(int) + 16;
+    if (smem > 227 * 1024) {
+      set_error("sweep: shared-memory table too large for this mesh/region count");
+      return RTE_ERR_UNSUPPORTED;
+    }
+#define RTE_BAND_CASE(DD)                                                                                   \
+  case DD: {                                                                                                \
+    auto kern = k_sweep2d_bands<T, TI, DD, ANG>;                                                            \
+    static size_t smem_set = 48 * 1024;                                                                     \
+    if (smem > smem_set) {                                                                                  \
+      RTE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));   \
+      smem_set = smem;                                                                                      \
+    }                                                                                                       \
+    kern<<<a.ntasks, W * 32, smem, st>>>(a);                                                                \
+    count_launch();                                                                                         \
+    break;                                                                                                  \
+  }
+    switch (D) {
+      RTE_BAND_CASE(1)
+      RTE_BAND_CASE(2)
+      RTE_BAND_CASE(4)
+      RTE_BAND_CASE(8)
+      default:
+        set_error("sweep: unsupported directions-per-warp");
+        return RTE_ERR_UNSUPPORTED;
+    }
+#undef RTE_BAND_CASE
+    RTE_CHECK_CUDA(cudaGetLastError());
+    return RTE_OK;
+  }
   a.smem_per_warp = D * p->R * 16 + D * maxnx * 2 + p->R;
   a.smem_per_warp = (a.smem_per_warp + 3) & ~3;
   size_t per_warp = (size_t)a.smem_per_warp * sizeof(T);
