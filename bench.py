@@ -172,6 +172,44 @@ def run_reference(args, spec, B, world, rank):
 
 
 # ------------------------------------------------------------------ GPU legs
+def measure_sweep_hbm(RB, torch, dev, stream, flush, reps=5):
+    spec3 = wl.config(3)
+    ss, sa = wl.draw_params(spec3, spec3.n_instances, wl.seed_for(3, 1))
+    prob = RB.Problem(spec3, ss, sa)
+    n = prob.n_dof
+    src = torch.randn(n, dtype=torch.float32, device=dev)
+    psi = torch.empty(prob.n_directions * n, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        prob.sweep(src, psi, with_bc=True, stream=stream)
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        prob.sweep(src, psi, with_bc=True, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = statistics.median(times)
+    nbytes = prob.n_directions * n * 4 + n * 4
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    cells = sum(nx * ny for nx, ny in zip(spec3.nx, spec3.ny))
+    return {"workload": "batch256_uneven (96x32^2, 96x64^2, 64x128^2; 128 directions)", "kernel": "k_sweep2d (angular output, FP32)",
+            "bytes": nbytes, "ms": ms, "achieved_gbs": nbytes / (ms * 1e-3) / 1e9, "peak_gbs": peak,
+            "frac": nbytes / (ms * 1e-3) / 1e9 / peak,
+            "alu_tflops": SWEEP_FLOPS_PER_CELL_DIR * cells * prob.info.n_unique_directions / (ms * 1e-3) / 1e12}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,6 +222,7 @@ def main():
     ap.add_argument("--inner-rtol", type=float, default=1e-2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mlp-epochs", type=int, default=300)
+    ap.add_argument("--no-sweep-hbm", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=40, help="oracle FGMRES iterations per reference step")
     ap.add_argument("--ref-iters", type=int, default=500, help="iterations of a full solve for extrapolation")
     args = ap.parse_args()
@@ -319,6 +358,9 @@ def main():
                 "achieved": flops / (ms64 * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = None
+    # angular-output sweep (rte_sweep, FP32) on the batched 256-instance problem: HBM-bound write of
+    # N_Omega * N_dof * 4 bytes; this is the sweep GB/s of the metric
+    sweep_hbm = measure_sweep_hbm(RB, torch, dev, stream, flush) if not args.no_sweep_hbm else None
     roof["ms_per_launch_fp32"] = ms32
     roof["ms_per_launch_fp64"] = ms64
     roof["peak_source"] = "unit counts x max SM clock (FP32); GB300 nominal (FP64)"
@@ -349,6 +391,7 @@ def main():
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(launches_mixed * args.steps / n_sets),
         "roofline": roof,
+        "sweep_hbm": sweep_hbm,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

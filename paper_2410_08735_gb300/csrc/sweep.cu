@@ -297,7 +297,10 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
   T* tab = reinterpret_cast<T*>(smem_raw);                 // [D][R][16]
   T* sgs = tab + D * R * 16;                                // [R] (4-aligned)
   T* ybuf = sgs + ((R + 3) & ~3);                           // [nwarps-1][D][nx][2]
-  int* xreg = reinterpret_cast<int*>(ybuf + (size_t)(nwarps > 1 ? nwarps - 1 : 1) * D * nx * 2);   // [nx]
+  int* xreg = reinterpret_cast<int*>(ybuf + (((size_t)(nwarps > 1 ? nwarps - 1 : 1) * D * nx * 2 + 3) & ~(size_t)3));
+  // angular output staging: per lane and direction the last 8 cells of its row (a ring), written out
+  // as aligned 8-cell (128 B in FP32) row segments by the whole warp
+  T* ring = reinterpret_cast<T*>(xreg + ((nx + 3) & ~3)) + ((size_t)warp * 32 + lane) * D * 32;
   const T* linv = reinterpret_cast<const T*>(a.linv) + ((size_t)tk.b * a.nu + tk.u0) * R * 16;
   for (int e = threadIdx.x; e < D * R * 16; e += blockDim.x) tab[e] = linv[e];
   if (a.sig_s)
@@ -417,19 +420,54 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
           }
           if (ANG) {
             const T q1 = sx > 0 ? p1 : -p1, q2 = sy > 0 ? p2 : -p2, q3 = (sx * sy) > 0 ? p3 : -p3;
-            if (a.psi_unique) {
-              Vec4<T>::store(psi + (size_t)(tk.u0 + d) * in.ndof + 4 * c, p0, q1, q2, q3);
-            } else {
-              const UDir u = a.udir[tk.u0 + d];
-              for (int k = 0; k < u.ndup; ++k)
-                Vec4<T>::store(psi + (size_t)u.dup[k] * in.ndof + 4 * c, p0, q1, q2, q3);
-            }
+            Vec4<T>::store(ring + d * 32 + (col & 7) * 4, p0, q1, q2, q3);
           }
         }
         acc1 = sx > 0 ? acc1 : -acc1;
         acc2 = sy > 0 ? acc2 : -acc2;
         acc3 = (sx * sy) > 0 ? acc3 : -acc3;
         Vec4<T>::store(part + 4 * c, acc0, acc1, acc2, acc3);
+      }
+      if (ANG) {
+        // lanes that completed an aligned 8-cell segment (or their row) hand it to the warp: lanes
+        // 8k..8k+7 store the k-th completed segment, one cell each, so every store instruction writes
+        // whole 128-byte lines
+        const bool flush = act && ((col & 7) == 7 || col == nx - 1);
+        __syncwarp();
+        unsigned fm = __ballot_sync(0xffffffffu, flush);
+        while (fm) {
+          int fl[4], n = 0;
+          while (fm && n < 4) {
+            fl[n++] = __ffs(fm) - 1;
+            fm &= fm - 1;
+          }
+          const int k = lane >> 3, e = lane & 7;
+          if (k < n) {
+            const int f = fl[k];
+            const int colf = s - 32 * band - f;
+            const int cs = colf & ~7;
+            if (e <= colf - cs) {
+              const int cl = cs + e;
+              const int rowf = band * 32 + f;
+              const int iyf = sy > 0 ? rowf : ny - 1 - rowf;
+              const long long cellf = (long long)iyf * nx + (sx > 0 ? cl : nx - 1 - cl);
+              const T* src_ring = ring - (size_t)(lane - f) * D * 32;
+#pragma unroll
+              for (int d = 0; d < D; ++d) {
+                T v0, v1, v2, v3;
+                Vec4<T>::load(src_ring + d * 32 + e * 4, v0, v1, v2, v3);
+                if (a.psi_unique) {
+                  Vec4<T>::store(psi + (size_t)(tk.u0 + d) * in.ndof + 4 * cellf, v0, v1, v2, v3);
+                } else {
+                  const UDir u = a.udir[tk.u0 + d];
+                  for (int q = 0; q < u.ndup; ++q)
+                    Vec4<T>::store(psi + (size_t)u.dup[q] * in.ndof + 4 * cellf, v0, v1, v2, v3);
+                }
+              }
+            }
+          }
+        }
+        __syncwarp();
       }
       if (nwarps > 1) __syncthreads();
       else __syncwarp();
@@ -659,8 +697,9 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
   if (nbands <= 8 && !fp64_throughput) {
     // band-parallel kernel: one CTA per task, one warp per 32-row band
     const int W = nbands;
-    size_t elems = (size_t)D * p->R * 16 + ((p->R + 3) & ~3) + (size_t)(W > 1 ? W - 1 : 1) * D * maxnx * 2;
-    size_t smem = elems * sizeof(T) + (size_t)maxnx * sizeof(int) + 16;
+    size_t elems = (size_t)D * p->R * 16 + ((p->R + 3) & ~3) + (((size_t)(W > 1 ? W - 1 : 1) * D * maxnx * 2 + 3) & ~(size_t)3);
+    size_t smem = elems * sizeof(T) + (size_t)((maxnx + 3) & ~3) * sizeof(int) + 16;
+    if (ANG) smem += (size_t)W * 32 * D * 32 * sizeof(T);   // output staging rings
     if (smem > 227 * 1024) {
       set_error("sweep: shared-memory table too large for this mesh/region count");
       return RTE_ERR_UNSUPPORTED;
@@ -807,7 +846,7 @@ int launch_T(rte_problem* p, int mode, bool f64, const void* src, bool in_f64, c
 
 int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st,
                    bool scale_sigma_s, bool unique_layout) {
-  int D = pick_D(p, f64);
+  int D = std::min(2, pick_D(p, f64));   // the output staging rings grow with D
   RTE_TRY(ensure_tasks(p, D));
   RTE_TRY(ensure_partial(p, f64));
   SweepArgs a;
