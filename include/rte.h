@@ -117,6 +117,20 @@ int rte_apply_T(rte_problem_t p, int dtype, const void* s, void* phi, void* stre
 int rte_apply_op(rte_problem_t p, int dtype, const void* z, void* w, void* stream);
 /* btilde = sum_j omega_j (D_j + Sigma_t)^{-1} (G + g_j^bc) (eq. memory-efficient-SI). */
 int rte_rhs(rte_problem_t p, int dtype, void* btilde, void* stream);
+/* Allocation-free form of rte_apply_op (the paper has no counterpart; this is a deployment aid).
+ * Computes the same w = z - T (Sigma_s z), but allocates no device memory: no cudaMalloc, cudaFree or
+ * allocating library routine is called.  It is meant for callers that cannot allocate, for example a
+ * host code whose own pool allocator owns all device memory, or a solver step issued where an implicit
+ * device synchronisation of cudaMalloc is not acceptable.  Its scratch (sweep task list and per-task
+ * partial scalar fluxes) lives in one fixed 16 MiB __device__ array that every GPU which loads the
+ * library holds until the process exits; a problem needing more returns RTE_ERR_INVALID_ARG (use
+ * rte_apply_op).  All calls share that array, so calls that overlap on the GPU (different streams,
+ * threads or processes sharing the context) race: serialise them.  Nothing in the array needs to start
+ * at zero: every call rewrites the parts it reads.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  The problem handle itself must have been created beforehand (rte_problem_create
+ * allocates).  Results agree with rte_apply_op up to the order of the partial sums. */
+int rte_apply_op_noalloc(rte_problem_t p, int dtype, const void* z, void* w, void* stream);
 
 /* ----------------------------------------------------------- ROMSAD (Sec. 4) */
 typedef struct romsad* romsad_t;

@@ -102,6 +102,8 @@ _SIGS = {
     "rte_apply_op": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p]),
     "rte_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
+    "rte_apply_op_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p]),
     "romsad_create_from_basis": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p)]),
     "romsad_build_greedy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -274,6 +276,11 @@ class Problem:
 
     def apply_op(self, z, w, stream=None):
         _check(load().rte_apply_op(self.h, _dtype_code(z), _ptr(z), _ptr(w), _stream(stream)), "rte_apply_op")
+
+    def apply_op_noalloc(self, z, w, stream=None):
+        """rte_apply_op without device allocation (fixed 16 MiB scratch shared by all calls)."""
+        _check(load().rte_apply_op_noalloc(self.h, _dtype_code(z), _ptr(z), _ptr(w), _stream(stream)),
+               "rte_apply_op_noalloc")
 
     def rhs(self, out, stream=None):
         _check(load().rte_rhs(self.h, _dtype_code(out), _ptr(out), _stream(stream)), "rte_rhs")

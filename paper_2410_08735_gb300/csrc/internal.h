@@ -165,6 +165,9 @@ int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void*
                    bool scale_sigma_s = false, bool unique_layout = false);
 // task lists and partial buffer for both precisions (stable pointers for graph capture)
 int prepare_sweeps(rte_problem* p);
+// A~ z with caller-provided task list and partial storage (no allocation)
+int launch_op_external(rte_problem* p, bool f64, const void* z, void* w, const SweepTask* tasks, int ntasks,
+                       int tasks_per_inst, int D, void* partial, cudaStream_t st);
 int launch_scalar_flux(rte_problem* p, bool f64, const void* psi, void* phi, cudaStream_t st);
 // forward operator y = (D_u + sigma_t) x (FP64) for ncol columns on one mesh; used offline
 int launch_forward_cols(int dim, int nx, int ny, double hx, double hy, const UDir& u, int rx, int ry,

@@ -844,6 +844,45 @@ int launch_T(rte_problem* p, int mode, bool f64, const void* src, bool in_f64, c
   return RTE_OK;
 }
 
+// A~ z (mode OP) with caller-provided task list and partial-sum storage: allocates nothing.  D must be
+// a valid directions-per-warp value; tasks holds ntasks entries in the layout of ensure_tasks.
+int launch_op_external(rte_problem* p, bool f64, const void* z, void* w, const SweepTask* tasks, int ntasks,
+                       int tasks_per_inst, int D, void* partial, cudaStream_t st) {
+  SweepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.inst = p->d_inst.p;
+  a.udir = p->d_udir.p;
+  a.tasks = tasks;
+  a.ntasks = ntasks;
+  a.linv = f64 ? (const void*)p->d_linv64.p : (const void*)p->d_linv32.p;
+  a.g = p->g;
+  a.tasks_per_inst = tasks_per_inst;
+  a.ndir = p->ndir;
+  a.nu = p->nu;
+  a.R = p->R;
+  a.rx = p->rx;
+  a.ry = p->ry;
+  a.src = z;
+  a.sig_s = f64 ? (const void*)p->d_sig_s.p : (const void*)p->d_sig_s32.p;
+  a.partial = partial;
+  if (f64) RTE_TRY((launch_sweep_t<double, double, false>(p, D, a, st)));
+  else RTE_TRY((launch_sweep_t<float, float, false>(p, D, a, st)));
+  int maxn = 0;
+  for (int b = 0; b < p->B; ++b) maxn = std::max(maxn, (int)(p->off[b + 1] - p->off[b]));
+  dim3 grid((maxn + 255) / 256, p->B);
+  if (f64)
+    k_reduce<double, double, double><<<grid, 256, 0, st>>>(reinterpret_cast<const double*>(partial), tasks_per_inst,
+                                                          p->d_inst.p, MODE_OP, reinterpret_cast<const double*>(z),
+                                                          nullptr, reinterpret_cast<double*>(w), nullptr);
+  else
+    k_reduce<float, float, float><<<grid, 256, 0, st>>>(reinterpret_cast<const float*>(partial), tasks_per_inst,
+                                                       p->d_inst.p, MODE_OP, reinterpret_cast<const float*>(z),
+                                                       nullptr, reinterpret_cast<float*>(w), nullptr);
+  count_launch();
+  RTE_CHECK_CUDA(cudaGetLastError());
+  return RTE_OK;
+}
+
 int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st,
                    bool scale_sigma_s, bool unique_layout) {
   int D = std::min(2, pick_D(p, f64));   // the output staging rings grow with D
