@@ -297,9 +297,13 @@ def main():
     clk = ClockSampler(local)
     clk.start()
     launches0 = RB.kernel_launches()
+    torch.cuda.nvtx.range_push("timed_mixed")      # ncu --nvtx-include timed_mixed/ selects this region
     t_mixed, st_mixed = timed_loop(RB.RTE_MODE_MIXED)
+    torch.cuda.nvtx.range_pop()
     launches_mixed = RB.kernel_launches() - launches0
+    torch.cuda.nvtx.range_push("timed_fp64")
     t_fp64, st_fp64 = timed_loop(RB.RTE_MODE_FP64)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop()

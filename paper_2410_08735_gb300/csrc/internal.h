@@ -165,6 +165,8 @@ int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void*
                    bool scale_sigma_s = false, bool unique_layout = false);
 // task lists and partial buffer for both precisions (stable pointers for graph capture)
 int prepare_sweeps(rte_problem* p);
+// sweep part of A~ z (per-task partial fluxes in p->d_partial; FP64 input z)
+int launch_op_partials(rte_problem* p, bool f64, const void* z, const int* d_active, cudaStream_t st);
 // A~ z with caller-provided task list and partial storage (no allocation)
 int launch_op_external(rte_problem* p, bool f64, const void* z, void* w, const SweepTask* tasks, int ntasks,
                        int tasks_per_inst, int D, void* partial, cudaStream_t st);

@@ -20,6 +20,8 @@
 #include <cstring>
 #include <unordered_map>
 
+#include <cooperative_groups.h>
+
 #include "romsad.h"
 
 namespace rte {
@@ -97,6 +99,7 @@ __global__ void k_copy_active(double* dst, const double* src, const InstInfo* in
     dst[in.off + i] = src[in.off + i];
 }
 
+// ------------------------------------------------------------------------------------------------
 // Modified Gram-Schmidt in compact-WY form.  The MGS recurrence h_i = v_i.w^(i-1),
 // w^(i) = w^(i-1) - h_i v_i gives h_i = v_i.w - sum_{k<i} (v_i.v_k) h_k, i.e. (I + L) h = V^T w with L
 // the strictly lower part of the Gram matrix V^T V, and w^(j) = w - V h.  The same coefficients are
@@ -105,213 +108,324 @@ __global__ void k_copy_active(double* dst, const double* src, const InstInfo* in
 // Ananthan, Yang, Thomas, Numer. Linear Algebra Appl. 2020).  Rounding differs from the sequential
 // loop; the projector is the MGS projector.
 //
-// Pass 1: per (instance, chunk of dofs) partials of a_k = v_k . w (k <= j), g_k = v_k . v_j (k < j)
-// and w . w.  part layout [b][chunk][slot], slots: a (0..j), g (m+1 .. m+j), ww (2m+2).
-__global__ void __launch_bounds__(256) k_cwy_dots(const double* V, long long ntot, int j, int m, const InstInfo* inst,
-                                                  const int* active, int chunk, double* part) {
-  const int b = blockIdx.y;
-  if (!active[b]) return;
-  const InstInfo in = inst[b];
-  const int i0 = blockIdx.x * chunk;
-  if (i0 >= in.ndof) return;
+// Fused iteration kernels.  One Arnoldi iteration of one or many instances is three launches: the
+// ROMSAD preconditioner (k_precond_coop), the sweep (sweep.cu, per-task partial fluxes), and the
+// Arnoldi step (k_arnoldi_coop: reduction of the partials into w = A~ z, compact-WY MGS, Givens,
+// normalisation).  The two fused kernels are cooperative launches: phases over vector chunks ("items",
+// 256 dofs of one instance) and phases over instances are separated by grid-wide barriers, so the
+// per-instance reductions need no extra launches.  Partial sums are always combined in chunk order.
+struct RomInstDev {
+  const double* P;
+  const double* W;
+  const float* P32;
+  const float* W32;
+  const double* inv;   // (U^T A_mu U)^{-1}, r x r row-major
+  int r, rmax, has;
+};
+
+__device__ __forceinline__ double block_sum256(double v, double* sh) {
+  // 256 threads; result valid in thread 0
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nslot = 2 * m + 3;
-  extern __shared__ double red[];   // [8][nslot]
-  const double* w = V + (size_t)(j + 1) * ntot + in.off;
-  const double* vj = V + (size_t)j * ntot + in.off;
-  const int i = i0 + threadIdx.x;
-  const bool ok = i < in.ndof && threadIdx.x < chunk;
-  const double wi = ok ? w[i] : 0.0;
-  const double vji = ok ? vj[i] : 0.0;
-  double vk = ok ? V[in.off + i] : 0.0;
-  for (int kk = 0; kk <= j; ++kk) {
-    const double vnext = (kk < j && ok) ? V[(size_t)(kk + 1) * ntot + in.off + i] : 0.0;
-    double a = vk * wi;
-    double g = vk * vji;
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      g += __shfl_xor_sync(0xffffffffu, g, o);
-    }
-    if (lane == 0) {
-      red[warp * nslot + kk] = a;
-      if (kk < j) red[warp * nslot + m + 1 + kk] = g;
-    }
-    vk = vnext;
-  }
-  double s = wi * wi;
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) red[warp * nslot + 2 * m + 2] = s;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   __syncthreads();
-  double* out = part + ((size_t)b * gridDim.x + blockIdx.x) * nslot;
-  const int nw = blockDim.x >> 5;
-  for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
-    const bool used = t <= j || (t >= m + 1 && t < m + 1 + j) || t == 2 * m + 2;
-    if (!used) continue;
-    double acc = 0.0;
-    for (int q = 0; q < nw; ++q) acc += red[q * nslot + t];
-    out[t] = acc;
-  }
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < 8; ++w) t += sh[w];
+  return t;
 }
 
-// Pass 2 (one block per instance): sum the partials in chunk order, store the Gram row (transposed:
-// Lt[k][j] = v_k . v_j), solve (I + L) h = a by forward substitution in one warp, write H[:, j] and w0.
-__global__ void k_cwy_solve(const double* part, int nchunk, int j, int m, const int* active, double* Lt, double* H,
-                            double* Hraw, double* w0) {
-  const int b = blockIdx.x;
-  if (!active[b]) return;
-  const int nslot = 2 * m + 3;
-  __shared__ double a[130];
-  const double* pb = part + (size_t)b * nchunk * nslot;
-  double* L = Lt + (size_t)b * (m + 1) * (m + 1);
-  for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
-    const bool used = t <= j || (t >= m + 1 && t < m + 1 + j) || t == 2 * m + 2;
-    if (!used) continue;
-    double acc = 0.0;
-    for (int c = 0; c < nchunk; ++c) acc += pb[(size_t)c * nslot + t];
-    if (t <= j) a[t] = acc;
-    else if (t < m + 1 + j) L[(size_t)(t - m - 1) * (m + 1) + j] = acc;
-    else w0[b] = sqrt(acc);
-  }
-  __syncthreads();
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
-  double* h = H + ((size_t)b * m + j) * (m + 1);
-  double* hr = Hraw ? Hraw + ((size_t)b * m + j) * (m + 1) : nullptr;
-  // forward substitution (I + L) h = a; lane owns rows t = lane + 32 q; the Gram row of step i + 1
-  // (Lt[i+1][t] = v_{i+1} . v_t) is loaded while step i is processed
-  double at[5], lr[5];
-  for (int q = 0; q < 5; ++q) {
-    const int t = lane + 32 * q;
-    at[q] = t <= j ? a[t] : 0.0;
-    lr[q] = (t > 0 && t <= j) ? L[t] : 0.0;   // row 0
-  }
-  for (int i = 0; i <= j; ++i) {
-    double nx[5];
-    for (int q = 0; q < 5; ++q) {
-      const int t = lane + 32 * q;
-      nx[q] = (i + 1 <= j && t > i + 1 && t <= j) ? L[(size_t)(i + 1) * (m + 1) + t] : 0.0;
+__global__ void __launch_bounds__(256) k_precond_coop(int B, const int2* items, int nitems, const InstInfo* inst,
+                                                      const int* active, const RomInstDev* ri, const double* sig_dof,
+                                                      const double* v, double* z, double* rpart, double* rc,
+                                                      int nchunk, int f64) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double red[8][64];
+  __shared__ double ys[64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // phase 1: copy (instances without a ROM) or projection partials P^T Sigma_s v over the chunk
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int b = items[it].x, ch = items[it].y;
+    if (!active[b]) continue;
+    const InstInfo in = inst[b];
+    const int i0 = ch * 256, i1 = min(in.ndof, i0 + 256);
+    const RomInstDev R = ri[b];
+    if (!R.has) {
+      const int i = i0 + threadIdx.x;
+      if (i < i1) z[in.off + i] = v[in.off + i];
+      continue;
     }
-    const int owner = i & 31, qi = i >> 5;
-    double mine = 0.0;
-    for (int q = 0; q < 5; ++q)
-      if (q == qi) mine = at[q];
-    const double hi = __shfl_sync(0xffffffffu, mine, owner);
-    if (lane == 0) {
-      h[i] = hi;
-      if (hr) hr[i] = hi;
+    double acc0 = 0.0, acc1 = 0.0;
+    for (int i = i0 + warp; i < i1; i += 8) {
+      const double sv = sig_dof[in.off + i] * v[in.off + i];
+      if (f64) {
+        if (lane < R.r) acc0 += R.P[(size_t)i * R.rmax + lane] * sv;
+        if (lane + 32 < R.r) acc1 += R.P[(size_t)i * R.rmax + lane + 32] * sv;
+      } else {
+        if (lane < R.r) acc0 += (double)R.P32[(size_t)i * R.rmax + lane] * sv;
+        if (lane + 32 < R.r) acc1 += (double)R.P32[(size_t)i * R.rmax + lane + 32] * sv;
+      }
     }
-    for (int q = 0; q < 5; ++q) {
-      const int t = lane + 32 * q;
-      if (t > i && t <= j) at[q] -= lr[q] * hi;
-      lr[q] = nx[q];
-    }
-  }
-}
-
-// Pass 3: w -= sum_k h_k v_k for the chunk, partial ||w||^2 per block.
-__global__ void __launch_bounds__(256) k_cwy_update(double* V, long long ntot, int j, int m, const InstInfo* inst,
-                                                    const int* active, const double* H, int chunk, double* part) {
-  const int b = blockIdx.y;
-  if (!active[b]) return;
-  const InstInfo in = inst[b];
-  const int i0 = blockIdx.x * chunk;
-  if (i0 >= in.ndof) return;
-  __shared__ double hs[130];
-  __shared__ double red[8];
-  const double* h = H + ((size_t)b * m + j) * (m + 1);
-  for (int t = threadIdx.x; t <= j; t += blockDim.x) hs[t] = h[t];
-  __syncthreads();
-  const int i = i0 + threadIdx.x;
-  const bool ok = i < in.ndof && threadIdx.x < chunk;
-  double s = 0.0;
-  if (ok) {
-    double wi = V[(size_t)(j + 1) * ntot + in.off + i];
-    for (int kk = 0; kk <= j; ++kk) wi -= hs[kk] * V[(size_t)kk * ntot + in.off + i];
-    V[(size_t)(j + 1) * ntot + in.off + i] = wi;
-    s = wi * wi;
-  }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double acc = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) acc += red[q];
-    part[(size_t)b * gridDim.x + blockIdx.x] = acc;
-  }
-}
-
-// Pass 5: v_{j+1} = w / h_{j+1,j} unless the instance broke down.
-__global__ void k_cwy_normalize(double* V, long long ntot, int j, const InstInfo* inst, const int* active0,
-                                const int* brk, const double* hnorm) {
-  const int b = blockIdx.y;
-  if (!active0[b] || brk[b]) return;
-  const InstInfo in = inst[b];
-  const double inv = 1.0 / hnorm[b];
-  double* w = V + (size_t)(j + 1) * ntot + in.off;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) w[i] *= inv;
-}
-
-// Givens update of column j (one block per active instance): the column and the stored rotations are
-// staged in shared memory by all threads, then one thread applies the j previous rotations.
-__global__ void k_givens(double* H, double* cs, double* sn, double* g, int j, int m, int B, int* active,
-                         int* brk, const double* bnorm, const double* rtol_p, int* iters_left, double* est,
-                         int* flag, int* kcols, const double* npart, int nchunk, const double* w0, double* hnorm,
-                         double* Hraw, int* active0) {
-  const int b = blockIdx.x;
-  if (!active[b]) {
-    if (threadIdx.x == 0) active0[b] = 0;
-    return;
-  }
-  __shared__ double hs[130], css[128], sns[128];
-  double* h = H + ((size_t)b * m + j) * (m + 1);
-  if (npart) {
-    // finish the orthogonalisation: h_{j+1,j} = ||w|| (partials summed in chunk order), breakdown test
-    if (threadIdx.x == 0) {
-      double acc = 0.0;
-      for (int c = 0; c < nchunk; ++c) acc += npart[(size_t)b * nchunk + c];
-      const double hn = sqrt(acc);
-      h[j + 1] = hn;
-      if (Hraw) Hraw[((size_t)b * m + j) * (m + 1) + j + 1] = hn;
-      hnorm[b] = hn;
-      brk[b] = (hn > 1e-14 * w0[b]) ? 0 : 1;
-      active0[b] = 1;
+    red[warp][lane] = acc0;
+    red[warp][lane + 32] = acc1;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+      double s = 0.0;
+      for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+      rpart[((size_t)b * nchunk + ch) * 64 + threadIdx.x] = s;
     }
     __syncthreads();
   }
-  double* c = cs + (size_t)b * m;
-  double* s = sn + (size_t)b * m;
-  double* gg = g + (size_t)b * (m + 1);
-  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) hs[i] = h[i];
-  for (int i = threadIdx.x; i < j; i += blockDim.x) { css[i] = c[i]; sns[i] = s[i]; }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  for (int i = 0; i < j; ++i) {
-    const double t = css[i] * hs[i] + sns[i] * hs[i + 1];
-    hs[i + 1] = -sns[i] * hs[i] + css[i] * hs[i + 1];
-    hs[i] = t;
+  grid.sync();
+  // phase 2: c = (U^T A_mu U)^{-1} (sum of the partials) per instance
+  for (int b = blockIdx.x; b < B; b += gridDim.x) {
+    if (!active[b] || !ri[b].has) continue;
+    const RomInstDev R = ri[b];
+    const int nch = (inst[b].ndof + 255) / 256;
+    if (threadIdx.x < R.r) {
+      double s = 0.0;
+      for (int c = 0; c < nch; ++c) s += rpart[((size_t)b * nchunk + c) * 64 + threadIdx.x];
+      ys[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < R.r) {
+      const double* row = R.inv + (size_t)threadIdx.x * R.r;
+      double s = 0.0;
+      for (int q = 0; q < R.r; ++q) s += row[q] * ys[q];
+      rc[(size_t)b * 64 + threadIdx.x] = s;
+    }
+    __syncthreads();
   }
-  const double den = hypot(hs[j], hs[j + 1]);
-  double cj = 1.0, sj = 0.0;
-  if (den > 0.0) { cj = hs[j] / den; sj = hs[j + 1] / den; }
-  for (int i = 0; i < j; ++i) h[i] = hs[i];
-  c[j] = cj;
-  s[j] = sj;
-  h[j] = den;
-  h[j + 1] = 0.0;
-  const double gj = gg[j];
-  gg[j + 1] = -sj * gj;
-  gg[j] = cj * gj;
-  const double e = fabs(sj * gj);
-  est[b] = e;
-  kcols[b] = j + 1;
-  int f = RUN;
-  if (!isfinite(e) || !isfinite(den)) f = STOP_NUMERIC;
-  else if (e <= rtol_p[0] * bnorm[b]) f = STOP_CONV;
-  else if (brk[b]) f = STOP_BREAK;
-  else if (j + 1 == m || iters_left[b] <= 1) f = STOP_RESTART;
-  flag[b] = f;
-  iters_left[b] -= 1;
-  if (f != RUN) active[b] = 0;   // the instance leaves this cycle; the host mirrors it from flag
+  grid.sync();
+  // phase 3: z = v + W c
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int b = items[it].x, ch = items[it].y;
+    if (!active[b] || !ri[b].has) continue;
+    const InstInfo in = inst[b];
+    const RomInstDev R = ri[b];
+    const int i = ch * 256 + threadIdx.x;
+    if (i >= in.ndof) continue;
+    const double* c = rc + (size_t)b * 64;
+    double s = 0.0;
+    if (f64) {
+      const double* w = R.W + (size_t)i * R.rmax;
+      for (int q = 0; q < R.r; ++q) s += w[q] * c[q];
+    } else {
+      const float* w = R.W32 + (size_t)i * R.rmax;
+      for (int q = 0; q < R.r; ++q) s += (double)w[q] * c[q];
+    }
+    z[in.off + i] = v[in.off + i] + s;
+  }
+}
+
+template <typename TP>
+__global__ void __launch_bounds__(256) k_arnoldi_coop(
+    int B, const int2* items, int nitems, const InstInfo* inst, int* active, const TP* partial, int ntask,
+    const double* z, double* V, long long ntot, int j, int m, int nchunk, double* part, double* npart, double* Lt,
+    double* H, double* Hraw, double* w0, double* cs, double* sn, double* g, int* brk, const double* bnorm,
+    const double* rtol_p, int* iters_left, double* est, int* flag, int* kcols, double* hnorm, int* active0) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nslot = 2 * m + 3;
+  __shared__ double red[8][260];
+  __shared__ double sh[8];
+  __shared__ double hs[130], css[128], sns[128];
+  // P0: w = z - sum_t partial_t (the A~ z of this iteration) into V[j+1], then the chunk's partial dots
+  //     a_k = v_k . w (k <= j), g_k = v_k . v_j (k < j), w . w.  w and v_j are staged in shared memory
+  //     and warp q owns k = q, q + 8, ...: its reductions are independent of the other warps'.
+  __shared__ double wsh[256], vjsh[256];
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int b = items[it].x, ch = items[it].y;
+    if (!active[b]) continue;
+    const InstInfo in = inst[b];
+    const int i0 = ch * 256;
+    const int i = i0 + threadIdx.x;
+    const bool ok = i < in.ndof;
+    double wi = 0.0;
+    if (ok) {
+      const TP* pp = partial + (size_t)ntask * in.off;
+      TP s = 0;
+      for (int t = 0; t < ntask; ++t) s += pp[(size_t)t * in.ndof + i];
+      wi = z[in.off + i] - (double)s;
+      V[(size_t)(j + 1) * ntot + in.off + i] = wi;
+    }
+    wsh[threadIdx.x] = wi;
+    vjsh[threadIdx.x] = ok ? V[(size_t)j * ntot + in.off + i] : 0.0;
+    __syncthreads();
+    const int nvalid = min(256, in.ndof - i0);
+    for (int kk = warp; kk <= j; kk += 8) {
+      const double* vk = V + (size_t)kk * ntot + in.off + i0;
+      double a = 0.0, gg = 0.0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int ii = lane + 32 * e;
+        const double x = ii < nvalid ? vk[ii] : 0.0;
+        a += x * wsh[ii];
+        gg += x * vjsh[ii];
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        gg += __shfl_xor_sync(0xffffffffu, gg, o);
+      }
+      if (lane == 0) {
+        red[0][kk] = a;
+        if (kk < j) red[0][m + 1 + kk] = gg;
+      }
+    }
+    if (warp == 7) {
+      double ww = 0.0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) ww += wsh[lane + 32 * e] * wsh[lane + 32 * e];
+      for (int o = 16; o > 0; o >>= 1) ww += __shfl_xor_sync(0xffffffffu, ww, o);
+      if (lane == 0) red[0][2 * m + 2] = ww;
+    }
+    __syncthreads();
+    double* out = part + ((size_t)b * nchunk + ch) * nslot;
+    for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
+      const bool used = t <= j || (t >= m + 1 && t < m + 1 + j) || t == 2 * m + 2;
+      if (used) out[t] = red[0][t];
+    }
+    __syncthreads();
+  }
+  grid.sync();
+  // P1: per instance: sum the partials (chunk order), Gram row, (I + L) h = a by forward substitution
+  for (int b = blockIdx.x; b < B; b += gridDim.x) {
+    if (!active[b]) continue;
+    const int nch = (inst[b].ndof + 255) / 256;
+    const double* pb = part + (size_t)b * nchunk * nslot;
+    double* L = Lt + (size_t)b * (m + 1) * (m + 1);
+    double* a = hs;
+    for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
+      const bool used = t <= j || (t >= m + 1 && t < m + 1 + j) || t == 2 * m + 2;
+      if (!used) continue;
+      double acc = 0.0;
+      for (int c = 0; c < nch; ++c) acc += pb[(size_t)c * nslot + t];
+      if (t <= j) a[t] = acc;
+      else if (t < m + 1 + j) L[(size_t)(t - m - 1) * (m + 1) + j] = acc;
+      else w0[b] = sqrt(acc);
+    }
+    __syncthreads();
+    if (warp == 0) {
+      double* h = H + ((size_t)b * m + j) * (m + 1);
+      double* hr = Hraw ? Hraw + ((size_t)b * m + j) * (m + 1) : nullptr;
+      double at[5], lr[5];
+      for (int q = 0; q < 5; ++q) {
+        const int t = lane + 32 * q;
+        at[q] = t <= j ? a[t] : 0.0;
+        lr[q] = (t > 0 && t <= j) ? L[t] : 0.0;
+      }
+      for (int i = 0; i <= j; ++i) {
+        double nx[5];
+        for (int q = 0; q < 5; ++q) {
+          const int t = lane + 32 * q;
+          nx[q] = (i + 1 <= j && t > i + 1 && t <= j) ? L[(size_t)(i + 1) * (m + 1) + t] : 0.0;
+        }
+        const int owner = i & 31, qi = i >> 5;
+        double mine = 0.0;
+        for (int q = 0; q < 5; ++q)
+          if (q == qi) mine = at[q];
+        const double hi = __shfl_sync(0xffffffffu, mine, owner);
+        if (lane == 0) {
+          h[i] = hi;
+          if (hr) hr[i] = hi;
+        }
+        for (int q = 0; q < 5; ++q) {
+          const int t = lane + 32 * q;
+          if (t > i && t <= j) at[q] -= lr[q] * hi;
+          lr[q] = nx[q];
+        }
+      }
+    }
+    __syncthreads();
+  }
+  grid.sync();
+  // P2: w -= sum_k h_k v_k over the chunk, partial ||w||^2
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int b = items[it].x, ch = items[it].y;
+    if (!active[b]) continue;
+    const InstInfo in = inst[b];
+    const double* h = H + ((size_t)b * m + j) * (m + 1);
+    for (int t = threadIdx.x; t <= j; t += blockDim.x) hs[t] = h[t];
+    __syncthreads();
+    const int i = ch * 256 + threadIdx.x;
+    double s2 = 0.0;
+    if (i < in.ndof) {
+      double wi = V[(size_t)(j + 1) * ntot + in.off + i];
+      for (int kk = 0; kk <= j; ++kk) wi -= hs[kk] * V[(size_t)kk * ntot + in.off + i];
+      V[(size_t)(j + 1) * ntot + in.off + i] = wi;
+      s2 = wi * wi;
+    }
+    const double tot = block_sum256(s2, sh);
+    if (threadIdx.x == 0) npart[(size_t)b * nchunk + ch] = tot;
+    __syncthreads();
+  }
+  grid.sync();
+  // P3: per instance: h_{j+1,j} = ||w||, breakdown test, Givens rotation, stopping flags
+  for (int b = blockIdx.x; b < B; b += gridDim.x) {
+    if (!active[b]) {
+      if (threadIdx.x == 0) active0[b] = 0;
+      continue;
+    }
+    double* h = H + ((size_t)b * m + j) * (m + 1);
+    double* c = cs + (size_t)b * m;
+    double* s = sn + (size_t)b * m;
+    double* gg = g + (size_t)b * (m + 1);
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) hs[i] = h[i];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) { css[i] = c[i]; sns[i] = s[i]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int nch = (inst[b].ndof + 255) / 256;
+      double acc = 0.0;
+      for (int cc = 0; cc < nch; ++cc) acc += npart[(size_t)b * nchunk + cc];
+      const double hn = sqrt(acc);
+      hs[j + 1] = hn;
+      if (Hraw) Hraw[((size_t)b * m + j) * (m + 1) + j + 1] = hn;
+      hnorm[b] = hn;
+      const int bk = (hn > 1e-14 * w0[b]) ? 0 : 1;
+      brk[b] = bk;
+      active0[b] = 1;
+      for (int i = 0; i < j; ++i) {
+        const double t = css[i] * hs[i] + sns[i] * hs[i + 1];
+        hs[i + 1] = -sns[i] * hs[i] + css[i] * hs[i + 1];
+        hs[i] = t;
+      }
+      const double den = hypot(hs[j], hs[j + 1]);
+      double cj = 1.0, sj = 0.0;
+      if (den > 0.0) { cj = hs[j] / den; sj = hs[j + 1] / den; }
+      for (int i = 0; i < j; ++i) h[i] = hs[i];
+      c[j] = cj;
+      s[j] = sj;
+      h[j] = den;
+      h[j + 1] = 0.0;
+      const double gj = gg[j];
+      gg[j + 1] = -sj * gj;
+      gg[j] = cj * gj;
+      const double e = fabs(sj * gj);
+      est[b] = e;
+      kcols[b] = j + 1;
+      int f = RUN;
+      if (!isfinite(e) || !isfinite(den)) f = STOP_NUMERIC;
+      else if (e <= rtol_p[0] * bnorm[b]) f = STOP_CONV;
+      else if (bk) f = STOP_BREAK;
+      else if (j + 1 == m || iters_left[b] <= 1) f = STOP_RESTART;
+      flag[b] = f;
+      iters_left[b] -= 1;
+      if (f != RUN) active[b] = 0;
+    }
+    __syncthreads();
+  }
+  grid.sync();
+  // P4: v_{j+1} = w / h_{j+1,j}
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int b = items[it].x, ch = items[it].y;
+    if (!active0[b] || brk[b]) continue;
+    const InstInfo in = inst[b];
+    const int i = ch * 256 + threadIdx.x;
+    if (i < in.ndof) V[(size_t)(j + 1) * ntot + in.off + i] *= 1.0 / hnorm[b];
+  }
 }
 
 // y = R^{-1} g (R: rotated H, upper triangular k x k), one block per instance with k > 0:
@@ -394,6 +508,13 @@ struct Ws {
   };
   std::unordered_map<int, Graph> graphs;
   std::vector<RomPlan> plans;   // persistent across solves (same ROM groups -> same buffers)
+  // fused iteration kernels: vector chunks (instance, 256-dof chunk), per-instance ROM data, and the
+  // co-resident grid sizes of the cooperative launches
+  DevBuf<int2> items;
+  int nitems = 0;
+  DevBuf<RomInstDev> rominst;
+  DevBuf<double> rpart, rc;
+  int grid_pre = 0, grid_post64 = 0, grid_post32 = 0;
   std::vector<romsad_t> plan_rom;
   std::vector<std::vector<int>> plan_ids;
   void drop_graphs() {
@@ -429,6 +550,29 @@ struct Ws {
       nchunk = (maxn + 255) / 256;
     }
     RTE_TRY(Lt.alloc((size_t)B * (m + 1) * (m + 1)));
+    {
+      std::vector<int2> it;
+      for (int b = 0; b < p->B; ++b) {
+        const int nb = (int)((p->off[b + 1] - p->off[b] + 255) / 256);
+        for (int c = 0; c < nb; ++c) it.push_back(make_int2(b, c));
+      }
+      nitems = (int)it.size();
+      RTE_TRY(items.alloc(it.size()));
+      RTE_CHECK_CUDA(cudaMemcpy(items.p, it.data(), it.size() * sizeof(int2), cudaMemcpyHostToDevice));
+      RTE_TRY(rominst.alloc(B));
+      RTE_TRY(rpart.alloc((size_t)B * nchunk * 64));
+      RTE_TRY(rc.alloc((size_t)B * 64));
+      int dev = 0, nsm = 0, occ = 0;
+      RTE_CHECK_CUDA(cudaGetDevice(&dev));
+      RTE_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+      const int want = std::max(nitems, B);
+      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_precond_coop, 256, 0));
+      grid_pre = std::min(want, std::max(1, occ) * nsm);
+      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_coop<double>, 256, 0));
+      grid_post64 = std::min(want, std::max(1, occ) * nsm);
+      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_coop<float>, 256, 0));
+      grid_post32 = std::min(want, std::max(1, occ) * nsm);
+    }
     RTE_TRY(part.alloc((size_t)B * nchunk * (2 * m + 3)));
     RTE_TRY(npart.alloc((size_t)B * nchunk));
     RTE_TRY(w0.alloc(B));
@@ -476,11 +620,6 @@ struct SolveCtx {
   std::vector<int> no_rom_mask;       // [B] 1 for instances without a ROM
 };
 
-// dst[b] = a[b] && m[b]
-__global__ void k_mask_and2(int* dst, const int* a, const int* m, int B) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b < B) dst[b] = a[b] && m[b];
-}
 
 static dim3 vec_grid(rte_problem* p) {
   int maxn = 0;
@@ -586,34 +725,62 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
         double* zj = Zbase + (size_t)j * ntot;
         if (W.withZ) {
           if (use_rom) {
-            // copy for instances without a ROM, ROMSAD for the others
-            k_mask_and2<<<(B + 127) / 128, 128, 0, s>>>(W.brk.p, W.norom.p, W.active.p, B);
+            const int2* it_p = W.items.p;
+            int nit = W.nitems, Bv = B, nch = W.nchunk, f = f64 ? 1 : 0;
+            const InstInfo* inst_p = p->d_inst.p;
+            const int* act_p = W.active.p;
+            const RomInstDev* ri_p = W.rominst.p;
+            const double* sd_p = p->d_sig_dof.p;
+            double* rp_p = W.rpart.p;
+            double* rc_p = W.rc.p;
+            void* args[] = {&Bv, &it_p, &nit, &inst_p, &act_p, &ri_p, &sd_p, &vj, &zj, &rp_p, &rc_p, &nch, &f};
+            RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_precond_coop, dim3(W.grid_pre), dim3(256), args,
+                                                       0, s));
             count_launch();
-            k_copy_active<<<vg, 256, 0, s>>>(zj, vj, p->d_inst.p, W.brk.p);
-            count_launch();
-            for (auto& pl : *C.plans) RTE_TRY(pl.apply(p, W.active.p, vj, zj, f64, s));
           } else {
             k_copy_active<<<vg, 256, 0, s>>>(zj, vj, p->d_inst.p, W.active.p);
             count_launch();
           }
         }
-        RTE_TRY(launch_T(p, MODE_OP, f64, zj, true, nullptr, W.V.p + (size_t)(j + 1) * ntot, true, W.active.p, s));
-        const int chunk = 256;
-        const dim3 gch((unsigned)W.nchunk, B);
-        const size_t smem = (size_t)8 * (2 * m + 3) * sizeof(double);
-        k_cwy_dots<<<gch, 256, smem, s>>>(W.V.p, ntot, j, m, p->d_inst.p, W.active.p, chunk, W.part.p);
-        count_launch();
-        k_cwy_solve<<<B, 256, 0, s>>>(W.part.p, W.nchunk, j, m, W.active.p, W.Lt.p, W.H.p,
-                                      C.rec ? W.Hraw.p : nullptr, W.w0.p);
-        count_launch();
-        k_cwy_update<<<gch, 256, 0, s>>>(W.V.p, ntot, j, m, p->d_inst.p, W.active.p, W.H.p, chunk, W.npart.p);
-        count_launch();
-        k_givens<<<B, 128, 0, s>>>(W.H.p, W.cs.p, W.sn.p, W.g.p, j, m, B, W.active.p, W.brk.p, W.bnorm.p, W.d_rtol.p,
-                                   W.iters_left.p, W.est.p, W.flag.p, W.kcols.p, W.npart.p, W.nchunk, W.w0.p,
-                                   W.hnorm.p, C.rec ? W.Hraw.p : nullptr, W.active0.p);
-        count_launch();
-        k_cwy_normalize<<<vg, 256, 0, s>>>(W.V.p, ntot, j, p->d_inst.p, W.active0.p, W.brk.p, W.hnorm.p);
-        count_launch();
+        RTE_TRY(launch_op_partials(p, f64, zj, W.active.p, s));
+        {
+          int Bv = B, nit = W.nitems, ntask = p->tasks_per_inst, jj = j, mm = m, nch = W.nchunk;
+          long long nt = ntot;
+          const int2* it_p = W.items.p;
+          const InstInfo* inst_p = p->d_inst.p;
+          int* act_p = W.active.p;
+          const void* part_p = p->d_partial.p;
+          const double* z_p = zj;
+          double* V_p = W.V.p;
+          double* dp_p = W.part.p;
+          double* np_p = W.npart.p;
+          double* Lt_p = W.Lt.p;
+          double* H_p = W.H.p;
+          double* Hr_p = C.rec ? W.Hraw.p : nullptr;
+          double* w0_p = W.w0.p;
+          double* cs_p = W.cs.p;
+          double* sn_p = W.sn.p;
+          double* g_p = W.g.p;
+          int* brk_p = W.brk.p;
+          const double* bn_p = W.bnorm.p;
+          const double* rt_p = W.d_rtol.p;
+          int* il_p = W.iters_left.p;
+          double* est_p = W.est.p;
+          int* fl_p = W.flag.p;
+          int* kc_p = W.kcols.p;
+          double* hn_p = W.hnorm.p;
+          int* a0_p = W.active0.p;
+          void* args[] = {&Bv, &it_p, &nit, &inst_p, &act_p, &part_p, &ntask, &z_p, &V_p, &nt, &jj, &mm, &nch,
+                          &dp_p, &np_p, &Lt_p, &H_p, &Hr_p, &w0_p, &cs_p, &sn_p, &g_p, &brk_p, &bn_p, &rt_p,
+                          &il_p, &est_p, &fl_p, &kc_p, &hn_p, &a0_p};
+          if (f64)
+            RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop<double>, dim3(W.grid_post64),
+                                                       dim3(256), args, 0, s));
+          else
+            RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop<float>, dim3(W.grid_post32),
+                                                       dim3(256), args, 0, s));
+          count_launch();
+        }
         RTE_CHECK_CUDA(cudaGetLastError());
         return RTE_OK;
       };
@@ -824,6 +991,16 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     }
     for (size_t q = 0; q < prom.size(); ++q) RTE_TRY(ws->plans[q].build(prom[q], p, pids[q], st));
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->norom.p, C.no_rom_mask.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    std::vector<RomInstDev> ri(B);
+    for (int b = 0; b < B; ++b) ri[b] = RomInstDev{nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0};
+    for (size_t q = 0; q < prom.size(); ++q)
+      for (size_t sl = 0; sl < pids[q].size(); ++sl) {
+        romsad* rm = prom[q];
+        ri[pids[q][sl]] = RomInstDev{rm->P.p, rm->W.p, rm->P32.p, rm->W32.p, ws->plans[q].lu.p + sl * 64 * 64,
+                                     rm->r, rm->rmax, 1};
+      }
+    RTE_CHECK_CUDA(cudaMemcpyAsync(ws->rominst.p, ri.data(), B * sizeof(RomInstDev), cudaMemcpyHostToDevice, st));
+    RTE_CHECK_CUDA(cudaStreamSynchronize(st));
   }
   RTE_TRY(prepare_sweeps(p));
   C.plans = &ws->plans;

@@ -88,6 +88,9 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
   T* tab = reinterpret_cast<T*>(smem_raw) + (size_t)warp * a.smem_per_warp;
   T* ybuf = tab + D * R * 16;
   T* sgs = ybuf + D * nx * 2;   // sigma_s per region
+  // angular-output staging ring: per lane and direction the last 8 cells of its current row
+  T* ring = ANG ? reinterpret_cast<T*>(smem_raw) + (size_t)wpb * a.smem_per_warp + ((size_t)warp * 32 + lane) * D * 32
+                : nullptr;
   const T* linv = reinterpret_cast<const T*>(a.linv) + ((size_t)tk.b * a.nu + tk.u0) * R * 16;
   for (int e = lane; e < D * R * 16; e += 32) tab[e] = linv[e];
   if (a.sig_s)
@@ -257,19 +260,52 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
         }
         if (ANG) {
           const T q1 = sx > 0 ? p1 : -p1, q2 = sy > 0 ? p2 : -p2, q3 = (sx * sy) > 0 ? p3 : -p3;
-          if (a.psi_unique) {
-            Vec4<T>::store(psi + (size_t)(tk.u0 + d) * in.ndof + 4 * c, p0, q1, q2, q3);
-          } else {
-            const UDir u = a.udir[tk.u0 + d];
-            for (int k = 0; k < u.ndup; ++k)
-              Vec4<T>::store(psi + (size_t)u.dup[k] * in.ndof + 4 * c, p0, q1, q2, q3);
-          }
+          Vec4<T>::store(ring + d * 32 + (col & 7) * 4, p0, q1, q2, q3);
         }
       }
       acc1 = sx > 0 ? acc1 : -acc1;
       acc2 = sy > 0 ? acc2 : -acc2;
       acc3 = (sx * sy) > 0 ? acc3 : -acc3;
       Vec4<T>::store(part + 4 * c, acc0, acc1, acc2, acc3);
+    }
+    if (ANG) {
+      // lanes that completed an aligned 8-cell row segment (or their row) hand it to the warp: lanes
+      // 8k..8k+7 store the k-th completed segment, one cell each, i.e. whole 128-byte lines
+      const bool flush = act && ((col & 7) == 7 || col == nx - 1);
+      const long long myc = act ? c : 0;
+      const int mycol = act ? col : 0;
+      __syncwarp();
+      unsigned fm = __ballot_sync(0xffffffffu, flush);
+      while (fm) {
+        int fl[4], n = 0;
+        while (fm && n < 4) {
+          fl[n++] = __ffs(fm) - 1;
+          fm &= fm - 1;
+        }
+        const int k = lane >> 3, e = lane & 7;
+        const int f = fl[k < n ? k : 0];
+        const long long cf = __shfl_sync(0xffffffffu, myc, f);
+        const int colf = __shfl_sync(0xffffffffu, mycol, f);
+        if (k < n) {
+          const int cs = colf & ~7;
+          if (e <= colf - cs) {
+            const long long cellf = cf + (sx > 0 ? (cs + e - colf) : (colf - cs - e));
+            const T* src_ring = ring - (size_t)(lane - f) * D * 32;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              T v0, v1, v2, v3;
+              Vec4<T>::load(src_ring + d * 32 + e * 4, v0, v1, v2, v3);
+              if (a.psi_unique) {
+                Vec4<T>::store(psi + (size_t)(tk.u0 + d) * in.ndof + 4 * cellf, v0, v1, v2, v3);
+              } else {
+                const UDir u = a.udir[tk.u0 + d];
+                for (int q = 0; q < u.ndup; ++q)
+                  Vec4<T>::store(psi + (size_t)u.dup[q] * in.ndof + 4 * cellf, v0, v1, v2, v3);
+              }
+            }
+          }
+        }
+      }
     }
     __syncwarp();
   }
@@ -693,8 +729,11 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
   // The band kernel shortens the critical path (latency-bound launches, FP32); for FP64 launches with
   // enough tasks to fill the GPU the FP64 pipe is the limit and the warp-per-task kernel keeps more
   // warps per SM (no idle band warps on smaller meshes of a mixed batch).
-  const bool fp64_throughput = sizeof(T) == 8 && a.ntasks >= 152 * 8;
-  if (nbands <= 8 && !fp64_throughput) {
+  const bool throughput = a.ntasks >= 152 * 8;
+  const bool fp64_throughput = sizeof(T) == 8 && throughput;
+  // angular output with many tasks: independent warps (no per-step CTA barrier) hide the store latency
+  const bool ang_throughput = ANG && throughput;
+  if (nbands <= 8 && !fp64_throughput && !ang_throughput) {
     // band-parallel kernel: one CTA per task, one warp per 32-row band
     const int W = nbands;
     size_t elems = (size_t)D * p->R * 16 + ((p->R + 3) & ~3) + (((size_t)(W > 1 ? W - 1 : 1) * D * maxnx * 2 + 3) & ~(size_t)3);
@@ -731,7 +770,7 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
   }
   a.smem_per_warp = D * p->R * 16 + D * maxnx * 2 + p->R;
   a.smem_per_warp = (a.smem_per_warp + 3) & ~3;
-  size_t per_warp = (size_t)a.smem_per_warp * sizeof(T);
+  size_t per_warp = (size_t)a.smem_per_warp * sizeof(T) + (ANG ? (size_t)32 * D * 32 * sizeof(T) : 0);
   int wpb = 4;
   while (wpb > 1 && per_warp * wpb > 96 * 1024) --wpb;
   size_t smem = per_warp * wpb;
@@ -841,6 +880,23 @@ int launch_T(rte_problem* p, int mode, bool f64, const void* src, bool in_f64, c
 #undef RTE_RED
   count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
+  return RTE_OK;
+}
+
+// Sweep part of A~ z only: fills the per-task partial scalar fluxes (Sigma_s scaling fused); the
+// subtraction z - sum_t partial_t is left to the caller's kernel (the fused Arnoldi step).
+int launch_op_partials(rte_problem* p, bool f64, const void* z, const int* d_active, cudaStream_t st) {
+  int D = pick_D(p, f64);
+  RTE_TRY(ensure_tasks(p, D));
+  RTE_TRY(ensure_partial(p, f64));
+  SweepArgs a;
+  fill_args(p, a, f64);
+  a.src = z;
+  a.sig_s = f64 ? (const void*)p->d_sig_s.p : (const void*)p->d_sig_s32.p;
+  a.partial = p->d_partial.p;
+  a.active = d_active;
+  if (f64) RTE_TRY((launch_sweep_t<double, double, false>(p, D, a, st)));
+  else RTE_TRY((launch_sweep_t<float, double, false>(p, D, a, st)));
   return RTE_OK;
 }
 
