@@ -142,6 +142,12 @@ struct rte_problem {
   int ntasks_by_D[17] = {0};
   int per_inst_by_D[17] = {0};
   int tasks_D = -1;                           // D of the most recent launch
+  // sweep autotuner (sweep.cu): tuned directions per warp and kernel variant per [fp64][angular]
+  // (0 = not tuned); force_* steer launches while candidates are timed
+  int tuned_D[2][2] = {{0, 0}, {0, 0}};
+  int tuned_var[2][2] = {{-1, -1}, {-1, -1}};
+  int force_D = 0, force_var = -1;
+  float tuned_ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
   int ntasks = 0, tasks_per_inst = 0;
   rte::DevBuf<int> d_active;                  // [B] instance mask (1 = active), all 1 by default
   rte::DevBuf<double> d_tmp64;                // [ntot] temporaries

@@ -654,8 +654,10 @@ int launch_forward_cols(int dim, int nx, int ny, double hx, double hy, const UDi
 }
 
 // ----------------------------------------------------------------- host side
-static int pick_D(const rte_problem* p, bool f64) {
+static int pick_D(const rte_problem* p, bool f64, bool ang = false) {
   if (p->dim == 1) return 1;
+  if (p->force_D > 0) return p->force_D;
+  if (p->tuned_D[f64 ? 1 : 0][ang ? 1 : 0] > 0) return p->tuned_D[f64 ? 1 : 0][ang ? 1 : 0];
   const int nq = p->quad_start[1] - p->quad_start[0];
   // Directions per warp: the largest D that still leaves at least 8 warps per SM (152 SMs) in
   // flight; with fewer tasks (a single small instance) parallelism wins and D = 1.  FP64 keeps D
@@ -733,7 +735,9 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
   const bool fp64_throughput = sizeof(T) == 8 && throughput;
   // angular output with many tasks: independent warps (no per-step CTA barrier) hide the store latency
   const bool ang_throughput = ANG && throughput;
-  if (nbands <= 8 && !fp64_throughput && !ang_throughput) {
+  const int tv = p->force_var >= 0 ? p->force_var : p->tuned_var[sizeof(T) == 8 ? 1 : 0][ANG ? 1 : 0];
+  const bool band = tv >= 0 ? (tv == 0 && nbands <= 8) : (nbands <= 8 && !fp64_throughput && !ang_throughput);
+  if (band) {
     // band-parallel kernel: one CTA per task, one warp per 32-row band
     const int W = nbands;
     size_t elems = (size_t)D * p->R * 16 + ((p->R + 3) & ~3) + (((size_t)(W > 1 ? W - 1 : 1) * D * maxnx * 2 + 3) & ~(size_t)3);
@@ -826,9 +830,75 @@ static int ensure_partial(rte_problem* p, bool f64) {
   return p->d_partial.ensure(bytes);
 }
 
-// Build the task lists of both precisions and size the partial-sum buffer for the larger one, so
-// that later launches (including captured CUDA graphs) see stable device pointers.
+// Sweep autotuner: times every valid (kernel variant, directions per warp) pair for one precision and
+// output mode on this problem (two launches each after a warm-up, CUDA events on the stream) and keeps
+// the fastest.  Candidates: D in {1, 2, 4, 8} dividing the directions of a quadrant (FP64: D <= 4;
+// angular output: D <= 4), variant band (ny <= 256) or warp-per-task.  The operator apply is timed
+// with its partial-sum reduction, since D also sets the number of partials.
+int autotune(rte_problem* p, bool f64, bool ang, const void* src, void* psi, cudaStream_t st, bool scale_sigma_s,
+             bool unique_layout) {
+  const int fi = f64 ? 1 : 0, ai = ang ? 1 : 0;
+  if (p->tuned_D[fi][ai] > 0 || p->dim == 1) return RTE_OK;
+  const int nq = p->quad_start[1] - p->quad_start[0];
+  int maxny = 0;
+  for (int b = 0; b < p->B; ++b) maxny = std::max(maxny, p->ny[b]);
+  RTE_TRY(p->d_tmp64.ensure((size_t)p->ntot));
+  // partials for the largest candidate task count (D = 1)
+  RTE_TRY(ensure_tasks(p, 1));
+  RTE_TRY(ensure_partial(p, f64));
+  std::vector<double> zeros;
+  const void* in = src;
+  if (!in) {
+    in = p->d_G.p;   // any input of the right size times the same
+  }
+  cudaEvent_t e0, e1;
+  RTE_CHECK_CUDA(cudaEventCreate(&e0));
+  RTE_CHECK_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bestD = 0, bestV = -1;
+  for (int var = 0; var < 2; ++var) {
+    if (var == 0 && (maxny + 31) / 32 > 8) continue;
+    for (int D : {1, 2, 4, 8}) {
+      if (nq % D || (f64 && D > 4) || (ang && D > 4)) continue;
+      p->force_D = D;
+      p->force_var = var;
+      int rc = RTE_OK;
+      float ms = 0.f;
+      for (int rep = 0; rep < 3 && rc == RTE_OK; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, st);
+        if (ang) rc = launch_angular(p, f64, in, 0, psi, st, scale_sigma_s, unique_layout);
+        else rc = launch_T(p, MODE_OP, f64, in, !f64 && src ? false : true, nullptr, p->d_tmp64.p, true, nullptr, st);
+      }
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      if (rc == RTE_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / 2 < best) {
+        best = ms / 2;
+        bestD = D;
+        bestV = var;
+      }
+      cudaGetLastError();
+    }
+  }
+  p->force_D = 0;
+  p->force_var = -1;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (bestD == 0) {
+    set_error("sweep autotuner: no candidate ran");
+    return RTE_ERR_CUDA;
+  }
+  p->tuned_D[fi][ai] = bestD;
+  p->tuned_var[fi][ai] = bestV;
+  p->tuned_ms[fi][ai] = best;
+  return RTE_OK;
+}
+
+// Tune both precisions of the operator apply, then build their task lists and size the partial-sum
+// buffer for the larger one, so that later launches (including captured CUDA graphs) see stable
+// device pointers.
 int prepare_sweeps(rte_problem* p) {
+  RTE_TRY(autotune(p, false, false, nullptr, nullptr, 0, false, false));
+  RTE_TRY(autotune(p, true, false, nullptr, nullptr, 0, false, false));
   const int d64 = pick_D(p, true), d32 = pick_D(p, false);
   RTE_TRY(ensure_tasks(p, d32));
   const size_t b32 = (size_t)p->tasks_per_inst * p->ntot * 4;
@@ -939,9 +1009,13 @@ int launch_op_external(rte_problem* p, bool f64, const void* z, void* w, const S
   return RTE_OK;
 }
 
+int autotune(rte_problem* p, bool f64, bool ang, const void* src, void* psi, cudaStream_t st, bool scale_sigma_s,
+             bool unique_layout);
+
 int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st,
                    bool scale_sigma_s, bool unique_layout) {
-  int D = std::min(2, pick_D(p, f64));   // the output staging rings grow with D
+  if (p->force_D == 0) RTE_TRY(autotune(p, f64, true, src, psi, st, scale_sigma_s, unique_layout));
+  int D = pick_D(p, f64, true);
   RTE_TRY(ensure_tasks(p, D));
   RTE_TRY(ensure_partial(p, f64));
   SweepArgs a;
