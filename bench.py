@@ -202,6 +202,60 @@ def measure_sweep_hbm(RB, torch, dev, stream, flush, reps=5):
             "alu_tflops": SWEEP_FLOPS_PER_CELL_DIR * cells * prob.info.n_unique_directions / (ms * 1e-3) / 1e12}
 
 
+def measure_batched(RB, torch, dev, stream, flush, args, reps=1):
+    """Batched throughput: the 256-instance uneven workload solved by one fgmres_solve call per batch,
+    mixed (FP32 sweeps) vs FP64, each mesh group preconditioned by its own greedy ROM."""
+    spec3 = wl.config(3)
+    R = spec3.n_regions
+    B = spec3.n_instances
+    ss, sa = wl.draw_params(spec3, B, wl.seed_for(3, 1))
+    prob = RB.Problem(spec3, ss, sa)
+    t0 = time.perf_counter()
+    roms = {}
+    tr_ss, tr_sa = wl.draw_params(spec3, args.batched_train, wl.seed_for(3, 0))
+    for n in sorted(set(spec3.nx)):
+        sp = spec3.with_instances([n], [n])
+        tmpl = RB.Problem(sp, tr_ss[:1], tr_sa[:1])
+        rom, rep = RB.Rom.greedy(tmpl, tr_ss, tr_sa, window=spec3.window, max_greedy_iter=args.batched_rank // 2,
+                                 max_rank=args.batched_rank, eps_rom=0.0, hf_rtol=1e-8, hf_restart=args.restart,
+                                 hf_max_iter=args.max_iter, indicator_f32=True)
+        roms[n] = rom
+    t_off = time.perf_counter() - t0
+    rl = [roms[n] for n in spec3.nx]
+    phi = torch.zeros(prob.n_dof, dtype=torch.float64, device=dev)
+    out = {"workload": "batch256_uneven: 96x32^2 + 96x64^2 + 64x128^2, 128 directions, one solve call per batch",
+           "instances": B, "rom_rank": args.batched_rank, "offline_s": t_off}
+    for name, mode in (("mixed", RB.RTE_MODE_MIXED), ("fp64", RB.RTE_MODE_FP64)):
+        RB.fgmres_solve(prob, rl, phi, restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec3.window,
+                        mode=mode, inner_rtol=args.inner_rtol, max_outer=30, stream=stream,
+                        raise_on_fail=False)   # warm-up / tuning
+        times, st_all = [], []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = RB.fgmres_solve(prob, rl, phi, restart=args.restart, rtol=1e-8, max_iter=args.max_iter,
+                                 window=spec3.window, mode=mode, inner_rtol=args.inner_rtol, max_outer=30,
+                                 stream=stream, raise_on_fail=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            st_all.extend(st)
+        ms = statistics.mean(times)
+        conv = sum(1 for s in st_all if s["status"] == 0) / reps
+        # only instances that met rtol count as solved
+        out[name] = {"value": conv / (ms * 1e-3), "unit": "param solves/s", "ms_per_batch": ms,
+                     "converged": conv, "escalated_to_fp64": sum(s["escalated"] for s in st_all) / reps,
+                     "iterations_max": max(s["iterations"] for s in st_all),
+                     "iterations_mean": statistics.mean(s["iterations"] for s in st_all),
+                     "true_rel_residual_max": max(s["true_rel_residual"] for s in st_all),
+                     "status": sorted({s["status"] for s in st_all})}
+    out["speedup_mixed_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -223,6 +277,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mlp-epochs", type=int, default=300)
     ap.add_argument("--no-sweep-hbm", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-train", type=int, default=16)
+    ap.add_argument("--batched-rank", type=int, default=16)
     ap.add_argument("--ref-sample", type=int, default=40, help="oracle FGMRES iterations per reference step")
     ap.add_argument("--ref-iters", type=int, default=500, help="iterations of a full solve for extrapolation")
     args = ap.parse_args()
@@ -365,6 +422,7 @@ def main():
     # angular-output sweep (rte_sweep, FP32) on the batched 256-instance problem: HBM-bound write of
     # N_Omega * N_dof * 4 bytes; this is the sweep GB/s of the metric
     sweep_hbm = measure_sweep_hbm(RB, torch, dev, stream, flush) if not args.no_sweep_hbm else None
+    batched = measure_batched(RB, torch, dev, stream, flush, args) if not args.no_batched and world == 1 else None
     roof["ms_per_launch_fp32"] = ms32
     roof["ms_per_launch_fp64"] = ms64
     roof["peak_source"] = "unit counts x max SM clock (FP32); GB300 nominal (FP64)"
@@ -396,6 +454,7 @@ def main():
         "gpu_launches": int(launches_mixed * args.steps / n_sets),
         "roofline": roof,
         "sweep_hbm": sweep_hbm,
+        "batched": batched,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

@@ -230,8 +230,13 @@ typedef struct fgmres_opts {
     int window;              /* w of eq. ROMSAD-preconditioner                        */
     int post_mode;           /* RTE_POST_ROM or RTE_POST_IDENTITY                      */
     int mode;                /* RTE_MODE_FP64 or RTE_MODE_MIXED                        */
-    double inner_rtol;       /* mixed: relative target of each inner solve             */
-    int max_outer;           /* mixed: cap on refinement steps                         */
+    double inner_rtol;       /* mixed: relative target of each inner solve (1e-2 is a good
+                                default: FP32 rounding of I - T Sigma_s limits the inner
+                                solves of strongly scattering instances near 1e-3)     */
+    int max_outer;           /* mixed: cap on refinement steps; an instance still above
+                                rtol after it, or whose refinement step cut its FP64
+                                residual by less than max(1/4, sqrt(inner_rtol)), is
+                                finished by FP64 FGMRES from its current iterate       */
     int true_residual_check; /* FP64 mode: recompute b~ - A~ phi after convergence     */
     int warm_start;          /* 0: zero initial guess; 1: phi0; 2: learned phi0 = b~ + W c_hat(mu)
                                 from each instance's ROM MLP (instances without one start at 0) */
@@ -245,6 +250,7 @@ typedef struct fgmres_stats {
     int sweeps_fp64;         /* of which in FP64                                       */
     int restarts;
     int outer;               /* mixed: refinement steps                                */
+    int escalated;           /* mixed: 1 if the instance was finished by FP64 FGMRES   */
     double est_rel_residual; /* last Givens estimate |g_{j+1}| / ||b~||                */
     double true_rel_residual;/* ||b~ - A~ phi||_2 / ||b~||_2 in FP64 (NaN if not computed) */
     double true_linf_residual;

@@ -75,8 +75,8 @@ class FgmresOpts(ctypes.Structure):
 class FgmresStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("sweeps", ctypes.c_int),
                 ("sweeps_fp64", ctypes.c_int), ("restarts", ctypes.c_int), ("outer", ctypes.c_int),
-                ("est_rel_residual", ctypes.c_double), ("true_rel_residual", ctypes.c_double),
-                ("true_linf_residual", ctypes.c_double)]
+                ("escalated", ctypes.c_int), ("est_rel_residual", ctypes.c_double),
+                ("true_rel_residual", ctypes.c_double), ("true_linf_residual", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -439,7 +439,7 @@ def attach_mlp(rom: "Rom", mlp: Optional[Mlp]):
 
 def fgmres_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi, phi0=None, restart=30,
                  rtol=1e-10, max_iter=1000, window=2, post_mode=RTE_POST_ROM, mode=RTE_MODE_FP64,
-                 inner_rtol=1e-5, max_outer=20, true_residual_check=True, stream=None, raise_on_fail=True,
+                 inner_rtol=1e-2, max_outer=20, true_residual_check=True, stream=None, raise_on_fail=True,
                  learned_warm_start=False):
     """FGMRES-ROMSAD for all instances; phi: FP64 device tensor or host (numpy/pinned) buffer.
 

@@ -491,7 +491,7 @@ struct Ws {
   int B = 0, m = 0;
   long long ntot = 0;
   bool withZ = false;
-  DevBuf<double> V, Z, H, Hraw, cs, sn, g, y, bt, r, d, phi_in;
+  DevBuf<double> V, Z, H, Hraw, cs, sn, g, y, bt, r, ro, d, phi_in;
   DevBuf<double> Lt, part, npart, w0, hnorm;   // compact-WY MGS
   DevBuf<int> active0;
   int nchunk = 0;
@@ -584,6 +584,7 @@ struct Ws {
     RTE_TRY(y.alloc((size_t)B * m));
     RTE_TRY(bt.alloc(ntot));
     RTE_TRY(r.alloc(ntot));
+    RTE_TRY(ro.alloc(ntot));
     RTE_TRY(d.alloc(ntot));
     RTE_TRY(bnorm.alloc(B));
     RTE_TRY(beta.alloc(B));
@@ -637,8 +638,8 @@ struct RunStats {
 // zero_guess) and result.  f64: sweep arithmetic.  true_check: recompute the residual after
 // convergence (FP64 sweep if f64).  it_base: iterations already done per instance (window count).
 static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess, const std::vector<int>& want,
-                      double rtol, int max_iter, bool f64, bool true_check, const std::vector<int>& it_base,
-                      RunStats& rs) {
+                      double rtol, const std::vector<int>& max_it, bool f64, bool true_check,
+                      const std::vector<int>& it_base, RunStats& rs) {
   rte_problem* p = C.p;
   Ws& W = *C.ws;
   const int B = p->B, m = C.m;
@@ -685,7 +686,7 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
       if (!std::isfinite(hb[b])) { act[b] = 0; rs.status[b] = RTE_ERR_NUMERIC; continue; }
       rs.est[b] = hb[b] / hbn[b];
       if (hb[b] <= rtol * hbn[b]) { act[b] = 0; continue; }
-      if (rs.iterations[b] >= max_iter) { act[b] = 0; rs.status[b] = RTE_ERR_NOT_CONVERGED; continue; }
+      if (rs.iterations[b] >= max_it[b]) { act[b] = 0; rs.status[b] = RTE_ERR_NOT_CONVERGED; continue; }
       ++nact;
     }
     if (nact == 0) break;
@@ -698,7 +699,7 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
       std::vector<int> left(B, 0);
       for (int b = 0; b < B; ++b) {
         g0[(size_t)b * (m + 1)] = hb[b];
-        left[b] = max_iter - rs.iterations[b];
+        left[b] = max_it[b] - rs.iterations[b];
       }
       RTE_CHECK_CUDA(cudaMemcpyAsync(W.g.p, g0.data(), g0.size() * 8, cudaMemcpyHostToDevice, st));
       RTE_CHECK_CUDA(cudaMemcpyAsync(W.iters_left.p, left.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -865,7 +866,7 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
         continue;
       }
       // restart or iteration cap
-      if (rs.iterations[b] >= max_iter) { rs.status[b] = RTE_ERR_NOT_CONVERGED; continue; }
+      if (rs.iterations[b] >= max_it[b]) { rs.status[b] = RTE_ERR_NOT_CONVERGED; continue; }
       resid[b] = 2;
     }
     bool any = false;
@@ -887,7 +888,7 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
       RTE_CHECK_CUDA(cudaStreamSynchronize(st));
       for (int b = 0; b < B; ++b) {
         if (resid[b] != 1) continue;
-        if (hn[b] <= 2.0 * rtol * hbn[b] || rs.iterations[b] >= max_iter) {
+        if (hn[b] <= 2.0 * rtol * hbn[b] || rs.iterations[b] >= max_it[b]) {
           act[b] = 0;
           if (!(hn[b] <= 2.0 * rtol * hbn[b])) rs.status[b] = RTE_ERR_NOT_CONVERGED;
         } else {
@@ -917,7 +918,8 @@ int hf_solve(rte_problem* p, double rtol, int restart, int max_iter, double* x, 
   RTE_TRY(launch_T(p, MODE_RHS, true, nullptr, true, nullptr, ws->bt.p, true, nullptr, 0));
   std::vector<int> all(p->B, 1), zero(p->B, 0);
   RunStats rs;
-  RTE_TRY(run_fgmres(C, ws->bt.p, x, true, all, rtol, max_iter, true, false, zero, rs));
+  std::vector<int> cap(p->B, max_iter);
+  RTE_TRY(run_fgmres(C, ws->bt.p, x, true, all, rtol, cap, true, false, zero, rs));
   *iterations = rs.iterations[0];
   *status = rs.status[0];
   return RTE_OK;
@@ -1038,7 +1040,8 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
   }
   if (o->mode == RTE_MODE_FP64) {
     RunStats rs;
-    RTE_TRY(run_fgmres(C, ws->bt.p, x, !warm, all, o->rtol, o->max_iter, true, o->true_residual_check != 0, zero, rs));
+    std::vector<int> cap(B, o->max_iter);
+    RTE_TRY(run_fgmres(C, ws->bt.p, x, !warm, all, o->rtol, cap, true, o->true_residual_check != 0, zero, rs));
     for (int b = 0; b < B; ++b) {
       S[b].iterations = rs.iterations[b];
       S[b].sweeps += rs.sweeps[b];
@@ -1048,17 +1051,27 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       S[b].status = rs.status[b];
     }
   } else {
-    // FP64 iterative refinement around the FP32-sweep inner FGMRES
+    // FP64 iterative refinement around the FP32-sweep inner FGMRES.  The outer residual has its own
+    // buffer (ro): the inner solve keeps its working residual in r and recomputes it from its
+    // right-hand side at every restart, so the two must not alias.
     const dim3 vg = vec_grid(p);
-    std::vector<int> act(B, 1), it_done(B, 0);
+    double* ro = ws->ro.p;
+    std::vector<int> act(B, 1), esc(B, 0);
     if (warm) {
-      RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ws->r.p, true, nullptr, st));
+      RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ro, true, nullptr, st));
       for (int b = 0; b < B; ++b) { S[b].sweeps += 1; S[b].sweeps_fp64 += 1; }
     } else {
       RTE_CHECK_CUDA(cudaMemsetAsync(x, 0, p->ntot * 8, st));
-      RTE_CHECK_CUDA(cudaMemcpyAsync(ws->r.p, ws->bt.p, p->ntot * 8, cudaMemcpyDeviceToDevice, st));
+      RTE_CHECK_CUDA(cudaMemcpyAsync(ro, ws->bt.p, p->ntot * 8, cudaMemcpyDeviceToDevice, st));
     }
-    std::vector<double> hb(B), hr(B);
+    // An outer step is meant to cut the true residual by about inner_rtol.  An instance whose step
+    // cut it by less than esc_ratio is one whose slowest modes the FP32 operator cannot resolve
+    // (eigenvalues of A~ near the FP32 rounding of I - T Sigma_s); it leaves the refinement and is
+    // finished by FP64 FGMRES from its current iterate.  Each inner solve is capped at inner_cap
+    // iterations so that a stagnating instance is caught early.
+    const double esc_ratio = std::max(0.25, std::sqrt(o->inner_rtol));
+    const int inner_cap = std::max(4 * o->restart, 512);
+    std::vector<double> hb(B), hr(B), hprev(B, 0.0);
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
     k_norm<<<B, 512, 0, st>>>(ws->bt.p, p->d_inst.p, ws->active.p, ws->nrm.p);
     count_launch();
@@ -1066,7 +1079,7 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     RTE_CHECK_CUDA(cudaStreamSynchronize(st));
     for (int outer = 0; outer <= o->max_outer; ++outer) {
       RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-      k_norm<<<B, 512, 0, st>>>(ws->r.p, p->d_inst.p, ws->active.p, ws->nrm.p);
+      k_norm<<<B, 512, 0, st>>>(ro, p->d_inst.p, ws->active.p, ws->nrm.p);
       count_launch();
       RTE_CHECK_CUDA(cudaMemcpyAsync(hr.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
       RTE_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -1078,22 +1091,30 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
         S[b].est_rel_residual = rel;
         if (!std::isfinite(rel)) { act[b] = 0; S[b].status = RTE_ERR_NUMERIC; continue; }
         if (rel <= o->rtol) { act[b] = 0; continue; }
-        if (outer == o->max_outer || S[b].iterations >= o->max_iter) {
+        if (S[b].iterations >= o->max_iter) {
           act[b] = 0;
           S[b].status = RTE_ERR_NOT_CONVERGED;
           continue;
         }
+        if (outer == o->max_outer || (outer > 0 && hr[b] > esc_ratio * hprev[b])) {
+          act[b] = 0;
+          esc[b] = 1;
+          continue;
+        }
+        hprev[b] = hr[b];
         ++nact;
       }
       if (nact == 0) break;
-      // inner solve A~ d = r (FP32 sweeps), zero guess
+      // inner solve A~ d = ro (FP32 sweeps), zero guess
+      std::vector<int> cap(B, 0);
+      for (int b = 0; b < B; ++b) cap[b] = std::min(inner_cap, o->max_iter - S[b].iterations);
       RunStats rs;
-      RTE_TRY(run_fgmres(C, ws->r.p, ws->d.p, true, act, o->inner_rtol, o->max_iter, false, false, zero, rs));
+      RTE_TRY(run_fgmres(C, ro, ws->d.p, true, act, o->inner_rtol, cap, false, false, zero, rs));
       RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
       k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d.p, p->d_inst.p, ws->active.p);
       count_launch();
-      // r = b~ - A~ x in FP64
-      RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ws->r.p, true, ws->active.p, st));
+      // ro = b~ - A~ x in FP64
+      RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ro, true, ws->active.p, st));
       for (int b = 0; b < B; ++b) {
         if (!act[b]) continue;
         S[b].iterations += rs.iterations[b];
@@ -1103,6 +1124,26 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
         S[b].outer += 1;
         if (rs.status[b] == RTE_ERR_NUMERIC) { act[b] = 0; S[b].status = RTE_ERR_NUMERIC; }
       }
+    }
+    bool any_esc = false;
+    for (int b = 0; b < B; ++b) any_esc = any_esc || esc[b];
+    if (any_esc) {
+      std::vector<int> cap(B, 0);
+      for (int b = 0; b < B; ++b) cap[b] = std::max(1, o->max_iter - S[b].iterations);
+      RunStats rs;
+      RTE_TRY(run_fgmres(C, ws->bt.p, x, false, esc, o->rtol, cap, true, o->true_residual_check != 0, zero, rs));
+      for (int b = 0; b < B; ++b) {
+        if (!esc[b]) continue;
+        S[b].iterations += rs.iterations[b];
+        S[b].sweeps += rs.sweeps[b];
+        S[b].sweeps_fp64 += rs.sweeps[b];
+        S[b].restarts += rs.restarts[b];
+        S[b].escalated = 1;
+        S[b].status = rs.status[b];
+      }
+      // FP64 residual of the escalated instances for the report below (not a solver sweep)
+      RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, esc.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+      RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ro, true, ws->active.p, st));
     }
   }
   // FP64 true residual (l2, linf) for reporting; not counted as a solver sweep
@@ -1118,13 +1159,14 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     }
   }
   if (o->mode == RTE_MODE_MIXED || o->true_residual_check) {
+    const double* rfin = o->mode == RTE_MODE_MIXED ? ws->ro.p : ws->r.p;
     std::vector<int> all1(B, 1);
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, all1.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-    k_norm<<<B, 512, 0, st>>>(ws->r.p, p->d_inst.p, ws->active.p, ws->nrm.p);
+    k_norm<<<B, 512, 0, st>>>(rfin, p->d_inst.p, ws->active.p, ws->nrm.p);
     count_launch();
     k_norm<<<B, 512, 0, st>>>(ws->bt.p, p->d_inst.p, ws->active.p, ws->beta.p);
     count_launch();
-    k_linf<<<B, 512, 0, st>>>(ws->r.p, p->d_inst.p, ws->est.p);
+    k_linf<<<B, 512, 0, st>>>(rfin, p->d_inst.p, ws->est.p);
     count_launch();
     std::vector<double> hn(B), hb(B), hl(B);
     RTE_CHECK_CUDA(cudaMemcpyAsync(hn.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));

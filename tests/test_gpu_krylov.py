@@ -139,6 +139,46 @@ def test_mixed_precision_meets_fp64_accuracy():
         assert rel(split(phi, gp.offsets)[b], ref) < 1e-7
 
 
+def test_mixed_inner_restarts_keep_their_right_hand_side():
+    """Mixed mode with a short restart: every inner solve restarts several times; the inner
+    right-hand side (the FP64 outer residual) must survive those restarts, so the refinement
+    converges without falling back to FP64 and matches the FP64 oracle."""
+    B = lib()
+    spec = spec2d([24, 40], [24, 40], n_polar=4, n_azim=8)
+    ss, sa = wl.draw_params(spec, 2, 31)
+    ss = np.minimum(ss, 30.0)
+    gp = B.Problem(spec, ss, sa)
+    ops = oracle_problems(spec, ss, sa)
+    phi, stats = _solve_gpu(B, gp, None, restart=4, rtol=1e-8, max_iter=3000, mode=B.RTE_MODE_MIXED,
+                            inner_rtol=1e-2, max_outer=30)
+    for b, op in enumerate(ops):
+        ref, _ = ORS.solve(op, None, restart=200, rtol=1e-13, max_iter=3000)
+        assert stats[b]["status"] == 0
+        assert stats[b]["escalated"] == 0
+        assert stats[b]["restarts"] >= stats[b]["outer"] >= 2
+        assert stats[b]["true_rel_residual"] <= 1e-8
+        assert rel(split(phi, gp.offsets)[b], ref) < 1e-7
+
+
+def test_mixed_escalates_to_fp64_after_max_outer():
+    """max_outer = 1: one FP32 refinement step, then FP64 FGMRES from the refined iterate
+    finishes the solve to the FP64 target."""
+    B = lib()
+    spec = spec2d([16, 24], [16, 24], n_polar=4, n_azim=8)
+    ss, sa = wl.draw_params(spec, 2, 37)
+    ss = np.minimum(ss, 100.0)
+    gp = B.Problem(spec, ss, sa)
+    ops = oracle_problems(spec, ss, sa)
+    phi, stats = _solve_gpu(B, gp, None, restart=40, rtol=1e-11, max_iter=3000, mode=B.RTE_MODE_MIXED,
+                            inner_rtol=1e-2, max_outer=1)
+    for b, op in enumerate(ops):
+        ref, _ = ORS.solve(op, None, restart=200, rtol=1e-13, max_iter=3000)
+        assert stats[b]["status"] == 0
+        assert stats[b]["escalated"] == 1 and stats[b]["outer"] == 1
+        assert stats[b]["true_rel_residual"] <= 2e-11
+        assert rel(split(phi, gp.offsets)[b], ref) < 1e-8
+
+
 def test_host_output_pointer_and_not_converged_status():
     torch = torch_cuda()
     B = lib()
