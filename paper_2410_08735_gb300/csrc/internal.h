@@ -132,6 +132,7 @@ struct rte_problem {
   rte::DevBuf<double> d_sig_s, d_sig_t;       // [B][R]
   rte::DevBuf<float> d_sig_s32;               // [B][R]
   rte::DevBuf<double> d_sig_dof;              // [ntot] sigma_s of every dof (ROM projections)
+  rte::DevBuf<float> d_sig_dof32;             // the same in FP32
   rte::DevBuf<double> d_G;                    // [ntot] source moments
   rte::DevBuf<double> d_linv64;               // [B][nu][R][nd*nd]
   rte::DevBuf<float> d_linv32;
@@ -171,8 +172,8 @@ int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void*
                    bool scale_sigma_s = false, bool unique_layout = false);
 // task lists and partial buffer for both precisions (stable pointers for graph capture)
 int prepare_sweeps(rte_problem* p);
-// sweep part of A~ z (per-task partial fluxes in p->d_partial; FP64 input z)
-int launch_op_partials(rte_problem* p, bool f64, const void* z, const int* d_active, cudaStream_t st);
+// sweep part of A~ z (per-task partial fluxes in p->d_partial); z is double if in_f64, else float
+int launch_op_partials(rte_problem* p, bool f64, const void* z, bool in_f64, const int* d_active, cudaStream_t st);
 // A~ z with caller-provided task list and partial storage (no allocation)
 int launch_op_external(rte_problem* p, bool f64, const void* z, void* w, const SweepTask* tasks, int ntasks,
                        int tasks_per_inst, int D, void* partial, cudaStream_t st);

@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <unordered_map>
 
 #include <cooperative_groups.h>
@@ -50,14 +51,16 @@ __device__ double block_sum(double v, double* sh) {
   return sh[32];
 }
 
-__global__ void k_norm(const double* x, const InstInfo* inst, const int* active, double* out) {
+// Norms accumulate in FP64 whatever the vector type (one launch per restart, not per iteration).
+template <typename TV>
+__global__ void k_norm(const TV* x, const InstInfo* inst, const int* active, double* out) {
   __shared__ double sh[33];
   const int b = blockIdx.x;
   if (active && !active[b]) return;
   const InstInfo in = inst[b];
   double s = 0.0;
   for (int i = threadIdx.x; i < in.ndof; i += blockDim.x) {
-    double v = x[in.off + i];
+    double v = (double)x[in.off + i];
     s += v * v;
   }
   s = block_sum(s, sh);
@@ -81,69 +84,88 @@ __global__ void k_linf(const double* x, const InstInfo* inst, double* out) {
 }
 
 // dst = src * (1/scale_b) on active instances; grid (chunks, B)
-__global__ void k_scale(double* dst, const double* src, const double* scale, const InstInfo* inst,
-                        const int* active) {
+template <typename TV>
+__global__ void k_scale(TV* dst, const TV* src, const double* scale, const InstInfo* inst, const int* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const InstInfo in = inst[b];
-  const double s = 1.0 / scale[b];
+  const TV s = (TV)(1.0 / scale[b]);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x)
     dst[in.off + i] = src[in.off + i] * s;
 }
 
-__global__ void k_copy_active(double* dst, const double* src, const InstInfo* inst, const int* active) {
+// dst = src (with conversion) on active instances
+template <typename TD, typename TS>
+__global__ void k_copy_active(TD* dst, const TS* src, const InstInfo* inst, const int* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const InstInfo in = inst[b];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x)
-    dst[in.off + i] = src[in.off + i];
+    dst[in.off + i] = (TD)src[in.off + i];
 }
 
 // ------------------------------------------------------------------------------------------------
-// Modified Gram-Schmidt in compact-WY form.  The MGS recurrence h_i = v_i.w^(i-1),
+// Modified Gram-Schmidt in inverse compact-WY form.  The MGS recurrence h_i = v_i.w^(i-1),
 // w^(i) = w^(i-1) - h_i v_i gives h_i = v_i.w - sum_{k<i} (v_i.v_k) h_k, i.e. (I + L) h = V^T w with L
 // the strictly lower part of the Gram matrix V^T V, and w^(j) = w - V h.  The same coefficients are
-// therefore obtained from one pass of dot products (V^T w, plus the new Gram row v_j . V), a (j+1)-long
-// triangular solve and one update pass, instead of j+1 dependent reductions (Swirydowicz, Langou,
-// Ananthan, Yang, Thomas, Numer. Linear Algebra Appl. 2020).  Rounding differs from the sequential
-// loop; the projector is the MGS projector.
+// therefore obtained from one pass of dot products (V^T w, plus the new Gram row v_j . V) and one
+// update pass instead of j+1 dependent reductions (Swirydowicz, Langou, Ananthan, Yang, Thomas,
+// Numer. Linear Algebra Appl. 2020).  The triangular system is solved with T = (I + L)^{-1}, kept per
+// instance and grown by one row per iteration: with l the new Gram row, T's new row is -l^T T and
+// h = T a.  Both products are spread over the threads of a block, so no step of the iteration is a
+// j-long serial chain of dependent arithmetic.  Rounding differs from the sequential loop; the
+// projector is the MGS projector.
 //
 // Fused iteration kernels.  One Arnoldi iteration of one or many instances is three launches: the
 // ROMSAD preconditioner (k_precond_coop), the sweep (sweep.cu, per-task partial fluxes), and the
-// Arnoldi step (k_arnoldi_coop: reduction of the partials into w = A~ z, compact-WY MGS, Givens,
+// Arnoldi step (k_arnoldi_coop: reduction of the partials into w = A~ z, MGS, Givens,
 // normalisation).  The two fused kernels are cooperative launches: phases over vector chunks ("items",
 // 256 dofs of one instance) and phases over instances are separated by grid-wide barriers, so the
-// per-instance reductions need no extra launches.  Partial sums are always combined in chunk order.
+// per-instance reductions need no extra launches.  Partial sums are always combined in a fixed order.
+//
+// Both kernels are templated on the vector type TV.  FP64 solves run them in double; the inner solves
+// of the mixed-precision refinement run them in float (Krylov basis, MGS, Givens, ROM products), which
+// on this GPU's 1:64 FP64:FP32 throughput ratio removes FP64 arithmetic from the iteration.
 struct RomInstDev {
   const double* P;
   const double* W;
   const float* P32;
   const float* W32;
   const double* inv;   // (U^T A_mu U)^{-1}, r x r row-major
+  const float* inv32;  // the same, rounded to FP32
   int r, rmax, has;
 };
 
-__device__ __forceinline__ double block_sum256(double v, double* sh) {
-  // 256 threads; result valid in thread 0
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+template <typename TV>
+struct RomSel;
+template <>
+struct RomSel<double> {
+  __device__ static const double* P(const RomInstDev& R) { return R.P; }
+  __device__ static const double* W(const RomInstDev& R) { return R.W; }
+  __device__ static const double* inv(const RomInstDev& R) { return R.inv; }
+};
+template <>
+struct RomSel<float> {
+  __device__ static const float* P(const RomInstDev& R) { return R.P32; }
+  __device__ static const float* W(const RomInstDev& R) { return R.W32; }
+  __device__ static const float* inv(const RomInstDev& R) { return R.inv32; }
+};
+
+template <typename TV>
+__device__ __forceinline__ TV warp_sum_t(TV v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) sh[warp] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int w = 0; w < 8; ++w) t += sh[w];
-  return t;
+  return v;
 }
 
+// z = M_ROM^{-1} v = v + W (U^T A_mu U)^{-1} P^T Sigma_s v for instances with a ROM, z = v otherwise.
+template <typename TV>
 __global__ void __launch_bounds__(256) k_precond_coop(int B, const int2* items, int nitems, const InstInfo* inst,
-                                                      const int* active, const RomInstDev* ri, const double* sig_dof,
-                                                      const double* v, double* z, double* rpart, double* rc,
-                                                      int nchunk, int f64) {
+                                                      const int* active, const RomInstDev* ri, const TV* sig_dof,
+                                                      const TV* v, TV* z, TV* rpart, TV* rc, int nchunk) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
-  __shared__ double red[8][64];
-  __shared__ double ys[64];
+  __shared__ TV red[8][64];
+  __shared__ TV ys[64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // phase 1: copy (instances without a ROM) or projection partials P^T Sigma_s v over the chunk
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -157,42 +179,46 @@ __global__ void __launch_bounds__(256) k_precond_coop(int B, const int2* items, 
       if (i < i1) z[in.off + i] = v[in.off + i];
       continue;
     }
-    double acc0 = 0.0, acc1 = 0.0;
+    const TV* Pm = RomSel<TV>::P(R);
+    TV acc0 = 0, acc1 = 0;
     for (int i = i0 + warp; i < i1; i += 8) {
-      const double sv = sig_dof[in.off + i] * v[in.off + i];
-      if (f64) {
-        if (lane < R.r) acc0 += R.P[(size_t)i * R.rmax + lane] * sv;
-        if (lane + 32 < R.r) acc1 += R.P[(size_t)i * R.rmax + lane + 32] * sv;
-      } else {
-        if (lane < R.r) acc0 += (double)R.P32[(size_t)i * R.rmax + lane] * sv;
-        if (lane + 32 < R.r) acc1 += (double)R.P32[(size_t)i * R.rmax + lane + 32] * sv;
-      }
+      const TV sv = sig_dof[in.off + i] * v[in.off + i];
+      const TV* row = Pm + (size_t)i * R.rmax;
+      if (lane < R.r) acc0 += row[lane] * sv;
+      if (lane + 32 < R.r) acc1 += row[lane + 32] * sv;
     }
     red[warp][lane] = acc0;
     red[warp][lane + 32] = acc1;
     __syncthreads();
     if (threadIdx.x < 64) {
-      double s = 0.0;
+      TV s = 0;
       for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
       rpart[((size_t)b * nchunk + ch) * 64 + threadIdx.x] = s;
     }
     __syncthreads();
   }
   grid.sync();
-  // phase 2: c = (U^T A_mu U)^{-1} (sum of the partials) per instance
+  // phase 2: c = (U^T A_mu U)^{-1} (sum of the partials) per instance; warp w sums chunks w, w+8, ...
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
     if (!active[b] || !ri[b].has) continue;
     const RomInstDev R = ri[b];
     const int nch = (inst[b].ndof + 255) / 256;
+    for (int q = lane; q < 64; q += 32) {
+      TV s = 0;
+      if (q < R.r)
+        for (int c = warp; c < nch; c += 8) s += rpart[((size_t)b * nchunk + c) * 64 + q];
+      red[warp][q] = s;
+    }
+    __syncthreads();
     if (threadIdx.x < R.r) {
-      double s = 0.0;
-      for (int c = 0; c < nch; ++c) s += rpart[((size_t)b * nchunk + c) * 64 + threadIdx.x];
+      TV s = 0;
+      for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
       ys[threadIdx.x] = s;
     }
     __syncthreads();
     if (threadIdx.x < R.r) {
-      const double* row = R.inv + (size_t)threadIdx.x * R.r;
-      double s = 0.0;
+      const TV* row = RomSel<TV>::inv(R) + (size_t)threadIdx.x * R.r;
+      TV s = 0;
       for (int q = 0; q < R.r; ++q) s += row[q] * ys[q];
       rc[(size_t)b * 64 + threadIdx.x] = s;
     }
@@ -205,38 +231,37 @@ __global__ void __launch_bounds__(256) k_precond_coop(int B, const int2* items, 
     if (!active[b] || !ri[b].has) continue;
     const InstInfo in = inst[b];
     const RomInstDev R = ri[b];
+    __syncthreads();
+    if (threadIdx.x < R.r) ys[threadIdx.x] = rc[(size_t)b * 64 + threadIdx.x];
+    __syncthreads();
     const int i = ch * 256 + threadIdx.x;
     if (i >= in.ndof) continue;
-    const double* c = rc + (size_t)b * 64;
-    double s = 0.0;
-    if (f64) {
-      const double* w = R.W + (size_t)i * R.rmax;
-      for (int q = 0; q < R.r; ++q) s += w[q] * c[q];
-    } else {
-      const float* w = R.W32 + (size_t)i * R.rmax;
-      for (int q = 0; q < R.r; ++q) s += (double)w[q] * c[q];
-    }
+    const TV* w = RomSel<TV>::W(R) + (size_t)i * R.rmax;
+    TV s = 0;
+    for (int q = 0; q < R.r; ++q) s += w[q] * ys[q];
     z[in.off + i] = v[in.off + i] + s;
   }
 }
 
-template <typename TP>
+// One Arnoldi step for every active instance (see the block comment above).  part/npart/Tm hold
+// values of type TV; part is laid out [instance][slot][chunk] so that each slot's chunk partials are
+// contiguous for the per-instance reduction.  TP: type of the sweep's per-task partial fluxes.
+template <typename TP, typename TV>
 __global__ void __launch_bounds__(256) k_arnoldi_coop(
     int B, const int2* items, int nitems, const InstInfo* inst, int* active, const TP* partial, int ntask,
-    const double* z, double* V, long long ntot, int j, int m, int nchunk, double* part, double* npart, double* Lt,
+    const TV* z, TV* V, long long ntot, int j, int m, int nchunk, TV* part, TV* npart, TV* Tm, int ldT,
     double* H, double* Hraw, double* w0, double* cs, double* sn, double* g, int* brk, const double* bnorm,
     const double* rtol_p, int* iters_left, double* est, int* flag, int* kcols, double* hnorm, int* active0) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nslot = 2 * m + 3;
-  __shared__ double red[8][260];
-  __shared__ double sh[8];
-  __shared__ double hs[130], css[128], sns[128];
+  __shared__ TV red[260];
+  __shared__ TV as[130], ls[130], css[128], sns[128], hsv[130];
   // P0: w = z - sum_t partial_t (the A~ z of this iteration) into V[j+1], then the chunk's partial dots
   //     a_k = v_k . w (k <= j), g_k = v_k . v_j (k < j), w . w.  w and v_j are staged in shared memory
   //     and warp q owns k = q, q + 8, ...: its reductions are independent of the other warps'.
-  __shared__ double wsh[256], vjsh[256];
+  __shared__ TV wsh[256], vjsh[256];
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int b = items[it].x, ch = items[it].y;
     if (!active[b]) continue;
@@ -244,100 +269,89 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(
     const int i0 = ch * 256;
     const int i = i0 + threadIdx.x;
     const bool ok = i < in.ndof;
-    double wi = 0.0;
+    TV wi = 0;
     if (ok) {
       const TP* pp = partial + (size_t)ntask * in.off;
       TP s = 0;
       for (int t = 0; t < ntask; ++t) s += pp[(size_t)t * in.ndof + i];
-      wi = z[in.off + i] - (double)s;
+      wi = z[in.off + i] - (TV)s;
       V[(size_t)(j + 1) * ntot + in.off + i] = wi;
     }
     wsh[threadIdx.x] = wi;
-    vjsh[threadIdx.x] = ok ? V[(size_t)j * ntot + in.off + i] : 0.0;
+    vjsh[threadIdx.x] = ok ? V[(size_t)j * ntot + in.off + i] : TV(0);
     __syncthreads();
     const int nvalid = min(256, in.ndof - i0);
     for (int kk = warp; kk <= j; kk += 8) {
-      const double* vk = V + (size_t)kk * ntot + in.off + i0;
-      double a = 0.0, gg = 0.0;
+      const TV* vk = V + (size_t)kk * ntot + in.off + i0;
+      TV a = 0, gg = 0;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int ii = lane + 32 * e;
-        const double x = ii < nvalid ? vk[ii] : 0.0;
+        const TV x = ii < nvalid ? vk[ii] : TV(0);
         a += x * wsh[ii];
         gg += x * vjsh[ii];
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        gg += __shfl_xor_sync(0xffffffffu, gg, o);
-      }
+      a = warp_sum_t(a);
+      gg = warp_sum_t(gg);
       if (lane == 0) {
-        red[0][kk] = a;
-        if (kk < j) red[0][m + 1 + kk] = gg;
+        red[kk] = a;
+        if (kk < j) red[m + 1 + kk] = gg;
       }
     }
     if (warp == 7) {
-      double ww = 0.0;
+      TV ww = 0;
 #pragma unroll
       for (int e = 0; e < 8; ++e) ww += wsh[lane + 32 * e] * wsh[lane + 32 * e];
-      for (int o = 16; o > 0; o >>= 1) ww += __shfl_xor_sync(0xffffffffu, ww, o);
-      if (lane == 0) red[0][2 * m + 2] = ww;
+      ww = warp_sum_t(ww);
+      if (lane == 0) red[2 * m + 2] = ww;
     }
     __syncthreads();
-    double* out = part + ((size_t)b * nchunk + ch) * nslot;
     for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
       const bool used = t <= j || (t >= m + 1 && t < m + 1 + j) || t == 2 * m + 2;
-      if (used) out[t] = red[0][t];
+      if (used) part[((size_t)b * nslot + t) * nchunk + ch] = red[t];
     }
     __syncthreads();
   }
   grid.sync();
-  // P1: per instance: sum the partials (chunk order), Gram row, (I + L) h = a by forward substitution
+  // P1: per instance: sum the chunk partials, grow T = (I + L)^{-1} by the new row, h = T a
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
     if (!active[b]) continue;
     const int nch = (inst[b].ndof + 255) / 256;
-    const double* pb = part + (size_t)b * nchunk * nslot;
-    double* L = Lt + (size_t)b * (m + 1) * (m + 1);
-    double* a = hs;
     for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
       const bool used = t <= j || (t >= m + 1 && t < m + 1 + j) || t == 2 * m + 2;
       if (!used) continue;
-      double acc = 0.0;
-      for (int c = 0; c < nch; ++c) acc += pb[(size_t)c * nslot + t];
-      if (t <= j) a[t] = acc;
-      else if (t < m + 1 + j) L[(size_t)(t - m - 1) * (m + 1) + j] = acc;
-      else w0[b] = sqrt(acc);
+      const TV* pp = part + ((size_t)b * nslot + t) * nchunk;
+      TV s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      int c = 0;
+      for (; c + 4 <= nch; c += 4) {
+        s0 += pp[c];
+        s1 += pp[c + 1];
+        s2 += pp[c + 2];
+        s3 += pp[c + 3];
+      }
+      for (; c < nch; ++c) s0 += pp[c];
+      const TV acc = (s0 + s1) + (s2 + s3);
+      if (t <= j) as[t] = acc;
+      else if (t < m + 1 + j) ls[t - m - 1] = acc;
+      else w0[b] = sqrt((double)acc);
     }
     __syncthreads();
-    if (warp == 0) {
-      double* h = H + ((size_t)b * m + j) * (m + 1);
-      double* hr = Hraw ? Hraw + ((size_t)b * m + j) * (m + 1) : nullptr;
-      double at[5], lr[5];
-      for (int q = 0; q < 5; ++q) {
-        const int t = lane + 32 * q;
-        at[q] = t <= j ? a[t] : 0.0;
-        lr[q] = (t > 0 && t <= j) ? L[t] : 0.0;
-      }
-      for (int i = 0; i <= j; ++i) {
-        double nx[5];
-        for (int q = 0; q < 5; ++q) {
-          const int t = lane + 32 * q;
-          nx[q] = (i + 1 <= j && t > i + 1 && t <= j) ? L[(size_t)(i + 1) * (m + 1) + t] : 0.0;
-        }
-        const int owner = i & 31, qi = i >> 5;
-        double mine = 0.0;
-        for (int q = 0; q < 5; ++q)
-          if (q == qi) mine = at[q];
-        const double hi = __shfl_sync(0xffffffffu, mine, owner);
-        if (lane == 0) {
-          h[i] = hi;
-          if (hr) hr[i] = hi;
-        }
-        for (int q = 0; q < 5; ++q) {
-          const int t = lane + 32 * q;
-          if (t > i && t <= j) at[q] -= lr[q] * hi;
-          lr[q] = nx[q];
-        }
-      }
+    TV* Tb = Tm + (size_t)b * (m + 1) * ldT;
+    // row j of T: T[j][k] = -(l_k + sum_{i=k+1}^{j-1} l_i T[i][k]), k < j (T[i][i] = 1 implicit)
+    for (int k = threadIdx.x; k < j; k += blockDim.x) {
+      TV s = ls[k];
+      for (int i = k + 1; i < j; ++i) s += ls[i] * Tb[(size_t)i * ldT + k];
+      Tb[(size_t)j * ldT + k] = -s;
+    }
+    __syncthreads();
+    double* h = H + ((size_t)b * m + j) * (m + 1);
+    double* hr = Hraw ? Hraw + ((size_t)b * m + j) * (m + 1) : nullptr;
+    for (int t = threadIdx.x; t <= j; t += blockDim.x) {
+      const TV* row = Tb + (size_t)t * ldT;
+      TV s = as[t];
+      for (int k = 0; k < t; ++k) s += row[k] * as[k];
+      h[t] = (double)s;
+      if (hr) hr[t] = (double)s;
     }
     __syncthreads();
   }
@@ -348,18 +362,24 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(
     if (!active[b]) continue;
     const InstInfo in = inst[b];
     const double* h = H + ((size_t)b * m + j) * (m + 1);
-    for (int t = threadIdx.x; t <= j; t += blockDim.x) hs[t] = h[t];
+    for (int t = threadIdx.x; t <= j; t += blockDim.x) hsv[t] = (TV)h[t];
     __syncthreads();
     const int i = ch * 256 + threadIdx.x;
-    double s2 = 0.0;
+    TV s2 = 0;
     if (i < in.ndof) {
-      double wi = V[(size_t)(j + 1) * ntot + in.off + i];
-      for (int kk = 0; kk <= j; ++kk) wi -= hs[kk] * V[(size_t)kk * ntot + in.off + i];
+      TV wi = V[(size_t)(j + 1) * ntot + in.off + i];
+      for (int kk = 0; kk <= j; ++kk) wi -= hsv[kk] * V[(size_t)kk * ntot + in.off + i];
       V[(size_t)(j + 1) * ntot + in.off + i] = wi;
       s2 = wi * wi;
     }
-    const double tot = block_sum256(s2, sh);
-    if (threadIdx.x == 0) npart[(size_t)b * nchunk + ch] = tot;
+    s2 = warp_sum_t(s2);
+    if (lane == 0) red[warp] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      TV tot = 0;
+      for (int w = 0; w < 8; ++w) tot += red[w];
+      npart[(size_t)b * nchunk + ch] = tot;
+    }
     __syncthreads();
   }
   grid.sync();
@@ -373,41 +393,51 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(
     double* c = cs + (size_t)b * m;
     double* s = sn + (size_t)b * m;
     double* gg = g + (size_t)b * (m + 1);
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) hs[i] = h[i];
-    for (int i = threadIdx.x; i < j; i += blockDim.x) { css[i] = c[i]; sns[i] = s[i]; }
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) hsv[i] = (TV)h[i];
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
+      css[i] = (TV)c[i];
+      sns[i] = (TV)s[i];
+    }
+    if (warp == 0) {
+      const int nch = (inst[b].ndof + 255) / 256;
+      TV acc = 0;
+      for (int cc = lane; cc < nch; cc += 32) acc += npart[(size_t)b * nchunk + cc];
+      acc = warp_sum_t(acc);
+      if (lane == 0) red[0] = acc;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-      const int nch = (inst[b].ndof + 255) / 256;
-      double acc = 0.0;
-      for (int cc = 0; cc < nch; ++cc) acc += npart[(size_t)b * nchunk + cc];
-      const double hn = sqrt(acc);
-      hs[j + 1] = hn;
-      if (Hraw) Hraw[((size_t)b * m + j) * (m + 1) + j + 1] = hn;
-      hnorm[b] = hn;
-      const int bk = (hn > 1e-14 * w0[b]) ? 0 : 1;
+      const TV hn = sqrt(red[0]);
+      hsv[j + 1] = hn;
+      if (Hraw) Hraw[((size_t)b * m + j) * (m + 1) + j + 1] = (double)hn;
+      hnorm[b] = (double)hn;
+      const int bk = ((double)hn > 1e-14 * w0[b]) ? 0 : 1;
       brk[b] = bk;
       active0[b] = 1;
       for (int i = 0; i < j; ++i) {
-        const double t = css[i] * hs[i] + sns[i] * hs[i + 1];
-        hs[i + 1] = -sns[i] * hs[i] + css[i] * hs[i + 1];
-        hs[i] = t;
+        const TV t = css[i] * hsv[i] + sns[i] * hsv[i + 1];
+        hsv[i + 1] = -sns[i] * hsv[i] + css[i] * hsv[i + 1];
+        hsv[i] = t;
       }
-      const double den = hypot(hs[j], hs[j + 1]);
-      double cj = 1.0, sj = 0.0;
-      if (den > 0.0) { cj = hs[j] / den; sj = hs[j + 1] / den; }
-      for (int i = 0; i < j; ++i) h[i] = hs[i];
-      c[j] = cj;
-      s[j] = sj;
-      h[j] = den;
+      const TV den = hypot(hsv[j], hsv[j + 1]);
+      TV cj = 1, sj = 0;
+      if (den > TV(0)) {
+        cj = hsv[j] / den;
+        sj = hsv[j + 1] / den;
+      }
+      for (int i = 0; i < j; ++i) h[i] = (double)hsv[i];
+      c[j] = (double)cj;
+      s[j] = (double)sj;
+      h[j] = (double)den;
       h[j + 1] = 0.0;
-      const double gj = gg[j];
-      gg[j + 1] = -sj * gj;
-      gg[j] = cj * gj;
-      const double e = fabs(sj * gj);
+      const TV gj = (TV)gg[j];
+      gg[j + 1] = (double)(-sj * gj);
+      gg[j] = (double)(cj * gj);
+      const double e = fabs((double)(sj * gj));
       est[b] = e;
       kcols[b] = j + 1;
       int f = RUN;
-      if (!isfinite(e) || !isfinite(den)) f = STOP_NUMERIC;
+      if (!isfinite(e) || !isfinite((double)den)) f = STOP_NUMERIC;
       else if (e <= rtol_p[0] * bnorm[b]) f = STOP_CONV;
       else if (bk) f = STOP_BREAK;
       else if (j + 1 == m || iters_left[b] <= 1) f = STOP_RESTART;
@@ -424,66 +454,76 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(
     if (!active0[b] || brk[b]) continue;
     const InstInfo in = inst[b];
     const int i = ch * 256 + threadIdx.x;
-    if (i < in.ndof) V[(size_t)(j + 1) * ntot + in.off + i] *= 1.0 / hnorm[b];
+    if (i < in.ndof) V[(size_t)(j + 1) * ntot + in.off + i] *= (TV)(1.0 / hnorm[b]);
   }
 }
 
 // y = R^{-1} g (R: rotated H, upper triangular k x k), one block per instance with k > 0:
-// column-oriented back substitution, column i of R read by all threads (coalesced).
+// column-oriented back substitution, column i of R read by all threads (coalesced).  Arithmetic in TV.
+template <typename TV>
 __global__ void k_backsolve(const double* H, const double* g, int m, int B, const int* kcols, double* y) {
   const int b = blockIdx.x;
   const int k = kcols[b];
   if (k <= 0) return;
-  __shared__ double rhs[129];
-  __shared__ double yi;
+  __shared__ TV rhs[129];
+  __shared__ TV yi;
   const double* Hb = H + (size_t)b * m * (m + 1);
-  for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = g[(size_t)b * (m + 1) + i];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) rhs[i] = (TV)g[(size_t)b * (m + 1) + i];
   __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
     const double* col = Hb + (size_t)i * (m + 1);
     if (threadIdx.x == 0) {
-      const double d = col[i];
-      yi = d != 0.0 ? rhs[i] / d : 0.0;
-      y[(size_t)b * m + i] = yi;
+      const TV d = (TV)col[i];
+      yi = d != TV(0) ? rhs[i] / d : TV(0);
+      y[(size_t)b * m + i] = (double)yi;
     }
     __syncthreads();
-    const double v = yi;
-    for (int t = threadIdx.x; t < i; t += blockDim.x) rhs[t] -= col[t] * v;
+    const TV v = yi;
+    for (int t = threadIdx.x; t < i; t += blockDim.x) rhs[t] -= (TV)col[t] * v;
     __syncthreads();
   }
 }
 
 // phi += sum_c y_c Z_c for instances with k > 0; grid (chunks, B)
-__global__ void k_update(double* phi, const double* Z, long long ntot, int m, const InstInfo* inst, const int* kcols,
+template <typename TV>
+__global__ void k_update(TV* phi, const TV* Z, long long ntot, int m, const InstInfo* inst, const int* kcols,
                          const double* y) {
   const int b = blockIdx.y;
   const int k = kcols[b];
   if (k <= 0) return;
   const InstInfo in = inst[b];
-  __shared__ double ys[128];
-  for (int q = threadIdx.x; q < k; q += blockDim.x) ys[q] = y[(size_t)b * m + q];
+  __shared__ TV ys[128];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) ys[q] = (TV)y[(size_t)b * m + q];
   __syncthreads();
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) {
-    double s = phi[in.off + i];
+    TV s = phi[in.off + i];
     for (int q = 0; q < k; ++q) s += ys[q] * Z[(size_t)q * ntot + in.off + i];
     phi[in.off + i] = s;
   }
 }
 
-// phi += d (FP64), all instances in mask
-__global__ void k_axpy_active(double* phi, const double* d, const InstInfo* inst, const int* active) {
+// phi += d (FP64 phi), all instances in mask
+template <typename TS>
+__global__ void k_axpy_active(double* phi, const TS* d, const InstInfo* inst, const int* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const InstInfo in = inst[b];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x)
-    phi[in.off + i] += d[in.off + i];
+    phi[in.off + i] += (double)d[in.off + i];
 }
 
-__global__ void k_zero_active(double* x, const InstInfo* inst, const int* active) {
+template <typename TV>
+__global__ void k_zero_active(TV* x, const InstInfo* inst, const int* active) {
   const int b = blockIdx.y;
   if (active && !active[b]) return;
   const InstInfo in = inst[b];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) x[in.off + i] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) x[in.off + i] = TV(0);
+}
+
+// FP32 copy of the ROM inverse operators
+__global__ void k_inv_to_f32(const double* a, float* b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
 }
 
 // ----------------------------------------------------------------- host driver
@@ -492,7 +532,10 @@ struct Ws {
   long long ntot = 0;
   bool withZ = false;
   DevBuf<double> V, Z, H, Hraw, cs, sn, g, y, bt, r, ro, d, phi_in;
-  DevBuf<double> Lt, part, npart, w0, hnorm;   // compact-WY MGS
+  DevBuf<float> V32, Z32, r32, rin32, d32;     // FP32 Krylov basis of the mixed-precision inner solves
+  // MGS scratch, typed double or float by the solve's vector type: T = (I + L)^{-1} [B][m+1][m+1],
+  // chunk partials of the dot products [B][2m+3][nchunk] and of ||w||^2 [B][nchunk]
+  DevBuf<double> Lt, part, npart, w0, hnorm;
   DevBuf<int> active0;
   int nchunk = 0;
   bool cwy_attr = false;
@@ -542,6 +585,11 @@ struct Ws {
     withZ = withZ_ || withZ;
     RTE_TRY(V.alloc((size_t)(m + 1) * ntot));
     if (withZ) RTE_TRY(Z.alloc((size_t)m * ntot));
+    RTE_TRY(V32.alloc((size_t)(m + 1) * ntot));
+    if (withZ) RTE_TRY(Z32.alloc((size_t)m * ntot));
+    RTE_TRY(r32.alloc(ntot));
+    RTE_TRY(rin32.alloc(ntot));
+    RTE_TRY(d32.alloc(ntot));
     RTE_TRY(H.alloc((size_t)B * m * (m + 1)));
     RTE_TRY(Hraw.alloc((size_t)B * m * (m + 1)));
     {
@@ -566,11 +614,15 @@ struct Ws {
       RTE_CHECK_CUDA(cudaGetDevice(&dev));
       RTE_CHECK_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
       const int want = std::max(nitems, B);
-      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_precond_coop, 256, 0));
+      int o1 = 0, o2 = 0;
+      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_precond_coop<double>, 256, 0));
+      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_precond_coop<float>, 256, 0));
+      occ = std::min(o1, o2);
       grid_pre = std::min(want, std::max(1, occ) * nsm);
-      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_coop<double>, 256, 0));
+      RTE_CHECK_CUDA(
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_coop<double, double>, 256, 0));
       grid_post64 = std::min(want, std::max(1, occ) * nsm);
-      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_coop<float>, 256, 0));
+      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_coop<float, float>, 256, 0));
       grid_post32 = std::min(want, std::max(1, occ) * nsm);
     }
     RTE_TRY(part.alloc((size_t)B * nchunk * (2 * m + 3)));
@@ -635,13 +687,36 @@ struct RunStats {
 };
 
 // Restarted FGMRES on A~ x = rhs for the instances with want[b] = 1.  x: initial guess (zero if
-// zero_guess) and result.  f64: sweep arithmetic.  true_check: recompute the residual after
-// convergence (FP64 sweep if f64).  it_base: iterations already done per instance (window count).
-static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess, const std::vector<int>& want,
-                      double rtol, const std::vector<int>& max_it, bool f64, bool true_check,
-                      const std::vector<int>& it_base, RunStats& rs) {
+// zero_guess) and result.  TV: type of rhs, x, the Krylov vectors and the iteration arithmetic, and
+// of the sweeps (double: FP64 solve; float: inner solve of the mixed-precision refinement).
+// true_check: recompute the residual after convergence.  it_base: iterations already done per
+// instance (window count).  max_it: per-instance iteration budget of this run.
+template <typename TV>
+static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, const std::vector<int>& want,
+                        double rtol, const std::vector<int>& max_it, bool true_check, const std::vector<int>& it_base,
+                        RunStats& rs) {
+  constexpr bool f64 = std::is_same<TV, double>::value;
   rte_problem* p = C.p;
   Ws& W = *C.ws;
+  if (C.rec && !f64) {
+    set_error("run_fgmres: the first-cycle record needs an FP64 solve");
+    return RTE_ERR_UNSUPPORTED;
+  }
+  TV* Vb;
+  TV* Zb;
+  TV* rb;
+  const TV* sig_dof;
+  if constexpr (f64) {
+    Vb = W.V.p;
+    Zb = W.Z.p;
+    rb = W.r.p;
+    sig_dof = p->d_sig_dof.p;
+  } else {
+    Vb = W.V32.p;
+    Zb = W.Z32.p;
+    rb = W.r32.p;
+    sig_dof = p->d_sig_dof32.p;
+  }
   const int B = p->B, m = C.m;
   const long long ntot = p->ntot;
   cudaStream_t st = C.st;
@@ -659,12 +734,12 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
   count_launch();
   // r0
   if (zero_guess) {
-    k_copy_active<<<vg, 256, 0, st>>>(W.r.p, rhs, p->d_inst.p, W.active.p);
+    k_copy_active<<<vg, 256, 0, st>>>(rb, rhs, p->d_inst.p, W.active.p);
     count_launch();
     k_zero_active<<<vg, 256, 0, st>>>(x, p->d_inst.p, W.active.p);
     count_launch();
   } else {
-    RTE_TRY(launch_T(p, MODE_RES, f64, x, true, rhs, W.r.p, true, W.active.p, st));
+    RTE_TRY(launch_T(p, MODE_RES, f64, x, f64, rhs, rb, f64, W.active.p, st));
     for (int b = 0; b < B; ++b) rs.sweeps[b] += act[b];
   }
   RTE_CHECK_CUDA(cudaGetLastError());
@@ -672,11 +747,11 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
   RTE_CHECK_CUDA(cudaStreamSynchronize(st));
   for (int b = 0; b < B; ++b)
     if (act[b] && hbn[b] == 0.0) { act[b] = 0; rs.est[b] = 0.0; }
-  double* Zbase = W.withZ ? W.Z.p : W.V.p;
+  TV* Zbase = W.withZ ? Zb : Vb;
   while (true) {
     // beta = ||r||
     RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-    k_norm<<<B, 512, 0, st>>>(W.r.p, p->d_inst.p, W.active.p, W.beta.p);
+    k_norm<<<B, 512, 0, st>>>(rb, p->d_inst.p, W.active.p, W.beta.p);
     count_launch();
     RTE_CHECK_CUDA(cudaMemcpyAsync(hb.data(), W.beta.p, B * 8, cudaMemcpyDeviceToHost, st));
     RTE_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -692,7 +767,7 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
     if (nact == 0) break;
     // v_0 = r / beta, g = beta e_1
     RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-    k_scale<<<vg, 256, 0, st>>>(W.V.p, W.r.p, W.beta.p, p->d_inst.p, W.active.p);
+    k_scale<<<vg, 256, 0, st>>>(Vb, rb, W.beta.p, p->d_inst.p, W.active.p);
     count_launch();
     {
       std::vector<double> g0((size_t)B * (m + 1), 0.0);
@@ -722,40 +797,41 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
       const bool use_rom = W.withZ && (jg <= C.window || C.post == RTE_POST_ROM);
       // One Arnoldi iteration: preconditioner, w = A~ z_j into V[j+1], compact-WY MGS, Givens.
       auto body = [&](cudaStream_t s) -> int {
-        double* vj = W.V.p + (size_t)j * ntot;
-        double* zj = Zbase + (size_t)j * ntot;
+        TV* vj = Vb + (size_t)j * ntot;
+        TV* zj = Zbase + (size_t)j * ntot;
         if (W.withZ) {
           if (use_rom) {
             const int2* it_p = W.items.p;
-            int nit = W.nitems, Bv = B, nch = W.nchunk, f = f64 ? 1 : 0;
+            int nit = W.nitems, Bv = B, nch = W.nchunk;
             const InstInfo* inst_p = p->d_inst.p;
             const int* act_p = W.active.p;
             const RomInstDev* ri_p = W.rominst.p;
-            const double* sd_p = p->d_sig_dof.p;
-            double* rp_p = W.rpart.p;
-            double* rc_p = W.rc.p;
-            void* args[] = {&Bv, &it_p, &nit, &inst_p, &act_p, &ri_p, &sd_p, &vj, &zj, &rp_p, &rc_p, &nch, &f};
-            RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_precond_coop, dim3(W.grid_pre), dim3(256), args,
-                                                       0, s));
+            const TV* sd_p = sig_dof;
+            const TV* v_p = vj;
+            TV* rp_p = reinterpret_cast<TV*>(W.rpart.p);
+            TV* rc_p = reinterpret_cast<TV*>(W.rc.p);
+            void* args[] = {&Bv, &it_p, &nit, &inst_p, &act_p, &ri_p, &sd_p, &v_p, &zj, &rp_p, &rc_p, &nch};
+            RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_precond_coop<TV>, dim3(W.grid_pre), dim3(256),
+                                                       args, 0, s));
             count_launch();
           } else {
             k_copy_active<<<vg, 256, 0, s>>>(zj, vj, p->d_inst.p, W.active.p);
             count_launch();
           }
         }
-        RTE_TRY(launch_op_partials(p, f64, zj, W.active.p, s));
+        RTE_TRY(launch_op_partials(p, f64, zj, f64, W.active.p, s));
         {
-          int Bv = B, nit = W.nitems, ntask = p->tasks_per_inst, jj = j, mm = m, nch = W.nchunk;
+          int Bv = B, nit = W.nitems, ntask = p->tasks_per_inst, jj = j, mm = m, nch = W.nchunk, ldT = m + 1;
           long long nt = ntot;
           const int2* it_p = W.items.p;
           const InstInfo* inst_p = p->d_inst.p;
           int* act_p = W.active.p;
           const void* part_p = p->d_partial.p;
-          const double* z_p = zj;
-          double* V_p = W.V.p;
-          double* dp_p = W.part.p;
-          double* np_p = W.npart.p;
-          double* Lt_p = W.Lt.p;
+          const TV* z_p = zj;
+          TV* V_p = Vb;
+          TV* dp_p = reinterpret_cast<TV*>(W.part.p);
+          TV* np_p = reinterpret_cast<TV*>(W.npart.p);
+          TV* Lt_p = reinterpret_cast<TV*>(W.Lt.p);
           double* H_p = W.H.p;
           double* Hr_p = C.rec ? W.Hraw.p : nullptr;
           double* w0_p = W.w0.p;
@@ -772,14 +848,14 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
           double* hn_p = W.hnorm.p;
           int* a0_p = W.active0.p;
           void* args[] = {&Bv, &it_p, &nit, &inst_p, &act_p, &part_p, &ntask, &z_p, &V_p, &nt, &jj, &mm, &nch,
-                          &dp_p, &np_p, &Lt_p, &H_p, &Hr_p, &w0_p, &cs_p, &sn_p, &g_p, &brk_p, &bn_p, &rt_p,
+                          &dp_p, &np_p, &Lt_p, &ldT, &H_p, &Hr_p, &w0_p, &cs_p, &sn_p, &g_p, &brk_p, &bn_p, &rt_p,
                           &il_p, &est_p, &fl_p, &kc_p, &hn_p, &a0_p};
-          if (f64)
-            RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop<double>, dim3(W.grid_post64),
-                                                       dim3(256), args, 0, s));
+          if constexpr (f64)
+            RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop<double, double>,
+                                                       dim3(W.grid_post64), dim3(256), args, 0, s));
           else
-            RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop<float>, dim3(W.grid_post32),
-                                                       dim3(256), args, 0, s));
+            RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop<float, float>,
+                                                       dim3(W.grid_post32), dim3(256), args, 0, s));
           count_launch();
         }
         RTE_CHECK_CUDA(cudaGetLastError());
@@ -846,7 +922,7 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
       C.rec->done = true;
     }
     // end of cycle: phi += Z y for the instances of this cycle
-    k_backsolve<<<B, 128, 0, st>>>(W.H.p, W.g.p, m, B, W.kcols.p, W.y.p);
+    k_backsolve<TV><<<B, 128, 0, st>>>(W.H.p, W.g.p, m, B, W.kcols.p, W.y.p);
     count_launch();
     k_update<<<vg, 256, 0, st>>>(x, Zbase, ntot, m, p->d_inst.p, W.kcols.p, W.y.p);
     count_launch();
@@ -875,13 +951,13 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
     std::vector<int> mask(B);
     for (int b = 0; b < B; ++b) mask[b] = resid[b] ? 1 : 0;
     RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, mask.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-    RTE_TRY(launch_T(p, MODE_RES, f64, x, true, rhs, W.r.p, true, W.active.p, st));
+    RTE_TRY(launch_T(p, MODE_RES, f64, x, f64, rhs, rb, f64, W.active.p, st));
     for (int b = 0; b < B; ++b)
       if (resid[b] == 2) { rs.sweeps[b] += 1; rs.restarts[b] += 1; }
     for (int b = 0; b < B; ++b) act[b] = mask[b];
     // check-sweep instances: the loop head computes beta and stops them if within 2 rtol
     if (true_check) {
-      k_norm<<<B, 512, 0, st>>>(W.r.p, p->d_inst.p, W.active.p, W.nrm.p);
+      k_norm<<<B, 512, 0, st>>>(rb, p->d_inst.p, W.active.p, W.nrm.p);
       count_launch();
       std::vector<double> hn(B);
       RTE_CHECK_CUDA(cudaMemcpyAsync(hn.data(), W.nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
@@ -898,6 +974,16 @@ static int run_fgmres(SolveCtx& C, const double* rhs, double* x, bool zero_guess
     }
   }
   return RTE_OK;
+}
+
+static int run_fgmres(SolveCtx& C, const void* rhs, void* x, bool zero_guess, const std::vector<int>& want,
+                      double rtol, const std::vector<int>& max_it, bool f64, bool true_check,
+                      const std::vector<int>& it_base, RunStats& rs) {
+  if (f64)
+    return run_fgmres_t<double>(C, static_cast<const double*>(rhs), static_cast<double*>(x), zero_guess, want, rtol,
+                                max_it, true_check, it_base, rs);
+  return run_fgmres_t<float>(C, static_cast<const float*>(rhs), static_cast<float*>(x), zero_guess, want, rtol, max_it,
+                             true_check, it_base, rs);
 }
 
 static Ws* get_ws(rte_problem* p) {
@@ -991,15 +1077,28 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       ws->plan_rom = prom;
       ws->plan_ids = pids;
     }
-    for (size_t q = 0; q < prom.size(); ++q) RTE_TRY(ws->plans[q].build(prom[q], p, pids[q], st));
+    for (size_t q = 0; q < prom.size(); ++q) {
+      RomPlan& pl = ws->plans[q];
+      RTE_TRY(pl.build(prom[q], p, pids[q], st));
+      RTE_TRY(pl.inv32.ensure(pl.lu.n));
+      k_inv_to_f32<<<64, 256, 0, st>>>(pl.lu.p, pl.inv32.p, (long long)pl.lu.n);
+      count_launch();
+    }
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->norom.p, C.no_rom_mask.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
     std::vector<RomInstDev> ri(B);
-    for (int b = 0; b < B; ++b) ri[b] = RomInstDev{nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0};
+    for (int b = 0; b < B; ++b) ri[b] = RomInstDev{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0};
     for (size_t q = 0; q < prom.size(); ++q)
       for (size_t sl = 0; sl < pids[q].size(); ++sl) {
         romsad* rm = prom[q];
-        ri[pids[q][sl]] = RomInstDev{rm->P.p, rm->W.p, rm->P32.p, rm->W32.p, ws->plans[q].lu.p + sl * 64 * 64,
-                                     rm->r, rm->rmax, 1};
+        ri[pids[q][sl]] = RomInstDev{rm->P.p,
+                                     rm->W.p,
+                                     rm->P32.p,
+                                     rm->W32.p,
+                                     ws->plans[q].lu.p + sl * 64 * 64,
+                                     ws->plans[q].inv32.p + sl * 64 * 64,
+                                     rm->r,
+                                     rm->rmax,
+                                     1};
       }
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->rominst.p, ri.data(), B * sizeof(RomInstDev), cudaMemcpyHostToDevice, st));
     RTE_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -1105,13 +1204,16 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
         ++nact;
       }
       if (nact == 0) break;
-      // inner solve A~ d = ro (FP32 sweeps), zero guess
+      // inner solve A~ d = ro entirely in FP32 (right-hand side rounded to FP32), zero guess
       std::vector<int> cap(B, 0);
       for (int b = 0; b < B; ++b) cap[b] = std::min(inner_cap, o->max_iter - S[b].iterations);
-      RunStats rs;
-      RTE_TRY(run_fgmres(C, ro, ws->d.p, true, act, o->inner_rtol, cap, false, false, zero, rs));
       RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-      k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d.p, p->d_inst.p, ws->active.p);
+      k_copy_active<<<vg, 256, 0, st>>>(ws->rin32.p, ro, p->d_inst.p, ws->active.p);
+      count_launch();
+      RunStats rs;
+      RTE_TRY(run_fgmres(C, ws->rin32.p, ws->d32.p, true, act, o->inner_rtol, cap, false, false, zero, rs));
+      RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+      k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d32.p, p->d_inst.p, ws->active.p);
       count_launch();
       // ro = b~ - A~ x in FP64
       RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ro, true, ws->active.p, st));

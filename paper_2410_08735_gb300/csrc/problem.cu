@@ -121,14 +121,17 @@ __global__ void k_linv(int B, int nu, int R, int dim, const InstInfo* inst, cons
 }
 
 // sigma_s of the cell of every dof (instance-major scalar-vector layout)
-__global__ void k_sig_dof(const InstInfo* inst, int B, int R, int rx, int ry, int nd, const double* sig_s, double* out) {
+__global__ void k_sig_dof(const InstInfo* inst, int B, int R, int rx, int ry, int nd, const double* sig_s, double* out,
+                          float* out32) {
   const int b = blockIdx.y;
   const InstInfo in = inst[b];
   const int cx = in.nx / rx, cy = in.ny / ry;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) {
     const int c = i / nd;
     const int ix = c % in.nx, iy = c / in.nx;
-    out[in.off + i] = sig_s[(size_t)b * R + (iy / cy) * rx + ix / cx];
+    const double v = sig_s[(size_t)b * R + (iy / cy) * rx + ix / cx];
+    out[in.off + i] = v;
+    out32[in.off + i] = (float)v;
   }
 }
 
@@ -153,7 +156,8 @@ int upload_params(rte_problem* p) {
     int maxn = 0;
     for (int b = 0; b < p->B; ++b) maxn = std::max(maxn, (int)(p->off[b + 1] - p->off[b]));
     dim3 g((maxn + 255) / 256, p->B);
-    k_sig_dof<<<g, 256>>>(p->d_inst.p, p->B, p->R, p->rx, p->ry, p->nd, p->d_sig_s.p, p->d_sig_dof.p);
+    k_sig_dof<<<g, 256>>>(p->d_inst.p, p->B, p->R, p->rx, p->ry, p->nd, p->d_sig_s.p, p->d_sig_dof.p,
+                            p->d_sig_dof32.p);
     count_launch();
     RTE_CHECK_CUDA(cudaGetLastError());
   }
@@ -319,6 +323,7 @@ static int create_impl(const rte_problem_desc* d, rte_problem* p) {
   RTE_TRY(p->d_sig_s32.alloc(nR));
   RTE_TRY(p->d_G.alloc(p->ntot));
   RTE_TRY(p->d_sig_dof.alloc(p->ntot));
+  RTE_TRY(p->d_sig_dof32.alloc(p->ntot));
   size_t nl = (size_t)p->B * p->nu * p->R * p->nd * p->nd;
   RTE_TRY(p->d_linv64.alloc(nl));
   RTE_TRY(p->d_linv32.alloc(nl));

@@ -955,7 +955,7 @@ int launch_T(rte_problem* p, int mode, bool f64, const void* src, bool in_f64, c
 
 // Sweep part of A~ z only: fills the per-task partial scalar fluxes (Sigma_s scaling fused); the
 // subtraction z - sum_t partial_t is left to the caller's kernel (the fused Arnoldi step).
-int launch_op_partials(rte_problem* p, bool f64, const void* z, const int* d_active, cudaStream_t st) {
+int launch_op_partials(rte_problem* p, bool f64, const void* z, bool in_f64, const int* d_active, cudaStream_t st) {
   int D = pick_D(p, f64);
   RTE_TRY(ensure_tasks(p, D));
   RTE_TRY(ensure_partial(p, f64));
@@ -965,8 +965,13 @@ int launch_op_partials(rte_problem* p, bool f64, const void* z, const int* d_act
   a.sig_s = f64 ? (const void*)p->d_sig_s.p : (const void*)p->d_sig_s32.p;
   a.partial = p->d_partial.p;
   a.active = d_active;
-  if (f64) RTE_TRY((launch_sweep_t<double, double, false>(p, D, a, st)));
-  else RTE_TRY((launch_sweep_t<float, double, false>(p, D, a, st)));
+  if (f64) {
+    if (in_f64) RTE_TRY((launch_sweep_t<double, double, false>(p, D, a, st)));
+    else RTE_TRY((launch_sweep_t<double, float, false>(p, D, a, st)));
+  } else {
+    if (in_f64) RTE_TRY((launch_sweep_t<float, double, false>(p, D, a, st)));
+    else RTE_TRY((launch_sweep_t<float, float, false>(p, D, a, st)));
+  }
   return RTE_OK;
 }
 
