@@ -179,13 +179,33 @@ __global__ void __launch_bounds__(256) k_precond_coop(int B, const int2* items, 
       if (i < i1) z[in.off + i] = v[in.off + i];
       continue;
     }
+    // warp w owns rows i0 + 32 w .. +31: one coalesced load of Sigma_s v for its rows, then the 32
+    // P rows (lane = rank index), all loads independent so that they are in flight together
+    // (row and column indices are clamped into the array and the surplus terms multiplied by zero, so
+    // that every load is unconditional)
     const TV* Pm = RomSel<TV>::P(R);
+    const int ib = i0 + warp * 32;
+    const int nrow = min(32, i1 - ib);
     TV acc0 = 0, acc1 = 0;
-    for (int i = i0 + warp; i < i1; i += 8) {
-      const TV sv = sig_dof[in.off + i] * v[in.off + i];
-      const TV* row = Pm + (size_t)i * R.rmax;
-      if (lane < R.r) acc0 += row[lane] * sv;
-      if (lane + 32 < R.r) acc1 += row[lane + 32] * sv;
+    if (nrow > 0) {
+      const TV svl = lane < nrow ? sig_dof[in.off + ib + lane] * v[in.off + ib + lane] : TV(0);
+      const TV m0 = lane < R.r ? TV(1) : TV(0);
+      const TV m1 = lane + 32 < R.r ? TV(1) : TV(0);
+      const int c0 = min(lane, R.rmax - 1), c1 = min(lane + 32, R.rmax - 1);
+#pragma unroll
+      for (int k = 0; k < 32; ++k) {
+        const TV sv = __shfl_sync(0xffffffffu, svl, k);
+        const TV* row = Pm + (size_t)(ib + min(k, nrow - 1)) * R.rmax;
+        acc0 += row[c0] * (sv * m0);
+      }
+      if (R.r > 32) {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const TV sv = __shfl_sync(0xffffffffu, svl, k);
+          const TV* row = Pm + (size_t)(ib + min(k, nrow - 1)) * R.rmax;
+          acc1 += row[c1] * (sv * m1);
+        }
+      }
     }
     red[warp][lane] = acc0;
     red[warp][lane + 32] = acc1;
@@ -205,21 +225,28 @@ __global__ void __launch_bounds__(256) k_precond_coop(int B, const int2* items, 
     const int nch = (inst[b].ndof + 255) / 256;
     for (int q = lane; q < 64; q += 32) {
       TV s = 0;
-      if (q < R.r)
+      if (q < R.r) {
+#pragma unroll 8
         for (int c = warp; c < nch; c += 8) s += rpart[((size_t)b * nchunk + c) * 64 + q];
+      }
       red[warp][q] = s;
     }
     __syncthreads();
-    if (threadIdx.x < R.r) {
+    if (threadIdx.x < 64) {
       TV s = 0;
       for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
-      ys[threadIdx.x] = s;
+      ys[threadIdx.x] = threadIdx.x < R.r ? s : TV(0);
     }
     __syncthreads();
     if (threadIdx.x < R.r) {
       const TV* row = RomSel<TV>::inv(R) + (size_t)threadIdx.x * R.r;
       TV s = 0;
-      for (int q = 0; q < R.r; ++q) s += row[q] * ys[q];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) s += row[min(q, R.r - 1)] * ys[q];
+      if (R.r > 32) {
+#pragma unroll
+        for (int q = 32; q < 64; ++q) s += row[min(q, R.r - 1)] * ys[q];
+      }
       rc[(size_t)b * 64 + threadIdx.x] = s;
     }
     __syncthreads();
@@ -232,22 +259,401 @@ __global__ void __launch_bounds__(256) k_precond_coop(int B, const int2* items, 
     const InstInfo in = inst[b];
     const RomInstDev R = ri[b];
     __syncthreads();
-    if (threadIdx.x < R.r) ys[threadIdx.x] = rc[(size_t)b * 64 + threadIdx.x];
+    if (threadIdx.x < 64) ys[threadIdx.x] = threadIdx.x < R.r ? rc[(size_t)b * 64 + threadIdx.x] : TV(0);
     __syncthreads();
     const int i = ch * 256 + threadIdx.x;
     if (i >= in.ndof) continue;
     const TV* w = RomSel<TV>::W(R) + (size_t)i * R.rmax;
+    const int cl = R.rmax - 1;
     TV s = 0;
-    for (int q = 0; q < R.r; ++q) s += w[q] * ys[q];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) s += w[min(q, cl)] * ys[q];
+    if (R.r > 32) {
+#pragma unroll
+      for (int q = 32; q < 64; ++q) s += w[min(q, cl)] * ys[q];
+    }
     z[in.off + i] = v[in.off + i] + s;
   }
 }
 
-// One Arnoldi step for every active instance (see the block comment above).  part/npart/Tm hold
-// values of type TV; part is laid out [instance][slot][chunk] so that each slot's chunk partials are
-// contiguous for the per-instance reduction.  TP: type of the sweep's per-task partial fluxes.
+// Arguments of one fused Arnoldi step (k_arnoldi_coop).
 template <typename TP, typename TV>
-__global__ void __launch_bounds__(256) k_arnoldi_coop(
+struct ArnArgs {
+  int B, nitems, ntask, j, m, nchunk, ldT, rom_next;
+  long long ntot;
+  const int2* items;
+  const InstInfo* inst;
+  int* active;          // device mask; cleared here for instances that stop
+  int* active0;         // snapshot of active taken in phase B, read in phase C
+  const TP* partial;    // per-task partial fluxes of the sweep of z_j
+  const TV* z;          // z_j
+  TV* V;                // Krylov basis; v_{j+1} is written here
+  TV* znext;            // z_{j+1} = M_{j+1}^{-1} v_{j+1} (null: not needed)
+  TV* part;             // [B][2m+3][nchunk] chunk partials of the dot products
+  TV* npart;            // [B][nchunk] chunk partials of ||w||^2
+  TV* Tm;               // [B][m+1][ldT] T = (I + L)^{-1}
+  TV* rpart;            // [B][nchunk][64] chunk partials of P^T Sigma_s w
+  const RomInstDev* ri;
+  const TV* sig_dof;
+  double* H;            // [B][m][m+1] column j: rotated Hessenberg column
+  double* Hraw;         // unrotated copy (first-cycle record) or null
+  double* w0;           // [B] ||w|| before orthogonalisation
+  double* cs;
+  double* sn;
+  double* g;
+  double* est;
+  const double* bnorm;
+  const double* rtol;
+  int* iters_left;
+  int* flag;
+  int* kcols;
+};
+
+// One Arnoldi iteration for every active instance, three phases over vector chunks ("items": 256
+// dofs of one instance) separated by two grid-wide barriers:
+//   A  w = z_j - sum_t partial_t (= A~ z_j) into V[j+1]; chunk partials of v_k . w (k <= j),
+//      v_k . v_j (k < j) and w . w.
+//   B  every block of an instance sums the partials of that instance itself (the same fixed order in
+//      every block, so all blocks hold identical values) and forms h = T a: h_i = (T a)_i for i < j
+//      from the stored rows of T, h_j = a_j - sum_{i<j} l_i h_i.  Then w -= V h on its chunk, the
+//      chunk partial of ||w||^2 and, when the next iteration applies the ROM, of P^T Sigma_s w.  The
+//      block of chunk 0 stores column j of H and the new row of T (-l^T T).
+//   C  every block sums the ||w||^2 partials (h_{j+1,j}) and the projection partials, normalises its
+//      chunk of v_{j+1} and writes z_{j+1} = v_{j+1} + W (U^T A_mu U)^{-1} P^T Sigma_s v_{j+1} (or
+//      v_{j+1}); the block of chunk 0 applies the Givens rotations and sets the stopping flags.
+// The per-instance reductions are repeated by each block of the instance instead of being done once
+// behind an extra barrier: on a latency-bound problem a barrier costs more than the repeated sums.
+template <typename TP, typename TV>
+__global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
+  namespace cg = cooperative_groups;
+  cg::grid_group grid = cg::this_grid();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = A.j, m = A.m, nslot = 2 * m + 3;
+  const long long ntot = A.ntot;
+  __shared__ TV sl[260];          // chunk dot products (phase A) / instance sums (phase B)
+  __shared__ TV hsv[132];
+  __shared__ TV wsh[256], vjsh[256];
+  __shared__ TV red[8][128];
+  __shared__ TV ys[64];
+  __shared__ TV css[128], sns[128];
+  __shared__ TV hsc;
+  auto used = [&](int t) { return t <= j || (t >= m + 1 && t < m + 1 + j) || t == 2 * m + 2; };
+  // ---------------------------------------------------------------- phase A
+  for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
+    const int b = A.items[it].x, ch = A.items[it].y;
+    if (!A.active[b]) continue;
+    const InstInfo in = A.inst[b];
+    const int i0 = ch * 256;
+    const int i = i0 + threadIdx.x;
+    const bool ok = i < in.ndof;
+    TV wi = 0;
+    if (ok) {
+      const TP* pp = A.partial + (size_t)A.ntask * in.off;
+      TP s = 0;
+#pragma unroll 8
+      for (int t = 0; t < A.ntask; ++t) s += pp[(size_t)t * in.ndof + i];
+      wi = A.z[in.off + i] - (TV)s;
+      A.V[(size_t)(j + 1) * ntot + in.off + i] = wi;
+    }
+    wsh[threadIdx.x] = wi;
+    vjsh[threadIdx.x] = ok ? A.V[(size_t)j * ntot + in.off + i] : TV(0);
+    __syncthreads();
+    const int nvalid = min(256, in.ndof - i0);
+    // warp q owns k = q, q + 8, ...: its reductions are independent of the other warps'
+#pragma unroll 4
+    for (int kk = warp; kk <= j; kk += 8) {
+      const TV* vk = A.V + (size_t)kk * ntot + in.off + i0;
+      TV a = 0, gg = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int ii = lane + 32 * e;
+        const TV x = vk[min(ii, nvalid - 1)];   // surplus lanes meet zeros in wsh / vjsh
+        a += x * wsh[ii];
+        gg += x * vjsh[ii];
+      }
+      a = warp_sum_t(a);
+      gg = warp_sum_t(gg);
+      if (lane == 0) {
+        sl[kk] = a;
+        if (kk < j) sl[m + 1 + kk] = gg;
+      }
+    }
+    if (warp == 7) {
+      TV ww = 0;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) ww += wsh[lane + 32 * e] * wsh[lane + 32 * e];
+      ww = warp_sum_t(ww);
+      if (lane == 0) sl[2 * m + 2] = ww;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nslot; t += blockDim.x)
+      if (used(t)) A.part[((size_t)b * nslot + t) * A.nchunk + ch] = sl[t];
+    __syncthreads();
+  }
+  grid.sync();
+  // ---------------------------------------------------------------- phase B
+  for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
+    const int b = A.items[it].x, ch = A.items[it].y;
+    if (!A.active[b]) {
+      if (ch == 0 && threadIdx.x == 0) A.active0[b] = 0;
+      continue;
+    }
+    const InstInfo in = A.inst[b];
+    const int nch = (in.ndof + 255) / 256;
+    // instance sums of the chunk partials, one slot per thread, chunks in order
+    for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
+      if (!used(t)) continue;
+      const TV* pp = A.part + ((size_t)b * nslot + t) * A.nchunk;
+      TV acc = 0;
+#pragma unroll 32
+      for (int c = 0; c < nch; ++c) acc += pp[c];
+      sl[t] = acc;
+    }
+    __syncthreads();
+    const TV* Tb = A.Tm + (size_t)b * (m + 1) * A.ldT;
+    // h_i = a_i + sum_{k<i} T[i][k] a_k for i < j (warp per row, lanes over k)
+#pragma unroll 4
+    for (int r = warp; r < j; r += 8) {
+      const TV* row = Tb + (size_t)r * A.ldT;
+      TV s = 0;
+      for (int k = lane; k < r; k += 32) s += row[k] * sl[k];
+      s = warp_sum_t(s);
+      if (lane == 0) hsv[r] = sl[r] + s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      TV s = 0;
+      for (int r = lane; r < j; r += 32) s += sl[m + 1 + r] * hsv[r];
+      s = warp_sum_t(s);
+      if (lane == 0) hsv[j] = sl[j] - s;
+    }
+    __syncthreads();
+    if (ch == 0) {
+      double* h = A.H + ((size_t)b * m + j) * (m + 1);
+      double* hr = A.Hraw ? A.Hraw + ((size_t)b * m + j) * (m + 1) : nullptr;
+      for (int t = threadIdx.x; t <= j; t += blockDim.x) {
+        h[t] = (double)hsv[t];
+        if (hr) hr[t] = (double)hsv[t];
+      }
+      if (threadIdx.x == 0) {
+        A.w0[b] = sqrt((double)sl[2 * m + 2]);
+        A.active0[b] = 1;
+      }
+      // new row of T: T[j][k] = -(l_k + sum_{i=k+1}^{j-1} l_i T[i][k]), k < j.  Warp w accumulates
+      // rows i = w, w+8, ... for the columns k = lane + 32 q; the warps' sums are combined in order.
+      TV acc[4] = {0, 0, 0, 0};
+#pragma unroll 2
+      for (int r = warp; r < j; r += 8) {
+        const TV* row = Tb + (size_t)r * A.ldT;
+        const TV lr = sl[m + 1 + r];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int k = lane + 32 * q;
+          if (k < r) acc[q] += lr * row[k];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) red[warp][lane + 32 * q] = acc[q];
+      __syncthreads();
+      for (int k = threadIdx.x; k < j; k += blockDim.x) {
+        TV s = sl[m + 1 + k];
+        for (int w = 0; w < 8; ++w) s += red[w][k];
+        A.Tm[(size_t)b * (m + 1) * A.ldT + (size_t)j * A.ldT + k] = -s;
+      }
+      __syncthreads();
+    }
+    // w -= V h on this chunk, ||w||^2 partial
+    const int i = ch * 256 + threadIdx.x;
+    const bool ok = i < in.ndof;
+    TV wi = 0;
+    if (ok) {
+      wi = A.V[(size_t)(j + 1) * ntot + in.off + i];
+      constexpr int U = sizeof(TV) == 4 ? 32 : 8;
+#pragma unroll(U)
+      for (int kk = 0; kk <= j; ++kk) wi -= hsv[kk] * A.V[(size_t)kk * ntot + in.off + i];
+      A.V[(size_t)(j + 1) * ntot + in.off + i] = wi;
+    }
+    TV s2 = warp_sum_t(wi * wi);
+    if (lane == 0) red[warp][0] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      TV tot = 0;
+      for (int w = 0; w < 8; ++w) tot += red[w][0];
+      A.npart[(size_t)b * A.nchunk + ch] = tot;
+    }
+    // projection partials P^T Sigma_s w for the next preconditioner apply
+    const RomInstDev R = A.ri[b];
+    if (A.rom_next && A.znext && R.has) {
+      wsh[threadIdx.x] = ok ? A.sig_dof[in.off + i] * wi : TV(0);
+      __syncthreads();
+      const TV* Pm = RomSel<TV>::P(R);
+      const int ib = warp * 32;                       // chunk-local first row of this warp
+      const int nrow = min(32, in.ndof - ch * 256 - ib);
+      TV acc0 = 0, acc1 = 0;
+      if (nrow > 0) {
+        const TV svl = wsh[ib + lane];
+        const TV m0 = lane < R.r ? TV(1) : TV(0);
+        const TV m1 = lane + 32 < R.r ? TV(1) : TV(0);
+        const int c0 = min(lane, R.rmax - 1), c1 = min(lane + 32, R.rmax - 1);
+        const size_t rb = (size_t)(ch * 256 + ib);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const TV sv = __shfl_sync(0xffffffffu, svl, k);
+          acc0 += Pm[(rb + min(k, nrow - 1)) * R.rmax + c0] * (sv * m0);
+        }
+        if (R.r > 32) {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const TV sv = __shfl_sync(0xffffffffu, svl, k);
+            acc1 += Pm[(rb + min(k, nrow - 1)) * R.rmax + c1] * (sv * m1);
+          }
+        }
+      }
+      __syncthreads();
+      red[warp][lane] = acc0;
+      red[warp][lane + 32] = acc1;
+      __syncthreads();
+      if (threadIdx.x < 64) {
+        TV s = 0;
+        for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+        A.rpart[((size_t)b * A.nchunk + ch) * 64 + threadIdx.x] = s;
+      }
+    }
+    __syncthreads();
+  }
+  grid.sync();
+  // ---------------------------------------------------------------- phase C
+  for (int it = blockIdx.x; it < A.nitems; it += gridDim.x) {
+    const int b = A.items[it].x, ch = A.items[it].y;
+    if (!A.active0[b]) continue;
+    const InstInfo in = A.inst[b];
+    const int nch = (in.ndof + 255) / 256;
+    const RomInstDev R = A.ri[b];
+    const bool lift = A.znext && A.rom_next && R.has;
+    if (warp == 0) {
+      TV acc = 0;
+      for (int c = lane; c < nch; c += 32) acc += A.npart[(size_t)b * A.nchunk + c];
+      acc = warp_sum_t(acc);
+      if (lane == 0) hsc = sqrt(acc);
+    }
+    if (lift) {
+      // c = (U^T A_mu U)^{-1} P^T Sigma_s w / h_{j+1,j}; warp w sums chunks w, w+8, ...
+      for (int q = lane; q < 64; q += 32) {
+        TV s = 0;
+        if (q < R.r) {
+#pragma unroll 8
+          for (int c = warp; c < nch; c += 8) s += A.rpart[((size_t)b * A.nchunk + c) * 64 + q];
+        }
+        red[warp][q] = s;
+      }
+    }
+    __syncthreads();
+    const TV hn = hsc;
+    const bool bk = !((double)hn > 1e-14 * A.w0[b]);
+    const TV inv_h = bk ? TV(0) : TV(1) / hn;
+    if (lift) {
+      if (threadIdx.x < 64) {
+        TV s = 0;
+        for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+        wsh[threadIdx.x] = threadIdx.x < R.r ? s * inv_h : TV(0);
+      }
+      __syncthreads();
+      if (threadIdx.x < R.r) {
+        const TV* row = RomSel<TV>::inv(R) + (size_t)threadIdx.x * R.r;
+        TV s = 0;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) s += row[min(q, R.r - 1)] * wsh[q];
+        if (R.r > 32) {
+#pragma unroll
+          for (int q = 32; q < 64; ++q) s += row[min(q, R.r - 1)] * wsh[q];
+        }
+        ys[threadIdx.x] = s;
+      } else if (threadIdx.x < 64) {
+        ys[threadIdx.x] = TV(0);
+      }
+      __syncthreads();
+    }
+    // v_{j+1} = w / h_{j+1,j} and z_{j+1} on this chunk
+    const int i = ch * 256 + threadIdx.x;
+    if (!bk && i < in.ndof) {
+      const size_t o = (size_t)(j + 1) * ntot + in.off + i;
+      const TV v = A.V[o] * inv_h;
+      A.V[o] = v;
+      if (A.znext) {
+        TV zv = v;
+        if (lift) {
+          const TV* w = RomSel<TV>::W(R) + (size_t)i * R.rmax;
+          const int cl = R.rmax - 1;
+          TV s = 0;
+#pragma unroll
+          for (int q = 0; q < 32; ++q) s += w[min(q, cl)] * ys[q];
+          if (R.r > 32) {
+#pragma unroll
+            for (int q = 32; q < 64; ++q) s += w[min(q, cl)] * ys[q];
+          }
+          zv += s;
+        }
+        A.znext[in.off + i] = zv;
+      }
+    }
+    if (ch == 0) {
+      // h_{j+1,j}, Givens rotation of column j, stopping flags (one thread)
+      double* h = A.H + ((size_t)b * m + j) * (m + 1);
+      double* c = A.cs + (size_t)b * m;
+      double* s = A.sn + (size_t)b * m;
+      double* gg = A.g + (size_t)b * (m + 1);
+      for (int t = threadIdx.x; t <= j; t += blockDim.x) hsv[t] = (TV)h[t];
+      for (int t = threadIdx.x; t < j; t += blockDim.x) {
+        css[t] = (TV)c[t];
+        sns[t] = (TV)s[t];
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        hsv[j + 1] = hn;
+        if (A.Hraw) A.Hraw[((size_t)b * m + j) * (m + 1) + j + 1] = (double)hn;
+        for (int t = 0; t < j; ++t) {
+          const TV x = css[t] * hsv[t] + sns[t] * hsv[t + 1];
+          hsv[t + 1] = -sns[t] * hsv[t] + css[t] * hsv[t + 1];
+          hsv[t] = x;
+        }
+        const TV den = hypot(hsv[j], hsv[j + 1]);
+        TV cj = 1, sj = 0;
+        if (den > TV(0)) {
+          cj = hsv[j] / den;
+          sj = hsv[j + 1] / den;
+        }
+        for (int t = 0; t < j; ++t) h[t] = (double)hsv[t];
+        c[j] = (double)cj;
+        s[j] = (double)sj;
+        h[j] = (double)den;
+        h[j + 1] = 0.0;
+        const TV gj = (TV)gg[j];
+        gg[j + 1] = (double)(-sj * gj);
+        gg[j] = (double)(cj * gj);
+        const double e = fabs((double)(sj * gj));
+        A.est[b] = e;
+        A.kcols[b] = j + 1;
+        int f = RUN;
+        if (!isfinite(e) || !isfinite((double)den)) f = STOP_NUMERIC;
+        else if (e <= A.rtol[0] * A.bnorm[b]) f = STOP_CONV;
+        else if (bk) f = STOP_BREAK;
+        else if (j + 1 == m || A.iters_left[b] <= 1) f = STOP_RESTART;
+        A.flag[b] = f;
+        A.iters_left[b] -= 1;
+        if (f != RUN) A.active[b] = 0;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Arnoldi step for large batches: the per-instance work (sums of the chunk partials, the T update and
+// h = T a; norm, Givens and flags) runs once per instance, in phases of its own between grid-wide
+// barriers (five phases, four barriers), and the preconditioner is a separate launch.  Compared with
+// k_arnoldi_coop this adds barriers but does not repeat any reduction, which is the better trade
+// once the chunks of the batch fill the GPU several times over.
+template <typename TP, typename TV>
+__global__ void __launch_bounds__(256) k_arnoldi_wide(
     int B, const int2* items, int nitems, const InstInfo* inst, int* active, const TP* partial, int ntask,
     const TV* z, TV* V, long long ntot, int j, int m, int nchunk, TV* part, TV* npart, TV* Tm, int ldT,
     double* H, double* Hraw, double* w0, double* cs, double* sn, double* g, int* brk, const double* bnorm,
@@ -273,6 +679,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(
     if (ok) {
       const TP* pp = partial + (size_t)ntask * in.off;
       TP s = 0;
+#pragma unroll 8
       for (int t = 0; t < ntask; ++t) s += pp[(size_t)t * in.ndof + i];
       wi = z[in.off + i] - (TV)s;
       V[(size_t)(j + 1) * ntot + in.off + i] = wi;
@@ -281,13 +688,14 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(
     vjsh[threadIdx.x] = ok ? V[(size_t)j * ntot + in.off + i] : TV(0);
     __syncthreads();
     const int nvalid = min(256, in.ndof - i0);
+#pragma unroll 4
     for (int kk = warp; kk <= j; kk += 8) {
       const TV* vk = V + (size_t)kk * ntot + in.off + i0;
       TV a = 0, gg = 0;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int ii = lane + 32 * e;
-        const TV x = ii < nvalid ? vk[ii] : TV(0);
+        const TV x = vk[min(ii, nvalid - 1)];   // surplus lanes meet zeros in wsh / vjsh
         a += x * wsh[ii];
         gg += x * vjsh[ii];
       }
@@ -321,16 +729,9 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(
       const bool used = t <= j || (t >= m + 1 && t < m + 1 + j) || t == 2 * m + 2;
       if (!used) continue;
       const TV* pp = part + ((size_t)b * nslot + t) * nchunk;
-      TV s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-      int c = 0;
-      for (; c + 4 <= nch; c += 4) {
-        s0 += pp[c];
-        s1 += pp[c + 1];
-        s2 += pp[c + 2];
-        s3 += pp[c + 3];
-      }
-      for (; c < nch; ++c) s0 += pp[c];
-      const TV acc = (s0 + s1) + (s2 + s3);
+      TV acc = 0;
+#pragma unroll 16
+      for (int c = 0; c < nch; ++c) acc += pp[c];
       if (t <= j) as[t] = acc;
       else if (t < m + 1 + j) ls[t - m - 1] = acc;
       else w0[b] = sqrt((double)acc);
@@ -340,6 +741,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(
     // row j of T: T[j][k] = -(l_k + sum_{i=k+1}^{j-1} l_i T[i][k]), k < j (T[i][i] = 1 implicit)
     for (int k = threadIdx.x; k < j; k += blockDim.x) {
       TV s = ls[k];
+#pragma unroll 8
       for (int i = k + 1; i < j; ++i) s += ls[i] * Tb[(size_t)i * ldT + k];
       Tb[(size_t)j * ldT + k] = -s;
     }
@@ -349,6 +751,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(
     for (int t = threadIdx.x; t <= j; t += blockDim.x) {
       const TV* row = Tb + (size_t)t * ldT;
       TV s = as[t];
+#pragma unroll 8
       for (int k = 0; k < t; ++k) s += row[k] * as[k];
       h[t] = (double)s;
       if (hr) hr[t] = (double)s;
@@ -368,6 +771,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(
     TV s2 = 0;
     if (i < in.ndof) {
       TV wi = V[(size_t)(j + 1) * ntot + in.off + i];
+#pragma unroll 16
       for (int kk = 0; kk <= j; ++kk) wi -= hsv[kk] * V[(size_t)kk * ntot + in.off + i];
       V[(size_t)(j + 1) * ntot + in.off + i] = wi;
       s2 = wi * wi;
@@ -457,6 +861,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(
     if (i < in.ndof) V[(size_t)(j + 1) * ntot + in.off + i] *= (TV)(1.0 / hnorm[b]);
   }
 }
+
 
 // y = R^{-1} g (R: rotated H, upper triangular k x k), one block per instance with k > 0:
 // column-oriented back substitution, column i of R read by all threads (coalesced).  Arithmetic in TV.
@@ -557,7 +962,10 @@ struct Ws {
   int nitems = 0;
   DevBuf<RomInstDev> rominst;
   DevBuf<double> rpart, rc;
-  int grid_pre = 0, grid_post64 = 0, grid_post32 = 0;
+  int grid_pre = 0, grid_post64 = 0, grid_post32 = 0, grid_wide64 = 0, grid_wide32 = 0;
+  // latency-bound problems (all chunks resident at once, few chunks per instance) take the fused
+  // two-barrier Arnoldi step; larger batches the multi-phase one (k_arnoldi_wide)
+  bool fused = true;
   std::vector<romsad_t> plan_rom;
   std::vector<std::vector<int>> plan_ids;
   void drop_graphs() {
@@ -624,6 +1032,11 @@ struct Ws {
       grid_post64 = std::min(want, std::max(1, occ) * nsm);
       RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_coop<float, float>, 256, 0));
       grid_post32 = std::min(want, std::max(1, occ) * nsm);
+      fused = nitems <= std::min(grid_post32, grid_post64) && nchunk <= 64;
+      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_wide<double, double>, 256, 0));
+      grid_wide64 = std::min(want, std::max(1, occ) * nsm);
+      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_wide<float, float>, 256, 0));
+      grid_wide32 = std::min(want, std::max(1, occ) * nsm);
     }
     RTE_TRY(part.alloc((size_t)B * nchunk * (2 * m + 3)));
     RTE_TRY(npart.alloc((size_t)B * nchunk));
@@ -786,20 +1199,22 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
     int it_first = 0;
     for (int b = 0; b < B; ++b)
       if (act[b]) { it_first = it_base[b] + rs.iterations[b]; break; }
-    // The device drops finished instances from the active mask itself (k_givens), so the host reads
-    // the flags only every kCheck iterations: instances that stopped in between are skipped by
-    // every kernel until the host catches up.
+    // The device drops finished instances from the active mask itself (Arnoldi step, phase C), so the
+    // host reads the flags only every kCheck iterations: instances that stopped in between are skipped
+    // by every kernel until the host catches up.
     const int kCheck = 8;
     *W.h_rtol = rtol;
     RTE_CHECK_CUDA(cudaMemcpyAsync(W.d_rtol.p, W.h_rtol, sizeof(double), cudaMemcpyHostToDevice, st));
     for (int j = 0; j < m; ++j) {
       const int jg = it_first + j + 1;   // lock-step instances share the global iteration index
       const bool use_rom = W.withZ && (jg <= C.window || C.post == RTE_POST_ROM);
-      // One Arnoldi iteration: preconditioner, w = A~ z_j into V[j+1], compact-WY MGS, Givens.
+      const bool rom_next = W.withZ && (jg + 1 <= C.window || C.post == RTE_POST_ROM);
+      // One Arnoldi iteration: w = A~ z_j into V[j+1], MGS, Givens, and the next preconditioned vector
+      // z_{j+1} (the first one of a cycle, z_0, by the preconditioner kernel).
       auto body = [&](cudaStream_t s) -> int {
         TV* vj = Vb + (size_t)j * ntot;
         TV* zj = Zbase + (size_t)j * ntot;
-        if (W.withZ) {
+        if (W.withZ && (j == 0 || !W.fused)) {
           if (use_rom) {
             const int2* it_p = W.items.p;
             int nit = W.nitems, Bv = B, nch = W.nchunk;
@@ -820,13 +1235,13 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
           }
         }
         RTE_TRY(launch_op_partials(p, f64, zj, f64, W.active.p, s));
-        {
+        if (!W.fused) {
           int Bv = B, nit = W.nitems, ntask = p->tasks_per_inst, jj = j, mm = m, nch = W.nchunk, ldT = m + 1;
           long long nt = ntot;
           const int2* it_p = W.items.p;
           const InstInfo* inst_p = p->d_inst.p;
           int* act_p = W.active.p;
-          const void* part_p = p->d_partial.p;
+          const TV* part_p = reinterpret_cast<const TV*>(p->d_partial.p);
           const TV* z_p = zj;
           TV* V_p = Vb;
           TV* dp_p = reinterpret_cast<TV*>(W.part.p);
@@ -850,18 +1265,58 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
           void* args[] = {&Bv, &it_p, &nit, &inst_p, &act_p, &part_p, &ntask, &z_p, &V_p, &nt, &jj, &mm, &nch,
                           &dp_p, &np_p, &Lt_p, &ldT, &H_p, &Hr_p, &w0_p, &cs_p, &sn_p, &g_p, &brk_p, &bn_p, &rt_p,
                           &il_p, &est_p, &fl_p, &kc_p, &hn_p, &a0_p};
-          if constexpr (f64)
-            RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop<double, double>,
-                                                       dim3(W.grid_post64), dim3(256), args, 0, s));
-          else
-            RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop<float, float>,
-                                                       dim3(W.grid_post32), dim3(256), args, 0, s));
+          RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_wide<TV, TV>,
+                                                     dim3(f64 ? W.grid_wide64 : W.grid_wide32), dim3(256), args, 0,
+                                                     s));
+          count_launch();
+        } else {
+          ArnArgs<TV, TV> A;
+          A.B = B;
+          A.nitems = W.nitems;
+          A.ntask = p->tasks_per_inst;
+          A.j = j;
+          A.m = m;
+          A.nchunk = W.nchunk;
+          A.ldT = m + 1;
+          A.rom_next = rom_next ? 1 : 0;
+          A.ntot = ntot;
+          A.items = W.items.p;
+          A.inst = p->d_inst.p;
+          A.active = W.active.p;
+          A.active0 = W.active0.p;
+          A.partial = reinterpret_cast<const TV*>(p->d_partial.p);
+          A.z = zj;
+          A.V = Vb;
+          A.znext = (W.withZ && j + 1 < m) ? Zbase + (size_t)(j + 1) * ntot : nullptr;
+          A.part = reinterpret_cast<TV*>(W.part.p);
+          A.npart = reinterpret_cast<TV*>(W.npart.p);
+          A.Tm = reinterpret_cast<TV*>(W.Lt.p);
+          A.rpart = reinterpret_cast<TV*>(W.rpart.p);
+          A.ri = W.rominst.p;
+          A.sig_dof = sig_dof;
+          A.H = W.H.p;
+          A.Hraw = C.rec ? W.Hraw.p : nullptr;
+          A.w0 = W.w0.p;
+          A.cs = W.cs.p;
+          A.sn = W.sn.p;
+          A.g = W.g.p;
+          A.est = W.est.p;
+          A.bnorm = W.bnorm.p;
+          A.rtol = W.d_rtol.p;
+          A.iters_left = W.iters_left.p;
+          A.flag = W.flag.p;
+          A.kcols = W.kcols.p;
+          void* args[] = {&A};
+          RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop<TV, TV>,
+                                                     dim3(f64 ? W.grid_post64 : W.grid_post32), dim3(256), args, 0,
+                                                     s));
           count_launch();
         }
         RTE_CHECK_CUDA(cudaGetLastError());
         return RTE_OK;
       };
-      const int key = j | (use_rom ? 1 << 8 : 0) | (f64 ? 1 << 9 : 0) | (C.rec ? 1 << 10 : 0);
+      const int key = j | (use_rom ? 1 << 8 : 0) | (f64 ? 1 << 9 : 0) | (C.rec ? 1 << 10 : 0) |
+                      (rom_next ? 1 << 11 : 0);
       auto it = W.graphs.find(key);
       if (it == W.graphs.end()) {
         // capture this iteration once; later iterations with the same key replay it

@@ -179,6 +179,26 @@ def test_mixed_escalates_to_fp64_after_max_outer():
         assert rel(split(phi, gp.offsets)[b], ref) < 1e-8
 
 
+def test_large_instance_multiphase_arnoldi_matches_oracle():
+    """A 132x132 instance has 272 chunks of 256 dofs, more than the 64 per instance for which the
+    fused two-barrier Arnoldi step repeats the per-instance sums in every block, so the solve runs
+    the multi-phase step (k_arnoldi_wide).  FP64 and mixed solves both match the oracle."""
+    B = lib()
+    spec = spec2d([132], [132], n_polar=2, n_azim=8)
+    ss, sa = wl.draw_params(spec, 1, 41)
+    ss = np.minimum(ss, 20.0)
+    gp = B.Problem(spec, ss, sa)
+    op = oracle_problems(spec, ss, sa)[0]
+    ref, _ = ORS.solve(op, None, restart=200, rtol=1e-13, max_iter=3000)
+    phi, st = _solve_gpu(B, gp, None, restart=40, rtol=1e-11, max_iter=2000)
+    assert st[0]["status"] == 0
+    assert rel(phi, ref) < 1e-9
+    phi, st = _solve_gpu(B, gp, None, restart=40, rtol=1e-9, max_iter=2000, mode=B.RTE_MODE_MIXED,
+                         inner_rtol=1e-2, max_outer=30)
+    assert st[0]["status"] == 0 and st[0]["true_rel_residual"] <= 1e-9
+    assert rel(phi, ref) < 1e-7
+
+
 def test_host_output_pointer_and_not_converged_status():
     torch = torch_cuda()
     B = lib()
