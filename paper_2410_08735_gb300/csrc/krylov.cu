@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
     if (ok) {
       const TP* pp = A.partial + (size_t)A.ntask * in.off;
       TP s = 0;
-#pragma unroll 8
+#pragma unroll 32
       for (int t = 0; t < A.ntask; ++t) s += pp[(size_t)t * in.ndof + i];
       wi = A.z[in.off + i] - (TV)s;
       A.V[(size_t)(j + 1) * ntot + in.off + i] = wi;
@@ -410,25 +410,60 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
       sl[t] = acc;
     }
     __syncthreads();
+    // One pass over the stored triangle of T (rows r < j, columns k < r), 8 rows per warp and pass,
+    // lanes over k.  Row sums give h_r = a_r + sum_k T[r][k] a_k; the block of chunk 0 also forms the
+    // column sums sum_r l_r T[r][k] for the new row of T.  Row and column indices are clamped into the
+    // array and the surplus terms selected away, so that every load of a pass is unconditional.
     const TV* Tb = A.Tm + (size_t)b * (m + 1) * A.ldT;
-    // h_i = a_i + sum_{k<i} T[i][k] a_k for i < j (warp per row, lanes over k)
-#pragma unroll 4
-    for (int r = warp; r < j; r += 8) {
-      const TV* row = Tb + (size_t)r * A.ldT;
-      TV s = 0;
-      for (int k = lane; k < r; k += 32) s += row[k] * sl[k];
-      s = warp_sum_t(s);
-      if (lane == 0) hsv[r] = sl[r] + s;
+    const bool trow = ch == 0;
+    TV cacc[4] = {0, 0, 0, 0};
+    const int jm = max(j - 1, 0);
+    for (int r0 = 0; r0 < j; r0 += 64) {
+      TV tv[8][4];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const TV* row = Tb + (size_t)min(r0 + warp + 8 * q, jm) * A.ldT;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) tv[q][p] = row[min(lane + 32 * p, A.ldT - 1)];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int r = r0 + warp + 8 * q;
+        const TV lr = sl[min(m + 1 + r, 2 * m + 1)];
+        TV s = 0;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const int k = lane + 32 * p;
+          const bool tri = r < j && k < r;
+          s += tri ? tv[q][p] * sl[k] : TV(0);
+          cacc[p] += tri ? lr * tv[q][p] : TV(0);
+        }
+        s = warp_sum_t(s);
+        if (lane == 0 && r < j) hsv[r] = sl[r] + s;
+      }
+    }
+    if (trow) {
+#pragma unroll
+      for (int p = 0; p < 4; ++p) red[warp][lane + 32 * p] = cacc[p];
     }
     __syncthreads();
     if (warp == 0) {
+      // h_j = a_j - sum_{i<j} l_i h_i
       TV s = 0;
       for (int r = lane; r < j; r += 32) s += sl[m + 1 + r] * hsv[r];
       s = warp_sum_t(s);
       if (lane == 0) hsv[j] = sl[j] - s;
     }
+    if (trow) {
+      // new row of T: T[j][k] = -(l_k + sum_{r=k+1}^{j-1} l_r T[r][k]), k < j
+      for (int k = threadIdx.x; k < j; k += blockDim.x) {
+        TV s = sl[m + 1 + k];
+        for (int w = 0; w < 8; ++w) s += red[w][k];
+        A.Tm[(size_t)b * (m + 1) * A.ldT + (size_t)j * A.ldT + k] = -s;
+      }
+    }
     __syncthreads();
-    if (ch == 0) {
+    if (trow) {
       double* h = A.H + ((size_t)b * m + j) * (m + 1);
       double* hr = A.Hraw ? A.Hraw + ((size_t)b * m + j) * (m + 1) : nullptr;
       for (int t = threadIdx.x; t <= j; t += blockDim.x) {
@@ -439,28 +474,6 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
         A.w0[b] = sqrt((double)sl[2 * m + 2]);
         A.active0[b] = 1;
       }
-      // new row of T: T[j][k] = -(l_k + sum_{i=k+1}^{j-1} l_i T[i][k]), k < j.  Warp w accumulates
-      // rows i = w, w+8, ... for the columns k = lane + 32 q; the warps' sums are combined in order.
-      TV acc[4] = {0, 0, 0, 0};
-#pragma unroll 2
-      for (int r = warp; r < j; r += 8) {
-        const TV* row = Tb + (size_t)r * A.ldT;
-        const TV lr = sl[m + 1 + r];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int k = lane + 32 * q;
-          if (k < r) acc[q] += lr * row[k];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) red[warp][lane + 32 * q] = acc[q];
-      __syncthreads();
-      for (int k = threadIdx.x; k < j; k += blockDim.x) {
-        TV s = sl[m + 1 + k];
-        for (int w = 0; w < 8; ++w) s += red[w][k];
-        A.Tm[(size_t)b * (m + 1) * A.ldT + (size_t)j * A.ldT + k] = -s;
-      }
-      __syncthreads();
     }
     // w -= V h on this chunk, ||w||^2 partial
     const int i = ch * 256 + threadIdx.x;
@@ -474,6 +487,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
       A.V[(size_t)(j + 1) * ntot + in.off + i] = wi;
     }
     TV s2 = warp_sum_t(wi * wi);
+    __syncthreads();   // red is free again
     if (lane == 0) red[warp][0] = s2;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -530,6 +544,31 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
     const int nch = (in.ndof + 255) / 256;
     const RomInstDev R = A.ri[b];
     const bool lift = A.znext && A.rom_next && R.has;
+    const int i = ch * 256 + threadIdx.x;
+    const bool ok = i < in.ndof;
+    const size_t o = (size_t)(j + 1) * ntot + in.off + min(i, in.ndof - 1);
+    // loads that do not depend on this phase's sums are issued first: w, the W row and the inverse row
+    // of this thread, w0, and the Givens inputs of the block of chunk 0
+    const TV wv = A.V[o];
+    const double w0b = A.w0[b];
+    TV wr[32], ir[32];
+    if (lift) {
+      const TV* w = RomSel<TV>::W(R) + (size_t)min(i, in.ndof - 1) * R.rmax;
+      const int cl = R.rmax - 1;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) wr[q] = w[min(q, cl)];
+      const TV* row = RomSel<TV>::inv(R) + (size_t)min((int)threadIdx.x, R.r - 1) * R.r;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) ir[q] = row[min(q, R.r - 1)];
+    }
+    if (ch == 0) {
+      const double* h = A.H + ((size_t)b * m + j) * (m + 1);
+      for (int t = threadIdx.x; t <= j; t += blockDim.x) hsv[t] = (TV)h[t];
+      for (int t = threadIdx.x; t < j; t += blockDim.x) {
+        css[t] = (TV)A.cs[(size_t)b * m + t];
+        sns[t] = (TV)A.sn[(size_t)b * m + t];
+      }
+    }
     if (warp == 0) {
       TV acc = 0;
       for (int c = lane; c < nch; c += 32) acc += A.npart[(size_t)b * A.nchunk + c];
@@ -537,7 +576,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
       if (lane == 0) hsc = sqrt(acc);
     }
     if (lift) {
-      // c = (U^T A_mu U)^{-1} P^T Sigma_s w / h_{j+1,j}; warp w sums chunks w, w+8, ...
+      // warp w sums the projection partials of chunks w, w+8, ...
       for (int q = lane; q < 64; q += 32) {
         TV s = 0;
         if (q < R.r) {
@@ -549,9 +588,10 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
     }
     __syncthreads();
     const TV hn = hsc;
-    const bool bk = !((double)hn > 1e-14 * A.w0[b]);
+    const bool bk = !((double)hn > 1e-14 * w0b);
     const TV inv_h = bk ? TV(0) : TV(1) / hn;
     if (lift) {
+      // c = (U^T A_mu U)^{-1} P^T Sigma_s w / h_{j+1,j}
       if (threadIdx.x < 64) {
         TV s = 0;
         for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
@@ -559,13 +599,12 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
       }
       __syncthreads();
       if (threadIdx.x < R.r) {
-        const TV* row = RomSel<TV>::inv(R) + (size_t)threadIdx.x * R.r;
         TV s = 0;
 #pragma unroll
-        for (int q = 0; q < 32; ++q) s += row[min(q, R.r - 1)] * wsh[q];
+        for (int q = 0; q < 32; ++q) s += ir[q] * wsh[q];
         if (R.r > 32) {
-#pragma unroll
-          for (int q = 32; q < 64; ++q) s += row[min(q, R.r - 1)] * wsh[q];
+          const TV* row = RomSel<TV>::inv(R) + (size_t)threadIdx.x * R.r;
+          for (int q = 32; q < R.r; ++q) s += row[q] * wsh[q];
         }
         ys[threadIdx.x] = s;
       } else if (threadIdx.x < 64) {
@@ -574,22 +613,18 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
       __syncthreads();
     }
     // v_{j+1} = w / h_{j+1,j} and z_{j+1} on this chunk
-    const int i = ch * 256 + threadIdx.x;
-    if (!bk && i < in.ndof) {
-      const size_t o = (size_t)(j + 1) * ntot + in.off + i;
-      const TV v = A.V[o] * inv_h;
+    if (!bk && ok) {
+      const TV v = wv * inv_h;
       A.V[o] = v;
       if (A.znext) {
         TV zv = v;
         if (lift) {
-          const TV* w = RomSel<TV>::W(R) + (size_t)i * R.rmax;
-          const int cl = R.rmax - 1;
           TV s = 0;
 #pragma unroll
-          for (int q = 0; q < 32; ++q) s += w[min(q, cl)] * ys[q];
+          for (int q = 0; q < 32; ++q) s += wr[q] * ys[q];
           if (R.r > 32) {
-#pragma unroll
-            for (int q = 32; q < 64; ++q) s += w[min(q, cl)] * ys[q];
+            const TV* w = RomSel<TV>::W(R) + (size_t)i * R.rmax;
+            for (int q = 32; q < R.r; ++q) s += w[q] * ys[q];
           }
           zv += s;
         }
@@ -597,34 +632,34 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
       }
     }
     if (ch == 0) {
-      // h_{j+1,j}, Givens rotation of column j, stopping flags (one thread)
+      // Givens rotations of column j: one thread, the running entry kept in a register; the rotated
+      // entries are then stored by all threads (the FP64 conversions are slow one at a time)
       double* h = A.H + ((size_t)b * m + j) * (m + 1);
-      double* c = A.cs + (size_t)b * m;
-      double* s = A.sn + (size_t)b * m;
-      double* gg = A.g + (size_t)b * (m + 1);
-      for (int t = threadIdx.x; t <= j; t += blockDim.x) hsv[t] = (TV)h[t];
-      for (int t = threadIdx.x; t < j; t += blockDim.x) {
-        css[t] = (TV)c[t];
-        sns[t] = (TV)s[t];
+      if (threadIdx.x == 0) {
+        TV cur = hsv[0];
+#pragma unroll 4
+        for (int t = 0; t < j; ++t) {
+          const TV nx = hsv[t + 1], c = css[t], s = sns[t];
+          hsv[t] = c * cur + s * nx;
+          cur = c * nx - s * cur;
+        }
+        hsv[j] = cur;
       }
       __syncthreads();
+      for (int t = threadIdx.x; t < j; t += blockDim.x) h[t] = (double)hsv[t];
       if (threadIdx.x == 0) {
-        hsv[j + 1] = hn;
+        // h_{j+1,j}, the new rotation, the residual estimate and the stopping flags
+        double* gg = A.g + (size_t)b * (m + 1);
         if (A.Hraw) A.Hraw[((size_t)b * m + j) * (m + 1) + j + 1] = (double)hn;
-        for (int t = 0; t < j; ++t) {
-          const TV x = css[t] * hsv[t] + sns[t] * hsv[t + 1];
-          hsv[t + 1] = -sns[t] * hsv[t] + css[t] * hsv[t + 1];
-          hsv[t] = x;
-        }
-        const TV den = hypot(hsv[j], hsv[j + 1]);
+        const TV cur = hsv[j];
+        const TV den = hypot(cur, hn);
         TV cj = 1, sj = 0;
         if (den > TV(0)) {
-          cj = hsv[j] / den;
-          sj = hsv[j + 1] / den;
+          cj = cur / den;
+          sj = hn / den;
         }
-        for (int t = 0; t < j; ++t) h[t] = (double)hsv[t];
-        c[j] = (double)cj;
-        s[j] = (double)sj;
+        A.cs[(size_t)b * m + j] = (double)cj;
+        A.sn[(size_t)b * m + j] = (double)sj;
         h[j] = (double)den;
         h[j + 1] = 0.0;
         const TV gj = (TV)gg[j];
