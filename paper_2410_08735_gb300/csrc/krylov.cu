@@ -133,7 +133,9 @@ struct RomInstDev {
   const float* W32;
   const double* inv;   // (U^T A_mu U)^{-1}, r x r row-major
   const float* inv32;  // the same, rounded to FP32
-  int r, rmax, has;
+  const double* WT;    // W transposed, [r][N]
+  const float* WT32;
+  int r, rmax, has, N;
 };
 
 template <typename TV>
@@ -143,12 +145,14 @@ struct RomSel<double> {
   __device__ static const double* P(const RomInstDev& R) { return R.P; }
   __device__ static const double* W(const RomInstDev& R) { return R.W; }
   __device__ static const double* inv(const RomInstDev& R) { return R.inv; }
+  __device__ static const double* WT(const RomInstDev& R) { return R.WT; }
 };
 template <>
 struct RomSel<float> {
   __device__ static const float* P(const RomInstDev& R) { return R.P32; }
   __device__ static const float* W(const RomInstDev& R) { return R.W32; }
   __device__ static const float* inv(const RomInstDev& R) { return R.inv32; }
+  __device__ static const float* WT(const RomInstDev& R) { return R.WT32; }
 };
 
 template <typename TV>
@@ -263,14 +267,13 @@ __global__ void __launch_bounds__(256) k_precond_coop(int B, const int2* items, 
     __syncthreads();
     const int i = ch * 256 + threadIdx.x;
     if (i >= in.ndof) continue;
-    const TV* w = RomSel<TV>::W(R) + (size_t)i * R.rmax;
-    const int cl = R.rmax - 1;
+    const TV* wt = RomSel<TV>::WT(R) + i;   // W^T: consecutive dofs per rank index (coalesced)
     TV s = 0;
 #pragma unroll
-    for (int q = 0; q < 32; ++q) s += w[min(q, cl)] * ys[q];
+    for (int q = 0; q < 32; ++q) s += wt[(size_t)min(q, R.r - 1) * R.N] * ys[q];
     if (R.r > 32) {
 #pragma unroll
-      for (int q = 32; q < 64; ++q) s += w[min(q, cl)] * ys[q];
+      for (int q = 32; q < 64; ++q) s += wt[(size_t)min(q, R.r - 1) * R.N] * ys[q];
     }
     z[in.off + i] = v[in.off + i] + s;
   }
@@ -359,23 +362,32 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
     vjsh[threadIdx.x] = ok ? A.V[(size_t)j * ntot + in.off + i] : TV(0);
     __syncthreads();
     const int nvalid = min(256, in.ndof - i0);
-    // warp q owns k = q, q + 8, ...: its reductions are independent of the other warps'
-#pragma unroll 4
-    for (int kk = warp; kk <= j; kk += 8) {
-      const TV* vk = A.V + (size_t)kk * ntot + in.off + i0;
-      TV a = 0, gg = 0;
+    // warp q owns k = q, q + 8, ...: its reductions are independent of the other warps'.  Vectors are
+    // taken four at a time with the index clamped to j (the surplus results are not stored), so every
+    // batch issues all of its loads before the first use and there is no remainder loop.
+    for (int k0 = warp; k0 <= j; k0 += 32) {
+      TV x[4][8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int ii = lane + 32 * e;
-        const TV x = vk[min(ii, nvalid - 1)];   // surplus lanes meet zeros in wsh / vjsh
-        a += x * wsh[ii];
-        gg += x * vjsh[ii];
+      for (int u = 0; u < 4; ++u) {
+        const TV* vk = A.V + (size_t)min(k0 + 8 * u, j) * ntot + in.off + i0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[u][e] = vk[min(lane + 32 * e, nvalid - 1)];   // surplus lanes meet zeros
       }
-      a = warp_sum_t(a);
-      gg = warp_sum_t(gg);
-      if (lane == 0) {
-        sl[kk] = a;
-        if (kk < j) sl[m + 1 + kk] = gg;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int kk = k0 + 8 * u;
+        TV a = 0, gg = 0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          a += x[u][e] * wsh[lane + 32 * e];
+          gg += x[u][e] * vjsh[lane + 32 * e];
+        }
+        a = warp_sum_t(a);
+        gg = warp_sum_t(gg);
+        if (lane == 0 && kk <= j) {
+          sl[kk] = a;
+          if (kk < j) sl[m + 1 + kk] = gg;
+        }
       }
     }
     if (warp == 7) {
@@ -400,14 +412,27 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
     }
     const InstInfo in = A.inst[b];
     const int nch = (in.ndof + 255) / 256;
-    // instance sums of the chunk partials, one slot per thread, chunks in order
-    for (int t = threadIdx.x; t < nslot; t += blockDim.x) {
-      if (!used(t)) continue;
-      const TV* pp = A.part + ((size_t)b * nslot + t) * A.nchunk;
-      TV acc = 0;
-#pragma unroll 32
-      for (int c = 0; c < nch; ++c) acc += pp[c];
-      sl[t] = acc;
+    // instance sums of the chunk partials over the 2j+2 used slots (a_0..a_j, l_0..l_{j-1}, w.w):
+    // warp w takes used slots w, w+8, ..., its lanes the chunks (coalesced; this path has at most 64
+    // chunks per instance, two per lane), then a fixed shuffle tree.  Eight slots per batch, indices
+    // clamped, all loads issued before the first use.
+    const int nused = 2 * j + 2;
+    auto slot_of = [&](int u) { return u <= j ? u : (u < 2 * j + 1 ? m + 1 + (u - j - 1) : 2 * m + 2); };
+    for (int u0 = warp; u0 < nused; u0 += 64) {
+      TV x0[8], x1[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const TV* pp = A.part + ((size_t)b * nslot + slot_of(min(u0 + 8 * q, nused - 1))) * A.nchunk;
+        x0[q] = pp[min(lane, nch - 1)];
+        x1[q] = pp[min(lane + 32, nch - 1)];
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        TV v = (lane < nch ? x0[q] : TV(0)) + (lane + 32 < nch ? x1[q] : TV(0));
+        v = warp_sum_t(v);
+        const int u = u0 + 8 * q;
+        if (lane == 0 && u < nused) sl[slot_of(u)] = v;
+      }
     }
     __syncthreads();
     // One pass over the stored triangle of T (rows r < j, columns k < r), 8 rows per warp and pass,
@@ -481,9 +506,15 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
     TV wi = 0;
     if (ok) {
       wi = A.V[(size_t)(j + 1) * ntot + in.off + i];
-      constexpr int U = sizeof(TV) == 4 ? 32 : 8;
-#pragma unroll(U)
-      for (int kk = 0; kk <= j; ++kk) wi -= hsv[kk] * A.V[(size_t)kk * ntot + in.off + i];
+      // batches of U vectors, index clamped to j and the surplus terms selected away: no remainder loop
+      constexpr int U = sizeof(TV) == 4 ? 16 : 8;
+      for (int k0 = 0; k0 <= j; k0 += U) {
+        TV x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) x[u] = A.V[(size_t)min(k0 + u, j) * ntot + in.off + i];
+#pragma unroll
+        for (int u = 0; u < U; ++u) wi -= (k0 + u <= j) ? hsv[min(k0 + u, j)] * x[u] : TV(0);
+      }
       A.V[(size_t)(j + 1) * ntot + in.off + i] = wi;
     }
     TV s2 = warp_sum_t(wi * wi);
@@ -553,10 +584,10 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
     const double w0b = A.w0[b];
     TV wr[32], ir[32];
     if (lift) {
-      const TV* w = RomSel<TV>::W(R) + (size_t)min(i, in.ndof - 1) * R.rmax;
-      const int cl = R.rmax - 1;
+      // W^T [r][N]: for each rank index the threads of a chunk read consecutive dofs
+      const TV* wt = RomSel<TV>::WT(R) + min(i, in.ndof - 1);
 #pragma unroll
-      for (int q = 0; q < 32; ++q) wr[q] = w[min(q, cl)];
+      for (int q = 0; q < 32; ++q) wr[q] = wt[(size_t)min(q, R.r - 1) * R.N];
       const TV* row = RomSel<TV>::inv(R) + (size_t)min((int)threadIdx.x, R.r - 1) * R.r;
 #pragma unroll
       for (int q = 0; q < 32; ++q) ir[q] = row[min(q, R.r - 1)];
@@ -623,8 +654,8 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
 #pragma unroll
           for (int q = 0; q < 32; ++q) s += wr[q] * ys[q];
           if (R.r > 32) {
-            const TV* w = RomSel<TV>::W(R) + (size_t)i * R.rmax;
-            for (int q = 32; q < R.r; ++q) s += w[q] * ys[q];
+            const TV* wt = RomSel<TV>::WT(R) + i;
+            for (int q = 32; q < R.r; ++q) s += wt[(size_t)q * R.N] * ys[q];
           }
           zv += s;
         }
@@ -958,6 +989,17 @@ __global__ void k_zero_active(TV* x, const InstInfo* inst, const int* active) {
   if (active && !active[b]) return;
   const InstInfo in = inst[b];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) x[in.off + i] = TV(0);
+}
+
+// W^T [r][N] (FP64 and FP32) from W [N][rmax]
+__global__ void k_w_transpose(const double* W, int N, int rmax, int r, double* WT, float* WT32) {
+  const long long n = (long long)N * r;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(e / N), i = (int)(e % N);
+    const double w = W[(size_t)i * rmax + q];
+    WT[e] = w;
+    WT32[e] = (float)w;
+  }
 }
 
 // FP32 copy of the ROM inverse operators
@@ -1573,10 +1615,16 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       RTE_TRY(pl.inv32.ensure(pl.lu.n));
       k_inv_to_f32<<<64, 256, 0, st>>>(pl.lu.p, pl.inv32.p, (long long)pl.lu.n);
       count_launch();
+      romsad* rm = prom[q];
+      RTE_TRY(pl.WT.ensure((size_t)rm->N * std::max(1, rm->r)));
+      RTE_TRY(pl.WT32.ensure((size_t)rm->N * std::max(1, rm->r)));
+      k_w_transpose<<<152, 256, 0, st>>>(rm->W.p, rm->N, rm->rmax, rm->r, pl.WT.p, pl.WT32.p);
+      count_launch();
     }
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->norom.p, C.no_rom_mask.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
     std::vector<RomInstDev> ri(B);
-    for (int b = 0; b < B; ++b) ri[b] = RomInstDev{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0};
+    for (int b = 0; b < B; ++b)
+      ri[b] = RomInstDev{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, 0};
     for (size_t q = 0; q < prom.size(); ++q)
       for (size_t sl = 0; sl < pids[q].size(); ++sl) {
         romsad* rm = prom[q];
@@ -1586,9 +1634,12 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
                                      rm->W32.p,
                                      ws->plans[q].lu.p + sl * 64 * 64,
                                      ws->plans[q].inv32.p + sl * 64 * 64,
+                                     ws->plans[q].WT.p,
+                                     ws->plans[q].WT32.p,
                                      rm->r,
                                      rm->rmax,
-                                     1};
+                                     1,
+                                     rm->N};
       }
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->rominst.p, ri.data(), B * sizeof(RomInstDev), cudaMemcpyHostToDevice, st));
     RTE_CHECK_CUDA(cudaStreamSynchronize(st));

@@ -59,6 +59,8 @@ struct RomPlan {
   DevBuf<int> d_ids, piv;
   DevBuf<double> lu, part, c;
   DevBuf<float> inv32;   // FP32 copy of lu (the inverses), filled by the FGMRES driver
+  DevBuf<double> WT;     // W transposed [r][N] (coalesced lift), filled by the FGMRES driver
+  DevBuf<float> WT32;
   int chunk = 1024, nchunk = 0;
   int build(romsad* rom, rte_problem* p, const std::vector<int>& ids, cudaStream_t st);
   int apply(rte_problem* p, const int* d_active, const double* v, double* z, bool f64, cudaStream_t st);
