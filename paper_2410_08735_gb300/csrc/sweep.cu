@@ -74,6 +74,30 @@ struct Vec4<double> {
   }
 };
 
+// Angular output: lane (f's segment, cell e) stores one cell of the completed 8-cell segment of lane f,
+// whose current column is colf at cell cf, from f's staging ring to every block of the task's
+// directions (offsets ob0/ob1, or the direction table when a direction stands for more than two).
+#define RTE_STORE_SEGMENT(f, cf, colf, e)                                                              \
+  do {                                                                                                 \
+    const int cs_ = (colf) & ~7;                                                                       \
+    if ((e) <= (colf) - cs_) {                                                                         \
+      const long long cellf_ = (cf) + (sx > 0 ? (cs_ + (e) - (colf)) : ((colf) - cs_ - (e)));          \
+      const T* sr_ = ring - (size_t)(lane - (f)) * D * 32;                                             \
+      _Pragma("unroll") for (int d = 0; d < D; ++d) {                                                  \
+        T v0, v1, v2, v3;                                                                              \
+        Vec4<T>::load(sr_ + d * 32 + (e) * 4, v0, v1, v2, v3);                                         \
+        if (dup2) {                                                                                    \
+          Vec4<T>::store(psi + ob0[d] + 4 * cellf_, v0, v1, v2, v3);                                   \
+          if (ob1[d] >= 0) Vec4<T>::store(psi + ob1[d] + 4 * cellf_, v0, v1, v2, v3);                 \
+        } else {                                                                                       \
+          const UDir u_ = a.udir[tk.u0 + d];                                                           \
+          for (int q = 0; q < u_.ndup; ++q)                                                            \
+            Vec4<T>::store(psi + (size_t)u_.dup[q] * in.ndof + 4 * cellf_, v0, v1, v2, v3);           \
+        }                                                                                              \
+      }                                                                                                \
+    }                                                                                                  \
+  } while (0)
+
 template <typename T, typename TI, int D, bool ANG>
 __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -109,6 +133,28 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
   const TI* src = reinterpret_cast<const TI*>(a.src) + in.off;
   T* part = reinterpret_cast<T*>(a.partial) + (size_t)a.tasks_per_inst * in.off + (size_t)tk.t * in.ndof;
   T* psi = ANG ? reinterpret_cast<T*>(a.psi) + (size_t)(a.psi_unique ? a.nu : a.ndir) * in.off : nullptr;
+  // angular output: element offsets (within the instance) of the blocks each of the task's directions
+  // is stored to (its unique block, or the one or two N_Omega blocks it stands for), read once here
+  // instead of from the direction table at every flush
+  int ob0[D], ob1[D];
+  bool dup2 = true;   // every direction stands for at most two stored blocks
+  if (ANG) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const UDir u = a.udir[tk.u0 + d];
+      if (a.psi_unique) {
+        ob0[d] = (tk.u0 + d) * in.ndof;
+        ob1[d] = -1;
+      } else {
+        ob0[d] = u.dup[0] * in.ndof;
+        ob1[d] = u.ndup > 1 ? u.dup[1] * in.ndof : -1;
+        dup2 = dup2 && u.ndup <= 2;
+      }
+    }
+  }
+  // in a mesh whose width is a multiple of 8 the lanes that complete an 8-cell segment at step s are
+  // exactly f = (s + 1) mod 8 + 8k, k = 0..3 (lane l works on column s - l modulo the band length)
+  const bool regular = (in.nx & 7) == 0 && dup2;
   const T S3 = (T)1.7320508075688772;
   const int P = nx > 32 ? nx : 32;
   const int nbands = (ny + 31) >> 5;
@@ -275,35 +321,25 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
       const long long myc = act ? c : 0;
       const int mycol = act ? col : 0;
       __syncwarp();
-      unsigned fm = __ballot_sync(0xffffffffu, flush);
-      while (fm) {
-        int fl[4], n = 0;
-        while (fm && n < 4) {
-          fl[n++] = __ffs(fm) - 1;
-          fm &= fm - 1;
-        }
-        const int k = lane >> 3, e = lane & 7;
-        const int f = fl[k < n ? k : 0];
+      const int k = lane >> 3, e = lane & 7;
+      if (regular) {
+        const int f = ((s + 1) & 7) + 8 * k;
+        const bool ff = __shfl_sync(0xffffffffu, flush, f);
         const long long cf = __shfl_sync(0xffffffffu, myc, f);
         const int colf = __shfl_sync(0xffffffffu, mycol, f);
-        if (k < n) {
-          const int cs = colf & ~7;
-          if (e <= colf - cs) {
-            const long long cellf = cf + (sx > 0 ? (cs + e - colf) : (colf - cs - e));
-            const T* src_ring = ring - (size_t)(lane - f) * D * 32;
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-              T v0, v1, v2, v3;
-              Vec4<T>::load(src_ring + d * 32 + e * 4, v0, v1, v2, v3);
-              if (a.psi_unique) {
-                Vec4<T>::store(psi + (size_t)(tk.u0 + d) * in.ndof + 4 * cellf, v0, v1, v2, v3);
-              } else {
-                const UDir u = a.udir[tk.u0 + d];
-                for (int q = 0; q < u.ndup; ++q)
-                  Vec4<T>::store(psi + (size_t)u.dup[q] * in.ndof + 4 * cellf, v0, v1, v2, v3);
-              }
-            }
+        if (ff) RTE_STORE_SEGMENT(f, cf, colf, e);
+      } else {
+        unsigned fm = __ballot_sync(0xffffffffu, flush);
+        while (fm) {
+          int fl[4], n = 0;
+          while (fm && n < 4) {
+            fl[n++] = __ffs(fm) - 1;
+            fm &= fm - 1;
           }
+          const int f = fl[k < n ? k : 0];
+          const long long cf = __shfl_sync(0xffffffffu, myc, f);
+          const int colf = __shfl_sync(0xffffffffu, mycol, f);
+          if (k < n) RTE_STORE_SEGMENT(f, cf, colf, e);
         }
       }
     }
@@ -357,6 +393,28 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
   const TI* src = reinterpret_cast<const TI*>(a.src) + in.off;
   T* part = reinterpret_cast<T*>(a.partial) + (size_t)a.tasks_per_inst * in.off + (size_t)tk.t * in.ndof;
   T* psi = ANG ? reinterpret_cast<T*>(a.psi) + (size_t)(a.psi_unique ? a.nu : a.ndir) * in.off : nullptr;
+  // angular output: element offsets (within the instance) of the blocks each of the task's directions
+  // is stored to (its unique block, or the one or two N_Omega blocks it stands for), read once here
+  // instead of from the direction table at every flush
+  int ob0[D], ob1[D];
+  bool dup2 = true;   // every direction stands for at most two stored blocks
+  if (ANG) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const UDir u = a.udir[tk.u0 + d];
+      if (a.psi_unique) {
+        ob0[d] = (tk.u0 + d) * in.ndof;
+        ob1[d] = -1;
+      } else {
+        ob0[d] = u.dup[0] * in.ndof;
+        ob1[d] = u.ndup > 1 ? u.dup[1] * in.ndof : -1;
+        dup2 = dup2 && u.ndup <= 2;
+      }
+    }
+  }
+  // in a mesh whose width is a multiple of 8 the lanes that complete an 8-cell segment at step s are
+  // exactly f = (s + 1) mod 8 + 8k, k = 0..3 (lane l works on column s - l modulo the band length)
+  const bool regular = (in.nx & 7) == 0 && dup2;
   const T S3 = (T)1.7320508075688772;
   const int band = warp;
   const int row = band * 32 + lane;
@@ -470,36 +528,34 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
         // whole 128-byte lines
         const bool flush = act && ((col & 7) == 7 || col == nx - 1);
         __syncwarp();
-        unsigned fm = __ballot_sync(0xffffffffu, flush);
-        while (fm) {
-          int fl[4], n = 0;
-          while (fm && n < 4) {
-            fl[n++] = __ffs(fm) - 1;
-            fm &= fm - 1;
+        const int k = lane >> 3, e = lane & 7;
+        // cell of the flushing lane f's current column (its row is band * 32 + f)
+        auto cell_at = [&](int f, int colf) -> long long {
+          const int rowf = band * 32 + f;
+          const int iyf = sy > 0 ? rowf : ny - 1 - rowf;
+          return (long long)iyf * nx + (sx > 0 ? colf : nx - 1 - colf);
+        };
+        if (regular) {
+          const int f = ((s + 1) & 7) + 8 * k;
+          const bool ff = __shfl_sync(0xffffffffu, flush, f);
+          const int colf = s - 32 * band - f;
+          if (ff) {
+            const long long cf = cell_at(f, colf);
+            RTE_STORE_SEGMENT(f, cf, colf, e);
           }
-          const int k = lane >> 3, e = lane & 7;
-          if (k < n) {
-            const int f = fl[k];
-            const int colf = s - 32 * band - f;
-            const int cs = colf & ~7;
-            if (e <= colf - cs) {
-              const int cl = cs + e;
-              const int rowf = band * 32 + f;
-              const int iyf = sy > 0 ? rowf : ny - 1 - rowf;
-              const long long cellf = (long long)iyf * nx + (sx > 0 ? cl : nx - 1 - cl);
-              const T* src_ring = ring - (size_t)(lane - f) * D * 32;
-#pragma unroll
-              for (int d = 0; d < D; ++d) {
-                T v0, v1, v2, v3;
-                Vec4<T>::load(src_ring + d * 32 + e * 4, v0, v1, v2, v3);
-                if (a.psi_unique) {
-                  Vec4<T>::store(psi + (size_t)(tk.u0 + d) * in.ndof + 4 * cellf, v0, v1, v2, v3);
-                } else {
-                  const UDir u = a.udir[tk.u0 + d];
-                  for (int q = 0; q < u.ndup; ++q)
-                    Vec4<T>::store(psi + (size_t)u.dup[q] * in.ndof + 4 * cellf, v0, v1, v2, v3);
-                }
-              }
+        } else {
+          unsigned fm = __ballot_sync(0xffffffffu, flush);
+          while (fm) {
+            int fl[4], n = 0;
+            while (fm && n < 4) {
+              fl[n++] = __ffs(fm) - 1;
+              fm &= fm - 1;
+            }
+            if (k < n) {
+              const int f = fl[k];
+              const int colf = s - 32 * band - f;
+              const long long cf = cell_at(f, colf);
+              RTE_STORE_SEGMENT(f, cf, colf, e);
             }
           }
         }
