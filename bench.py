@@ -32,6 +32,7 @@ import workloads as wl  # noqa: E402
 # Arithmetic per cell and unique direction of the fused sweep (rhs assembly 8 FMA, 4x4 solve 16 FMA,
 # outflow traces 4 FMA, quadrature 4 FMA).
 SWEEP_FLOPS_PER_CELL_DIR = 64
+SWEEP32_DRAM_BYTES_64x64 = 108032   # dram__bytes_read.sum + dram__bytes_write.sum, one launch (ncu)
 # ALU peaks from the unit counts and the maximum SM clock (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz);
 # FP64: GB300 nominal 1.25 TFLOP/s.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -418,7 +419,9 @@ def main():
         roof = {"kernel": "k_sweep2d<double> (A~ apply, FP64)", "bound": "alu",
                 "achieved": flops / (ms64 * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    # DRAM bytes per launch of the FP32 sweep kernel from one ncu capture of this workload
+    # (profiles/sweep_band_f32_square2d_64.md); none recorded for the FP64 kernel
+    roof["traffic"] = SWEEP32_DRAM_BYTES_64x64 if roof["unit"] == "TFLOP/s" and "float" in roof["kernel"] else None
     # angular-output sweep (rte_sweep, FP32) on the batched 256-instance problem: HBM-bound write of
     # N_Omega * N_dof * 4 bytes; this is the sweep GB/s of the metric
     sweep_hbm = measure_sweep_hbm(RB, torch, dev, stream, flush) if not args.no_sweep_hbm else None
