@@ -155,6 +155,17 @@ struct RomSel<float> {
   __device__ static const float* WT(const RomInstDev& R) { return R.WT32; }
 };
 
+// four consecutive values from a 16-byte aligned address
+__device__ __forceinline__ void load4(const float* p, float& a, float& b, float& c, float& d) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  a = v.x; b = v.y; c = v.z; d = v.w;
+}
+__device__ __forceinline__ void load4(const double* p, double& a, double& b, double& c, double& d) {
+  const double2 v0 = reinterpret_cast<const double2*>(p)[0];
+  const double2 v1 = reinterpret_cast<const double2*>(p)[1];
+  a = v0.x; b = v0.y; c = v1.x; d = v1.y;
+}
+
 template <typename TV>
 __device__ __forceinline__ TV warp_sum_t(TV v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -335,7 +346,8 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
   const long long ntot = A.ntot;
   __shared__ TV sl[260];          // chunk dot products (phase A) / instance sums (phase B)
   __shared__ TV hsv[132];
-  __shared__ TV wsh[256], vjsh[256];
+  __shared__ __align__(16) TV wsh[256];
+  __shared__ __align__(16) TV vjsh[256];
   __shared__ TV red[8][128];
   __shared__ TV ys[64];
   __shared__ TV css[128], sns[128];
@@ -366,12 +378,16 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
     // taken four at a time with the index clamped to j (the surplus results are not stored), so every
     // batch issues all of its loads before the first use and there is no remainder loop.
     for (int k0 = warp; k0 <= j; k0 += 32) {
+      // lane l reads dofs 4l..4l+3 and 128+4l..128+4l+3 of the chunk as two 4-wide loads (chunk
+      // offsets and instance sizes are multiples of 4); surplus lanes re-read valid dofs and meet zeros
       TV x[4][8];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const TV* vk = A.V + (size_t)min(k0 + 8 * u, j) * ntot + in.off + i0;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) x[u][e] = vk[min(lane + 32 * e, nvalid - 1)];   // surplus lanes meet zeros
+        for (int h = 0; h < 2; ++h)
+          load4(vk + min(4 * lane + 128 * h, nvalid - 4), x[u][4 * h], x[u][4 * h + 1], x[u][4 * h + 2],
+                x[u][4 * h + 3]);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -379,8 +395,9 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
         TV a = 0, gg = 0;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          a += x[u][e] * wsh[lane + 32 * e];
-          gg += x[u][e] * vjsh[lane + 32 * e];
+          const int ii = 4 * lane + 128 * (e >> 2) + (e & 3);
+          a += x[u][e] * wsh[ii];
+          gg += x[u][e] * vjsh[ii];
         }
         a = warp_sum_t(a);
         gg = warp_sum_t(gg);
@@ -507,7 +524,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
     if (ok) {
       wi = A.V[(size_t)(j + 1) * ntot + in.off + i];
       // batches of U vectors, index clamped to j and the surplus terms selected away: no remainder loop
-      constexpr int U = sizeof(TV) == 4 ? 16 : 8;
+      constexpr int U = sizeof(TV) == 4 ? 32 : 8;
       for (int k0 = 0; k0 <= j; k0 += U) {
         TV x[U];
 #pragma unroll
