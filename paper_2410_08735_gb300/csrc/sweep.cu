@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
     for (int e = threadIdx.x; e < R; e += blockDim.x) sgs[e] = reinterpret_cast<const T*>(a.sig_s)[(size_t)tk.b * R + e];
   const int cx = nx / a.rx, cy = ny / a.ry;
   for (int e = threadIdx.x; e < nx; e += blockDim.x) xreg[e] = e / cx;
-  T al[D], be[D], wg[D];
+  T al[D], be[D], wg[D], wg1[D], wg2[D], wg3[D];
   const int sx = a.udir[tk.u0].sx, sy = a.udir[tk.u0].sy;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
@@ -387,6 +387,10 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
     al[d] = (T)(u.ax / in.hx);
     be[d] = (T)(u.ay / in.hy);
     wg[d] = (T)u.w;
+    // quadrature weights with the reflection signs of the odd modes folded in
+    wg1[d] = sx > 0 ? wg[d] : -wg[d];
+    wg2[d] = sy > 0 ? wg[d] : -wg[d];
+    wg3[d] = sx * sy > 0 ? wg[d] : -wg[d];
   }
   const T bnd = a.with_bc ? (T)(a.g * sqrt(in.hx * in.hy)) : (T)0;
   const bool sig_s = a.sig_s != nullptr;
@@ -428,7 +432,7 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
   T tx0[D], tx1[D], ty0[D], ty1[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) { tx0[d] = tx1[d] = ty0[d] = ty1[d] = (T)0; }
-  constexpr int PF = 4;
+  constexpr int PF = 8;
   TI q0[PF], q1[PF], q2[PF], q3[PF];
 #pragma unroll
   for (int k = 0; k < PF; ++k) {
@@ -504,9 +508,9 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
           ty0[d] = p0 + S3 * p2;
           ty1[d] = p1 + S3 * p3;
           acc0 += wg[d] * p0;
-          acc1 += wg[d] * p1;
-          acc2 += wg[d] * p2;
-          acc3 += wg[d] * p3;
+          acc1 += wg1[d] * p1;
+          acc2 += wg2[d] * p2;
+          acc3 += wg3[d] * p3;
           if (lane == 31 && band + 1 < nb) {
             T* yb = ybuf + (size_t)band * D * nx * 2;
             yb[(d * nx + col) * 2] = ty0[d];
@@ -517,9 +521,6 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
             Vec4<T>::store(ring + d * 32 + (col & 7) * 4, p0, q1, q2, q3);
           }
         }
-        acc1 = sx > 0 ? acc1 : -acc1;
-        acc2 = sy > 0 ? acc2 : -acc2;
-        acc3 = (sx * sy) > 0 ? acc3 : -acc3;
         Vec4<T>::store(part + 4 * c, acc0, acc1, acc2, acc3);
       }
       if (ANG) {
