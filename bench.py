@@ -202,9 +202,11 @@ def run_reference(args, spec, B, world, rank):
 
 
 # ------------------------------------------------------------------ GPU legs
-def measure_sweep_hbm(RB, torch, dev, stream, flush, reps=5):
-    spec3 = wl.config(3)
-    ss, sa = wl.draw_params(spec3, spec3.n_instances, wl.seed_for(3, 1))
+def measure_sweep_hbm(RB, torch, dev, stream, flush, reps=5, config=3):
+    """Angular-output sweep (rte_sweep, FP32) over a whole batched workload: an HBM-bound write of
+    N_Omega * N_dof * 4 bytes (both duplicate directions stored), timed with CUDA events after warm-up."""
+    spec3 = wl.config(config)
+    ss, sa = wl.draw_params(spec3, spec3.n_instances, wl.seed_for(config, 1))
     prob = RB.Problem(spec3, ss, sa)
     n = prob.n_dof
     src = torch.randn(n, dtype=torch.float32, device=dev)
@@ -226,10 +228,18 @@ def measure_sweep_hbm(RB, torch, dev, stream, flush, reps=5):
     nbytes = prob.n_directions * n * 4 + n * 4
     peak = measured_peaks().get("hbm_gbs", 6800.0)
     cells = sum(nx * ny for nx, ny in zip(spec3.nx, spec3.ny))
-    return {"workload": "batch256_uneven (96x32^2, 96x64^2, 64x128^2; 128 directions)", "kernel": "k_sweep2d (angular output, FP32)",
-            "bytes": nbytes, "ms": ms, "achieved_gbs": nbytes / (ms * 1e-3) / 1e9, "peak_gbs": peak,
-            "frac": nbytes / (ms * 1e-3) / 1e9 / peak,
-            "alu_tflops": SWEEP_FLOPS_PER_CELL_DIR * cells * prob.info.n_unique_directions / (ms * 1e-3) / 1e12}
+    meshes = {}
+    for nx, ny in zip(spec3.nx, spec3.ny):
+        meshes[f"{nx}x{ny}"] = meshes.get(f"{nx}x{ny}", 0) + 1
+    desc = ", ".join(f"{c}x{m}" for m, c in meshes.items())
+    out = {"workload": f"{spec3.name} ({desc}; {prob.n_directions} directions, {spec3.n_regions} regions)",
+           "kernel": "k_sweep2d / k_sweep2d_bands (angular output, FP32; autotuned)",
+           "bytes": nbytes, "ms": ms, "achieved_gbs": nbytes / (ms * 1e-3) / 1e9, "peak_gbs": peak,
+           "frac": nbytes / (ms * 1e-3) / 1e9 / peak,
+           "alu_tflops": SWEEP_FLOPS_PER_CELL_DIR * cells * prob.info.n_unique_directions / (ms * 1e-3) / 1e12}
+    del psi
+    torch.cuda.empty_cache()
+    return out
 
 
 def measure_batched(RB, torch, dev, stream, flush, args, reps=1):
@@ -454,6 +464,9 @@ def main():
     # angular-output sweep (rte_sweep, FP32) on the batched 256-instance problem: HBM-bound write of
     # N_Omega * N_dof * 4 bytes; this is the sweep GB/s of the metric
     sweep_hbm = measure_sweep_hbm(RB, torch, dev, stream, flush) if not args.no_sweep_hbm else None
+    if sweep_hbm is not None and world == 1:
+        # the largest workload (64 x 256^2, 192 directions, 8x8 regions): 12.9 GB of angular output
+        sweep_hbm["large"] = measure_sweep_hbm(RB, torch, dev, stream, flush, reps=3, config=5)
     batched = measure_batched(RB, torch, dev, stream, flush, args) if not args.no_batched and world == 1 else None
     roof["ms_per_launch_fp32"] = ms32
     roof["ms_per_launch_fp64"] = ms64

@@ -98,3 +98,30 @@ def test_batch256_mixed_solve_true_residual_by_oracle():
         bt = OT.rhs_btilde(op)
         r = bt - OT.Atilde_apply(op, h[off[b]:off[b + 1]])
         assert np.linalg.norm(r) / np.linalg.norm(bt) <= 1.05e-8, b
+
+
+def test_large256_angular_sweep_fp32_sampled():
+    """The largest workload's angular sweep (64 x 256^2, 192 directions, 8x8 regions; 12.9 GB of FP32
+    output), as the HBM measurement runs it: sampled (instance, direction) blocks against the oracle."""
+    torch = torch_cuda()
+    B = lib()
+    spec = wl.config(5)
+    ss, sa = wl.draw_params(spec, spec.n_instances, wl.seed_for(5, 1))
+    gp = B.Problem(spec, ss, sa)
+    off = [int(x) for x in gp.offsets]
+    ndir = gp.n_directions
+    s = np.random.default_rng(33).standard_normal(gp.n_dof).astype(np.float32)
+    psi = torch.empty(ndir * gp.n_dof, dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        gp.sweep(to_dev(s), psi, with_bc=True)
+    torch.cuda.synchronize()
+    for b in (0, 63):
+        op = _oracle(spec, ss, sa, b)
+        n = off[b + 1] - off[b]
+        sb = s[off[b]:off[b + 1]].astype(np.float64)
+        blk = psi[ndir * off[b]:ndir * off[b + 1]].view(ndir, n)
+        for j in (0, 95, 96, ndir - 1):
+            ref = op.sweep(j, sb + op.gbc(j))
+            assert rel(blk[j].cpu().numpy(), ref) < 2e-5, (b, j)
+    del psi
+    torch.cuda.empty_cache()
