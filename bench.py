@@ -170,7 +170,8 @@ def bench_config(args, spec, B):
     """The workload description both arms print (no model keys: the workload is named by its sizes)."""
     return {"workload": args.workload, "instances_per_step": B, "mesh": f"{spec.nx[0]}x{spec.ny[0]}",
             "directions": spec.n_directions, "restart": args.restart,
-            "preconditioner": f"ROMSAD rank {spec.rom_rank} (window {spec.window}, kept after the window)",
+            "preconditioner": f"ROMSAD rank {getattr(args, 'rom_rank', 0) or spec.rom_rank} (window {spec.window}, kept after "
+                              f"the window)",
             "warm_start": "MLP 8-128-128-r (mixed path only)",
             "l2": "flushed (256 MiB write) before every timed step"}
 
@@ -320,6 +321,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-train", type=int, default=16)
     ap.add_argument("--batched-rank", type=int, default=16)
+    ap.add_argument("--rom-rank", type=int, default=0, help="ROM rank cap (0: the workload's)")
     ap.add_argument("--ref-sample", type=int, default=40, help="oracle FGMRES iterations per reference step")
     ap.add_argument("--ref-iters", type=int, default=180,
                     help="iterations of a full solve for the extrapolation (the FP64 FGMRES-ROMSAD solve of this "
@@ -353,8 +355,9 @@ def main():
     t_off = time.perf_counter()
     tr_ss, tr_sa = wl.draw_params(spec, spec.n_train, wl.seed_for(2, 0))
     tmpl = RB.Problem(spec.with_instances(spec.nx[:1], spec.ny[:1]), tr_ss[:1], tr_sa[:1])
-    rom, rep = RB.Rom.greedy(tmpl, tr_ss, tr_sa, window=spec.window, max_greedy_iter=spec.rom_rank // spec.window,
-                             max_rank=spec.rom_rank, eps_rom=0.0, hf_rtol=1e-10, hf_restart=args.restart,
+    rank_cap = args.rom_rank or spec.rom_rank
+    rom, rep = RB.Rom.greedy(tmpl, tr_ss, tr_sa, window=spec.window, max_greedy_iter=rank_cap // spec.window,
+                             max_rank=rank_cap, eps_rom=0.0, hf_rtol=1e-10, hf_restart=args.restart,
                              hf_max_iter=args.max_iter, want_labels=True, indicator_f32=True)
     t_greedy = time.perf_counter() - t_off
     net = RB.Mlp(2 * R, 128, rep["rank"], seed=2410)

@@ -447,7 +447,12 @@ int RomPlan::build(romsad* rom_, rte_problem* p, const std::vector<int>& ids_, c
   nchunk = (rom->N + chunk - 1) / chunk;
   RTE_TRY(part.ensure((size_t)n * nchunk * 64));
   RTE_TRY(c.ensure((size_t)n * 64));
-  size_t smem = (size_t)2 * rom->r * rom->r * 8;
+  size_t smem = (size_t)2 * rom->r * rom->r * 8;   // 64 KiB at the largest rank (64)
+  static size_t smem_set = 48 * 1024;
+  if (smem > smem_set) {
+    RTE_CHECK_CUDA(cudaFuncSetAttribute(k_rom_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    smem_set = smem;
+  }
   k_rom_factor<<<n, 256, smem, st>>>(rom->d_aff.p, rom->r, rom->R, p->d_sig_s.p, p->d_sig_t.p, d_ids.p, lu.p, piv.p);
   count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());

@@ -96,6 +96,44 @@ def test_romsad_apply_and_reduced_operator_match_oracle():
         assert torch.equal(z, z2)
 
 
+def test_rank64_rom_apply_and_solves():
+    """A ROM of the largest supported rank (64) from a random orthonormal basis: reduced operator and
+    ROMSAD apply against the oracle, and FP64 and mixed FGMRES-ROMSAD solves that use it (the ROM
+    coefficients then span two warps' lanes and the factorisation needs 64 KiB of shared memory)."""
+    torch = torch_cuda()
+    B = lib()
+    from oracle import Problem
+    spec = wl.config(1)
+    ts, ta = wl.draw_params(spec, 2, wl.seed_for(1, 1))
+    p0 = Problem(spec, 0, ts[0], ta[0])
+    Q, _ = np.linalg.qr(np.random.default_rng(64).standard_normal((p0.ndir * p0.ndof, 64)))
+    U = Q.T.reshape(64, p0.ndir, p0.ndof).copy()
+    orom = ORS.build_rom(p0, U)
+    spec2 = spec.with_instances([128] * 2, [1] * 2)
+    gp = B.Problem(spec2, ts, ta)
+    grom = B.Rom.from_basis(gp, U, instance=0)
+    assert grom.rank == 64
+    for b in range(2):
+        A_gpu = grom.reduced_operator(ts[b], ta[b])
+        A_ref = ORS.reduced_operator(orom, ts[b], ta[b])
+        assert np.max(np.abs(A_gpu - A_ref)) < 1e-10 * np.max(np.abs(A_ref))
+    v = np.random.default_rng(5).standard_normal(gp.n_dof)
+    z = torch.empty(gp.n_dof, dtype=torch.float64, device="cuda")
+    grom.apply(gp, to_dev(v), z)
+    zh = split(z.cpu().numpy(), gp.offsets)
+    for b in range(2):
+        q = with_params(p0, ts[b], ta[b])
+        assert rel(zh[b], ORS.romsad_apply(orom, q, split(v, gp.offsets)[b])) < 1e-11
+    ops = oracle_problems(spec2, ts, ta)
+    refs = [ORS.solve(op, None, restart=200, rtol=1e-13, max_iter=3000)[0] for op in ops]
+    for mode, tol in ((B.RTE_MODE_FP64, 1e-9), (B.RTE_MODE_MIXED, 1e-7)):
+        phi, st = _solve_gpu(B, gp, [grom, grom], restart=40, rtol=1e-10, max_iter=2000, mode=mode,
+                             inner_rtol=1e-2, max_outer=30)
+        for b in range(2):
+            assert st[b]["status"] == 0
+            assert rel(split(phi, gp.offsets)[b], refs[b]) < tol
+
+
 def test_fgmres_romsad_fp64_slab_matches_oracle():
     """FP64 FGMRES-ROMSAD on the 1D slab workload (128 cells, S16, rank <= 10 ROM from 20 training
     parameters): phi within 1e-10 of the oracle, iteration counts within 1."""
