@@ -245,31 +245,41 @@ def measure_sweep_hbm(RB, torch, dev, stream, flush, reps=5, config=3):
 
 def measure_batched(RB, torch, dev, stream, flush, args, reps=1):
     """Batched throughput: the 256-instance uneven workload solved by one fgmres_solve call per batch,
-    mixed (FP32 sweeps) vs FP64, each mesh group preconditioned by its own greedy ROM."""
+    mixed (FP32 inner solves) with the learned warm start vs plain FP64, each mesh group preconditioned by
+    its own greedy ROM, whose labels train that group's MLP (offline, untimed)."""
     spec3 = wl.config(3)
     R = spec3.n_regions
     B = spec3.n_instances
     ss, sa = wl.draw_params(spec3, B, wl.seed_for(3, 1))
     prob = RB.Problem(spec3, ss, sa)
     t0 = time.perf_counter()
-    roms = {}
+    roms, nets, losses = {}, {}, {}
     tr_ss, tr_sa = wl.draw_params(spec3, args.batched_train, wl.seed_for(3, 0))
+    feats = np.concatenate([tr_ss, tr_sa], axis=1)
     for n in sorted(set(spec3.nx)):
         sp = spec3.with_instances([n], [n])
         tmpl = RB.Problem(sp, tr_ss[:1], tr_sa[:1])
         rom, rep = RB.Rom.greedy(tmpl, tr_ss, tr_sa, window=spec3.window, max_greedy_iter=args.batched_rank // 2,
                                  max_rank=args.batched_rank, eps_rom=0.0, hf_rtol=1e-8, hf_restart=args.restart,
-                                 hf_max_iter=args.max_iter, indicator_f32=True)
-        roms[n] = rom
+                                 hf_max_iter=args.max_iter, want_labels=True, indicator_f32=True)
+        net = RB.Mlp(2 * R, 128, rep["rank"], seed=2410 + n)
+        losses[n] = net.train(feats, rep["labels"], epochs=args.mlp_epochs, batch=min(64, len(feats)), lr=2e-3,
+                              bf16=True)
+        RB.attach_mlp(rom, net)
+        roms[n], nets[n] = rom, net
     t_off = time.perf_counter() - t0
     rl = [roms[n] for n in spec3.nx]
     phi = torch.zeros(prob.n_dof, dtype=torch.float64, device=dev)
     out = {"workload": "batch256_uneven: 96x32^2 + 96x64^2 + 64x128^2, 128 directions, one solve call per batch",
-           "instances": B, "rom_rank": args.batched_rank, "offline_s": t_off}
-    for name, mode in (("mixed", RB.RTE_MODE_MIXED), ("fp64", RB.RTE_MODE_FP64)):
+           "instances": B, "rom_rank": args.batched_rank, "training_draws": args.batched_train, "offline_s": t_off,
+           "mlp_final_loss": {f"{n}x{n}": v for n, v in losses.items()}}
+    # "mixed": FP32 inner solves + MLP warm start (the batched form of the method); "mixed_plain_romsad":
+    # the same without the warm start; "fp64": plain FP64 FGMRES-ROMSAD
+    for name, mode, learned in (("mixed", RB.RTE_MODE_MIXED, True), ("mixed_plain_romsad", RB.RTE_MODE_MIXED, False),
+                                ("fp64", RB.RTE_MODE_FP64, False)):
         RB.fgmres_solve(prob, rl, phi, restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec3.window,
                         mode=mode, inner_rtol=args.inner_rtol, max_outer=30, stream=stream,
-                        raise_on_fail=False)   # warm-up / tuning
+                        raise_on_fail=False, learned_warm_start=learned)   # warm-up / tuning
         times, st_all = [], []
         for _ in range(reps):
             flush.zero_()
@@ -279,7 +289,7 @@ def measure_batched(RB, torch, dev, stream, flush, args, reps=1):
             e0.record(stream)
             st = RB.fgmres_solve(prob, rl, phi, restart=args.restart, rtol=1e-8, max_iter=args.max_iter,
                                  window=spec3.window, mode=mode, inner_rtol=args.inner_rtol, max_outer=30,
-                                 stream=stream, raise_on_fail=False)
+                                 stream=stream, raise_on_fail=False, learned_warm_start=learned)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -319,9 +329,12 @@ def main():
     ap.add_argument("--mlp-epochs", type=int, default=300)
     ap.add_argument("--no-sweep-hbm", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--batched-train", type=int, default=16)
-    ap.add_argument("--batched-rank", type=int, default=16)
+    ap.add_argument("--batched-train", type=int, default=32)
+    ap.add_argument("--batched-rank", type=int, default=32)
     ap.add_argument("--rom-rank", type=int, default=0, help="ROM rank cap (0: the workload's)")
+    ap.add_argument("--n-train", type=int, default=1024,
+                    help="training draws of the greedy and the MLP (2048 leaves the network less trained in the "
+                         "same epoch budget)")
     ap.add_argument("--ref-sample", type=int, default=40, help="oracle FGMRES iterations per reference step")
     ap.add_argument("--ref-iters", type=int, default=180,
                     help="iterations of a full solve for the extrapolation (the FP64 FGMRES-ROMSAD solve of this "
@@ -353,7 +366,8 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     # offline (untimed): greedy ROM on the training draws, MLP trained on its labels
     t_off = time.perf_counter()
-    tr_ss, tr_sa = wl.draw_params(spec, spec.n_train, wl.seed_for(2, 0))
+    n_train = args.n_train or spec.n_train
+    tr_ss, tr_sa = wl.draw_params(spec, n_train, wl.seed_for(2, 0))
     tmpl = RB.Problem(spec.with_instances(spec.nx[:1], spec.ny[:1]), tr_ss[:1], tr_sa[:1])
     rank_cap = args.rom_rank or spec.rom_rank
     rom, rep = RB.Rom.greedy(tmpl, tr_ss, tr_sa, window=spec.window, max_greedy_iter=rank_cap // spec.window,
@@ -362,19 +376,19 @@ def main():
     t_greedy = time.perf_counter() - t_off
     net = RB.Mlp(2 * R, 128, rep["rank"], seed=2410)
     mlp_loss = net.train(np.concatenate([tr_ss, tr_sa], axis=1), rep["labels"], epochs=args.mlp_epochs,
-                         batch=min(64, spec.n_train), lr=2e-3, bf16=True)
+                         batch=min(64, n_train), lr=2e-3, bf16=True)
     RB.attach_mlp(rom, net)
     t_offline = time.perf_counter() - t_off
     roms = [rom] * B
     common = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window, stream=stream)
 
-    def solve(mode):
+    def solve(mode, learned=True):
         if mode == RB.RTE_MODE_MIXED:
             return RB.fgmres_solve(prob, roms, phi, mode=mode, inner_rtol=args.inner_rtol, max_outer=30,
-                                   learned_warm_start=True, **common)
+                                   learned_warm_start=learned, **common)
         return RB.fgmres_solve(prob, roms, phi, mode=mode, true_residual_check=True, **common)
 
-    def timed_loop(mode):
+    def timed_loop(mode, learned=True):
         per_step, stats_all = [], []
         for s in range(n_sets):
             ss, sa = params(s)
@@ -384,7 +398,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st = solve(mode)
+            st = solve(mode, learned)
             e1.record(stream)
             torch.cuda.synchronize()
             if s >= args.warmup:
@@ -404,11 +418,14 @@ def main():
     torch.cuda.nvtx.range_push("timed_fp64")
     t_fp64, st_fp64 = timed_loop(RB.RTE_MODE_FP64)
     torch.cuda.nvtx.range_pop()
+    # the mixed path without the learned warm start (plain ROMSAD), for the MLP's net effect
+    t_plain, st_plain = timed_loop(RB.RTE_MODE_MIXED, learned=False)
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop()
     mixed_s = max_over_ranks(world, sum(t_mixed) / 1e3)
     fp64_s = max_over_ranks(world, sum(t_fp64) / 1e3)
+    plain_s = max_over_ranks(world, sum(t_plain) / 1e3)
     solves = args.steps * B * world
     value = solves / mixed_s
     fp64_value = solves / fp64_s
@@ -483,6 +500,8 @@ def main():
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": bench_config(args, spec, B),
         "fp64": {"value": fp64_value, "unit": "param solves/s", "ms_per_step": 1e3 * fp64_s / args.steps},
+        "mixed_plain_romsad": {"value": solves / plain_s, "unit": "param solves/s",
+                               "iterations_mean": statistics.mean(s["iterations"] for s in st_plain)},
         "speedup_mixed_vs_fp64": value / fp64_value,
         "offline": {"greedy_s": t_greedy, "total_s": t_offline, "rank": rep["rank"], "sampled": len(rep["sampled"]),
                     "mlp_final_loss": mlp_loss},

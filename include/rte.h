@@ -239,7 +239,9 @@ typedef struct fgmres_opts {
                                 finished by FP64 FGMRES from its current iterate       */
     int true_residual_check; /* FP64 mode: recompute b~ - A~ phi after convergence     */
     int warm_start;          /* 0: zero initial guess; 1: phi0; 2: learned phi0 = b~ + W c_hat(mu)
-                                from each instance's ROM MLP (instances without one start at 0) */
+                                from each instance's ROM MLP (instances without one start at 0;
+                                so does an instance whose learned start is not finite: plain
+                                ROMSAD is the fallback) */
 } fgmres_opts;
 
 typedef struct fgmres_stats {
@@ -251,6 +253,9 @@ typedef struct fgmres_stats {
     int restarts;
     int outer;               /* mixed: refinement steps                                */
     int escalated;           /* mixed: 1 if the instance was finished by FP64 FGMRES   */
+    int learned_start;       /* 1 if the learned warm start was used (warm_start = 2); 0 if
+                                the instance had no MLP or its learned start was not finite,
+                                so it started from zero (plain ROMSAD) */
     double est_rel_residual; /* last Givens estimate |g_{j+1}| / ||b~||                */
     double true_rel_residual;/* ||b~ - A~ phi||_2 / ||b~||_2 in FP64 (NaN if not computed) */
     double true_linf_residual;

@@ -75,7 +75,7 @@ class FgmresOpts(ctypes.Structure):
 class FgmresStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("sweeps", ctypes.c_int),
                 ("sweeps_fp64", ctypes.c_int), ("restarts", ctypes.c_int), ("outer", ctypes.c_int),
-                ("escalated", ctypes.c_int), ("est_rel_residual", ctypes.c_double),
+                ("escalated", ctypes.c_int), ("learned_start", ctypes.c_int), ("est_rel_residual", ctypes.c_double),
                 ("true_rel_residual", ctypes.c_double), ("true_linf_residual", ctypes.c_double)]
 
     def as_dict(self):

@@ -1687,11 +1687,45 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     }
     warm = !groups.empty();
   }
+  std::vector<int> learned(B, 0);
+  bool ro_ready = false;   // ws->ro holds b~ - A~ x for every instance
+  if (o->warm_start == 2 && warm) {
+    // The plain ROMSAD start (zero) is the fallback for an instance whose learned start is not finite.
+    // (The residual norm is no test of a learned start: it removes the slow, smooth error components
+    // that take FGMRES-ROMSAD many iterations while it can raise the residual in fast ones.)  The
+    // residual is needed by the refinement anyway (mixed mode); in FP64 mode it is one extra sweep.
+    RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ws->ro.p, true, nullptr, st));
+    std::vector<int> all1(B, 1);
+    RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, all1.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_norm<<<B, 512, 0, st>>>(ws->ro.p, p->d_inst.p, ws->active.p, ws->nrm.p);
+    count_launch();
+    std::vector<double> hr(B);
+    RTE_CHECK_CUDA(cudaMemcpyAsync(hr.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
+    RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> fallback(B, 0);
+    bool anyf = false;
+    for (int b = 0; b < B; ++b) {
+      const bool has = roms[b] && roms[b]->mlp;
+      learned[b] = has && std::isfinite(hr[b]);
+      fallback[b] = !learned[b];
+      anyf = anyf || fallback[b];
+    }
+    if (anyf) {
+      const dim3 vg = vec_grid(p);
+      RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, fallback.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+      k_zero_active<<<vg, 256, 0, st>>>(x, p->d_inst.p, ws->active.p);
+      count_launch();
+      k_copy_active<<<vg, 256, 0, st>>>(ws->ro.p, ws->bt.p, p->d_inst.p, ws->active.p);
+      count_launch();
+    }
+    ro_ready = true;
+  }
   std::vector<fgmres_stats> S(B);
   for (int b = 0; b < B; ++b) {
     std::memset(&S[b], 0, sizeof(fgmres_stats));
-    S[b].sweeps = 1;
-    S[b].sweeps_fp64 = 1;
+    S[b].sweeps = ro_ready ? 2 : 1;
+    S[b].sweeps_fp64 = ro_ready ? 2 : 1;
+    S[b].learned_start = learned[b];
     S[b].true_rel_residual = NAN;
     S[b].true_linf_residual = NAN;
   }
@@ -1714,7 +1748,9 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     const dim3 vg = vec_grid(p);
     double* ro = ws->ro.p;
     std::vector<int> act(B, 1), esc(B, 0);
-    if (warm) {
+    if (ro_ready) {
+      // residual of the (learned or zero) start already in ro, counted above
+    } else if (warm) {
       RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ro, true, nullptr, st));
       for (int b = 0; b < B; ++b) { S[b].sweeps += 1; S[b].sweeps_fp64 += 1; }
     } else {

@@ -109,7 +109,40 @@ def test_learned_warm_start_reduces_iterations():
     it0 = sum(s["iterations"] for s in st0)
     it1 = sum(s["iterations"] for s in st1)
     assert it1 < it0, (it0, it1)
+    assert all(s["learned_start"] == 1 for s in st1)
     p0 = Problem(spec, 0, ss[0], sa[0])
     for b in range(nt):
         ref, _ = ORS.solve(with_params(p0, ts[b], ta[b]), None, restart=200, rtol=1e-13, max_iter=5000)
         assert rel(split(phi1.cpu().numpy(), tp.offsets)[b], ref) < 1e-8
+
+
+def test_non_finite_learned_start_falls_back_to_plain_romsad():
+    """A network whose outputs are not finite (NaN weights): every instance starts from zero instead
+    (plain ROMSAD) and reports learned_start = 0; the solve then takes exactly the iterations of the zero
+    start and gives the same phi."""
+    torch = torch_cuda()
+    B = lib()
+    spec = spec2d([16], [16], n_polar=2, n_azim=8)
+    ss, sa = wl.draw_params(spec, 24, 43)
+    ss = np.minimum(ss, 100.0)
+    gp = B.Problem(spec, ss[:1], sa[:1])
+    rom, rep = B.Rom.greedy(gp, ss, sa, window=2, max_greedy_iter=4, max_rank=8, eps_rom=0.0, hf_rtol=1e-12,
+                            hf_restart=128, hf_max_iter=4000, want_labels=True)
+    net = B.Mlp(2 * spec.n_regions, 128, rep["rank"], seed=3)
+    flat = net.get_params()[0]
+    net.set_params(np.full(flat.shape, np.nan))
+    B.attach_mlp(rom, net)
+    nt = 3
+    ts, ta = wl.draw_params(spec, nt, 44)
+    ts = np.minimum(ts, 100.0)
+    tp = B.Problem(spec.with_instances([16] * nt, [16] * nt), ts, ta)
+    for mode in (B.RTE_MODE_FP64, B.RTE_MODE_MIXED):
+        phi0 = torch.zeros(tp.n_dof, dtype=torch.float64, device="cuda")
+        phi1 = torch.zeros_like(phi0)
+        common = dict(restart=100, rtol=1e-10, max_iter=3000, window=2, mode=mode, inner_rtol=1e-2, max_outer=30)
+        st0 = B.fgmres_solve(tp, [rom] * nt, phi0, **common)
+        st1 = B.fgmres_solve(tp, [rom] * nt, phi1, learned_warm_start=True, **common)
+        for b in range(nt):
+            assert st1[b]["learned_start"] == 0
+            assert st1[b]["iterations"] == st0[b]["iterations"]
+        assert rel(phi1.cpu().numpy(), phi0.cpu().numpy()) < 1e-12
