@@ -382,13 +382,13 @@ def main():
     roms = [rom] * B
     common = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window, stream=stream)
 
-    def solve(mode, learned=True):
+    def solve(mode, learned=True, slot=False):
         if mode == RB.RTE_MODE_MIXED:
             return RB.fgmres_solve(prob, roms, phi, mode=mode, inner_rtol=args.inner_rtol, max_outer=30,
-                                   learned_warm_start=learned, **common)
+                                   learned_warm_start=learned, learned_slot=slot, **common)
         return RB.fgmres_solve(prob, roms, phi, mode=mode, true_residual_check=True, **common)
 
-    def timed_loop(mode, learned=True):
+    def timed_loop(mode, learned=True, slot=False):
         per_step, stats_all = [], []
         for s in range(n_sets):
             ss, sa = params(s)
@@ -398,7 +398,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st = solve(mode, learned)
+            st = solve(mode, learned, slot)
             e1.record(stream)
             torch.cuda.synchronize()
             if s >= args.warmup:
@@ -420,12 +420,15 @@ def main():
     torch.cuda.nvtx.range_pop()
     # the mixed path without the learned warm start (plain ROMSAD), for the MLP's net effect
     t_plain, st_plain = timed_loop(RB.RTE_MODE_MIXED, learned=False)
+    # the mixed path with the learned correction in the ROMSAD slot instead of the learned start
+    t_slot, st_slot = timed_loop(RB.RTE_MODE_MIXED, learned=False, slot=True)
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop()
     mixed_s = max_over_ranks(world, sum(t_mixed) / 1e3)
     fp64_s = max_over_ranks(world, sum(t_fp64) / 1e3)
     plain_s = max_over_ranks(world, sum(t_plain) / 1e3)
+    slot_s = max_over_ranks(world, sum(t_slot) / 1e3)
     solves = args.steps * B * world
     value = solves / mixed_s
     fp64_value = solves / fp64_s
@@ -502,6 +505,8 @@ def main():
         "fp64": {"value": fp64_value, "unit": "param solves/s", "ms_per_step": 1e3 * fp64_s / args.steps},
         "mixed_plain_romsad": {"value": solves / plain_s, "unit": "param solves/s",
                                "iterations_mean": statistics.mean(s["iterations"] for s in st_plain)},
+        "mixed_learned_slot": {"value": solves / slot_s, "unit": "param solves/s",
+                               "iterations_mean": statistics.mean(s["iterations"] for s in st_slot)},
         "speedup_mixed_vs_fp64": value / fp64_value,
         "offline": {"greedy_s": t_greedy, "total_s": t_offline, "rank": rep["rank"], "sampled": len(rep["sampled"]),
                     "mlp_final_loss": mlp_loss},

@@ -242,6 +242,10 @@ typedef struct fgmres_opts {
                                 from each instance's ROM MLP (instances without one start at 0;
                                 so does an instance whose learned start is not finite: plain
                                 ROMSAD is the fallback) */
+    int learned_slot;        /* 1: with a zero start, the first ROMSAD apply takes its reduced
+                                coefficients from each instance's ROM MLP (c_hat(mu) / ||b~||)
+                                instead of the reduced solve (instances without an MLP, or with a
+                                non-finite prediction, keep the plain apply)               */
 } fgmres_opts;
 
 typedef struct fgmres_stats {
@@ -256,6 +260,7 @@ typedef struct fgmres_stats {
     int learned_start;       /* 1 if the learned warm start was used (warm_start = 2); 0 if
                                 the instance had no MLP or its learned start was not finite,
                                 so it started from zero (plain ROMSAD) */
+    int learned_slot;        /* 1 if the learned ROMSAD-slot correction was used            */
     double est_rel_residual; /* last Givens estimate |g_{j+1}| / ||b~||                */
     double true_rel_residual;/* ||b~ - A~ phi||_2 / ||b~||_2 in FP64 (NaN if not computed) */
     double true_linf_residual;

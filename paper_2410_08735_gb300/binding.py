@@ -69,13 +69,14 @@ class FgmresOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("window", ctypes.c_int), ("post_mode", ctypes.c_int), ("mode", ctypes.c_int),
                 ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int),
-                ("true_residual_check", ctypes.c_int), ("warm_start", ctypes.c_int)]
+                ("true_residual_check", ctypes.c_int), ("warm_start", ctypes.c_int), ("learned_slot", ctypes.c_int)]
 
 
 class FgmresStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("sweeps", ctypes.c_int),
                 ("sweeps_fp64", ctypes.c_int), ("restarts", ctypes.c_int), ("outer", ctypes.c_int),
-                ("escalated", ctypes.c_int), ("learned_start", ctypes.c_int), ("est_rel_residual", ctypes.c_double),
+                ("escalated", ctypes.c_int), ("learned_start", ctypes.c_int), ("learned_slot", ctypes.c_int),
+                ("est_rel_residual", ctypes.c_double),
                 ("true_rel_residual", ctypes.c_double), ("true_linf_residual", ctypes.c_double)]
 
     def as_dict(self):
@@ -440,7 +441,7 @@ def attach_mlp(rom: "Rom", mlp: Optional[Mlp]):
 def fgmres_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi, phi0=None, restart=30,
                  rtol=1e-10, max_iter=1000, window=2, post_mode=RTE_POST_ROM, mode=RTE_MODE_FP64,
                  inner_rtol=1e-2, max_outer=20, true_residual_check=True, stream=None, raise_on_fail=True,
-                 learned_warm_start=False):
+                 learned_warm_start=False, learned_slot=False):
     """FGMRES-ROMSAD for all instances; phi: FP64 device tensor or host (numpy/pinned) buffer.
 
     Returns the list of per-instance stats dicts.
@@ -448,7 +449,7 @@ def fgmres_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi,
     B = problem.spec.n_instances
     ws = 2 if learned_warm_start else int(phi0 is not None)
     o = FgmresOpts(restart, rtol, max_iter, window, post_mode, mode, inner_rtol, max_outer,
-                   int(true_residual_check), ws)
+                   int(true_residual_check), ws, int(learned_slot))
     st = (FgmresStats * B)()
     if roms is None:
         rarr = None

@@ -173,10 +173,13 @@ __device__ __forceinline__ TV warp_sum_t(TV v) {
 }
 
 // z = M_ROM^{-1} v = v + W (U^T A_mu U)^{-1} P^T Sigma_s v for instances with a ROM, z = v otherwise.
+// slot (null: none): instances with slot[b] = 1 take the reduced coefficients from slot_c [B][64]
+// instead of the reduced solve (the learned correction in the ROMSAD slot).
 template <typename TV>
 __global__ void __launch_bounds__(256) k_precond_coop(int B, const int2* items, int nitems, const InstInfo* inst,
                                                       const int* active, const RomInstDev* ri, const TV* sig_dof,
-                                                      const TV* v, TV* z, TV* rpart, TV* rc, int nchunk) {
+                                                      const TV* v, TV* z, TV* rpart, TV* rc, int nchunk,
+                                                      const int* slot, const TV* slot_c) {
   namespace cg = cooperative_groups;
   cg::grid_group grid = cg::this_grid();
   __shared__ TV red[8][64];
@@ -236,6 +239,10 @@ __global__ void __launch_bounds__(256) k_precond_coop(int B, const int2* items, 
   // phase 2: c = (U^T A_mu U)^{-1} (sum of the partials) per instance; warp w sums chunks w, w+8, ...
   for (int b = blockIdx.x; b < B; b += gridDim.x) {
     if (!active[b] || !ri[b].has) continue;
+    if (slot && slot[b]) {
+      if (threadIdx.x < 64) rc[(size_t)b * 64 + threadIdx.x] = slot_c[(size_t)b * 64 + threadIdx.x];
+      continue;
+    }
     const RomInstDev R = ri[b];
     const int nch = (inst[b].ndof + 255) / 256;
     for (int q = lane; q < 64; q += 32) {
@@ -1069,6 +1076,10 @@ struct Ws {
   DevBuf<double> bnorm, beta, est, nrm;
   DevBuf<int> active, brk, flag, kcols, iters_left, list;
   DevBuf<double> rom_y, rom_c;
+  // learned ROMSAD slot: per-instance flag and coefficients c_hat / beta (FP64 and FP32)
+  DevBuf<int> slot;
+  DevBuf<double> slot_c;
+  DevBuf<float> slot_c32;
   int* hflag = nullptr;   // pinned host mirrors of flag and kcols
   int* hk = nullptr;
   ~Ws() {
@@ -1157,6 +1168,9 @@ struct Ws {
     RTE_TRY(list.alloc(B));
     RTE_TRY(rom_y.alloc((size_t)B * 64));
     RTE_TRY(rom_c.alloc((size_t)B * 64));
+    RTE_TRY(slot.alloc(B));
+    RTE_TRY(slot_c.alloc((size_t)B * 64));
+    RTE_TRY(slot_c32.alloc((size_t)B * 64));
     if (hflag) cudaFreeHost(hflag);
     if (hk) cudaFreeHost(hk);
     RTE_CHECK_CUDA(cudaMallocHost(&hflag, B * sizeof(int)));
@@ -1178,6 +1192,7 @@ struct SolveCtx {
   FirstCycle* rec = nullptr;          // records the first cycle of instance 0 (greedy high-fidelity solve)
   std::vector<RomPlan>* plans = nullptr;  // one per ROM group (factored once per solve)
   std::vector<int> no_rom_mask;       // [B] 1 for instances without a ROM
+  bool slot_pending = false;          // the next first-cycle preconditioner apply uses the learned slot
 };
 
 
@@ -1299,6 +1314,8 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
     const int kCheck = 8;
     *W.h_rtol = rtol;
     RTE_CHECK_CUDA(cudaMemcpyAsync(W.d_rtol.p, W.h_rtol, sizeof(double), cudaMemcpyHostToDevice, st));
+    // the learned ROMSAD slot replaces the reduced solve of the first preconditioner apply of the solve
+    const bool slot_now = C.slot_pending && W.withZ;
     for (int j = 0; j < m; ++j) {
       const int jg = it_first + j + 1;   // lock-step instances share the global iteration index
       const bool use_rom = W.withZ && (jg <= C.window || C.post == RTE_POST_ROM);
@@ -1319,7 +1336,15 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
             const TV* v_p = vj;
             TV* rp_p = reinterpret_cast<TV*>(W.rpart.p);
             TV* rc_p = reinterpret_cast<TV*>(W.rc.p);
-            void* args[] = {&Bv, &it_p, &nit, &inst_p, &act_p, &ri_p, &sd_p, &v_p, &zj, &rp_p, &rc_p, &nch};
+            const bool sl = slot_now && j == 0;
+            const int* sl_p = sl ? W.slot.p : nullptr;
+            const TV* slc_p = nullptr;
+            if (sl) {
+              if constexpr (f64) slc_p = W.slot_c.p;
+              else slc_p = W.slot_c32.p;
+            }
+            void* args[] = {&Bv, &it_p, &nit, &inst_p, &act_p, &ri_p, &sd_p, &v_p, &zj, &rp_p, &rc_p, &nch, &sl_p,
+                            &slc_p};
             RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_precond_coop<TV>, dim3(W.grid_pre), dim3(256),
                                                        args, 0, s));
             count_launch();
@@ -1410,7 +1435,7 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
         return RTE_OK;
       };
       const int key = j | (use_rom ? 1 << 8 : 0) | (f64 ? 1 << 9 : 0) | (C.rec ? 1 << 10 : 0) |
-                      (rom_next ? 1 << 11 : 0);
+                      (rom_next ? 1 << 11 : 0) | (slot_now && j == 0 ? 1 << 12 : 0);
       auto it = W.graphs.find(key);
       if (it == W.graphs.end()) {
         // capture this iteration once; later iterations with the same key replay it
@@ -1432,6 +1457,7 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
         add_launches(-(long long)it->second.launches);   // counted when replayed
       }
       RTE_CHECK_CUDA(cudaGraphLaunch(it->second.exec, st));
+      if (j == 0) C.slot_pending = false;
       add_launches(it->second.launches);
       if ((j + 1) % kCheck != 0 && j != m - 1) continue;
       RTE_CHECK_CUDA(cudaMemcpyAsync(W.hflag, W.flag.p, B * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1720,12 +1746,56 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     }
     ro_ready = true;
   }
+  // learned correction in the ROMSAD slot (zero start only): the first preconditioner apply takes the
+  // coefficients c_hat(mu) / ||b~|| from each instance's ROM MLP instead of the reduced solve; instances
+  // without an MLP, or whose prediction is not finite, keep the plain ROMSAD apply
+  std::vector<int> slot_used(B, 0);
+  if (o->learned_slot && roms && !warm) {
+    std::vector<int> all1(B, 1);
+    RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, all1.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_norm<<<B, 512, 0, st>>>(ws->bt.p, p->d_inst.p, ws->active.p, ws->beta.p);
+    count_launch();
+    std::vector<double> hb(B), cs((size_t)B * 64, 0.0);
+    RTE_CHECK_CUDA(cudaMemcpyAsync(hb.data(), ws->beta.p, B * 8, cudaMemcpyDeviceToHost, st));
+    std::vector<std::pair<romsad_t, int>> groups;
+    for (int b = 0; b < B; ++b)
+      if (roms[b] && roms[b]->mlp) groups.push_back({roms[b], b});
+    std::sort(groups.begin(), groups.end());
+    size_t g0 = 0;
+    while (g0 < groups.size()) {
+      size_t g1 = g0;
+      std::vector<int> ids;
+      while (g1 < groups.size() && groups[g1].first == groups[g0].first) ids.push_back(groups[g1++].second);
+      RTE_CHECK_CUDA(cudaMemcpyAsync(ws->list.p, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+      RTE_TRY(mlp_predict_instances(groups[g0].first->mlp, p, ws->list.p, ids, ws->rom_c.p, st));
+      std::vector<double> hc(ids.size() * 64);
+      RTE_CHECK_CUDA(cudaMemcpyAsync(hc.data(), ws->rom_c.p, hc.size() * 8, cudaMemcpyDeviceToHost, st));
+      RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+      for (size_t k = 0; k < ids.size(); ++k) {
+        const int b = ids[k];
+        const int r = roms[b]->r;
+        bool ok = hb[b] > 0.0 && std::isfinite(hb[b]);
+        for (int q = 0; q < r; ++q) ok = ok && std::isfinite(hc[k * 64 + q]);
+        if (!ok) continue;
+        slot_used[b] = 1;
+        for (int q = 0; q < r; ++q) cs[(size_t)b * 64 + q] = hc[k * 64 + q] / hb[b];
+      }
+      g0 = g1;
+    }
+    std::vector<float> cs32(cs.begin(), cs.end());
+    RTE_CHECK_CUDA(cudaMemcpyAsync(ws->slot.p, slot_used.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    RTE_CHECK_CUDA(cudaMemcpyAsync(ws->slot_c.p, cs.data(), cs.size() * 8, cudaMemcpyHostToDevice, st));
+    RTE_CHECK_CUDA(cudaMemcpyAsync(ws->slot_c32.p, cs32.data(), cs32.size() * 4, cudaMemcpyHostToDevice, st));
+    RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+    for (int b = 0; b < B; ++b) C.slot_pending = C.slot_pending || slot_used[b];
+  }
   std::vector<fgmres_stats> S(B);
   for (int b = 0; b < B; ++b) {
     std::memset(&S[b], 0, sizeof(fgmres_stats));
     S[b].sweeps = ro_ready ? 2 : 1;
     S[b].sweeps_fp64 = ro_ready ? 2 : 1;
     S[b].learned_start = learned[b];
+    S[b].learned_slot = slot_used[b];
     S[b].true_rel_residual = NAN;
     S[b].true_linf_residual = NAN;
   }

@@ -146,3 +146,69 @@ def test_non_finite_learned_start_falls_back_to_plain_romsad():
             assert st1[b]["learned_start"] == 0
             assert st1[b]["iterations"] == st0[b]["iterations"]
         assert rel(phi1.cpu().numpy(), phi0.cpu().numpy()) < 1e-12
+
+
+def _slot_setup(B, seed_net=11, nan=False):
+    spec = spec2d([16], [16], n_polar=2, n_azim=8)
+    ss, sa = wl.draw_params(spec, 48, 45)
+    ss = np.minimum(ss, 100.0)
+    gp = B.Problem(spec, ss[:1], sa[:1])
+    rom, rep = B.Rom.greedy(gp, ss, sa, window=2, max_greedy_iter=8, max_rank=16, eps_rom=0.0, hf_rtol=1e-12,
+                            hf_restart=128, hf_max_iter=4000, want_labels=True)
+    net = B.Mlp(2 * spec.n_regions, 128, rep["rank"], seed=seed_net)
+    if nan:
+        net.set_params(np.full(net.get_params()[0].shape, np.nan))
+    else:
+        net.train(np.concatenate([ss, sa], axis=1), rep["labels"], epochs=400, batch=48, lr=2e-3, bf16=True)
+    B.attach_mlp(rom, net)
+    return spec, ss, sa, rom
+
+
+def test_learned_romsad_slot_solves_to_the_oracle():
+    """The learned correction in the ROMSAD slot (first preconditioner apply of a zero-start solve takes
+    the MLP's coefficients instead of the reduced solve): FP64 and mixed solves reach the oracle's
+    solution, every instance reports the slot as used, and the iteration count stays close to plain
+    ROMSAD's (a perfect network would reproduce it exactly)."""
+    torch = torch_cuda()
+    B = lib()
+    spec, ss, sa, rom = _slot_setup(B)
+    nt = 4
+    ts, ta = wl.draw_params(spec, nt, 46)
+    ts = np.minimum(ts, 100.0)
+    tp = B.Problem(spec.with_instances([16] * nt, [16] * nt), ts, ta)
+    p0 = Problem(spec, 0, ss[0], sa[0])
+    refs = [ORS.solve(with_params(p0, ts[b], ta[b]), None, restart=200, rtol=1e-13, max_iter=5000)[0]
+            for b in range(nt)]
+    for mode, tol in ((B.RTE_MODE_FP64, 1e-8), (B.RTE_MODE_MIXED, 1e-7)):
+        phi0 = torch.zeros(tp.n_dof, dtype=torch.float64, device="cuda")
+        phi1 = torch.zeros_like(phi0)
+        common = dict(restart=100, rtol=1e-10, max_iter=3000, window=2, mode=mode, inner_rtol=1e-2, max_outer=30)
+        st0 = B.fgmres_solve(tp, [rom] * nt, phi0, **common)
+        st1 = B.fgmres_solve(tp, [rom] * nt, phi1, learned_slot=True, **common)
+        for b in range(nt):
+            assert st1[b]["learned_slot"] == 1 and st0[b]["learned_slot"] == 0
+            assert st1[b]["status"] == 0
+            assert abs(st1[b]["iterations"] - st0[b]["iterations"]) <= max(3, st0[b]["iterations"] // 5)
+            assert rel(split(phi1.cpu().numpy(), tp.offsets)[b], refs[b]) < tol
+
+
+def test_non_finite_learned_slot_keeps_plain_romsad():
+    """With a network whose outputs are not finite the slot falls back to the plain ROMSAD apply: the
+    solve is the plain one (same iterations, same phi) and reports learned_slot = 0."""
+    torch = torch_cuda()
+    B = lib()
+    spec, ss, sa, rom = _slot_setup(B, nan=True)
+    nt = 3
+    ts, ta = wl.draw_params(spec, nt, 47)
+    ts = np.minimum(ts, 100.0)
+    tp = B.Problem(spec.with_instances([16] * nt, [16] * nt), ts, ta)
+    for mode in (B.RTE_MODE_FP64, B.RTE_MODE_MIXED):
+        phi0 = torch.zeros(tp.n_dof, dtype=torch.float64, device="cuda")
+        phi1 = torch.zeros_like(phi0)
+        common = dict(restart=100, rtol=1e-10, max_iter=3000, window=2, mode=mode, inner_rtol=1e-2, max_outer=30)
+        st0 = B.fgmres_solve(tp, [rom] * nt, phi0, **common)
+        st1 = B.fgmres_solve(tp, [rom] * nt, phi1, learned_slot=True, **common)
+        for b in range(nt):
+            assert st1[b]["learned_slot"] == 0
+            assert st1[b]["iterations"] == st0[b]["iterations"]
+        assert rel(phi1.cpu().numpy(), phi0.cpu().numpy()) < 1e-12
