@@ -32,7 +32,7 @@ import workloads as wl  # noqa: E402
 # Arithmetic per cell and unique direction of the fused sweep (rhs assembly 8 FMA, 4x4 solve 16 FMA,
 # outflow traces 4 FMA, quadrature 4 FMA).
 SWEEP_FLOPS_PER_CELL_DIR = 64
-SWEEP32_DRAM_BYTES_64x64 = 108032   # dram__bytes_read.sum + dram__bytes_write.sum, one launch (ncu)
+SWEEP32_DRAM_BYTES_64x64 = 116480   # dram__bytes_read.sum + dram__bytes_write.sum, one launch (ncu)
 # ALU peaks from the unit counts and the maximum SM clock (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz);
 # FP64: GB300 nominal 1.25 TFLOP/s.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
