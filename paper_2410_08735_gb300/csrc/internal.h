@@ -152,6 +152,7 @@ struct rte_problem {
   int ntasks = 0, tasks_per_inst = 0;
   rte::DevBuf<int> d_active;                  // [B] instance mask (1 = active), all 1 by default
   rte::DevBuf<double> d_tmp64;                // [ntot] temporaries
+  rte::DevBuf<float> d_tmp32;                 // [2 ntot] FP32 input and output of the autotuner's timing
   rte::DevBuf<double> d_wq;                   // [ndir] quadrature weights (paper order)
   std::shared_ptr<void> krylov_ws;            // FGMRES workspace (krylov.cu), grown on demand
 };
