@@ -136,7 +136,7 @@ int rte_apply_op_noalloc(rte_problem_t p, int dtype, const void* z, void* w, voi
 typedef struct romsad* romsad_t;
 
 /* ROM from an orthonormal basis U_r given on the HOST as [r][N_Omega][N_b] doubles
- * for the mesh of instance `instance` of tmpl.  The library forms P, W and the
+ * (1 <= r <= 64) for the mesh of instance `instance` of tmpl.  The library forms P, W and the
  * affine reduced operators A_D, T_R, S_R (Sec. 4.1):
  *   U^T A_mu U = A_D + sum_R (sigma_a,R + sigma_s,R) T_R - sum_R sigma_s,R S_R. */
 int romsad_create_from_basis(rte_problem_t tmpl, int instance, int r, const double* U_host, romsad_t* out);
@@ -144,7 +144,7 @@ int romsad_create_from_basis(rte_problem_t tmpl, int instance, int r, const doub
 typedef struct romsad_greedy_opts {
     int window;           /* w: FGMRES iterations whose corrections enter the ROM (Sec. 4.3)  */
     int max_greedy_iter;  /* N_g-iter                                                         */
-    int max_rank;         /* cap on r                                                         */
+    int max_rank;         /* cap on r (at most 64)                                            */
     double eps_rom;       /* stop when max relative indicator R_mu/||eta_mu^(0)|| < eps_rom   */
     double eps_qr;        /* appendix B truncation, relative to the snapshot norm (1e-13)     */
     int mu1;              /* index of the first sample, or -1: nearest the centroid of
@@ -187,8 +187,9 @@ int romsad_destroy(romsad_t rom);
 #define RTE_POST_ROM 0       /* keep M_ROM after the window (a fixed linear operator) */
 #define RTE_POST_IDENTITY 1  /* z = v after the window                                */
 #define RTE_MODE_FP64 0      /* every sweep, MGS and least squares in FP64             */
-#define RTE_MODE_MIXED 1     /* FP64 iterative refinement around an FGMRES whose sweeps
-                                and ROM products run in FP32; MGS/Givens in FP64       */
+#define RTE_MODE_MIXED 1     /* FP64 iterative refinement (FP64 b~, residuals and update)
+                                around inner FGMRES solves that run entirely in FP32:
+                                sweeps, ROM products, Krylov basis, MGS and Givens     */
 
 /* ------------------------------------------------- learned warm start (MLP) */
 /* A small MLP maps mu = (sigma_s[R], sigma_a[R]) of an instance to the r reduced-basis
