@@ -383,7 +383,7 @@ def main():
     common = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window, stream=stream)
 
     def solve(mode, learned=True, slot=False):
-        if mode == RB.RTE_MODE_MIXED:
+        if mode in (RB.RTE_MODE_MIXED, RB.RTE_MODE_MIXED_F64KRYLOV):
             return RB.fgmres_solve(prob, roms, phi, mode=mode, inner_rtol=args.inner_rtol, max_outer=30,
                                    learned_warm_start=learned, learned_slot=slot, **common)
         return RB.fgmres_solve(prob, roms, phi, mode=mode, true_residual_check=True, **common)
@@ -422,6 +422,8 @@ def main():
     t_plain, st_plain = timed_loop(RB.RTE_MODE_MIXED, learned=False)
     # the mixed path with the learned correction in the ROMSAD slot instead of the learned start
     t_slot, st_slot = timed_loop(RB.RTE_MODE_MIXED, learned=False, slot=True)
+    # the precision form with FP64 Krylov vectors, MGS and Givens around the FP32 sweeps
+    t_f64k, st_f64k = timed_loop(RB.RTE_MODE_MIXED_F64KRYLOV)
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop()
@@ -429,6 +431,7 @@ def main():
     fp64_s = max_over_ranks(world, sum(t_fp64) / 1e3)
     plain_s = max_over_ranks(world, sum(t_plain) / 1e3)
     slot_s = max_over_ranks(world, sum(t_slot) / 1e3)
+    f64k_s = max_over_ranks(world, sum(t_f64k) / 1e3)
     solves = args.steps * B * world
     value = solves / mixed_s
     fp64_value = solves / fp64_s
@@ -507,6 +510,9 @@ def main():
                                "iterations_mean": statistics.mean(s["iterations"] for s in st_plain)},
         "mixed_learned_slot": {"value": solves / slot_s, "unit": "param solves/s",
                                "iterations_mean": statistics.mean(s["iterations"] for s in st_slot)},
+        "mixed_fp64_krylov": {"value": solves / f64k_s, "unit": "param solves/s",
+                              "iterations_mean": statistics.mean(s["iterations"] for s in st_f64k),
+                              "true_rel_residual_max": max(s["true_rel_residual"] for s in st_f64k)},
         "speedup_mixed_vs_fp64": value / fp64_value,
         "offline": {"greedy_s": t_greedy, "total_s": t_offline, "rank": rep["rank"], "sampled": len(rep["sampled"]),
                     "mlp_final_loss": mlp_loss},

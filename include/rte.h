@@ -190,6 +190,9 @@ int romsad_destroy(romsad_t rom);
 #define RTE_MODE_MIXED 1     /* FP64 iterative refinement (FP64 b~, residuals and update)
                                 around inner FGMRES solves that run entirely in FP32:
                                 sweeps, ROM products, Krylov basis, MGS and Givens     */
+#define RTE_MODE_MIXED_F64KRYLOV 2   /* the same refinement, inner solves with FP32 sweeps
+                                        (and per-direction partial fluxes) but FP64 Krylov
+                                        vectors, ROM products, MGS and Givens           */
 
 /* ------------------------------------------------- learned warm start (MLP) */
 /* A small MLP maps mu = (sigma_s[R], sigma_a[R]) of an instance to the r reduced-basis
@@ -230,7 +233,7 @@ typedef struct fgmres_opts {
     int max_iter;            /* cap on Arnoldi iterations (summed over restarts / outer steps) */
     int window;              /* w of eq. ROMSAD-preconditioner                        */
     int post_mode;           /* RTE_POST_ROM or RTE_POST_IDENTITY                      */
-    int mode;                /* RTE_MODE_FP64 or RTE_MODE_MIXED                        */
+    int mode;                /* RTE_MODE_FP64, RTE_MODE_MIXED or RTE_MODE_MIXED_F64KRYLOV */
     double inner_rtol;       /* mixed: relative target of each inner solve (1e-2 is a good
                                 default: FP32 rounding of I - T Sigma_s limits the inner
                                 solves of strongly scattering instances near 1e-3)     */

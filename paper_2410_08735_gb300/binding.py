@@ -19,7 +19,7 @@ RTE_OK = 0
 RTE_ERR_NOT_CONVERGED = 4
 RTE_F64, RTE_F32 = 0, 1
 RTE_POST_ROM, RTE_POST_IDENTITY = 0, 1
-RTE_MODE_FP64, RTE_MODE_MIXED = 0, 1
+RTE_MODE_FP64, RTE_MODE_MIXED, RTE_MODE_MIXED_F64KRYLOV = 0, 1, 2
 
 _lib = None
 

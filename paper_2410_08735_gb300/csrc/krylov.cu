@@ -1132,13 +1132,18 @@ struct Ws {
       RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_precond_coop<float>, 256, 0));
       occ = std::min(o1, o2);
       grid_pre = std::min(want, std::max(1, occ) * nsm);
-      RTE_CHECK_CUDA(
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_coop<double, double>, 256, 0));
+      // the FP64-vector grids serve both FP64 and FP32 sweeps (partials), so they take the smaller
+      // co-resident count of the two instantiations
+      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_arnoldi_coop<double, double>, 256, 0));
+      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_arnoldi_coop<float, double>, 256, 0));
+      occ = std::min(o1, o2);
       grid_post64 = std::min(want, std::max(1, occ) * nsm);
       RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_coop<float, float>, 256, 0));
       grid_post32 = std::min(want, std::max(1, occ) * nsm);
       fused = nitems <= std::min(grid_post32, grid_post64) && nchunk <= 64;
-      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_wide<double, double>, 256, 0));
+      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_arnoldi_wide<double, double>, 256, 0));
+      RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_arnoldi_wide<float, double>, 256, 0));
+      occ = std::min(o1, o2);
       grid_wide64 = std::min(want, std::max(1, occ) * nsm);
       RTE_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_arnoldi_wide<float, float>, 256, 0));
       grid_wide32 = std::min(want, std::max(1, occ) * nsm);
@@ -1213,14 +1218,17 @@ struct RunStats {
 // of the sweeps (double: FP64 solve; float: inner solve of the mixed-precision refinement).
 // true_check: recompute the residual after convergence.  it_base: iterations already done per
 // instance (window count).  max_it: per-instance iteration budget of this run.
-template <typename TV>
+template <typename TV, bool SW64>
 static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, const std::vector<int>& want,
                         double rtol, const std::vector<int>& max_it, bool true_check, const std::vector<int>& it_base,
                         RunStats& rs) {
-  constexpr bool f64 = std::is_same<TV, double>::value;
+  constexpr bool f64 = std::is_same<TV, double>::value;   // Krylov vectors and iteration arithmetic
+  constexpr bool sw64 = SW64;                             // sweep arithmetic
+  using TP = typename std::conditional<SW64, double, float>::type;   // per-task partial fluxes
+  static_assert(f64 || !sw64, "FP64 sweeps need FP64 vectors");
   rte_problem* p = C.p;
   Ws& W = *C.ws;
-  if (C.rec && !f64) {
+  if (C.rec && !(f64 && sw64)) {
     set_error("run_fgmres: the first-cycle record needs an FP64 solve");
     return RTE_ERR_UNSUPPORTED;
   }
@@ -1261,7 +1269,7 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
     k_zero_active<<<vg, 256, 0, st>>>(x, p->d_inst.p, W.active.p);
     count_launch();
   } else {
-    RTE_TRY(launch_T(p, MODE_RES, f64, x, f64, rhs, rb, f64, W.active.p, st));
+    RTE_TRY(launch_T(p, MODE_RES, sw64, x, f64, rhs, rb, f64, W.active.p, st));
     for (int b = 0; b < B; ++b) rs.sweeps[b] += act[b];
   }
   RTE_CHECK_CUDA(cudaGetLastError());
@@ -1353,14 +1361,14 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
             count_launch();
           }
         }
-        RTE_TRY(launch_op_partials(p, f64, zj, f64, W.active.p, s));
+        RTE_TRY(launch_op_partials(p, sw64, zj, f64, W.active.p, s));
         if (!W.fused) {
           int Bv = B, nit = W.nitems, ntask = p->tasks_per_inst, jj = j, mm = m, nch = W.nchunk, ldT = m + 1;
           long long nt = ntot;
           const int2* it_p = W.items.p;
           const InstInfo* inst_p = p->d_inst.p;
           int* act_p = W.active.p;
-          const TV* part_p = reinterpret_cast<const TV*>(p->d_partial.p);
+          const TP* part_p = reinterpret_cast<const TP*>(p->d_partial.p);
           const TV* z_p = zj;
           TV* V_p = Vb;
           TV* dp_p = reinterpret_cast<TV*>(W.part.p);
@@ -1384,12 +1392,12 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
           void* args[] = {&Bv, &it_p, &nit, &inst_p, &act_p, &part_p, &ntask, &z_p, &V_p, &nt, &jj, &mm, &nch,
                           &dp_p, &np_p, &Lt_p, &ldT, &H_p, &Hr_p, &w0_p, &cs_p, &sn_p, &g_p, &brk_p, &bn_p, &rt_p,
                           &il_p, &est_p, &fl_p, &kc_p, &hn_p, &a0_p};
-          RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_wide<TV, TV>,
+          RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_wide<TP, TV>,
                                                      dim3(f64 ? W.grid_wide64 : W.grid_wide32), dim3(256), args, 0,
                                                      s));
           count_launch();
         } else {
-          ArnArgs<TV, TV> A;
+          ArnArgs<TP, TV> A;
           A.B = B;
           A.nitems = W.nitems;
           A.ntask = p->tasks_per_inst;
@@ -1403,7 +1411,7 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
           A.inst = p->d_inst.p;
           A.active = W.active.p;
           A.active0 = W.active0.p;
-          A.partial = reinterpret_cast<const TV*>(p->d_partial.p);
+          A.partial = reinterpret_cast<const TP*>(p->d_partial.p);
           A.z = zj;
           A.V = Vb;
           A.znext = (W.withZ && j + 1 < m) ? Zbase + (size_t)(j + 1) * ntot : nullptr;
@@ -1426,7 +1434,7 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
           A.flag = W.flag.p;
           A.kcols = W.kcols.p;
           void* args[] = {&A};
-          RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop<TV, TV>,
+          RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_arnoldi_coop<TP, TV>,
                                                      dim3(f64 ? W.grid_post64 : W.grid_post32), dim3(256), args, 0,
                                                      s));
           count_launch();
@@ -1435,7 +1443,7 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
         return RTE_OK;
       };
       const int key = j | (use_rom ? 1 << 8 : 0) | (f64 ? 1 << 9 : 0) | (C.rec ? 1 << 10 : 0) |
-                      (rom_next ? 1 << 11 : 0) | (slot_now && j == 0 ? 1 << 12 : 0);
+                      (rom_next ? 1 << 11 : 0) | (slot_now && j == 0 ? 1 << 12 : 0) | (sw64 ? 1 << 13 : 0);
       auto it = W.graphs.find(key);
       if (it == W.graphs.end()) {
         // capture this iteration once; later iterations with the same key replay it
@@ -1526,7 +1534,7 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
     std::vector<int> mask(B);
     for (int b = 0; b < B; ++b) mask[b] = resid[b] ? 1 : 0;
     RTE_CHECK_CUDA(cudaMemcpyAsync(W.active.p, mask.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-    RTE_TRY(launch_T(p, MODE_RES, f64, x, f64, rhs, rb, f64, W.active.p, st));
+    RTE_TRY(launch_T(p, MODE_RES, sw64, x, f64, rhs, rb, f64, W.active.p, st));
     for (int b = 0; b < B; ++b)
       if (resid[b] == 2) { rs.sweeps[b] += 1; rs.restarts[b] += 1; }
     for (int b = 0; b < B; ++b) act[b] = mask[b];
@@ -1551,14 +1559,21 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
   return RTE_OK;
 }
 
+// Precision of a run: everything FP64; everything FP32; or FP32 sweeps (and partial fluxes) with FP64
+// Krylov vectors, MGS and Givens.  rhs and x are double unless the run is all FP32.
+enum RunPrecision { RUN_F64 = 0, RUN_F32 = 1, RUN_F32_SWEEP_F64_KRYLOV = 2 };
+
 static int run_fgmres(SolveCtx& C, const void* rhs, void* x, bool zero_guess, const std::vector<int>& want,
-                      double rtol, const std::vector<int>& max_it, bool f64, bool true_check,
+                      double rtol, const std::vector<int>& max_it, int prec, bool true_check,
                       const std::vector<int>& it_base, RunStats& rs) {
-  if (f64)
-    return run_fgmres_t<double>(C, static_cast<const double*>(rhs), static_cast<double*>(x), zero_guess, want, rtol,
-                                max_it, true_check, it_base, rs);
-  return run_fgmres_t<float>(C, static_cast<const float*>(rhs), static_cast<float*>(x), zero_guess, want, rtol, max_it,
-                             true_check, it_base, rs);
+  if (prec == RUN_F64)
+    return run_fgmres_t<double, true>(C, static_cast<const double*>(rhs), static_cast<double*>(x), zero_guess, want,
+                                      rtol, max_it, true_check, it_base, rs);
+  if (prec == RUN_F32_SWEEP_F64_KRYLOV)
+    return run_fgmres_t<double, false>(C, static_cast<const double*>(rhs), static_cast<double*>(x), zero_guess, want,
+                                       rtol, max_it, true_check, it_base, rs);
+  return run_fgmres_t<float, false>(C, static_cast<const float*>(rhs), static_cast<float*>(x), zero_guess, want, rtol,
+                                    max_it, true_check, it_base, rs);
 }
 
 static Ws* get_ws(rte_problem* p) {
@@ -1580,7 +1595,7 @@ int hf_solve(rte_problem* p, double rtol, int restart, int max_iter, double* x, 
   std::vector<int> all(p->B, 1), zero(p->B, 0);
   RunStats rs;
   std::vector<int> cap(p->B, max_iter);
-  RTE_TRY(run_fgmres(C, ws->bt.p, x, true, all, rtol, cap, true, false, zero, rs));
+  RTE_TRY(run_fgmres(C, ws->bt.p, x, true, all, rtol, cap, RUN_F64, false, zero, rs));
   *iterations = rs.iterations[0];
   *status = rs.status[0];
   return RTE_OK;
@@ -1595,7 +1610,8 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
   RTE_ARG(p && o && phi && stats, "null handle or pointer");
   RTE_ARG(o->restart >= 1 && o->restart <= 128, "restart must be in [1, 128]");
   RTE_ARG(o->rtol > 0.0 && o->max_iter >= 1, "rtol must be > 0 and max_iter >= 1");
-  RTE_ARG(o->mode == RTE_MODE_FP64 || o->mode == RTE_MODE_MIXED, "unknown mode");
+  RTE_ARG(o->mode == RTE_MODE_FP64 || o->mode == RTE_MODE_MIXED || o->mode == RTE_MODE_MIXED_F64KRYLOV,
+          "unknown mode");
   RTE_ARG(o->post_mode == RTE_POST_ROM || o->post_mode == RTE_POST_IDENTITY, "unknown post_mode");
   if (roms)
     for (int b = 0; b < p->B; ++b)
@@ -1802,7 +1818,7 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
   if (o->mode == RTE_MODE_FP64) {
     RunStats rs;
     std::vector<int> cap(B, o->max_iter);
-    RTE_TRY(run_fgmres(C, ws->bt.p, x, !warm, all, o->rtol, cap, true, o->true_residual_check != 0, zero, rs));
+    RTE_TRY(run_fgmres(C, ws->bt.p, x, !warm, all, o->rtol, cap, RUN_F64, o->true_residual_check != 0, zero, rs));
     for (int b = 0; b < B; ++b) {
       S[b].iterations = rs.iterations[b];
       S[b].sweeps += rs.sweeps[b];
@@ -1868,16 +1884,23 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
         ++nact;
       }
       if (nact == 0) break;
-      // inner solve A~ d = ro entirely in FP32 (right-hand side rounded to FP32), zero guess
+      // inner solve A~ d = ro, zero guess: entirely in FP32 (right-hand side rounded to FP32), or with FP32
+      // sweeps and FP64 Krylov vectors, MGS and Givens (RTE_MODE_MIXED_F64KRYLOV)
       std::vector<int> cap(B, 0);
       for (int b = 0; b < B; ++b) cap[b] = std::min(inner_cap, o->max_iter - S[b].iterations);
       RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-      k_copy_active<<<vg, 256, 0, st>>>(ws->rin32.p, ro, p->d_inst.p, ws->active.p);
-      count_launch();
       RunStats rs;
-      RTE_TRY(run_fgmres(C, ws->rin32.p, ws->d32.p, true, act, o->inner_rtol, cap, false, false, zero, rs));
-      RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-      k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d32.p, p->d_inst.p, ws->active.p);
+      if (o->mode == RTE_MODE_MIXED_F64KRYLOV) {
+        RTE_TRY(run_fgmres(C, ro, ws->d.p, true, act, o->inner_rtol, cap, RUN_F32_SWEEP_F64_KRYLOV, false, zero, rs));
+        RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+        k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d.p, p->d_inst.p, ws->active.p);
+      } else {
+        k_copy_active<<<vg, 256, 0, st>>>(ws->rin32.p, ro, p->d_inst.p, ws->active.p);
+        count_launch();
+        RTE_TRY(run_fgmres(C, ws->rin32.p, ws->d32.p, true, act, o->inner_rtol, cap, RUN_F32, false, zero, rs));
+        RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+        k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d32.p, p->d_inst.p, ws->active.p);
+      }
       count_launch();
       // ro = b~ - A~ x in FP64
       RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ro, true, ws->active.p, st));
@@ -1897,7 +1920,7 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       std::vector<int> cap(B, 0);
       for (int b = 0; b < B; ++b) cap[b] = std::max(1, o->max_iter - S[b].iterations);
       RunStats rs;
-      RTE_TRY(run_fgmres(C, ws->bt.p, x, false, esc, o->rtol, cap, true, o->true_residual_check != 0, zero, rs));
+      RTE_TRY(run_fgmres(C, ws->bt.p, x, false, esc, o->rtol, cap, RUN_F64, o->true_residual_check != 0, zero, rs));
       for (int b = 0; b < B; ++b) {
         if (!esc[b]) continue;
         S[b].iterations += rs.iterations[b];
@@ -1924,8 +1947,8 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ws->r.p, true, ws->active.p, st));
     }
   }
-  if (o->mode == RTE_MODE_MIXED || o->true_residual_check) {
-    const double* rfin = o->mode == RTE_MODE_MIXED ? ws->ro.p : ws->r.p;
+  if (o->mode != RTE_MODE_FP64 || o->true_residual_check) {
+    const double* rfin = o->mode != RTE_MODE_FP64 ? ws->ro.p : ws->r.p;
     std::vector<int> all1(B, 1);
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, all1.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
     k_norm<<<B, 512, 0, st>>>(rfin, p->d_inst.p, ws->active.p, ws->nrm.p);

@@ -126,7 +126,7 @@ def test_rank64_rom_apply_and_solves():
         assert rel(zh[b], ORS.romsad_apply(orom, q, split(v, gp.offsets)[b])) < 1e-11
     ops = oracle_problems(spec2, ts, ta)
     refs = [ORS.solve(op, None, restart=200, rtol=1e-13, max_iter=3000)[0] for op in ops]
-    for mode, tol in ((B.RTE_MODE_FP64, 1e-9), (B.RTE_MODE_MIXED, 1e-7)):
+    for mode, tol in ((B.RTE_MODE_FP64, 1e-9), (B.RTE_MODE_MIXED, 1e-7), (B.RTE_MODE_MIXED_F64KRYLOV, 1e-7)):
         phi, st = _solve_gpu(B, gp, [grom, grom], restart=40, rtol=1e-10, max_iter=2000, mode=mode,
                              inner_rtol=1e-2, max_outer=30)
         for b in range(2):
@@ -159,15 +159,18 @@ def test_fgmres_romsad_fp64_slab_matches_oracle():
     assert sum(s["iterations"] for s in stats) < sum(s["iterations"] for s in st0)
 
 
-def test_mixed_precision_meets_fp64_accuracy():
-    """Mixed mode: FP64 true residual <= 1e-8 and phi within 1e-7 of the FP64 oracle."""
+@pytest.mark.parametrize("mode", ["mixed", "mixed_f64krylov"])
+def test_mixed_precision_meets_fp64_accuracy(mode):
+    """Mixed modes (inner solves all FP32, or FP32 sweeps with FP64 Krylov vectors, MGS and Givens): FP64
+    true residual <= 1e-8 and phi within 1e-7 of the FP64 oracle."""
     B = lib()
     spec = spec2d([32, 16], [32, 16], n_polar=4, n_azim=8)
     ss, sa = wl.draw_params(spec, 2, 23)
     ss = np.minimum(ss, 50.0)
     gp = B.Problem(spec, ss, sa)
     ops = oracle_problems(spec, ss, sa)
-    phi, stats = _solve_gpu(B, gp, None, restart=60, rtol=1e-8, max_iter=2000, mode=B.RTE_MODE_MIXED,
+    md = B.RTE_MODE_MIXED if mode == "mixed" else B.RTE_MODE_MIXED_F64KRYLOV
+    phi, stats = _solve_gpu(B, gp, None, restart=60, rtol=1e-8, max_iter=2000, mode=md,
                             inner_rtol=1e-4, max_outer=20)
     for b, op in enumerate(ops):
         ref, _ = ORS.solve(op, None, restart=200, rtol=1e-13, max_iter=3000)
