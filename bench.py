@@ -307,6 +307,41 @@ def measure_batched(RB, torch, dev, stream, flush, args, reps=1):
     return out
 
 
+def measure_learned_eval(RB, torch, dev, stream, flush, args, spec, rom, n_test=512):
+    """The learned part on held-out draws: n_test parameter instances of the single-instance workload (seeded
+    test split, never seen by the greedy or the MLP) solved in one mixed-precision call, with the learned
+    warm start, with the learned ROMSAD slot, and with plain ROMSAD."""
+    ts, ta = wl.draw_params(spec, n_test, wl.seed_for(4, 1))
+    sp = spec.with_instances([spec.nx[0]] * n_test, [spec.ny[0]] * n_test)
+    prob = RB.Problem(sp, ts, ta)
+    phi = torch.zeros(prob.n_dof, dtype=torch.float64, device=dev)
+    roms = [rom] * n_test
+    out = {"workload": f"{n_test} held-out draws of {spec.name} in one batched call", "instances": n_test}
+    for name, kw in (("learned_start", {"learned_warm_start": True}), ("learned_slot", {"learned_slot": True}),
+                     ("plain_romsad", {})):
+        common = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window,
+                      mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol, max_outer=30, stream=stream,
+                      raise_on_fail=False, **kw)
+        RB.fgmres_solve(prob, roms, phi, **common)   # warm-up / tuning
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = RB.fgmres_solve(prob, roms, phi, **common)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        conv = sum(1 for s in st if s["status"] == 0)
+        out[name] = {"value": conv / (ms * 1e-3), "unit": "param solves/s", "converged": conv,
+                     "iterations_mean": statistics.mean(s["iterations"] for s in st),
+                     "iterations_max": max(s["iterations"] for s in st),
+                     "true_rel_residual_max": max(s["true_rel_residual"] for s in st)}
+    del phi, prob
+    torch.cuda.empty_cache()
+    return out
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -494,6 +529,8 @@ def main():
         # the largest workload (64 x 256^2, 192 directions, 8x8 regions): 12.9 GB of angular output
         sweep_hbm["large"] = measure_sweep_hbm(RB, torch, dev, stream, flush, reps=3, config=5)
     batched = measure_batched(RB, torch, dev, stream, flush, args) if not args.no_batched and world == 1 else None
+    learned_eval = (measure_learned_eval(RB, torch, dev, stream, flush, args, spec, rom)
+                    if not args.no_batched and world == 1 else None)
     roof["ms_per_launch_fp32"] = ms32
     roof["ms_per_launch_fp64"] = ms64
     roof["peak_source"] = "unit counts x max SM clock (FP32); GB300 nominal (FP64)"
@@ -529,6 +566,7 @@ def main():
         "roofline": roof,
         "sweep_hbm": sweep_hbm,
         "batched": batched,
+        "learned_eval": learned_eval,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
