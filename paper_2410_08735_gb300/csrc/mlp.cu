@@ -205,13 +205,6 @@ static int upload_features(rte_mlp* M, MlpScratch& S, int n, const double* mu_ho
 
 // c_hat for instances whose parameters are on the device ([B][R] sigma_s, sigma_a): used by the
 // learned warm start inside fgmres_solve.  out: [B][64] doubles.
-__global__ void k_params_to_mu(const double* ss, const double* sa, int B, int R, double* mu) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= B * 2 * R) return;
-  const int b = t / (2 * R), f = t % (2 * R);
-  mu[t] = f < R ? ss[(size_t)b * R + f] : sa[(size_t)b * R + (f - R)];
-}
-
 __global__ void k_pad_out(const float* y, int n, int r, double* out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * 64) return;
