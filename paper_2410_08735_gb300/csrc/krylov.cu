@@ -3,18 +3,22 @@
 // All instances of a problem advance in lock step: one launch per step covers every instance that
 // is still active in the current cycle.  Per iteration j (0-based):
 //   z_j = M_j^{-1} v_j              ROMSAD (romsad.cu) for j < window, then the post-window operator
-//   w   = A~ z_j                    fused sweep (sweep.cu), written straight into v_{j+1}
-//   MGS: h_ij = w . v_i, w -= h_ij v_i (i = 0..j), h_{j+1,j} = ||w||, v_{j+1} = w / h  (compact-WY form)
+//   w   = A~ z_j                    sweep (sweep.cu, per-task partial fluxes), reduced into v_{j+1}
+//   MGS: h_ij = w . v_i, w -= h_ij v_i (i = 0..j), h_{j+1,j} = ||w||, v_{j+1} = w / h  (inverse
+//        compact-WY form)
 //   Givens: rotate column j of H, new rotation, |g_{j+1}| = residual estimate
-// At the end of a cycle y = R^{-1} g and phi += Z y.  MGS, Givens and all Krylov vectors are FP64.
+// At the end of a cycle y = R^{-1} g and phi += Z y.  In FP64 solves the Krylov vectors, MGS and Givens
+// are FP64; the inner solves of the mixed modes run them in FP32 (RTE_MODE_MIXED) or in FP64 around
+// FP32 sweeps (RTE_MODE_MIXED_F64KRYLOV).
 //
 // Readings where Alg. 1 is silent: stop when |g_{j+1}| / ||b~|| <= rtol; happy breakdown when
 // h_{j+1,j} <= 1e-14 ||w|| (before orthogonalisation); restart: phi0 <- phi, r0 = b~ - A~ phi0
 // (one sweep); after convergence the true residual is recomputed once (optional) and the solve
 // restarts from it if it exceeds 2 rtol.  The window counts iterations from the start of the solve.
 //
-// Mixed mode: FP64 iterative refinement.  r_k = b~ - A~ phi_k in FP64 (FP64 sweep), inner FGMRES on
-// A~ d = r_k with FP32 sweeps and FP32 ROM products (MGS/Givens FP64) to inner_rtol, phi += d.
+// Mixed modes: FP64 iterative refinement.  r_k = b~ - A~ phi_k in FP64 (FP64 sweep), inner FGMRES on
+// A~ d = r_k to inner_rtol (FP32 sweeps and ROM products; Krylov vectors, MGS and Givens in FP32 or
+// FP64 by mode), phi += d; an instance whose refinement stalls is finished by FP64 FGMRES.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
