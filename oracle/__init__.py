@@ -13,8 +13,10 @@ Modules (each cites the passages it follows):
   romsad          ROMSAD preconditioner, xi recurrence, snapshots, MGS truncation,
                   greedy ROM construction (Sec. 4, appendix B)
   mlp             MLP forward/backward/Adam used for the learned warm start
+  dsa             DG central-flux and jump operators, partially / fully consistent DSA (appendix A,
+                  extended to 2D axis by axis), exact sparse solves
 Pins are in tests/test_oracle_*.py.  Every function listed here is pinned;
 none is "parity unpinned".
 """
-from . import discretization, transport, krylov, romsad  # noqa: F401
+from . import discretization, transport, krylov, romsad, dsa  # noqa: F401
 from .discretization import Problem, with_params, gauss_legendre, slab_quadrature, cl_quadrature  # noqa: F401

@@ -16,6 +16,8 @@ ROM data (Sec. 4.4.1): xi^(1) = (phi - phi^(0)) / ||r^(0)|| (eq. correction-fgmr
 xi^(l) = (z^(l-1) - sum_{i<l} H_{i,l-1} xi^(i)) / H_{l,l-1} (eq. correction-fgmres2),
 delta psi_j^(l) = (D_j + Sigma_t)^{-1} Sigma_s xi^(l) (eq. fgmres-psi-correction).
 Greedy (Sec. 4.4.2) with the modified Gram-Schmidt + truncation of appendix B.
+After the window the switch (eq. ROMSAD-preconditioner) can hand over to the DSA preconditioner of
+appendix A (oracle.dsa), as in the paper.
 
 Readings where the paper is silent:
   * truncation test of appendix B is relative: ||u|| > eps_QR * ||psi|| (the
@@ -33,6 +35,7 @@ from typing import List, Optional
 
 import numpy as np
 
+from . import dsa
 from .discretization import Problem, with_params
 from .krylov import fgmres
 from .transport import Atilde_apply, rhs_btilde
@@ -105,14 +108,22 @@ def romsad_apply(rom: Rom, p: Problem, v: np.ndarray, A_r: Optional[np.ndarray] 
 
 
 def make_preconditioner(rom: Optional[Rom], p: Problem, window: int, post: str = "rom"):
-    """M_j of eq. ROMSAD-preconditioner: ROM for j <= window; afterwards 'rom' or 'identity'."""
+    """M_j of eq. ROMSAD-preconditioner: ROM for j <= window; afterwards 'rom', 'identity', or the DSA
+    preconditioner of appendix A ('dsa': fully consistent, 'dsa_pc': partially consistent).  Without a ROM,
+    'dsa'/'dsa_pc' give the right DSA preconditioner for every j (GMRES-DSA) and anything else none."""
+    dsa_kind = {"dsa": "full", "dsa_pc": "partial"}.get(post)
+    D = dsa.Dsa(p, dsa_kind) if dsa_kind is not None else None
     if rom is None:
-        return None
+        if D is None:
+            return None
+        return lambda j, v: D.apply(v)
     A_r = reduced_operator(rom, p.sigma_s_region, p.sigma_a_region)
 
     def precond(j: int, v: np.ndarray) -> np.ndarray:
         if j <= window or post == "rom":
             return romsad_apply(rom, p, v, A_r)
+        if D is not None:
+            return D.apply(v)
         return v.copy()
 
     return precond
