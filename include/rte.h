@@ -186,6 +186,10 @@ int romsad_destroy(romsad_t rom);
 /* ------------------------------------------------------------ FGMRES (Alg. 1) */
 #define RTE_POST_ROM 0       /* keep M_ROM after the window (a fixed linear operator) */
 #define RTE_POST_IDENTITY 1  /* z = v after the window                                */
+#define RTE_POST_DSA 2       /* the DSA preconditioner after the window, as in eq.
+                                ROMSAD-preconditioner (rte_dsa_apply; 2D meshes); with
+                                roms = NULL (or for instances without a ROM) DSA from the
+                                first iteration: right-preconditioned GMRES-DSA         */
 #define RTE_MODE_FP64 0      /* every sweep, MGS and least squares in FP64             */
 #define RTE_MODE_MIXED 1     /* FP64 iterative refinement (FP64 b~, residuals and update)
                                 around inner FGMRES solves that run entirely in FP32:
@@ -193,6 +197,32 @@ int romsad_destroy(romsad_t rom);
 #define RTE_MODE_MIXED_F64KRYLOV 2   /* the same refinement, inner solves with FP32 sweeps
                                         (and per-direction partial fluxes) but FP64 Krylov
                                         vectors, ROM products, MGS and Givens           */
+
+/* ---------------------------------------------------------- DSA (appendix A) */
+/* Diffusion synthetic acceleration consistent with the upwind DG discretisation, the paper's
+ * preconditioner after the ROMSAD window (eq. ROMSAD-preconditioner, appendix A), extended to the
+ * 2D X-Y geometry axis by axis.  Per axis d: central-flux and jump operators D_C,d and D_J,d (exterior
+ * traces zero on the boundary), with D_j = sum_d Omega_d (D_C,d - sign(Omega_d)/2 D_J,d).  From the
+ * 0th and first angular moments of the correction equation with a P1 angular shape, eliminating the
+ * current dJ:
+ *   K = Sigma_a - sum_d kappa_d D_J,d - sum_d 3 mu2_d^2 D_C,d B_d^{-1} D_C,d,
+ *   mu2_d = sum w Omega_d^2, kappa_d = sum_{Omega_d>0} w Omega_d, c_de = sum w Omega_d^2 |Omega_e|;
+ *   RTE_DSA_PARTIAL: B_d = 3 mu2_d Sigma_t (the partially consistent DSA of appendix A);
+ *   RTE_DSA_LUMPED:  B_d = the cell-diagonal blocks of 3 mu2_d Sigma_t - 3/2 sum_e c_de D_J,e (the fully
+ *                    consistent first-moment operator lumped to its diagonal blocks; fewer
+ *                    iterations on optically thick problems, unstable in optically thin, strongly
+ *                    scattering cells).
+ * M_DSA^{-1} v = v + x with x = one multigrid V-cycle applied to K x = Sigma_s v (the paper solves
+ * this system by algebraic multigrid): 4x4 cell-block Jacobi on the DG level, continuous bilinear
+ * elements on the same mesh and on meshes coarsened by 2 (Galerkin operators), one damped Jacobi step
+ * per vertex level, a dense solve on the coarsest.  Covers 2D meshes whose cell counts, halved while
+ * both are even, end with at most 100 vertices (RTE_ERR_UNSUPPORTED otherwise and for 1D).
+ * Arithmetic in FP32 for both dtypes. */
+#define RTE_DSA_PARTIAL 0
+#define RTE_DSA_LUMPED 1
+/* z = M_DSA^{-1} v for every instance of p with its own sigma.  v, z: scalar vectors of dtype
+ * (device, not aliased).  Each call redoes the per-parameter set-up (one extra kernel). */
+int rte_dsa_apply(rte_problem_t p, int variant, int dtype, const void* v, void* z, void* stream);
 
 /* ------------------------------------------------- learned warm start (MLP) */
 /* A small MLP maps mu = (sigma_s[R], sigma_a[R]) of an instance to the r reduced-basis
@@ -232,7 +262,7 @@ typedef struct fgmres_opts {
     double rtol;             /* FP64 mode: ||r||/||b~|| target; mixed: FP64 true residual target */
     int max_iter;            /* cap on Arnoldi iterations (summed over restarts / outer steps) */
     int window;              /* w of eq. ROMSAD-preconditioner                        */
-    int post_mode;           /* RTE_POST_ROM or RTE_POST_IDENTITY                      */
+    int post_mode;           /* RTE_POST_ROM, RTE_POST_IDENTITY or RTE_POST_DSA        */
     int mode;                /* RTE_MODE_FP64, RTE_MODE_MIXED or RTE_MODE_MIXED_F64KRYLOV */
     double inner_rtol;       /* mixed: relative target of each inner solve (1e-2 is a good
                                 default: FP32 rounding of I - T Sigma_s limits the inner
@@ -250,6 +280,7 @@ typedef struct fgmres_opts {
                                 coefficients from each instance's ROM MLP (c_hat(mu) / ||b~||)
                                 instead of the reduced solve (instances without an MLP, or with a
                                 non-finite prediction, keep the plain apply)               */
+    int dsa_variant;         /* RTE_POST_DSA: RTE_DSA_PARTIAL or RTE_DSA_LUMPED            */
 } fgmres_opts;
 
 typedef struct fgmres_stats {

@@ -22,6 +22,9 @@ quadrature exact on quadratics 3 mu2_d = 1 and, in 1D (c = 2 sum_{v>0} w v^3), t
 two moment equations.  Fully consistent DSA solves the coupled (dphi, dJ) system; partially consistent
 DSA drops the D_J term of the first-moment equation, dJ_d = -Sigma_t^{-1} D_C,d dphi / 3, leaving
   K_PC = Sigma_a - sum_d kappa_d D_J,d - sum_d mu2_d D_C,d Sigma_t^{-1} D_C,d     (symmetric positive definite).
+The lumped fully consistent form ("lumped") keeps the D_J term but replaces the first-moment operator
+B_d = 3 mu2_d Sigma_t - 3/2 sum_e c_de D_J,e by its cell-diagonal blocks before eliminating dJ:
+  K_LFC = Sigma_a - sum_d kappa_d D_J,d - sum_d 3 mu2_d^2 D_C,d blockdiag(B_d)^{-1} D_C,d            (SPD).
 As a right preconditioner of A~ = I - T Sigma_s (one source iteration plus its DSA correction):
   M_DSA^{-1} v = v + dphi(Sigma_s v).
 """
@@ -128,12 +131,40 @@ def quadrature_moments(p):
     return mu2, kappa, c
 
 
+def _cell_blocks(M, nd):
+    """Keep only the cell-diagonal nd x nd blocks of a sparse matrix."""
+    M = sp.coo_matrix(M)
+    keep = (M.row // nd) == (M.col // nd)
+    return sp.csr_matrix((M.data[keep], (M.row[keep], M.col[keep])), shape=M.shape)
+
+
+def eliminated_operator(p, kind, ops=None):
+    """K_PC ('partial') or K_LFC ('lumped') as a sparse matrix on the DG space."""
+    ops = dg_operators(p) if ops is None else ops
+    mu2, kappa, c = quadrature_moments(p)
+    K = sp.diags(p.sig_t_dof - p.sig_s_dof)
+    for d, (DC, DJ) in enumerate(ops):
+        K = K - kappa[d] * DJ
+    for d, (DC, DJ) in enumerate(ops):
+        if kind == "partial":
+            Binv = sp.diags(1.0 / (3.0 * mu2[d] * p.sig_t_dof))
+        else:
+            Bd = 3.0 * mu2[d] * sp.diags(p.sig_t_dof)
+            for e, (DCe, DJe) in enumerate(ops):
+                Bd = Bd - 1.5 * c[d, e] * DJe
+            Bd = _cell_blocks(Bd, p.nd)
+            Binv = sp.block_diag([sp.csr_matrix(np.linalg.inv(Bd[i:i + p.nd, i:i + p.nd].toarray()))
+                                  for i in range(0, p.ndof, p.nd)], format="csr")
+        K = K - 3.0 * mu2[d] ** 2 * (DC @ Binv @ DC)
+    return sp.csr_matrix(K)
+
+
 class Dsa:
     """The DSA correction of one problem: solve(rhs) returns dphi for the 0th-moment right-hand side
     Sigma_s r; apply(v) = v + solve(Sigma_s v) is the right preconditioner of A~."""
 
     def __init__(self, p, consistent: str = "full"):
-        assert consistent in ("full", "partial")
+        assert consistent in ("full", "partial", "lumped")
         self.p = p
         self.kind = consistent
         ops = dg_operators(p)
@@ -144,12 +175,8 @@ class Dsa:
         Kphi = sa.copy()
         for d, (DC, DJ) in enumerate(ops):
             Kphi = Kphi - kappa[d] * DJ
-        if consistent == "partial":
-            K = Kphi
-            inv_st = sp.diags(1.0 / p.sig_t_dof)
-            for d, (DC, DJ) in enumerate(ops):
-                K = K - mu2[d] * (DC @ inv_st @ DC)
-            self.K = sp.csc_matrix(K)
+        if consistent in ("partial", "lumped"):
+            self.K = sp.csc_matrix(eliminated_operator(p, consistent, ops))
             self.n_unknowns = n
         else:
             naxes = len(ops)
@@ -174,3 +201,121 @@ class Dsa:
 
     def apply(self, v: np.ndarray) -> np.ndarray:
         return v + self.solve(self.p.sig_s_dof * v)
+
+
+# ----------------------------------------------------------------------------- approximate DSA solve
+# The paper solves the DSA diffusion system with algebraic multigrid and does not fix the cycle.  The
+# approximate solve used with the GPU path is one multigrid V-cycle on K_LFC (or K_PC):
+#   DG level:  damped 4x4 (2x2 in 1D) cell-block Jacobi, x = omega Kcc^{-1} b, then the coarse correction,
+#              then x += omega Kcc^{-1} (b - K x);
+#   level 1:   continuous piecewise bilinear (linear in 1D) functions on the same mesh, embedded into the
+#              DG space by P_c, with the Galerkin operator P_c^T K P_c;
+#   level l+1: the same on the mesh coarsened by 2 in every axis (bilinear interpolation, Galerkin
+#              operator), while every axis stays even and the mesh has more than 4 cells (2 in 1D);
+#   vertex levels: one damped point-Jacobi step before and after the coarse correction;
+#   coarsest:  exact dense solve.
+# Written with explicit sparse matrices and triple products so that every step can be read off directly.
+
+
+def continuous_prolongation(p):
+    """P_c: vertex values of a continuous piecewise (bi)linear function -> its DG coefficients.  On a cell of
+    width h the 1D factor maps the end values (u_lo, u_hi) to (sqrt(h)(u_lo+u_hi)/2, sqrt(h)(u_hi-u_lo)/(2 sqrt 3)),
+    the orthonormal Legendre coefficients of the linear interpolant; 2D is the tensor product."""
+    def factor(h):
+        r = math.sqrt(h)
+        return np.array([[r / 2.0, r / 2.0], [-r / (2.0 * math.sqrt(3.0)), r / (2.0 * math.sqrt(3.0))]])
+
+    Fx = factor(p.hx)
+    nvx = p.nx + 1
+    rows, cols, vals = [], [], []
+    if p.dim == 1:
+        for ix in range(p.nx):
+            for a in range(2):
+                for vx in range(2):
+                    rows.append(ix * 2 + a)
+                    cols.append(ix + vx)
+                    vals.append(Fx[a, vx])
+        return sp.csr_matrix((vals, (rows, cols)), shape=(p.ndof, nvx))
+    Fy = factor(p.hy)
+    for iy in range(p.ny):
+        for ix in range(p.nx):
+            c = iy * p.nx + ix
+            for b in range(2):
+                for a in range(2):
+                    for vy in range(2):
+                        for vx in range(2):
+                            rows.append(c * 4 + a + 2 * b)
+                            cols.append((iy + vy) * nvx + ix + vx)
+                            vals.append(Fx[a, vx] * Fy[b, vy])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(p.ndof, nvx * (p.ny + 1)))
+
+
+def _interp_1d(nc):
+    """Linear interpolation from nc+1 coarse vertices to 2nc+1 fine vertices."""
+    P = np.zeros((2 * nc + 1, nc + 1))
+    for i in range(2 * nc + 1):
+        if i % 2 == 0:
+            P[i, i // 2] = 1.0
+        else:
+            P[i, i // 2] = P[i, i // 2 + 1] = 0.5
+    return sp.csr_matrix(P)
+
+
+def vertex_interpolation(ncx, ncy, dim=2):
+    """Bilinear interpolation from the vertices of an ncx x ncy cell grid to those of the 2ncx x 2ncy grid
+    (row-major, x fastest)."""
+    if dim == 1:
+        return _interp_1d(ncx)
+    return sp.csr_matrix(sp.kron(_interp_1d(ncy), _interp_1d(ncx)))
+
+
+def coarsen(ncx, ncy, dim=2):
+    """Next coarser cell grid, or None at the coarsest level."""
+    if dim == 1:
+        return (ncx // 2, 1) if ncx % 2 == 0 and ncx > 2 else None
+    if ncx % 2 == 0 and ncy % 2 == 0 and ncx * ncy > 4:
+        return ncx // 2, ncy // 2
+    return None
+
+
+class MultigridDsa:
+    """One V-cycle of the approximate DSA solve (see the comment above); apply(v) = v + cycle(Sigma_s v)."""
+
+    def __init__(self, p, kind="lumped", omega=0.7, omega_v=0.7):
+        assert kind in ("lumped", "partial")
+        self.p = p
+        self.omega, self.omega_v = omega, omega_v
+        self.K = eliminated_operator(p, kind)
+        nd = p.nd
+        self.Kcc_inv = sp.block_diag([sp.csr_matrix(np.linalg.inv(self.K[i:i + nd, i:i + nd].toarray()))
+                                      for i in range(0, p.ndof, nd)], format="csr")
+        self.P = [continuous_prolongation(p)]          # P[0]: level 1 -> DG; P[l]: level l+1 -> level l
+        self.A = [sp.csr_matrix(self.P[0].T @ self.K @ self.P[0])]
+        self.dims = [(p.nx, p.ny)]
+        nxt = coarsen(p.nx, p.ny, p.dim)
+        while nxt is not None:
+            Pv = vertex_interpolation(nxt[0], nxt[1], p.dim)
+            self.P.append(Pv)
+            self.A.append(sp.csr_matrix(Pv.T @ self.A[-1] @ Pv))
+            self.dims.append(nxt)
+            nxt = coarsen(nxt[0], nxt[1], p.dim)
+        self.Dinv = [1.0 / A.diagonal() for A in self.A]
+        self.coarsest = self.A[-1].toarray()
+
+    def _vertex_cycle(self, l, b):
+        if l == len(self.A) - 1:
+            return np.linalg.solve(self.coarsest, b)
+        A = self.A[l]
+        u = self.omega_v * self.Dinv[l] * b
+        r = b - A @ u
+        u = u + self.P[l + 1] @ self._vertex_cycle(l + 1, self.P[l + 1].T @ r)
+        return u + self.omega_v * self.Dinv[l] * (b - A @ u)
+
+    def cycle(self, b):
+        x = self.omega * (self.Kcc_inv @ b)
+        r = b - self.K @ x
+        x = x + self.P[0] @ self._vertex_cycle(0, self.P[0].T @ r)
+        return x + self.omega * (self.Kcc_inv @ (b - self.K @ x))
+
+    def apply(self, v):
+        return v + self.cycle(self.p.sig_s_dof * v)

@@ -18,7 +18,8 @@ from . import build_lib
 RTE_OK = 0
 RTE_ERR_NOT_CONVERGED = 4
 RTE_F64, RTE_F32 = 0, 1
-RTE_POST_ROM, RTE_POST_IDENTITY = 0, 1
+RTE_POST_ROM, RTE_POST_IDENTITY, RTE_POST_DSA = 0, 1, 2
+RTE_DSA_PARTIAL, RTE_DSA_LUMPED = 0, 1
 RTE_MODE_FP64, RTE_MODE_MIXED, RTE_MODE_MIXED_F64KRYLOV = 0, 1, 2
 
 _lib = None
@@ -69,7 +70,8 @@ class FgmresOpts(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("rtol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("window", ctypes.c_int), ("post_mode", ctypes.c_int), ("mode", ctypes.c_int),
                 ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int),
-                ("true_residual_check", ctypes.c_int), ("warm_start", ctypes.c_int), ("learned_slot", ctypes.c_int)]
+                ("true_residual_check", ctypes.c_int), ("warm_start", ctypes.c_int), ("learned_slot", ctypes.c_int),
+                ("dsa_variant", ctypes.c_int)]
 
 
 class FgmresStats(ctypes.Structure):
@@ -105,6 +107,8 @@ _SIGS = {
     "rte_rhs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]),
     "rte_apply_op_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p]),
+    "rte_dsa_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p]),
     "romsad_create_from_basis": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p)]),
     "romsad_build_greedy": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -286,6 +290,11 @@ class Problem:
     def rhs(self, out, stream=None):
         _check(load().rte_rhs(self.h, _dtype_code(out), _ptr(out), _stream(stream)), "rte_rhs")
 
+    def dsa_apply(self, v, z, variant=RTE_DSA_PARTIAL, stream=None):
+        """z = M_DSA^{-1} v (one multigrid V-cycle on the DSA system of each instance)."""
+        _check(load().rte_dsa_apply(self.h, variant, _dtype_code(v), _ptr(v), _ptr(z), _stream(stream)),
+               "rte_dsa_apply")
+
 
 class Rom:
     """Owns a romsad_t."""
@@ -441,15 +450,16 @@ def attach_mlp(rom: "Rom", mlp: Optional[Mlp]):
 def fgmres_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi, phi0=None, restart=30,
                  rtol=1e-10, max_iter=1000, window=2, post_mode=RTE_POST_ROM, mode=RTE_MODE_FP64,
                  inner_rtol=1e-2, max_outer=20, true_residual_check=True, stream=None, raise_on_fail=True,
-                 learned_warm_start=False, learned_slot=False):
+                 learned_warm_start=False, learned_slot=False, dsa_variant=RTE_DSA_PARTIAL):
     """FGMRES-ROMSAD for all instances; phi: FP64 device tensor or host (numpy/pinned) buffer.
+    post_mode=RTE_POST_DSA switches to DSA after the window (with roms=None: GMRES-DSA).
 
     Returns the list of per-instance stats dicts.
     """
     B = problem.spec.n_instances
     ws = 2 if learned_warm_start else int(phi0 is not None)
     o = FgmresOpts(restart, rtol, max_iter, window, post_mode, mode, inner_rtol, max_outer,
-                   int(true_residual_check), ws, int(learned_slot))
+                   int(true_residual_check), ws, int(learned_slot), int(dsa_variant))
     st = (FgmresStats * B)()
     if roms is None:
         rarr = None

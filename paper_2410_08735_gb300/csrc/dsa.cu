@@ -1,0 +1,787 @@
+// DSA preconditioner (paper appendix A, extended to the 2D X-Y geometry axis by axis), applied through
+// one multigrid V-cycle per call.
+//
+// Operators on the DG space of an instance, per axis d (D_C: central flux, D_J: jump, exterior traces
+// zero on the boundary), with D_j = sum_d Omega_d (D_C,d - sign(Omega_d)/2 D_J,d):
+//   K = Sigma_a - sum_d kappa_d D_J,d - sum_d 3 mu2_d^2 D_C,d B_d^{-1} D_C,d
+//   mu2_d = sum w Omega_d^2,  kappa_d = sum_{Omega_d>0} w Omega_d,  c_de = sum w Omega_d^2 |Omega_e|
+//   B_d^{-1} = 1 / (3 mu2_d sigma_t)                                    partially consistent (default)
+//   B_d^{-1} = cell-diagonal block of (3 mu2_d Sigma_t - 3/2 sum_e c_de D_J,e), inverted: a diagonal,
+//              3 mu2_d sigma_t + 3/2 sum_e c_de (2 or 6)/h_e by the dof's degree along e
+//                                                                      lumped fully consistent
+// M_DSA^{-1} v = v + x,  x ~ K^{-1} Sigma_s v (the 0th-moment equation of the appendix).
+//
+// The approximate solve (the paper uses algebraic multigrid without fixing the cycle): one V-cycle.
+//   DG level: x = omega Kcc^{-1} b (4x4 cell-block Jacobi), r = b - K x, coarse correction,
+//             x += omega Kcc^{-1} (b - K x).
+//   Level 1: continuous bilinear functions on the same mesh, embedded by P_c (vertex values -> Legendre
+//            coefficients of the bilinear interpolant).  For a continuous u, D_C,d P_c u is cell-local
+//            (interior central fluxes cancel the integration by parts; boundary faces keep half their
+//            own trace) and D_J,d P_c u lives on boundary faces only, so the Galerkin operator P_c^T K P_c
+//            is assembled from 4x4 element matrices E_T computed per cell.
+//   Level l+1: the mesh coarsened by 2 per axis (while both counts are even and the mesh has more than
+//            4 cells); bilinear interpolation nests the spaces, so the Galerkin element matrix of a coarse
+//            cell is the sum over its 4 children of I^T E_child I.
+//   Vertex levels: one damped point-Jacobi step before and after the coarse correction; the coarsest
+//            level (<= kMaxCoarse vertices) is solved with its dense inverse, formed at set-up.
+// Everything of one instance is done by one thread block (barriers are __syncthreads only), FP32.
+// k_dsa_setup runs once per parameter set, k_dsa_vcycle once per preconditioner apply.
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace rte {
+
+namespace {
+
+constexpr int kMaxLevels = 16;
+constexpr int kMaxCoarse = 100;
+constexpr int kThreads = 1024;
+constexpr int kSetupThreads = 512;
+constexpr float kSqrt3 = 1.7320508075688772f;
+
+struct DsaInst {
+  int nx, ny;                  // DG mesh (cells)
+  int L;                       // vertex levels 1..L (L = coarsest)
+  float hx, hy;
+  long long o_sgs, o_sga, o_binv, o_kinv, o_b0, o_x0, o_t, o_r0;
+  int ncx[kMaxLevels + 1], ncy[kMaxLevels + 1];
+  long long o_E[kMaxLevels + 1], o_dinv[kMaxLevels + 1], o_u[kMaxLevels + 1], o_b[kMaxLevels + 1],
+      o_r[kMaxLevels + 1];
+  long long o_ainv;
+};
+
+struct DsaConst {
+  float mu2[2], kappa[2], c[2][2];
+  float omega, omega_v;
+  int lumped;
+};
+
+// 1D axis factors of the orthonormal Legendre basis on a cell of width h: traces at the low and high
+// ends and the volume term int p_1' p_0 = 2 sqrt(3) / h (the only nonzero entry).
+struct Axis {
+  float lo0, lo1, hi0, hi1, v10;
+  __device__ explicit Axis(float h) {
+    const float s = rsqrtf(h);
+    lo0 = s;
+    lo1 = -kSqrt3 * s;
+    hi0 = s;
+    hi1 = kSqrt3 * s;
+    v10 = 2.f * kSqrt3 / h;
+  }
+};
+
+// local dof of (degree a along axis d, transverse degree t)
+__device__ __forceinline__ int dof_of(int d, int a, int t) { return d == 0 ? a + 2 * t : t + 2 * a; }
+
+__device__ __forceinline__ void traces(const float* X, int d, float f0, float f1, float* T) {
+#pragma unroll
+  for (int t = 0; t < 2; ++t) T[t] = f0 * X[dof_of(d, 0, t)] + f1 * X[dof_of(d, 1, t)];
+}
+
+// (D_C,d X) on a cell from its own values and those of its low / high neighbours along d (absent
+// neighbours: exterior trace zero).
+__device__ void dc_cell(const float* Xc, const float* Xl, const float* Xh, bool has_l, bool has_h, int d,
+                        const Axis& ax, float* out) {
+  float Tl[2], Th[2], Nl[2] = {0.f, 0.f}, Nh[2] = {0.f, 0.f};
+  traces(Xc, d, ax.lo0, ax.lo1, Tl);
+  traces(Xc, d, ax.hi0, ax.hi1, Th);
+  if (has_l) traces(Xl, d, ax.hi0, ax.hi1, Nl);
+  if (has_h) traces(Xh, d, ax.lo0, ax.lo1, Nh);
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const float al = 0.5f * (Tl[t] + Nl[t]), ah = 0.5f * (Th[t] + Nh[t]);
+    out[dof_of(d, 0, t)] = -ax.lo0 * al + ax.hi0 * ah;
+    out[dof_of(d, 1, t)] = -ax.v10 * Xc[dof_of(d, 0, t)] - ax.lo1 * al + ax.hi1 * ah;
+  }
+}
+
+// (D_J,d X) on a cell: -sum over its two faces of [X] [eta_k], [f] = f(high side) - f(low side).
+__device__ void dj_cell(const float* Xc, const float* Xl, const float* Xh, bool has_l, bool has_h, int d,
+                        const Axis& ax, float* out) {
+  float Tl[2], Th[2], Nl[2] = {0.f, 0.f}, Nh[2] = {0.f, 0.f};
+  traces(Xc, d, ax.lo0, ax.lo1, Tl);
+  traces(Xc, d, ax.hi0, ax.hi1, Th);
+  if (has_l) traces(Xl, d, ax.hi0, ax.hi1, Nl);
+  if (has_h) traces(Xh, d, ax.lo0, ax.lo1, Nh);
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const float jl = Tl[t] - Nl[t], jh = Nh[t] - Th[t];
+    out[dof_of(d, 0, t)] = -ax.lo0 * jl + ax.hi0 * jh;
+    out[dof_of(d, 1, t)] = -ax.lo1 * jl + ax.hi1 * jh;
+  }
+}
+
+// For a continuous function with DG coefficients X on a cell: D_C,d (cell-local; boundary faces keep
+// half their own trace) and -D_J,d (boundary faces only).
+__device__ void dc_cont(const float* X, bool has_l, bool has_h, int d, const Axis& ax, float* out) {
+  float Tl[2], Th[2];
+  traces(X, d, ax.lo0, ax.lo1, Tl);
+  traces(X, d, ax.hi0, ax.hi1, Th);
+  const float fl = has_l ? 1.f : 0.5f, fh = has_h ? 1.f : 0.5f;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    out[dof_of(d, 0, t)] = -ax.lo0 * fl * Tl[t] + ax.hi0 * fh * Th[t];
+    out[dof_of(d, 1, t)] = -ax.v10 * X[dof_of(d, 0, t)] - ax.lo1 * fl * Tl[t] + ax.hi1 * fh * Th[t];
+  }
+}
+__device__ void mdj_cont(const float* X, bool has_l, bool has_h, int d, const Axis& ax, float* out) {
+  float Tl[2], Th[2];
+  traces(X, d, ax.lo0, ax.lo1, Tl);
+  traces(X, d, ax.hi0, ax.hi1, Th);
+  const float fl = has_l ? 0.f : 1.f, fh = has_h ? 0.f : 1.f;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    out[dof_of(d, 0, t)] = ax.lo0 * fl * Tl[t] + ax.hi0 * fh * Th[t];
+    out[dof_of(d, 1, t)] = ax.lo1 * fl * Tl[t] + ax.hi1 * fh * Th[t];
+  }
+}
+
+__device__ __forceinline__ void load4(const float* p, float* x) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  x[0] = v.x;
+  x[1] = v.y;
+  x[2] = v.z;
+  x[3] = v.w;
+}
+__device__ __forceinline__ void store4(float* p, const float* x) {
+  *reinterpret_cast<float4*>(p) = make_float4(x[0], x[1], x[2], x[3]);
+}
+
+// P_c on one cell: Legendre coefficient k = a + 2b of the bilinear interpolant from corner q = vx + 2vy:
+// F_x[a][vx] F_y[b][vy], F(h) = [[sqrt(h)/2, sqrt(h)/2], [-sqrt(h)/(2 sqrt 3), sqrt(h)/(2 sqrt 3)]].
+__device__ __forceinline__ float pc_entry(int k, int q, float hx, float hy) {
+  const int a = k & 1, b = k >> 1, vx = q & 1, vy = q >> 1;
+  const float rx = sqrtf(hx), ry = sqrtf(hy);
+  const float fx = a == 0 ? 0.5f * rx : (vx ? 1.f : -1.f) * rx / (2.f * kSqrt3);
+  const float fy = b == 0 ? 0.5f * ry : (vy ? 1.f : -1.f) * ry / (2.f * kSqrt3);
+  return fx * fy;
+}
+
+// neighbour bookkeeping of DG cell c = iy*nx + ix along axis d
+struct Nb {
+  bool l, h;
+  int cl, ch;
+};
+__device__ __forceinline__ Nb nb_of(int ix, int iy, int nx, int ny, int d) {
+  Nb n;
+  if (d == 0) {
+    n.l = ix > 0;
+    n.h = ix < nx - 1;
+    n.cl = iy * nx + max(ix - 1, 0);
+    n.ch = iy * nx + min(ix + 1, nx - 1);
+  } else {
+    n.l = iy > 0;
+    n.h = iy < ny - 1;
+    n.cl = max(iy - 1, 0) * nx + ix;
+    n.ch = min(iy + 1, ny - 1) * nx + ix;
+  }
+  return n;
+}
+
+// y = A_l u at vertex (ix, iy) of a level with ncx x ncy cells and element matrices E [cells][4][4]
+__device__ float vertex_apply(const float* E, const float* u, int ncx, int ncy, int ix, int iy) {
+  const int nvx = ncx + 1;
+  float y = 0.f;
+#pragma unroll
+  for (int sy = 0; sy < 2; ++sy) {
+    const int cy = iy - 1 + sy;
+    if (cy < 0 || cy >= ncy) continue;
+#pragma unroll
+    for (int sx = 0; sx < 2; ++sx) {
+      const int cx = ix - 1 + sx;
+      if (cx < 0 || cx >= ncx) continue;
+      const int qv = (ix - cx) + 2 * (iy - cy);
+      const float* e = E + ((size_t)(cy * ncx + cx) * 16 + qv * 4);
+      const int v0 = cy * nvx + cx;
+      y += e[0] * u[v0] + e[1] * u[v0 + 1] + e[2] * u[v0 + nvx] + e[3] * u[v0 + nvx + 1];
+    }
+  }
+  return y;
+}
+
+// ----------------------------------------------------------------------------------------------- set-up
+__global__ void __launch_bounds__(kSetupThreads) k_dsa_setup(const InstInfo* inst, const DsaInst* dinfo,
+                                                             float* base, const double* sig_s, const double* sig_t,
+                                                             int R, int rx, int ry, DsaConst k) {
+  __shared__ float A[kMaxCoarse * kMaxCoarse];
+  const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  const DsaInst& di = dinfo[b];
+  const int nx = di.nx, ny = di.ny, nc = nx * ny;
+  const int cxr = nx / rx, cyr = ny / ry;
+  float* sgs = base + di.o_sgs;
+  float* sga = base + di.o_sga;
+  float* binv = base + di.o_binv;
+  float* kinv = base + di.o_kinv;
+  const float hs[2] = {di.hx, di.hy};
+  // S1: per-cell cross sections and B_d^{-1}
+  for (int c = tid; c < nc; c += nth) {
+    const int ix = c % nx, iy = c / nx;
+    const int reg = (iy / cyr) * rx + ix / cxr;
+    const float ss = (float)sig_s[(size_t)b * R + reg];
+    const float st = (float)sig_t[(size_t)b * R + reg];
+    sgs[c] = ss;
+    sga[c] = st - ss;
+#pragma unroll
+    for (int d = 0; d < 2; ++d)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float Bv = 3.f * k.mu2[d] * st;
+        if (k.lumped)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) Bv += 1.5f * k.c[d][e] * (((q >> e) & 1) ? 6.f : 2.f) / hs[e];
+        binv[(size_t)c * 8 + d * 4 + q] = Bv > 0.f ? 1.f / Bv : 0.f;   // a void cell carries no diffusion
+      }
+  }
+  __syncthreads();
+  // S2: the 4x4 diagonal block of K per cell (inverted) and the level-1 element matrices
+  const Axis ax[2] = {Axis(di.hx), Axis(di.hy)};
+  float* E1 = base + di.o_E[1];
+  for (int c = tid; c < nc; c += nth) {
+    const int ix = c % nx, iy = c / nx;
+    float Kc[16];
+    const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int col = 0; col < 4; ++col) {
+      float e[4] = {0.f, 0.f, 0.f, 0.f};
+      e[col] = 1.f;
+      float out[4];
+      for (int q = 0; q < 4; ++q) out[q] = sga[c] * e[q];
+      for (int d = 0; d < 2; ++d) {
+        const Nb n = nb_of(ix, iy, nx, ny, d);
+        float tmp[4];
+        dj_cell(e, zero4, zero4, n.l, n.h, d, ax[d], tmp);
+        for (int q = 0; q < 4; ++q) out[q] -= k.kappa[d] * tmp[q];
+        // Y = B^{-1} D_C e on the cell and its neighbours (e lives on this cell only)
+        float Yc[4], Yl[4] = {0.f, 0.f, 0.f, 0.f}, Yh[4] = {0.f, 0.f, 0.f, 0.f};
+        dc_cell(e, zero4, zero4, n.l, n.h, d, ax[d], Yc);
+        for (int q = 0; q < 4; ++q) Yc[q] *= binv[(size_t)c * 8 + d * 4 + q];
+        if (n.l) {
+          dc_cell(zero4, zero4, e, true, true, d, ax[d], Yl);
+          for (int q = 0; q < 4; ++q) Yl[q] *= binv[(size_t)n.cl * 8 + d * 4 + q];
+        }
+        if (n.h) {
+          dc_cell(zero4, e, zero4, true, true, d, ax[d], Yh);
+          for (int q = 0; q < 4; ++q) Yh[q] *= binv[(size_t)n.ch * 8 + d * 4 + q];
+        }
+        dc_cell(Yc, Yl, Yh, n.l, n.h, d, ax[d], tmp);
+        const float f = 3.f * k.mu2[d] * k.mu2[d];
+        for (int q = 0; q < 4; ++q) out[q] -= f * tmp[q];
+      }
+      for (int q = 0; q < 4; ++q) Kc[q * 4 + col] = out[q];
+    }
+    // Gauss-Jordan inverse in place (symmetric positive definite: no pivoting)
+    for (int p = 0; p < 4; ++p) {
+      const float piv = 1.f / Kc[p * 4 + p];
+      Kc[p * 4 + p] = 1.f;
+      for (int q = 0; q < 4; ++q) Kc[p * 4 + q] *= piv;
+      for (int r = 0; r < 4; ++r) {
+        if (r == p) continue;
+        const float f = Kc[r * 4 + p];
+        Kc[r * 4 + p] = 0.f;
+        for (int q = 0; q < 4; ++q) Kc[r * 4 + q] -= f * Kc[p * 4 + q];
+      }
+    }
+    for (int q = 0; q < 16; ++q) kinv[(size_t)c * 16 + q] = Kc[q];
+    // element matrix: P^T (sigma_a + sum_e kappa_e J_e) P + sum_d 3 mu2_d^2 (G_d P)^T B_d^{-1} (G_d P)
+    float Pq[4][4], M[4][4], G[2][4][4];
+    for (int q = 0; q < 4; ++q) {
+      for (int kk = 0; kk < 4; ++kk) Pq[q][kk] = pc_entry(kk, q, di.hx, di.hy);
+      for (int kk = 0; kk < 4; ++kk) M[q][kk] = sga[c] * Pq[q][kk];
+      for (int d = 0; d < 2; ++d) {
+        const Nb n = nb_of(ix, iy, nx, ny, d);
+        float tmp[4];
+        mdj_cont(Pq[q], n.l, n.h, d, ax[d], tmp);
+        for (int kk = 0; kk < 4; ++kk) M[q][kk] += k.kappa[d] * tmp[kk];
+        dc_cont(Pq[q], n.l, n.h, d, ax[d], G[d][q]);
+      }
+    }
+    for (int q = 0; q < 4; ++q)
+      for (int q2 = 0; q2 < 4; ++q2) {
+        float s = 0.f;
+        for (int kk = 0; kk < 4; ++kk) s += Pq[q][kk] * M[q2][kk];
+        for (int d = 0; d < 2; ++d) {
+          const float f = 3.f * k.mu2[d] * k.mu2[d];
+          for (int kk = 0; kk < 4; ++kk) s += f * G[d][q][kk] * binv[(size_t)c * 8 + d * 4 + kk] * G[d][q2][kk];
+        }
+        E1[(size_t)c * 16 + q * 4 + q2] = s;
+      }
+  }
+  __syncthreads();
+  // S3: coarse element matrices, sum over the 4 children of I^T E_child I
+  for (int l = 2; l <= di.L; ++l) {
+    const int ncx = di.ncx[l], ncy = di.ncy[l], fcx = di.ncx[l - 1];
+    const float* Ef = base + di.o_E[l - 1];
+    float* Ec = base + di.o_E[l];
+    for (int cc = tid; cc < ncx * ncy; cc += nth) {
+      const int CX = cc % ncx, CY = cc / ncx;
+      float acc[16];
+      for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+      for (int s = 0; s < 4; ++s) {
+        const int sx = s & 1, sy = s >> 1;
+        const float* e = Ef + (size_t)((2 * CY + sy) * fcx + 2 * CX + sx) * 16;
+        // I[child corner][coarse corner] = w(Vx, (sx+vx)/2) w(Vy, (sy+vy)/2), w(0,t) = 1-t, w(1,t) = t
+        float I[4][4];
+        for (int qc = 0; qc < 4; ++qc) {
+          const float tx = 0.5f * (sx + (qc & 1)), ty = 0.5f * (sy + (qc >> 1));
+          for (int Q = 0; Q < 4; ++Q) I[qc][Q] = ((Q & 1) ? tx : 1.f - tx) * ((Q >> 1) ? ty : 1.f - ty);
+        }
+        float EI[4][4];
+        for (int r = 0; r < 4; ++r)
+          for (int Q = 0; Q < 4; ++Q) {
+            float s2 = 0.f;
+            for (int q = 0; q < 4; ++q) s2 += e[r * 4 + q] * I[q][Q];
+            EI[r][Q] = s2;
+          }
+        for (int P = 0; P < 4; ++P)
+          for (int Q = 0; Q < 4; ++Q) {
+            float s2 = 0.f;
+            for (int r = 0; r < 4; ++r) s2 += I[r][P] * EI[r][Q];
+            acc[P * 4 + Q] += s2;
+          }
+      }
+      for (int q = 0; q < 16; ++q) Ec[(size_t)cc * 16 + q] = acc[q];
+    }
+    __syncthreads();
+  }
+  // S4: inverse diagonals of the vertex levels above the coarsest
+  for (int l = 1; l < di.L; ++l) {
+    const int ncx = di.ncx[l], ncy = di.ncy[l], nvx = ncx + 1, nv = nvx * (ncy + 1);
+    const float* E = base + di.o_E[l];
+    float* dinv = base + di.o_dinv[l];
+    for (int v = tid; v < nv; v += nth) {
+      const int ix = v % nvx, iy = v / nvx;
+      float s = 0.f;
+      for (int sy = 0; sy < 2; ++sy)
+        for (int sx = 0; sx < 2; ++sx) {
+          const int cx = ix - 1 + sx, cy = iy - 1 + sy;
+          if (cx < 0 || cx >= ncx || cy < 0 || cy >= ncy) continue;
+          const int qv = (ix - cx) + 2 * (iy - cy);
+          s += E[(size_t)(cy * ncx + cx) * 16 + qv * 5];
+        }
+      dinv[v] = 1.f / s;
+    }
+  }
+  // S5: dense inverse of the coarsest level (Gauss-Jordan in shared memory, one row per thread)
+  {
+    const int l = di.L, ncx = di.ncx[l], ncy = di.ncy[l], nvx = ncx + 1, n = nvx * (ncy + 1);
+    const float* E = base + di.o_E[l];
+    for (int idx = tid; idx < n * n; idx += nth) {
+      const int i = idx / n, j = idx % n;
+      const int ix = i % nvx, iy = i / nvx, jx = j % nvx, jy = j / nvx;
+      float s = 0.f;
+      if (abs(ix - jx) <= 1 && abs(iy - jy) <= 1)
+        for (int cy = max(iy, jy) - 1; cy <= min(iy, jy); ++cy)
+          for (int cx = max(ix, jx) - 1; cx <= min(ix, jx); ++cx) {
+            if (cx < 0 || cx >= ncx || cy < 0 || cy >= ncy) continue;
+            const int qi = (ix - cx) + 2 * (iy - cy), qj = (jx - cx) + 2 * (jy - cy);
+            s += E[(size_t)(cy * ncx + cx) * 16 + qi * 4 + qj];
+          }
+      A[idx] = s;
+    }
+    for (int p = 0; p < n; ++p) {
+      __syncthreads();
+      const float piv = 1.f / A[p * n + p];
+      const float fcol = tid < n ? A[tid * n + p] : 0.f;
+      __syncthreads();
+      if (tid < n) A[p * n + tid] = (tid == p ? 1.f : A[p * n + tid]) * piv;
+      __syncthreads();
+      if (tid < n && tid != p)
+        for (int j = 0; j < n; ++j) A[tid * n + j] = (j == p ? 0.f : A[tid * n + j]) - fcol * A[p * n + j];
+    }
+    __syncthreads();
+    float* ainv = base + di.o_ainv;
+    for (int idx = tid; idx < n * n; idx += nth) ainv[idx] = A[idx];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------- V-cycle
+template <typename TV>
+__global__ void __launch_bounds__(kThreads) k_dsa_vcycle(const InstInfo* inst, const DsaInst* dinfo, float* base,
+                                                         DsaConst k, const TV* v, TV* z, const int* active,
+                                                         const int* only) {
+  const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+  if (active && !active[b]) return;
+  if (only && !only[b]) return;
+  __shared__ float Pc[16];
+  const DsaInst& di = dinfo[b];
+  const InstInfo in = inst[b];
+  const int nx = di.nx, ny = di.ny, nc = nx * ny;
+  const float* sgs = base + di.o_sgs;
+  const float* sga = base + di.o_sga;
+  const float* binv = base + di.o_binv;
+  const float* kinv = base + di.o_kinv;
+  float* b0 = base + di.o_b0;
+  float* x0 = base + di.o_x0;
+  float* t = base + di.o_t;
+  float* r0 = base + di.o_r0;
+  const TV* vb = v + in.off;
+  TV* zb = z + in.off;
+  const Axis ax[2] = {Axis(di.hx), Axis(di.hy)};
+  const float om = k.omega, omv = k.omega_v;
+  if (tid < 16) Pc[tid] = pc_entry(tid >> 2, tid & 3, di.hx, di.hy);   // [k][q]
+  __syncthreads();
+
+  // K x0 on cell c from x0 and t (= B^{-1} D_C x0 per axis, stored)
+  auto Kx = [&](int c, float* out) {
+    const int ix = c % nx, iy = c / nx;
+    float xc[4];
+    load4(x0 + (size_t)c * 4, xc);
+    for (int q = 0; q < 4; ++q) out[q] = sga[c] * xc[q];
+#pragma unroll
+    for (int d = 0; d < 2; ++d) {
+      const Nb n = nb_of(ix, iy, nx, ny, d);
+      float xl[4], xh[4], tc[4], tl[4], th[4], tmp[4];
+      load4(x0 + (size_t)n.cl * 4, xl);
+      load4(x0 + (size_t)n.ch * 4, xh);
+      dj_cell(xc, xl, xh, n.l, n.h, d, ax[d], tmp);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) out[q] -= k.kappa[d] * tmp[q];
+      const float* td = t + (size_t)d * nc * 4;
+      load4(td + (size_t)c * 4, tc);
+      load4(td + (size_t)n.cl * 4, tl);
+      load4(td + (size_t)n.ch * 4, th);
+      dc_cell(tc, tl, th, n.l, n.h, d, ax[d], tmp);
+      const float f = 3.f * k.mu2[d] * k.mu2[d];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) out[q] -= f * tmp[q];
+    }
+  };
+  auto stage_t = [&]() {
+    for (int c = tid; c < nc; c += nth) {
+      const int ix = c % nx, iy = c / nx;
+      float xc[4];
+      load4(x0 + (size_t)c * 4, xc);
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const Nb n = nb_of(ix, iy, nx, ny, d);
+        float xl[4], xh[4], out[4];
+        load4(x0 + (size_t)n.cl * 4, xl);
+        load4(x0 + (size_t)n.ch * 4, xh);
+        dc_cell(xc, xl, xh, n.l, n.h, d, ax[d], out);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) out[q] *= binv[(size_t)c * 8 + d * 4 + q];
+        store4(t + ((size_t)d * nc + c) * 4, out);
+      }
+    }
+  };
+
+  // A: b0 = Sigma_s v, x0 = omega Kcc^{-1} b0
+  for (int c = tid; c < nc; c += nth) {
+    float bc[4], xc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) bc[q] = sgs[c] * (float)vb[(size_t)c * 4 + q];
+    store4(b0 + (size_t)c * 4, bc);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      float kr[4];
+      load4(kinv + (size_t)c * 16 + r * 4, kr);
+      xc[r] = om * (kr[0] * bc[0] + kr[1] * bc[1] + kr[2] * bc[2] + kr[3] * bc[3]);
+    }
+    store4(x0 + (size_t)c * 4, xc);
+  }
+  __syncthreads();
+  stage_t();
+  __syncthreads();
+  // C: r0 = b0 - K x0
+  for (int c = tid; c < nc; c += nth) {
+    float kx[4], bc[4];
+    Kx(c, kx);
+    load4(b0 + (size_t)c * 4, bc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) kx[q] = bc[q] - kx[q];
+    store4(r0 + (size_t)c * 4, kx);
+  }
+  __syncthreads();
+  // D: restriction to level 1, b1_v = sum over the cells around v of (P_T^T r0_T)_v
+  {
+    const int nvx = nx + 1, nv = nvx * (ny + 1);
+    float* b1 = base + di.o_b[1];
+    for (int vv = tid; vv < nv; vv += nth) {
+      const int ix = vv % nvx, iy = vv / nvx;
+      float s = 0.f;
+      for (int sy = 0; sy < 2; ++sy)
+        for (int sx = 0; sx < 2; ++sx) {
+          const int cx = ix - 1 + sx, cy = iy - 1 + sy;
+          if (cx < 0 || cx >= nx || cy < 0 || cy >= ny) continue;
+          const int qv = (ix - cx) + 2 * (iy - cy);
+          float rc[4];
+          load4(r0 + (size_t)(cy * nx + cx) * 4, rc);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) s += Pc[kk * 4 + qv] * rc[kk];
+        }
+      b1[vv] = s;
+    }
+  }
+  __syncthreads();
+  // vertex levels, descending
+  for (int l = 1; l < di.L; ++l) {
+    const int ncx = di.ncx[l], ncy = di.ncy[l], nvx = ncx + 1, nv = nvx * (ncy + 1);
+    const float* E = base + di.o_E[l];
+    const float* dinv = base + di.o_dinv[l];
+    float* u = base + di.o_u[l];
+    const float* bl = base + di.o_b[l];
+    float* rl = base + di.o_r[l];
+    for (int vv = tid; vv < nv; vv += nth) u[vv] = omv * dinv[vv] * bl[vv];
+    __syncthreads();
+    for (int vv = tid; vv < nv; vv += nth) rl[vv] = bl[vv] - vertex_apply(E, u, ncx, ncy, vv % nvx, vv / nvx);
+    __syncthreads();
+    // full-weighting restriction (transpose of bilinear interpolation)
+    const int Cx = di.ncx[l + 1], Cy = di.ncy[l + 1], nCx = Cx + 1, nC = nCx * (Cy + 1);
+    float* bc = base + di.o_b[l + 1];
+    for (int V = tid; V < nC; V += nth) {
+      const int I = V % nCx, J = V / nCx;
+      float s = 0.f;
+      for (int dj = -1; dj <= 1; ++dj) {
+        const int fy = 2 * J + dj;
+        if (fy < 0 || fy > ncy) continue;
+        for (int dii = -1; dii <= 1; ++dii) {
+          const int fx = 2 * I + dii;
+          if (fx < 0 || fx > ncx) continue;
+          s += (dii == 0 ? 1.f : 0.5f) * (dj == 0 ? 1.f : 0.5f) * rl[fy * nvx + fx];
+        }
+      }
+      bc[V] = s;
+    }
+    __syncthreads();
+  }
+  // coarsest: dense inverse
+  {
+    const int l = di.L, nvx = di.ncx[l] + 1, n = nvx * (di.ncy[l] + 1);
+    const float* ainv = base + di.o_ainv;
+    const float* bl = base + di.o_b[l];
+    float* u = base + di.o_u[l];
+    for (int i = tid; i < n; i += nth) {
+      float s = 0.f;
+      for (int j = 0; j < n; ++j) s += ainv[(size_t)i * n + j] * bl[j];
+      u[i] = s;
+    }
+  }
+  __syncthreads();
+  // vertex levels, ascending: prolongation, then one damped Jacobi step
+  for (int l = di.L - 1; l >= 1; --l) {
+    const int ncx = di.ncx[l], ncy = di.ncy[l], nvx = ncx + 1, nv = nvx * (ncy + 1);
+    const int nCx = di.ncx[l + 1] + 1;
+    const float* uc = base + di.o_u[l + 1];
+    const float* E = base + di.o_E[l];
+    const float* dinv = base + di.o_dinv[l];
+    float* u = base + di.o_u[l];
+    const float* bl = base + di.o_b[l];
+    float* rl = base + di.o_r[l];
+    for (int vv = tid; vv < nv; vv += nth) {
+      const int ix = vv % nvx, iy = vv / nvx;
+      // bilinear interpolation: the coarse neighbours of an even index coincide
+      const int x0i = ix >> 1, y0i = iy >> 1, x1i = (ix + 1) >> 1, y1i = (iy + 1) >> 1;
+      u[vv] += 0.25f * (uc[y0i * nCx + x0i] + uc[y0i * nCx + x1i] + uc[y1i * nCx + x0i] + uc[y1i * nCx + x1i]);
+    }
+    __syncthreads();
+    for (int vv = tid; vv < nv; vv += nth) rl[vv] = bl[vv] - vertex_apply(E, u, ncx, ncy, vv % nvx, vv / nvx);
+    __syncthreads();
+    for (int vv = tid; vv < nv; vv += nth) u[vv] += omv * dinv[vv] * rl[vv];
+    __syncthreads();
+  }
+  // E: x0 += P_c u1
+  {
+    const float* u1 = base + di.o_u[1];
+    const int nvx = nx + 1;
+    for (int c = tid; c < nc; c += nth) {
+      const int ix = c % nx, iy = c / nx;
+      const int v0 = iy * nvx + ix;
+      const float uq[4] = {u1[v0], u1[v0 + 1], u1[v0 + nvx], u1[v0 + nvx + 1]};
+      float xc[4];
+      load4(x0 + (size_t)c * 4, xc);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xc[kk] += Pc[kk * 4 + q] * uq[q];
+      store4(x0 + (size_t)c * 4, xc);
+    }
+  }
+  __syncthreads();
+  stage_t();
+  __syncthreads();
+  // G: z = v + x0 + omega Kcc^{-1} (b0 - K x0)
+  for (int c = tid; c < nc; c += nth) {
+    float kx[4], bc[4], xc[4];
+    Kx(c, kx);
+    load4(b0 + (size_t)c * 4, bc);
+    load4(x0 + (size_t)c * 4, xc);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) kx[q] = bc[q] - kx[q];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      float kr[4];
+      load4(kinv + (size_t)c * 16 + r * 4, kr);
+      const float x = xc[r] + om * (kr[0] * kx[0] + kr[1] * kx[1] + kr[2] * kx[2] + kr[3] * kx[3]);
+      zb[(size_t)c * 4 + r] = vb[(size_t)c * 4 + r] + (TV)x;
+    }
+  }
+}
+
+struct DsaWs {
+  DevBuf<float> data;
+  DevBuf<DsaInst> d_di;
+  std::vector<DsaInst> di;
+  int lumped = -1;
+};
+
+DsaWs* get_dsa_ws(rte_problem* p) {
+  if (!p->dsa_ws) p->dsa_ws = std::make_shared<DsaWs>();
+  return static_cast<DsaWs*>(p->dsa_ws.get());
+}
+
+long long align4(long long x) { return (x + 3) & ~3LL; }
+
+// Layout of the workspace (float offsets, 16-byte aligned blocks); fails on meshes the V-cycle does not
+// cover (1D, or a coarsest level above kMaxCoarse vertices, or more than kMaxLevels levels).
+int dsa_layout(rte_problem* p, std::vector<DsaInst>& out, long long& total) {
+  if (p->dim != 2) {
+    set_error("DSA: the V-cycle covers 2D meshes only");
+    return RTE_ERR_UNSUPPORTED;
+  }
+  out.assign(p->B, DsaInst{});
+  long long o = 0;
+  for (int b = 0; b < p->B; ++b) {
+    DsaInst& d = out[b];
+    d.nx = p->inst[b].nx;
+    d.ny = p->inst[b].ny;
+    d.hx = (float)p->inst[b].hx;
+    d.hy = (float)p->inst[b].hy;
+    const long long nc = (long long)d.nx * d.ny;
+    d.o_sgs = o;
+    o = align4(o + nc);
+    d.o_sga = o;
+    o = align4(o + nc);
+    d.o_binv = o;
+    o += 8 * nc;
+    d.o_kinv = o;
+    o += 16 * nc;
+    d.o_b0 = o;
+    o += 4 * nc;
+    d.o_x0 = o;
+    o += 4 * nc;
+    d.o_t = o;
+    o += 8 * nc;
+    d.o_r0 = o;
+    o += 4 * nc;
+    int cx = d.nx, cy = d.ny, l = 1;
+    while (true) {
+      if (l > kMaxLevels) {
+        set_error("DSA: too many multigrid levels");
+        return RTE_ERR_UNSUPPORTED;
+      }
+      d.ncx[l] = cx;
+      d.ncy[l] = cy;
+      const long long nv = (long long)(cx + 1) * (cy + 1);
+      d.o_E[l] = o;
+      o += 16LL * cx * cy;
+      d.o_dinv[l] = o;
+      o = align4(o + nv);
+      d.o_u[l] = o;
+      o = align4(o + nv);
+      d.o_b[l] = o;
+      o = align4(o + nv);
+      d.o_r[l] = o;
+      o = align4(o + nv);
+      if (cx % 2 == 0 && cy % 2 == 0 && cx * cy > 4) {
+        cx /= 2;
+        cy /= 2;
+        ++l;
+      } else {
+        break;
+      }
+    }
+    d.L = l;
+    const long long nvL = (long long)(cx + 1) * (cy + 1);
+    if (nvL > kMaxCoarse) {
+      set_error("DSA: the coarsest multigrid level has more than 100 vertices (mesh counts need more "
+                "factors of 2)");
+      return RTE_ERR_UNSUPPORTED;
+    }
+    d.o_ainv = o;
+    o = align4(o + nvL * nvL);
+  }
+  total = o;
+  return RTE_OK;
+}
+
+DsaConst dsa_constants(rte_problem* p, int variant) {
+  DsaConst k{};
+  double mu2[2] = {0, 0}, kap[2] = {0, 0}, c[2][2] = {{0, 0}, {0, 0}};
+  for (size_t j = 0; j < p->w.size(); ++j) {
+    const double om[2] = {p->om_x[j], p->om_y[j]};
+    for (int d = 0; d < 2; ++d) {
+      mu2[d] += p->w[j] * om[d] * om[d];
+      if (om[d] > 0) kap[d] += p->w[j] * om[d];
+      for (int e = 0; e < 2; ++e) c[d][e] += p->w[j] * om[d] * om[d] * std::fabs(om[e]);
+    }
+  }
+  for (int d = 0; d < 2; ++d) {
+    k.mu2[d] = (float)mu2[d];
+    k.kappa[d] = (float)kap[d];
+    for (int e = 0; e < 2; ++e) k.c[d][e] = (float)c[d][e];
+  }
+  k.omega = 0.7f;
+  k.omega_v = 0.7f;
+  k.lumped = variant == RTE_DSA_LUMPED ? 1 : 0;
+  return k;
+}
+
+}  // namespace
+
+int dsa_check(rte_problem* p) {
+  std::vector<DsaInst> di;
+  long long total = 0;
+  return dsa_layout(p, di, total);
+}
+
+int dsa_prepare(rte_problem* p, int variant, cudaStream_t st) {
+  RTE_ARG(variant == RTE_DSA_PARTIAL || variant == RTE_DSA_LUMPED, "unknown DSA variant");
+  DsaWs* w = get_dsa_ws(p);
+  if (w->di.empty()) {
+    long long total = 0;
+    RTE_TRY(dsa_layout(p, w->di, total));
+    RTE_TRY(w->data.alloc((size_t)total));
+    RTE_TRY(w->d_di.alloc(w->di.size()));
+    RTE_CHECK_CUDA(cudaMemcpy(w->d_di.p, w->di.data(), w->di.size() * sizeof(DsaInst), cudaMemcpyHostToDevice));
+  }
+  const DsaConst k = dsa_constants(p, variant);
+  k_dsa_setup<<<p->B, kSetupThreads, 0, st>>>(p->d_inst.p, w->d_di.p, w->data.p, p->d_sig_s.p, p->d_sig_t.p, p->R,
+                                              p->rx, p->ry, k);
+  count_launch();
+  RTE_CHECK_CUDA(cudaGetLastError());
+  w->lumped = k.lumped;
+  return RTE_OK;
+}
+
+int dsa_launch(rte_problem* p, bool f64, const void* v, void* z, const int* active, const int* only,
+               cudaStream_t st) {
+  DsaWs* w = get_dsa_ws(p);
+  if (w->di.empty() || w->lumped < 0) {
+    set_error("DSA: set-up missing");
+    return RTE_ERR_INVALID_ARG;
+  }
+  const DsaConst k = dsa_constants(p, w->lumped ? RTE_DSA_LUMPED : RTE_DSA_PARTIAL);
+  if (f64)
+    k_dsa_vcycle<double><<<p->B, kThreads, 0, st>>>(p->d_inst.p, w->d_di.p, w->data.p, k, (const double*)v,
+                                                    (double*)z, active, only);
+  else
+    k_dsa_vcycle<float><<<p->B, kThreads, 0, st>>>(p->d_inst.p, w->d_di.p, w->data.p, k, (const float*)v,
+                                                   (float*)z, active, only);
+  count_launch();
+  RTE_CHECK_CUDA(cudaGetLastError());
+  return RTE_OK;
+}
+
+}  // namespace rte
+
+using namespace rte;
+
+extern "C" int rte_dsa_apply(rte_problem_t p, int variant, int dtype, const void* v, void* z, void* stream) {
+  RTE_ARG(p && v && z, "null handle or pointer");
+  RTE_ARG(dtype == RTE_F64 || dtype == RTE_F32, "unknown dtype");
+  RTE_ARG(v != z, "v and z must not alias");
+  cudaStream_t st = (cudaStream_t)stream;
+  RTE_TRY(dsa_prepare(p, variant, st));
+  return dsa_launch(p, dtype == RTE_F64, v, z, nullptr, nullptr, st);
+}

@@ -110,6 +110,13 @@ struct SweepTask {
   int pad;
 };
 
+// dsa.cu: DSA preconditioner through one multigrid V-cycle.  dsa_check: whether the meshes are covered;
+// dsa_prepare: per-parameter set-up (cross sections, cell blocks, Galerkin hierarchy); dsa_launch:
+// z = v + x (x ~ K^{-1} Sigma_s v) for instances with active[b] (and only[b], when given).
+int dsa_check(rte_problem* p);
+int dsa_prepare(rte_problem* p, int variant, cudaStream_t st);
+int dsa_launch(rte_problem* p, bool f64, const void* v, void* z, const int* active, const int* only,
+               cudaStream_t st);
 }  // namespace rte
 
 struct rte_problem {
@@ -155,6 +162,7 @@ struct rte_problem {
   rte::DevBuf<float> d_tmp32;                 // [2 ntot] FP32 input and output of the autotuner's timing
   rte::DevBuf<double> d_wq;                   // [ndir] quadrature weights (paper order)
   std::shared_ptr<void> krylov_ws;            // FGMRES workspace (krylov.cu), grown on demand
+  std::shared_ptr<void> dsa_ws;               // DSA multigrid workspace (dsa.cu), sized once
 };
 
 namespace rte {
@@ -183,4 +191,11 @@ int launch_scalar_flux(rte_problem* p, bool f64, const void* psi, void* phi, cud
 int launch_forward_cols(int dim, int nx, int ny, double hx, double hy, const UDir& u, int rx, int ry,
                         const double* sig_t_reg, const double* x, long long ldx, double* y, long long ldy, int ncol,
                         cudaStream_t st);
+// dsa.cu: DSA preconditioner through one multigrid V-cycle.  dsa_check: whether the meshes are covered;
+// dsa_prepare: per-parameter set-up (cross sections, cell blocks, Galerkin hierarchy); dsa_launch:
+// z = v + x (x ~ K^{-1} Sigma_s v) for instances with active[b] (and only[b], when given).
+int dsa_check(rte_problem* p);
+int dsa_prepare(rte_problem* p, int variant, cudaStream_t st);
+int dsa_launch(rte_problem* p, bool f64, const void* v, void* z, const int* active, const int* only,
+               cudaStream_t st);
 }  // namespace rte

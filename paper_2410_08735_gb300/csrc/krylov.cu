@@ -1202,6 +1202,9 @@ struct SolveCtx {
   std::vector<RomPlan>* plans = nullptr;  // one per ROM group (factored once per solve)
   std::vector<int> no_rom_mask;       // [B] 1 for instances without a ROM
   bool slot_pending = false;          // the next first-cycle preconditioner apply uses the learned slot
+  bool any_rom = false;               // some instance has a ROM
+  bool any_norom = false;             // some instance has none
+  bool dsa = false;                   // DSA after the window (and throughout for instances without a ROM)
 };
 
 
@@ -1330,8 +1333,12 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
     const bool slot_now = C.slot_pending && W.withZ;
     for (int j = 0; j < m; ++j) {
       const int jg = it_first + j + 1;   // lock-step instances share the global iteration index
-      const bool use_rom = W.withZ && (jg <= C.window || C.post == RTE_POST_ROM);
-      const bool rom_next = W.withZ && (jg + 1 <= C.window || C.post == RTE_POST_ROM);
+      const bool use_rom = W.withZ && C.any_rom && (jg <= C.window || C.post == RTE_POST_ROM);
+      const bool rom_next = W.withZ && C.any_rom && (jg + 1 <= C.window || C.post == RTE_POST_ROM);
+      // DSA on z_j (cycle start or multi-phase step) and on z_{j+1} (after the fused step): for every
+      // instance outside the ROM window, for instances without a ROM inside it
+      const bool dsa_now = C.dsa && W.withZ && (!use_rom || C.any_norom);
+      const bool dsa_next = C.dsa && W.withZ && W.fused && j + 1 < m && (!rom_next || C.any_norom);
       // One Arnoldi iteration: w = A~ z_j into V[j+1], MGS, Givens, and the next preconditioned vector
       // z_{j+1} (the first one of a cycle, z_0, by the preconditioner kernel).
       auto body = [&](cudaStream_t s) -> int {
@@ -1360,10 +1367,11 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
             RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_precond_coop<TV>, dim3(W.grid_pre), dim3(256),
                                                        args, 0, s));
             count_launch();
-          } else {
+          } else if (!dsa_now) {
             k_copy_active<<<vg, 256, 0, s>>>(zj, vj, p->d_inst.p, W.active.p);
             count_launch();
           }
+          if (dsa_now) RTE_TRY(dsa_launch(p, f64, vj, zj, W.active.p, use_rom ? W.norom.p : nullptr, s));
         }
         RTE_TRY(launch_op_partials(p, sw64, zj, f64, W.active.p, s));
         if (!W.fused) {
@@ -1442,12 +1450,16 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
                                                      dim3(f64 ? W.grid_post64 : W.grid_post32), dim3(256), args, 0,
                                                      s));
           count_launch();
+          if (dsa_next)
+            RTE_TRY(dsa_launch(p, f64, Vb + (size_t)(j + 1) * ntot, A.znext, W.active.p,
+                               rom_next ? W.norom.p : nullptr, s));
         }
         RTE_CHECK_CUDA(cudaGetLastError());
         return RTE_OK;
       };
       const int key = j | (use_rom ? 1 << 8 : 0) | (f64 ? 1 << 9 : 0) | (C.rec ? 1 << 10 : 0) |
-                      (rom_next ? 1 << 11 : 0) | (slot_now && j == 0 ? 1 << 12 : 0) | (sw64 ? 1 << 13 : 0);
+                      (rom_next ? 1 << 11 : 0) | (slot_now && j == 0 ? 1 << 12 : 0) | (sw64 ? 1 << 13 : 0) |
+                      (dsa_now ? 1 << 14 : 0) | (dsa_next ? 1 << 15 : 0);
       auto it = W.graphs.find(key);
       if (it == W.graphs.end()) {
         // capture this iteration once; later iterations with the same key replay it
@@ -1616,7 +1628,13 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
   RTE_ARG(o->rtol > 0.0 && o->max_iter >= 1, "rtol must be > 0 and max_iter >= 1");
   RTE_ARG(o->mode == RTE_MODE_FP64 || o->mode == RTE_MODE_MIXED || o->mode == RTE_MODE_MIXED_F64KRYLOV,
           "unknown mode");
-  RTE_ARG(o->post_mode == RTE_POST_ROM || o->post_mode == RTE_POST_IDENTITY, "unknown post_mode");
+  RTE_ARG(o->post_mode == RTE_POST_ROM || o->post_mode == RTE_POST_IDENTITY || o->post_mode == RTE_POST_DSA,
+          "unknown post_mode");
+  const bool use_dsa = o->post_mode == RTE_POST_DSA;
+  if (use_dsa) {
+    RTE_ARG(o->dsa_variant == RTE_DSA_PARTIAL || o->dsa_variant == RTE_DSA_LUMPED, "unknown dsa_variant");
+    RTE_TRY(dsa_check(p));
+  }
   if (roms)
     for (int b = 0; b < p->B; ++b)
       if (roms[b]) RTE_TRY(rom_check_mesh(roms[b], p, b));
@@ -1625,7 +1643,7 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
   if (roms)
     for (int b = 0; b < p->B; ++b) any_rom = any_rom || roms[b] != nullptr;
   Ws* ws = get_ws(p);
-  RTE_TRY(ws->alloc(p, o->restart, any_rom));
+  RTE_TRY(ws->alloc(p, o->restart, any_rom || use_dsa));
   // output location: device pointer, or host pointer (solve into a device buffer, copy back)
   cudaPointerAttributes attr;
   bool host_out = false;
@@ -1685,6 +1703,10 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       count_launch();
     }
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->norom.p, C.no_rom_mask.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    C.any_rom = any_rom;
+    for (int b = 0; b < B; ++b) C.any_norom = C.any_norom || C.no_rom_mask[b] != 0;
+    C.dsa = use_dsa;
+    if (use_dsa) RTE_TRY(dsa_prepare(p, o->dsa_variant, st));
     std::vector<RomInstDev> ri(B);
     for (int b = 0; b < B; ++b)
       ri[b] = RomInstDev{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, 0};

@@ -155,3 +155,121 @@ def test_gmres_dsa_and_romsad_with_dsa_solve_the_dense_system(post):
     rom = RS.build_rom(p, Q.T.reshape(6, p.ndir, p.ndof))
     sol2, st2 = RS.solve(p, rom, window=2, post=post, restart=100, rtol=1e-10, max_iter=2000)
     assert rel(sol2, ref) < 1e-8
+
+
+# ------------------------------------------------------------------ approximate solve (one V-cycle)
+def _eval_dg(p, coef, x, y):
+    """Value of a DG Q1 function (orthonormal tensor Legendre) at a point, evaluated from the basis."""
+    ix = min(int((x - p.x0) / p.hx), p.nx - 1)
+    iy = min(int((y - p.y0) / p.hy), p.ny - 1)
+    xi = 2.0 * (x - p.x0 - (ix + 0.5) * p.hx) / p.hx
+    et = 2.0 * (y - p.y0 - (iy + 0.5) * p.hy) / p.hy
+    px = [1.0 / np.sqrt(p.hx), np.sqrt(3.0 / p.hx) * xi]
+    py = [1.0 / np.sqrt(p.hy), np.sqrt(3.0 / p.hy) * et]
+    c = iy * p.nx + ix
+    return sum(coef[c * 4 + a + 2 * b] * px[a] * py[b] for a in range(2) for b in range(2))
+
+
+def test_continuous_prolongation_reproduces_bilinear_functions():
+    p = _homogeneous(small_2d(nx=5, ny=3, n_polar=2, n_azim=4), 1.0, 1.0)
+    u = lambda x, y: 1.0 + 2.0 * x - 3.0 * y + 5.0 * x * y
+    vx = p.x0 + p.hx * np.arange(p.nx + 1)
+    vy = p.y0 + p.hy * np.arange(p.ny + 1)
+    uv = np.array([u(x, y) for y in vy for x in vx])
+    coef = dsa.continuous_prolongation(p) @ uv
+    rng = np.random.default_rng(0)
+    for x, y in zip(rng.uniform(p.x0, p.x0 + p.nx * p.hx, 40), rng.uniform(p.y0, p.y0 + p.ny * p.hy, 40)):
+        assert abs(_eval_dg(p, coef, x, y) - u(x, y)) < 1e-12
+
+
+def test_vertex_interpolation_reproduces_bilinear_functions():
+    u = lambda x, y: 0.5 - x + 4.0 * y + 3.0 * x * y
+    ncx, ncy = 3, 2
+    coarse = np.array([u(i / ncx, j / ncy) for j in range(ncy + 1) for i in range(ncx + 1)])
+    fine = dsa.vertex_interpolation(ncx, ncy) @ coarse
+    ref = np.array([u(i / (2 * ncx), j / (2 * ncy)) for j in range(2 * ncy + 1) for i in range(2 * ncx + 1)])
+    assert np.abs(fine - ref).max() < 1e-14
+
+
+def test_lumped_first_moment_blocks_have_the_closed_form():
+    """Cell-diagonal block of B_d = 3 mu2_d Sigma_t - 3/2 sum_e c_de D_J,e: the jump operator's own-cell block
+    along axis e is -(lo lo^T + hi hi^T) = -diag(2, 6)/h_e in that axis' degree, so the block is diagonal,
+    3 mu2_d sigma_t + 3/2 sum_e c_de (2 or 6)/h_e by the dof's degree along e."""
+    p = Problem(small_2d(nx=4, ny=3, n_polar=2, n_azim=8), 0, [20.0, 1.0, 300.0, 2.0], [0.1, 0.3, 0.2, 0.05])
+    ops = dsa.dg_operators(p)
+    mu2, kappa, c = dsa.quadrature_moments(p)
+    h = (p.hx, p.hy)
+    for d in range(2):
+        Bd = 3.0 * mu2[d] * np.diag(p.sig_t_dof)
+        for e, (DCe, DJe) in enumerate(ops):
+            Bd = Bd - 1.5 * c[d, e] * DJe.toarray()
+        for cell in range(p.ncell):
+            blk = Bd[cell * 4:cell * 4 + 4, cell * 4:cell * 4 + 4]
+            ref = np.array([3.0 * mu2[d] * p.sig_t[cell]
+                            + 1.5 * sum(c[d, e] * (2.0 if (k >> e) & 1 == 0 else 6.0) / h[e] for e in range(2))
+                            for k in range(4)])
+            assert np.abs(blk - np.diag(ref)).max() < 1e-12 * ref.max()
+
+
+@pytest.mark.parametrize("kind", ["partial", "lumped"])
+def test_galerkin_hierarchy(kind):
+    """A_0 = P_c^T K P_c and A_l = P_l^T A_{l-1} P_l are SPD, and the exact coarse correction leaves a
+    residual orthogonal to the coarse space."""
+    p = Problem(small_2d(nx=8, ny=8, n_polar=2, n_azim=8), 0, [20.0, 1.0, 300.0, 2.0], [0.1, 0.3, 0.2, 0.05])
+    mg = dsa.MultigridDsa(p, kind)
+    assert mg.dims == [(8, 8), (4, 4), (2, 2)]
+    for A in mg.A:
+        A = A.toarray()
+        assert np.abs(A - A.T).max() < 1e-12 * np.abs(A).max()
+        assert np.linalg.eigvalsh(A).min() > 0.0
+    b = np.random.default_rng(2).standard_normal(p.ndof)
+    P = mg.P[0].toarray()
+    x = P @ np.linalg.solve(mg.A[0].toarray(), P.T @ b)
+    assert np.linalg.norm(P.T @ (b - mg.K @ x)) < 1e-10 * np.linalg.norm(P.T @ b)
+
+
+@pytest.mark.parametrize("spec", [small_2d(nx=8, ny=4, n_polar=2, n_azim=8), small_1d(nx=16, rx=2)])
+@pytest.mark.parametrize("kind", ["partial", "lumped"])
+def test_iterated_vcycle_converges_to_the_exact_dsa_solve(spec, kind):
+    R = spec.n_regions
+    p = Problem(spec, 0, list(np.geomspace(1.0, 400.0, R)), list(np.linspace(0.05, 0.4, R)))
+    mg = dsa.MultigridDsa(p, kind)
+    b = np.random.default_rng(4).standard_normal(p.ndof)
+    ref = dsa.Dsa(p, kind).solve(b)
+    x = np.zeros_like(b)
+    for _ in range(200):                                            # a stationary iteration: contraction < 1
+        x = x + mg.cycle(b - mg.K @ x)
+    assert rel(x, ref) < 1e-10
+
+
+@pytest.mark.parametrize("sig_t_h", [0.025, 0.25, 2.5, 25.0])
+def test_1d_partially_consistent_vcycle_is_stable(sig_t_h):
+    """c = 0.9999: source iteration with the V-cycle PC-DSA correction contracts at every cell optical
+    thickness.  The lumped form does not in optically thin cells (its cell-diagonal first-moment operator
+    misses the inter-cell jump coupling that dominates there), which is why PC is the default."""
+    spec = small_1d(nx=40, rx=1)
+    p0 = _homogeneous(spec, 1.0, 1.0)
+    sig_t = sig_t_h / p0.hx
+    p = _homogeneous(spec, 0.9999 * sig_t, 1e-4 * sig_t)
+    A = _dense(lambda z: T.Atilde_apply(p, z), p.ndof)
+    for kind, bound in (("partial", 0.55), ("lumped", None)):
+        M = _dense(dsa.MultigridDsa(p, kind).apply, p.ndof)
+        rho = float(np.abs(np.linalg.eigvals(np.eye(p.ndof) - M @ A)).max())
+        if bound is not None:
+            assert rho < bound
+        elif sig_t_h <= 0.25:
+            assert rho > 1.0
+
+
+@pytest.mark.parametrize("kind", ["partial", "lumped"])
+def test_gmres_with_the_vcycle_dsa_solves_the_dense_system(kind):
+    p = Problem(small_2d(nx=8, ny=8, n_polar=2, n_azim=8), 0, [20.0, 1.0, 300.0, 2.0], [0.1, 0.3, 0.2, 0.05])
+    A = _dense(lambda z: T.Atilde_apply(p, z), p.ndof)
+    bt = T.rhs_btilde(p)
+    ref = np.linalg.solve(A, bt)
+    mg = dsa.MultigridDsa(p, kind)
+    _, st_plain = fgmres(lambda z: T.Atilde_apply(p, z), bt, None, restart=100, rtol=1e-10, max_iter=3000)
+    sol, st = fgmres(lambda z: T.Atilde_apply(p, z), bt, lambda j, v: mg.apply(v), restart=100, rtol=1e-10,
+                     max_iter=3000)
+    assert rel(sol, ref) < 1e-8
+    assert st.iterations * 3 < st_plain.iterations
