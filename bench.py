@@ -24,6 +24,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the CPU oracle legs run on one host core: cap the BLAS / OpenMP pools before numpy starts them
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 import numpy as np  # noqa: E402
 
@@ -142,24 +145,31 @@ def shard(rank: int, n_sets: int, B: int, step: int) -> tuple[int, int]:
 
 
 # ------------------------------------------------------------------ oracle legs
-def oracle_sample(spec, ss, sa, iters_needed: int, sample_iters: int):
-    """Time the CPU oracle on one instance: b~ plus a bounded number of FGMRES iterations, and
-    extrapolate to one full solve (the same algorithm needs `iters_needed` iterations)."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-    from oracle import Problem as OProblem, transport as OT
+def oracle_sample(spec, ss, sa, iters_needed: int, sample_iters: int, dsa: bool = True):
+    """Time the CPU oracle on one instance: b~ plus a bounded number of FGMRES iterations (preconditioned by
+    the oracle's DSA V-cycle when dsa, whose set-up is timed too), and extrapolate to one full solve (the
+    same algorithm needs `iters_needed` iterations; the ROMSAD applies of the window cost a small dense
+    solve each and are left out)."""
+    from oracle import Problem as OProblem, dsa as ODSA, transport as OT
     from oracle.krylov import fgmres
     p = OProblem(spec, 0, ss, sa)
     t0 = time.perf_counter()
     bt = OT.rhs_btilde(p)
     t1 = time.perf_counter()
-    fgmres(lambda z: OT.Atilde_apply(p, z), bt, None, restart=min(sample_iters, 128), rtol=1e-30,
+    pre = None
+    if dsa:
+        mg = ODSA.MultigridDsa(p, "partial")
+        pre = lambda j, v: mg.apply(v)
+    t_setup = time.perf_counter() - t1
+    t1b = time.perf_counter()
+    fgmres(lambda z: OT.Atilde_apply(p, z), bt, pre, restart=min(sample_iters, 128), rtol=1e-30,
            max_iter=sample_iters, true_residual_check=False)
     t2 = time.perf_counter()
-    per_iter = (t2 - t1) / sample_iters
-    solve_s = (t1 - t0) + iters_needed * per_iter + (t1 - t0)   # b~, iterations, final FP64 residual
+    per_iter = (t2 - t1b) / sample_iters
+    solve_s = (t1 - t0) + t_setup + iters_needed * per_iter + (t1 - t0)   # b~, DSA set-up, iterations, residual
+    what = "FGMRES-DSA" if dsa else "FGMRES"
     return {"value": 1.0 / solve_s, "unit": "param solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"b~ + {sample_iters} FGMRES iterations of one {spec.name} instance on 1 host core "
+            "sample": f"b~ + {sample_iters} {what} iterations of one {spec.name} instance on 1 host core "
                       f"({t2 - t0:.1f} s), extrapolated to {iters_needed} iterations + 1 residual sweep"}
 
 
@@ -170,8 +180,9 @@ def bench_config(args, spec, B):
     """The workload description both arms print (no model keys: the workload is named by its sizes)."""
     return {"workload": args.workload, "instances_per_step": B, "mesh": f"{spec.nx[0]}x{spec.ny[0]}",
             "directions": spec.n_directions, "restart": args.restart,
-            "preconditioner": f"ROMSAD rank {getattr(args, 'rom_rank', 0) or spec.rom_rank} (window {spec.window}, kept after "
-                              f"the window)",
+            "preconditioner": f"ROMSAD rank {getattr(args, 'rom_rank', 0) or spec.rom_rank} (window {spec.window}), then "
+                              + ("DSA (partially consistent, one multigrid V-cycle)" if getattr(args, "post", "dsa") == "dsa"
+                                 else "ROMSAD kept after the window"),
             "warm_start": "MLP 8-128-128-r (mixed path only)",
             "l2": "flushed (256 MiB write) before every timed step"}
 
@@ -185,9 +196,9 @@ def run_reference(args, spec, B, world, rank):
     t_start = time.perf_counter()
     one = spec.with_instances(spec.nx[:1], spec.ny[:1])
     for _ in range(args.warmup):   # untimed warm-up samples
-        oracle_sample(one, ss[0], sa[0], iters, args.ref_sample)
+        oracle_sample(one, ss[0], sa[0], iters, args.ref_sample, getattr(args, "post", "dsa") == "dsa")
     for s in range(args.steps):
-        cb = oracle_sample(one, ss[0], sa[0], iters, args.ref_sample)
+        cb = oracle_sample(one, ss[0], sa[0], iters, args.ref_sample, getattr(args, "post", "dsa") == "dsa")
         vals.append(1.0 / cb["value"])
     total = sum(vals)
     value = args.steps * B / total if B else 0.0
@@ -203,6 +214,14 @@ def run_reference(args, spec, B, world, rank):
 
 
 # ------------------------------------------------------------------ GPU legs
+def post_kwargs(RB, args):
+    """fgmres_solve keywords of the preconditioner after the ROMSAD window."""
+    if args.post == "dsa":
+        return {"post_mode": RB.RTE_POST_DSA,
+                "dsa_variant": RB.RTE_DSA_LUMPED if args.dsa_variant == "lumped" else RB.RTE_DSA_PARTIAL}
+    return {"post_mode": RB.RTE_POST_ROM}
+
+
 def measure_sweep_hbm(RB, torch, dev, stream, flush, reps=5, config=3):
     """Angular-output sweep (rte_sweep, FP32) over a whole batched workload: an HBM-bound write of
     N_Omega * N_dof * 4 bytes (both duplicate directions stored), timed with CUDA events after warm-up."""
@@ -279,7 +298,7 @@ def measure_batched(RB, torch, dev, stream, flush, args, reps=1):
                                 ("fp64", RB.RTE_MODE_FP64, False)):
         RB.fgmres_solve(prob, rl, phi, restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec3.window,
                         mode=mode, inner_rtol=args.inner_rtol, max_outer=30, stream=stream,
-                        raise_on_fail=False, learned_warm_start=learned)   # warm-up / tuning
+                        raise_on_fail=False, learned_warm_start=learned, **post_kwargs(RB, args))   # warm-up / tuning
         times, st_all = [], []
         for _ in range(reps):
             flush.zero_()
@@ -289,7 +308,8 @@ def measure_batched(RB, torch, dev, stream, flush, args, reps=1):
             e0.record(stream)
             st = RB.fgmres_solve(prob, rl, phi, restart=args.restart, rtol=1e-8, max_iter=args.max_iter,
                                  window=spec3.window, mode=mode, inner_rtol=args.inner_rtol, max_outer=30,
-                                 stream=stream, raise_on_fail=False, learned_warm_start=learned)
+                                 stream=stream, raise_on_fail=False, learned_warm_start=learned,
+                                 **post_kwargs(RB, args))
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -321,7 +341,7 @@ def measure_learned_eval(RB, torch, dev, stream, flush, args, spec, rom, n_test=
                      ("plain_romsad", {})):
         common = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window,
                       mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol, max_outer=30, stream=stream,
-                      raise_on_fail=False, **kw)
+                      raise_on_fail=False, **kw, **post_kwargs(RB, args))
         RB.fgmres_solve(prob, roms, phi, **common)   # warm-up / tuning
         flush.zero_()
         torch.cuda.synchronize()
@@ -359,7 +379,11 @@ def main():
     ap.add_argument("--workload", default="square2d_64")
     ap.add_argument("--restart", type=int, default=128)
     ap.add_argument("--max-iter", type=int, default=6000)
-    ap.add_argument("--inner-rtol", type=float, default=1e-2)
+    ap.add_argument("--inner-rtol", type=float, default=None,
+                    help="inner target of the mixed refinement (default 1e-3 with DSA after the window, else 1e-2)")
+    ap.add_argument("--post", default="dsa", choices=["dsa", "rom"],
+                    help="preconditioner after the ROMSAD window: DSA (the paper's) or ROMSAD kept")
+    ap.add_argument("--dsa-variant", default="partial", choices=["partial", "lumped"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mlp-epochs", type=int, default=300)
     ap.add_argument("--no-sweep-hbm", action="store_true")
@@ -371,10 +395,14 @@ def main():
                     help="training draws of the greedy and the MLP (2048 leaves the network less trained in the "
                          "same epoch budget)")
     ap.add_argument("--ref-sample", type=int, default=40, help="oracle FGMRES iterations per reference step")
-    ap.add_argument("--ref-iters", type=int, default=180,
-                    help="iterations of a full solve for the extrapolation (the FP64 FGMRES-ROMSAD solve of this "
-                         "workload takes 176-186)")
+    ap.add_argument("--ref-iters", type=int, default=None,
+                    help="iterations of a full solve for the extrapolation (default: those of the FP64 solve of this "
+                         "workload on the GPU, 16 with DSA after the window, 180 with ROMSAD kept)")
     args = ap.parse_args()
+    if args.inner_rtol is None:
+        args.inner_rtol = 1e-3 if args.post == "dsa" else 1e-2
+    if args.ref_iters is None:
+        args.ref_iters = 16 if args.post == "dsa" else 180
     spec, B = workload_spec(args.workload)
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -415,7 +443,8 @@ def main():
     RB.attach_mlp(rom, net)
     t_offline = time.perf_counter() - t_off
     roms = [rom] * B
-    common = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window, stream=stream)
+    common = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window, stream=stream,
+                  **post_kwargs(RB, args))
 
     def solve(mode, learned=True, slot=False):
         if mode in (RB.RTE_MODE_MIXED, RB.RTE_MODE_MIXED_F64KRYLOV):
@@ -423,7 +452,7 @@ def main():
                                    learned_warm_start=learned, learned_slot=slot, **common)
         return RB.fgmres_solve(prob, roms, phi, mode=mode, true_residual_check=True, **common)
 
-    def timed_loop(mode, learned=True, slot=False):
+    def timed_loop(mode, learned=True, slot=False, solver=None):
         per_step, stats_all = [], []
         for s in range(n_sets):
             ss, sa = params(s)
@@ -433,7 +462,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st = solve(mode, learned, slot)
+            st = solve(mode, learned, slot) if solver is None else solver()
             e1.record(stream)
             torch.cuda.synchronize()
             if s >= args.warmup:
@@ -459,6 +488,15 @@ def main():
     t_slot, st_slot = timed_loop(RB.RTE_MODE_MIXED, learned=False, slot=True)
     # the precision form with FP64 Krylov vectors, MGS and Givens around the FP32 sweeps
     t_f64k, st_f64k = timed_loop(RB.RTE_MODE_MIXED_F64KRYLOV)
+    # the mixed path with ROMSAD kept after the window (no DSA), learned start, inner target 1e-2
+    base_kw = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window, stream=stream)
+    t_prom, st_prom = timed_loop(None, solver=lambda: RB.fgmres_solve(
+        prob, roms, phi, mode=RB.RTE_MODE_MIXED, inner_rtol=1e-2, max_outer=30, learned_warm_start=True,
+        post_mode=RB.RTE_POST_ROM, **base_kw))
+    # right-preconditioned GMRES-DSA (no ROM), mixed
+    t_gdsa, st_gdsa = timed_loop(None, solver=lambda: RB.fgmres_solve(
+        prob, None, phi, mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol, max_outer=30,
+        post_mode=RB.RTE_POST_DSA, **base_kw))
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop()
@@ -467,6 +505,8 @@ def main():
     plain_s = max_over_ranks(world, sum(t_plain) / 1e3)
     slot_s = max_over_ranks(world, sum(t_slot) / 1e3)
     f64k_s = max_over_ranks(world, sum(t_f64k) / 1e3)
+    prom_s = max_over_ranks(world, sum(t_prom) / 1e3)
+    gdsa_s = max_over_ranks(world, sum(t_gdsa) / 1e3)
     solves = args.steps * B * world
     value = solves / mixed_s
     fp64_value = solves / fp64_s
@@ -506,6 +546,22 @@ def main():
 
     ms32 = time_op(z32, w32)
     ms64 = time_op(z64, w64)
+
+    def time_dsa(reps=20):
+        # rte_dsa_apply: the per-parameter set-up plus one V-cycle, FP32 vectors
+        for _ in range(3):
+            prob.dsa_apply(z32, w32, stream=stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            prob.dsa_apply(z32, w32, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_dsa = time_dsa() if args.post == "dsa" else None
     cells = sum(nx * ny for nx, ny in zip(spec.nx[:B], spec.ny[:B]))
     nu = prob.info.n_unique_directions
     flops = SWEEP_FLOPS_PER_CELL_DIR * cells * nu
@@ -550,6 +606,12 @@ def main():
         "mixed_fp64_krylov": {"value": solves / f64k_s, "unit": "param solves/s",
                               "iterations_mean": statistics.mean(s["iterations"] for s in st_f64k),
                               "true_rel_residual_max": max(s["true_rel_residual"] for s in st_f64k)},
+        "mixed_post_rom": {"value": solves / prom_s, "unit": "param solves/s",
+                           "iterations_mean": statistics.mean(s["iterations"] for s in st_prom),
+                           "note": "ROMSAD kept after the window instead of DSA, learned start, inner target 1e-2"},
+        "gmres_dsa_mixed": {"value": solves / gdsa_s, "unit": "param solves/s",
+                            "iterations_mean": statistics.mean(s["iterations"] for s in st_gdsa),
+                            "note": "no ROM: DSA from the first iteration"},
         "speedup_mixed_vs_fp64": value / fp64_value,
         "offline": {"greedy_s": t_greedy, "total_s": t_offline, "rank": rep["rank"], "sampled": len(rep["sampled"]),
                     "mlp_final_loss": mlp_loss},
@@ -563,6 +625,7 @@ def main():
         "e2e": {"value": solves / e2e_s, "unit": "param solves/s", "h2d_bytes_per_step": 2 * R * 8 * B,
                 "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(launches_mixed * args.steps / n_sets),
+        "dsa_apply_us": None if ms_dsa is None else 1e3 * ms_dsa,
         "roofline": roof,
         "sweep_hbm": sweep_hbm,
         "batched": batched,
@@ -573,7 +636,7 @@ def main():
         ss, sa = params(args.warmup)
         iters = int(round(statistics.mean(s["iterations"] for s in st_fp64)))
         line["cpu_baseline"] = oracle_sample(spec.with_instances(spec.nx[:1], spec.ny[:1]), ss[0], sa[0], iters,
-                                             args.ref_sample)
+                                             args.ref_sample, args.post == "dsa")
     print(json.dumps(line))
 
 

@@ -24,9 +24,14 @@
 //            cell is the sum over its 4 children of I^T E_child I.
 //   Vertex levels: one damped point-Jacobi step before and after the coarse correction; the coarsest
 //            level (<= kMaxCoarse vertices) is solved with its dense inverse, formed at set-up.
-// Everything of one instance is done by one thread block (barriers are __syncthreads only), FP32.
-// k_dsa_setup runs once per parameter set, k_dsa_vcycle once per preconditioner apply.
+// FP32 throughout.  Set-up once per parameter set (k_dsa_setup_cells over every cell of every instance,
+// k_dsa_setup_levels one block per instance), then k_dsa_vcycle once per preconditioner apply, one
+// cluster of blocks per instance (hardware cluster barriers only: no spin-waits).
+#include <cooperative_groups.h>
+
+#include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -37,8 +42,10 @@ namespace {
 
 constexpr int kMaxLevels = 16;
 constexpr int kMaxCoarse = 100;
-constexpr int kThreads = 1024;
-constexpr int kSetupThreads = 512;
+constexpr int kThreads = 512;         // per block of the V-cycle cluster
+constexpr int kCluster = 8;           // blocks per instance in the V-cycle
+constexpr int kClusterVerts = 2048;   // vertex levels at least this large are split over the cluster
+constexpr int kSetupThreads = 256;
 constexpr float kSqrt3 = 1.7320508075688772f;
 
 struct DsaInst {
@@ -180,7 +187,25 @@ __device__ __forceinline__ Nb nb_of(int ix, int iy, int nx, int ny, int d) {
   return n;
 }
 
+// L2 loads of data written earlier in the same launch by other thread blocks of the cluster (the L1 of an
+// SM is not coherent with the others)
+__device__ __forceinline__ float ldg2(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ void load4cg(const float* p, float* x) {
+  const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+  x[0] = v.x;
+  x[1] = v.y;
+  x[2] = v.z;
+  x[3] = v.w;
+}
+
+template <bool CG>
+__device__ __forceinline__ float ldv(const float* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
 // y = A_l u at vertex (ix, iy) of a level with ncx x ncy cells and element matrices E [cells][4][4]
+template <bool CG>
 __device__ float vertex_apply(const float* E, const float* u, int ncx, int ncy, int ix, int iy) {
   const int nvx = ncx + 1;
   float y = 0.f;
@@ -193,122 +218,138 @@ __device__ float vertex_apply(const float* E, const float* u, int ncx, int ncy, 
       const int cx = ix - 1 + sx;
       if (cx < 0 || cx >= ncx) continue;
       const int qv = (ix - cx) + 2 * (iy - cy);
-      const float* e = E + ((size_t)(cy * ncx + cx) * 16 + qv * 4);
+      float e[4];
+      load4(E + ((size_t)(cy * ncx + cx) * 16 + qv * 4), e);
       const int v0 = cy * nvx + cx;
-      y += e[0] * u[v0] + e[1] * u[v0 + 1] + e[2] * u[v0 + nvx] + e[3] * u[v0 + nvx + 1];
+      y += e[0] * ldv<CG>(u + v0) + e[1] * ldv<CG>(u + v0 + 1) + e[2] * ldv<CG>(u + v0 + nvx) +
+           e[3] * ldv<CG>(u + v0 + nvx + 1);
     }
   }
   return y;
 }
 
+// B_d^{-1} of one cell (4 dofs) from its sigma_t
+__device__ __forceinline__ void binv_of(float st, int d, const DsaConst& k, const float* hs, float* out) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    float Bv = 3.f * k.mu2[d] * st;
+    if (k.lumped)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) Bv += 1.5f * k.c[d][e] * (((q >> e) & 1) ? 6.f : 2.f) / hs[e];
+    out[q] = Bv > 0.f ? 1.f / Bv : 0.f;   // a void cell carries no diffusion
+  }
+}
+
 // ----------------------------------------------------------------------------------------------- set-up
-__global__ void __launch_bounds__(kSetupThreads) k_dsa_setup(const InstInfo* inst, const DsaInst* dinfo,
-                                                             float* base, const double* sig_s, const double* sig_t,
-                                                             int R, int rx, int ry, DsaConst k) {
+// Per cell, every instance at once (grid [cells / kSetupThreads, B]): cross sections, B_d^{-1}, the
+// inverted 4x4 diagonal block of K and the level-1 element matrix.  Neighbours' B^{-1} are recomputed
+// from their sigma_t, so cells are independent.
+__global__ void __launch_bounds__(kSetupThreads) k_dsa_setup_cells(const DsaInst* dinfo, float* base,
+                                                                   const double* sig_s, const double* sig_t, int R,
+                                                                   int rx, int ry, DsaConst k) {
+  const int b = blockIdx.y;
+  const DsaInst& di = dinfo[b];
+  const int nx = di.nx, ny = di.ny, nc = nx * ny;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
+  const int cxr = nx / rx, cyr = ny / ry;
+  const float hs[2] = {di.hx, di.hy};
+  auto st_of = [&](int cell) {
+    const int ix = cell % nx, iy = cell / nx;
+    return (float)sig_t[(size_t)b * R + (iy / cyr) * rx + ix / cxr];
+  };
+  const int ix = c % nx, iy = c / nx;
+  const int reg = (iy / cyr) * rx + ix / cxr;
+  const float ss = (float)sig_s[(size_t)b * R + reg];
+  const float st = (float)sig_t[(size_t)b * R + reg];
+  const float sa = st - ss;
+  base[di.o_sgs + c] = ss;
+  base[di.o_sga + c] = sa;
+  float bc[2][4];
+  binv_of(st, 0, k, hs, bc[0]);
+  binv_of(st, 1, k, hs, bc[1]);
+  for (int d = 0; d < 2; ++d)
+    for (int q = 0; q < 4; ++q) base[di.o_binv + (size_t)c * 8 + d * 4 + q] = bc[d][q];
+  const Axis ax[2] = {Axis(di.hx), Axis(di.hy)};
+  const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
+  // diagonal block of K, column by column: K e_col restricted to this cell
+  float Kc[16];
+  for (int col = 0; col < 4; ++col) {
+    float e[4] = {0.f, 0.f, 0.f, 0.f};
+    e[col] = 1.f;
+    float out[4];
+    for (int q = 0; q < 4; ++q) out[q] = sa * e[q];
+    for (int d = 0; d < 2; ++d) {
+      const Nb n = nb_of(ix, iy, nx, ny, d);
+      float tmp[4];
+      dj_cell(e, zero4, zero4, n.l, n.h, d, ax[d], tmp);
+      for (int q = 0; q < 4; ++q) out[q] -= k.kappa[d] * tmp[q];
+      // Y = B^{-1} D_C e on this cell and its neighbours (e lives on this cell only)
+      float Yc[4], Yl[4] = {0.f, 0.f, 0.f, 0.f}, Yh[4] = {0.f, 0.f, 0.f, 0.f}, bn[4];
+      dc_cell(e, zero4, zero4, n.l, n.h, d, ax[d], Yc);
+      for (int q = 0; q < 4; ++q) Yc[q] *= bc[d][q];
+      if (n.l) {
+        dc_cell(zero4, zero4, e, true, true, d, ax[d], Yl);
+        binv_of(st_of(n.cl), d, k, hs, bn);
+        for (int q = 0; q < 4; ++q) Yl[q] *= bn[q];
+      }
+      if (n.h) {
+        dc_cell(zero4, e, zero4, true, true, d, ax[d], Yh);
+        binv_of(st_of(n.ch), d, k, hs, bn);
+        for (int q = 0; q < 4; ++q) Yh[q] *= bn[q];
+      }
+      dc_cell(Yc, Yl, Yh, n.l, n.h, d, ax[d], tmp);
+      const float f = 3.f * k.mu2[d] * k.mu2[d];
+      for (int q = 0; q < 4; ++q) out[q] -= f * tmp[q];
+    }
+    for (int q = 0; q < 4; ++q) Kc[q * 4 + col] = out[q];
+  }
+  // Gauss-Jordan inverse in place (symmetric positive definite: no pivoting)
+  for (int p = 0; p < 4; ++p) {
+    const float piv = 1.f / Kc[p * 4 + p];
+    Kc[p * 4 + p] = 1.f;
+    for (int q = 0; q < 4; ++q) Kc[p * 4 + q] *= piv;
+    for (int r = 0; r < 4; ++r) {
+      if (r == p) continue;
+      const float f = Kc[r * 4 + p];
+      Kc[r * 4 + p] = 0.f;
+      for (int q = 0; q < 4; ++q) Kc[r * 4 + q] -= f * Kc[p * 4 + q];
+    }
+  }
+  for (int q = 0; q < 16; ++q) base[di.o_kinv + (size_t)c * 16 + q] = Kc[q];
+  // element matrix: P^T (sigma_a + sum_e kappa_e J_e) P + sum_d 3 mu2_d^2 (G_d P)^T B_d^{-1} (G_d P)
+  float Pq[4][4], M[4][4], G[2][4][4];
+  for (int q = 0; q < 4; ++q) {
+    for (int kk = 0; kk < 4; ++kk) Pq[q][kk] = pc_entry(kk, q, di.hx, di.hy);
+    for (int kk = 0; kk < 4; ++kk) M[q][kk] = sa * Pq[q][kk];
+    for (int d = 0; d < 2; ++d) {
+      const Nb n = nb_of(ix, iy, nx, ny, d);
+      float tmp[4];
+      mdj_cont(Pq[q], n.l, n.h, d, ax[d], tmp);
+      for (int kk = 0; kk < 4; ++kk) M[q][kk] += k.kappa[d] * tmp[kk];
+      dc_cont(Pq[q], n.l, n.h, d, ax[d], G[d][q]);
+    }
+  }
+  float* E1 = base + di.o_E[1];
+  for (int q = 0; q < 4; ++q)
+    for (int q2 = 0; q2 < 4; ++q2) {
+      float s = 0.f;
+      for (int kk = 0; kk < 4; ++kk) s += Pq[q][kk] * M[q2][kk];
+      for (int d = 0; d < 2; ++d) {
+        const float f = 3.f * k.mu2[d] * k.mu2[d];
+        for (int kk = 0; kk < 4; ++kk) s += f * G[d][q][kk] * bc[d][kk] * G[d][q2][kk];
+      }
+      E1[(size_t)c * 16 + q * 4 + q2] = s;
+    }
+}
+
+// Per instance (one block): coarse element matrices, inverse diagonals and the dense inverse of the
+// coarsest level.
+__global__ void __launch_bounds__(kSetupThreads) k_dsa_setup_levels(const DsaInst* dinfo, float* base) {
   __shared__ float A[kMaxCoarse * kMaxCoarse];
   const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
   const DsaInst& di = dinfo[b];
-  const int nx = di.nx, ny = di.ny, nc = nx * ny;
-  const int cxr = nx / rx, cyr = ny / ry;
-  float* sgs = base + di.o_sgs;
-  float* sga = base + di.o_sga;
-  float* binv = base + di.o_binv;
-  float* kinv = base + di.o_kinv;
-  const float hs[2] = {di.hx, di.hy};
-  // S1: per-cell cross sections and B_d^{-1}
-  for (int c = tid; c < nc; c += nth) {
-    const int ix = c % nx, iy = c / nx;
-    const int reg = (iy / cyr) * rx + ix / cxr;
-    const float ss = (float)sig_s[(size_t)b * R + reg];
-    const float st = (float)sig_t[(size_t)b * R + reg];
-    sgs[c] = ss;
-    sga[c] = st - ss;
-#pragma unroll
-    for (int d = 0; d < 2; ++d)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float Bv = 3.f * k.mu2[d] * st;
-        if (k.lumped)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) Bv += 1.5f * k.c[d][e] * (((q >> e) & 1) ? 6.f : 2.f) / hs[e];
-        binv[(size_t)c * 8 + d * 4 + q] = Bv > 0.f ? 1.f / Bv : 0.f;   // a void cell carries no diffusion
-      }
-  }
-  __syncthreads();
-  // S2: the 4x4 diagonal block of K per cell (inverted) and the level-1 element matrices
-  const Axis ax[2] = {Axis(di.hx), Axis(di.hy)};
-  float* E1 = base + di.o_E[1];
-  for (int c = tid; c < nc; c += nth) {
-    const int ix = c % nx, iy = c / nx;
-    float Kc[16];
-    const float zero4[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int col = 0; col < 4; ++col) {
-      float e[4] = {0.f, 0.f, 0.f, 0.f};
-      e[col] = 1.f;
-      float out[4];
-      for (int q = 0; q < 4; ++q) out[q] = sga[c] * e[q];
-      for (int d = 0; d < 2; ++d) {
-        const Nb n = nb_of(ix, iy, nx, ny, d);
-        float tmp[4];
-        dj_cell(e, zero4, zero4, n.l, n.h, d, ax[d], tmp);
-        for (int q = 0; q < 4; ++q) out[q] -= k.kappa[d] * tmp[q];
-        // Y = B^{-1} D_C e on the cell and its neighbours (e lives on this cell only)
-        float Yc[4], Yl[4] = {0.f, 0.f, 0.f, 0.f}, Yh[4] = {0.f, 0.f, 0.f, 0.f};
-        dc_cell(e, zero4, zero4, n.l, n.h, d, ax[d], Yc);
-        for (int q = 0; q < 4; ++q) Yc[q] *= binv[(size_t)c * 8 + d * 4 + q];
-        if (n.l) {
-          dc_cell(zero4, zero4, e, true, true, d, ax[d], Yl);
-          for (int q = 0; q < 4; ++q) Yl[q] *= binv[(size_t)n.cl * 8 + d * 4 + q];
-        }
-        if (n.h) {
-          dc_cell(zero4, e, zero4, true, true, d, ax[d], Yh);
-          for (int q = 0; q < 4; ++q) Yh[q] *= binv[(size_t)n.ch * 8 + d * 4 + q];
-        }
-        dc_cell(Yc, Yl, Yh, n.l, n.h, d, ax[d], tmp);
-        const float f = 3.f * k.mu2[d] * k.mu2[d];
-        for (int q = 0; q < 4; ++q) out[q] -= f * tmp[q];
-      }
-      for (int q = 0; q < 4; ++q) Kc[q * 4 + col] = out[q];
-    }
-    // Gauss-Jordan inverse in place (symmetric positive definite: no pivoting)
-    for (int p = 0; p < 4; ++p) {
-      const float piv = 1.f / Kc[p * 4 + p];
-      Kc[p * 4 + p] = 1.f;
-      for (int q = 0; q < 4; ++q) Kc[p * 4 + q] *= piv;
-      for (int r = 0; r < 4; ++r) {
-        if (r == p) continue;
-        const float f = Kc[r * 4 + p];
-        Kc[r * 4 + p] = 0.f;
-        for (int q = 0; q < 4; ++q) Kc[r * 4 + q] -= f * Kc[p * 4 + q];
-      }
-    }
-    for (int q = 0; q < 16; ++q) kinv[(size_t)c * 16 + q] = Kc[q];
-    // element matrix: P^T (sigma_a + sum_e kappa_e J_e) P + sum_d 3 mu2_d^2 (G_d P)^T B_d^{-1} (G_d P)
-    float Pq[4][4], M[4][4], G[2][4][4];
-    for (int q = 0; q < 4; ++q) {
-      for (int kk = 0; kk < 4; ++kk) Pq[q][kk] = pc_entry(kk, q, di.hx, di.hy);
-      for (int kk = 0; kk < 4; ++kk) M[q][kk] = sga[c] * Pq[q][kk];
-      for (int d = 0; d < 2; ++d) {
-        const Nb n = nb_of(ix, iy, nx, ny, d);
-        float tmp[4];
-        mdj_cont(Pq[q], n.l, n.h, d, ax[d], tmp);
-        for (int kk = 0; kk < 4; ++kk) M[q][kk] += k.kappa[d] * tmp[kk];
-        dc_cont(Pq[q], n.l, n.h, d, ax[d], G[d][q]);
-      }
-    }
-    for (int q = 0; q < 4; ++q)
-      for (int q2 = 0; q2 < 4; ++q2) {
-        float s = 0.f;
-        for (int kk = 0; kk < 4; ++kk) s += Pq[q][kk] * M[q2][kk];
-        for (int d = 0; d < 2; ++d) {
-          const float f = 3.f * k.mu2[d] * k.mu2[d];
-          for (int kk = 0; kk < 4; ++kk) s += f * G[d][q][kk] * binv[(size_t)c * 8 + d * 4 + kk] * G[d][q2][kk];
-        }
-        E1[(size_t)c * 16 + q * 4 + q2] = s;
-      }
-  }
-  __syncthreads();
-  // S3: coarse element matrices, sum over the 4 children of I^T E_child I
+  // coarse element matrices: sum over the 4 children of I^T E_child I
   for (int l = 2; l <= di.L; ++l) {
     const int ncx = di.ncx[l], ncy = di.ncy[l], fcx = di.ncx[l - 1];
     const float* Ef = base + di.o_E[l - 1];
@@ -344,7 +385,7 @@ __global__ void __launch_bounds__(kSetupThreads) k_dsa_setup(const InstInfo* ins
     }
     __syncthreads();
   }
-  // S4: inverse diagonals of the vertex levels above the coarsest
+  // inverse diagonals of the vertex levels above the coarsest
   for (int l = 1; l < di.L; ++l) {
     const int ncx = di.ncx[l], ncy = di.ncy[l], nvx = ncx + 1, nv = nvx * (ncy + 1);
     const float* E = base + di.o_E[l];
@@ -362,47 +403,54 @@ __global__ void __launch_bounds__(kSetupThreads) k_dsa_setup(const InstInfo* ins
       dinv[v] = 1.f / s;
     }
   }
-  // S5: dense inverse of the coarsest level (Gauss-Jordan in shared memory, one row per thread)
-  {
-    const int l = di.L, ncx = di.ncx[l], ncy = di.ncy[l], nvx = ncx + 1, n = nvx * (ncy + 1);
-    const float* E = base + di.o_E[l];
-    for (int idx = tid; idx < n * n; idx += nth) {
-      const int i = idx / n, j = idx % n;
-      const int ix = i % nvx, iy = i / nvx, jx = j % nvx, jy = j / nvx;
-      float s = 0.f;
-      if (abs(ix - jx) <= 1 && abs(iy - jy) <= 1)
-        for (int cy = max(iy, jy) - 1; cy <= min(iy, jy); ++cy)
-          for (int cx = max(ix, jx) - 1; cx <= min(ix, jx); ++cx) {
-            if (cx < 0 || cx >= ncx || cy < 0 || cy >= ncy) continue;
-            const int qi = (ix - cx) + 2 * (iy - cy), qj = (jx - cx) + 2 * (jy - cy);
-            s += E[(size_t)(cy * ncx + cx) * 16 + qi * 4 + qj];
-          }
-      A[idx] = s;
-    }
-    for (int p = 0; p < n; ++p) {
-      __syncthreads();
-      const float piv = 1.f / A[p * n + p];
-      const float fcol = tid < n ? A[tid * n + p] : 0.f;
-      __syncthreads();
-      if (tid < n) A[p * n + tid] = (tid == p ? 1.f : A[p * n + tid]) * piv;
-      __syncthreads();
-      if (tid < n && tid != p)
-        for (int j = 0; j < n; ++j) A[tid * n + j] = (j == p ? 0.f : A[tid * n + j]) - fcol * A[p * n + j];
-    }
-    __syncthreads();
-    float* ainv = base + di.o_ainv;
-    for (int idx = tid; idx < n * n; idx += nth) ainv[idx] = A[idx];
+  // dense inverse of the coarsest level (Gauss-Jordan in shared memory, one row per thread)
+  const int l = di.L, ncx = di.ncx[l], ncy = di.ncy[l], nvx = ncx + 1, n = nvx * (ncy + 1);
+  const float* E = base + di.o_E[l];
+  for (int idx = tid; idx < n * n; idx += nth) {
+    const int i = idx / n, j = idx % n;
+    const int ix = i % nvx, iy = i / nvx, jx = j % nvx, jy = j / nvx;
+    float s = 0.f;
+    if (abs(ix - jx) <= 1 && abs(iy - jy) <= 1)
+      for (int cy = max(iy, jy) - 1; cy <= min(iy, jy); ++cy)
+        for (int cx = max(ix, jx) - 1; cx <= min(ix, jx); ++cx) {
+          if (cx < 0 || cx >= ncx || cy < 0 || cy >= ncy) continue;
+          const int qi = (ix - cx) + 2 * (iy - cy), qj = (jx - cx) + 2 * (jy - cy);
+          s += E[(size_t)(cy * ncx + cx) * 16 + qi * 4 + qj];
+        }
+    A[idx] = s;
   }
+  for (int p = 0; p < n; ++p) {
+    __syncthreads();
+    const float piv = 1.f / A[p * n + p];
+    const float fcol = tid < n ? A[tid * n + p] : 0.f;
+    __syncthreads();
+    if (tid < n) A[p * n + tid] = (tid == p ? 1.f : A[p * n + tid]) * piv;
+    __syncthreads();
+    if (tid < n && tid != p)
+      for (int j = 0; j < n; ++j) A[tid * n + j] = (j == p ? 0.f : A[tid * n + j]) - fcol * A[p * n + j];
+  }
+  __syncthreads();
+  float* ainv = base + di.o_ainv;
+  for (int idx = tid; idx < n * n; idx += nth) ainv[idx] = A[idx];
 }
 
 // ---------------------------------------------------------------------------------------------- V-cycle
+// One cluster of kCluster blocks per instance.  The DG stages and the vertex levels with at least
+// kClusterVerts vertices are split over the cluster (barrier: cluster.sync, which orders the global
+// writes; data written in this launch is read through L2); the smaller levels and the coarsest solve
+// are done by block 0 alone.
+namespace cg = cooperative_groups;
+
 template <typename TV>
 __global__ void __launch_bounds__(kThreads) k_dsa_vcycle(const InstInfo* inst, const DsaInst* dinfo, float* base,
                                                          DsaConst k, const TV* v, TV* z, const int* active,
                                                          const int* only) {
-  const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
-  if (active && !active[b]) return;
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+  const int b = blockIdx.x / CS, tid = threadIdx.x, nth = blockDim.x;
+  if (active && !active[b]) return;   // uniform over the cluster
   if (only && !only[b]) return;
+  const int gt = rank * nth + tid, gn = CS * nth;
   __shared__ float Pc[16];
   const DsaInst& di = dinfo[b];
   const InstInfo in = inst[b];
@@ -421,26 +469,33 @@ __global__ void __launch_bounds__(kThreads) k_dsa_vcycle(const InstInfo* inst, c
   const float om = k.omega, omv = k.omega_v;
   if (tid < 16) Pc[tid] = pc_entry(tid >> 2, tid & 3, di.hx, di.hy);   // [k][q]
   __syncthreads();
+  // first vertex level handled by block 0 alone
+  int lsplit = di.L;
+  for (int l = 1; l < di.L; ++l)
+    if ((di.ncx[l] + 1) * (di.ncy[l] + 1) < kClusterVerts) {
+      lsplit = l;
+      break;
+    }
 
-  // K x0 on cell c from x0 and t (= B^{-1} D_C x0 per axis, stored)
+  // K x0 on cell c from x0 and t (= B^{-1} D_C x0 per axis)
   auto Kx = [&](int c, float* out) {
     const int ix = c % nx, iy = c / nx;
     float xc[4];
-    load4(x0 + (size_t)c * 4, xc);
+    load4cg(x0 + (size_t)c * 4, xc);
     for (int q = 0; q < 4; ++q) out[q] = sga[c] * xc[q];
 #pragma unroll
     for (int d = 0; d < 2; ++d) {
       const Nb n = nb_of(ix, iy, nx, ny, d);
       float xl[4], xh[4], tc[4], tl[4], th[4], tmp[4];
-      load4(x0 + (size_t)n.cl * 4, xl);
-      load4(x0 + (size_t)n.ch * 4, xh);
+      load4cg(x0 + (size_t)n.cl * 4, xl);
+      load4cg(x0 + (size_t)n.ch * 4, xh);
       dj_cell(xc, xl, xh, n.l, n.h, d, ax[d], tmp);
 #pragma unroll
       for (int q = 0; q < 4; ++q) out[q] -= k.kappa[d] * tmp[q];
       const float* td = t + (size_t)d * nc * 4;
-      load4(td + (size_t)c * 4, tc);
-      load4(td + (size_t)n.cl * 4, tl);
-      load4(td + (size_t)n.ch * 4, th);
+      load4cg(td + (size_t)c * 4, tc);
+      load4cg(td + (size_t)n.cl * 4, tl);
+      load4cg(td + (size_t)n.ch * 4, th);
       dc_cell(tc, tl, th, n.l, n.h, d, ax[d], tmp);
       const float f = 3.f * k.mu2[d] * k.mu2[d];
 #pragma unroll
@@ -448,26 +503,98 @@ __global__ void __launch_bounds__(kThreads) k_dsa_vcycle(const InstInfo* inst, c
     }
   };
   auto stage_t = [&]() {
-    for (int c = tid; c < nc; c += nth) {
+    for (int c = gt; c < nc; c += gn) {
       const int ix = c % nx, iy = c / nx;
       float xc[4];
-      load4(x0 + (size_t)c * 4, xc);
+      load4cg(x0 + (size_t)c * 4, xc);
 #pragma unroll
       for (int d = 0; d < 2; ++d) {
         const Nb n = nb_of(ix, iy, nx, ny, d);
-        float xl[4], xh[4], out[4];
-        load4(x0 + (size_t)n.cl * 4, xl);
-        load4(x0 + (size_t)n.ch * 4, xh);
+        float xl[4], xh[4], out[4], bi[4];
+        load4cg(x0 + (size_t)n.cl * 4, xl);
+        load4cg(x0 + (size_t)n.ch * 4, xh);
         dc_cell(xc, xl, xh, n.l, n.h, d, ax[d], out);
+        load4(binv + (size_t)c * 8 + d * 4, bi);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) out[q] *= binv[(size_t)c * 8 + d * 4 + q];
+        for (int q = 0; q < 4; ++q) out[q] *= bi[q];
         store4(t + ((size_t)d * nc + c) * 4, out);
       }
     }
   };
+  // Vertex levels.  On entry to level l, b_l and the pre-smoothed u_l = omega D^{-1} b_l are stored
+  // (written by the restriction into l).  descend: r_l = b_l - A u_l, then restriction into l+1 (with its
+  // pre-smoothing).  ascend: u_l += P (u_{l+1} + omega D^{-1} r_{l+1}), the post-smoothing of level l+1
+  // folded into the interpolation (none on the coarsest), then r_l = b_l - A u_l.  The post-smoothing
+  // of level 1 is folded into the interpolation to the DG level.  CG: every load through L2 (stages split
+  // over the cluster); otherwise block 0 alone, plain loads except those of b and u on the first level
+  // of block 0, written by the cluster (ecg: through L2, since an L1 line may hold stale bytes).
+  auto descend = [&](int l, int t0, int tn, auto sync, auto cgtag, bool ecg) {
+    constexpr bool CG = decltype(cgtag)::value;
+    const int ncx = di.ncx[l], ncy = di.ncy[l], nvx = ncx + 1, nv = nvx * (ncy + 1);
+    const float* E = base + di.o_E[l];
+    float* u = base + di.o_u[l];
+    const float* bl = base + di.o_b[l];
+    float* rl = base + di.o_r[l];
+    if (CG || ecg)
+      for (int vv = t0; vv < nv; vv += tn) rl[vv] = __ldcg(bl + vv) - vertex_apply<true>(E, u, ncx, ncy, vv % nvx, vv / nvx);
+    else
+      for (int vv = t0; vv < nv; vv += tn) rl[vv] = bl[vv] - vertex_apply<false>(E, u, ncx, ncy, vv % nvx, vv / nvx);
+    sync();
+    // full-weighting restriction (transpose of bilinear interpolation) and pre-smoothing of level l+1
+    const int Cx = di.ncx[l + 1], Cy = di.ncy[l + 1], nCx = Cx + 1, nC = nCx * (Cy + 1);
+    float* bc = base + di.o_b[l + 1];
+    float* uc = base + di.o_u[l + 1];
+    const float* dinvc = base + di.o_dinv[l + 1];
+    const bool smooth_next = l + 1 < di.L;
+    for (int V = t0; V < nC; V += tn) {
+      const int I = V % nCx, J = V / nCx;
+      float s = 0.f;
+      for (int dj = -1; dj <= 1; ++dj) {
+        const int fy = 2 * J + dj;
+        if (fy < 0 || fy > ncy) continue;
+        for (int dii = -1; dii <= 1; ++dii) {
+          const int fx = 2 * I + dii;
+          if (fx < 0 || fx > ncx) continue;
+          s += (dii == 0 ? 1.f : 0.5f) * (dj == 0 ? 1.f : 0.5f) * ldv<CG>(rl + fy * nvx + fx);
+        }
+      }
+      bc[V] = s;
+      if (smooth_next) uc[V] = omv * dinvc[V] * s;
+    }
+    sync();
+  };
+  auto ascend = [&](int l, int t0, int tn, auto sync, auto cgtag, bool ecg) {
+    constexpr bool CG = decltype(cgtag)::value;
+    const int ncx = di.ncx[l], ncy = di.ncy[l], nvx = ncx + 1, nv = nvx * (ncy + 1);
+    const int nCx = di.ncx[l + 1] + 1;
+    const float* uc = base + di.o_u[l + 1];
+    const float* rc = base + di.o_r[l + 1];
+    const float* dinvc = base + di.o_dinv[l + 1];
+    const float ws = l + 1 < di.L ? omv : 0.f;   // post-smoothing weight of level l+1
+    const float* E = base + di.o_E[l];
+    float* u = base + di.o_u[l];
+    const float* bl = base + di.o_b[l];
+    float* rl = base + di.o_r[l];
+    auto ucf = [&](int V) { return ldv<CG>(uc + V) + (ws != 0.f ? ws * dinvc[V] * ldv<CG>(rc + V) : 0.f); };
+    for (int vv = t0; vv < nv; vv += tn) {
+      // bilinear interpolation: the coarse neighbours of an even index coincide
+      const int ix = vv % nvx, iy = vv / nvx;
+      const int x0i = ix >> 1, y0i = iy >> 1, x1i = (ix + 1) >> 1, y1i = (iy + 1) >> 1;
+      const float uo = (CG || ecg) ? __ldcg(u + vv) : u[vv];
+      u[vv] = uo + 0.25f * (ucf(y0i * nCx + x0i) + ucf(y0i * nCx + x1i) + ucf(y1i * nCx + x0i) + ucf(y1i * nCx + x1i));
+    }
+    sync();
+    for (int vv = t0; vv < nv; vv += tn)
+      rl[vv] = ((CG || ecg) ? __ldcg(bl + vv) : bl[vv]) - vertex_apply<CG>(E, u, ncx, ncy, vv % nvx, vv / nvx);
+    sync();
+  };
+  auto csync = [&]() { cl.sync(); };
+  auto bsync = [&]() { __syncthreads(); };
+  using CgOn = std::integral_constant<bool, true>;
+  using CgOff = std::integral_constant<bool, false>;
 
   // A: b0 = Sigma_s v, x0 = omega Kcc^{-1} b0
-  for (int c = tid; c < nc; c += nth) {
+  for (int c = gt; c < nc; c += gn) {
     float bc[4], xc[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) bc[q] = sgs[c] * (float)vb[(size_t)c * 4 + q];
@@ -480,24 +607,24 @@ __global__ void __launch_bounds__(kThreads) k_dsa_vcycle(const InstInfo* inst, c
     }
     store4(x0 + (size_t)c * 4, xc);
   }
-  __syncthreads();
+  cl.sync();
   stage_t();
-  __syncthreads();
+  cl.sync();
   // C: r0 = b0 - K x0
-  for (int c = tid; c < nc; c += nth) {
+  for (int c = gt; c < nc; c += gn) {
     float kx[4], bc[4];
     Kx(c, kx);
-    load4(b0 + (size_t)c * 4, bc);
+    load4cg(b0 + (size_t)c * 4, bc);
 #pragma unroll
     for (int q = 0; q < 4; ++q) kx[q] = bc[q] - kx[q];
     store4(r0 + (size_t)c * 4, kx);
   }
-  __syncthreads();
+  cl.sync();
   // D: restriction to level 1, b1_v = sum over the cells around v of (P_T^T r0_T)_v
   {
     const int nvx = nx + 1, nv = nvx * (ny + 1);
     float* b1 = base + di.o_b[1];
-    for (int vv = tid; vv < nv; vv += nth) {
+    for (int vv = gt; vv < nv; vv += gn) {
       const int ix = vv % nvx, iy = vv / nvx;
       float s = 0.f;
       for (int sy = 0; sy < 2; ++sy)
@@ -506,90 +633,50 @@ __global__ void __launch_bounds__(kThreads) k_dsa_vcycle(const InstInfo* inst, c
           if (cx < 0 || cx >= nx || cy < 0 || cy >= ny) continue;
           const int qv = (ix - cx) + 2 * (iy - cy);
           float rc[4];
-          load4(r0 + (size_t)(cy * nx + cx) * 4, rc);
+          load4cg(r0 + (size_t)(cy * nx + cx) * 4, rc);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) s += Pc[kk * 4 + qv] * rc[kk];
         }
       b1[vv] = s;
+      if (di.L > 1) base[di.o_u[1] + vv] = omv * base[di.o_dinv[1] + vv] * s;
     }
   }
-  __syncthreads();
-  // vertex levels, descending
-  for (int l = 1; l < di.L; ++l) {
-    const int ncx = di.ncx[l], ncy = di.ncy[l], nvx = ncx + 1, nv = nvx * (ncy + 1);
-    const float* E = base + di.o_E[l];
-    const float* dinv = base + di.o_dinv[l];
-    float* u = base + di.o_u[l];
-    const float* bl = base + di.o_b[l];
-    float* rl = base + di.o_r[l];
-    for (int vv = tid; vv < nv; vv += nth) u[vv] = omv * dinv[vv] * bl[vv];
-    __syncthreads();
-    for (int vv = tid; vv < nv; vv += nth) rl[vv] = bl[vv] - vertex_apply(E, u, ncx, ncy, vv % nvx, vv / nvx);
-    __syncthreads();
-    // full-weighting restriction (transpose of bilinear interpolation)
-    const int Cx = di.ncx[l + 1], Cy = di.ncy[l + 1], nCx = Cx + 1, nC = nCx * (Cy + 1);
-    float* bc = base + di.o_b[l + 1];
-    for (int V = tid; V < nC; V += nth) {
-      const int I = V % nCx, J = V / nCx;
-      float s = 0.f;
-      for (int dj = -1; dj <= 1; ++dj) {
-        const int fy = 2 * J + dj;
-        if (fy < 0 || fy > ncy) continue;
-        for (int dii = -1; dii <= 1; ++dii) {
-          const int fx = 2 * I + dii;
-          if (fx < 0 || fx > ncx) continue;
-          s += (dii == 0 ? 1.f : 0.5f) * (dj == 0 ? 1.f : 0.5f) * rl[fy * nvx + fx];
-        }
-      }
-      bc[V] = s;
-    }
-    __syncthreads();
-  }
-  // coarsest: dense inverse
-  {
+  cl.sync();
+  for (int l = 1; l < lsplit; ++l) descend(l, gt, gn, csync, CgOn{}, true);
+  if (rank == 0) {
+    for (int l = lsplit; l < di.L; ++l) descend(l, tid, nth, bsync, CgOff{}, l == lsplit);
+    // coarsest: dense inverse (b_L from the cluster when nothing was left to block 0)
     const int l = di.L, nvx = di.ncx[l] + 1, n = nvx * (di.ncy[l] + 1);
     const float* ainv = base + di.o_ainv;
     const float* bl = base + di.o_b[l];
     float* u = base + di.o_u[l];
     for (int i = tid; i < n; i += nth) {
       float s = 0.f;
-      for (int j = 0; j < n; ++j) s += ainv[(size_t)i * n + j] * bl[j];
+      if (lsplit == di.L)
+        for (int j = 0; j < n; ++j) s += ainv[(size_t)i * n + j] * __ldcg(bl + j);
+      else
+        for (int j = 0; j < n; ++j) s += ainv[(size_t)i * n + j] * bl[j];
       u[i] = s;
     }
+    __syncthreads();
+    for (int l2 = di.L - 1; l2 >= lsplit; --l2) ascend(l2, tid, nth, bsync, CgOff{}, l2 == lsplit);
   }
-  __syncthreads();
-  // vertex levels, ascending: prolongation, then one damped Jacobi step
-  for (int l = di.L - 1; l >= 1; --l) {
-    const int ncx = di.ncx[l], ncy = di.ncy[l], nvx = ncx + 1, nv = nvx * (ncy + 1);
-    const int nCx = di.ncx[l + 1] + 1;
-    const float* uc = base + di.o_u[l + 1];
-    const float* E = base + di.o_E[l];
-    const float* dinv = base + di.o_dinv[l];
-    float* u = base + di.o_u[l];
-    const float* bl = base + di.o_b[l];
-    float* rl = base + di.o_r[l];
-    for (int vv = tid; vv < nv; vv += nth) {
-      const int ix = vv % nvx, iy = vv / nvx;
-      // bilinear interpolation: the coarse neighbours of an even index coincide
-      const int x0i = ix >> 1, y0i = iy >> 1, x1i = (ix + 1) >> 1, y1i = (iy + 1) >> 1;
-      u[vv] += 0.25f * (uc[y0i * nCx + x0i] + uc[y0i * nCx + x1i] + uc[y1i * nCx + x0i] + uc[y1i * nCx + x1i]);
-    }
-    __syncthreads();
-    for (int vv = tid; vv < nv; vv += nth) rl[vv] = bl[vv] - vertex_apply(E, u, ncx, ncy, vv % nvx, vv / nvx);
-    __syncthreads();
-    for (int vv = tid; vv < nv; vv += nth) u[vv] += omv * dinv[vv] * rl[vv];
-    __syncthreads();
-  }
-  // E: x0 += P_c u1
+  cl.sync();
+  for (int l = lsplit - 1; l >= 1; --l) ascend(l, gt, gn, csync, CgOn{}, true);
+  // E: x0 += P_c (u1 + omega D^{-1} r1), the post-smoothing of level 1 folded in
   {
     const float* u1 = base + di.o_u[1];
+    const float* r1 = base + di.o_r[1];
+    const float* d1 = base + di.o_dinv[1];
+    const float w1 = di.L > 1 ? omv : 0.f;
     const int nvx = nx + 1;
-    for (int c = tid; c < nc; c += nth) {
+    auto uf = [&](int vv) { return ldg2(u1 + vv) + (w1 != 0.f ? w1 * d1[vv] * ldg2(r1 + vv) : 0.f); };
+    for (int c = gt; c < nc; c += gn) {
       const int ix = c % nx, iy = c / nx;
       const int v0 = iy * nvx + ix;
-      const float uq[4] = {u1[v0], u1[v0 + 1], u1[v0 + nvx], u1[v0 + nvx + 1]};
+      const float uq[4] = {uf(v0), uf(v0 + 1), uf(v0 + nvx), uf(v0 + nvx + 1)};
       float xc[4];
-      load4(x0 + (size_t)c * 4, xc);
+      load4cg(x0 + (size_t)c * 4, xc);
 #pragma unroll
       for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
@@ -597,15 +684,15 @@ __global__ void __launch_bounds__(kThreads) k_dsa_vcycle(const InstInfo* inst, c
       store4(x0 + (size_t)c * 4, xc);
     }
   }
-  __syncthreads();
+  cl.sync();
   stage_t();
-  __syncthreads();
+  cl.sync();
   // G: z = v + x0 + omega Kcc^{-1} (b0 - K x0)
-  for (int c = tid; c < nc; c += nth) {
+  for (int c = gt; c < nc; c += gn) {
     float kx[4], bc[4], xc[4];
     Kx(c, kx);
-    load4(b0 + (size_t)c * 4, bc);
-    load4(x0 + (size_t)c * 4, xc);
+    load4cg(b0 + (size_t)c * 4, bc);
+    load4cg(x0 + (size_t)c * 4, xc);
 #pragma unroll
     for (int q = 0; q < 4; ++q) kx[q] = bc[q] - kx[q];
 #pragma unroll
@@ -746,8 +833,12 @@ int dsa_prepare(rte_problem* p, int variant, cudaStream_t st) {
     RTE_CHECK_CUDA(cudaMemcpy(w->d_di.p, w->di.data(), w->di.size() * sizeof(DsaInst), cudaMemcpyHostToDevice));
   }
   const DsaConst k = dsa_constants(p, variant);
-  k_dsa_setup<<<p->B, kSetupThreads, 0, st>>>(p->d_inst.p, w->d_di.p, w->data.p, p->d_sig_s.p, p->d_sig_t.p, p->R,
-                                              p->rx, p->ry, k);
+  int max_nc = 0;
+  for (const DsaInst& d : w->di) max_nc = std::max(max_nc, d.nx * d.ny);
+  k_dsa_setup_cells<<<dim3((max_nc + kSetupThreads - 1) / kSetupThreads, p->B), kSetupThreads, 0, st>>>(
+      w->d_di.p, w->data.p, p->d_sig_s.p, p->d_sig_t.p, p->R, p->rx, p->ry, k);
+  count_launch();
+  k_dsa_setup_levels<<<p->B, kSetupThreads, 0, st>>>(w->d_di.p, w->data.p);
   count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   w->lumped = k.lumped;
@@ -762,12 +853,26 @@ int dsa_launch(rte_problem* p, bool f64, const void* v, void* z, const int* acti
     return RTE_ERR_INVALID_ARG;
   }
   const DsaConst k = dsa_constants(p, w->lumped ? RTE_DSA_LUMPED : RTE_DSA_PARTIAL);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p->B * kCluster);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (f64)
-    k_dsa_vcycle<double><<<p->B, kThreads, 0, st>>>(p->d_inst.p, w->d_di.p, w->data.p, k, (const double*)v,
-                                                    (double*)z, active, only);
+    RTE_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_dsa_vcycle<double>, (const InstInfo*)p->d_inst.p,
+                                      (const DsaInst*)w->d_di.p, w->data.p, k, (const double*)v, (double*)z, active,
+                                      only));
   else
-    k_dsa_vcycle<float><<<p->B, kThreads, 0, st>>>(p->d_inst.p, w->d_di.p, w->data.p, k, (const float*)v,
-                                                   (float*)z, active, only);
+    RTE_CHECK_CUDA(cudaLaunchKernelEx(&cfg, k_dsa_vcycle<float>, (const InstInfo*)p->d_inst.p,
+                                      (const DsaInst*)w->d_di.p, w->data.p, k, (const float*)v, (float*)z, active,
+                                      only));
   count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   return RTE_OK;

@@ -1912,18 +1912,22 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       if (nact == 0) break;
       // inner solve A~ d = ro, zero guess: entirely in FP32 (right-hand side rounded to FP32), or with FP32
       // sweeps and FP64 Krylov vectors, MGS and Givens (RTE_MODE_MIXED_F64KRYLOV)
-      std::vector<int> cap(B, 0);
-      for (int b = 0; b < B; ++b) cap[b] = std::min(inner_cap, o->max_iter - S[b].iterations);
+      // the ROMSAD window counts the iterations of the whole solve: only the first inner solve opens with it
+      std::vector<int> cap(B, 0), done(B, 0);
+      for (int b = 0; b < B; ++b) {
+        cap[b] = std::min(inner_cap, o->max_iter - S[b].iterations);
+        done[b] = S[b].iterations;
+      }
       RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
       RunStats rs;
       if (o->mode == RTE_MODE_MIXED_F64KRYLOV) {
-        RTE_TRY(run_fgmres(C, ro, ws->d.p, true, act, o->inner_rtol, cap, RUN_F32_SWEEP_F64_KRYLOV, false, zero, rs));
+        RTE_TRY(run_fgmres(C, ro, ws->d.p, true, act, o->inner_rtol, cap, RUN_F32_SWEEP_F64_KRYLOV, false, done, rs));
         RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
         k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d.p, p->d_inst.p, ws->active.p);
       } else {
         k_copy_active<<<vg, 256, 0, st>>>(ws->rin32.p, ro, p->d_inst.p, ws->active.p);
         count_launch();
-        RTE_TRY(run_fgmres(C, ws->rin32.p, ws->d32.p, true, act, o->inner_rtol, cap, RUN_F32, false, zero, rs));
+        RTE_TRY(run_fgmres(C, ws->rin32.p, ws->d32.p, true, act, o->inner_rtol, cap, RUN_F32, false, done, rs));
         RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
         k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d32.p, p->d_inst.p, ws->active.p);
       }
@@ -1943,10 +1947,13 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     bool any_esc = false;
     for (int b = 0; b < B; ++b) any_esc = any_esc || esc[b];
     if (any_esc) {
-      std::vector<int> cap(B, 0);
-      for (int b = 0; b < B; ++b) cap[b] = std::max(1, o->max_iter - S[b].iterations);
+      std::vector<int> cap(B, 0), done(B, 0);
+      for (int b = 0; b < B; ++b) {
+        cap[b] = std::max(1, o->max_iter - S[b].iterations);
+        done[b] = S[b].iterations;
+      }
       RunStats rs;
-      RTE_TRY(run_fgmres(C, ws->bt.p, x, false, esc, o->rtol, cap, RUN_F64, o->true_residual_check != 0, zero, rs));
+      RTE_TRY(run_fgmres(C, ws->bt.p, x, false, esc, o->rtol, cap, RUN_F64, o->true_residual_check != 0, done, rs));
       for (int b = 0; b < B; ++b) {
         if (!esc[b]) continue;
         S[b].iterations += rs.iterations[b];
