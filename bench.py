@@ -497,6 +497,10 @@ def main():
     t_gdsa, st_gdsa = timed_loop(None, solver=lambda: RB.fgmres_solve(
         prob, None, phi, mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol, max_outer=30,
         post_mode=RB.RTE_POST_DSA, **base_kw))
+    # SI-ROMSAD (source iteration: the ROM correction in the window, DSA afterwards), FP64
+    t_si, st_si = timed_loop(None, solver=lambda: RB.si_solve(
+        prob, roms, phi, rtol=1e-8, max_iter=2000, window=spec.window, post_mode=RB.RTE_POST_DSA, stream=stream,
+        raise_on_fail=False))
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop()
@@ -507,6 +511,8 @@ def main():
     f64k_s = max_over_ranks(world, sum(t_f64k) / 1e3)
     prom_s = max_over_ranks(world, sum(t_prom) / 1e3)
     gdsa_s = max_over_ranks(world, sum(t_gdsa) / 1e3)
+    si_s = max_over_ranks(world, sum(t_si) / 1e3)
+    si_conv = sum(1 for s in st_si if s["status"] == 0)
     solves = args.steps * B * world
     value = solves / mixed_s
     fp64_value = solves / fp64_s
@@ -612,6 +618,11 @@ def main():
         "gmres_dsa_mixed": {"value": solves / gdsa_s, "unit": "param solves/s",
                             "iterations_mean": statistics.mean(s["iterations"] for s in st_gdsa),
                             "note": "no ROM: DSA from the first iteration"},
+        "si_romsad_fp64": {"value": si_conv * world / si_s, "unit": "param solves/s",
+                           "converged": si_conv, "of": len(st_si),
+                           "iterations_mean": statistics.mean(s["iterations"] for s in st_si),
+                           "iterations_max": max(s["iterations"] for s in st_si),
+                           "note": "source iteration, ROM correction in the window then DSA (FP64)"},
         "speedup_mixed_vs_fp64": value / fp64_value,
         "offline": {"greedy_s": t_greedy, "total_s": t_offline, "rank": rep["rank"], "sampled": len(rep["sampled"]),
                     "mlp_final_loss": mlp_loss},

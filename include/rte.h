@@ -310,6 +310,18 @@ typedef struct fgmres_stats {
 int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_opts* opts, const void* phi0,
                  void* phi, fgmres_stats* stats, void* stream);
 
+/* Source iteration with synthetic acceleration, SI-ROMSAD (Sec. 3.1-3.2, eq. preconditioned-richardson):
+ * phi <- phi + M_l^{-1} (b~ - A~ phi), with M_l = M_ROM for the first opts->window iterations on
+ * instances with a ROM, then opts->post_mode (RTE_POST_DSA: SI-DSA; RTE_POST_ROM: the ROM throughout;
+ * RTE_POST_IDENTITY: classical SI).  Instances without a ROM take DSA from the first iteration when
+ * post_mode is RTE_POST_DSA, no correction otherwise.  Stops when ||b~ - A~ phi||_2 <= rtol ||b~||_2 or
+ * after max_iter iterations.  Uses opts->rtol, max_iter, window, post_mode, dsa_variant; mode must be
+ * RTE_MODE_FP64 (RTE_ERR_UNSUPPORTED otherwise); the other fields are ignored.  Arguments as for
+ * fgmres_solve; stats: iterations, sweeps (b~ plus one per residual: a zero start takes r = b~), status,
+ * true residuals of the returned phi. */
+int si_solve(rte_problem_t p, const romsad_t* roms, const fgmres_opts* opts, const void* phi0, void* phi,
+             fgmres_stats* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -140,6 +140,40 @@ def fgmres(apply_A: Callable[[np.ndarray], np.ndarray], b: np.ndarray,
     return (phi, st, first) if record_first_cycle else (phi, st)
 
 
+def preconditioned_richardson(apply_A: Callable[[np.ndarray], np.ndarray], b: np.ndarray,
+                              precond: Optional[Callable[[int, np.ndarray], np.ndarray]] = None,
+                              phi0: Optional[np.ndarray] = None, rtol: float = 1e-10, max_iter: int = 1000,
+                              rhs_sweeps: int = 1):
+    """Source iteration with synthetic acceleration as a preconditioned Richardson iteration
+    (Sec. 3.2, eq. preconditioned-richardson): phi^(l) = phi^(l-1) + M_l^{-1} r^(l-1), r = b - A phi.
+    precond(l, r) returns M_l^{-1} r (None: M = I, classical SI, eq. richardson).  Stops when
+    ||r||_2 <= rtol ||b||_2, checked on the residual of every iterate.  sweeps counts operator applies:
+    rhs_sweeps for b, one per residual (none for the first one of a zero start, r = b)."""
+    st = SolveStats(sweeps=rhs_sweeps)
+    bnorm = float(np.linalg.norm(b))
+    phi = np.zeros_like(b) if phi0 is None else phi0.astype(np.float64).copy()
+    l = 0
+    while True:
+        if l == 0 and phi0 is None:
+            r = b.copy()
+        else:
+            r = b - apply_A(phi)
+            st.sweeps += 1
+        rel = float(np.linalg.norm(r)) / bnorm if bnorm > 0 else 0.0
+        st.history.append(rel)
+        st.true_rel_residual = st.est_rel_residual = rel
+        st.true_linf_residual = float(np.abs(r).max()) if r.size else 0.0
+        if rel <= rtol:
+            st.converged = True
+            break
+        if st.iterations >= max_iter:
+            break
+        l += 1
+        phi = phi + (r if precond is None else precond(l, r))
+        st.iterations += 1
+    return phi, st
+
+
 def source_iteration(p, n_iter: int, phi0: Optional[np.ndarray] = None):
     """Memory-efficient SI (eq. memory-efficient-SI): phi <- T Sigma_s phi + b~.
 

@@ -109,10 +109,15 @@ def romsad_apply(rom: Rom, p: Problem, v: np.ndarray, A_r: Optional[np.ndarray] 
 
 def make_preconditioner(rom: Optional[Rom], p: Problem, window: int, post: str = "rom"):
     """M_j of eq. ROMSAD-preconditioner: ROM for j <= window; afterwards 'rom', 'identity', or the DSA
-    preconditioner of appendix A ('dsa': fully consistent, 'dsa_pc': partially consistent).  Without a ROM,
-    'dsa'/'dsa_pc' give the right DSA preconditioner for every j (GMRES-DSA) and anything else none."""
-    dsa_kind = {"dsa": "full", "dsa_pc": "partial"}.get(post)
-    D = dsa.Dsa(p, dsa_kind) if dsa_kind is not None else None
+    preconditioner of appendix A ('dsa': fully consistent, 'dsa_pc': partially consistent, both solved
+    exactly; 'dsa_vcycle' / 'dsa_vcycle_lumped': partially / lumped fully consistent through one V-cycle of
+    dsa.MultigridDsa).  Without a ROM, the DSA options give the DSA preconditioner for every j (GMRES-DSA,
+    SI-DSA) and anything else none."""
+    if post in ("dsa_vcycle", "dsa_vcycle_lumped"):
+        D = dsa.MultigridDsa(p, "partial" if post == "dsa_vcycle" else "lumped")
+    else:
+        dsa_kind = {"dsa": "full", "dsa_pc": "partial"}.get(post)
+        D = dsa.Dsa(p, dsa_kind) if dsa_kind is not None else None
     if rom is None:
         if D is None:
             return None
@@ -138,6 +143,17 @@ def solve(p: Problem, rom: Optional[Rom] = None, window: int = 2, post: str = "r
     return fgmres(lambda z: Atilde_apply(p, z), bt, pre, phi0=phi0, restart=restart, rtol=rtol,
                   max_iter=max_iter, true_residual_check=true_residual_check,
                   record_first_cycle=record_first_cycle)
+
+
+def si_solve(p: Problem, rom: Optional[Rom] = None, window: int = 2, post: str = "rom", rtol: float = 1e-10,
+             max_iter: int = 1000, phi0=None):
+    """SI-ROMSAD (Sec. 3.1-3.2, 4.2): source iteration with the ROM correction for the first `window`
+    iterations and `post` afterwards, as the preconditioned Richardson iteration of eq.
+    preconditioned-richardson with the M_l of eq. ROMSAD-preconditioner."""
+    from .krylov import preconditioned_richardson
+    bt = rhs_btilde(p)
+    pre = make_preconditioner(rom, p, window, post)
+    return preconditioned_richardson(lambda z: Atilde_apply(p, z), bt, pre, phi0=phi0, rtol=rtol, max_iter=max_iter)
 
 
 def xi_recurrence(phi: np.ndarray, first: dict, window: int) -> List[np.ndarray]:

@@ -143,6 +143,8 @@ _SIGS = {
     "fgmres_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(FgmresOpts),
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(FgmresStats),
                                     ctypes.c_void_p]),
+    "si_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(FgmresOpts),
+                                ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(FgmresStats), ctypes.c_void_p]),
 }
 
 
@@ -474,4 +476,24 @@ def fgmres_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi,
     stats = [st[b].as_dict() for b in range(B)]
     if s != RTE_OK and (raise_on_fail or s != RTE_ERR_NOT_CONVERGED):
         _check(s, "fgmres_solve")
+    return stats
+
+
+def si_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi, phi0=None, rtol=1e-10, max_iter=1000,
+             window=2, post_mode=RTE_POST_DSA, dsa_variant=RTE_DSA_PARTIAL, stream=None, raise_on_fail=True):
+    """SI-ROMSAD (source iteration, ROM correction in the window, then post_mode) for all instances, FP64.
+    phi: FP64 device tensor or host (numpy) buffer.  Returns the list of per-instance stats dicts."""
+    B = problem.spec.n_instances
+    o = FgmresOpts(1, rtol, max_iter, window, post_mode, RTE_MODE_FP64, 0.0, 0, 0, 0, 0, int(dsa_variant))
+    st = (FgmresStats * B)()
+    rarr = None if roms is None else (ctypes.c_void_p * B)(*[(r.h.value if r is not None else None) for r in roms])
+    if isinstance(phi, np.ndarray):
+        assert phi.dtype == np.float64 and phi.flags["C_CONTIGUOUS"]
+        phi_ptr = ctypes.c_void_p(phi.ctypes.data)
+    else:
+        phi_ptr = _ptr(phi)
+    s = load().si_solve(problem.h, rarr, ctypes.byref(o), _ptr(phi0), phi_ptr, st, _stream(stream))
+    stats = [st[b].as_dict() for b in range(B)]
+    if s != RTE_OK and (raise_on_fail or s != RTE_ERR_NOT_CONVERGED):
+        _check(s, "si_solve")
     return stats

@@ -2013,3 +2013,176 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
   if (ret == RTE_ERR_NUMERIC) set_error("fgmres_solve: NaN/Inf met");
   return ret;
 }
+
+// ----------------------------------------------------------------------------------------------- SI-SA
+// Source iteration with synthetic acceleration as a preconditioned Richardson iteration (Sec. 3.2, eq.
+// preconditioned-richardson): phi <- phi + M_l^{-1} r, r = b~ - A~ phi.  M_l = M_ROM for l <= window on
+// instances with a ROM, then the post-window operator (DSA, ROMSAD kept, or none); instances without a ROM
+// take the post-window operator from the first iteration when it is DSA, none otherwise.  FP64; every
+// iteration ends with a host check of ||r|| / ||b~|| (an FP64 sweep costs far more than the round trip).
+extern "C" int si_solve(rte_problem_t p, const romsad_t* roms, const fgmres_opts* o, const void* phi0, void* phi,
+                        fgmres_stats* stats, void* stream) {
+  RTE_ARG(p && o && phi && stats, "null handle or pointer");
+  RTE_ARG(o->rtol > 0.0 && o->max_iter >= 1, "rtol must be > 0 and max_iter >= 1");
+  RTE_ARG(o->post_mode == RTE_POST_ROM || o->post_mode == RTE_POST_IDENTITY || o->post_mode == RTE_POST_DSA,
+          "unknown post_mode");
+  if (o->mode != RTE_MODE_FP64) {
+    set_error("si_solve: source iteration runs in FP64 only");
+    return RTE_ERR_UNSUPPORTED;
+  }
+  const bool use_dsa = o->post_mode == RTE_POST_DSA;
+  if (use_dsa) {
+    RTE_ARG(o->dsa_variant == RTE_DSA_PARTIAL || o->dsa_variant == RTE_DSA_LUMPED, "unknown dsa_variant");
+    RTE_TRY(dsa_check(p));
+  }
+  const int B = p->B;
+  if (roms)
+    for (int b = 0; b < B; ++b)
+      if (roms[b]) RTE_TRY(rom_check_mesh(roms[b], p, b));
+  cudaStream_t st = (cudaStream_t)stream;
+  Ws* ws = get_ws(p);
+  RTE_TRY(ws->alloc(p, ws->m > 0 ? ws->m : 1, false));
+  RTE_TRY(prepare_sweeps(p));
+  cudaPointerAttributes attr;
+  bool host_out = false;
+  if (cudaPointerGetAttributes(&attr, phi) != cudaSuccess || attr.type == cudaMemoryTypeHost ||
+      attr.type == cudaMemoryTypeUnregistered) {
+    cudaGetLastError();
+    host_out = true;
+  }
+  double* x;
+  if (host_out) {
+    RTE_TRY(ws->phi_in.ensure(p->ntot));
+    x = ws->phi_in.p;
+  } else {
+    x = (double*)phi;
+  }
+  // ROM groups (one factorisation of U^T A_mu U per group)
+  std::vector<int> norom(B, 1);
+  std::vector<RomPlan> plans;
+  bool any_rom = false, any_norom = false;
+  if (roms) {
+    std::vector<std::pair<romsad_t, int>> groups;
+    for (int b = 0; b < B; ++b)
+      if (roms[b]) {
+        groups.push_back({roms[b], b});
+        norom[b] = 0;
+      }
+    std::sort(groups.begin(), groups.end());
+    size_t g0 = 0;
+    while (g0 < groups.size()) {
+      size_t g1 = g0;
+      std::vector<int> ids;
+      while (g1 < groups.size() && groups[g1].first == groups[g0].first) ids.push_back(groups[g1++].second);
+      plans.emplace_back();
+      RTE_TRY(plans.back().build(groups[g0].first, p, ids, st));
+      g0 = g1;
+    }
+  }
+  for (int b = 0; b < B; ++b) {
+    any_rom = any_rom || !norom[b];
+    any_norom = any_norom || norom[b];
+  }
+  RTE_CHECK_CUDA(cudaMemcpyAsync(ws->norom.p, norom.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+  if (use_dsa) RTE_TRY(dsa_prepare(p, o->dsa_variant, st));
+  const dim3 vg = vec_grid(p);
+  std::vector<fgmres_stats> S(B);
+  for (int b = 0; b < B; ++b) {
+    std::memset(&S[b], 0, sizeof(fgmres_stats));
+    S[b].sweeps = 1;
+    S[b].sweeps_fp64 = 1;
+  }
+  // b~ and its norm
+  RTE_TRY(launch_T(p, MODE_RHS, true, nullptr, true, nullptr, ws->bt.p, true, nullptr, st));
+  std::vector<int> act(B, 1), sub(B, 0);
+  RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+  k_norm<<<B, 512, 0, st>>>(ws->bt.p, p->d_inst.p, ws->active.p, ws->bnorm.p);
+  count_launch();
+  if (phi0) {
+    RTE_CHECK_CUDA(cudaMemcpyAsync(x, phi0, p->ntot * 8, cudaMemcpyDeviceToDevice, st));
+  } else {
+    RTE_CHECK_CUDA(cudaMemsetAsync(x, 0, p->ntot * 8, st));
+  }
+  std::vector<double> hb(B), hr(B);
+  RTE_CHECK_CUDA(cudaMemcpyAsync(hb.data(), ws->bnorm.p, B * 8, cudaMemcpyDeviceToHost, st));
+  for (int l = 0;; ++l) {
+    // r = b~ - A~ x (r = b~ for a zero start)
+    RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (l == 0 && !phi0) {
+      k_copy_active<<<vg, 256, 0, st>>>(ws->r.p, ws->bt.p, p->d_inst.p, ws->active.p);
+      count_launch();
+    } else {
+      RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ws->r.p, true, ws->active.p, st));
+      for (int b = 0; b < B; ++b)
+        if (act[b]) {
+          ++S[b].sweeps;
+          ++S[b].sweeps_fp64;
+        }
+    }
+    k_norm<<<B, 512, 0, st>>>(ws->r.p, p->d_inst.p, ws->active.p, ws->nrm.p);
+    count_launch();
+    k_linf<<<B, 512, 0, st>>>(ws->r.p, p->d_inst.p, ws->est.p);
+    count_launch();
+    std::vector<double> hl(B);
+    RTE_CHECK_CUDA(cudaMemcpyAsync(hr.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
+    RTE_CHECK_CUDA(cudaMemcpyAsync(hl.data(), ws->est.p, B * 8, cudaMemcpyDeviceToHost, st));
+    RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+    int nact = 0;
+    for (int b = 0; b < B; ++b) {
+      if (!act[b]) continue;
+      const double rel = hb[b] > 0 ? hr[b] / hb[b] : 0.0;
+      S[b].true_rel_residual = S[b].est_rel_residual = rel;
+      S[b].true_linf_residual = hl[b];
+      if (!std::isfinite(rel)) {
+        act[b] = 0;
+        S[b].status = RTE_ERR_NUMERIC;
+      } else if (rel <= o->rtol) {
+        act[b] = 0;
+      } else if (S[b].iterations >= o->max_iter) {
+        act[b] = 0;
+        S[b].status = RTE_ERR_NOT_CONVERGED;
+      } else {
+        ++nact;
+      }
+    }
+    if (nact == 0) break;
+    RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+    // z = M_l^{-1} r into d
+    const bool rom_now = any_rom && (l + 1 <= o->window || o->post_mode == RTE_POST_ROM);
+    if (rom_now) {
+      for (RomPlan& pl : plans) RTE_TRY(pl.apply(p, ws->active.p, ws->r.p, ws->d.p, true, st));
+      if (any_norom) {
+        if (use_dsa) {
+          RTE_TRY(dsa_launch(p, true, ws->r.p, ws->d.p, ws->active.p, ws->norom.p, st));
+        } else {
+          for (int b = 0; b < B; ++b) sub[b] = act[b] && norom[b];
+          RTE_CHECK_CUDA(cudaMemcpyAsync(ws->list.p, sub.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+          k_copy_active<<<vg, 256, 0, st>>>(ws->d.p, ws->r.p, p->d_inst.p, ws->list.p);
+          count_launch();
+        }
+      }
+    } else if (use_dsa) {
+      RTE_TRY(dsa_launch(p, true, ws->r.p, ws->d.p, ws->active.p, nullptr, st));
+    } else {
+      k_copy_active<<<vg, 256, 0, st>>>(ws->d.p, ws->r.p, p->d_inst.p, ws->active.p);
+      count_launch();
+    }
+    k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d.p, p->d_inst.p, ws->active.p);
+    count_launch();
+    RTE_CHECK_CUDA(cudaGetLastError());
+    for (int b = 0; b < B; ++b)
+      if (act[b]) ++S[b].iterations;
+  }
+  if (host_out) {
+    RTE_CHECK_CUDA(cudaMemcpyAsync(phi, x, p->ntot * 8, cudaMemcpyDeviceToHost, st));
+  }
+  RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+  int ret = RTE_OK;
+  for (int b = 0; b < B; ++b) {
+    stats[b] = S[b];
+    if (S[b].status != RTE_OK && ret == RTE_OK) ret = S[b].status;
+  }
+  if (ret == RTE_ERR_NOT_CONVERGED) set_error("si_solve: at least one instance missed its tolerance");
+  if (ret == RTE_ERR_NUMERIC) set_error("si_solve: NaN/Inf met");
+  return ret;
+}

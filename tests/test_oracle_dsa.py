@@ -273,3 +273,33 @@ def test_gmres_with_the_vcycle_dsa_solves_the_dense_system(kind):
                      max_iter=3000)
     assert rel(sol, ref) < 1e-8
     assert st.iterations * 3 < st_plain.iterations
+
+
+# ------------------------------------------------------------------ SI-SA (preconditioned Richardson)
+def test_unaccelerated_richardson_is_source_iteration():
+    """eq. richardson: phi^(l) = phi^(l-1) + r^(l-1) reproduces the source-iteration iterates phi <- T Sigma_s phi + b~."""
+    from oracle.krylov import preconditioned_richardson, source_iteration
+    p = Problem(small_2d(nx=4, ny=3, n_polar=2, n_azim=4), 0, [2.0, 1.0, 3.0, 0.5], [0.5, 0.3, 0.2, 0.4])
+    its = source_iteration(p, 6)
+    phi, st = preconditioned_richardson(lambda z: T.Atilde_apply(p, z), T.rhs_btilde(p), None, rtol=0.0, max_iter=6)
+    assert st.iterations == 6 and rel(phi, its[-1]) < 1e-13
+
+
+def test_richardson_with_the_exact_inverse_converges_in_one_step():
+    from oracle.krylov import preconditioned_richardson
+    p = Problem(small_2d(nx=4, ny=3, n_polar=2, n_azim=4), 0, [20.0, 1.0, 300.0, 2.0], [0.1, 0.3, 0.2, 0.05])
+    A = _dense(lambda z: T.Atilde_apply(p, z), p.ndof)
+    phi, st = preconditioned_richardson(lambda z: A @ z, T.rhs_btilde(p), lambda l, r: np.linalg.solve(A, r),
+                                        rtol=1e-12, max_iter=5)
+    assert st.iterations == 1 and st.converged
+
+
+def test_si_dsa_contracts_at_the_spectral_radius():
+    """SI with the exact PC-DSA correction: the residual ratio of late iterations approaches the spectral radius
+    of I - M^{-1} A~ (the iteration matrix of the error; left and right preconditioning share the spectrum)."""
+    p = _homogeneous(small_2d(nx=6, ny=6, n_polar=2, n_azim=8), 100.0 * 0.99, 100.0 * 0.01)
+    phi, st = RS.si_solve(p, None, post="dsa_pc", rtol=1e-13, max_iter=200)
+    assert st.converged
+    h = st.history
+    ratio = (h[-2] / h[-6]) ** 0.25
+    assert abs(ratio - _rho(p, "partial")) < 0.05
