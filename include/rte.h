@@ -224,6 +224,25 @@ int romsad_destroy(romsad_t rom);
  * (device, not aliased).  Each call redoes the per-parameter set-up (one extra kernel). */
 int rte_dsa_apply(rte_problem_t p, int variant, int dtype, const void* v, void* z, void* stream);
 
+/* ---------------------------------------- RBF-interpolated initial guess (Sec. 5) */
+/* The interpolation baseline of the paper's experiments: the high-fidelity scalar fluxes phi_k of K sampled
+ * parameters mu_k are interpolated in parameter space and the interpolant at an instance's mu is used as
+ * its initial guess (fgmres_solve with phi0).  The paper does not state the kernel; this build uses
+ * features x = (log sigma_s[R], sigma_a[R]) standardised by the samples' mean and standard deviation and
+ * the polyharmonic cubic kernel |x - x_k|^3 with a degree-1 polynomial term, so that
+ * phi0(mu) = sum_k w_k(mu) phi_k with the cardinal weights w(mu) = (A^{-1} [g(x); 1; x])[0:K],
+ * A = [[Phi, P], [P^T, 0]], Phi_kl = |x_k - x_l|^3, P_k = (1, x_k), g_k(x) = |x - x_k|^3. */
+typedef struct rte_rbf* rte_rbf_t;
+/* tmpl: the mesh and region grid of the samples (its instance 0).  sigma_s, sigma_a: host [K][R]
+ * (sigma_s > 0); solutions: [K][N] FP64 scalar fluxes on that mesh, device or host, copied.  Needs
+ * K >= 2R + 2; RTE_ERR_NUMERIC if the interpolation system is singular. */
+int rte_rbf_create(rte_problem_t tmpl, int K, const double* sigma_s, const double* sigma_a, const void* solutions,
+                   rte_rbf_t* out);
+/* phi0 (device FP64 scalar vector of p) = the interpolant at every instance's parameters; every instance
+ * must use the samples' mesh and region grid, and have sigma_s > 0.  Synchronises the stream. */
+int rte_rbf_initial_guess(rte_rbf_t rbf, rte_problem_t p, void* phi0, void* stream);
+int rte_rbf_destroy(rte_rbf_t rbf);
+
 /* ------------------------------------------------- learned warm start (MLP) */
 /* A small MLP maps mu = (sigma_s[R], sigma_a[R]) of an instance to the r reduced-basis
  * coefficients c of eq. greedy-rom (labels from romsad_build_greedy).  Since the first FGMRES

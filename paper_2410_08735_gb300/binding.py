@@ -145,6 +145,11 @@ _SIGS = {
                                     ctypes.c_void_p]),
     "si_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(FgmresOpts),
                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(FgmresStats), ctypes.c_void_p]),
+    "rte_rbf_create": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p,
+                                      ctypes.POINTER(ctypes.c_void_p)]),
+    "rte_rbf_initial_guess": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "rte_rbf_destroy": (ctypes.c_int, [ctypes.c_void_p]),
 }
 
 
@@ -497,3 +502,32 @@ def si_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi, phi
     if s != RTE_OK and (raise_on_fail or s != RTE_ERR_NOT_CONVERGED):
         _check(s, "si_solve")
     return stats
+
+
+class Rbf:
+    """Owns an rte_rbf_t: the RBF interpolant of sampled scalar fluxes (the interpolated initial guess)."""
+
+    def __init__(self, tmpl: Problem, sigma_s, sigma_a, solutions):
+        """sigma_s, sigma_a: [K][R]; solutions: [K][N] FP64 (device tensor or numpy array), copied."""
+        ss = np.ascontiguousarray(sigma_s, dtype=np.float64)
+        sa = np.ascontiguousarray(sigma_a, dtype=np.float64)
+        if isinstance(solutions, np.ndarray):
+            sol = np.ascontiguousarray(solutions, dtype=np.float64)
+            sptr = ctypes.c_void_p(sol.ctypes.data)
+        else:
+            sptr = _ptr(solutions)
+        h = ctypes.c_void_p()
+        _check(load().rte_rbf_create(tmpl.h, ss.shape[0], _dptr(ss), _dptr(sa), sptr, ctypes.byref(h)),
+               "rte_rbf_create")
+        self.h = h
+
+    def initial_guess(self, problem: Problem, phi0, stream=None):
+        _check(load().rte_rbf_initial_guess(self.h, problem.h, _ptr(phi0), _stream(stream)), "rte_rbf_initial_guess")
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) and self.h.value:
+                load().rte_rbf_destroy(self.h)
+                self.h = ctypes.c_void_p()
+        except Exception:
+            pass
