@@ -156,7 +156,11 @@ class Problem:
         self.inflow = np.zeros((self.ndir, 4), dtype=np.int32)
         for j in range(self.ndir):
             self.M[j], self.C[j], self.inflow[j] = self._assemble_dir(self.dirs[j])
-        self.G = self._project_source(spec.src_q, spec.src_box)
+        if getattr(spec, "src_gauss", None) is not None:
+            self.G = self._project_gauss(*spec.src_gauss)
+        else:
+            self.G = self._project_source(spec.src_q, spec.src_box)
+        self.inflow_faces = tuple(getattr(spec, "inflow_faces", ("x-", "x+", "y-", "y+")))
         self._gbc = {}
 
     # ---------------------------------------------------------- assembly
@@ -271,6 +275,24 @@ class Problem:
                 G[c * 4:(c + 1) * 4] = qv * (eta @ W2) * 0.25 * (hi_x - lo_x) * (hi_y - lo_y)
         return G
 
+    def _project_gauss(self, amp: float, a: float, xc: float, yc: float, npts: int = 16) -> np.ndarray:
+        """G_k = int_T G eta_k for G = amp exp(-a ((x-xc)^2 + (y-yc)^2)) (2D), by npts x npts Gauss-Legendre
+        points per cell (the integrand is smooth; 16 points integrate it to rounding at the workloads' cells)."""
+        assert self.dim == 2
+        xg, wg = gauss_legendre(npts)
+        XI, ZE = np.meshgrid(xg, xg, indexing="ij")
+        W2 = np.outer(wg, wg).ravel()
+        eta = self._eta(XI.ravel(), ZE.ravel())
+        G = np.zeros(self.ndof)
+        for iy in range(self.ny):
+            for ix in range(self.nx):
+                c = iy * self.nx + ix
+                px = self.x0 + (ix + 0.5 + 0.5 * XI.ravel()) * self.hx
+                py = self.y0 + (iy + 0.5 + 0.5 * ZE.ravel()) * self.hy
+                qv = amp * np.exp(-a * ((px - xc) ** 2 + (py - yc) ** 2))
+                G[c * 4:(c + 1) * 4] = (eta * qv) @ W2 * 0.25 * self.hx * self.hy
+        return G
+
     def gbc(self, j: int) -> np.ndarray:
         """(g_j^bc)_k = -int over inflow boundary faces of g eta_k (Omega_j . n)."""
         if self.g == 0.0:
@@ -293,17 +315,19 @@ class Problem:
             return v
         ox, oy = om[0], om[1]
         ones = np.ones_like(q)
+        fx_lo, fx_hi = "x-" in self.inflow_faces, "x+" in self.inflow_faces
+        fy_lo, fy_hi = "y-" in self.inflow_faces, "y+" in self.inflow_faces
         for iy in range(self.ny):
             for ix in range(self.nx):
                 c = iy * self.nx + ix
                 contrib = np.zeros(4)
-                if ox > 0 and ix == 0:
+                if ox > 0 and ix == 0 and fx_lo:
                     contrib += -self.g * (self._eta(-ones, q) @ wq) * (-ox) * self.hy / 2.0
-                if ox < 0 and ix == self.nx - 1:
+                if ox < 0 and ix == self.nx - 1 and fx_hi:
                     contrib += -self.g * (self._eta(ones, q) @ wq) * ox * self.hy / 2.0
-                if oy > 0 and iy == 0:
+                if oy > 0 and iy == 0 and fy_lo:
                     contrib += -self.g * (self._eta(q, -ones) @ wq) * (-oy) * self.hx / 2.0
-                if oy < 0 and iy == self.ny - 1:
+                if oy < 0 and iy == self.ny - 1 and fy_hi:
                     contrib += -self.g * (self._eta(q, ones) @ wq) * oy * self.hx / 2.0
                 v[c * 4:(c + 1) * 4] += contrib
         self._gbc[j] = v

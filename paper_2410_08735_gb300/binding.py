@@ -225,6 +225,10 @@ class Problem:
         sa = np.ascontiguousarray(np.asarray(sigma_a, dtype=np.float64).reshape(B, -1))
         nx = (ctypes.c_int * B)(*spec.nx)
         ny = (ctypes.c_int * B)(*spec.ny)
+        if getattr(spec, "src_gauss", None) is not None or \
+                tuple(getattr(spec, "inflow_faces", ("x-", "x+", "y-", "y+"))) != ("x-", "x+", "y-", "y+"):
+            raise NotImplementedError("rte_problem_desc has no Gaussian source or one-sided inflow yet: "
+                                      f"workload {spec.name} cannot be built on the GPU")
         d = ProblemDesc()
         d.dim = spec.dim
         d.n_instances = B

@@ -55,9 +55,11 @@ class ProblemSpec:
     rx, ry     region grid (equal blocks); R = rx * ry regions.
     src_q      isotropic source value inside src_box, zero outside.
     src_box    (xa, xb, ya, yb); y ignored in 1D.
-    inflow_g   isotropic inflow value on every inflow boundary (0 = vacuum).
+    inflow_g   isotropic inflow value on the inflow boundary faces (0 = vacuum).
     sigma_s_range  log-uniform range of sigma_s per region.
     sigma_a_range  uniform range of sigma_a per region.
+    src_gauss  None, or (A, a, xc, yc): the source A exp(-a ((x-xc)^2 + (y-yc)^2)) replaces the box source.
+    inflow_faces  domain faces that carry the inflow g: a subset of ("x-", "x+", "y-", "y+") (2D).
     """
 
     name: str
@@ -79,6 +81,8 @@ class ProblemSpec:
     rom_rank: int = 32
     window: int = 2
     n_train: int = 20
+    src_gauss: Optional[Sequence[float]] = None
+    inflow_faces: Sequence[str] = ("x-", "x+", "y-", "y+")
 
     @property
     def n_instances(self) -> int:
@@ -159,3 +163,55 @@ def config(n: int) -> ProblemSpec:
                            8, 8, 1.0, (0.4, 0.6, 0.4, 0.6), 0.0, (1.0, 1e4), (0.0, 1.0),
                            restart=40, rtol=1e-8, rom_rank=32, window=2, n_train=256)
     raise ValueError(f"no workload {n}")
+
+
+# ---------------------------------------------------------------- the paper's other 2D problems (N2)
+# Region grid 4 x 4 on [-1, 1]^2: the central 2 x 2 blocks are the inner square |x|, |y| <= 0.5.
+_INNER = (5, 6, 9, 10)
+
+
+def pincell() -> ProblemSpec:
+    """Pin-cell problem (Sec. 5): [-1,1]^2, 80 x 80 cells, CL(30, 6), zero inflow, source exp(-100 (x^2+y^2)),
+    sigma_s = 100 and sigma_a = 0 outside the inner square, (sigma_a, sigma_s) = (mu_a, mu_s) in
+    [0.05, 0.5]^2 inside; relative residual 1e-11."""
+    return ProblemSpec("pincell_80", 2, [80], [80], (-1.0, 1.0, -1.0, 1.0), 6, 30, 4, 4,
+                       0.0, (0.0, 0.0, 0.0, 0.0), 0.0, (0.05, 0.5), (0.05, 0.5),
+                       restart=30, rtol=1e-11, rom_rank=64, window=2, n_train=25, src_gauss=(1.0, 100.0, 0.0, 0.0))
+
+
+def pincell_params(mu_a: float, mu_s: float):
+    """Per-region (sigma_s [16], sigma_a [16]) of the pin-cell problem for one parameter point."""
+    ss = np.full(16, 100.0)
+    sa = np.zeros(16)
+    for r in _INNER:
+        ss[r], sa[r] = mu_s, mu_a
+    return ss, sa
+
+
+def param_inflow() -> ProblemSpec:
+    """Two-material problem with a parametric inflow (Sec. 5): [-1,1]^2, 64 x 64 cells, CL(60, 6), no source,
+    sigma_s = mu_s and sigma_a = 0 in the inner square, sigma_s = 0 and sigma_a = 1 outside; inflow
+    mu_bc on the left face only (Omega_x > 0); mu = (mu_s, mu_bc) in [1, 5] x [0.5, 1.5]; residual 1e-11.
+    The inflow value is the spec's inflow_g (set per parameter point with dataclasses.replace)."""
+    return ProblemSpec("param_inflow_64", 2, [64], [64], (-1.0, 1.0, -1.0, 1.0), 6, 60, 4, 4,
+                       0.0, (0.0, 0.0, 0.0, 0.0), 1.0, (1.0, 5.0), (0.0, 0.0),
+                       restart=30, rtol=1e-11, rom_rank=32, window=2, n_train=99, inflow_faces=("x-",))
+
+
+def param_inflow_params(mu_s: float):
+    """Per-region (sigma_s [16], sigma_a [16]) of the two-material problem."""
+    ss = np.zeros(16)
+    sa = np.ones(16)
+    for r in _INNER:
+        ss[r], sa[r] = mu_s, 0.0
+    return ss, sa
+
+
+def draw_box(n: int, lo: Sequence[float], hi: Sequence[float], seed: int) -> np.ndarray:
+    """n points uniform in the box [lo, hi] (SplitMix64, coordinates in order): [n][len(lo)]."""
+    rng = SplitMix64(seed)
+    out = np.empty((n, len(lo)))
+    for i in range(n):
+        for k in range(len(lo)):
+            out[i, k] = lo[k] + rng.uniform() * (hi[k] - lo[k])
+    return out
