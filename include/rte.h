@@ -80,7 +80,15 @@ typedef struct rte_problem_desc {
     double src_q;          /* isotropic source value inside src_box, 0 outside (eq. 1 G)    */
     double src_box[4];     /* xa, xb, ya, yb                                                */
     double inflow_g;       /* isotropic inflow value g on all inflow boundaries (eq. 1c)    */
+    int src_kind;          /* RTE_SRC_BOX (src_q on src_box) or RTE_SRC_GAUSS (2D):
+                              G = A exp(-a ((x-xc)^2 + (y-yc)^2)), src_gauss = (A, a, xc, yc),
+                              projected in closed form (erf / exp differences per cell)      */
+    double src_gauss[4];
+    int inflow_faces;      /* 0: inflow g on every boundary face; a one-sided inflow (bit mask of
+                              x-, x+, y-, y+) is RTE_ERR_UNSUPPORTED in this build          */
 } rte_problem_desc;
+#define RTE_SRC_BOX 0
+#define RTE_SRC_GAUSS 1
 
 typedef struct rte_problem* rte_problem_t;
 

@@ -37,7 +37,8 @@ class ProblemDesc(ctypes.Structure):
                 ("box", ctypes.c_double * 4), ("n_polar", ctypes.c_int), ("n_azim", ctypes.c_int),
                 ("rx", ctypes.c_int), ("ry", ctypes.c_int),
                 ("sigma_s", ctypes.POINTER(ctypes.c_double)), ("sigma_a", ctypes.POINTER(ctypes.c_double)),
-                ("src_q", ctypes.c_double), ("src_box", ctypes.c_double * 4), ("inflow_g", ctypes.c_double)]
+                ("src_q", ctypes.c_double), ("src_box", ctypes.c_double * 4), ("inflow_g", ctypes.c_double),
+                ("src_kind", ctypes.c_int), ("src_gauss", ctypes.c_double * 4), ("inflow_faces", ctypes.c_int)]
 
 
 class ProblemInfo(ctypes.Structure):
@@ -225,10 +226,7 @@ class Problem:
         sa = np.ascontiguousarray(np.asarray(sigma_a, dtype=np.float64).reshape(B, -1))
         nx = (ctypes.c_int * B)(*spec.nx)
         ny = (ctypes.c_int * B)(*spec.ny)
-        if getattr(spec, "src_gauss", None) is not None or \
-                tuple(getattr(spec, "inflow_faces", ("x-", "x+", "y-", "y+"))) != ("x-", "x+", "y-", "y+"):
-            raise NotImplementedError("rte_problem_desc has no Gaussian source or one-sided inflow yet: "
-                                      f"workload {spec.name} cannot be built on the GPU")
+        faces = tuple(getattr(spec, "inflow_faces", ("x-", "x+", "y-", "y+")))
         d = ProblemDesc()
         d.dim = spec.dim
         d.n_instances = B
@@ -244,6 +242,12 @@ class Problem:
         d.src_q = spec.src_q
         d.src_box = (ctypes.c_double * 4)(*spec.src_box)
         d.inflow_g = spec.inflow_g
+        gauss = getattr(spec, "src_gauss", None)
+        d.src_kind = 0 if gauss is None else 1
+        d.src_gauss = (ctypes.c_double * 4)(*(gauss if gauss is not None else (0.0, 0.0, 0.0, 0.0)))
+        bits = {"x-": 1, "x+": 2, "y-": 4, "y+": 8}
+        mask = sum(bits[f] for f in set(faces))
+        d.inflow_faces = 0 if mask == 15 else mask
         h = ctypes.c_void_p()
         _check(lib.rte_problem_create(ctypes.byref(d), ctypes.byref(h)), "rte_problem_create")
         self.h = h

@@ -127,6 +127,8 @@ struct rte_problem {
   long long ntot = 0;
   double box[4] = {0, 1, 0, 1};
   double g = 0.0, src_q = 0.0, src_box[4] = {0, 0, 0, 0};
+  int src_kind = RTE_SRC_BOX;
+  double src_gauss[4] = {0, 0, 0, 0};   // A, a, xc, yc
   std::vector<double> ss, sa;        // [B][R] host copies
   std::vector<double> om_x, om_y, om_z, w;  // [ndir] quadrature (paper order)
   std::vector<int> uniq_of_dir;      // [ndir]

@@ -64,6 +64,23 @@ static void mode_integrals(double xl, double h, double lo, double hi, double* I)
   I[1] = std::sqrt(3.0 / h) * (h / 4.0) * (b * b - a * a);
 }
 
+// Integrals of the two orthonormal Legendre modes of a cell [xl, xl+h] against exp(-a (x-xc)^2):
+// with t = x - xc, int e = sqrt(pi/a)/2 (erf(sqrt(a) t1) - erf(sqrt(a) t0)) (through erfc on a one-signed
+// interval, where the erf difference would cancel) and int t e = (exp(-a t0^2) - exp(-a t1^2)) / (2a);
+// p_1 = sqrt(3/h) (2/h) (t + xc - x_mid).
+static void gauss_mode_integrals(double xl, double h, double a, double xc, double* I) {
+  const double t0 = xl - xc, t1 = xl + h - xc, sa = std::sqrt(a);
+  double de;
+  if (t0 >= 0.0) de = std::erfc(sa * t0) - std::erfc(sa * t1);
+  else if (t1 <= 0.0) de = std::erfc(-sa * t1) - std::erfc(-sa * t0);
+  else de = std::erf(sa * t1) - std::erf(sa * t0);
+  const double ie = 0.5 * std::sqrt(M_PI / a) * de;
+  const double ite = (std::exp(-a * t0 * t0) - std::exp(-a * t1 * t1)) / (2.0 * a);
+  const double xm = xl + 0.5 * h;
+  I[0] = ie / std::sqrt(h);
+  I[1] = std::sqrt(3.0 / h) * (2.0 / h) * (ite + (xc - xm) * ie);
+}
+
 __global__ void k_linv(int B, int nu, int R, int dim, const InstInfo* inst, const UDir* ud,
                        const double* sig_t, double* out64, float* out32) {
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -188,6 +205,17 @@ static int create_impl(const rte_problem_desc* d, rte_problem* p) {
   p->g = d->inflow_g;
   p->src_q = d->src_q;
   std::memcpy(p->src_box, d->src_box, sizeof(p->src_box));
+  RTE_ARG(d->src_kind == RTE_SRC_BOX || d->src_kind == RTE_SRC_GAUSS, "unknown src_kind");
+  if (d->src_kind == RTE_SRC_GAUSS) {
+    RTE_ARG(d->dim == 2, "the Gaussian source is 2D");
+    RTE_ARG(d->src_gauss[1] > 0.0 && std::isfinite(d->src_gauss[0]), "Gaussian source needs a > 0 and a finite A");
+  }
+  p->src_kind = d->src_kind;
+  std::memcpy(p->src_gauss, d->src_gauss, sizeof(p->src_gauss));
+  if (d->inflow_faces != 0 && d->inflow_faces != 15) {
+    set_error("rte_problem_create: a one-sided inflow is not supported by this build");
+    return RTE_ERR_UNSUPPORTED;
+  }
   p->nx.resize(p->B);
   p->ny.resize(p->B);
   p->off.assign(p->B + 1, 0);
@@ -292,7 +320,23 @@ static int create_impl(const rte_problem_desc* d, rte_problem* p) {
   p->nu = (int)p->udir.size();
   // source moments G_k = int_T G eta_k (closed form, exact for the box source)
   std::vector<double> G(p->ntot, 0.0);
-  for (int b = 0; b < p->B; ++b) {
+  if (p->src_kind == RTE_SRC_GAUSS) {
+    for (int b = 0; b < p->B; ++b) {
+      const InstInfo& in = p->inst[b];
+      std::vector<double> Ix(2 * in.nx), Iy(2 * in.ny);
+      for (int ix = 0; ix < in.nx; ++ix)
+        gauss_mode_integrals(p->box[0] + ix * in.hx, in.hx, p->src_gauss[1], p->src_gauss[2], &Ix[2 * ix]);
+      for (int iy = 0; iy < in.ny; ++iy)
+        gauss_mode_integrals(p->box[2] + iy * in.hy, in.hy, p->src_gauss[1], p->src_gauss[3], &Iy[2 * iy]);
+      for (int iy = 0; iy < in.ny; ++iy)
+        for (int ix = 0; ix < in.nx; ++ix) {
+          const long long c = (long long)iy * in.nx + ix;
+          for (int k = 0; k < 4; ++k)
+            G[in.off + 4 * c + k] = p->src_gauss[0] * Ix[2 * ix + (k & 1)] * Iy[2 * iy + (k >> 1)];
+        }
+    }
+  }
+  for (int b = 0; b < p->B && p->src_kind == RTE_SRC_BOX; ++b) {
     const InstInfo& in = p->inst[b];
     for (int iy = 0; iy < in.ny; ++iy)
       for (int ix = 0; ix < in.nx; ++ix) {
