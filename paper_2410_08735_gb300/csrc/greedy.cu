@@ -159,6 +159,8 @@ static int make_problem_like(const rte_problem* tmpl, int n, const double* ss, c
   d.sigma_a = sa;
   d.src_q = tmpl->src_q;
   std::memcpy(d.src_box, tmpl->src_box, sizeof(d.src_box));
+  d.src_kind = tmpl->src_kind;
+  std::memcpy(d.src_gauss, tmpl->src_gauss, sizeof(d.src_gauss));
   d.inflow_g = tmpl->g;
   return rte_problem_create(&d, out);
 }
