@@ -7,6 +7,8 @@ Test infrastructure only.
   psi_j    = (D_j + Sigma_t)^{-1} s, all j (the angular-output sweep)
   phi      = Q psi = sum_j omega_j psi_j                           (Sec. 2.3)
   A        = the fully coupled N_Omega*N_DOF system                (eq. one_equation)
+  A_refl   = the same system of a 1D slab whose ends reflect specularly (an oracle-only boundary
+             condition; the paper's problems have inflow boundaries, eq. 1c)
 Every direction is swept separately (no merging of directions).
 """
 from __future__ import annotations
@@ -71,3 +73,40 @@ def dense_coupled_system(p: Problem):
             A[i * n:(i + 1) * n, k * n:(k + 1) * n] -= p.w[k] * Ss
         b[i * n:(i + 1) * n] = p.G + p.gbc(i)
     return A, b
+
+
+def dense_reflecting_1d(p: Problem, left: bool = True, right: bool = True):
+    """The coupled system A psi = b (eq. one_equation) of a 1D slab with specular reflection at the
+    chosen ends, assembled densely; vacuum at an end that does not reflect.  Only for tiny meshes.
+
+    At a reflecting end the inflow value of ordinate mu is the outgoing value of the mirrored ordinate
+    -mu at the same point, psi(x_b, mu) = psi(x_b, -mu).  In the upwind flux of eq. DG (eq. upwind) the
+    inflow face term (Omega . n) eta_k psi^up of direction i then couples to the trace of direction i'
+    (mu_i' = -mu_i) taken from the boundary cell itself, instead of a known g moved to the right-hand
+    side.  The Gauss-Legendre ordinates are symmetric, so i' exists.
+    """
+    assert p.dim == 1
+    A, b = dense_coupled_system(p)
+    n = p.ndof
+    mus = np.array([d[0] for d in p.dirs])
+    e_lo = p._eta(np.array([-1.0]))[:, 0]   # basis values at the cell's low end
+    e_hi = p._eta(np.array([1.0]))[:, 0]
+    for i in range(p.ndir):
+        mirror = int(np.argmin(np.abs(mus + mus[i])))
+        assert abs(mus[mirror] + mus[i]) < 1e-14
+        if mus[i] > 0 and left:          # inflow through the low face of cell 0 (n = -1)
+            c = 0
+            on = -mus[i]
+            A[i * n + 2 * c:i * n + 2 * c + 2, mirror * n + 2 * c:mirror * n + 2 * c + 2] += on * np.outer(e_lo, e_lo)
+        if mus[i] < 0 and right:         # inflow through the high face of the last cell (n = +1)
+            c = p.nx - 1
+            on = mus[i]
+            A[i * n + 2 * c:i * n + 2 * c + 2, mirror * n + 2 * c:mirror * n + 2 * c + 2] += on * np.outer(e_hi, e_hi)
+    return A, b
+
+
+def solve_reflecting_1d(p: Problem, left: bool = True, right: bool = True) -> np.ndarray:
+    """phi = Q A_refl^{-1} b by dense LU (numpy), for the reflecting slab of dense_reflecting_1d."""
+    A, b = dense_reflecting_1d(p, left, right)
+    psi = np.linalg.solve(A, b).reshape(p.ndir, p.ndof)
+    return scalar_flux(p, psi)

@@ -47,6 +47,31 @@ def test_backward_matches_central_differences():
             assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)) + 1e-9, (k, idx, fd, an)
 
 
+def test_forward_hand_computed_network():
+    """A 2 -> 2 -> 2 -> 2 network whose pre-activations land on 1, -1, 1 and 2, so that every hidden value is a
+    tabulated standard normal CDF value (gelu(t) = t Phi(t); Phi(1) = 0.8413447460685429, Phi(2) =
+    0.9772498680518208, Abramowitz and Stegun Table 26.1).  The output is written out by hand; it changes if
+    GELU is applied to the output layer, if any bias is dropped, or if any weight matrix is transposed."""
+    P1, P2 = 0.8413447460685429, 0.9772498680518208
+    h1 = np.array([P1, -(1.0 - P1)])            # gelu(1), gelu(-1) = -Phi(-1)
+    params = {
+        "W1": np.array([[1.0, 2.0], [0.5, 1.0]]), "b1": np.array([0.0, -1.5]),
+        # a2 = W2 h1 + b2 = (1, 2): b2 chosen from the tabulated values
+        "W2": np.array([[1.0, 1.0], [2.0, 1.0]]),
+        "b2": np.array([1.0 - (h1[0] + h1[1]), 2.0 - (2 * h1[0] + h1[1])]),
+        "W3": np.array([[2.0, -1.0], [0.0, 1.0]]), "b3": np.array([0.5, -1.0]),
+    }
+    X = np.array([[0.5, 0.25]])                # a1 = W1 x + b1 = (1, -1)
+    Y, (_, a1, h1_o, a2, h2) = mlp.forward(params, X)
+    np.testing.assert_allclose(a1[0], [1.0, -1.0], atol=1e-15)
+    np.testing.assert_allclose(h1_o[0], h1, atol=1e-15)
+    np.testing.assert_allclose(a2[0], [1.0, 2.0], atol=1e-15)
+    np.testing.assert_allclose(h2[0], [P1, 2.0 * P2], atol=1e-15)
+    # y = W3 (gelu(1), gelu(2)) + b3 = (2 Phi(1) - 2 Phi(2) + 0.5, 2 Phi(2) - 1)
+    np.testing.assert_allclose(Y[0], [2 * P1 - 2 * P2 + 0.5, 2 * P2 - 1.0], rtol=0, atol=1e-15)
+    assert abs(Y[0, 0] - 0.2281897560334442) < 1e-15
+
+
 def test_forward_matches_golden():
     ref = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "mlp_forward_8_16_16_4.txt"))
     Y, _ = mlp.forward(make_golden._weights(), make_golden._inputs())

@@ -1,4 +1,5 @@
 """Pins of the oracle solvers (Sec. 3, Alg. 1): P5, P6, P7, GMRES equivalence, SI identity."""
+import dataclasses
 import math
 
 import numpy as np
@@ -26,6 +27,43 @@ def test_p5_infinite_homogeneous_medium(dim):
     ref[0::p.nd] = (q / sa) * math.sqrt(p.hx * (p.hy if dim == 2 else 1.0))
     assert np.max(np.abs(phi - ref)) < 1e-11 * np.max(ref)
     assert st.converged
+
+
+def test_p5_infinite_medium_by_reflecting_slab():
+    """The infinite homogeneous medium as a slab whose two ends reflect specularly (dense LU of the coupled
+    system with the mirrored ordinates coupled at the ends): phi == q / sigma_a exactly, with no inflow."""
+    q, ss, sa = 1.0, 7.0, 0.5
+    p = Problem(small_1d(nx=10, n_polar=8, rx=1, src_box=(0, 1, 0, 1), src_q=q, inflow_g=0.0), 0, [ss], [sa])
+    phi = T.solve_reflecting_1d(p)
+    ref = np.zeros(p.ndof)
+    ref[0::2] = (q / sa) * math.sqrt(p.hx)
+    assert np.max(np.abs(phi - ref)) < 1e-12 * np.max(ref)
+    # the same medium with vacuum ends loses particles: the reflection terms are what keeps phi flat
+    A, b = T.dense_coupled_system(p)
+    vac = T.scalar_flux(p, np.linalg.solve(A, b).reshape(p.ndir, p.ndof))
+    assert np.max(np.abs(vac - ref)) > 0.1 * np.max(ref)
+
+
+def test_reflecting_end_equals_mirrored_slab():
+    """A reflecting end at x = 0 is a mirror: the slab [0, 1] with reflection at 0 and vacuum at 1 has the scalar
+    flux of the symmetric slab [-1, 1] (mirrored cross sections and source, vacuum at both ends) on [0, 1],
+    for non-uniform cross sections and source (pins the end coupling: sign, trace and mirrored ordinate)."""
+    ss, sa = [5.0, 1.0, 30.0, 2.0], [0.1, 0.3, 0.2, 0.05]
+    half = small_1d(nx=8, n_polar=8, rx=4, src_box=(0.25, 0.5, 0, 1), src_q=1.0, inflow_g=0.0)
+    p = Problem(half, 0, ss, sa)
+    phi_refl = T.solve_reflecting_1d(p, left=True, right=False)
+    full = dataclasses.replace(half, nx=[16], box=(-1.0, 1.0, 0.0, 1.0), rx=8, src_box=(-0.5, 0.5, 0, 1))
+    # mirrored regions and source: [-1, 0] is the reflection of [0, 1]; the source box [0.25, 0.5] and its
+    # mirror [-0.5, -0.25] are covered by one box [-0.5, 0.5] minus the centre [-0.25, 0.25]
+    pf = Problem(full, 0, ss[::-1] + ss, sa[::-1] + sa)
+    inner = Problem(dataclasses.replace(full, src_box=(-0.25, 0.25, 0, 1)), 0, ss[::-1] + ss, sa[::-1] + sa)
+    A, b = T.dense_coupled_system(pf)
+    b = b - np.tile(inner.G, pf.ndir)
+    phi_full = T.scalar_flux(pf, np.linalg.solve(A, b).reshape(pf.ndir, pf.ndof))
+    assert rel(phi_full[p.ndof:], phi_refl) < 1e-12
+    # and the mirror image on [-1, 0]: cell order reversed, odd Legendre mode flips sign
+    left = phi_full[:p.ndof].reshape(-1, 2)[::-1] * np.array([1.0, -1.0])
+    assert rel(left.reshape(-1), phi_refl) < 1e-12
 
 
 def test_p6_pure_absorber_one_iteration():
