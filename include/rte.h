@@ -57,6 +57,9 @@ extern "C" {
 /* arithmetic type of the vectors handed to a call */
 #define RTE_F64 0
 #define RTE_F32 1
+#define RTE_F64_DF 2   /* FP64 vectors, sweep arithmetic in double-float (pairs of FP32 numbers, ~48
+                          significant bits): accepted by rte_apply_op only (the refinement residual of the
+                          mixed-precision solves, run on the FP32 pipe) */
 
 const char* rte_status_string(int status);
 const char* rte_last_error(void);
@@ -64,6 +67,11 @@ const char* rte_last_error(void);
 int rte_version(int* major, int* minor);
 /* Number of CUDA kernels this library has launched in this process (monotonic counter). */
 long long rte_kernel_launches(void);
+/* Measured fused multiply-add throughput of the current device (no paper counterpart: the denominator of
+ * the roofline fractions of the ALU-bound sweep kernels).  dtype RTE_F32 or RTE_F64; *tflops = the best
+ * of three timed launches (after one warm-up) of a kernel whose threads run eight independent FMA chains
+ * each, 2 flop per FMA, on a grid of 8 blocks of 256 threads per SM.  Synchronises the stream. */
+int rte_fma_peak(int dtype, double* tflops, void* stream);
 
 /* ----------------------------------------------------------------- problem */
 typedef struct rte_problem_desc {
@@ -121,7 +129,8 @@ int rte_sweep(rte_problem_t p, int dtype, const void* src, int with_bc, void* ps
 int rte_scalar_flux(rte_problem_t p, int dtype, const void* psi, void* phi, void* stream);
 /* phi = T s = sum_j omega_j (D_j + Sigma_t)^{-1} s (eq. memory-efficient-SI), fused, psi never stored. */
 int rte_apply_T(rte_problem_t p, int dtype, const void* s, void* phi, void* stream);
-/* w = A~ z = z - T (Sigma_s z) (eq. memory-efficient-rte), fused. */
+/* w = A~ z = z - T (Sigma_s z) (eq. memory-efficient-rte), fused.  dtype RTE_F64_DF: z and w are FP64, the
+ * sweep and the sum of its partial fluxes run in double-float and z - (.) in FP64 (relative error ~1e-14). */
 int rte_apply_op(rte_problem_t p, int dtype, const void* z, void* w, void* stream);
 /* btilde = sum_j omega_j (D_j + Sigma_t)^{-1} (G + g_j^bc) (eq. memory-efficient-SI). */
 int rte_rhs(rte_problem_t p, int dtype, void* btilde, void* stream);
@@ -162,6 +171,9 @@ typedef struct romsad_greedy_opts {
     int hf_max_iter;
     int indicator_f32;    /* 1: evaluate the eq. rom-residual indicator in FP32 (it only decides the
                              argmax sample); 0: FP64                                           */
+    int hf_dsa;           /* 1: the high-fidelity solves of step 2(a) are FGMRES-DSA (partially consistent DSA
+                             through one V-cycle from the first iteration, 2D), the paper's solver there;
+                             the xi recurrence uses the recorded z = M^{-1} v.  0: FGMRES with M = I */
 } romsad_greedy_opts;
 
 typedef struct romsad_report {
@@ -308,7 +320,15 @@ typedef struct fgmres_opts {
                                 instead of the reduced solve (instances without an MLP, or with a
                                 non-finite prediction, keep the plain apply)               */
     int dsa_variant;         /* RTE_POST_DSA: RTE_DSA_PARTIAL or RTE_DSA_LUMPED            */
+    int refine_residual;     /* mixed: precision of the refinement residuals b~ - A~ phi that steer the
+                                inner solves.  RTE_RESIDUAL_DF (0): double-float sweeps (~1e-14 relative,
+                                on the FP32 pipe), except for a step predicted to converge; a residual that
+                                meets rtol is always recomputed by an FP64 sweep before the instance stops,
+                                so convergence is certified in FP64.  RTE_RESIDUAL_FP64 (1): every residual
+                                an FP64 sweep.  b~ is FP64 in both.                              */
 } fgmres_opts;
+#define RTE_RESIDUAL_DF 0
+#define RTE_RESIDUAL_FP64 1
 
 typedef struct fgmres_stats {
     int status;              /* RTE_OK or RTE_ERR_NOT_CONVERGED / RTE_ERR_NUMERIC      */
@@ -316,6 +336,7 @@ typedef struct fgmres_stats {
     int sweeps;              /* operator applies counted as in Sec. 5 (1 + iterations
                                 with a zero guess; +1 per restart / nonzero guess)   */
     int sweeps_fp64;         /* of which in FP64                                       */
+    int sweeps_df;           /* of which in double-float (mixed refinement residuals)  */
     int restarts;
     int outer;               /* mixed: refinement steps                                */
     int escalated;           /* mixed: 1 if the instance was finished by FP64 FGMRES   */

@@ -207,8 +207,12 @@ class GreedyReport:
 def greedy(p_template: Problem, sigma_s: np.ndarray, sigma_a: np.ndarray, window: int = 2,
            max_greedy_iter: int = 10, max_rank: int = 32, eps_rom: float = 1e-8,
            eps_qr: float = 1e-13, mu1: Optional[int] = None, hf_rtol: float = 1e-12,
-           restart: int = 30, want_labels: bool = False):
-    """Greedy ROM construction of Sec. 4.4.2.  Returns (Rom, GreedyReport)."""
+           restart: int = 30, want_labels: bool = False, hf_post: Optional[str] = None):
+    """Greedy ROM construction of Sec. 4.4.2.  Returns (Rom, GreedyReport).
+
+    hf_post: preconditioner of the step 2(a) high-fidelity FGMRES, None (M = I) or one of the DSA options of
+    make_preconditioner (the paper solves step 2(a) with FGMRES-DSA); the first cycle keeps the
+    preconditioned vectors z that the xi recurrence reads."""
     n_train = sigma_s.shape[0]
     probs = [with_params(p_template, sigma_s[i], sigma_a[i]) for i in range(n_train)]
     # Step 1: b~_mu and eta_mu^(0) = Sigma_s r_mu^(0) with r^(0) = b~ (zero initial guess)
@@ -222,8 +226,9 @@ def greedy(p_template: Problem, sigma_s: np.ndarray, sigma_a: np.ndarray, window
     rom = None
     while True:
         q = probs[k_idx]
-        # Step 2(a): high-fidelity FGMRES (M = I, zero guess), keep the first cycle
-        phi, st, first = fgmres(lambda z: Atilde_apply(q, z), bt[k_idx], None, restart=restart,
+        # Step 2(a): high-fidelity FGMRES (M = I or DSA, zero guess), keep the first cycle
+        pre = make_preconditioner(None, q, window, hf_post) if hf_post else None
+        phi, st, first = fgmres(lambda z: Atilde_apply(q, z), bt[k_idx], pre, restart=restart,
                                 rtol=hf_rtol, true_residual_check=False, record_first_cycle=True)
         rep.hf_iterations.append(st.iterations)
         xis = xi_recurrence(phi, first, window)

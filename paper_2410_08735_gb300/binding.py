@@ -17,10 +17,12 @@ from . import build_lib
 
 RTE_OK = 0
 RTE_ERR_NOT_CONVERGED = 4
-RTE_F64, RTE_F32 = 0, 1
+RTE_ERR_NUMERIC = 5
+RTE_F64, RTE_F32, RTE_F64_DF = 0, 1, 2
 RTE_POST_ROM, RTE_POST_IDENTITY, RTE_POST_DSA = 0, 1, 2
 RTE_DSA_PARTIAL, RTE_DSA_LUMPED = 0, 1
 RTE_MODE_FP64, RTE_MODE_MIXED, RTE_MODE_MIXED_F64KRYLOV = 0, 1, 2
+RTE_RESIDUAL_DF, RTE_RESIDUAL_FP64 = 0, 1
 
 _lib = None
 
@@ -52,7 +54,7 @@ class GreedyOpts(ctypes.Structure):
     _fields_ = [("window", ctypes.c_int), ("max_greedy_iter", ctypes.c_int), ("max_rank", ctypes.c_int),
                 ("eps_rom", ctypes.c_double), ("eps_qr", ctypes.c_double), ("mu1", ctypes.c_int),
                 ("hf_rtol", ctypes.c_double), ("hf_restart", ctypes.c_int), ("hf_max_iter", ctypes.c_int),
-                ("indicator_f32", ctypes.c_int)]
+                ("indicator_f32", ctypes.c_int), ("hf_dsa", ctypes.c_int)]
 
 
 class GreedyReport(ctypes.Structure):
@@ -72,12 +74,13 @@ class FgmresOpts(ctypes.Structure):
                 ("window", ctypes.c_int), ("post_mode", ctypes.c_int), ("mode", ctypes.c_int),
                 ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("true_residual_check", ctypes.c_int), ("warm_start", ctypes.c_int), ("learned_slot", ctypes.c_int),
-                ("dsa_variant", ctypes.c_int)]
+                ("dsa_variant", ctypes.c_int), ("refine_residual", ctypes.c_int)]
 
 
 class FgmresStats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("sweeps", ctypes.c_int),
-                ("sweeps_fp64", ctypes.c_int), ("restarts", ctypes.c_int), ("outer", ctypes.c_int),
+                ("sweeps_fp64", ctypes.c_int), ("sweeps_df", ctypes.c_int), ("restarts", ctypes.c_int),
+                ("outer", ctypes.c_int),
                 ("escalated", ctypes.c_int), ("learned_start", ctypes.c_int), ("learned_slot", ctypes.c_int),
                 ("est_rel_residual", ctypes.c_double),
                 ("true_rel_residual", ctypes.c_double), ("true_linf_residual", ctypes.c_double)]
@@ -91,6 +94,7 @@ _SIGS = {
     "rte_last_error": (ctypes.c_char_p, []),
     "rte_version": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "rte_kernel_launches": (ctypes.c_longlong, []),
+    "rte_fma_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
     "rte_problem_create": (ctypes.c_int, [ctypes.POINTER(ProblemDesc), ctypes.POINTER(ctypes.c_void_p)]),
     "rte_problem_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "rte_problem_get_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ProblemInfo)]),
@@ -182,6 +186,13 @@ def exported_symbols():
 def kernel_launches() -> int:
     """Kernels launched by librte_gb300 so far in this process."""
     return int(load().rte_kernel_launches())
+
+
+def fma_peak(dtype: int = RTE_F32, stream=None) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (RTE_F32 or RTE_F64)."""
+    out = ctypes.c_double(0.0)
+    _check(load().rte_fma_peak(dtype, ctypes.byref(out), _stream(stream)), "rte_fma_peak")
+    return out.value
 
 
 def _check(status: int, where: str):
@@ -294,8 +305,10 @@ class Problem:
     def apply_T(self, s, phi, stream=None):
         _check(load().rte_apply_T(self.h, _dtype_code(s), _ptr(s), _ptr(phi), _stream(stream)), "rte_apply_T")
 
-    def apply_op(self, z, w, stream=None):
-        _check(load().rte_apply_op(self.h, _dtype_code(z), _ptr(z), _ptr(w), _stream(stream)), "rte_apply_op")
+    def apply_op(self, z, w, stream=None, double_float=False):
+        """w = A~ z; double_float=True: FP64 tensors, sweep in double-float arithmetic (RTE_F64_DF)."""
+        code = RTE_F64_DF if double_float else _dtype_code(z)
+        _check(load().rte_apply_op(self.h, code, _ptr(z), _ptr(w), _stream(stream)), "rte_apply_op")
 
     def apply_op_noalloc(self, z, w, stream=None):
         """rte_apply_op without device allocation (fixed 16 MiB scratch shared by all calls)."""
@@ -328,12 +341,12 @@ class Rom:
     @classmethod
     def greedy(cls, problem: Problem, train_ss, train_sa, window=2, max_greedy_iter=10, max_rank=32,
                eps_rom=1e-8, eps_qr=1e-13, mu1=-1, hf_rtol=1e-12, hf_restart=30, hf_max_iter=2000,
-               want_labels=False, indicator_f32=False):
+               want_labels=False, indicator_f32=False, hf_dsa=False):
         ss = np.ascontiguousarray(train_ss, dtype=np.float64)
         sa = np.ascontiguousarray(train_sa, dtype=np.float64)
         n_train = ss.shape[0]
         o = GreedyOpts(window, max_greedy_iter, max_rank, eps_rom, eps_qr, mu1, hf_rtol, hf_restart, hf_max_iter,
-                       int(indicator_f32))
+                       int(indicator_f32), int(hf_dsa))
         sampled = (ctypes.c_int * max_greedy_iter)()
         ind = (ctypes.c_double * max_greedy_iter)()
         labels = np.zeros((n_train, max_rank)) if want_labels else None
@@ -465,7 +478,8 @@ def attach_mlp(rom: "Rom", mlp: Optional[Mlp]):
 def fgmres_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi, phi0=None, restart=30,
                  rtol=1e-10, max_iter=1000, window=2, post_mode=RTE_POST_ROM, mode=RTE_MODE_FP64,
                  inner_rtol=1e-2, max_outer=20, true_residual_check=True, stream=None, raise_on_fail=True,
-                 learned_warm_start=False, learned_slot=False, dsa_variant=RTE_DSA_PARTIAL):
+                 learned_warm_start=False, learned_slot=False, dsa_variant=RTE_DSA_PARTIAL,
+                 refine_residual=RTE_RESIDUAL_DF):
     """FGMRES-ROMSAD for all instances; phi: FP64 device tensor or host (numpy/pinned) buffer.
     post_mode=RTE_POST_DSA switches to DSA after the window (with roms=None: GMRES-DSA).
 
@@ -474,7 +488,7 @@ def fgmres_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi,
     B = problem.spec.n_instances
     ws = 2 if learned_warm_start else int(phi0 is not None)
     o = FgmresOpts(restart, rtol, max_iter, window, post_mode, mode, inner_rtol, max_outer,
-                   int(true_residual_check), ws, int(learned_slot), int(dsa_variant))
+                   int(true_residual_check), ws, int(learned_slot), int(dsa_variant), int(refine_residual))
     st = (FgmresStats * B)()
     if roms is None:
         rarr = None
@@ -487,7 +501,7 @@ def fgmres_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi,
         phi_ptr = _ptr(phi)
     s = load().fgmres_solve(problem.h, rarr, ctypes.byref(o), _ptr(phi0), phi_ptr, st, _stream(stream))
     stats = [st[b].as_dict() for b in range(B)]
-    if s != RTE_OK and (raise_on_fail or s != RTE_ERR_NOT_CONVERGED):
+    if s != RTE_OK and (raise_on_fail or s not in (RTE_ERR_NOT_CONVERGED, RTE_ERR_NUMERIC)):
         _check(s, "fgmres_solve")
     return stats
 
@@ -497,7 +511,7 @@ def si_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi, phi
     """SI-ROMSAD (source iteration, ROM correction in the window, then post_mode) for all instances, FP64.
     phi: FP64 device tensor or host (numpy) buffer.  Returns the list of per-instance stats dicts."""
     B = problem.spec.n_instances
-    o = FgmresOpts(1, rtol, max_iter, window, post_mode, RTE_MODE_FP64, 0.0, 0, 0, 0, 0, int(dsa_variant))
+    o = FgmresOpts(1, rtol, max_iter, window, post_mode, RTE_MODE_FP64, 0.0, 0, 0, 0, 0, int(dsa_variant), 0)
     st = (FgmresStats * B)()
     rarr = None if roms is None else (ctypes.c_void_p * B)(*[(r.h.value if r is not None else None) for r in roms])
     if isinstance(phi, np.ndarray):
@@ -507,7 +521,7 @@ def si_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi, phi
         phi_ptr = _ptr(phi)
     s = load().si_solve(problem.h, rarr, ctypes.byref(o), _ptr(phi0), phi_ptr, st, _stream(stream))
     stats = [st[b].as_dict() for b in range(B)]
-    if s != RTE_OK and (raise_on_fail or s != RTE_ERR_NOT_CONVERGED):
+    if s != RTE_OK and (raise_on_fail or s not in (RTE_ERR_NOT_CONVERGED, RTE_ERR_NUMERIC)):
         _check(s, "si_solve")
     return stats
 

@@ -11,7 +11,8 @@
 //      max_j ||(D_j + Sigma_t) U_j c - Sigma_s W c - eta^(0)|| (eq. rom-residual); sample the argmax.
 //
 // Readings where the paper is silent: the indicator is divided by ||eta^(0)||_2 before the eps_ROM
-// test; the truncation test is relative to the snapshot norm; the high-fidelity solve uses M = I;
+// test; the truncation test is relative to the snapshot norm; the high-fidelity solve is FGMRES-DSA as in
+// the paper (partially consistent DSA through one V-cycle; opts->hf_dsa) or FGMRES with M = I;
 // argmax ties go to the lowest index; mu_1 defaults to the training point nearest the centroid of
 // (log sigma_s, sigma_a).  U is stored per unique in-plane direction (the +-Omega_z duplicates have
 // identical angular fluxes) with the duplicate count as weight of the inner product.
@@ -251,7 +252,8 @@ static int greedy_impl(rte_problem* tmpl, int n_train, const double* tss, const 
     FirstCycle rec;
     rec.want = window;
     int its = 0, hst = 0;
-    RTE_TRY(hf_solve(hp.p, o->hf_rtol, o->hf_restart, o->hf_max_iter, phi.p, &rec, &its, &hst));
+    RTE_TRY(hf_solve(hp.p, o->hf_rtol, o->hf_restart, o->hf_max_iter, o->hf_dsa ? RTE_DSA_PARTIAL : -1, phi.p, &rec,
+                     &its, &hst));
     if (hst != RTE_OK) {
       set_error("romsad_build_greedy: high-fidelity solve did not converge (raise hf_max_iter or hf_restart)");
       return RTE_ERR_NOT_CONVERGED;

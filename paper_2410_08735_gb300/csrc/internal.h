@@ -145,6 +145,9 @@ struct rte_problem {
   rte::DevBuf<double> d_G;                    // [ntot] source moments
   rte::DevBuf<double> d_linv64;               // [B][nu][R][nd*nd]
   rte::DevBuf<float> d_linv32;
+  rte::DevBuf<float> d_linv_df;               // the same as double-float pairs (hi, lo) [..][2]
+  rte::DevBuf<float> d_sig_s_df;              // [B][R][2] sigma_s as double-float pairs
+  rte::DevBuf<float> d_xdf;                   // [ntot][2] operator input split into double-float pairs
   // sweep scratch (grown on demand)
   rte::DevBuf<unsigned char> d_partial;       // partial scalar fluxes per task
   // task lists per directions-per-warp value D (index D), built once; stable device pointers
@@ -152,12 +155,12 @@ struct rte_problem {
   int ntasks_by_D[17] = {0};
   int per_inst_by_D[17] = {0};
   int tasks_D = -1;                           // D of the most recent launch
-  // sweep autotuner (sweep.cu): tuned directions per warp and kernel variant per [fp64][angular]
-  // (0 = not tuned); force_* steer launches while candidates are timed
-  int tuned_D[2][2] = {{0, 0}, {0, 0}};
-  int tuned_var[2][2] = {{-1, -1}, {-1, -1}};
+  // sweep autotuner (sweep.cu): tuned directions per warp and kernel variant per [precision][angular]
+  // (precision: PREC_F32, PREC_F64, PREC_DF; 0 = not tuned); force_* steer launches while candidates are timed
+  int tuned_D[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  int tuned_var[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
   int force_D = 0, force_var = -1;
-  float tuned_ms[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  float tuned_ms[3][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   int ntasks = 0, tasks_per_inst = 0;
   rte::DevBuf<int> d_active;                  // [B] instance mask (1 = active), all 1 by default
   rte::DevBuf<double> d_tmp64;                // [ntot] temporaries
@@ -175,8 +178,15 @@ int upload_params(rte_problem* p);
 //   mode: 0 phi = T s ; 1 w = z - T(Sigma_s z) ; 2 r = b - (z - T(Sigma_s z)) ; 3 b~ (src = G, bc)
 //   compute_f64: arithmetic of the sweep; out_f64: type of out and b
 enum SweepMode { MODE_T = 0, MODE_OP = 1, MODE_RES = 2, MODE_RHS = 3 };
+// arithmetic of a sweep: FP32, FP64, or double-float (pairs of FP32, dfloat.cuh)
+enum SweepPrec { PREC_F32 = 0, PREC_F64 = 1, PREC_DF = 2 };
 int launch_T(rte_problem* p, int mode, bool compute_f64, const void* src, bool in_f64, const void* bvec,
              void* out, bool out_f64, const int* d_active, cudaStream_t st);
+// A~ x (MODE_OP) or b - A~ x (MODE_RES) with FP64 vectors and double-float sweep arithmetic: x is split into
+// double-float pairs, swept, and the partial fluxes are summed in double-float; the final z - T Sigma_s z and
+// b - (.) are formed in FP64.
+int launch_T_df(rte_problem* p, int mode, const double* x, const double* bvec, double* out, const int* d_active,
+                cudaStream_t st);
 // Angular-output sweep; scale_sigma_s multiplies the source by sigma_s, unique_layout writes one block
 // per unique direction ([nu][N] per instance) instead of all N_Omega directions.
 int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st,

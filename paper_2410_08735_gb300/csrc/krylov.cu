@@ -1597,16 +1597,27 @@ static Ws* get_ws(rte_problem* p) {
   return static_cast<Ws*>(p->krylov_ws.get());
 }
 
-// High-fidelity FP64 FGMRES (M = I, zero initial guess) on a one-instance problem, recording the first
-// cycle; used by the greedy ROM construction (step 2(a)).  x: device output [N].
-int hf_solve(rte_problem* p, double rtol, int restart, int max_iter, double* x, FirstCycle* rec, int* iterations,
-             int* status) {
+// High-fidelity FP64 FGMRES (zero initial guess) on a one-instance problem, recording the first cycle; used
+// by the greedy ROM construction (step 2(a)).  dsa_variant < 0: M = I; otherwise FGMRES-DSA (the DSA
+// preconditioner of that variant from the first iteration), the paper's high-fidelity solver.  The recorded
+// Z holds the preconditioned vectors z = M^{-1} v the xi recurrence needs.  x: device output [N].
+int hf_solve(rte_problem* p, double rtol, int restart, int max_iter, int dsa_variant, double* x, FirstCycle* rec,
+             int* iterations, int* status) {
   Ws* ws = get_ws(p);
-  RTE_TRY(ws->alloc(p, restart, false));
+  const bool dsa = dsa_variant >= 0;
+  if (dsa) RTE_TRY(dsa_check(p));
+  RTE_TRY(ws->alloc(p, restart, dsa));
   RTE_TRY(prepare_sweeps(p));
-  SolveCtx C{p, nullptr, restart, 0, RTE_POST_IDENTITY, 0, ws, rec};
+  SolveCtx C{p, nullptr, restart, 0, dsa ? RTE_POST_DSA : RTE_POST_IDENTITY, 0, ws, rec};
   std::vector<RomPlan> none;
   C.plans = &none;
+  if (dsa) {
+    C.dsa = true;
+    C.no_rom_mask.assign(p->B, 1);
+    C.any_norom = true;
+    RTE_CHECK_CUDA(cudaMemcpy(ws->norom.p, C.no_rom_mask.data(), p->B * sizeof(int), cudaMemcpyHostToDevice));
+    RTE_TRY(dsa_prepare(p, dsa_variant, 0));
+  }
   RTE_TRY(launch_T(p, MODE_RHS, true, nullptr, true, nullptr, ws->bt.p, true, nullptr, 0));
   std::vector<int> all(p->B, 1), zero(p->B, 0);
   RunStats rs;
@@ -1630,6 +1641,8 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
           "unknown mode");
   RTE_ARG(o->post_mode == RTE_POST_ROM || o->post_mode == RTE_POST_IDENTITY || o->post_mode == RTE_POST_DSA,
           "unknown post_mode");
+  RTE_ARG(o->mode == RTE_MODE_FP64 || o->refine_residual == RTE_RESIDUAL_DF || o->refine_residual == RTE_RESIDUAL_FP64,
+          "unknown refine_residual");
   const bool use_dsa = o->post_mode == RTE_POST_DSA;
   if (use_dsa) {
     RTE_ARG(o->dsa_variant == RTE_DSA_PARTIAL || o->dsa_variant == RTE_DSA_LUMPED, "unknown dsa_variant");
@@ -1756,25 +1769,23 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     warm = !groups.empty();
   }
   std::vector<int> learned(B, 0);
-  bool ro_ready = false;   // ws->ro holds b~ - A~ x for every instance
   if (o->warm_start == 2 && warm) {
-    // The plain ROMSAD start (zero) is the fallback for an instance whose learned start is not finite.
-    // (The residual norm is no test of a learned start: it removes the slow, smooth error components
-    // that take FGMRES-ROMSAD many iterations while it can raise the residual in fast ones.)  The
-    // residual is needed by the refinement anyway (mixed mode); in FP64 mode it is one extra sweep.
-    RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ws->ro.p, true, nullptr, st));
+    // The plain ROMSAD start (zero) is the fallback for an instance whose learned start is not finite,
+    // read from the norm of the start itself (no sweep).  (The residual norm is no test of a learned
+    // start: it removes the slow, smooth error components that take FGMRES-ROMSAD many iterations while it
+    // can raise the residual in fast ones.)
     std::vector<int> all1(B, 1);
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, all1.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-    k_norm<<<B, 512, 0, st>>>(ws->ro.p, p->d_inst.p, ws->active.p, ws->nrm.p);
+    k_norm<<<B, 512, 0, st>>>(x, p->d_inst.p, ws->active.p, ws->nrm.p);
     count_launch();
-    std::vector<double> hr(B);
-    RTE_CHECK_CUDA(cudaMemcpyAsync(hr.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
+    std::vector<double> hx(B);
+    RTE_CHECK_CUDA(cudaMemcpyAsync(hx.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
     RTE_CHECK_CUDA(cudaStreamSynchronize(st));
     std::vector<int> fallback(B, 0);
     bool anyf = false;
     for (int b = 0; b < B; ++b) {
       const bool has = roms[b] && roms[b]->mlp;
-      learned[b] = has && std::isfinite(hr[b]);
+      learned[b] = has && std::isfinite(hx[b]);
       fallback[b] = !learned[b];
       anyf = anyf || fallback[b];
     }
@@ -1783,10 +1794,7 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, fallback.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
       k_zero_active<<<vg, 256, 0, st>>>(x, p->d_inst.p, ws->active.p);
       count_launch();
-      k_copy_active<<<vg, 256, 0, st>>>(ws->ro.p, ws->bt.p, p->d_inst.p, ws->active.p);
-      count_launch();
     }
-    ro_ready = true;
   }
   // learned correction in the ROMSAD slot (zero start only): the first preconditioner apply takes the
   // coefficients c_hat(mu) / ||b~|| from each instance's ROM MLP instead of the reduced solve; instances
@@ -1834,8 +1842,8 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
   std::vector<fgmres_stats> S(B);
   for (int b = 0; b < B; ++b) {
     std::memset(&S[b], 0, sizeof(fgmres_stats));
-    S[b].sweeps = ro_ready ? 2 : 1;
-    S[b].sweeps_fp64 = ro_ready ? 2 : 1;
+    S[b].sweeps = 1;
+    S[b].sweeps_fp64 = 1;
     S[b].learned_start = learned[b];
     S[b].learned_slot = slot_used[b];
     S[b].true_rel_residual = NAN;
@@ -1857,14 +1865,36 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     // FP64 iterative refinement around the FP32-sweep inner FGMRES.  The outer residual has its own
     // buffer (ro): the inner solve keeps its working residual in r and recomputes it from its
     // right-hand side at every restart, so the two must not alias.
+    //
+    // Residual precision.  b~ is FP64.  A refinement residual b~ - A~ x only steers the next inner solve, so
+    // it runs in double-float arithmetic (~1e-14 relative, on the FP32 pipe) unless the step is predicted to
+    // converge; the residual that certifies convergence is always an FP64 sweep: an instance whose
+    // double-float residual meets rtol is re-checked in FP64 before it stops (ro64 marks which residuals
+    // are FP64).  refine_residual = RTE_RESIDUAL_FP64 makes every residual FP64.
+    const bool res_df = o->refine_residual == RTE_RESIDUAL_DF;
     const dim3 vg = vec_grid(p);
     double* ro = ws->ro.p;
-    std::vector<int> act(B, 1), esc(B, 0);
-    if (ro_ready) {
-      // residual of the (learned or zero) start already in ro, counted above
-    } else if (warm) {
-      RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ro, true, nullptr, st));
-      for (int b = 0; b < B; ++b) { S[b].sweeps += 1; S[b].sweeps_fp64 += 1; }
+    std::vector<int> act(B, 1), esc(B, 0), ro64(B, 1);
+    auto residual = [&](const std::vector<int>& mask64, const std::vector<int>& maskdf) -> int {
+      bool any64 = false, anydf = false;
+      for (int b = 0; b < B; ++b) { any64 = any64 || mask64[b]; anydf = anydf || maskdf[b]; }
+      if (any64) {
+        RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, mask64.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+        RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ro, true, ws->active.p, st));
+      }
+      if (anydf) {
+        RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, maskdf.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+        RTE_TRY(launch_T_df(p, MODE_RES, x, ws->bt.p, ro, ws->active.p, st));
+      }
+      for (int b = 0; b < B; ++b) {
+        if (mask64[b]) { S[b].sweeps += 1; S[b].sweeps_fp64 += 1; ro64[b] = 1; }
+        if (maskdf[b]) { S[b].sweeps += 1; S[b].sweeps_df += 1; ro64[b] = 0; }
+      }
+      return RTE_OK;
+    };
+    if (warm) {
+      std::vector<int> m64(B, res_df ? 0 : 1), mdf(B, res_df ? 1 : 0);
+      RTE_TRY(residual(m64, mdf));
     } else {
       RTE_CHECK_CUDA(cudaMemsetAsync(x, 0, p->ntot * 8, st));
       RTE_CHECK_CUDA(cudaMemcpyAsync(ro, ws->bt.p, p->ntot * 8, cudaMemcpyDeviceToDevice, st));
@@ -1876,18 +1906,39 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     // iterations so that a stagnating instance is caught early.
     const double esc_ratio = std::max(0.25, std::sqrt(o->inner_rtol));
     const int inner_cap = std::max(4 * o->restart, 512);
+    // a step predicted (inner solve's own residual reduction x current residual) to land below
+    // kPredict * rtol takes its residual in FP64 directly, saving the double-float sweep of the check
+    const double kPredict = 0.5;
     std::vector<double> hb(B), hr(B), hprev(B, 0.0);
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
     k_norm<<<B, 512, 0, st>>>(ws->bt.p, p->d_inst.p, ws->active.p, ws->nrm.p);
     count_launch();
     RTE_CHECK_CUDA(cudaMemcpyAsync(hb.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
     RTE_CHECK_CUDA(cudaStreamSynchronize(st));
-    for (int outer = 0; outer <= o->max_outer; ++outer) {
+    auto read_norms = [&]() -> int {
       RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
       k_norm<<<B, 512, 0, st>>>(ro, p->d_inst.p, ws->active.p, ws->nrm.p);
       count_launch();
       RTE_CHECK_CUDA(cudaMemcpyAsync(hr.data(), ws->nrm.p, B * 8, cudaMemcpyDeviceToHost, st));
       RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+      return RTE_OK;
+    };
+    for (int outer = 0; outer <= o->max_outer; ++outer) {
+      RTE_TRY(read_norms());
+      // certification: a double-float residual that meets rtol is recomputed in FP64
+      {
+        std::vector<int> cert(B, 0), none(B, 0);
+        bool any = false;
+        for (int b = 0; b < B; ++b) {
+          if (!act[b] || ro64[b]) continue;
+          const double rel = hb[b] > 0 ? hr[b] / hb[b] : 0.0;
+          if (std::isfinite(rel) && rel <= o->rtol) { cert[b] = 1; any = true; }
+        }
+        if (any) {
+          RTE_TRY(residual(cert, none));
+          RTE_TRY(read_norms());
+        }
+      }
       int nact = 0;
       for (int b = 0; b < B; ++b) {
         if (!act[b]) continue;
@@ -1932,13 +1983,19 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
         k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d32.p, p->d_inst.p, ws->active.p);
       }
       count_launch();
-      // ro = b~ - A~ x in FP64
-      RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ro, true, ws->active.p, st));
+      // ro = b~ - A~ x: FP64 where the step is predicted to converge, double-float elsewhere
+      std::vector<int> m64(B, 0), mdf(B, 0);
+      for (int b = 0; b < B; ++b) {
+        if (!act[b]) continue;
+        const double predicted = rs.est[b] * (hb[b] > 0 ? hr[b] / hb[b] : 0.0);
+        if (!res_df || predicted <= kPredict * o->rtol) m64[b] = 1;
+        else mdf[b] = 1;
+      }
+      RTE_TRY(residual(m64, mdf));
       for (int b = 0; b < B; ++b) {
         if (!act[b]) continue;
         S[b].iterations += rs.iterations[b];
-        S[b].sweeps += rs.sweeps[b] + 1;
-        S[b].sweeps_fp64 += 1;
+        S[b].sweeps += rs.sweeps[b];
         S[b].restarts += rs.restarts[b];
         S[b].outer += 1;
         if (rs.status[b] == RTE_ERR_NUMERIC) { act[b] = 0; S[b].status = RTE_ERR_NUMERIC; }
@@ -1966,6 +2023,19 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       // FP64 residual of the escalated instances for the report below (not a solver sweep)
       RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, esc.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
       RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ro, true, ws->active.p, st));
+      for (int b = 0; b < B; ++b)
+        if (esc[b]) ro64[b] = 1;
+    }
+    // instances that stopped on a double-float residual (not converged, or NaN): their reported residual is
+    // recomputed in FP64 (not a solver sweep)
+    {
+      std::vector<int> redo(B, 0);
+      bool any = false;
+      for (int b = 0; b < B; ++b) { redo[b] = !ro64[b]; any = any || redo[b]; }
+      if (any) {
+        RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, redo.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
+        RTE_TRY(launch_T(p, MODE_RES, true, x, true, ws->bt.p, ro, true, ws->active.p, st));
+      }
     }
   }
   // FP64 true residual (l2, linf) for reporting; not counted as a solver sweep

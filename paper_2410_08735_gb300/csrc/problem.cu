@@ -82,7 +82,7 @@ static void gauss_mode_integrals(double xl, double h, double a, double xc, doubl
 }
 
 __global__ void k_linv(int B, int nu, int R, int dim, const InstInfo* inst, const UDir* ud,
-                       const double* sig_t, double* out64, float* out32) {
+                       const double* sig_t, double* out64, float* out32, float* outdf) {
   long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long total = (long long)B * nu * R;
   if (tid >= total) return;
@@ -134,6 +134,10 @@ __global__ void k_linv(int B, int nu, int R, int dim, const InstInfo* inst, cons
   for (int i = 0; i < nd * nd; ++i) {
     out64[base + i] = X[i];
     out32[base + i] = (float)X[i];
+    // double-float pair: the FP32 rounding and the FP32 rounding of what it misses
+    const float h = (float)X[i];
+    outdf[2 * (base + i)] = h;
+    outdf[2 * (base + i) + 1] = (float)(X[i] - (double)h);
   }
 }
 
@@ -154,19 +158,22 @@ __global__ void k_sig_dof(const InstInfo* inst, int B, int R, int rx, int ry, in
 
 int upload_params(rte_problem* p) {
   std::vector<double> st(p->ss.size());
-  std::vector<float> s32(p->ss.size());
+  std::vector<float> s32(p->ss.size()), sdf(2 * p->ss.size());
   for (size_t i = 0; i < st.size(); ++i) {
     st[i] = p->ss[i] + p->sa[i];
     s32[i] = (float)p->ss[i];
+    sdf[2 * i] = s32[i];
+    sdf[2 * i + 1] = (float)(p->ss[i] - (double)s32[i]);
   }
   RTE_CHECK_CUDA(cudaMemcpy(p->d_sig_s.p, p->ss.data(), st.size() * 8, cudaMemcpyHostToDevice));
   RTE_CHECK_CUDA(cudaMemcpy(p->d_sig_t.p, st.data(), st.size() * 8, cudaMemcpyHostToDevice));
   RTE_CHECK_CUDA(cudaMemcpy(p->d_sig_s32.p, s32.data(), s32.size() * 4, cudaMemcpyHostToDevice));
+  RTE_CHECK_CUDA(cudaMemcpy(p->d_sig_s_df.p, sdf.data(), sdf.size() * 4, cudaMemcpyHostToDevice));
   long long total = (long long)p->B * p->nu * p->R;
   int threads = 128;
   k_linv<<<(unsigned)((total + threads - 1) / threads), threads>>>(p->B, p->nu, p->R, p->dim, p->d_inst.p,
                                                                   p->d_udir.p, p->d_sig_t.p, p->d_linv64.p,
-                                                                  p->d_linv32.p);
+                                                                  p->d_linv32.p, p->d_linv_df.p);
   count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   {
@@ -365,12 +372,14 @@ static int create_impl(const rte_problem_desc* d, rte_problem* p) {
   RTE_TRY(p->d_sig_s.alloc(nR));
   RTE_TRY(p->d_sig_t.alloc(nR));
   RTE_TRY(p->d_sig_s32.alloc(nR));
+  RTE_TRY(p->d_sig_s_df.alloc(2 * nR));
   RTE_TRY(p->d_G.alloc(p->ntot));
   RTE_TRY(p->d_sig_dof.alloc(p->ntot));
   RTE_TRY(p->d_sig_dof32.alloc(p->ntot));
   size_t nl = (size_t)p->B * p->nu * p->R * p->nd * p->nd;
   RTE_TRY(p->d_linv64.alloc(nl));
   RTE_TRY(p->d_linv32.alloc(nl));
+  RTE_TRY(p->d_linv_df.alloc(2 * nl));
   RTE_TRY(p->d_active.alloc(p->B));
   RTE_TRY(p->d_wq.alloc(p->ndir));
   RTE_CHECK_CUDA(cudaMemcpy(p->d_inst.p, p->inst.data(), p->B * sizeof(InstInfo), cudaMemcpyHostToDevice));

@@ -41,8 +41,8 @@ struct FirstCycle {
   std::vector<double> H;     // unrotated Hessenberg, column-major [m][m+1]
   DevBuf<double> Z;          // [nz][N] z^(1..nz) (= v without a preconditioner)
 };
-int hf_solve(rte_problem* p, double rtol, int restart, int max_iter, double* x, FirstCycle* rec, int* iterations,
-             int* status);
+int hf_solve(rte_problem* p, double rtol, int restart, int max_iter, int dsa_variant, double* x, FirstCycle* rec,
+             int* iterations, int* status);
 int rom_add_column(romsad* rom, DevBuf<double>& d_mult, DevBuf<double>& d_wA, cudaStream_t st);
 int rom_compute_Y_column(romsad* rom, const rte_problem* p, int inst, int k, cudaStream_t st);
 void rom_init_geometry(romsad* rom, const rte_problem* p, int b);

@@ -23,9 +23,12 @@
 // (1, -sqrt3), tx_b = psi_0b + sqrt3 psi_1b (x-outflow trace), ty_a = psi_a0 + sqrt3 psi_a1; L^{-1}
 // per (instance, direction, region) is precomputed (problem.cu) and staged in shared memory.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
+#include "dfloat.cuh"
 #include "internal.h"
 
 namespace rte {
@@ -73,6 +76,31 @@ struct Vec4<double> {
     reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
   }
 };
+
+template <>
+struct Vec4<dfloat> {
+  __device__ static void load(const dfloat* p, dfloat& a, dfloat& b, dfloat& c, dfloat& d) {
+    const float4 v0 = reinterpret_cast<const float4*>(p)[0];
+    const float4 v1 = reinterpret_cast<const float4*>(p)[1];
+    a = dfloat(v0.x, v0.y); b = dfloat(v0.z, v0.w); c = dfloat(v1.x, v1.y); d = dfloat(v1.z, v1.w);
+  }
+  __device__ static void store(dfloat* p, dfloat a, dfloat b, dfloat c, dfloat d) {
+    reinterpret_cast<float4*>(p)[0] = make_float4(a.hi, a.lo, b.hi, b.lo);
+    reinterpret_cast<float4*>(p)[1] = make_float4(c.hi, c.lo, d.hi, d.lo);
+  }
+};
+
+// value of the lane below (lane - 1) in the warp
+template <typename T>
+__device__ __forceinline__ T shfl_up1(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <>
+__device__ __forceinline__ dfloat shfl_up1<dfloat>(dfloat v) {
+  return dfloat(__shfl_up_sync(0xffffffffu, v.hi, 1), __shfl_up_sync(0xffffffffu, v.lo, 1));
+}
+
+// precision slot of a sweep arithmetic type (autotuner tables, partial-sum element size)
+template <typename T>
+constexpr int prec_of() { return std::is_same<T, float>::value ? PREC_F32 : (std::is_same<T, double>::value ? PREC_F64 : PREC_DF); }
 
 // Angular output: lane (f's segment, cell e) stores one cell of the completed 8-cell segment of lane f,
 // whose current column is colf at cell cf, from f's staging ring to every block of the task's
@@ -247,8 +275,8 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
     T yi0[D], yi1[D];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      yi0[d] = __shfl_up_sync(0xffffffffu, ty0[d], 1);
-      yi1[d] = __shfl_up_sync(0xffffffffu, ty1[d], 1);
+      yi0[d] = shfl_up1(ty0[d]);
+      yi1[d] = shfl_up1(ty1[d]);
     }
     if (act) {
       if (lane == 0) {
@@ -454,8 +482,8 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
       T yi0[D], yi1[D];
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        yi0[d] = __shfl_up_sync(0xffffffffu, ty0[d], 1);
-        yi1[d] = __shfl_up_sync(0xffffffffu, ty1[d], 1);
+        yi0[d] = shfl_up1(ty0[d]);
+        yi1[d] = shfl_up1(ty1[d]);
       }
       if (act) {
         if (lane == 0) {
@@ -711,10 +739,11 @@ int launch_forward_cols(int dim, int nx, int ny, double hx, double hy, const UDi
 }
 
 // ----------------------------------------------------------------- host side
-static int pick_D(const rte_problem* p, bool f64, bool ang = false) {
+static int pick_D(const rte_problem* p, int prec, bool ang = false) {
   if (p->dim == 1) return 1;
   if (p->force_D > 0) return p->force_D;
-  if (p->tuned_D[f64 ? 1 : 0][ang ? 1 : 0] > 0) return p->tuned_D[f64 ? 1 : 0][ang ? 1 : 0];
+  if (p->tuned_D[prec][ang ? 1 : 0] > 0) return p->tuned_D[prec][ang ? 1 : 0];
+  const bool f64 = prec != PREC_F32;
   const int nq = p->quad_start[1] - p->quad_start[0];
   // Directions per warp: the largest D that still leaves at least 8 warps per SM (152 SMs) in
   // flight; with fewer tasks (a single small instance) parallelism wins and D = 1.  FP64 keeps D
@@ -770,6 +799,26 @@ static int ensure_tasks(rte_problem* p, int D) {
   return RTE_OK;
 }
 
+// Dynamic shared memory above the 48 KB default must be granted per kernel with cudaFuncSetAttribute, which
+// acts on the current device only; granted[dev] remembers the size already granted on each device (zero-
+// initialised statics), so a process that drives several GPUs grants it on each of them.
+constexpr int kMaxDevices = 64;
+template <typename K>
+static int grant_smem(K kern, size_t smem, std::atomic<size_t>* granted) {
+  if (smem <= 48 * 1024) return RTE_OK;
+  int dev = 0;
+  RTE_CHECK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("sweep: device ordinal beyond the supported range");
+    return RTE_ERR_UNSUPPORTED;
+  }
+  if (smem > granted[dev].load(std::memory_order_acquire)) {
+    RTE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    granted[dev].store(smem, std::memory_order_release);
+  }
+  return RTE_OK;
+}
+
 template <typename T, typename TI, bool ANG>
 static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) {
   if (p->dim == 1) {
@@ -789,10 +838,10 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
   // enough tasks to fill the GPU the FP64 pipe is the limit and the warp-per-task kernel keeps more
   // warps per SM (no idle band warps on smaller meshes of a mixed batch).
   const bool throughput = a.ntasks >= 152 * 8;
-  const bool fp64_throughput = sizeof(T) == 8 && throughput;
+  const bool fp64_throughput = sizeof(T) == 8 && throughput;   // FP64 or double-float
   // angular output with many tasks: independent warps (no per-step CTA barrier) hide the store latency
   const bool ang_throughput = ANG && throughput;
-  const int tv = p->force_var >= 0 ? p->force_var : p->tuned_var[sizeof(T) == 8 ? 1 : 0][ANG ? 1 : 0];
+  const int tv = p->force_var >= 0 ? p->force_var : p->tuned_var[prec_of<T>()][ANG ? 1 : 0];
   const bool band = tv >= 0 ? (tv == 0 && nbands <= 8) : (nbands <= 8 && !fp64_throughput && !ang_throughput);
   if (band) {
     // band-parallel kernel: one CTA per task, one warp per 32-row band
@@ -807,11 +856,8 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
 #define RTE_BAND_CASE(DD)                                                                                   \
   case DD: {                                                                                                \
     auto kern = k_sweep2d_bands<T, TI, DD, ANG>;                                                            \
-    static size_t smem_set = 48 * 1024;                                                                     \
-    if (smem > smem_set) {                                                                                  \
-      RTE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));   \
-      smem_set = smem;                                                                                      \
-    }                                                                                                       \
+    static std::atomic<size_t> granted[kMaxDevices];                                                        \
+    RTE_TRY(grant_smem(kern, smem, granted));                                                               \
     kern<<<a.ntasks, W * 32, smem, st>>>(a);                                                                \
     count_launch();                                                                                         \
     break;                                                                                                  \
@@ -843,11 +889,8 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
 #define RTE_SWEEP_CASE(DD)                                                                                  \
   case DD: {                                                                                                \
     auto kern = k_sweep2d<T, TI, DD, ANG>;                                                                  \
-    static size_t smem_set = 48 * 1024;                                                                     \
-    if (smem > smem_set) {                                                                                  \
-      RTE_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));   \
-      smem_set = smem;                                                                                      \
-    }                                                                                                       \
+    static std::atomic<size_t> granted[kMaxDevices];                                                        \
+    RTE_TRY(grant_smem(kern, smem, granted));                                                               \
     kern<<<blocks, wpb * 32, smem, st>>>(a);                                                                \
     count_launch();                                                                                         \
     break;                                                                                                  \
@@ -866,13 +909,14 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
   return RTE_OK;
 }
 
-static void fill_args(rte_problem* p, SweepArgs& a, bool f64) {
+static void fill_args(rte_problem* p, SweepArgs& a, int prec) {
   std::memset(&a, 0, sizeof(a));
   a.inst = p->d_inst.p;
   a.udir = p->d_udir.p;
   a.tasks = p->d_tasks_by_D[p->tasks_D].p;
   a.ntasks = p->ntasks;
-  a.linv = f64 ? (const void*)p->d_linv64.p : (const void*)p->d_linv32.p;
+  a.linv = prec == PREC_F64 ? (const void*)p->d_linv64.p
+                            : (prec == PREC_DF ? (const void*)p->d_linv_df.p : (const void*)p->d_linv32.p);
   a.g = p->g;
   a.tasks_per_inst = p->tasks_per_inst;
   a.ndir = p->ndir;
@@ -882,19 +926,20 @@ static void fill_args(rte_problem* p, SweepArgs& a, bool f64) {
   a.ry = p->ry;
 }
 
-static int ensure_partial(rte_problem* p, bool f64) {
-  size_t bytes = (size_t)p->tasks_per_inst * p->ntot * (f64 ? 8 : 4);
+static int ensure_partial(rte_problem* p, int prec) {
+  size_t bytes = (size_t)p->tasks_per_inst * p->ntot * (prec == PREC_F32 ? 4 : 8);
   return p->d_partial.ensure(bytes);
 }
 
 // Sweep autotuner: times every valid (kernel variant, directions per warp) pair for one precision and
 // output mode on this problem (two launches each after a warm-up, CUDA events on the stream) and keeps
-// the fastest.  Candidates: D in {1, 2, 4, 8} dividing the directions of a quadrant (FP64: D <= 4;
-// angular output: D <= 4), variant band (ny <= 256) or warp-per-task.  The operator apply is timed
-// with its partial-sum reduction, since D also sets the number of partials.
-int autotune(rte_problem* p, bool f64, bool ang, const void* src, void* psi, cudaStream_t st, bool scale_sigma_s,
+// the fastest.  Candidates: D in {1, 2, 4, 8} dividing the directions of a quadrant (FP64 and
+// double-float: D <= 4; angular output: D <= 4), variant band (ny <= 256) or warp-per-task.  The operator
+// apply is timed with its partial-sum reduction, since D also sets the number of partials.
+int autotune(rte_problem* p, int prec, bool ang, const void* src, void* psi, cudaStream_t st, bool scale_sigma_s,
              bool unique_layout) {
-  const int fi = f64 ? 1 : 0, ai = ang ? 1 : 0;
+  const int fi = prec, ai = ang ? 1 : 0;
+  const bool f64 = prec == PREC_F64;
   if (p->tuned_D[fi][ai] > 0 || p->dim == 1) return RTE_OK;
   const int nq = p->quad_start[1] - p->quad_start[0];
   int maxny = 0;
@@ -902,10 +947,10 @@ int autotune(rte_problem* p, bool f64, bool ang, const void* src, void* psi, cud
   RTE_TRY(p->d_tmp64.ensure((size_t)p->ntot));
   // partials for the largest candidate task count (D = 1)
   RTE_TRY(ensure_tasks(p, 1));
-  RTE_TRY(ensure_partial(p, f64));
+  RTE_TRY(ensure_partial(p, prec));
   const void* in = src;
   // the FP32 operator is timed with an FP32 input and output, as the inner solves launch it
-  const bool in32 = !f64 && !ang && !src;
+  const bool in32 = prec == PREC_F32 && !ang && !src;
   if (in32) {
     RTE_TRY(p->d_tmp32.ensure((size_t)2 * p->ntot));
     RTE_CHECK_CUDA(cudaMemsetAsync(p->d_tmp32.p, 0, (size_t)2 * p->ntot * sizeof(float), st));
@@ -921,7 +966,7 @@ int autotune(rte_problem* p, bool f64, bool ang, const void* src, void* psi, cud
   for (int var = 0; var < 2; ++var) {
     if (var == 0 && (maxny + 31) / 32 > 8) continue;
     for (int D : {1, 2, 4, 8}) {
-      if (nq % D || (f64 && D > 4) || (ang && D > 4)) continue;
+      if (nq % D || (prec != PREC_F32 && D > 4) || (ang && D > 4)) continue;
       p->force_D = D;
       p->force_var = var;
       // one warm-up launch, then the best of five timed launches (robust to a slow outlier)
@@ -931,6 +976,8 @@ int autotune(rte_problem* p, bool f64, bool ang, const void* src, void* psi, cud
         if (rep > 0) cudaEventRecord(e0, st);
         if (ang) rc = launch_angular(p, f64, in, 0, psi, st, scale_sigma_s, unique_layout);
         else if (in32) rc = launch_T(p, MODE_OP, false, in, false, nullptr, p->d_tmp32.p + p->ntot, false, nullptr, st);
+        else if (prec == PREC_DF)
+          rc = launch_T_df(p, MODE_OP, reinterpret_cast<const double*>(in), nullptr, p->d_tmp64.p, nullptr, st);
         else rc = launch_T(p, MODE_OP, f64, in, !f64 && src ? false : true, nullptr, p->d_tmp64.p, true, nullptr, st);
         if (rep > 0 && rc == RTE_OK) {
           float ms = 0.f;
@@ -961,27 +1008,70 @@ int autotune(rte_problem* p, bool f64, bool ang, const void* src, void* psi, cud
   return RTE_OK;
 }
 
-// Tune both precisions of the operator apply, then build their task lists and size the partial-sum
-// buffer for the larger one, so that later launches (including captured CUDA graphs) see stable
-// device pointers.
+// Tune the three precisions of the operator apply (FP32, FP64, double-float), then build their task lists
+// and size the partial-sum buffer (and the double-float input buffer) for the largest, so that later
+// launches (including captured CUDA graphs) see stable device pointers.
 int prepare_sweeps(rte_problem* p) {
-  RTE_TRY(autotune(p, false, false, nullptr, nullptr, 0, false, false));
-  RTE_TRY(autotune(p, true, false, nullptr, nullptr, 0, false, false));
-  const int d64 = pick_D(p, true), d32 = pick_D(p, false);
-  RTE_TRY(ensure_tasks(p, d32));
-  const size_t b32 = (size_t)p->tasks_per_inst * p->ntot * 4;
-  RTE_TRY(ensure_tasks(p, d64));
-  const size_t b64 = (size_t)p->tasks_per_inst * p->ntot * 8;
-  return p->d_partial.ensure(std::max(b32, b64));
+  RTE_TRY(p->d_xdf.ensure((size_t)2 * p->ntot));
+  RTE_TRY(autotune(p, PREC_F32, false, nullptr, nullptr, 0, false, false));
+  RTE_TRY(autotune(p, PREC_F64, false, nullptr, nullptr, 0, false, false));
+  RTE_TRY(autotune(p, PREC_DF, false, nullptr, nullptr, 0, false, false));
+  size_t bytes = 0;
+  for (int prec : {PREC_F32, PREC_F64, PREC_DF}) {
+    RTE_TRY(ensure_tasks(p, pick_D(p, prec)));
+    bytes = std::max(bytes, (size_t)p->tasks_per_inst * (size_t)p->ntot * (size_t)(prec == PREC_F32 ? 4 : 8));
+  }
+  return p->d_partial.ensure(bytes);
+}
+
+// x (FP64) -> double-float pairs, all instances
+__global__ void k_split_df(const double* x, long long n, float2* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    const float h = (float)v;
+    out[i] = make_float2(h, (float)(v - (double)h));
+  }
+}
+
+int launch_T_df(rte_problem* p, int mode, const double* x, const double* bvec, double* out, const int* d_active,
+                cudaStream_t st) {
+  if (mode != MODE_OP && mode != MODE_RES) {
+    set_error("launch_T_df: only the operator and the residual run in double-float");
+    return RTE_ERR_UNSUPPORTED;
+  }
+  RTE_TRY(p->d_xdf.ensure((size_t)2 * p->ntot));
+  const int D = pick_D(p, PREC_DF);
+  RTE_TRY(ensure_tasks(p, D));
+  RTE_TRY(ensure_partial(p, PREC_DF));
+  float2* xdf = reinterpret_cast<float2*>(p->d_xdf.p);
+  k_split_df<<<(unsigned)std::min<long long>(4096, (p->ntot + 255) / 256), 256, 0, st>>>(x, p->ntot, xdf);
+  count_launch();
+  SweepArgs a;
+  fill_args(p, a, PREC_DF);
+  a.src = xdf;
+  a.with_bc = 0;
+  a.sig_s = p->d_sig_s_df.p;
+  a.partial = p->d_partial.p;
+  a.active = d_active;
+  RTE_TRY((launch_sweep_t<dfloat, dfloat, false>(p, D, a, st)));
+  int maxn = 0;
+  for (int b = 0; b < p->B; ++b) maxn = std::max(maxn, (int)(p->off[b + 1] - p->off[b]));
+  dim3 grid((maxn + 255) / 256, p->B);
+  k_reduce<dfloat, double, double><<<grid, 256, 0, st>>>(reinterpret_cast<const dfloat*>(p->d_partial.p),
+                                                         p->tasks_per_inst, p->d_inst.p, mode, x, bvec, out, d_active);
+  count_launch();
+  RTE_CHECK_CUDA(cudaGetLastError());
+  return RTE_OK;
 }
 
 int launch_T(rte_problem* p, int mode, bool f64, const void* src, bool in_f64, const void* bvec, void* out,
              bool out_f64, const int* d_active, cudaStream_t st) {
-  int D = pick_D(p, f64);
+  const int prec = f64 ? PREC_F64 : PREC_F32;
+  int D = pick_D(p, prec);
   RTE_TRY(ensure_tasks(p, D));
-  RTE_TRY(ensure_partial(p, f64));
+  RTE_TRY(ensure_partial(p, prec));
   SweepArgs a;
-  fill_args(p, a, f64);
+  fill_args(p, a, prec);
   a.src = mode == MODE_RHS ? (const void*)p->d_G.p : src;
   bool src64 = mode == MODE_RHS ? true : in_f64;
   a.with_bc = mode == MODE_RHS ? 1 : 0;
@@ -1024,11 +1114,12 @@ int launch_T(rte_problem* p, int mode, bool f64, const void* src, bool in_f64, c
 // Sweep part of A~ z only: fills the per-task partial scalar fluxes (Sigma_s scaling fused); the
 // subtraction z - sum_t partial_t is left to the caller's kernel (the fused Arnoldi step).
 int launch_op_partials(rte_problem* p, bool f64, const void* z, bool in_f64, const int* d_active, cudaStream_t st) {
-  int D = pick_D(p, f64);
+  const int prec = f64 ? PREC_F64 : PREC_F32;
+  int D = pick_D(p, prec);
   RTE_TRY(ensure_tasks(p, D));
-  RTE_TRY(ensure_partial(p, f64));
+  RTE_TRY(ensure_partial(p, prec));
   SweepArgs a;
-  fill_args(p, a, f64);
+  fill_args(p, a, prec);
   a.src = z;
   a.sig_s = f64 ? (const void*)p->d_sig_s.p : (const void*)p->d_sig_s32.p;
   a.partial = p->d_partial.p;
@@ -1082,17 +1173,15 @@ int launch_op_external(rte_problem* p, bool f64, const void* z, void* w, const S
   return RTE_OK;
 }
 
-int autotune(rte_problem* p, bool f64, bool ang, const void* src, void* psi, cudaStream_t st, bool scale_sigma_s,
-             bool unique_layout);
-
 int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void* psi, cudaStream_t st,
                    bool scale_sigma_s, bool unique_layout) {
-  if (p->force_D == 0) RTE_TRY(autotune(p, f64, true, src, psi, st, scale_sigma_s, unique_layout));
-  int D = pick_D(p, f64, true);
+  const int prec = f64 ? PREC_F64 : PREC_F32;
+  if (p->force_D == 0) RTE_TRY(autotune(p, prec, true, src, psi, st, scale_sigma_s, unique_layout));
+  int D = pick_D(p, prec, true);
   RTE_TRY(ensure_tasks(p, D));
-  RTE_TRY(ensure_partial(p, f64));
+  RTE_TRY(ensure_partial(p, prec));
   SweepArgs a;
-  fill_args(p, a, f64);
+  fill_args(p, a, prec);
   a.src = src;
   a.with_bc = with_bc ? 1 : 0;
   a.partial = p->d_partial.p;
@@ -1150,6 +1239,9 @@ int rte_apply_T(rte_problem_t p, int dtype, const void* s, void* phi, void* stre
 
 int rte_apply_op(rte_problem_t p, int dtype, const void* z, void* w, void* stream) {
   RTE_ARG(p && z && w, "null handle or pointer");
+  if (dtype == RTE_F64_DF)
+    return rte::launch_T_df(p, rte::MODE_OP, reinterpret_cast<const double*>(z), nullptr, reinterpret_cast<double*>(w),
+                            nullptr, (cudaStream_t)stream);
   RTE_TRY(check_dtype(dtype));
   bool f = dtype == RTE_F64;
   return rte::launch_T(p, rte::MODE_OP, f, z, f, nullptr, w, f, nullptr, (cudaStream_t)stream);

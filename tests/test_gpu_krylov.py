@@ -159,10 +159,11 @@ def test_fgmres_romsad_fp64_slab_matches_oracle():
     assert sum(s["iterations"] for s in stats) < sum(s["iterations"] for s in st0)
 
 
-@pytest.mark.parametrize("mode", ["mixed", "mixed_f64krylov"])
-def test_mixed_precision_meets_fp64_accuracy(mode):
-    """Mixed modes (inner solves all FP32, or FP32 sweeps with FP64 Krylov vectors, MGS and Givens): FP64
-    true residual <= 1e-8 and phi within 1e-7 of the FP64 oracle."""
+@pytest.mark.parametrize("mode,residual", [("mixed", "df"), ("mixed", "fp64"), ("mixed_f64krylov", "df")])
+def test_mixed_precision_meets_fp64_accuracy(mode, residual):
+    """Mixed modes (inner solves all FP32, or FP32 sweeps with FP64 Krylov vectors, MGS and Givens), refinement
+    residuals in double-float (certified by a final FP64 residual) or all in FP64: FP64 true residual <= 1e-8
+    and phi within 1e-7 of the FP64 oracle, element by element."""
     B = lib()
     spec = spec2d([32, 16], [32, 16], n_polar=4, n_azim=8)
     ss, sa = wl.draw_params(spec, 2, 23)
@@ -170,14 +171,47 @@ def test_mixed_precision_meets_fp64_accuracy(mode):
     gp = B.Problem(spec, ss, sa)
     ops = oracle_problems(spec, ss, sa)
     md = B.RTE_MODE_MIXED if mode == "mixed" else B.RTE_MODE_MIXED_F64KRYLOV
+    rr = B.RTE_RESIDUAL_DF if residual == "df" else B.RTE_RESIDUAL_FP64
     phi, stats = _solve_gpu(B, gp, None, restart=60, rtol=1e-8, max_iter=2000, mode=md,
-                            inner_rtol=1e-4, max_outer=20)
+                            inner_rtol=1e-4, max_outer=20, refine_residual=rr)
     for b, op in enumerate(ops):
         ref, _ = ORS.solve(op, None, restart=200, rtol=1e-13, max_iter=3000)
-        assert stats[b]["status"] == 0
-        assert stats[b]["true_rel_residual"] <= 1e-8
-        assert stats[b]["outer"] >= 1 and stats[b]["sweeps_fp64"] >= 2
-        assert rel(split(phi, gp.offsets)[b], ref) < 1e-7
+        st = stats[b]
+        assert st["status"] == 0
+        assert st["true_rel_residual"] <= 1e-8
+        assert st["outer"] >= 1 and st["sweeps_fp64"] >= 2
+        # b~, one residual per refinement step, at most one FP64 re-check of a double-float residual
+        assert 1 + st["outer"] <= st["sweeps_fp64"] + st["sweeps_df"] <= 2 + st["outer"]
+        if residual == "fp64":
+            assert st["sweeps_df"] == 0
+        else:
+            assert st["sweeps_fp64"] <= 3
+        got = split(phi, gp.offsets)[b]
+        assert rel(got, ref) < 1e-7
+        assert np.max(np.abs(got - ref)) < 1e-6 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_nan_in_initial_guess_is_reported_as_numeric(mode):
+    """A NaN injected from the host into the initial guess reaches the first residual: fgmres_solve returns
+    RTE_ERR_NUMERIC (status of that instance too) instead of iterating on it; the other instance converges."""
+    torch = torch_cuda()
+    B = lib()
+    spec = spec2d([16, 16], [16, 16], n_polar=4, n_azim=8)
+    ss, sa = wl.draw_params(spec, 2, 41)
+    ss = np.minimum(ss, 20.0)
+    gp = B.Problem(spec, ss, sa)
+    phi0 = torch.zeros(gp.n_dof, dtype=torch.float64, device="cuda")
+    phi0[gp.offsets[1] + 7] = float("nan")
+    phi = torch.zeros_like(phi0)
+    md = B.RTE_MODE_FP64 if mode == "fp64" else B.RTE_MODE_MIXED
+    with pytest.raises(B.RteError) as ei:
+        B.fgmres_solve(gp, None, phi, phi0=phi0, restart=30, rtol=1e-8, max_iter=500, mode=md, inner_rtol=1e-3)
+    assert ei.value.status == 5   # RTE_ERR_NUMERIC
+    stats = B.fgmres_solve(gp, None, phi, phi0=phi0, restart=30, rtol=1e-8, max_iter=500, mode=md, inner_rtol=1e-3,
+                           raise_on_fail=False)
+    assert stats[1]["status"] == 5
+    assert stats[0]["status"] == 0 and stats[0]["true_rel_residual"] <= 1e-8
 
 
 def test_mixed_inner_restarts_keep_their_right_hand_side():

@@ -18,11 +18,14 @@ def _dense_Atilde(p):
     return np.stack([T.Atilde_apply(p, e) for e in np.eye(p.ndof)], axis=1)
 
 
-def test_xi_recurrence_equals_dense_solve():
-    """xi^(l) from eqs. correction-fgmres1/2 equals A~^{-1} v^(l)."""
+@pytest.mark.parametrize("pre", [None, "dsa_vcycle"])
+def test_xi_recurrence_equals_dense_solve(pre):
+    """xi^(l) from eqs. correction-fgmres1/2 equals A~^{-1} v^(l), for FGMRES with M = I and with the DSA
+    preconditioner (the recorded z = M^{-1} v enter the recurrence; the identity holds for any M)."""
     p = _problem()
     bt = T.rhs_btilde(p)
-    phi, st, first = fgmres(lambda z: T.Atilde_apply(p, z), bt, None, restart=200, rtol=1e-14,
+    M = RS.make_preconditioner(None, p, 2, pre) if pre else None
+    phi, st, first = fgmres(lambda z: T.Atilde_apply(p, z), bt, M, restart=200, rtol=1e-14,
                             true_residual_check=False, record_first_cycle=True)
     Ad = _dense_Atilde(p)
     xis = RS.xi_recurrence(phi, first, 4)
