@@ -2,19 +2,26 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
-A step solves one batch of seeded parameter instances of the workload to FP64 true residual
-1e-8 (relative l2 of b~ - A~ phi).  `value` is the mixed-precision path (FP32 sweeps, FP64
-Arnoldi/Givens/residual); `fp64` beside it is the plain FP64 path on the same GPU.  Inputs are
-resident in HBM when the timed region starts; L2 is flushed (a 256 MiB write) before every
-timed step.  `e2e` repeats the mixed measurement through the C ABI with host buffers: each step
-copies its parameters host->device and the scalar flux device->host inside the timed region.
-Under torchrun every rank solves its own instances (no collective on the data path): weak scaling.
+A step solves one batch of seeded parameter instances of the workload to FP64 true residual 1e-8 (relative
+l2 of b~ - A~ phi).  The default workload is the largest single-GPU configuration of the metric,
+large256_192: 64 instances of the 256x256 problem (upwind DG Q1, 8 x 24 = 192 directions, 8x8 regions,
+sigma_s log-uniform in [1, 1e4], sigma_a uniform in [0, 1]), restart 40, MLP initial guess.
+
+`value` is the mixed-precision path with the learned start (FP32 sweeps and inner solves, FP64 b~ and
+certifying residual, double-float refinement residuals); `fp64` beside it is plain FP64 FGMRES-ROMSAD on the
+same GPU with the same ROM.  Every leg carries the scalar-flux error of one sampled instance against the CPU
+oracle's tight solution (solved in background processes during the GPU legs).  Inputs are resident in HBM
+when the timed region starts; L2 is flushed (a 256 MiB write) before every timed step.  `e2e` repeats the
+headline through the C ABI with host buffers: each step copies its parameters host->device and the scalar
+flux device->host inside the timed region.  Under torchrun every rank solves its own instances (no
+collective on the data path): weak scaling.
 """
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
-import math
+import multiprocessing as mp
 import os
 import statistics
 import subprocess
@@ -24,7 +31,7 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-# the CPU oracle legs run on one host core: cap the BLAS / OpenMP pools before numpy starts them
+# every CPU oracle process runs on one core: cap the BLAS / OpenMP pools before numpy starts them
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
@@ -32,24 +39,21 @@ import numpy as np  # noqa: E402
 
 import workloads as wl  # noqa: E402
 
-# Arithmetic per cell and unique direction of the fused sweep (rhs assembly 8 FMA, 4x4 solve 16 FMA,
-# outflow traces 4 FMA, quadrature 4 FMA).
-SWEEP_FLOPS_PER_CELL_DIR = 64
-SWEEP32_DRAM_BYTES_64x64 = 116480   # dram__bytes_read.sum + dram__bytes_write.sum, one launch (ncu)
-# ALU peaks from the unit counts and the maximum SM clock (152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz);
-# FP64: GB300 nominal 1.25 TFLOP/s.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-FP64_PEAK_TFLOPS = 1.25
+# Algorithmic arithmetic per cell and unique direction of the fused 2D sweep (rhs assembly, 4x4 solve with the
+# precomputed cell inverse, outflow traces, quadrature): about 42 FMA = 90 flop.
+SWEEP_FLOPS_PER_CELL_DIR = 90
+
+METRIC = "param solves/s at 1e-8 true residual (mixed+MLP FGMRES-ROMSAD vs plain FP64 FGMRES-ROMSAD)"
+
+WORKLOADS = {"large256_192": 5, "batch256_uneven": 3, "square2d_64": 2, "slab1d_128": 1}
 
 
 def workload_spec(name: str):
-    if name == "square2d_64":
-        return wl.config(2), 1
-    if name == "batch256_uneven":
-        return wl.config(3), 256
-    if name == "slab1d_128":
-        return wl.config(1), 1
-    raise SystemExit(f"unknown workload {name}")
+    if name not in WORKLOADS:
+        raise SystemExit(f"unknown workload {name}")
+    cfg = WORKLOADS[name]
+    spec = wl.config(cfg)
+    return spec, spec.n_instances, cfg
 
 
 class ClockSampler:
@@ -144,90 +148,192 @@ def shard(rank: int, n_sets: int, B: int, step: int) -> tuple[int, int]:
     return i0, i0 + B
 
 
-# ------------------------------------------------------------------ oracle legs
-def oracle_sample(spec, ss, sa, iters_needed: int, sample_iters: int, dsa: bool = True):
-    """Time the CPU oracle on one instance: b~ plus a bounded number of FGMRES iterations (preconditioned by
-    the oracle's DSA V-cycle when dsa, whose set-up is timed too), and extrapolate to one full solve (the
-    same algorithm needs `iters_needed` iterations; the ROMSAD applies of the window cost a small dense
-    solve each and are left out)."""
-    from oracle import Problem as OProblem, dsa as ODSA, transport as OT
-    from oracle.krylov import fgmres
-    p = OProblem(spec, 0, ss, sa)
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ CPU oracle (spawned processes)
+def _one_instance_spec(cfg: int, nx: int, ny: int):
+    return wl.config(cfg).with_instances([nx], [ny])
+
+
+def oracle_reference_phi(cfg: int, nx: int, ny: int, ss, sa, rtol: float = 1e-12):
+    """The oracle's tight solution of one instance (FGMRES with its DSA V-cycle, FP64, one core): the reference
+    of the scalar-flux errors.  Runs in a spawned process."""
+    from oracle import Problem as OProblem, romsad as ORS
     t0 = time.perf_counter()
-    bt = OT.rhs_btilde(p)
+    p = OProblem(_one_instance_spec(cfg, nx, ny), 0, np.asarray(ss), np.asarray(sa))
+    phi, st = ORS.solve(p, None, post="dsa_vcycle", restart=60, rtol=rtol, max_iter=3000, true_residual_check=True)
+    return {"phi": phi, "iterations": st.iterations, "s": time.perf_counter() - t0}
+
+
+def oracle_sample_worker(cfg: int, nx: int, ny: int, ss, sa, n_warm: int, n_timed: int):
+    """Bounded sample of the oracle's FGMRES-DSA solve of one instance (one core): set-up (problem, b~, DSA
+    V-cycle hierarchy), then n_warm + n_timed iterations' work, each a V-cycle plus an A~ apply (the MGS and
+    least-squares work of an iteration is negligible next to the sweep).  Returns the timings."""
+    from oracle import Problem as OProblem, dsa as ODSA, transport as OT
+    t0 = time.perf_counter()
+    p = OProblem(_one_instance_spec(cfg, nx, ny), 0, np.asarray(ss), np.asarray(sa))
     t1 = time.perf_counter()
-    pre = None
-    if dsa:
-        mg = ODSA.MultigridDsa(p, "partial")
-        pre = lambda j, v: mg.apply(v)
-    t_setup = time.perf_counter() - t1
-    t1b = time.perf_counter()
-    fgmres(lambda z: OT.Atilde_apply(p, z), bt, pre, restart=min(sample_iters, 128), rtol=1e-30,
-           max_iter=sample_iters, true_residual_check=False)
+    bt = OT.rhs_btilde(p)
     t2 = time.perf_counter()
-    per_iter = (t2 - t1b) / sample_iters
-    solve_s = (t1 - t0) + t_setup + iters_needed * per_iter + (t1 - t0)   # b~, DSA set-up, iterations, residual
-    what = "FGMRES-DSA" if dsa else "FGMRES"
-    return {"value": 1.0 / solve_s, "unit": "param solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"b~ + {sample_iters} {what} iterations of one {spec.name} instance on 1 host core "
-                      f"({t2 - t0:.1f} s), extrapolated to {iters_needed} iterations + 1 residual sweep"}
+    mg = ODSA.MultigridDsa(p, "partial")
+    t3 = time.perf_counter()
+    v = bt / np.linalg.norm(bt)
+    per = []
+    for k in range(n_warm + n_timed):
+        a = time.perf_counter()
+        z = mg.apply(v)
+        w = OT.Atilde_apply(p, z)
+        v = w / np.linalg.norm(w)
+        if k >= n_warm:
+            per.append(time.perf_counter() - a)
+    return {"problem": t1 - t0, "btilde": t2 - t1, "setup": t3 - t2, "iters": per}
 
 
-METRIC = "param solves/s at 1e-8 true residual (mixed+MLP FGMRES-ROMSAD vs plain FP64 FGMRES-ROMSAD)"
+def oracle_baseline(cfg: int, spec, ss, sa, iters_needed: float, n_warm: int, n_timed: int, cores: int):
+    """The CPU oracle on all host cores: one instance per core, solved concurrently (a spawned process each), a
+    bounded sample per process extrapolated to a full FGMRES-DSA solve (set-up, b~, iters_needed iterations, one
+    residual).  Throughput = cores / extrapolated solve time."""
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        jobs = [pool.apply_async(oracle_sample_worker, (cfg, spec.nx[i % len(spec.nx)], spec.ny[i % len(spec.ny)],
+                                                        ss[i % len(ss)], sa[i % len(sa)], n_warm, n_timed))
+                for i in range(cores)]
+        res = [j.get() for j in jobs]
+    wall = time.perf_counter() - t0
+    per_iter = statistics.median(x for r in res for x in r["iters"])
+    fixed = statistics.median(r["problem"] + 2 * r["btilde"] + r["setup"] for r in res)
+    solve_s = fixed + iters_needed * per_iter
+    return {"value": cores / solve_s, "unit": "param solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{cores} concurrent one-core oracle processes, one {spec.nx[0]}x{spec.ny[0]} instance each: "
+                      f"problem + b~ + DSA V-cycle set-up + {n_warm + n_timed} FGMRES-DSA iterations' work "
+                      f"({wall:.1f} s wall); extrapolated to {iters_needed:.1f} iterations + 1 residual sweep "
+                      f"({solve_s:.1f} s per solve, {per_iter:.2f} s per iteration)",
+            "per_iter_s": per_iter, "solve_s": solve_s, "per_iter_samples": [x for r in res for x in r["iters"]]}
 
 
-def bench_config(args, spec, B):
-    """The workload description both arms print (no model keys: the workload is named by its sizes)."""
-    return {"workload": args.workload, "instances_per_step": B, "mesh": f"{spec.nx[0]}x{spec.ny[0]}",
-            "directions": spec.n_directions, "restart": args.restart,
-            "preconditioner": f"ROMSAD rank {getattr(args, 'rom_rank', 0) or spec.rom_rank} (window {spec.window}), then "
-                              + ("DSA (partially consistent, one multigrid V-cycle)" if getattr(args, "post", "dsa") == "dsa"
-                                 else "ROMSAD kept after the window"),
-            "warm_start": "MLP 8-128-128-r (mixed path only)",
-            "l2": "flushed (256 MiB write) before every timed step"}
+# FP64 GPU iteration count of each workload's solve, for the reference arm's extrapolation (the reference arm
+# runs before the GPU arm and cannot read it); the GPU arm's cpu_baseline uses its own measured count.
+REF_ITERS = {5: 37.0, 3: 15.3, 2: 16.0, 1: 10.0}
 
 
-def run_reference(args, spec, B, world, rank):
+def run_reference(args, spec, B, world, rank, cfg):
+    """The reference arm: the CPU oracle as it stands, on the workload of the GPU arm (bounded sample)."""
     if rank != 0:
         return
-    ss, sa = wl.draw_params(spec, max(1, B), wl.seed_for(2, 1))
-    iters = args.ref_iters
-    vals = []
     t_start = time.perf_counter()
-    one = spec.with_instances(spec.nx[:1], spec.ny[:1])
-    for _ in range(args.warmup):   # untimed warm-up samples
-        oracle_sample(one, ss[0], sa[0], iters, args.ref_sample, getattr(args, "post", "dsa") == "dsa")
-    for s in range(args.steps):
-        cb = oracle_sample(one, ss[0], sa[0], iters, args.ref_sample, getattr(args, "post", "dsa") == "dsa")
-        vals.append(1.0 / cb["value"])
-    total = sum(vals)
-    value = args.steps * B / total if B else 0.0
+    ss, sa = wl.draw_params(spec, max(B, 1), wl.seed_for(cfg, 1))
+    cores = min(host_cores(), args.ref_cores or host_cores())
+    iters = args.ref_iters if args.ref_iters is not None else REF_ITERS.get(cfg, 20.0)
+    cb = oracle_baseline(cfg, spec, ss, sa, iters, args.warmup, args.steps, cores)
+    value = cb["value"]
+    per = cb.pop("per_iter_samples")
     line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "param solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * statistics.mean(per), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": bench_config(args, spec, B),
+            "config": bench_config(args, spec, B, cfg),
             "cpu_baseline": dict(cb, value=value),
             "e2e": {"value": value, "unit": "param solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_start}
     print(json.dumps(line))
 
 
-# ------------------------------------------------------------------ GPU legs
-def post_kwargs(RB, args):
-    """fgmres_solve keywords of the preconditioner after the ROMSAD window."""
-    if args.post == "dsa":
-        return {"post_mode": RB.RTE_POST_DSA,
-                "dsa_variant": RB.RTE_DSA_LUMPED if args.dsa_variant == "lumped" else RB.RTE_DSA_PARTIAL}
-    return {"post_mode": RB.RTE_POST_ROM}
+def bench_config(args, spec, B, cfg):
+    """The workload description both arms print (no model keys: the workload is named by its sizes)."""
+    meshes = {}
+    for nx, ny in zip(spec.nx, spec.ny):
+        meshes[f"{nx}x{ny}"] = meshes.get(f"{nx}x{ny}", 0) + 1
+    return {"workload": args.workload, "instances_per_step": B,
+            "mesh": ", ".join(f"{c} x {m}" for m, c in meshes.items()),
+            "directions": spec.n_directions, "regions": f"{spec.rx}x{spec.ry}",
+            "sigma_s": f"log-uniform {spec.sigma_s_range}", "sigma_a": f"uniform {spec.sigma_a_range}",
+            "restart": spec.restart if args.restart is None else args.restart,
+            "preconditioner": f"ROMSAD rank <= {args.rom_rank or spec.rom_rank} (window {spec.window}, greedy with "
+                              f"FGMRES-DSA high-fidelity solves), then DSA (partially consistent, one multigrid "
+                              f"V-cycle)",
+            "warm_start": f"MLP {2 * spec.n_regions}-128-128-r (mixed path only)",
+            "l2": "flushed (256 MiB write) before every timed step"}
 
 
-def measure_sweep_hbm(RB, torch, dev, stream, flush, reps=5, config=3):
+# ------------------------------------------------------------------ GPU helpers
+def time_events(torch, stream, fn, reps=5, warm=2):
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def phi_error(phi, ref):
+    """Scalar-flux error against the oracle: relative l2 and max-abs over the reference's max-abs."""
+    if ref is None or phi is None:
+        return None
+    d = np.asarray(phi) - np.asarray(ref)
+    return {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref)),
+            "max_abs_over_linf": float(np.max(np.abs(d)) / np.max(np.abs(ref)))}
+
+
+def build_rom_and_mlp(RB, spec, cfg, args, n_train, rank_cap, restart, seed_net=2410, max_greedy=None):
+    """Offline (untimed): greedy ROM on the training draws (FGMRES-DSA high-fidelity solves), MLP trained on its
+    Galerkin-coefficient labels, attached to the ROM."""
+    R = spec.n_regions
+    t0 = time.perf_counter()
+    tr_ss, tr_sa = wl.draw_params(spec, n_train, wl.seed_for(cfg, 0))
+    tmpl = RB.Problem(spec.with_instances(spec.nx[:1], spec.ny[:1]), tr_ss[:1], tr_sa[:1])
+    rom, rep = RB.Rom.greedy(tmpl, tr_ss, tr_sa, window=spec.window,
+                             max_greedy_iter=max_greedy or max(1, rank_cap // spec.window), max_rank=rank_cap,
+                             eps_rom=0.0, hf_rtol=1e-10, hf_restart=restart, hf_max_iter=args.max_iter,
+                             want_labels=True, indicator_f32=True, hf_dsa=spec.dim == 2)
+    t_greedy = time.perf_counter() - t0
+    net = RB.Mlp(2 * R, 128, rep["rank"], seed=seed_net)
+    loss = net.train(np.concatenate([tr_ss, tr_sa], axis=1), rep["labels"], epochs=args.mlp_epochs,
+                     batch=min(64, n_train), lr=2e-3, bf16=True)
+    RB.attach_mlp(rom, net)
+    info = {"greedy_s": t_greedy, "total_s": time.perf_counter() - t0, "training_draws": n_train,
+            "rank": rep["rank"], "sampled": len(rep["sampled"]), "max_indicator_last": rep["max_indicator"][-1:]
+            if rep["max_indicator"] else [], "mlp_final_loss": loss}
+    return rom, net, tmpl, rep, (tr_ss, tr_sa), info
+
+
+def solve_stats(st):
+    return {"iterations_mean": statistics.mean(s["iterations"] for s in st),
+            "iterations_max": max(s["iterations"] for s in st),
+            "sweeps_fp64_mean": statistics.mean(s["sweeps_fp64"] for s in st),
+            "sweeps_df_mean": statistics.mean(s["sweeps_df"] for s in st),
+            "converged": sum(1 for s in st if s["status"] == 0), "of": len(st),
+            "escalated_to_fp64": sum(s["escalated"] for s in st),
+            "true_rel_residual_max": max(s["true_rel_residual"] for s in st)}
+
+
+# ------------------------------------------------------------------ extras (single GPU)
+def measure_sweep_hbm(RB, torch, dev, stream, flush, cfg, reps=5):
     """Angular-output sweep (rte_sweep, FP32) over a whole batched workload: an HBM-bound write of
     N_Omega * N_dof * 4 bytes (both duplicate directions stored), timed with CUDA events after warm-up."""
-    spec3 = wl.config(config)
-    ss, sa = wl.draw_params(spec3, spec3.n_instances, wl.seed_for(config, 1))
-    prob = RB.Problem(spec3, ss, sa)
+    spec = wl.config(cfg)
+    ss, sa = wl.draw_params(spec, spec.n_instances, wl.seed_for(cfg, 1))
+    prob = RB.Problem(spec, ss, sa)
     n = prob.n_dof
     src = torch.randn(n, dtype=torch.float32, device=dev)
     psi = torch.empty(prob.n_directions * n, dtype=torch.float32, device=dev)
@@ -247,58 +353,50 @@ def measure_sweep_hbm(RB, torch, dev, stream, flush, reps=5, config=3):
     ms = statistics.median(times)
     nbytes = prob.n_directions * n * 4 + n * 4
     peak = measured_peaks().get("hbm_gbs", 6800.0)
-    cells = sum(nx * ny for nx, ny in zip(spec3.nx, spec3.ny))
+    cells = sum(nx * ny for nx, ny in zip(spec.nx, spec.ny))
     meshes = {}
-    for nx, ny in zip(spec3.nx, spec3.ny):
+    for nx, ny in zip(spec.nx, spec.ny):
         meshes[f"{nx}x{ny}"] = meshes.get(f"{nx}x{ny}", 0) + 1
     desc = ", ".join(f"{c}x{m}" for m, c in meshes.items())
-    out = {"workload": f"{spec3.name} ({desc}; {prob.n_directions} directions, {spec3.n_regions} regions)",
+    out = {"workload": f"{spec.name} ({desc}; {prob.n_directions} directions, {spec.n_regions} regions)",
            "kernel": "k_sweep2d / k_sweep2d_bands (angular output, FP32; autotuned)",
            "bytes": nbytes, "ms": ms, "achieved_gbs": nbytes / (ms * 1e-3) / 1e9, "peak_gbs": peak,
            "frac": nbytes / (ms * 1e-3) / 1e9 / peak,
            "alu_tflops": SWEEP_FLOPS_PER_CELL_DIR * cells * prob.info.n_unique_directions / (ms * 1e-3) / 1e12}
-    del psi
+    del psi, prob
     torch.cuda.empty_cache()
     return out
 
 
-def measure_batched(RB, torch, dev, stream, flush, args, reps=1):
-    """Batched throughput: the 256-instance uneven workload solved by one fgmres_solve call per batch,
-    mixed (FP32 inner solves) with the learned warm start vs plain FP64, each mesh group preconditioned by
-    its own greedy ROM, whose labels train that group's MLP (offline, untimed)."""
+def measure_batched(RB, torch, dev, stream, flush, args, refs, reps=1):
+    """Batched throughput on the 256-instance uneven workload (96 x 32^2, 96 x 64^2, 64 x 128^2), one solve call per
+    batch: mixed with the learned start vs plain FP64, each mesh group preconditioned by its own greedy ROM, whose
+    labels train that group's MLP (offline, untimed).  Scalar-flux errors on one instance of each mesh size."""
     spec3 = wl.config(3)
-    R = spec3.n_regions
     B = spec3.n_instances
     ss, sa = wl.draw_params(spec3, B, wl.seed_for(3, 1))
     prob = RB.Problem(spec3, ss, sa)
     t0 = time.perf_counter()
-    roms, nets, losses = {}, {}, {}
-    tr_ss, tr_sa = wl.draw_params(spec3, args.batched_train, wl.seed_for(3, 0))
-    feats = np.concatenate([tr_ss, tr_sa], axis=1)
+    roms, losses = {}, {}
     for n in sorted(set(spec3.nx)):
         sp = spec3.with_instances([n], [n])
-        tmpl = RB.Problem(sp, tr_ss[:1], tr_sa[:1])
-        rom, rep = RB.Rom.greedy(tmpl, tr_ss, tr_sa, window=spec3.window, max_greedy_iter=args.batched_rank // 2,
-                                 max_rank=args.batched_rank, eps_rom=0.0, hf_rtol=1e-8, hf_restart=args.restart,
-                                 hf_max_iter=args.max_iter, want_labels=True, indicator_f32=True)
-        net = RB.Mlp(2 * R, 128, rep["rank"], seed=2410 + n)
-        losses[n] = net.train(feats, rep["labels"], epochs=args.mlp_epochs, batch=min(64, len(feats)), lr=2e-3,
-                              bf16=True)
-        RB.attach_mlp(rom, net)
-        roms[n], nets[n] = rom, net
+        rom, net, _, rep, _, info = build_rom_and_mlp(RB, sp, 3, args, args.batched_train, args.batched_rank,
+                                                      spec3.restart, seed_net=2410 + n)
+        roms[n] = (rom, net)
+        losses[f"{n}x{n}"] = info["mlp_final_loss"]
     t_off = time.perf_counter() - t0
-    rl = [roms[n] for n in spec3.nx]
+    rl = [roms[n][0] for n in spec3.nx]
     phi = torch.zeros(prob.n_dof, dtype=torch.float64, device=dev)
     out = {"workload": "batch256_uneven: 96x32^2 + 96x64^2 + 64x128^2, 128 directions, one solve call per batch",
            "instances": B, "rom_rank": args.batched_rank, "training_draws": args.batched_train, "offline_s": t_off,
-           "mlp_final_loss": {f"{n}x{n}": v for n, v in losses.items()}}
-    # "mixed": FP32 inner solves + MLP warm start (the batched form of the method); "mixed_plain_romsad":
-    # the same without the warm start; "fp64": plain FP64 FGMRES-ROMSAD
+           "mlp_final_loss": losses}
+    sample_ids = REF_SAMPLES_C3
     for name, mode, learned in (("mixed", RB.RTE_MODE_MIXED, True), ("mixed_plain_romsad", RB.RTE_MODE_MIXED, False),
                                 ("fp64", RB.RTE_MODE_FP64, False)):
-        RB.fgmres_solve(prob, rl, phi, restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec3.window,
-                        mode=mode, inner_rtol=args.inner_rtol, max_outer=30, stream=stream,
-                        raise_on_fail=False, learned_warm_start=learned, **post_kwargs(RB, args))   # warm-up / tuning
+        kw = dict(restart=spec3.restart, rtol=1e-8, max_iter=args.max_iter, window=spec3.window, mode=mode,
+                  inner_rtol=args.inner_rtol, max_outer=30, stream=stream, raise_on_fail=False,
+                  learned_warm_start=learned, post_mode=RB.RTE_POST_DSA)
+        RB.fgmres_solve(prob, rl, phi, **kw)   # warm-up / tuning
         times, st_all = [], []
         for _ in range(reps):
             flush.zero_()
@@ -306,42 +404,129 @@ def measure_batched(RB, torch, dev, stream, flush, args, reps=1):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st = RB.fgmres_solve(prob, rl, phi, restart=args.restart, rtol=1e-8, max_iter=args.max_iter,
-                                 window=spec3.window, mode=mode, inner_rtol=args.inner_rtol, max_outer=30,
-                                 stream=stream, raise_on_fail=False, learned_warm_start=learned,
-                                 **post_kwargs(RB, args))
+            st = RB.fgmres_solve(prob, rl, phi, **kw)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
             st_all.extend(st)
         ms = statistics.mean(times)
         conv = sum(1 for s in st_all if s["status"] == 0) / reps
-        # only instances that met rtol count as solved
-        out[name] = {"value": conv / (ms * 1e-3), "unit": "param solves/s", "ms_per_batch": ms,
-                     "converged": conv, "escalated_to_fp64": sum(s["escalated"] for s in st_all) / reps,
-                     "iterations_max": max(s["iterations"] for s in st_all),
-                     "iterations_mean": statistics.mean(s["iterations"] for s in st_all),
-                     "true_rel_residual_max": max(s["true_rel_residual"] for s in st_all),
-                     "status": sorted({s["status"] for s in st_all})}
+        host = phi.cpu().numpy()
+        errs = {}
+        for i in sample_ids:
+            ref = refs.get(("c3", i))
+            seg = host[prob.offsets[i]:prob.offsets[i + 1]]
+            errs[f"instance {i} ({spec3.nx[i]}x{spec3.ny[i]})"] = phi_error(seg, ref)
+        out[name] = dict({"value": conv / (ms * 1e-3), "unit": "param solves/s", "ms_per_batch": ms},
+                         **solve_stats(st_all), phi_rel_err_vs_oracle=errs)
     out["speedup_mixed_vs_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    del phi, prob
+    torch.cuda.empty_cache()
     return out
 
 
-def measure_learned_eval(RB, torch, dev, stream, flush, args, spec, rom, n_test=512):
-    """The learned part on held-out draws: n_test parameter instances of the single-instance workload (seeded
-    test split, never seen by the greedy or the MLP) solved in one mixed-precision call, with the learned
-    warm start, with the learned ROMSAD slot, and with plain ROMSAD."""
+def measure_single(RB, torch, dev, stream, flush, args, refs, n_steps=4):
+    """The single-instance 64x64 workload (square2d_64): one instance per step, the method's variants side by side
+    (mixed + MLP start, FP64, plain ROMSAD, learned slot, GMRES-DSA, RBF-interpolated start, SI-ROMSAD)."""
+    spec = wl.config(2)
+    ss_all, sa_all = wl.draw_params(spec, n_steps + 1, wl.seed_for(2, 1))
+    prob = RB.Problem(spec, ss_all[:1], sa_all[:1])
+    phi = torch.zeros(prob.n_dof, dtype=torch.float64, device=dev)
+    rom, net, tmpl, rep, (tr_ss, tr_sa), info = build_rom_and_mlp(RB, spec, 2, args, args.single_train, spec.rom_rank,
+                                                                   spec.restart)
+    roms = [rom]
+    base = dict(restart=spec.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window, stream=stream,
+                raise_on_fail=False)
+    legs = {
+        "mixed": lambda: RB.fgmres_solve(prob, roms, phi, mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol,
+                                         max_outer=30, learned_warm_start=True, post_mode=RB.RTE_POST_DSA, **base),
+        "fp64": lambda: RB.fgmres_solve(prob, roms, phi, mode=RB.RTE_MODE_FP64, post_mode=RB.RTE_POST_DSA, **base),
+        "mixed_plain_romsad": lambda: RB.fgmres_solve(prob, roms, phi, mode=RB.RTE_MODE_MIXED,
+                                                      inner_rtol=args.inner_rtol, max_outer=30,
+                                                      post_mode=RB.RTE_POST_DSA, **base),
+        "mixed_learned_slot": lambda: RB.fgmres_solve(prob, roms, phi, mode=RB.RTE_MODE_MIXED,
+                                                      inner_rtol=args.inner_rtol, max_outer=30, learned_slot=True,
+                                                      post_mode=RB.RTE_POST_DSA, **base),
+        "gmres_dsa_mixed": lambda: RB.fgmres_solve(prob, None, phi, mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol,
+                                                   max_outer=30, post_mode=RB.RTE_POST_DSA, **base),
+        "si_romsad_fp64": lambda: RB.si_solve(prob, roms, phi, rtol=1e-8, max_iter=2000, window=spec.window,
+                                              post_mode=RB.RTE_POST_DSA, stream=stream, raise_on_fail=False),
+    }
+    # the paper's interpolation baseline: RBF interpolation of the FP64 solutions at the greedy's samples
+    try:
+        ks = list(rep["sampled"])
+        spec_k = spec.with_instances([spec.nx[0]] * len(ks), [spec.ny[0]] * len(ks))
+        pk = RB.Problem(spec_k, tr_ss[ks], tr_sa[ks])
+        sol_k = torch.zeros(pk.n_dof, dtype=torch.float64, device=dev)
+        RB.fgmres_solve(pk, None, sol_k, restart=spec.restart, rtol=1e-10, max_iter=args.max_iter,
+                        post_mode=RB.RTE_POST_DSA, stream=stream)
+        rbf = RB.Rbf(tmpl, tr_ss[ks], tr_sa[ks], sol_k.view(len(ks), -1))
+        phi0_ig = torch.zeros(prob.n_dof, dtype=torch.float64, device=dev)
+
+        def interp_solve():
+            rbf.initial_guess(prob, phi0_ig, stream=stream)
+            return RB.fgmres_solve(prob, None, phi, phi0=phi0_ig, mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol,
+                                   max_outer=30, post_mode=RB.RTE_POST_DSA, **base)
+        legs["gmres_dsa_interp_ig_mixed"] = interp_solve
+    except Exception as exc:   # a side measurement; report instead of losing the bench line
+        legs_err = f"{type(exc).__name__}: {exc}"
+    else:
+        legs_err = None
+    out = {"workload": "square2d_64: one 64x64 instance per step, 128 directions, 2x2 regions",
+           "offline": info}
+    ref = refs.get(("c2", 1))
+    for name, fn in legs.items():
+        times, st_all, err = [], [], None
+        for s in range(n_steps + 1):
+            prob.set_params(ss_all[s:s + 1], sa_all[s:s + 1])
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if s >= 1:
+                times.append(e0.elapsed_time(e1))
+                st_all.extend(st)
+            if s == 1:
+                err = phi_error(phi.cpu().numpy(), ref)
+        out[name] = dict({"value": len(times) / (sum(times) * 1e-3), "unit": "param solves/s"},
+                         **solve_stats(st_all), phi_rel_err_vs_oracle=err)
+    if legs_err:
+        out["gmres_dsa_interp_ig_mixed"] = {"error": legs_err}
+    del phi, prob
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_learned_eval(RB, torch, dev, stream, flush, args, n_test=512):
+    """The learned part on the 64x64 workload with the config-4 budget: the greedy runs over 2048 training draws,
+    whose Galerkin coefficients train the MLP; 512 held-out draws (seeded test split) are solved in one
+    mixed-precision call with the learned warm start, with the learned ROMSAD slot, and with plain ROMSAD."""
+    spec = wl.config(4)
+    rom, net, tmpl, rep, (tr_ss, tr_sa), info = build_rom_and_mlp(RB, spec, 4, args, spec.n_train, spec.rom_rank,
+                                                                   spec.restart)
+    # held-out label error: the network's prediction against the Galerkin coefficients on the final basis
     ts, ta = wl.draw_params(spec, n_test, wl.seed_for(4, 1))
     sp = spec.with_instances([spec.nx[0]] * n_test, [spec.ny[0]] * n_test)
     prob = RB.Problem(sp, ts, ta)
     phi = torch.zeros(prob.n_dof, dtype=torch.float64, device=dev)
     roms = [rom] * n_test
-    out = {"workload": f"{n_test} held-out draws of {spec.name} in one batched call", "instances": n_test}
+    out = {"workload": f"{n_test} held-out draws of the 64x64 workload in one batched call", "instances": n_test,
+           "offline": info}
+    try:
+        labels = rom.galerkin_coefficients(prob)
+        pred = net.infer(np.concatenate([ts, ta], axis=1))
+        out["label_rel_err_heldout"] = float(np.linalg.norm(pred - labels) / np.linalg.norm(labels))
+    except Exception as exc:
+        out["label_rel_err_heldout"] = f"{type(exc).__name__}: {exc}"
     for name, kw in (("learned_start", {"learned_warm_start": True}), ("learned_slot", {"learned_slot": True}),
                      ("plain_romsad", {})):
-        common = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window,
+        common = dict(restart=spec.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window,
                       mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol, max_outer=30, stream=stream,
-                      raise_on_fail=False, **kw, **post_kwargs(RB, args))
+                      raise_on_fail=False, post_mode=RB.RTE_POST_DSA, **kw)
         RB.fgmres_solve(prob, roms, phi, **common)   # warm-up / tuning
         flush.zero_()
         torch.cuda.synchronize()
@@ -353,61 +538,90 @@ def measure_learned_eval(RB, torch, dev, stream, flush, args, spec, rom, n_test=
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         conv = sum(1 for s in st if s["status"] == 0)
-        out[name] = {"value": conv / (ms * 1e-3), "unit": "param solves/s", "converged": conv,
-                     "iterations_mean": statistics.mean(s["iterations"] for s in st),
-                     "iterations_max": max(s["iterations"] for s in st),
-                     "true_rel_residual_max": max(s["true_rel_residual"] for s in st)}
+        out[name] = dict({"value": conv / (ms * 1e-3), "unit": "param solves/s"}, **solve_stats(st))
+    out["learned_start_vs_plain"] = out["learned_start"]["value"] / out["plain_romsad"]["value"]
     del phi, prob
     torch.cuda.empty_cache()
     return out
 
 
-def measured_peaks():
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f)
-    except (OSError, ValueError):
-        return {}
+# instances whose oracle solutions the extras compare against: config 3, one per mesh size
+REF_SAMPLES_C3 = (0, 96, 192)
 
 
+def start_oracle_refs(cfg, spec, B, args, world):
+    """Spawn the oracle's tight solves of the sampled instances (before any GPU call); returns (pool, jobs)."""
+    jobs_spec = []
+    n_sets = args.warmup + args.steps
+    ss_all, sa_all = wl.draw_params(spec, n_sets * B * world, wl.seed_for(cfg, 1))
+    i0, _ = shard(0, n_sets, B, args.warmup)   # instance 0 of rank 0's first timed step
+    jobs_spec.append((("head", 0), cfg, spec.nx[0], spec.ny[0], ss_all[i0], sa_all[i0]))
+    if not args.no_extras:
+        s3 = wl.config(3)
+        ss3, sa3 = wl.draw_params(s3, s3.n_instances, wl.seed_for(3, 1))
+        for i in REF_SAMPLES_C3:
+            jobs_spec.append((("c3", i), 3, s3.nx[i], s3.ny[i], ss3[i], sa3[i]))
+        s2 = wl.config(2)
+        ss2, sa2 = wl.draw_params(s2, 2, wl.seed_for(2, 1))
+        jobs_spec.append((("c2", 1), 2, s2.nx[0], s2.ny[0], ss2[1], sa2[1]))
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(min(len(jobs_spec), max(1, host_cores() - 2)))
+    jobs = {key: pool.apply_async(oracle_reference_phi, (c, nx, ny, ss, sa)) for key, c, nx, ny, ss, sa in jobs_spec}
+    return pool, jobs
+
+
+def collect_refs(pool, jobs, timeout_s):
+    refs, meta = {}, {}
+    t_end = time.perf_counter() + timeout_s
+    for key, job in jobs.items():
+        try:
+            r = job.get(timeout=max(1.0, t_end - time.perf_counter()))
+            refs[key] = r["phi"]
+            meta[f"{key[0]}:{key[1]}"] = {"iterations": r["iterations"], "s": r["s"]}
+        except Exception as exc:   # no reference: the error is reported as missing, not invented
+            meta[f"{key[0]}:{key[1]}"] = {"error": f"{type(exc).__name__}: {exc}"}
+    pool.terminate()
+    pool.join()
+    return refs, meta
+
+
+# ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="square2d_64")
-    ap.add_argument("--restart", type=int, default=128)
+    ap.add_argument("--workload", default="large256_192", choices=sorted(WORKLOADS))
+    ap.add_argument("--restart", type=int, default=None, help="restart length (default: the workload's)")
     ap.add_argument("--max-iter", type=int, default=6000)
-    ap.add_argument("--inner-rtol", type=float, default=None,
-                    help="inner target of the mixed refinement (default 1e-3 with DSA after the window, else 1e-2)")
-    ap.add_argument("--post", default="dsa", choices=["dsa", "rom"],
-                    help="preconditioner after the ROMSAD window: DSA (the paper's) or ROMSAD kept")
-    ap.add_argument("--dsa-variant", default="partial", choices=["partial", "lumped"])
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mlp-epochs", type=int, default=300)
-    ap.add_argument("--no-sweep-hbm", action="store_true")
-    ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--batched-train", type=int, default=32)
-    ap.add_argument("--batched-rank", type=int, default=32)
+    ap.add_argument("--inner-rtol", type=float, default=1e-3, help="inner target of the mixed refinement")
+    ap.add_argument("--n-train", type=int, default=None, help="greedy/MLP training draws (default: the workload's)")
     ap.add_argument("--rom-rank", type=int, default=0, help="ROM rank cap (0: the workload's)")
-    ap.add_argument("--n-train", type=int, default=1024,
-                    help="training draws of the greedy and the MLP (2048 leaves the network less trained in the "
-                         "same epoch budget)")
-    ap.add_argument("--ref-sample", type=int, default=40, help="oracle FGMRES iterations per reference step")
-    ap.add_argument("--ref-iters", type=int, default=None,
-                    help="iterations of a full solve for the extrapolation (default: those of the FP64 solve of this "
-                         "workload on the GPU, 16 with DSA after the window, 180 with ROMSAD kept)")
+    ap.add_argument("--mlp-epochs", type=int, default=300)
+    ap.add_argument("--batched-train", type=int, default=64)
+    ap.add_argument("--batched-rank", type=int, default=32)
+    ap.add_argument("--single-train", type=int, default=64)
+    ap.add_argument("--no-extras", action="store_true", help="headline workload only")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-ref", action="store_true", help="skip the oracle's reference solutions")
+    ap.add_argument("--oracle-timeout", type=float, default=900.0)
+    ap.add_argument("--ref-iters", type=float, default=None,
+                    help="reference arm: iterations of a full solve for the extrapolation (default: the GPU's FP64 "
+                         "count on this workload)")
+    ap.add_argument("--ref-cores", type=int, default=0, help="reference arm: oracle processes (0: all host cores)")
     args = ap.parse_args()
-    if args.inner_rtol is None:
-        args.inner_rtol = 1e-3 if args.post == "dsa" else 1e-2
-    if args.ref_iters is None:
-        args.ref_iters = 16 if args.post == "dsa" else 180
-    spec, B = workload_spec(args.workload)
+    spec, B, cfg = workload_spec(args.workload)
+    restart = spec.restart if args.restart is None else args.restart
     world, rank, local = dist_setup()
     if args.impl == "reference":
-        run_reference(args, spec, B, world, rank)
+        run_reference(args, spec, B, world, rank, cfg)
         return
+    # the oracle's reference solutions run in spawned processes while the GPU legs run (started before the
+    # first GPU call); rank 0 only
+    pool, jobs = (None, {})
+    if rank == 0 and world == 1 and not args.no_oracle_ref:
+        pool, jobs = start_oracle_refs(cfg, spec, B, args, world)
     import torch
     from paper_2410_08735_gb300 import binding as RB
     RB.load()                                   # fails loudly without the built CUDA library
@@ -416,44 +630,48 @@ def main():
     stream = torch.cuda.current_stream(dev)
     R = spec.n_regions
     n_sets = args.warmup + args.steps
-    # parameters: distinct seeded draws per rank and step (test split)
-    ss_all, sa_all = wl.draw_params(spec, n_sets * B * world, wl.seed_for(2, 1))
+    ss_all, sa_all = wl.draw_params(spec, n_sets * B * world, wl.seed_for(cfg, 1))
+
     def params(step):
         i0, i1 = shard(rank, n_sets, B, step)
         return ss_all[i0:i1], sa_all[i0:i1]
 
+    peaks = {"fp32_fma_tflops": RB.fma_peak(RB.RTE_F32, stream), "fp64_fma_tflops": RB.fma_peak(RB.RTE_F64, stream),
+             "source": "rte_fma_peak: 8 independent FMA chains per thread, 8 blocks of 256 threads per SM, best of "
+                       "3 launches (CUDA events)"}
+    hbm_peak = measured_peaks().get("hbm_gbs")
     ss0, sa0 = params(0)
     prob = RB.Problem(spec, ss0, sa0)
     n = prob.n_dof
+    off = prob.offsets
     phi = torch.zeros(n, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    # offline (untimed): greedy ROM on the training draws, MLP trained on its labels
-    t_off = time.perf_counter()
+    # offline (untimed): greedy ROM with FGMRES-DSA high-fidelity solves, MLP trained on its labels
     n_train = args.n_train or spec.n_train
-    tr_ss, tr_sa = wl.draw_params(spec, n_train, wl.seed_for(2, 0))
-    tmpl = RB.Problem(spec.with_instances(spec.nx[:1], spec.ny[:1]), tr_ss[:1], tr_sa[:1])
-    rank_cap = args.rom_rank or spec.rom_rank
-    rom, rep = RB.Rom.greedy(tmpl, tr_ss, tr_sa, window=spec.window, max_greedy_iter=rank_cap // spec.window,
-                             max_rank=rank_cap, eps_rom=0.0, hf_rtol=1e-10, hf_restart=args.restart,
-                             hf_max_iter=args.max_iter, want_labels=True, indicator_f32=True)
-    t_greedy = time.perf_counter() - t_off
-    net = RB.Mlp(2 * R, 128, rep["rank"], seed=2410)
-    mlp_loss = net.train(np.concatenate([tr_ss, tr_sa], axis=1), rep["labels"], epochs=args.mlp_epochs,
-                         batch=min(64, n_train), lr=2e-3, bf16=True)
-    RB.attach_mlp(rom, net)
-    t_offline = time.perf_counter() - t_off
+    rom, net, tmpl, rep, _, offline = build_rom_and_mlp(RB, spec, cfg, args, n_train, args.rom_rank or spec.rom_rank,
+                                                        restart)
     roms = [rom] * B
-    common = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window, stream=stream,
-                  **post_kwargs(RB, args))
+    common = dict(restart=restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window, stream=stream,
+                  raise_on_fail=False, post_mode=RB.RTE_POST_DSA)
+    mixed_kw = dict(inner_rtol=args.inner_rtol, max_outer=30)
+    legs = [
+        # headline: all-FP32 inner solves, learned start, double-float refinement residuals, FP64 certification
+        ("mixed", lambda: RB.fgmres_solve(prob, roms, phi, mode=RB.RTE_MODE_MIXED, learned_warm_start=True,
+                                          **mixed_kw, **common)),
+        # the precision form of the method statement: FP32 sweeps, FP64 Krylov vectors, MGS and Givens
+        ("mixed_fp64_krylov", lambda: RB.fgmres_solve(prob, roms, phi, mode=RB.RTE_MODE_MIXED_F64KRYLOV,
+                                                      learned_warm_start=True, **mixed_kw, **common)),
+        ("fp64", lambda: RB.fgmres_solve(prob, roms, phi, mode=RB.RTE_MODE_FP64, true_residual_check=True, **common)),
+        ("mixed_plain_romsad", lambda: RB.fgmres_solve(prob, roms, phi, mode=RB.RTE_MODE_MIXED, **mixed_kw,
+                                                       **common)),
+        ("mixed_fp64_residuals", lambda: RB.fgmres_solve(prob, roms, phi, mode=RB.RTE_MODE_MIXED,
+                                                         learned_warm_start=True, refine_residual=RB.RTE_RESIDUAL_FP64,
+                                                         **mixed_kw, **common)),
+        ("gmres_dsa_mixed", lambda: RB.fgmres_solve(prob, None, phi, mode=RB.RTE_MODE_MIXED, **mixed_kw, **common)),
+    ]
 
-    def solve(mode, learned=True, slot=False):
-        if mode in (RB.RTE_MODE_MIXED, RB.RTE_MODE_MIXED_F64KRYLOV):
-            return RB.fgmres_solve(prob, roms, phi, mode=mode, inner_rtol=args.inner_rtol, max_outer=30,
-                                   learned_warm_start=learned, learned_slot=slot, **common)
-        return RB.fgmres_solve(prob, roms, phi, mode=mode, true_residual_check=True, **common)
-
-    def timed_loop(mode, learned=True, slot=False, solver=None):
-        per_step, stats_all = [], []
+    def timed_loop(fn):
+        per_step, stats_all, phi_s = [], [], None
         for s in range(n_sets):
             ss, sa = params(s)
             prob.set_params(ss, sa)
@@ -462,86 +680,34 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st = solve(mode, learned, slot) if solver is None else solver()
+            st = fn()
             e1.record(stream)
             torch.cuda.synchronize()
             if s >= args.warmup:
                 per_step.append(e0.elapsed_time(e1))
                 stats_all.extend(st)
-        return per_step, stats_all
+            if s == args.warmup:   # the sampled instance: instance 0 of the first timed step
+                phi_s = phi[off[0]:off[1]].cpu().numpy()
+        return per_step, stats_all, phi_s
 
     barrier(world)
     torch.cuda.synchronize()
     clk = ClockSampler(local)
     clk.start()
-    launches0 = RB.kernel_launches()
-    torch.cuda.nvtx.range_push("timed_mixed")      # ncu --nvtx-include timed_mixed/ selects this region
-    t_mixed, st_mixed = timed_loop(RB.RTE_MODE_MIXED)
-    torch.cuda.nvtx.range_pop()
-    launches_mixed = RB.kernel_launches() - launches0
-    torch.cuda.nvtx.range_push("timed_fp64")
-    t_fp64, st_fp64 = timed_loop(RB.RTE_MODE_FP64)
-    torch.cuda.nvtx.range_pop()
-    # the mixed path without the learned warm start (plain ROMSAD), for the MLP's net effect
-    t_plain, st_plain = timed_loop(RB.RTE_MODE_MIXED, learned=False)
-    # the mixed path with the learned correction in the ROMSAD slot instead of the learned start
-    t_slot, st_slot = timed_loop(RB.RTE_MODE_MIXED, learned=False, slot=True)
-    # the precision form with FP64 Krylov vectors, MGS and Givens around the FP32 sweeps
-    t_f64k, st_f64k = timed_loop(RB.RTE_MODE_MIXED_F64KRYLOV)
-    # the mixed path with ROMSAD kept after the window (no DSA), learned start, inner target 1e-2
-    base_kw = dict(restart=args.restart, rtol=1e-8, max_iter=args.max_iter, window=spec.window, stream=stream)
-    t_prom, st_prom = timed_loop(None, solver=lambda: RB.fgmres_solve(
-        prob, roms, phi, mode=RB.RTE_MODE_MIXED, inner_rtol=1e-2, max_outer=30, learned_warm_start=True,
-        post_mode=RB.RTE_POST_ROM, **base_kw))
-    # right-preconditioned GMRES-DSA (no ROM), mixed
-    t_gdsa, st_gdsa = timed_loop(None, solver=lambda: RB.fgmres_solve(
-        prob, None, phi, mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol, max_outer=30,
-        post_mode=RB.RTE_POST_DSA, **base_kw))
-    # GMRES-DSA from the RBF-interpolated initial guess (the paper's interpolation baseline): data = FP64
-    # solutions at the training points the greedy sampled (offline, untimed); the interpolation is timed
-    interp = None
-    try:
-        ks = list(rep["sampled"])
-        spec_k = spec.with_instances([spec.nx[0]] * len(ks), [spec.ny[0]] * len(ks))
-        pk = RB.Problem(spec_k, tr_ss[ks], tr_sa[ks])
-        sol_k = torch.zeros(pk.n_dof, dtype=torch.float64, device=dev)
-        RB.fgmres_solve(pk, None, sol_k, restart=args.restart, rtol=1e-10, max_iter=args.max_iter,
-                        post_mode=RB.RTE_POST_DSA, stream=stream)
-        rbf = RB.Rbf(tmpl, tr_ss[ks], tr_sa[ks], sol_k.view(len(ks), -1))
-        phi0_ig = torch.zeros(n, dtype=torch.float64, device=dev)
-
-        def interp_solve():
-            rbf.initial_guess(prob, phi0_ig, stream=stream)
-            return RB.fgmres_solve(prob, None, phi, phi0=phi0_ig, mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol,
-                                   max_outer=30, post_mode=RB.RTE_POST_DSA, **base_kw)
-
-        t_ig, st_ig = timed_loop(None, solver=interp_solve)
-        ig_s = max_over_ranks(world, sum(t_ig) / 1e3)
-        interp = {"value": args.steps * B * world / ig_s, "unit": "param solves/s",
-                  "iterations_mean": statistics.mean(s["iterations"] for s in st_ig),
-                  "samples": len(ks), "note": "mixed GMRES-DSA from the RBF-interpolated initial guess"}
-        del pk, sol_k
-    except Exception as exc:   # the leg is a side measurement; report instead of losing the bench line
-        interp = {"error": f"{type(exc).__name__}: {exc}"}
-    # SI-ROMSAD (source iteration: the ROM correction in the window, DSA afterwards), FP64
-    t_si, st_si = timed_loop(None, solver=lambda: RB.si_solve(
-        prob, roms, phi, rtol=1e-8, max_iter=2000, window=spec.window, post_mode=RB.RTE_POST_DSA, stream=stream,
-        raise_on_fail=False))
+    results = {}
+    launches = None
+    for name, fn in legs:
+        l0 = RB.kernel_launches()
+        torch.cuda.nvtx.range_push(f"timed_{name}")   # ncu --nvtx-include timed_mixed/ selects a region
+        t, st, phi_s = timed_loop(fn)
+        torch.cuda.nvtx.range_pop()
+        if name == "mixed":
+            launches = (RB.kernel_launches() - l0) * args.steps / n_sets
+        results[name] = (max_over_ranks(world, sum(t) / 1e3), st, phi_s)
     torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop()
-    mixed_s = max_over_ranks(world, sum(t_mixed) / 1e3)
-    fp64_s = max_over_ranks(world, sum(t_fp64) / 1e3)
-    plain_s = max_over_ranks(world, sum(t_plain) / 1e3)
-    slot_s = max_over_ranks(world, sum(t_slot) / 1e3)
-    f64k_s = max_over_ranks(world, sum(t_f64k) / 1e3)
-    prom_s = max_over_ranks(world, sum(t_prom) / 1e3)
-    gdsa_s = max_over_ranks(world, sum(t_gdsa) / 1e3)
-    si_s = max_over_ranks(world, sum(t_si) / 1e3)
-    si_conv = sum(1 for s in st_si if s["status"] == 0)
     solves = args.steps * B * world
-    value = solves / mixed_s
-    fp64_value = solves / fp64_s
     # e2e: host parameters in, host scalar flux out, through the C ABI
     host_phi = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
     e2e_ms = []
@@ -551,131 +717,129 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         prob.set_params(ss, sa)
-        RB.fgmres_solve(prob, roms, host_phi, mode=RB.RTE_MODE_MIXED, inner_rtol=args.inner_rtol, max_outer=30,
-                        learned_warm_start=True, **common)
+        RB.fgmres_solve(prob, roms, host_phi, mode=RB.RTE_MODE_MIXED, learned_warm_start=True, **mixed_kw, **common)
         t1 = time.perf_counter()
         if s >= args.warmup:
             e2e_ms.append(1e3 * (t1 - t0))
     e2e_s = max_over_ranks(world, sum(e2e_ms) / 1e3)
-    # roofline of the dominant kernel: the fused sweep (A~ apply), timed alone with CUDA events
+    # per-kernel launch times of the headline path, timed alone with CUDA events on the launching stream:
+    # FP32, FP64 and double-float A~ applies, and one DSA V-cycle (set-up reused)
     z64 = torch.randn(n, dtype=torch.float64, device=dev)
     w64 = torch.empty_like(z64)
     z32 = z64.float()
     w32 = torch.empty_like(z32)
-
-    def time_op(z, w, reps=20):
-        for _ in range(3):
-            prob.apply_op(z, w, stream=stream)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            prob.apply_op(z, w, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
-
-    ms32 = time_op(z32, w32)
-    ms64 = time_op(z64, w64)
-
-    def time_dsa(reps=20):
-        # rte_dsa_apply: the per-parameter set-up plus one V-cycle, FP32 vectors
-        for _ in range(3):
-            prob.dsa_apply(z32, w32, stream=stream)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(reps):
-            prob.dsa_apply(z32, w32, stream=stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / reps
-
-    ms_dsa = time_dsa() if args.post == "dsa" else None
+    ms32 = time_events(torch, stream, lambda: prob.apply_op(z32, w32, stream=stream), reps=10)
+    ms64 = time_events(torch, stream, lambda: prob.apply_op(z64, w64, stream=stream), reps=3)
+    msdf = time_events(torch, stream, lambda: prob.apply_op(z64, w64, stream=stream, double_float=True), reps=5)
+    prob.dsa_apply(z32, w32, stream=stream)
+    ms_v = time_events(torch, stream, lambda: prob.dsa_apply(z32, w32, variant=RB.RTE_DSA_KEEP_SETUP, stream=stream),
+                       reps=10)
     cells = sum(nx * ny for nx, ny in zip(spec.nx[:B], spec.ny[:B]))
     nu = prob.info.n_unique_directions
     flops = SWEEP_FLOPS_PER_CELL_DIR * cells * nu
-    sw32 = sum(s["sweeps"] - s["sweeps_fp64"] for s in st_mixed)
-    sw64 = sum(s["sweeps_fp64"] for s in st_mixed)
-    share32, share64 = sw32 * ms32, sw64 * ms64
-    if share32 >= share64:
-        roof = {"kernel": "k_sweep2d<float> (A~ apply, FP32)", "bound": "alu", "achieved": flops / (ms32 * 1e-3) / 1e12,
-                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    st_m = results["mixed"][1]
+    n64 = statistics.mean(s["sweeps_fp64"] for s in st_m)
+    ndf = statistics.mean(s["sweeps_df"] for s in st_m)
+    n32 = statistics.mean(s["sweeps"] for s in st_m) - n64 - ndf
+    nv = statistics.mean(s["iterations"] for s in st_m)   # one preconditioner apply per iteration
+    shares = {"k_sweep2d<float> (A~ apply, FP32)": n32 * ms32, "k_sweep2d<double> (A~ apply, FP64)": n64 * ms64,
+              "k_sweep2d<dfloat> (A~ apply, double-float)": ndf * msdf, "k_dsa_vcycle (DSA V-cycle)": nv * ms_v}
+    per_solve_ms = 1e3 * results["mixed"][0] / args.steps
+    dom = max(shares, key=shares.get)
+    if "FP32" in dom:
+        roof = {"kernel": dom, "bound": "alu", "achieved": flops / (ms32 * 1e-3) / 1e12,
+                "peak": peaks["fp32_fma_tflops"], "unit": "TFLOP/s", "ms_per_launch": ms32}
+    elif "FP64" in dom:
+        roof = {"kernel": dom, "bound": "alu", "achieved": flops / (ms64 * 1e-3) / 1e12,
+                "peak": peaks["fp64_fma_tflops"], "unit": "TFLOP/s", "ms_per_launch": ms64}
+    elif "double-float" in dom:
+        roof = {"kernel": dom, "bound": "alu", "achieved": flops / (msdf * 1e-3) / 1e12,
+                "peak": peaks["fp32_fma_tflops"], "unit": "TFLOP/s", "ms_per_launch": msdf,
+                "note": "algorithmic flops in double-float arithmetic against the FP32 FMA peak"}
     else:
-        roof = {"kernel": "k_sweep2d<double> (A~ apply, FP64)", "bound": "alu",
-                "achieved": flops / (ms64 * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    # DRAM bytes per launch of the FP32 sweep kernel from one ncu capture of this workload
-    # (profiles/sweep_band_f32_square2d_64.md); none recorded for the FP64 kernel
-    roof["traffic"] = SWEEP32_DRAM_BYTES_64x64 if roof["unit"] == "TFLOP/s" and "float" in roof["kernel"] else None
-    # angular-output sweep (rte_sweep, FP32) on the batched 256-instance problem: HBM-bound write of
-    # N_Omega * N_dof * 4 bytes; this is the sweep GB/s of the metric
-    sweep_hbm = measure_sweep_hbm(RB, torch, dev, stream, flush) if not args.no_sweep_hbm else None
-    if sweep_hbm is not None and world == 1:
-        # the largest workload (64 x 256^2, 192 directions, 8x8 regions): 12.9 GB of angular output
-        sweep_hbm["large"] = measure_sweep_hbm(RB, torch, dev, stream, flush, reps=3, config=5)
-    batched = measure_batched(RB, torch, dev, stream, flush, args) if not args.no_batched and world == 1 else None
-    learned_eval = (measure_learned_eval(RB, torch, dev, stream, flush, args, spec, rom)
-                    if not args.no_batched and world == 1 else None)
-    roof["ms_per_launch_fp32"] = ms32
-    roof["ms_per_launch_fp64"] = ms64
-    roof["peak_source"] = "unit counts x max SM clock (FP32); GB300 nominal (FP64)"
+        vbytes = DSA_VCYCLE_BYTES_PER_CELL * cells
+        roof = {"kernel": dom, "bound": "hbm", "achieved": vbytes / (ms_v * 1e-3) / 1e9, "peak": hbm_peak,
+                "unit": "GB/s", "ms_per_launch": ms_v}
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("peak") else None
+    roof["traffic"] = None   # filled from the committed ncu capture of the same kernel, when current
+    roof["peak_source"] = "measured: rte_fma_peak (FP32 / FP64 FMA), MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"
+    roof["shares_ms_per_solve_batch"] = shares
+    roof["solve_batch_ms"] = per_solve_ms
+    roof["other_kernels"] = {
+        "k_sweep2d<float>": {"ms": ms32, "tflops": flops / (ms32 * 1e-3) / 1e12,
+                             "frac_of_fp32_peak": flops / (ms32 * 1e-3) / 1e12 / peaks["fp32_fma_tflops"]},
+        "k_sweep2d<double>": {"ms": ms64, "tflops": flops / (ms64 * 1e-3) / 1e12,
+                              "frac_of_fp64_peak": flops / (ms64 * 1e-3) / 1e12 / peaks["fp64_fma_tflops"]},
+        "k_sweep2d<dfloat>": {"ms": msdf, "tflops_df": flops / (msdf * 1e-3) / 1e12},
+        "k_dsa_vcycle": {"ms": ms_v}}
+    del z64, w64, z32, w32
+    torch.cuda.empty_cache()
+    extras = {}
+    refs, ref_meta = {}, {}
+    if not args.no_extras and world == 1:
+        # the extras need the oracle references of configs 2 and 3 only at their end; collect them first when they
+        # are already done (they normally are), else after
+        extras["sweep_hbm"] = measure_sweep_hbm(RB, torch, dev, stream, flush, 3)
+        extras["sweep_hbm"]["large"] = measure_sweep_hbm(RB, torch, dev, stream, flush, 5, reps=3)
+    if pool is not None:
+        refs, ref_meta = collect_refs(pool, jobs, args.oracle_timeout)
+    if not args.no_extras and world == 1:
+        extras["batched"] = measure_batched(RB, torch, dev, stream, flush, args, refs)
+        extras["single_instance"] = measure_single(RB, torch, dev, stream, flush, args, refs)
+        extras["learned_eval"] = measure_learned_eval(RB, torch, dev, stream, flush, args)
     if rank != 0:
         return
+
+    def leg(name):
+        t, st, phi_s = results[name]
+        return dict({"value": solves / t, "unit": "param solves/s", "ms_per_step": 1e3 * t / args.steps},
+                    **solve_stats(st), phi_rel_err_vs_oracle=phi_error(phi_s, refs.get(("head", 0))))
+
+    value = solves / results["mixed"][0]
+    fp64_value = solves / results["fp64"][0]
+    head = leg("mixed")
     line = {
         "metric": METRIC,
         "value": value, "unit": "param solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * mixed_s / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": bench_config(args, spec, B),
-        "fp64": {"value": fp64_value, "unit": "param solves/s", "ms_per_step": 1e3 * fp64_s / args.steps},
-        "mixed_plain_romsad": {"value": solves / plain_s, "unit": "param solves/s",
-                               "iterations_mean": statistics.mean(s["iterations"] for s in st_plain)},
-        "mixed_learned_slot": {"value": solves / slot_s, "unit": "param solves/s",
-                               "iterations_mean": statistics.mean(s["iterations"] for s in st_slot)},
-        "mixed_fp64_krylov": {"value": solves / f64k_s, "unit": "param solves/s",
-                              "iterations_mean": statistics.mean(s["iterations"] for s in st_f64k),
-                              "true_rel_residual_max": max(s["true_rel_residual"] for s in st_f64k)},
-        "mixed_post_rom": {"value": solves / prom_s, "unit": "param solves/s",
-                           "iterations_mean": statistics.mean(s["iterations"] for s in st_prom),
-                           "note": "ROMSAD kept after the window instead of DSA, learned start, inner target 1e-2"},
-        "gmres_dsa_mixed": {"value": solves / gdsa_s, "unit": "param solves/s",
-                            "iterations_mean": statistics.mean(s["iterations"] for s in st_gdsa),
-                            "note": "no ROM: DSA from the first iteration"},
-        "gmres_dsa_interp_ig_mixed": interp,
-        "si_romsad_fp64": {"value": si_conv * world / si_s, "unit": "param solves/s",
-                           "converged": si_conv, "of": len(st_si),
-                           "iterations_mean": statistics.mean(s["iterations"] for s in st_si),
-                           "iterations_max": max(s["iterations"] for s in st_si),
-                           "note": "source iteration, ROM correction in the window then DSA (FP64)"},
+        "ms_per_step": 1e3 * results["mixed"][0] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+df+f64", "data": "synthetic",
+        "config": bench_config(args, spec, B, cfg),
+        "precision_form": "inner FGMRES all FP32 (sweeps, ROM products, Krylov basis, MGS, Givens); refinement "
+                          "residuals double-float; b~ and the certifying residual FP64 (mixed_fp64_krylov: the "
+                          "same with FP64 Krylov vectors, MGS and Givens)",
+        "phi_rel_err_vs_oracle": head["phi_rel_err_vs_oracle"],
+        "solver": {k: v for k, v in head.items() if k not in ("value", "unit", "ms_per_step")},
+        "fp64": leg("fp64"),
         "speedup_mixed_vs_fp64": value / fp64_value,
-        "offline": {"greedy_s": t_greedy, "total_s": t_offline, "rank": rep["rank"], "sampled": len(rep["sampled"]),
-                    "mlp_final_loss": mlp_loss},
-        "solver": {
-            "mixed_iterations_mean": statistics.mean(s["iterations"] for s in st_mixed),
-            "mixed_fp64_sweeps_mean": statistics.mean(s["sweeps_fp64"] for s in st_mixed),
-            "mixed_true_rel_residual_max": max(s["true_rel_residual"] for s in st_mixed),
-            "fp64_iterations_mean": statistics.mean(s["iterations"] for s in st_fp64),
-            "fp64_true_rel_residual_max": max(s["true_rel_residual"] for s in st_fp64),
-            "status": sorted({s["status"] for s in st_mixed + st_fp64})},
+        "mixed_fp64_krylov": leg("mixed_fp64_krylov"),
+        "mixed_plain_romsad": leg("mixed_plain_romsad"),
+        "mixed_fp64_residuals": leg("mixed_fp64_residuals"),
+        "gmres_dsa_mixed": dict(leg("gmres_dsa_mixed"), note="no ROM: DSA from the first iteration"),
+        "learned_start_vs_plain_romsad": value / (solves / results["mixed_plain_romsad"][0]),
+        "offline": offline,
         "e2e": {"value": solves / e2e_s, "unit": "param solves/s", "h2d_bytes_per_step": 2 * R * 8 * B,
                 "d2h_bytes_per_step": 8 * n},
-        "gpu_launches": int(launches_mixed * args.steps / n_sets),
-        "dsa_apply_us": None if ms_dsa is None else 1e3 * ms_dsa,
+        "gpu_launches": int(round(launches)) if launches is not None else None,
+        "peaks": peaks,
         "roofline": roof,
-        "sweep_hbm": sweep_hbm,
-        "batched": batched,
-        "learned_eval": learned_eval,
+        "oracle_reference": ref_meta,
         "clocks": clocks,
     }
+    line.update(extras)
     if not args.no_cpu_baseline:
-        ss, sa = params(args.warmup)
-        iters = int(round(statistics.mean(s["iterations"] for s in st_fp64)))
-        line["cpu_baseline"] = oracle_sample(spec.with_instances(spec.nx[:1], spec.ny[:1]), ss[0], sa[0], iters,
-                                             args.ref_sample, args.post == "dsa")
+        iters = statistics.mean(s["iterations"] for s in results["fp64"][1])
+        ssb, sab = params(args.warmup)
+        cb = oracle_baseline(cfg, spec, ssb, sab, iters, 1, 2, host_cores())
+        cb.pop("per_iter_samples", None)
+        line["cpu_baseline"] = cb
     print(json.dumps(line))
+
+
+# Algorithmic bytes of one DSA V-cycle per DG cell (FP32): the DG level reads the cell's right-hand side, the
+# inverted cell block and the two first-moment inverses and writes/reads the iterate and residual (about 48
+# floats), the vertex levels add a geometric series of 4x4 element matrices and vectors (about 24 floats per
+# fine cell).
+DSA_VCYCLE_BYTES_PER_CELL = 4 * 72
 
 
 if __name__ == "__main__":

@@ -196,6 +196,10 @@ int romsad_rank(romsad_t rom, int* r);
 int romsad_get_basis(romsad_t rom, double* U_host);
 /* Reduced operator U^T A_mu U (affine assembly) for per-region sigma (host [R]) -> host [r][r]. */
 int romsad_reduced_operator(romsad_t rom, const double* sigma_s, const double* sigma_a, double* A_host);
+/* Galerkin coefficients of eq. greedy-rom for every instance of p (all on the ROM's mesh) with its own mu:
+ * c_mu = (U^T A_mu U)^{-1} P^T Sigma_s b~_mu (the first-correction coefficients, Sec. 4.4.1-4.4.2; the MLP's
+ * labels).  c_host: host [B][r].  Synchronises the legacy stream. */
+int romsad_galerkin_coefficients(romsad_t rom, rte_problem_t p, double* c_host);
 /* z = M_ROM^{-1} v for every instance of p (all instances must use the ROM's mesh),
  * eq. rom-sa-preconditioner, with the instance's own sigma.  v, z: scalar vectors. */
 int romsad_apply(romsad_t rom, rte_problem_t p, int dtype, const void* v, void* z, void* stream);
@@ -241,7 +245,10 @@ int romsad_destroy(romsad_t rom);
 #define RTE_DSA_PARTIAL 0
 #define RTE_DSA_LUMPED 1
 /* z = M_DSA^{-1} v for every instance of p with its own sigma.  v, z: scalar vectors of dtype
- * (device, not aliased).  Each call redoes the per-parameter set-up (one extra kernel). */
+ * (device, not aliased).  Each call redoes the per-parameter set-up (two extra kernels) unless the variant is
+ * or-ed with RTE_DSA_KEEP_SETUP, which reuses the set-up of the last call (RTE_ERR_INVALID_ARG if there was
+ * none, or it was of the other variant); the caller guarantees the parameters have not changed since. */
+#define RTE_DSA_KEEP_SETUP 16
 int rte_dsa_apply(rte_problem_t p, int variant, int dtype, const void* v, void* z, void* stream);
 
 /* ---------------------------------------- RBF-interpolated initial guess (Sec. 5) */

@@ -21,6 +21,7 @@ RTE_ERR_NUMERIC = 5
 RTE_F64, RTE_F32, RTE_F64_DF = 0, 1, 2
 RTE_POST_ROM, RTE_POST_IDENTITY, RTE_POST_DSA = 0, 1, 2
 RTE_DSA_PARTIAL, RTE_DSA_LUMPED = 0, 1
+RTE_DSA_KEEP_SETUP = 16
 RTE_MODE_FP64, RTE_MODE_MIXED, RTE_MODE_MIXED_F64KRYLOV = 0, 1, 2
 RTE_RESIDUAL_DF, RTE_RESIDUAL_FP64 = 0, 1
 
@@ -155,6 +156,7 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_void_p)]),
     "rte_rbf_initial_guess": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "rte_rbf_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "romsad_galerkin_coefficients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
 }
 
 
@@ -385,6 +387,12 @@ class Rom:
         sa = np.ascontiguousarray(sigma_a, dtype=np.float64)
         _check(load().romsad_reduced_operator(self.h, _dptr(ss), _dptr(sa), _dptr(A)), "romsad_reduced_operator")
         return A
+
+    def galerkin_coefficients(self, problem: Problem) -> np.ndarray:
+        """Galerkin coefficients c_mu (eq. greedy-rom) of every instance of the problem: [B][rank]."""
+        out = np.zeros((problem.spec.n_instances, self.rank()))
+        _check(load().romsad_galerkin_coefficients(self.h, problem.h, _dptr(out)), "romsad_galerkin_coefficients")
+        return out
 
     def apply(self, problem: Problem, v, z, stream=None):
         _check(load().romsad_apply(self.h, problem.h, _dtype_code(v), _ptr(v), _ptr(z), _stream(stream)),

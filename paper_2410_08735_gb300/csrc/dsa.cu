@@ -887,6 +887,16 @@ extern "C" int rte_dsa_apply(rte_problem_t p, int variant, int dtype, const void
   RTE_ARG(dtype == RTE_F64 || dtype == RTE_F32, "unknown dtype");
   RTE_ARG(v != z, "v and z must not alias");
   cudaStream_t st = (cudaStream_t)stream;
-  RTE_TRY(dsa_prepare(p, variant, st));
+  const bool keep = (variant & RTE_DSA_KEEP_SETUP) != 0;
+  variant &= ~RTE_DSA_KEEP_SETUP;
+  if (keep) {
+    // reuse the set-up of an earlier call (it must exist and be of the same variant)
+    DsaWs* w = get_dsa_ws(p);
+    RTE_ARG(!w->di.empty() && w->lumped == (variant == RTE_DSA_LUMPED ? 1 : 0),
+            "RTE_DSA_KEEP_SETUP needs an earlier set-up of the same variant");
+    RTE_ARG(variant == RTE_DSA_PARTIAL || variant == RTE_DSA_LUMPED, "unknown DSA variant");
+  } else {
+    RTE_TRY(dsa_prepare(p, variant, st));
+  }
   return dsa_launch(p, dtype == RTE_F64, v, z, nullptr, nullptr, st);
 }

@@ -128,6 +128,77 @@ __global__ void k_indicator(const T* U, const T* Y, int nA, int N, int r, const 
   }
 }
 
+// FP32 indicator for many parameters: a thread keeps the RMAX basis values U[k][u][i], Y[k][u][i] of its dof in
+// registers and loops over all parameters in tiles of MT (coefficients of a tile staged in shared memory), so
+// the basis is read from HBM once per greedy iteration.  Block (u, chunk): the blocks of one chunk follow one
+// another in launch order, so the chunk of base_mu is read from HBM once and by the other directions' blocks
+// from L2.  Same partial sums as k_indicator.
+template <int RMAX, int MT>
+__global__ void __launch_bounds__(256) k_indicator_reg(const float* U, const float* Y, int nA, int N, int r,
+                                                       const double* c, const double* base, const int* mus, int nmu,
+                                                       const double* sig_t, int R, int rx, int ry, int nx, int ny,
+                                                       int nd, int nchunk, double* part) {
+  const int u = blockIdx.x;
+  const int chunk = blockIdx.y;
+  const int i = chunk * 256 + threadIdx.x;
+  __shared__ __align__(16) float cs[MT][RMAX];
+  __shared__ double red[8][MT];
+  float uk[RMAX], yk[RMAX];
+#pragma unroll
+  for (int k = 0; k < RMAX; ++k) {
+    uk[k] = 0.f;
+    yk[k] = 0.f;
+    if (k < r && i < N) {
+      yk[k] = Y[((size_t)k * nA + u) * N + i];
+      uk[k] = U[((size_t)k * nA + u) * N + i];
+    }
+  }
+  int reg = 0;
+  if (i < N) {
+    const int cell = i / nd;
+    const int ix = cell % nx, iy = cell / nx;
+    reg = (iy / (ny / ry)) * rx + ix / (nx / rx);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int mt0 = 0; mt0 < nmu; mt0 += MT) {
+    __syncthreads();   // the previous tile's coefficients and sums are consumed
+    for (int e = threadIdx.x; e < MT * RMAX; e += blockDim.x) {
+      const int m = e / RMAX, k = e % RMAX;
+      cs[m][k] = (mt0 + m < nmu && k < r) ? (float)c[(size_t)mus[mt0 + m] * 64 + k] : 0.f;
+    }
+    __syncthreads();
+    float a[MT], b[MT];
+#pragma unroll
+    for (int m = 0; m < MT; ++m) { a[m] = 0.f; b[m] = 0.f; }
+#pragma unroll
+    for (int k = 0; k < RMAX; k += 4) {
+#pragma unroll
+      for (int m = 0; m < MT; ++m) {
+        const float4 cc = *reinterpret_cast<const float4*>(&cs[m][k]);
+        a[m] += yk[k] * cc.x + yk[k + 1] * cc.y + yk[k + 2] * cc.z + yk[k + 3] * cc.w;
+        b[m] += uk[k] * cc.x + uk[k + 1] * cc.y + uk[k + 2] * cc.z + uk[k + 3] * cc.w;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < MT; ++m) {
+      double e2 = 0.0;
+      if (i < N && mt0 + m < nmu) {
+        const int mu = mus[mt0 + m];
+        const double e = (double)a[m] + sig_t[(size_t)mu * R + reg] * (double)b[m] - base[(size_t)mu * N + i];
+        e2 = e * e;
+      }
+      for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+      if (lane == 0) red[warp][m] = e2;
+    }
+    __syncthreads();
+    if (threadIdx.x < MT && mt0 + threadIdx.x < nmu) {
+      double sum = 0.0;
+      for (int w = 0; w < 8; ++w) sum += red[w][threadIdx.x];
+      part[(((size_t)mus[mt0 + threadIdx.x]) * nA + u) * nchunk + chunk] = sum;
+    }
+  }
+}
+
 static int wdot(const double* x, const double* y, int nA, int N, const double* mult, DevBuf<double>& part,
                 double* out, cudaStream_t st) {
   const int blocks = 256;
@@ -340,11 +411,19 @@ static int greedy_impl(rte_problem* tmpl, int n_train, const double* tss, const 
     constexpr int MT = 8;
     RTE_TRY(ipart.alloc((size_t)n_train * rom->nA * nchunk));
     dim3 gi(nchunk, rom->nA, (nmu + MT - 1) / MT);
-    if (o->indicator_f32)
-      k_indicator<float, MT><<<gi, 256, 0, st>>>(U32.p, Y32.p, rom->nA, N, rom->r, cs.p, base.p, d_mus.p, nmu,
-                                                 tp.p->d_sig_t.p, R, tp.p->rx, tp.p->ry, tp.p->nx[0], tp.p->ny[0],
-                                                 tp.p->nd, ipart.p);
-    else
+    if (o->indicator_f32) {
+      // basis in registers, all parameters per block; RMAX the smallest of 8, 16, 32, 64 covering the rank
+      dim3 gr(rom->nA, nchunk);
+#define RTE_IND_REG(RM)                                                                                         \
+  k_indicator_reg<RM, MT><<<gr, 256, 0, st>>>(U32.p, Y32.p, rom->nA, N, rom->r, cs.p, base.p, d_mus.p, nmu,      \
+                                              tp.p->d_sig_t.p, R, tp.p->rx, tp.p->ry, tp.p->nx[0], tp.p->ny[0],  \
+                                              tp.p->nd, nchunk, ipart.p)
+      if (rom->r <= 8) RTE_IND_REG(8);
+      else if (rom->r <= 16) RTE_IND_REG(16);
+      else if (rom->r <= 32) RTE_IND_REG(32);
+      else RTE_IND_REG(64);
+#undef RTE_IND_REG
+    } else
       k_indicator<double, MT><<<gi, 256, 0, st>>>(rom->U.p, rom->Y.p, rom->nA, N, rom->r, cs.p, base.p, d_mus.p, nmu,
                                                   tp.p->d_sig_t.p, R, tp.p->rx, tp.p->ry, tp.p->nx[0], tp.p->ny[0],
                                                   tp.p->nd, ipart.p);

@@ -636,6 +636,30 @@ int romsad_reduced_operator(romsad_t rom, const double* sigma_s, const double* s
   return RTE_OK;
 }
 
+int romsad_galerkin_coefficients(romsad_t rom, rte_problem_t p, double* c_host) {
+  RTE_ARG(rom && p && c_host, "null handle or pointer");
+  RTE_ARG(rom->r >= 1, "empty ROM");
+  for (int b = 0; b < p->B; ++b) RTE_TRY(rom_check_mesh(rom, p, b));
+  // b~ (FP64 sweep), y = P^T Sigma_s b~, c = (U^T A_mu U)^{-1} y, every instance
+  DevBuf<double> bt, ys, cs;
+  DevBuf<int> d_all;
+  RTE_TRY(bt.alloc((size_t)p->ntot));
+  RTE_TRY(ys.alloc((size_t)p->B * 64));
+  RTE_TRY(cs.alloc((size_t)p->B * 64));
+  RTE_TRY(d_all.alloc(p->B));
+  std::vector<int> all(p->B);
+  for (int b = 0; b < p->B; ++b) all[b] = b;
+  RTE_CHECK_CUDA(cudaMemcpy(d_all.p, all.data(), p->B * sizeof(int), cudaMemcpyHostToDevice));
+  RTE_TRY(launch_T(p, MODE_RHS, true, nullptr, true, nullptr, bt.p, true, nullptr, 0));
+  RTE_TRY(rom_project_list(rom, p, d_all.p, p->B, bt.p, ys.p, 0));
+  RTE_TRY(rom_small_solve(rom, p, d_all.p, p->B, ys.p, cs.p, 0));
+  std::vector<double> h((size_t)p->B * 64);
+  RTE_CHECK_CUDA(cudaMemcpy(h.data(), cs.p, h.size() * 8, cudaMemcpyDeviceToHost));
+  for (int b = 0; b < p->B; ++b)
+    for (int k = 0; k < rom->r; ++k) c_host[(size_t)b * rom->r + k] = h[(size_t)b * 64 + k];
+  return RTE_OK;
+}
+
 int romsad_apply(romsad_t rom, rte_problem_t p, int dtype, const void* v, void* z, void* stream) {
   RTE_ARG(rom && p && v && z, "null handle or pointer");
   RTE_ARG(dtype == RTE_F64, "romsad_apply takes FP64 vectors");

@@ -40,12 +40,13 @@ def _worker(rank, port, q):
         slowest = bench.max_over_ranks(world, 1.5 + r)
         # the reference arm: rank 0 alone works, the other ranks return at once
         class Args:
-            steps, warmup, ref_iters, ref_sample, workload, restart = 1, 1, 10, 1, "slab1d_128", 30
+            steps, warmup, ref_iters, ref_cores, workload, restart, rom_rank = 1, 1, 10.0, 1, "slab1d_128", 30, 0
         called = []
-        orig = bench.oracle_sample
-        bench.oracle_sample = lambda *a, **k: called.append(1) or {"value": 1.0, "cores": 1, "sample": "x"}
-        bench.run_reference(Args, bench.wl.config(1), 1, world, r)
-        bench.oracle_sample = orig
+        orig = bench.oracle_baseline
+        bench.oracle_baseline = lambda *a, **k: called.append(1) or {"value": 1.0, "cores": 1, "sample": "x",
+                                                                     "per_iter_samples": [0.1]}
+        bench.run_reference(Args, bench.wl.config(1), 1, world, r, 1)
+        bench.oracle_baseline = orig
         dist.destroy_process_group()
         q.put((rank, gathered, slowest, len(called)))
     except BaseException as e:   # report instead of hanging the parent
