@@ -390,7 +390,7 @@ class Rom:
 
     def galerkin_coefficients(self, problem: Problem) -> np.ndarray:
         """Galerkin coefficients c_mu (eq. greedy-rom) of every instance of the problem: [B][rank]."""
-        out = np.zeros((problem.spec.n_instances, self.rank()))
+        out = np.zeros((problem.spec.n_instances, self.rank))
         _check(load().romsad_galerkin_coefficients(self.h, problem.h, _dptr(out)), "romsad_galerkin_coefficients")
         return out
 

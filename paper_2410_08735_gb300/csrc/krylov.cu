@@ -1892,13 +1892,13 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       }
       return RTE_OK;
     };
-    if (warm) {
-      std::vector<int> m64(B, res_df ? 0 : 1), mdf(B, res_df ? 1 : 0);
-      RTE_TRY(residual(m64, mdf));
-    } else {
-      RTE_CHECK_CUDA(cudaMemsetAsync(x, 0, p->ntot * 8, st));
-      RTE_CHECK_CUDA(cudaMemcpyAsync(ro, ws->bt.p, p->ntot * 8, cudaMemcpyDeviceToDevice, st));
-    }
+    // A warm start (given or learned) is folded into the first inner solve: it solves A~ d = b~ from
+    // d0 = phi0 in the inner precision (its starting residual is one FP32 sweep, counted by the inner run) and
+    // replaces x, instead of a refinement residual of phi0 being computed first.  The outer residual then
+    // starts at b~, as for a zero start.
+    const bool fold_warm = warm;
+    RTE_CHECK_CUDA(cudaMemcpyAsync(ro, ws->bt.p, p->ntot * 8, cudaMemcpyDeviceToDevice, st));
+    if (!warm) RTE_CHECK_CUDA(cudaMemsetAsync(x, 0, p->ntot * 8, st));
     // An outer step is meant to cut the true residual by about inner_rtol.  An instance whose step
     // cut it by less than esc_ratio is one whose slowest modes the FP32 operator cannot resolve
     // (eigenvalues of A~ near the FP32 rounding of I - T Sigma_s); it leaves the refinement and is
@@ -1971,16 +1971,28 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       }
       RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
       RunStats rs;
+      const bool from_x = fold_warm && outer == 0;   // first inner solve of a warm start: d0 = x, then x = d
       if (o->mode == RTE_MODE_MIXED_F64KRYLOV) {
-        RTE_TRY(run_fgmres(C, ro, ws->d.p, true, act, o->inner_rtol, cap, RUN_F32_SWEEP_F64_KRYLOV, false, done, rs));
+        if (from_x) {
+          k_copy_active<<<vg, 256, 0, st>>>(ws->d.p, x, p->d_inst.p, ws->active.p);
+          count_launch();
+        }
+        RTE_TRY(run_fgmres(C, ro, ws->d.p, !from_x, act, o->inner_rtol, cap, RUN_F32_SWEEP_F64_KRYLOV, false, done,
+                           rs));
         RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-        k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d.p, p->d_inst.p, ws->active.p);
+        if (from_x) k_copy_active<<<vg, 256, 0, st>>>(x, ws->d.p, p->d_inst.p, ws->active.p);
+        else k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d.p, p->d_inst.p, ws->active.p);
       } else {
         k_copy_active<<<vg, 256, 0, st>>>(ws->rin32.p, ro, p->d_inst.p, ws->active.p);
         count_launch();
-        RTE_TRY(run_fgmres(C, ws->rin32.p, ws->d32.p, true, act, o->inner_rtol, cap, RUN_F32, false, done, rs));
+        if (from_x) {
+          k_copy_active<<<vg, 256, 0, st>>>(ws->d32.p, x, p->d_inst.p, ws->active.p);
+          count_launch();
+        }
+        RTE_TRY(run_fgmres(C, ws->rin32.p, ws->d32.p, !from_x, act, o->inner_rtol, cap, RUN_F32, false, done, rs));
         RTE_CHECK_CUDA(cudaMemcpyAsync(ws->active.p, act.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
-        k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d32.p, p->d_inst.p, ws->active.p);
+        if (from_x) k_copy_active<<<vg, 256, 0, st>>>(x, ws->d32.p, p->d_inst.p, ws->active.p);
+        else k_axpy_active<<<vg, 256, 0, st>>>(x, ws->d32.p, p->d_inst.p, ws->active.p);
       }
       count_launch();
       // ro = b~ - A~ x: FP64 where the step is predicted to converge, double-float elsewhere
