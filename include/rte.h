@@ -92,9 +92,15 @@ typedef struct rte_problem_desc {
                               G = A exp(-a ((x-xc)^2 + (y-yc)^2)), src_gauss = (A, a, xc, yc),
                               projected in closed form (erf / exp differences per cell)      */
     double src_gauss[4];
-    int inflow_faces;      /* 0: inflow g on every boundary face; a one-sided inflow (bit mask of
-                              x-, x+, y-, y+) is RTE_ERR_UNSUPPORTED in this build          */
+    int inflow_faces;      /* faces carrying the inflow g: 0 = every boundary face, else a mask of
+                              RTE_FACE_XLO | RTE_FACE_XHI | RTE_FACE_YLO | RTE_FACE_YHI (a 1D slab has
+                              x- and x+ only); the other faces are vacuum (the paper's two-material
+                              problem has inflow on the left face only, Sec. 5)              */
 } rte_problem_desc;
+#define RTE_FACE_XLO 1
+#define RTE_FACE_XHI 2
+#define RTE_FACE_YLO 4
+#define RTE_FACE_YHI 8
 #define RTE_SRC_BOX 0
 #define RTE_SRC_GAUSS 1
 
@@ -109,7 +115,9 @@ typedef struct rte_problem_info {
 /* Build quadrature, geometry, region maps and the per-instance source on the device
  * (Sec. 2.1-2.3).  Returns RTE_ERR_INVALID_ARG for dim not in {1,2}, B < 1, a mesh
  * with fewer than 1 cell, a region grid that does not divide every mesh, an odd
- * n_azim, or negative cross sections. */
+ * n_azim, or negative cross sections.  With N_theta = 2 mod 4 two azimuths sit at pi/2 and
+ * 3pi/2; their Omega_x is the FP64 cos of those angles (a rounding error of order 1e-16, not
+ * exactly 0), and they are swept in the quadrant of its sign. */
 int rte_problem_create(const rte_problem_desc* desc, rte_problem_t* out);
 int rte_problem_destroy(rte_problem_t p);
 int rte_problem_get_info(rte_problem_t p, rte_problem_info* info);
@@ -118,6 +126,9 @@ int rte_problem_offsets(rte_problem_t p, long long* offsets);
 /* New material parameters mu = (sigma_s, sigma_a) per instance without rebuilding
  * (Sec. 4.1 parametric problem).  Host arrays [B][R], copied. */
 int rte_problem_set_params(rte_problem_t p, const double* sigma_s, const double* sigma_a);
+/* Per-instance inflow value g_b on the problem's inflow faces (host [B], copied), replacing the descriptor's
+ * inflow_g: a parametric boundary condition (Sec. 5, two-material problem, b~ affine in the inflow). */
+int rte_problem_set_inflow(rte_problem_t p, const double* g);
 
 /* --------------------------------------------------------- transport (Sec. 3) */
 /* Angular-output sweep (Sec. 3.1, eq. SI-equation): for every direction j,
@@ -143,10 +154,13 @@ int rte_rhs(rte_problem_t p, int dtype, void* btilde, void* stream);
  * library holds until the process exits; a problem needing more returns RTE_ERR_INVALID_ARG (use
  * rte_apply_op).  All calls share that array, so calls that overlap on the GPU (different streams,
  * threads or processes sharing the context) race: serialise them.  Nothing in the array needs to start
- * at zero: every call rewrites the parts it reads.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that first call before any
- * stream capture.  The problem handle itself must have been created beforehand (rte_problem_create
- * allocates).  Results agree with rte_apply_op up to the order of the partial sums. */
+ * at zero: every call rewrites the parts it reads.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) on the current device; the first call on a device may load the library's
+ * module there, so make that first call before any stream capture.  Directions per warp: the value the
+ * sweep autotuner chose for this precision (after rte_apply_op or a solve on the same problem) when its
+ * scratch fits, else the smallest value whose scratch fits (FP64: at most 4).  The problem handle itself
+ * must have been created beforehand (rte_problem_create allocates).  Results agree with rte_apply_op up to
+ * the order of the partial sums. */
 int rte_apply_op_noalloc(rte_problem_t p, int dtype, const void* z, void* w, void* stream);
 
 /* ----------------------------------------------------------- ROMSAD (Sec. 4) */

@@ -156,6 +156,7 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_void_p)]),
     "rte_rbf_initial_guess": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "rte_rbf_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "rte_problem_set_inflow": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "romsad_galerkin_coefficients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
 }
 
@@ -283,6 +284,11 @@ class Problem:
         ss = np.ascontiguousarray(np.asarray(sigma_s, dtype=np.float64))
         sa = np.ascontiguousarray(np.asarray(sigma_a, dtype=np.float64))
         _check(load().rte_problem_set_params(self.h, _dptr(ss), _dptr(sa)), "rte_problem_set_params")
+
+    def set_inflow(self, g):
+        """Per-instance inflow values on the problem's inflow faces: [B]."""
+        gv = np.ascontiguousarray(np.asarray(g, dtype=np.float64).reshape(-1))
+        _check(load().rte_problem_set_inflow(self.h, _dptr(gv)), "rte_problem_set_inflow")
 
     def close(self):
         if getattr(self, "h", None):

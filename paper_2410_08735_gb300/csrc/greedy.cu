@@ -233,7 +233,8 @@ static int make_problem_like(const rte_problem* tmpl, int n, const double* ss, c
   std::memcpy(d.src_box, tmpl->src_box, sizeof(d.src_box));
   d.src_kind = tmpl->src_kind;
   std::memcpy(d.src_gauss, tmpl->src_gauss, sizeof(d.src_gauss));
-  d.inflow_g = tmpl->g;
+  d.inflow_g = tmpl->inst[0].g;
+  d.inflow_faces = tmpl->inflow_mask;
   return rte_problem_create(&d, out);
 }
 

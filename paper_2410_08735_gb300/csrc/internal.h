@@ -90,6 +90,7 @@ struct InstInfo {
   long long off;       // dof offset in a scalar vector
   int ndof;            // nx*ny*nd
   double hx, hy;       // cell sizes
+  double g;            // isotropic inflow value on the inflow faces of the instance (eq. 1c)
 };
 
 // A unique in-plane direction (duplicates over +-Omega_z merged, weights summed).
@@ -127,6 +128,7 @@ struct rte_problem {
   long long ntot = 0;
   double box[4] = {0, 1, 0, 1};
   double g = 0.0, src_q = 0.0, src_box[4] = {0, 0, 0, 0};
+  int inflow_mask = 15;              // domain faces with inflow g: 1 x-low, 2 x-high, 4 y-low, 8 y-high
   int src_kind = RTE_SRC_BOX;
   double src_gauss[4] = {0, 0, 0, 0};   // A, a, xc, yc
   std::vector<double> ss, sa;        // [B][R] host copies
@@ -173,6 +175,9 @@ struct rte_problem {
 namespace rte {
 // problem.cu
 int upload_params(rte_problem* p);
+// greatest common divisor of the unique-direction counts of the quadrants (2D) or of the two half-ranges (1D):
+// a directions-per-warp value must divide it
+int quadrant_gcd(const rte_problem* p);
 // sweep.cu: generic launcher.
 //   src:  input vector (dtype in_f64 ? double : float)
 //   mode: 0 phi = T s ; 1 w = z - T(Sigma_s z) ; 2 r = b - (z - T(Sigma_s z)) ; 3 b~ (src = G, bc)

@@ -1,8 +1,6 @@
 // rte_apply_op_noalloc: the fused A~ z = z - T Sigma_s z of rte_apply_op for callers that must not
 // allocate device memory.  Its scratch (the sweep task list and the per-task partial scalar fluxes)
 // lives in one file-scope __device__ array instead of buffers obtained with cudaMalloc.
-#include <mutex>
-
 #include "internal.h"
 
 namespace rte {
@@ -28,29 +26,32 @@ __global__ void k_make_tasks(int B, int D, int q0, int q1, int q2, int q3, int q
   out[tid] = SweepTask{b, qs[q] + rem * D, t, 0};
 }
 
-// Device address of g_noalloc_scratch for each device, looked up once with that device current.
-static std::mutex g_mu;
-static void* g_addr[64] = {nullptr};
-
+// Device address of g_noalloc_scratch on the current device.  It is looked up on every call (with the device
+// current) rather than cached: cudaGetSymbolAddress allocates nothing once the library's module is loaded on
+// the device, and a cached address would go stale if the caller reset the device or its primary context was
+// released and re-created (the module, and the array with it, would then be loaded anew).
 static int scratch_address(void** out) {
-  int dev = 0;
-  RTE_CHECK_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) {
-    set_error("rte_apply_op_noalloc: device index out of range");
-    return RTE_ERR_UNSUPPORTED;
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess) {
+    set_error(std::string("rte_apply_op_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    return RTE_ERR_CUDA;
   }
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_addr[dev]) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) {
-      set_error(std::string("rte_apply_op_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      return RTE_ERR_CUDA;
-    }
-    g_addr[dev] = ptr;
-  }
-  *out = g_addr[dev];
+  *out = ptr;
   return RTE_OK;
+}
+
+// Scratch bytes (task list rounded to 256 bytes, then the partial fluxes) for D directions per warp.
+static size_t scratch_bytes(const rte_problem* p, int D, bool f64, int* per_inst_out) {
+  int per_inst = 0;
+  if (p->dim == 1) {
+    per_inst = p->nu;
+  } else {
+    for (int q = 0; q < 4; ++q) per_inst += (p->quad_start[q + 1] - p->quad_start[q]) / D;
+  }
+  *per_inst_out = per_inst;
+  const size_t ntasks = (size_t)p->B * per_inst;
+  return ((ntasks * sizeof(SweepTask) + 255) & ~(size_t)255) + (size_t)per_inst * p->ntot * (f64 ? 8 : 4);
 }
 
 }  // namespace rte
@@ -61,29 +62,34 @@ extern "C" int rte_apply_op_noalloc(rte_problem_t p, int dtype, const void* z, v
   RTE_ARG(p && z && w, "null handle or pointer");
   RTE_ARG(dtype == RTE_F64 || dtype == RTE_F32, "dtype must be RTE_F64 or RTE_F32");
   const bool f64 = dtype == RTE_F64;
-  // fewest tasks (largest directions-per-warp) keep the partial sums small
+  // Directions per warp: the value the sweep autotuner picked for this precision (when rte_apply_op or a
+  // solve has tuned it) if its scratch fits, else the smallest D whose scratch fits (the most warps in flight;
+  // FP64 takes D <= 4 like the tuned launches).
   int D = 1;
   if (p->dim == 2) {
-    const int nq = p->quad_start[1] - p->quad_start[0];
-    const int cands[] = {8, 4, 2, 1};
-    for (int d : cands)
-      if ((!f64 || d <= 4) && nq % d == 0) { D = d; break; }
+    const int nq = quadrant_gcd(p);
+    const int tuned = p->tuned_D[f64 ? PREC_F64 : PREC_F32][0];
+    int dummy = 0;
+    D = 0;
+    if (tuned > 0 && nq % tuned == 0 && scratch_bytes(p, tuned, f64, &dummy) <= kNoAllocScratchBytes) D = tuned;
+    for (int d : {1, 2, 4, 8}) {
+      if (D) break;
+      if ((f64 && d > 4) || nq % d) continue;
+      if (scratch_bytes(p, d, f64, &dummy) <= kNoAllocScratchBytes) D = d;
+    }
+    if (!D) D = f64 ? 4 : 8;   // nothing fits: reported below with the smallest requirement
+    while (nq % D) D >>= 1;
   }
   int per_inst = 0;
-  if (p->dim == 1) {
-    per_inst = p->nu;
-  } else {
-    for (int q = 0; q < 4; ++q) per_inst += (p->quad_start[q + 1] - p->quad_start[q]) / D;
-  }
-  const size_t ntasks = (size_t)p->B * per_inst;
-  const size_t task_bytes = (ntasks * sizeof(SweepTask) + 255) & ~(size_t)255;
-  const size_t part_bytes = (size_t)per_inst * p->ntot * (f64 ? 8 : 4);
-  if (task_bytes + part_bytes > kNoAllocScratchBytes) {
-    set_error("rte_apply_op_noalloc: problem needs " + std::to_string(task_bytes + part_bytes) +
+  const size_t need = scratch_bytes(p, D, f64, &per_inst);
+  if (need > kNoAllocScratchBytes) {
+    set_error("rte_apply_op_noalloc: problem needs " + std::to_string(need) +
               " bytes of scratch, more than the fixed " + std::to_string(kNoAllocScratchBytes) +
               "; use rte_apply_op");
     return RTE_ERR_INVALID_ARG;
   }
+  const size_t ntasks = (size_t)p->B * per_inst;
+  const size_t task_bytes = (ntasks * sizeof(SweepTask) + 255) & ~(size_t)255;
   void* base = nullptr;
   RTE_TRY(scratch_address(&base));
   SweepTask* tasks = static_cast<SweepTask*>(base);

@@ -156,6 +156,17 @@ __global__ void k_sig_dof(const InstInfo* inst, int B, int R, int rx, int ry, in
   }
 }
 
+int quadrant_gcd(const rte_problem* p) {
+  const int nq = p->dim == 2 ? 4 : 2;
+  int g = 0;
+  for (int q = 0; q < nq; ++q) {
+    int a = p->quad_start[q + 1] - p->quad_start[q], b = g;
+    while (b) { const int t = a % b; a = b; b = t; }
+    g = a;
+  }
+  return g > 0 ? g : 1;
+}
+
 int upload_params(rte_problem* p) {
   std::vector<double> st(p->ss.size());
   std::vector<float> s32(p->ss.size()), sdf(2 * p->ss.size());
@@ -197,8 +208,11 @@ static int create_impl(const rte_problem_desc* d, rte_problem* p) {
   RTE_ARG(d->n_polar >= 1 && d->n_polar <= 64, "n_polar must be in [1, 64]");
   RTE_ARG(d->rx >= 1 && (d->dim == 1 || d->ry >= 1), "region grid must be positive");
   RTE_ARG(d->box[1] > d->box[0] && (d->dim == 1 || d->box[3] > d->box[2]), "empty domain box");
-  if (d->dim == 2) RTE_ARG(d->n_azim >= 4 && d->n_azim % 4 == 0 && d->n_azim <= 256,
-                           "n_azim must be a positive multiple of 4 (no axis-parallel directions)");
+  // N_theta = 2 mod 4 puts two Chebyshev azimuths at pi/2 and 3pi/2, where the computed cos is a rounding error
+  // (+6e-17, -1.8e-16): those directions are swept in the quadrant of the computed signs, with an x-coupling of
+  // that size, as any direction; the quadrants then hold unequal numbers of directions
+  if (d->dim == 2) RTE_ARG(d->n_azim >= 4 && d->n_azim % 2 == 0 && d->n_azim <= 256,
+                           "n_azim must be even and in [4, 256]");
   if (d->dim == 1) RTE_ARG(d->n_polar % 2 == 0, "1D n_polar must be even");
   p->dim = d->dim;
   p->B = d->n_instances;
@@ -219,10 +233,9 @@ static int create_impl(const rte_problem_desc* d, rte_problem* p) {
   }
   p->src_kind = d->src_kind;
   std::memcpy(p->src_gauss, d->src_gauss, sizeof(p->src_gauss));
-  if (d->inflow_faces != 0 && d->inflow_faces != 15) {
-    set_error("rte_problem_create: a one-sided inflow is not supported by this build");
-    return RTE_ERR_UNSUPPORTED;
-  }
+  RTE_ARG(d->inflow_faces >= 0 && d->inflow_faces <= 15, "inflow_faces is a mask of 4 bits");
+  RTE_ARG(d->dim == 2 || (d->inflow_faces & 12) == 0, "a 1D slab has the faces x- and x+ only");
+  p->inflow_mask = d->inflow_faces == 0 ? 15 : d->inflow_faces;
   p->nx.resize(p->B);
   p->ny.resize(p->B);
   p->off.assign(p->B + 1, 0);
@@ -241,6 +254,7 @@ static int create_impl(const rte_problem_desc* d, rte_problem* p) {
     in.ndof = (int)nb;
     in.hx = (d->box[1] - d->box[0]) / p->nx[b];
     in.hy = d->dim == 2 ? (d->box[3] - d->box[2]) / p->ny[b] : 1.0;
+    in.g = d->inflow_g;
   }
   p->ntot = p->off[p->B];
   size_t nR = (size_t)p->B * p->R;
@@ -444,6 +458,14 @@ int rte_problem_set_params(rte_problem_t p, const double* sigma_s, const double*
   p->ss.assign(sigma_s, sigma_s + nR);
   p->sa.assign(sigma_a, sigma_a + nR);
   return rte::upload_params(p);
+}
+
+int rte_problem_set_inflow(rte_problem_t p, const double* g) {
+  RTE_ARG(p != nullptr && g != nullptr, "null handle or inflow array");
+  for (int b = 0; b < p->B; ++b) RTE_ARG(std::isfinite(g[b]), "inflow values must be finite");
+  for (int b = 0; b < p->B; ++b) p->inst[b].g = g[b];
+  RTE_CHECK_CUDA(cudaMemcpy(p->d_inst.p, p->inst.data(), p->B * sizeof(rte::InstInfo), cudaMemcpyHostToDevice));
+  return RTE_OK;
 }
 
 }  // extern "C"

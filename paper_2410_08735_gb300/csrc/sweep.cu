@@ -42,7 +42,7 @@ struct SweepArgs {
   const void* sig_s;    // compute type, [B][R]; null: no Sigma_s scaling of the input
   const void* src;      // input type, scalar vector
   int with_bc;
-  double g;
+  int inflow_mask;      // faces carrying the inflow: 1 x-low, 2 x-high, 4 y-low, 8 y-high
   void* partial;        // compute type, [tasks_per_inst * off_b + t * N_b + i]
   int tasks_per_inst;
   void* psi;            // compute type, angular vector, or null
@@ -156,7 +156,11 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
     be[d] = (T)(u.ay / in.hy);
     wg[d] = (T)u.w;
   }
-  const T bnd = a.with_bc ? (T)(a.g * sqrt(in.hx * in.hy)) : (T)0;
+  // inflow traces of the constant g on the task's inflow faces (x face by the sign of Omega_x, y face by that of
+  // Omega_y), zero on faces without inflow
+  const double gtr = a.with_bc ? in.g * sqrt(in.hx * in.hy) : 0.0;
+  const T bndx = (a.inflow_mask & (sx > 0 ? 1 : 2)) ? (T)gtr : (T)0;
+  const T bndy = (a.inflow_mask & (sy > 0 ? 4 : 8)) ? (T)gtr : (T)0;
   const bool sig_s = a.sig_s != nullptr;
   const TI* src = reinterpret_cast<const TI*>(a.src) + in.off;
   T* part = reinterpret_cast<T*>(a.partial) + (size_t)a.tasks_per_inst * in.off + (size_t)tk.t * in.ndof;
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
       if (lane == 0) {
         if (band == 0) {
 #pragma unroll
-          for (int d = 0; d < D; ++d) { yi0[d] = bnd; yi1[d] = (T)0; }
+          for (int d = 0; d < D; ++d) { yi0[d] = bndy; yi1[d] = (T)0; }
         } else {
 #pragma unroll
           for (int d = 0; d < D; ++d) {
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
       }
       if (col == 0) {
 #pragma unroll
-        for (int d = 0; d < D; ++d) { tx0[d] = bnd; tx1[d] = (T)0; }
+        for (int d = 0; d < D; ++d) { tx0[d] = bndx; tx1[d] = (T)0; }
       }
       if (sig_s) {
         const T sg = sgs[reg];
@@ -377,11 +381,14 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
 }
 
 // Band-parallel variant for meshes with ny <= 32 * 8: one CTA per task, warp w owns the 32-row band w
-// (lane l owns row 32w + l).  All bands advance in lock step, one CTA barrier per step: lane l of
-// band w handles column col = s - 32w - l at step s, so the y-inflow of a cell is the y-outflow of
-// the lane below one step earlier (warp shuffle; for lane 0 the last lane of the band below, through
-// shared memory).  The critical path is the nx + ny - 1 diagonals, and a lane's cell index moves by one
-// per step, so the step loop has no division and the source prefetch is a plain +-PF offset.
+// (lane l owns row 32w + l).  Lane l of band w handles column col = s - (32 + SK) w - l at step s, so the
+// y-inflow of a cell is the y-outflow of the lane below one step earlier (warp shuffle) and, for lane 0, the
+// y-outflow that the last lane of the band below produced SK + 1 steps earlier (through shared memory).
+// Bands are skewed by SK steps so that they need to meet at a CTA barrier only once every SK steps: a
+// value read at step s of group m (steps m SK .. m SK + SK - 1) was written at step s - SK - 1, in an
+// earlier group, before that group's barrier.  The critical path is the nx + ny - 1 diagonals plus the skew
+// of the bands, and a lane's cell index moves by one per step, so the step loop has no division and the
+// source prefetch is a plain +-PF offset.
 template <typename T, typename TI, int D, bool ANG>
 __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -420,7 +427,11 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
     wg2[d] = sy > 0 ? wg[d] : -wg[d];
     wg3[d] = sx * sy > 0 ? wg[d] : -wg[d];
   }
-  const T bnd = a.with_bc ? (T)(a.g * sqrt(in.hx * in.hy)) : (T)0;
+  // inflow traces of the constant g on the task's inflow faces (x face by the sign of Omega_x, y face by that of
+  // Omega_y), zero on faces without inflow
+  const double gtr = a.with_bc ? in.g * sqrt(in.hx * in.hy) : 0.0;
+  const T bndx = (a.inflow_mask & (sx > 0 ? 1 : 2)) ? (T)gtr : (T)0;
+  const T bndy = (a.inflow_mask & (sy > 0 ? 4 : 8)) ? (T)gtr : (T)0;
   const bool sig_s = a.sig_s != nullptr;
   const TI* src = reinterpret_cast<const TI*>(a.src) + in.off;
   T* part = reinterpret_cast<T*>(a.partial) + (size_t)a.tasks_per_inst * in.off + (size_t)tk.t * in.ndof;
@@ -454,13 +465,15 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
   const int iy = sy > 0 ? row : ny - 1 - row;
   const long long rowbase = (long long)(rowok ? iy : 0) * nx;
   const int rowreg = rowok ? (iy / cy) * a.rx : 0;
-  const int nsteps = 32 * (nb - 1) + 31 + nx;
-  const int col0 = -(32 * band + lane);      // column at step 0
+  constexpr int SK = 8;                        // band skew = steps between CTA barriers (a multiple of 8)
+  const int nsteps = (32 + SK) * (nb - 1) + 31 + nx;
+  const int col0 = -((32 + SK) * band + lane);      // column at step 0
   auto cell_of = [&](int col) -> long long { return rowbase + (sx > 0 ? col : nx - 1 - col); };
   T tx0[D], tx1[D], ty0[D], ty1[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) { tx0[d] = tx1[d] = ty0[d] = ty1[d] = (T)0; }
   constexpr int PF = 8;
+  static_assert(PF == SK, "the barrier closes each prefetch group of SK steps");
   TI q0[PF], q1[PF], q2[PF], q3[PF];
 #pragma unroll
   for (int k = 0; k < PF; ++k) {
@@ -489,7 +502,7 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
         if (lane == 0) {
           if (band == 0) {
 #pragma unroll
-            for (int d = 0; d < D; ++d) { yi0[d] = bnd; yi1[d] = (T)0; }
+            for (int d = 0; d < D; ++d) { yi0[d] = bndy; yi1[d] = (T)0; }
           } else {
             const T* yb = ybuf + (size_t)(band - 1) * D * nx * 2;
 #pragma unroll
@@ -501,7 +514,7 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
         }
         if (col == 0) {
 #pragma unroll
-          for (int d = 0; d < D; ++d) { tx0[d] = bnd; tx1[d] = (T)0; }
+          for (int d = 0; d < D; ++d) { tx0[d] = bndx; tx1[d] = (T)0; }
         }
         const int ix = sx > 0 ? col : nx - 1 - col;
         const long long c = rowbase + ix;
@@ -567,7 +580,7 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
         if (regular) {
           const int f = ((s + 1) & 7) + 8 * k;
           const bool ff = __shfl_sync(0xffffffffu, flush, f);
-          const int colf = s - 32 * band - f;
+          const int colf = s - (32 + SK) * band - f;
           if (ff) {
             const long long cf = cell_at(f, colf);
             RTE_STORE_SEGMENT(f, cf, colf, e);
@@ -582,7 +595,7 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
             }
             if (k < n) {
               const int f = fl[k];
-              const int colf = s - 32 * band - f;
+              const int colf = s - (32 + SK) * band - f;
               const long long cf = cell_at(f, colf);
               RTE_STORE_SEGMENT(f, cf, colf, e);
             }
@@ -590,7 +603,8 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
         }
         __syncwarp();
       }
-      if (nwarps > 1) __syncthreads();
+      // the bands meet once per group of SK steps (PF == SK: the last step of the prefetch group)
+      if (nwarps > 1 && kk == PF - 1) __syncthreads();
       else __syncwarp();
     }
   }
@@ -615,7 +629,7 @@ __global__ void k_sweep1d(SweepArgs a) {
   T* psi = ANG ? reinterpret_cast<T*>(a.psi) + (size_t)(a.psi_unique ? a.nu : a.ndir) * in.off +
                      (size_t)(a.psi_unique ? tk.u0 : u.dup[0]) * in.ndof
                 : nullptr;
-  T tx = a.with_bc ? (T)(a.g * sqrt(in.hx)) : (T)0;
+  T tx = a.with_bc && (a.inflow_mask & (u.sx > 0 ? 1 : 2)) ? (T)(in.g * sqrt(in.hx)) : (T)0;
   for (int col = 0; col < nx; ++col) {
     const int ix = u.sx > 0 ? col : nx - 1 - col;
     const int reg = ix / cx;
@@ -744,7 +758,7 @@ static int pick_D(const rte_problem* p, int prec, bool ang = false) {
   if (p->force_D > 0) return p->force_D;
   if (p->tuned_D[prec][ang ? 1 : 0] > 0) return p->tuned_D[prec][ang ? 1 : 0];
   const bool f64 = prec != PREC_F32;
-  const int nq = p->quad_start[1] - p->quad_start[0];
+  const int nq = quadrant_gcd(p);
   // Directions per warp: the largest D that still leaves at least 8 warps per SM (152 SMs) in
   // flight; with fewer tasks (a single small instance) parallelism wins and D = 1.  FP64 keeps D
   // small (registers; its pipe, not latency, bounds it).
@@ -917,7 +931,7 @@ static void fill_args(rte_problem* p, SweepArgs& a, int prec) {
   a.ntasks = p->ntasks;
   a.linv = prec == PREC_F64 ? (const void*)p->d_linv64.p
                             : (prec == PREC_DF ? (const void*)p->d_linv_df.p : (const void*)p->d_linv32.p);
-  a.g = p->g;
+  a.inflow_mask = p->inflow_mask;
   a.tasks_per_inst = p->tasks_per_inst;
   a.ndir = p->ndir;
   a.nu = p->nu;
@@ -941,7 +955,7 @@ int autotune(rte_problem* p, int prec, bool ang, const void* src, void* psi, cud
   const int fi = prec, ai = ang ? 1 : 0;
   const bool f64 = prec == PREC_F64;
   if (p->tuned_D[fi][ai] > 0 || p->dim == 1) return RTE_OK;
-  const int nq = p->quad_start[1] - p->quad_start[0];
+  const int nq = quadrant_gcd(p);
   int maxny = 0;
   for (int b = 0; b < p->B; ++b) maxny = std::max(maxny, p->ny[b]);
   RTE_TRY(p->d_tmp64.ensure((size_t)p->ntot));
@@ -1145,7 +1159,7 @@ int launch_op_external(rte_problem* p, bool f64, const void* z, void* w, const S
   a.tasks = tasks;
   a.ntasks = ntasks;
   a.linv = f64 ? (const void*)p->d_linv64.p : (const void*)p->d_linv32.p;
-  a.g = p->g;
+  a.inflow_mask = p->inflow_mask;
   a.tasks_per_inst = tasks_per_inst;
   a.ndir = p->ndir;
   a.nu = p->nu;

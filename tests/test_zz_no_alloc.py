@@ -9,23 +9,28 @@ import numpy as np
 import pytest
 
 import workloads as wl
+from oracle import transport as OT
 
-from gpu_common import lib, rel, spec2d, to_dev, torch_cuda
+from gpu_common import lib, oracle_problems, rel, spec1d, spec2d, split, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
 
-def _problem(B):
-    spec = spec2d([40, 24], [36, 48], n_polar=4, n_azim=8, inflow_g=0.2)
-    ss, sa = wl.draw_params(spec, 2, 61)
-    return B.Problem(spec, ss, sa)
+def _spec2d():
+    return spec2d([40, 24], [36, 48], n_polar=4, n_azim=8, inflow_g=0.2)
+
+
+def _problem(B, spec=None, seed=61):
+    spec = spec or _spec2d()
+    ss, sa = wl.draw_params(spec, spec.n_instances, seed)
+    return B.Problem(spec, ss, sa), spec, ss, sa
 
 
 @pytest.mark.parametrize("dtype_name,tol", [("float64", 1e-13), ("float32", 2e-5)])
 def test_noalloc_matches_apply_op_on_two_calls(dtype_name, tol):
     torch = torch_cuda()
     B = lib()
-    gp = _problem(B)
+    gp, _, _, _ = _problem(B)
     dt = getattr(torch, dtype_name)
     rng = np.random.default_rng(7)
     for call in range(2):   # two calls in a row share (and must not depend on) the scratch contents
@@ -37,6 +42,46 @@ def test_noalloc_matches_apply_op_on_two_calls(dtype_name, tol):
         torch.cuda.synchronize()
         assert torch.isfinite(out).all()
         assert rel(out.cpu().numpy(), ref.cpu().numpy()) < tol, call
+
+
+@pytest.mark.parametrize("dim", [2, 1])
+def test_noalloc_first_calls_allocate_nothing_and_match_the_oracle(dim):
+    """On a fresh problem (nothing tuned, no sweep buffers yet) the entry point is called first: the device's free
+    memory is the same before and after two calls, and the results equal the oracle's A~ z (FP64 1e-13, FP32 2e-5
+    on the FP32-rounded input), in the 2D geometry and in the 1D slab (one task per direction)."""
+    torch = torch_cuda()
+    B = lib()
+    # load the library's kernels on this device first (module loading may itself take device memory)
+    warm, _, _, _ = _problem(B, seed=63)
+    zw = torch.zeros(warm.n_dof, dtype=torch.float64, device="cuda")
+    warm.apply_op_noalloc(zw, torch.empty_like(zw))
+    w32 = zw.float()
+    warm.apply_op_noalloc(w32, torch.empty_like(w32))
+    spec = _spec2d() if dim == 2 else spec1d([48, 80], n_polar=8)
+    gp, spec, ss, sa = _problem(B, spec, seed=64)
+    ops = oracle_problems(spec, ss, sa)
+    rng = np.random.default_rng(8)
+    zs = [rng.standard_normal(gp.n_dof) for _ in range(2)]
+    z64 = [to_dev(z) for z in zs]
+    z32 = [to_dev(z, torch.float32) for z in zs]
+    o64 = [torch.empty_like(z) for z in z64]
+    o32 = [torch.empty_like(z) for z in z32]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in range(2):
+        gp.apply_op_noalloc(z64[k], o64[k])
+        gp.apply_op_noalloc(z32[k], o32[k])
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    for k in range(2):
+        h64 = split(o64[k].cpu().numpy(), gp.offsets)
+        h32 = split(o32[k].cpu().numpy(), gp.offsets)
+        zr = zs[k].astype(np.float32).astype(np.float64)
+        for b, op in enumerate(ops):
+            zb = split(zs[k], gp.offsets)[b]
+            zrb = split(zr, gp.offsets)[b]
+            assert rel(h64[b], OT.Atilde_apply(op, zb)) < 1e-13, (k, b)
+            assert rel(h32[b], OT.Atilde_apply(op, zrb)) < 2e-5, (k, b)
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch():
