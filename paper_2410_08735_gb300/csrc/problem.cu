@@ -234,7 +234,8 @@ static int create_impl(const rte_problem_desc* d, rte_problem* p) {
   p->src_kind = d->src_kind;
   std::memcpy(p->src_gauss, d->src_gauss, sizeof(p->src_gauss));
   RTE_ARG(d->inflow_faces >= 0 && d->inflow_faces <= 15, "inflow_faces is a mask of 4 bits");
-  RTE_ARG(d->dim == 2 || (d->inflow_faces & 12) == 0, "a 1D slab has the faces x- and x+ only");
+  RTE_ARG(d->dim == 2 || d->inflow_faces == 15 || (d->inflow_faces & 12) == 0,
+          "a 1D slab has the faces x- and x+ only");
   p->inflow_mask = d->inflow_faces == 0 ? 15 : d->inflow_faces;
   p->nx.resize(p->B);
   p->ny.resize(p->B);

@@ -300,4 +300,4 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(B.RteError):
         B.Problem(spec2d([15], [16], n_polar=2, n_azim=8), ss, sa)   # region grid does not divide
     with pytest.raises(B.RteError):
-        B.Problem(spec2d([16], [16], n_polar=2, n_azim=6), ss, sa)   # azimuths not a multiple of 4
+        B.Problem(spec2d([16], [16], n_polar=2, n_azim=7), ss, sa)   # odd number of azimuths
