@@ -156,7 +156,9 @@ int rte_rhs(rte_problem_t p, int dtype, void* btilde, void* stream);
  * threads or processes sharing the context) race: serialise them.  Nothing in the array needs to start
  * at zero: every call rewrites the parts it reads.  Every call looks up the array's device address
  * (cudaGetSymbolAddress) on the current device; the first call on a device may load the library's
- * module there, so make that first call before any stream capture.  Directions per warp: the value the
+ * module there, and the first launch of each kernel variant may load its code (device memory the driver
+ * takes, not this entry point), so make a first call of the same shape before any stream capture or
+ * allocation-free region.  Directions per warp: the value the
  * sweep autotuner chose for this precision (after rte_apply_op or a solve on the same problem) when its
  * scratch fits, else the smallest value whose scratch fits (FP64: at most 4).  The problem handle itself
  * must have been created beforehand (rte_problem_create allocates).  Results agree with rte_apply_op up to
@@ -215,7 +217,11 @@ int romsad_reduced_operator(romsad_t rom, const double* sigma_s, const double* s
  * labels).  c_host: host [B][r].  Synchronises the legacy stream. */
 int romsad_galerkin_coefficients(romsad_t rom, rte_problem_t p, double* c_host);
 /* z = M_ROM^{-1} v for every instance of p (all instances must use the ROM's mesh),
- * eq. rom-sa-preconditioner, with the instance's own sigma.  v, z: scalar vectors. */
+ * eq. rom-sa-preconditioner, with the instance's own sigma.  v, z: scalar vectors.
+ * dtype RTE_F64: FP64 products on the CUDA cores.  dtype RTE_F32: FP32 vectors; the instances share P and W,
+ * so the projection P^T Sigma_s V and the lift W C are matrix products over the instances, run on the tensor
+ * cores (mma.sync m16n8k16, BF16 operands, FP32 accumulation, chunk sums in a fixed order), the reduced solve
+ * with the FP32-rounded inverse of U^T A_mu U.  Synchronises the stream. */
 int romsad_apply(romsad_t rom, rte_problem_t p, int dtype, const void* v, void* z, void* stream);
 int romsad_save(romsad_t rom, const char* path);
 int romsad_load(const char* path, romsad_t* out);
@@ -341,6 +347,10 @@ typedef struct fgmres_opts {
                                 instead of the reduced solve (instances without an MLP, or with a
                                 non-finite prediction, keep the plain apply)               */
     int dsa_variant;         /* RTE_POST_DSA: RTE_DSA_PARTIAL or RTE_DSA_LUMPED            */
+    int rom_bf16;            /* RTE_MODE_MIXED: 1 = the ROMSAD applies of the inner (FP32) solves take
+                                their projection and lift on the tensor cores (BF16 operands, FP32
+                                accumulation, as romsad_apply with RTE_F32); 0 = FP32 CUDA-core
+                                products fused into the Arnoldi step                           */
     int refine_residual;     /* mixed: precision of the refinement residuals b~ - A~ phi that steer the
                                 inner solves.  RTE_RESIDUAL_DF (0): double-float sweeps (~1e-14 relative,
                                 on the FP32 pipe), except for a step predicted to converge; a residual that

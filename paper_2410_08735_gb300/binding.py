@@ -75,7 +75,7 @@ class FgmresOpts(ctypes.Structure):
                 ("window", ctypes.c_int), ("post_mode", ctypes.c_int), ("mode", ctypes.c_int),
                 ("inner_rtol", ctypes.c_double), ("max_outer", ctypes.c_int),
                 ("true_residual_check", ctypes.c_int), ("warm_start", ctypes.c_int), ("learned_slot", ctypes.c_int),
-                ("dsa_variant", ctypes.c_int), ("refine_residual", ctypes.c_int)]
+                ("dsa_variant", ctypes.c_int), ("rom_bf16", ctypes.c_int), ("refine_residual", ctypes.c_int)]
 
 
 class FgmresStats(ctypes.Structure):
@@ -493,7 +493,7 @@ def fgmres_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi,
                  rtol=1e-10, max_iter=1000, window=2, post_mode=RTE_POST_ROM, mode=RTE_MODE_FP64,
                  inner_rtol=1e-2, max_outer=20, true_residual_check=True, stream=None, raise_on_fail=True,
                  learned_warm_start=False, learned_slot=False, dsa_variant=RTE_DSA_PARTIAL,
-                 refine_residual=RTE_RESIDUAL_DF):
+                 refine_residual=RTE_RESIDUAL_DF, rom_bf16=False):
     """FGMRES-ROMSAD for all instances; phi: FP64 device tensor or host (numpy/pinned) buffer.
     post_mode=RTE_POST_DSA switches to DSA after the window (with roms=None: GMRES-DSA).
 
@@ -502,7 +502,8 @@ def fgmres_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi,
     B = problem.spec.n_instances
     ws = 2 if learned_warm_start else int(phi0 is not None)
     o = FgmresOpts(restart, rtol, max_iter, window, post_mode, mode, inner_rtol, max_outer,
-                   int(true_residual_check), ws, int(learned_slot), int(dsa_variant), int(refine_residual))
+                   int(true_residual_check), ws, int(learned_slot), int(dsa_variant), int(rom_bf16),
+                   int(refine_residual))
     st = (FgmresStats * B)()
     if roms is None:
         rarr = None
@@ -525,7 +526,7 @@ def si_solve(problem: Problem, roms: Optional[Sequence[Optional[Rom]]], phi, phi
     """SI-ROMSAD (source iteration, ROM correction in the window, then post_mode) for all instances, FP64.
     phi: FP64 device tensor or host (numpy) buffer.  Returns the list of per-instance stats dicts."""
     B = problem.spec.n_instances
-    o = FgmresOpts(1, rtol, max_iter, window, post_mode, RTE_MODE_FP64, 0.0, 0, 0, 0, 0, int(dsa_variant), 0)
+    o = FgmresOpts(1, rtol, max_iter, window, post_mode, RTE_MODE_FP64, 0.0, 0, 0, 0, 0, int(dsa_variant), 0, 0)
     st = (FgmresStats * B)()
     rarr = None if roms is None else (ctypes.c_void_p * B)(*[(r.h.value if r is not None else None) for r in roms])
     if isinstance(phi, np.ndarray):

@@ -1205,6 +1205,7 @@ struct SolveCtx {
   bool any_rom = false;               // some instance has a ROM
   bool any_norom = false;             // some instance has none
   bool dsa = false;                   // DSA after the window (and throughout for instances without a ROM)
+  bool rom_tc = false;                // FP32 runs: ROMSAD products on the tensor cores (romsad_tc.cu)
 };
 
 
@@ -1334,17 +1335,31 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
     for (int j = 0; j < m; ++j) {
       const int jg = it_first + j + 1;   // lock-step instances share the global iteration index
       const bool use_rom = W.withZ && C.any_rom && (jg <= C.window || C.post == RTE_POST_ROM);
-      const bool rom_next = W.withZ && C.any_rom && (jg + 1 <= C.window || C.post == RTE_POST_ROM);
+      const bool rom_next_full = W.withZ && C.any_rom && (jg + 1 <= C.window || C.post == RTE_POST_ROM);
+      // tensor-core ROMSAD products: applied at the start of each window iteration by their own kernels
+      // instead of inside the fused Arnoldi step
+      const bool tc = C.rom_tc && !f64;
+      const bool rom_next = rom_next_full && !tc;
       // DSA on z_j (cycle start or multi-phase step) and on z_{j+1} (after the fused step): for every
       // instance outside the ROM window, for instances without a ROM inside it
       const bool dsa_now = C.dsa && W.withZ && (!use_rom || C.any_norom);
-      const bool dsa_next = C.dsa && W.withZ && W.fused && j + 1 < m && (!rom_next || C.any_norom);
+      const bool dsa_next = C.dsa && W.withZ && W.fused && j + 1 < m && (!rom_next_full || C.any_norom);
       // One Arnoldi iteration: w = A~ z_j into V[j+1], MGS, Givens, and the next preconditioned vector
       // z_{j+1} (the first one of a cycle, z_0, by the preconditioner kernel).
       auto body = [&](cudaStream_t s) -> int {
         TV* vj = Vb + (size_t)j * ntot;
         TV* zj = Zbase + (size_t)j * ntot;
-        if (W.withZ && (j == 0 || !W.fused)) {
+        const bool start_pre = W.withZ && (j == 0 || !W.fused);
+        if (W.withZ && tc && use_rom) {
+          if constexpr (!f64) {
+            if (start_pre) {   // z = v everywhere, then the ROM instances' z from the tensor-core apply
+              k_copy_active<<<vg, 256, 0, s>>>(zj, vj, p->d_inst.p, W.active.p);
+              count_launch();
+            }
+            for (RomPlan& pl : *C.plans) RTE_TRY(rom_tc_apply(pl, p, W.active.p, vj, zj, s));
+          }
+          if (start_pre && dsa_now) RTE_TRY(dsa_launch(p, f64, vj, zj, W.active.p, W.norom.p, s));
+        } else if (start_pre) {
           if (use_rom) {
             const int2* it_p = W.items.p;
             int nit = W.nitems, Bv = B, nch = W.nchunk;
@@ -1452,14 +1467,14 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
           count_launch();
           if (dsa_next)
             RTE_TRY(dsa_launch(p, f64, Vb + (size_t)(j + 1) * ntot, A.znext, W.active.p,
-                               rom_next ? W.norom.p : nullptr, s));
+                               rom_next_full ? W.norom.p : nullptr, s));
         }
         RTE_CHECK_CUDA(cudaGetLastError());
         return RTE_OK;
       };
       const int key = j | (use_rom ? 1 << 8 : 0) | (f64 ? 1 << 9 : 0) | (C.rec ? 1 << 10 : 0) |
                       (rom_next ? 1 << 11 : 0) | (slot_now && j == 0 ? 1 << 12 : 0) | (sw64 ? 1 << 13 : 0) |
-                      (dsa_now ? 1 << 14 : 0) | (dsa_next ? 1 << 15 : 0);
+                      (dsa_now ? 1 << 14 : 0) | (dsa_next ? 1 << 15 : 0) | (tc ? 1 << 16 : 0);
       auto it = W.graphs.find(key);
       if (it == W.graphs.end()) {
         // capture this iteration once; later iterations with the same key replay it
@@ -1643,6 +1658,7 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
           "unknown post_mode");
   RTE_ARG(o->mode == RTE_MODE_FP64 || o->refine_residual == RTE_RESIDUAL_DF || o->refine_residual == RTE_RESIDUAL_FP64,
           "unknown refine_residual");
+  RTE_ARG(o->rom_bf16 == 0 || o->rom_bf16 == 1, "rom_bf16 must be 0 or 1");
   const bool use_dsa = o->post_mode == RTE_POST_DSA;
   if (use_dsa) {
     RTE_ARG(o->dsa_variant == RTE_DSA_PARTIAL || o->dsa_variant == RTE_DSA_LUMPED, "unknown dsa_variant");
@@ -1714,11 +1730,13 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
       RTE_TRY(pl.WT32.ensure((size_t)rm->N * std::max(1, rm->r)));
       k_w_transpose<<<152, 256, 0, st>>>(rm->W.p, rm->N, rm->rmax, rm->r, pl.WT.p, pl.WT32.p);
       count_launch();
+      if (o->rom_bf16 && o->mode == RTE_MODE_MIXED) RTE_TRY(rom_tc_plan_setup(pl, st));
     }
     RTE_CHECK_CUDA(cudaMemcpyAsync(ws->norom.p, C.no_rom_mask.data(), B * sizeof(int), cudaMemcpyHostToDevice, st));
     C.any_rom = any_rom;
     for (int b = 0; b < B; ++b) C.any_norom = C.any_norom || C.no_rom_mask[b] != 0;
     C.dsa = use_dsa;
+    C.rom_tc = o->rom_bf16 && o->mode == RTE_MODE_MIXED;
     if (use_dsa) RTE_TRY(dsa_prepare(p, o->dsa_variant, st));
     std::vector<RomInstDev> ri(B);
     for (int b = 0; b < B; ++b)

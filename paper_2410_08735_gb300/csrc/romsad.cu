@@ -662,14 +662,19 @@ int romsad_galerkin_coefficients(romsad_t rom, rte_problem_t p, double* c_host) 
 
 int romsad_apply(romsad_t rom, rte_problem_t p, int dtype, const void* v, void* z, void* stream) {
   RTE_ARG(rom && p && v && z, "null handle or pointer");
-  RTE_ARG(dtype == RTE_F64, "romsad_apply takes FP64 vectors");
+  RTE_ARG(dtype == RTE_F64 || dtype == RTE_F32, "dtype must be RTE_F64 or RTE_F32");
   for (int b = 0; b < p->B; ++b) RTE_TRY(rom_check_mesh(rom, p, b));
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<int> ids(p->B);
   for (int b = 0; b < p->B; ++b) ids[b] = b;
   RomPlan plan;
   RTE_TRY(plan.build(rom, p, ids, st));
-  RTE_TRY(plan.apply(p, nullptr, (const double*)v, (double*)z, true, st));
+  if (dtype == RTE_F32) {
+    RTE_TRY(rom_tc_plan_setup(plan, st));
+    RTE_TRY(rom_tc_apply(plan, p, nullptr, (const float*)v, (float*)z, st));
+  } else {
+    RTE_TRY(plan.apply(p, nullptr, (const double*)v, (double*)z, true, st));
+  }
   RTE_CHECK_CUDA(cudaStreamSynchronize(st));
   return RTE_OK;
 }

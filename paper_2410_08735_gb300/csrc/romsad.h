@@ -1,5 +1,7 @@
 // ROMSAD data structures shared by romsad.cu, greedy.cu and krylov.cu.
 #pragma once
+#include <cstdint>
+
 #include "internal.h"
 
 struct rte_mlp;
@@ -29,6 +31,8 @@ struct romsad {
   std::vector<double> S_R;     // [R][r][r] P^T chi_R W
   rte::DevBuf<double> d_aff;   // [(1 + 2R)][r][r] device copy: A_D, T_R..., S_R...
   rte_mlp* mlp = nullptr;      // learned warm start (not owned)
+  rte::DevBuf<uint16_t> P16, W16;   // BF16 copies of P32, W32 for the tensor-core products (romsad_tc.cu)
+  int bf16_rank = 0;                // rank the BF16 copies were made at (0: none)
 };
 
 namespace rte {
@@ -61,6 +65,7 @@ struct RomPlan {
   DevBuf<float> inv32;   // FP32 copy of lu (the inverses), filled by the FGMRES driver
   DevBuf<double> WT;     // W transposed [r][N] (coalesced lift), filled by the FGMRES driver
   DevBuf<float> WT32;
+  DevBuf<float> part32, c32;   // tensor-core path: projection partials [nchunk][n][64], coefficients [n][64]
   int chunk = 1024, nchunk = 0;
   int build(romsad* rom, rte_problem* p, const std::vector<int>& ids, cudaStream_t st);
   int apply(rte_problem* p, const int* d_active, const double* v, double* z, bool f64, cudaStream_t st);
@@ -77,5 +82,14 @@ int rom_lift_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, con
 int mlp_predict_instances(rte_mlp* M, rte_problem* p, const int* d_list, const std::vector<int>& list, double* c_out,
                           cudaStream_t st);
 int rom_upload_affine(romsad* rom);
+// Tensor-core ROMSAD products (romsad_tc.cu).  rom_tc_prepare: BF16 copies of P and W at the current rank and
+// the kernels' shared-memory limits on the current device; call it before any stream capture.  rom_tc_apply:
+// z = v + W (U^T A_mu U)^{-1} P^T Sigma_s v for the plan's instances with FP32 vectors (pl.inv32 filled),
+// projection and lift as BF16 mma.sync products with FP32 accumulation.
+int rom_tc_prepare(romsad* rom, cudaStream_t st);
+int rom_tc_apply(RomPlan& pl, rte_problem* p, const int* d_active, const float* v, float* z, cudaStream_t st);
+// Before the first rom_tc_apply of a plan (and before any stream capture): rom_tc_prepare, the plan's partial
+// and coefficient buffers, and the FP32 copy of its inverses (pl.inv32 from pl.lu).
+int rom_tc_plan_setup(RomPlan& pl, cudaStream_t st);
 int rom_build_operators_from_U(romsad* rom, rte_problem* tmpl, int inst, cudaStream_t st);
 }  // namespace rte

@@ -51,13 +51,13 @@ def test_noalloc_first_calls_allocate_nothing_and_match_the_oracle(dim):
     on the FP32-rounded input), in the 2D geometry and in the 1D slab (one task per direction)."""
     torch = torch_cuda()
     B = lib()
-    # load the library's kernels on this device first (module loading may itself take device memory)
-    warm, _, _, _ = _problem(B, seed=63)
+    spec = _spec2d() if dim == 2 else spec1d([48, 80], n_polar=8)
+    # run the same kernels once first: loading a kernel's code on its first launch may itself take device memory
+    warm, _, _, _ = _problem(B, spec, seed=63)
     zw = torch.zeros(warm.n_dof, dtype=torch.float64, device="cuda")
     warm.apply_op_noalloc(zw, torch.empty_like(zw))
     w32 = zw.float()
     warm.apply_op_noalloc(w32, torch.empty_like(w32))
-    spec = _spec2d() if dim == 2 else spec1d([48, 80], n_polar=8)
     gp, spec, ss, sa = _problem(B, spec, seed=64)
     ops = oracle_problems(spec, ss, sa)
     rng = np.random.default_rng(8)
