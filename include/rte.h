@@ -260,10 +260,14 @@ int romsad_destroy(romsad_t rom);
  * this system by algebraic multigrid): 4x4 cell-block Jacobi on the DG level, continuous bilinear
  * elements on the same mesh and on meshes coarsened by 2 (Galerkin operators), one damped Jacobi step
  * per vertex level, a dense solve on the coarsest.  Covers 2D meshes whose cell counts, halved while
- * both are even, end with at most 100 vertices (RTE_ERR_UNSUPPORTED otherwise and for 1D).
- * Arithmetic in FP32 for both dtypes. */
+ * both are even, end with at most 100 vertices (RTE_ERR_UNSUPPORTED otherwise).  Arithmetic in FP32 for both
+ * dtypes.  In the 1D slab (appendix A's own geometry) the systems are solved exactly instead, in FP64: the two
+ * moment equations in the unknowns (dphi, dJ) per cell form a block-tridiagonal system with 4x4 blocks, factored
+ * once per parameter set (block LU) and solved per apply; there RTE_DSA_FULL gives the fully consistent DSA,
+ * RTE_DSA_PARTIAL and RTE_DSA_LUMPED the B_d above (2D: RTE_DSA_FULL is RTE_ERR_UNSUPPORTED). */
 #define RTE_DSA_PARTIAL 0
 #define RTE_DSA_LUMPED 1
+#define RTE_DSA_FULL 2      /* fully consistent (the coupled dphi, dJ system), 1D slab only */
 /* z = M_DSA^{-1} v for every instance of p with its own sigma.  v, z: scalar vectors of dtype
  * (device, not aliased).  Each call redoes the per-parameter set-up (two extra kernels) unless the variant is
  * or-ed with RTE_DSA_KEEP_SETUP, which reuses the set-up of the last call (RTE_ERR_INVALID_ARG if there was

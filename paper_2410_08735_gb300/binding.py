@@ -20,7 +20,7 @@ RTE_ERR_NOT_CONVERGED = 4
 RTE_ERR_NUMERIC = 5
 RTE_F64, RTE_F32, RTE_F64_DF = 0, 1, 2
 RTE_POST_ROM, RTE_POST_IDENTITY, RTE_POST_DSA = 0, 1, 2
-RTE_DSA_PARTIAL, RTE_DSA_LUMPED = 0, 1
+RTE_DSA_PARTIAL, RTE_DSA_LUMPED, RTE_DSA_FULL = 0, 1, 2
 RTE_DSA_KEEP_SETUP = 16
 RTE_MODE_FP64, RTE_MODE_MIXED, RTE_MODE_MIXED_F64KRYLOV = 0, 1, 2
 RTE_RESIDUAL_DF, RTE_RESIDUAL_FP64 = 0, 1

@@ -705,11 +705,180 @@ __global__ void __launch_bounds__(kThreads) k_dsa_vcycle(const InstInfo* inst, c
   }
 }
 
+// ------------------------------------------------------------------------------------------------ 1D slab
+// In the slab the DSA systems are small and banded, so they are solved exactly.  Unknowns per cell c:
+// x_c = (dphi_c0, dphi_c1, dJ_c0, dJ_c1); the two moment equations of appendix A,
+//   (Sigma_a - kappa D_J) dphi + 3 mu2 D_C dJ = Sigma_s v,   mu2 D_C dphi + B dJ = 0,
+// with B = 3 mu2 Sigma_t - 3/2 c D_J (fully consistent), its cell-diagonal blocks (lumped) or 3 mu2 Sigma_t
+// (partially consistent), are block tridiagonal in the cells with 4x4 blocks (D_C and D_J couple a cell to its two
+// neighbours only).  Eliminating dJ from the partially consistent form gives the appendix's
+// K_PC = Sigma_a - kappa D_J - mu2 D_C Sigma_t^{-1} D_C exactly.  Block LU without inter-block pivoting (block
+// Thomas), partial pivoting inside each 4x4 inversion, FP64, one thread per instance: the factors
+// G_c^{-1} and M_c = L_c G_{c-1}^{-1} at set-up, forward and back substitution per apply.
+//
+// 2x2 blocks of D_C and D_J on a cell of width h (orthonormal Legendre, lo = (s, -sqrt3 s), hi = (s, sqrt3 s),
+// s = 1/sqrt h; [f] = f(high side) - f(low side), {f} the mean; exterior traces zero):
+//   diagonal:  D_C = -V - 1/2 lo lo^T + 1/2 hi hi^T,  V_10 = 2 sqrt3 / h;   D_J = -lo lo^T - hi hi^T
+//   (c, c-1):  D_C = -1/2 lo hi^T,   D_J = lo hi^T
+//   (c, c+1):  D_C =  1/2 hi lo^T,   D_J = hi lo^T                      (entry (k, l) = (test, trial))
+__device__ void dsa1d_blocks(double h, double sa, double st, double mu2, double kap, double c11, int variant,
+                             bool lower, bool upper, double* Dg, double* L, double* U) {
+  const double s = 1.0 / sqrt(h), s3 = 1.7320508075688772;
+  const double lo[2] = {s, -s3 * s}, hi[2] = {s, s3 * s};
+  double dc[4], dj[4], lc[4], lj[4], uc[4], uj[4];
+  for (int k = 0; k < 2; ++k)
+    for (int l = 0; l < 2; ++l) {
+      dc[k * 2 + l] = -0.5 * lo[k] * lo[l] + 0.5 * hi[k] * hi[l];
+      dj[k * 2 + l] = -lo[k] * lo[l] - hi[k] * hi[l];
+      lc[k * 2 + l] = -0.5 * lo[k] * hi[l];
+      lj[k * 2 + l] = lo[k] * hi[l];
+      uc[k * 2 + l] = 0.5 * hi[k] * lo[l];
+      uj[k * 2 + l] = hi[k] * lo[l];
+    }
+  dc[2] -= 2.0 * s3 / h;   // -V: entry (1, 0)
+  for (int e = 0; e < 16; ++e) { Dg[e] = 0.0; L[e] = 0.0; U[e] = 0.0; }
+  // rows 0-1: dphi equation; rows 2-3: dJ equation; columns likewise
+  for (int k = 0; k < 2; ++k)
+    for (int l = 0; l < 2; ++l) {
+      const int e = k * 2 + l;
+      Dg[k * 4 + l] = (k == l ? sa : 0.0) - kap * dj[e];
+      Dg[k * 4 + 2 + l] = 3.0 * mu2 * dc[e];
+      Dg[(2 + k) * 4 + l] = mu2 * dc[e];
+      Dg[(2 + k) * 4 + 2 + l] = (k == l ? 3.0 * mu2 * st : 0.0) - (variant == RTE_DSA_PARTIAL ? 0.0 : 1.5 * c11 * dj[e]);
+      if (lower) {
+        L[k * 4 + l] = -kap * lj[e];
+        L[k * 4 + 2 + l] = 3.0 * mu2 * lc[e];
+        L[(2 + k) * 4 + l] = mu2 * lc[e];
+        L[(2 + k) * 4 + 2 + l] = variant == RTE_DSA_FULL ? -1.5 * c11 * lj[e] : 0.0;
+      }
+      if (upper) {
+        U[k * 4 + l] = -kap * uj[e];
+        U[k * 4 + 2 + l] = 3.0 * mu2 * uc[e];
+        U[(2 + k) * 4 + l] = mu2 * uc[e];
+        U[(2 + k) * 4 + 2 + l] = variant == RTE_DSA_FULL ? -1.5 * c11 * uj[e] : 0.0;
+      }
+    }
+}
+
+// inverse of a 4x4 matrix by Gauss-Jordan with partial pivoting (A destroyed); false if singular
+__device__ bool inv4(double* A, double* X) {
+  for (int e = 0; e < 16; ++e) X[e] = (e / 4 == e % 4) ? 1.0 : 0.0;
+  for (int c = 0; c < 4; ++c) {
+    int piv = c;
+    for (int i = c + 1; i < 4; ++i)
+      if (fabs(A[i * 4 + c]) > fabs(A[piv * 4 + c])) piv = i;
+    if (A[piv * 4 + c] == 0.0) return false;
+    if (piv != c)
+      for (int j = 0; j < 4; ++j) {
+        double t = A[c * 4 + j]; A[c * 4 + j] = A[piv * 4 + j]; A[piv * 4 + j] = t;
+        t = X[c * 4 + j]; X[c * 4 + j] = X[piv * 4 + j]; X[piv * 4 + j] = t;
+      }
+    const double d = 1.0 / A[c * 4 + c];
+    for (int j = 0; j < 4; ++j) { A[c * 4 + j] *= d; X[c * 4 + j] *= d; }
+    for (int i = 0; i < 4; ++i) {
+      if (i == c) continue;
+      const double f = A[i * 4 + c];
+      for (int j = 0; j < 4; ++j) { A[i * 4 + j] -= f * A[c * 4 + j]; X[i * 4 + j] -= f * X[c * 4 + j]; }
+    }
+  }
+  return true;
+}
+
+__device__ void mm4(const double* A, const double* B, double* C) {
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double v = 0.0;
+      for (int k = 0; k < 4; ++k) v += A[i * 4 + k] * B[k * 4 + j];
+      C[i * 4 + j] = v;
+    }
+}
+
+// set-up: one thread per instance; f = [cell][Ginv 16 | M 16 | U 16]
+__global__ void k_dsa1d_setup(const InstInfo* inst, int B, const long long* o1d, const double* sig_s,
+                              const double* sig_t, int R, int rx, double mu2, double kap, double c11, int variant,
+                              double* f, int* bad) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const InstInfo in = inst[b];
+  const int nx = in.nx, cx = nx / rx;
+  double* fb = f + o1d[b] * 48;
+  double Dg[16], L[16], U[16], G[16], T[16];
+  for (int c = 0; c < nx; ++c) {
+    const int reg = c / cx;
+    const double st = sig_t[(size_t)b * R + reg], ss = sig_s[(size_t)b * R + reg];
+    dsa1d_blocks(in.hx, st - ss, st, mu2, kap, c11, variant, c > 0, c < nx - 1, Dg, L, U);
+    double* fc = fb + (size_t)c * 48;
+    if (c > 0) {
+      // M_c = L_c G_{c-1}^{-1};  G_c = Dg_c - M_c U_{c-1}
+      const double* fp = fb + (size_t)(c - 1) * 48;
+      mm4(L, fp, fc + 16);
+      mm4(fc + 16, fp + 32, T);
+      for (int e = 0; e < 16; ++e) G[e] = Dg[e] - T[e];
+    } else {
+      for (int e = 0; e < 16; ++e) { G[e] = Dg[e]; fc[16 + e] = 0.0; }
+    }
+    if (!inv4(G, fc)) { *bad = 1; return; }
+    for (int e = 0; e < 16; ++e) fc[32 + e] = U[e];
+  }
+}
+
+// z = v + dphi, dphi from the exact solve with right-hand side (Sigma_s v, 0); one thread per instance
+template <typename TV>
+__global__ void k_dsa1d_apply(const InstInfo* inst, int B, const long long* o1d, const double* sig_s, int R, int rx,
+                              const double* f, double* y, const TV* v, TV* z, const int* active, const int* only) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  if ((active && !active[b]) || (only && !only[b])) return;
+  const InstInfo in = inst[b];
+  const int nx = in.nx, cx = nx / rx;
+  const double* fb = f + o1d[b] * 48;
+  double* yb = y + o1d[b] * 4;
+  const TV* vb = v + in.off;
+  TV* zb = z + in.off;
+  double prev[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int c = 0; c < nx; ++c) {   // forward: y_c = b_c - M_c y_{c-1}
+    const double ss = sig_s[(size_t)b * R + c / cx];
+    double bc[4] = {ss * (double)vb[2 * c], ss * (double)vb[2 * c + 1], 0.0, 0.0};
+    const double* M = fb + (size_t)c * 48 + 16;
+    for (int i = 0; i < 4; ++i) {
+      double t = bc[i];
+      for (int k = 0; k < 4; ++k) t -= M[i * 4 + k] * prev[k];
+      yb[c * 4 + i] = t;
+    }
+    for (int i = 0; i < 4; ++i) prev[i] = yb[c * 4 + i];
+  }
+  double next[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int c = nx - 1; c >= 0; --c) {   // back: x_c = G_c^{-1} (y_c - U_c x_{c+1})
+    const double* Gi = fb + (size_t)c * 48;
+    const double* U = fb + (size_t)c * 48 + 32;
+    double r[4], x[4];
+    for (int i = 0; i < 4; ++i) {
+      double t = yb[c * 4 + i];
+      for (int k = 0; k < 4; ++k) t -= U[i * 4 + k] * next[k];
+      r[i] = t;
+    }
+    for (int i = 0; i < 4; ++i) {
+      double t = 0.0;
+      for (int k = 0; k < 4; ++k) t += Gi[i * 4 + k] * r[k];
+      x[i] = t;
+    }
+    zb[2 * c] = (TV)((double)vb[2 * c] + x[0]);
+    zb[2 * c + 1] = (TV)((double)vb[2 * c + 1] + x[1]);
+    for (int i = 0; i < 4; ++i) next[i] = x[i];
+  }
+}
+
 struct DsaWs {
   DevBuf<float> data;
   DevBuf<DsaInst> d_di;
   std::vector<DsaInst> di;
   int lumped = -1;
+  int variant = -1;            // variant of the last set-up
+  // 1D slab: exact block-tridiagonal factors, per instance and cell [Ginv 16 | M 16 | U 16] doubles, and the
+  // forward-sweep vectors [4] per cell
+  DevBuf<double> f1d, y1d;
+  std::vector<long long> o1d;  // [B+1] cell offsets
+  DevBuf<long long> d_o1d;
 };
 
 DsaWs* get_dsa_ws(rte_problem* p) {
@@ -817,13 +986,56 @@ DsaConst dsa_constants(rte_problem* p, int variant) {
 }  // namespace
 
 int dsa_check(rte_problem* p) {
+  if (p->dim == 1) return RTE_OK;   // exact block-tridiagonal solve, any slab mesh
   std::vector<DsaInst> di;
   long long total = 0;
   return dsa_layout(p, di, total);
 }
 
+static int dsa1d_prepare(rte_problem* p, int variant, cudaStream_t st) {
+  DsaWs* w = get_dsa_ws(p);
+  if (w->o1d.empty()) {
+    w->o1d.assign(p->B + 1, 0);
+    for (int b = 0; b < p->B; ++b) w->o1d[b + 1] = w->o1d[b] + p->nx[b];
+    RTE_TRY(w->f1d.alloc((size_t)w->o1d[p->B] * 48));
+    RTE_TRY(w->y1d.alloc((size_t)w->o1d[p->B] * 4));
+    RTE_TRY(w->d_o1d.alloc(p->B + 1));
+    RTE_CHECK_CUDA(cudaMemcpy(w->d_o1d.p, w->o1d.data(), (p->B + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+  }
+  // angular moments of the slab quadrature: mu2 = sum w mu^2, kappa = sum_{mu>0} w mu, c = sum w mu^2 |mu|
+  double mu2 = 0.0, kap = 0.0, c11 = 0.0;
+  for (size_t j = 0; j < p->w.size(); ++j) {
+    const double mu = p->om_x[j];
+    mu2 += p->w[j] * mu * mu;
+    if (mu > 0) kap += p->w[j] * mu;
+    c11 += p->w[j] * mu * mu * std::fabs(mu);
+  }
+  DevBuf<int> bad;
+  RTE_TRY(bad.alloc(1));
+  RTE_CHECK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(int), st));
+  k_dsa1d_setup<<<(p->B + 63) / 64, 64, 0, st>>>(p->d_inst.p, p->B, w->d_o1d.p, p->d_sig_s.p, p->d_sig_t.p, p->R,
+                                                 p->rx, mu2, kap, c11, variant, w->f1d.p, bad.p);
+  count_launch();
+  RTE_CHECK_CUDA(cudaGetLastError());
+  int hbad = 0;
+  RTE_CHECK_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  RTE_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (hbad) {
+    set_error("DSA (1D): a block of the factorisation is singular (a region with sigma_t = 0?)");
+    return RTE_ERR_NUMERIC;
+  }
+  w->variant = variant;
+  w->lumped = variant == RTE_DSA_LUMPED ? 1 : 0;
+  return RTE_OK;
+}
+
 int dsa_prepare(rte_problem* p, int variant, cudaStream_t st) {
-  RTE_ARG(variant == RTE_DSA_PARTIAL || variant == RTE_DSA_LUMPED, "unknown DSA variant");
+  RTE_ARG(variant == RTE_DSA_PARTIAL || variant == RTE_DSA_LUMPED || variant == RTE_DSA_FULL, "unknown DSA variant");
+  if (p->dim == 1) return dsa1d_prepare(p, variant, st);
+  if (variant == RTE_DSA_FULL) {
+    set_error("DSA: the fully consistent variant is solved exactly in the 1D slab only");
+    return RTE_ERR_UNSUPPORTED;
+  }
   DsaWs* w = get_dsa_ws(p);
   if (w->di.empty()) {
     long long total = 0;
@@ -842,12 +1054,29 @@ int dsa_prepare(rte_problem* p, int variant, cudaStream_t st) {
   count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   w->lumped = k.lumped;
+  w->variant = variant;
   return RTE_OK;
 }
 
 int dsa_launch(rte_problem* p, bool f64, const void* v, void* z, const int* active, const int* only,
                cudaStream_t st) {
   DsaWs* w = get_dsa_ws(p);
+  if (p->dim == 1) {
+    if (w->variant < 0 || w->o1d.empty()) {
+      set_error("DSA: set-up missing");
+      return RTE_ERR_INVALID_ARG;
+    }
+    const unsigned g = (unsigned)((p->B + 63) / 64);
+    if (f64)
+      k_dsa1d_apply<double><<<g, 64, 0, st>>>(p->d_inst.p, p->B, w->d_o1d.p, p->d_sig_s.p, p->R, p->rx, w->f1d.p,
+                                              w->y1d.p, (const double*)v, (double*)z, active, only);
+    else
+      k_dsa1d_apply<float><<<g, 64, 0, st>>>(p->d_inst.p, p->B, w->d_o1d.p, p->d_sig_s.p, p->R, p->rx, w->f1d.p,
+                                             w->y1d.p, (const float*)v, (float*)z, active, only);
+    count_launch();
+    RTE_CHECK_CUDA(cudaGetLastError());
+    return RTE_OK;
+  }
   if (w->di.empty() || w->lumped < 0) {
     set_error("DSA: set-up missing");
     return RTE_ERR_INVALID_ARG;
@@ -892,9 +1121,8 @@ extern "C" int rte_dsa_apply(rte_problem_t p, int variant, int dtype, const void
   if (keep) {
     // reuse the set-up of an earlier call (it must exist and be of the same variant)
     DsaWs* w = get_dsa_ws(p);
-    RTE_ARG(!w->di.empty() && w->lumped == (variant == RTE_DSA_LUMPED ? 1 : 0),
+    RTE_ARG(w->variant >= 0 && w->variant == variant,
             "RTE_DSA_KEEP_SETUP needs an earlier set-up of the same variant");
-    RTE_ARG(variant == RTE_DSA_PARTIAL || variant == RTE_DSA_LUMPED, "unknown DSA variant");
   } else {
     RTE_TRY(dsa_prepare(p, variant, st));
   }

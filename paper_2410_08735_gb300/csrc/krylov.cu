@@ -1661,7 +1661,8 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
   RTE_ARG(o->rom_bf16 == 0 || o->rom_bf16 == 1, "rom_bf16 must be 0 or 1");
   const bool use_dsa = o->post_mode == RTE_POST_DSA;
   if (use_dsa) {
-    RTE_ARG(o->dsa_variant == RTE_DSA_PARTIAL || o->dsa_variant == RTE_DSA_LUMPED, "unknown dsa_variant");
+    RTE_ARG(o->dsa_variant == RTE_DSA_PARTIAL || o->dsa_variant == RTE_DSA_LUMPED || o->dsa_variant == RTE_DSA_FULL,
+            "unknown dsa_variant");
     RTE_TRY(dsa_check(p));
   }
   if (roms)
@@ -2132,7 +2133,8 @@ extern "C" int si_solve(rte_problem_t p, const romsad_t* roms, const fgmres_opts
   }
   const bool use_dsa = o->post_mode == RTE_POST_DSA;
   if (use_dsa) {
-    RTE_ARG(o->dsa_variant == RTE_DSA_PARTIAL || o->dsa_variant == RTE_DSA_LUMPED, "unknown dsa_variant");
+    RTE_ARG(o->dsa_variant == RTE_DSA_PARTIAL || o->dsa_variant == RTE_DSA_LUMPED || o->dsa_variant == RTE_DSA_FULL,
+            "unknown dsa_variant");
     RTE_TRY(dsa_check(p));
   }
   const int B = p->B;

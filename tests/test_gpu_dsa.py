@@ -50,16 +50,73 @@ def test_dsa_apply_matches_the_oracle_vcycle(variant, dtype):
 def test_dsa_rejects_meshes_it_does_not_cover():
     B = lib()
     torch = torch_cuda()
-    for spec in (spec1d([16]), spec2d([44], [44])):      # 1D; 44 -> 22 -> 11: 12 x 12 coarsest vertices
-        ss, sa = wl.draw_params(spec, 1, 52)
-        gp = B.Problem(spec, ss, sa)
-        v = torch.zeros(gp.n_dof, dtype=torch.float64, device="cuda")
-        with pytest.raises(B.RteError) as e:
-            gp.dsa_apply(v, torch.empty_like(v))
-        assert e.value.status == 7
-        with pytest.raises(B.RteError) as e:
-            _solve_gpu(B, gp, None, restart=10, rtol=1e-8, max_iter=10, post_mode=B.RTE_POST_DSA)
-        assert e.value.status == 7
+    spec = spec2d([44], [44])      # 44 -> 22 -> 11: 12 x 12 coarsest vertices
+    ss, sa = wl.draw_params(spec, 1, 52)
+    gp = B.Problem(spec, ss, sa)
+    v = torch.zeros(gp.n_dof, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.RteError) as e:
+        gp.dsa_apply(v, torch.empty_like(v))
+    assert e.value.status == 7
+    with pytest.raises(B.RteError) as e:
+        _solve_gpu(B, gp, None, restart=10, rtol=1e-8, max_iter=10, post_mode=B.RTE_POST_DSA)
+    assert e.value.status == 7
+    # the fully consistent variant is solved exactly in the slab only
+    gp2 = B.Problem(spec2d([16], [16]), ss, sa)
+    v2 = torch.zeros(gp2.n_dof, dtype=torch.float64, device="cuda")
+    with pytest.raises(B.RteError) as e:
+        gp2.dsa_apply(v2, torch.empty_like(v2), variant=B.RTE_DSA_FULL)
+    assert e.value.status == 7
+
+
+@pytest.mark.parametrize("variant", ["full", "partial", "lumped"])
+def test_dsa_1d_exact_solve_matches_the_oracle(variant):
+    """1D slab (appendix A's geometry): the exact block-tridiagonal DSA solve of each variant equals the oracle's
+    sparse direct solve of the same system (1e-12), on uneven meshes in one call, FP64 and FP32 vectors."""
+    torch = torch_cuda()
+    B = lib()
+    from oracle import dsa as ODSA
+    spec = spec1d([128, 40, 64], n_polar=16)
+    ss, sa = wl.draw_params(spec, 3, 53)
+    gp = B.Problem(spec, ss, sa)
+    ops = oracle_problems(spec, ss, sa)
+    code = {"full": B.RTE_DSA_FULL, "partial": B.RTE_DSA_PARTIAL, "lumped": B.RTE_DSA_LUMPED}[variant]
+    v = np.random.default_rng(54).standard_normal(gp.n_dof)
+    z = torch.empty(gp.n_dof, dtype=torch.float64, device="cuda")
+    gp.dsa_apply(to_dev(v), z, variant=code)
+    z32 = torch.empty(gp.n_dof, dtype=torch.float32, device="cuda")
+    gp.dsa_apply(to_dev(v, torch.float32), z32, variant=code)
+    h, h32 = z.cpu().numpy(), z32.cpu().numpy().astype(np.float64)
+    for b, op in enumerate(ops):
+        vb = split(v, gp.offsets)[b]
+        ref = ODSA.Dsa(op, variant).apply(vb)
+        assert rel(split(h, gp.offsets)[b], ref) < 1e-12, b
+        ref32 = ODSA.Dsa(op, variant).apply(vb.astype(np.float32).astype(np.float64))
+        assert rel(split(h32, gp.offsets)[b], ref32) < 1e-6, b
+
+
+def test_gmres_dsa_1d_fully_consistent_matches_the_oracle():
+    """FGMRES with the fully consistent DSA (exact) on the 1D slab workload: phi within 1e-10 of the oracle's
+    solution and the same iteration count within 1; fewer iterations than with the partially consistent form."""
+    torch = torch_cuda()
+    B = lib()
+    from oracle import romsad as ORS
+    spec = wl.config(1).with_instances([128, 128], [1, 1])
+    ss, sa = wl.draw_params(spec, 2, 55)
+    gp = B.Problem(spec, ss, sa)
+    ops = oracle_problems(spec, ss, sa)
+    its = {}
+    for variant, code, post in (("full", B.RTE_DSA_FULL, "dsa"), ("partial", B.RTE_DSA_PARTIAL, "dsa_pc")):
+        phi = torch.zeros(gp.n_dof, dtype=torch.float64, device="cuda")
+        st = B.fgmres_solve(gp, None, phi, restart=30, rtol=1e-12, max_iter=500, post_mode=B.RTE_POST_DSA,
+                            dsa_variant=code)
+        h = phi.cpu().numpy()
+        its[variant] = [x["iterations"] for x in st]
+        for b, op in enumerate(ops):
+            ref, ost = ORS.solve(op, None, post=post, restart=30, rtol=1e-12, max_iter=500)
+            assert st[b]["status"] == 0
+            assert rel(split(h, gp.offsets)[b], ref) < 1e-10, (variant, b)
+            assert abs(st[b]["iterations"] - ost.iterations) <= 1, (variant, b, st[b]["iterations"], ost.iterations)
+    assert sum(its["full"]) <= sum(its["partial"])
 
 
 @pytest.mark.parametrize("variant", ["partial", "lumped"])
