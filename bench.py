@@ -638,6 +638,51 @@ def collect_refs(pool, jobs, timeout_s):
     return refs, meta
 
 
+def profile_target(args):
+    """One launch of a kernel of the headline path inside the NVTX range "profile" (for ncu --nvtx-include
+    "profile/"), after its autotuning and warm-up: the A~ apply in FP32, FP64 or double-float on the first
+    --profile-instances instances of the workload, the DSA V-cycle (set-up reused), or the tensor-core ROMSAD apply
+    (romsad_apply with FP32 vectors, a rank-32 orthonormal basis on 128x128 meshes with 32 directions)."""
+    import torch
+    from paper_2410_08735_gb300 import binding as RB
+    RB.load()
+    spec, B, cfg = workload_spec(args.workload)
+    nb = max(1, min(args.profile_instances, B))
+    what = args.profile
+    if what == "rom_tc":
+        spec = dataclasses.replace(wl.config(2), n_polar=2, n_azim=16).with_instances([128] * nb, [128] * nb)
+    else:
+        spec = spec.with_instances(spec.nx[:nb], spec.ny[:nb])
+    ss, sa = wl.draw_params(spec, nb, wl.seed_for(cfg, 1))
+    prob = RB.Problem(spec, ss, sa)
+    z = torch.randn(prob.n_dof, dtype=torch.float64, device="cuda")
+    w = torch.empty_like(z)
+    z32, w32 = z.float(), torch.empty(prob.n_dof, dtype=torch.float32, device="cuda")
+    if what == "rom_tc":
+        one = RB.Problem(spec.with_instances(spec.nx[:1], spec.ny[:1]), ss[:1], sa[:1])
+        n_a = spec.n_directions * prob.n_dof // nb
+        U, _ = np.linalg.qr(np.random.default_rng(0).standard_normal((n_a, 32)))
+        rom = RB.Rom.from_basis(one, np.ascontiguousarray(U.T.reshape(32, spec.n_directions, -1)), instance=0)
+        fn = lambda: rom.apply(prob, z32, w32)
+    elif what == "dsa":
+        prob.dsa_apply(z32, w32)
+        fn = lambda: prob.dsa_apply(z32, w32, variant=RB.RTE_DSA_KEEP_SETUP)
+    elif what == "sweep_f32":
+        fn = lambda: prob.apply_op(z32, w32)
+    elif what == "sweep_f64":
+        fn = lambda: prob.apply_op(z, w)
+    else:
+        fn = lambda: prob.apply_op(z, w, double_float=True)
+    for _ in range(2):   # autotuning and warm-up
+        fn()
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("profile")
+    fn()
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": what, "instances": nb, "n_dof": prob.n_dof}))
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -663,7 +708,13 @@ def main():
                     help="reference arm: iterations of a full solve for the extrapolation (default: the GPU's FP64 "
                          "count on this workload)")
     ap.add_argument("--ref-cores", type=int, default=0, help="reference arm: oracle processes (0: all host cores)")
+    ap.add_argument("--profile", default=None, choices=["sweep_f32", "sweep_f64", "sweep_df", "dsa", "rom_tc"],
+                    help="run one launch of that kernel inside the NVTX range 'profile' (an ncu target) and exit")
+    ap.add_argument("--profile-instances", type=int, default=16)
     args = ap.parse_args()
+    if args.profile:
+        profile_target(args)
+        return
     spec, B, cfg = workload_spec(args.workload)
     restart = spec.restart if args.restart is None else args.restart
     world, rank, local = dist_setup()

