@@ -651,14 +651,36 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && D <= 4) ? 2 : 1) k_swe
   int* xreg = reinterpret_cast<int*>(ybuf + (((size_t)(nwarps > 1 ? nwarps - 1 : 1) * D * nx * 2 + 3) & ~(size_t)3));
   const int cx = nx / a.rx, cy = ny / a.ry;
   for (int e = threadIdx.x; e < nx; e += blockDim.x) xreg[e] = e / cx;
+  // per-task parameters, computed once per task by the loading threads (the FP64 divisions of the direction
+  // coefficients must not run once per lane): coefficients, inflow traces, signs, partial-flux offset
+  __shared__ T s_al[2][D], s_be[2][D], s_wg[2][D], s_bnd[2][2];
+  __shared__ int s_sgn[2][2];
+  __shared__ long long s_poff[2];
   auto load_table = [&](int k) {
     const SweepTask tk = a.tasks[klist[k]];
+    const int bf = k & 1;
     const T* linv = reinterpret_cast<const T*>(a.linv) + ((size_t)tk.b * a.nu + tk.u0) * R * 16;
-    T* dst = tab + (size_t)(k & 1) * D * R * 16;
+    T* dst = tab + (size_t)bf * D * R * 16;
     for (int e = threadIdx.x; e < D * R * 16; e += blockDim.x) dst[e] = linv[e];
     if (a.sig_s)
       for (int e = threadIdx.x; e < R; e += blockDim.x)
-        sgs[(k & 1) * R4 + e] = reinterpret_cast<const T*>(a.sig_s)[(size_t)tk.b * R + e];
+        sgs[bf * R4 + e] = reinterpret_cast<const T*>(a.sig_s)[(size_t)tk.b * R + e];
+    if (threadIdx.x < D) {
+      const InstInfo in = a.inst[tk.b];
+      const UDir u = a.udir[tk.u0 + threadIdx.x];
+      s_al[bf][threadIdx.x] = (T)(u.ax / in.hx);
+      s_be[bf][threadIdx.x] = (T)(u.ay / in.hy);
+      s_wg[bf][threadIdx.x] = (T)u.w;
+    } else if (threadIdx.x == D) {
+      const InstInfo in = a.inst[tk.b];
+      const int tsx = a.udir[tk.u0].sx, tsy = a.udir[tk.u0].sy;
+      const double gtr = a.with_bc ? in.g * sqrt(in.hx * in.hy) : 0.0;
+      s_bnd[bf][0] = (a.inflow_mask & (tsx > 0 ? 1 : 2)) ? (T)gtr : (T)0;
+      s_bnd[bf][1] = (a.inflow_mask & (tsy > 0 ? 4 : 8)) ? (T)gtr : (T)0;
+      s_sgn[bf][0] = tsx;
+      s_sgn[bf][1] = tsy;
+      s_poff[bf] = (long long)a.tasks_per_inst * in.off + (long long)tk.t * in.ndof;
+    }
   };
   load_table(0);
   __syncthreads();
@@ -671,7 +693,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && D <= 4) ? 2 : 1) k_swe
   // state of the task the lane works on (k) and of the task its prefetch cursor is in (kp)
   int k = -1, col = -((32 + SK) * band + lane) - 1;   // advanced to step 0 below
   int kp = -1, colp = col + PF;
-  T al[D], be[D], wg[D], wg1[D], wg2[D], wg3[D];
+  T al[D], be[D], wg[D];
   T bndx = (T)0, bndy = (T)0;
   int sx = 1, sy = 1, rowreg = 0;
   long long rowbase = 0;
@@ -680,29 +702,23 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && D <= 4) ? 2 : 1) k_swe
   long long rowbase_p = 0;
   int sxp = 1;
 #pragma unroll
-  for (int d = 0; d < D; ++d) { al[d] = be[d] = wg[d] = wg1[d] = wg2[d] = wg3[d] = (T)0; }
-  auto enter_task = [&](int kk) {   // the lane's current task becomes kk
-    const SweepTask tk = a.tasks[klist[kk]];
-    const InstInfo in = a.inst[tk.b];
-    sx = a.udir[tk.u0].sx;
-    sy = a.udir[tk.u0].sy;
+  for (int d = 0; d < D; ++d) { al[d] = be[d] = wg[d] = (T)0; }
+  auto enter_task = [&](int kk) {   // the lane's current task becomes kk (its parameters are in buffer kk & 1)
+    const int bf = kk & 1;
+    sx = s_sgn[bf][0];
+    sy = s_sgn[bf][1];
 #pragma unroll
     for (int d = 0; d < D; ++d) {
-      const UDir u = a.udir[tk.u0 + d];
-      al[d] = (T)(u.ax / in.hx);
-      be[d] = (T)(u.ay / in.hy);
-      wg[d] = (T)u.w;
-      wg1[d] = sx > 0 ? wg[d] : -wg[d];
-      wg2[d] = sy > 0 ? wg[d] : -wg[d];
-      wg3[d] = sx * sy > 0 ? wg[d] : -wg[d];
+      al[d] = s_al[bf][d];
+      be[d] = s_be[bf][d];
+      wg[d] = s_wg[bf][d];
     }
-    const double gtr = a.with_bc ? in.g * sqrt(in.hx * in.hy) : 0.0;
-    bndx = (a.inflow_mask & (sx > 0 ? 1 : 2)) ? (T)gtr : (T)0;
-    bndy = (a.inflow_mask & (sy > 0 ? 4 : 8)) ? (T)gtr : (T)0;
+    bndx = s_bnd[bf][0];
+    bndy = s_bnd[bf][1];
     const int iy = sy > 0 ? row : ny - 1 - row;
     rowbase = (long long)(rowok ? iy : 0) * nx;
     rowreg = rowok ? (iy / cy) * a.rx : 0;
-    part = reinterpret_cast<T*>(a.partial) + (size_t)a.tasks_per_inst * in.off + (size_t)tk.t * in.ndof;
+    part = reinterpret_cast<T*>(a.partial) + s_poff[bf];
   };
   auto enter_prefetch = [&](int kk) {
     const SweepTask tk = a.tasks[klist[kk]];
@@ -817,15 +833,19 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && D <= 4) ? 2 : 1) k_swe
           ty0[d] = p0 + S3 * p2;
           ty1[d] = p1 + S3 * p3;
           acc0 += wg[d] * p0;
-          acc1 += wg1[d] * p1;
-          acc2 += wg2[d] * p2;
-          acc3 += wg3[d] * p3;
+          acc1 += wg[d] * p1;
+          acc2 += wg[d] * p2;
+          acc3 += wg[d] * p3;
           if (lane == 31 && band + 1 < nb) {
             T* yb = ybuf + (size_t)band * D * nx * 2;
             yb[(d * nx + col) * 2] = ty0[d];
             yb[(d * nx + col) * 2 + 1] = ty1[d];
           }
         }
+        // odd modes back from the reflected frame (the task's directions share its quadrant)
+        acc1 = sx > 0 ? acc1 : -acc1;
+        acc2 = sy > 0 ? acc2 : -acc2;
+        acc3 = (sx * sy) > 0 ? acc3 : -acc3;
         Vec4<T>::store(part + 4 * c, acc0, acc1, acc2, acc3);
       }
       if (nwarps > 1 && kk == PF - 1) __syncthreads();

@@ -101,3 +101,16 @@ def test_greedy_fp32_indicator_picks_the_oracle_samples():
     assert rep_g["sampled"] == rep_o.sampled
     n_ind = len(rep_o.max_indicator)
     np.testing.assert_allclose(rep_g["max_indicator"][:n_ind], rep_o.max_indicator, rtol=1e-4)
+
+
+def test_greedy_on_the_pincell_template_keeps_its_gaussian_source():
+    """The greedy's sub-problems take the template's source kind: on the pin-cell problem (Gaussian source,
+    CL(30, 6), FGMRES-DSA high-fidelity solves) the GPU greedy picks the oracle greedy's samples and reproduces its
+    basis and Galerkin labels, which a box source in the sub-problems would change (its b~ is zero here)."""
+    import dataclasses
+    spec = dataclasses.replace(wl.pincell().with_mesh(16, 16), n_azim=30, n_polar=6)
+    pts = [(a, s) for a in (0.05, 0.275, 0.5) for s in (0.05, 0.5)]
+    tr = [wl.pincell_params(a, s) for a, s in pts]
+    ss = np.array([x[0] for x in tr])
+    sa = np.array([x[1] for x in tr])
+    _compare(spec, ss, sa, window=2, max_iter=3, max_rank=6, restart=30, hf_dsa=True, tol=1e-4)
