@@ -655,6 +655,9 @@ def profile_target(args):
         spec = spec.with_instances(spec.nx[:nb], spec.ny[:nb])
     ss, sa = wl.draw_params(spec, nb, wl.seed_for(cfg, 1))
     prob = RB.Problem(spec, ss, sa)
+    if args.profile_pin:   # the kernel instantiation the full-size workload's autotuner picked
+        var, D = (int(x) for x in args.profile_pin.split(","))
+        prob.set_sweep_variant(var, D)
     z = torch.randn(prob.n_dof, dtype=torch.float64, device="cuda")
     w = torch.empty_like(z)
     z32, w32 = z.float(), torch.empty(prob.n_dof, dtype=torch.float32, device="cuda")
@@ -711,6 +714,7 @@ def main():
     ap.add_argument("--profile", default=None, choices=["sweep_f32", "sweep_f64", "sweep_df", "dsa", "rom_tc"],
                     help="run one launch of that kernel inside the NVTX range 'profile' (an ncu target) and exit")
     ap.add_argument("--profile-instances", type=int, default=16)
+    ap.add_argument("--profile-pin", default=None, help="with --profile: pin the sweep kernel as 'variant,D'")
     args = ap.parse_args()
     if args.profile:
         profile_target(args)
@@ -762,6 +766,9 @@ def main():
         # headline: all-FP32 inner solves, learned start, double-float refinement residuals, FP64 certification
         ("mixed", lambda: RB.fgmres_solve(prob, roms, phi, mode=RB.RTE_MODE_MIXED, learned_warm_start=True,
                                           **mixed_kw, **common)),
+        # the same with the ROM window's projection and lift on the tensor cores (BF16 operands, FP32 accumulation)
+        ("mixed_rom_bf16", lambda: RB.fgmres_solve(prob, roms, phi, mode=RB.RTE_MODE_MIXED, learned_warm_start=True,
+                                                   rom_bf16=True, **mixed_kw, **common)),
         # the precision form of the method statement: FP32 sweeps, FP64 Krylov vectors, MGS and Givens
         ("mixed_fp64_krylov", lambda: RB.fgmres_solve(prob, roms, phi, mode=RB.RTE_MODE_MIXED_F64KRYLOV,
                                                       learned_warm_start=True, **mixed_kw, **common)),
@@ -867,7 +874,7 @@ def main():
         roof = {"kernel": dom, "bound": "hbm", "achieved": vbytes / (ms_v * 1e-3) / 1e9, "peak": hbm_peak,
                 "unit": "GB/s", "ms_per_launch": ms_v}
     roof["frac"] = roof["achieved"] / roof["peak"] if roof.get("peak") else None
-    roof["traffic"] = None   # filled from the committed ncu capture of the same kernel, when current
+    roof["traffic"] = ncu_traffic(args.workload, dom)
     roof["peak_source"] = "measured: rte_fma_peak (FP32 / FP64 FMA), MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"
     roof["shares_ms_per_solve_batch"] = shares
     roof["solve_batch_ms"] = per_solve_ms
@@ -921,6 +928,7 @@ def main():
         "solver": {k: v for k, v in head.items() if k not in ("value", "unit", "ms_per_step")},
         "fp64": leg("fp64"),
         "speedup_mixed_vs_fp64": value / fp64_value,
+        "mixed_rom_bf16": dict(leg("mixed_rom_bf16"), note="ROM projection and lift as BF16 mma.sync products"),
         "mixed_fp64_krylov": leg("mixed_fp64_krylov"),
         "mixed_plain_romsad": leg("mixed_plain_romsad"),
         "mixed_fp64_residuals": leg("mixed_fp64_residuals"),
@@ -950,6 +958,34 @@ def main():
 # floats), the vertex levels add a geometric series of 4x4 element matrices and vectors (about 24 floats per
 # fine cell).
 DSA_VCYCLE_BYTES_PER_CELL = 4 * 72
+
+# DRAM traffic of one A~ apply (the sweep kernel plus the reduce of its partial fluxes), dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of each kernel (bench.py --profile ...), with the SHA-256 of the
+# sweep source it was taken on: reported only while that source is unchanged.  The FP64 capture ran 16 of the 64
+# instances; its traffic grows in proportion to the instances and is scaled by 4.
+NCU_TRAFFIC = {
+    ("large256_192", "k_sweep2d<float> (A~ apply, FP32)"): {
+        "bytes": (0.187697 + 1.575675 + 1.677798 + 0.066068) * 1e9, "instances_captured": 64,
+        "kernels": "k_sweep2d_bands<float, float, 4, 0> + k_reduce<float, float, float>",
+        "sweep_sha256": "77ab69c77e6a5fb38a19122c1097fa83f674723f0f19bcaf28959a452371932e"},
+    ("large256_192", "k_sweep2d<double> (A~ apply, FP64)"): {
+        "bytes": 4 * (0.114661 + 1.554624 + 1.644227 + 0.033997) * 1e9, "instances_captured": 16,
+        "kernels": "k_sweep2d<double, double, 2, 0> + k_reduce<double, double, double>",
+        "sweep_sha256": "77ab69c77e6a5fb38a19122c1097fa83f674723f0f19bcaf28959a452371932e"},
+}
+
+
+def ncu_traffic(workload: str, kernel: str):
+    """Bytes per launch of the dominant kernel from its ncu capture, or None when there is none or the sweep
+    source has changed since."""
+    import hashlib
+    rec = NCU_TRAFFIC.get((workload, kernel))
+    if rec is None:
+        return None
+    with open(os.path.join(ROOT, "paper_2410_08735_gb300", "csrc", "sweep.cu"), "rb") as fh:
+        if hashlib.sha256(fh.read()).hexdigest() != rec["sweep_sha256"]:
+            return None
+    return rec["bytes"]
 
 
 if __name__ == "__main__":
