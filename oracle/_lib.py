@@ -32,7 +32,7 @@ def lib():
         _lib = ctypes.CDLL(build())
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
-        for name in ("oracle_sweep_dir", "oracle_apply_dir"):
+        for name in ("oracle_sweep_dir", "oracle_apply_dir", "oracle_sweep_dir_blk", "oracle_apply_dir_blk"):
             f = getattr(_lib, name)
             f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, ip, dp, dp, dp]
             f.restype = ctypes.c_int
@@ -68,4 +68,30 @@ def apply_dir(nx, ny, nd, M, C, inflow, sigt, x):
     sigt = np.ascontiguousarray(sigt, dtype=np.float64)
     x = np.ascontiguousarray(x, dtype=np.float64)
     lib().oracle_apply_dir(nx, ny, nd, _dp(M), _dp(C), _ip(inflow), _dp(sigt), _dp(x), _dp(out))
+    return out
+
+
+def sweep_dir_blk(nx, ny, nd, M, C, inflow, St, rhs):
+    """sweep_dir with a full Sigma_t block per cell: St [ncell, nd, nd]."""
+    out = np.empty(nx * ny * nd)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    inflow = np.ascontiguousarray(inflow, dtype=np.int32)
+    St = np.ascontiguousarray(St, dtype=np.float64)
+    rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+    rc = lib().oracle_sweep_dir_blk(nx, ny, nd, _dp(M), _dp(C), _ip(inflow), _dp(St), _dp(rhs), _dp(out))
+    if rc != 0:
+        raise FloatingPointError(f"oracle sweep failed ({rc})")
+    return out
+
+
+def apply_dir_blk(nx, ny, nd, M, C, inflow, St, x):
+    """apply_dir with a full Sigma_t block per cell: St [ncell, nd, nd]."""
+    out = np.empty(nx * ny * nd)
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    inflow = np.ascontiguousarray(inflow, dtype=np.int32)
+    St = np.ascontiguousarray(St, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    lib().oracle_apply_dir_blk(nx, ny, nd, _dp(M), _dp(C), _ip(inflow), _dp(St), _dp(x), _dp(out))
     return out

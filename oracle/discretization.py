@@ -150,6 +150,16 @@ class Problem:
         self.sig_t = ss[region] + sa[region]
         self.sig_s_dof = np.repeat(self.sig_s, self.nd)
         self.sig_t_dof = np.repeat(self.sig_t, self.nd)
+        # cross-section profiles (spec.sigma_modes): Sigma is a full block per cell, (Sigma)_kl = int_T sigma eta_k eta_l
+        self.sigma_modes = getattr(spec, "sigma_modes", None)
+        self.mode_blocks = None
+        self.Ss_blk = self.St_blk = None
+        if self.sigma_modes is not None:
+            if self.sigma_modes != "variable_scattering" or self.dim != 2 or len(ss) != 2:
+                raise ValueError("sigma_modes: 'variable_scattering' takes two coefficients in 2D")
+            eye = np.broadcast_to(np.eye(self.nd), (self.ncell, self.nd, self.nd))
+            self.mode_blocks = np.stack([self._project_profile(_varscat_profile), eye])
+            _set_blocks(self, ss, sa)
         # per-direction local matrices
         self.M = np.empty((self.ndir, self.nd, self.nd))
         self.C = np.empty((self.ndir, 4, self.nd, self.nd))
@@ -293,6 +303,37 @@ class Problem:
                 G[c * 4:(c + 1) * 4] = (eta * qv) @ W2 * 0.25 * self.hx * self.hy
         return G
 
+    def _project_profile(self, fn, npts: int = 16) -> np.ndarray:
+        """Blocks F_c[k, l] = int_T f eta_k eta_l of a cross-section profile f(x, y), by npts x npts Gauss-Legendre
+        points per cell: [ncell, nd, nd]."""
+        xg, wg = gauss_legendre(npts)
+        XI, ZE = np.meshgrid(xg, xg, indexing="ij")
+        W2 = np.outer(wg, wg).ravel()
+        eta = self._eta(XI.ravel(), ZE.ravel())
+        F = np.empty((self.ncell, self.nd, self.nd))
+        for iy in range(self.ny):
+            for ix in range(self.nx):
+                px = self.x0 + (ix + 0.5 + 0.5 * XI.ravel()) * self.hx
+                py = self.y0 + (iy + 0.5 + 0.5 * ZE.ravel()) * self.hy
+                fw = fn(px, py) * W2 * 0.25 * self.hx * self.hy
+                F[iy * self.nx + ix] = (eta * fw) @ eta.T
+        return F
+
+    def Ss_apply(self, v: np.ndarray) -> np.ndarray:
+        """Sigma_s v (diagonal per region, or the cell blocks of a cross-section profile)."""
+        if self.Ss_blk is None:
+            return self.sig_s_dof * v
+        return np.einsum("ckl,cl->ck", self.Ss_blk, v.reshape(self.ncell, self.nd)).ravel()
+
+    def mode_apply(self, m: int, v: np.ndarray) -> np.ndarray:
+        """The m-th term of the affine split applied to v (..., N_DOF): the indicator of region m, or the blocks
+        of profile m."""
+        if self.mode_blocks is None:
+            return v * np.repeat((self.region == m).astype(np.float64), self.nd)
+        sh = v.shape
+        x = v.reshape(sh[:-1] + (self.ncell, self.nd))
+        return np.einsum("ckl,...cl->...ck", self.mode_blocks[m], x).reshape(sh)
+
     def gbc(self, j: int) -> np.ndarray:
         """(g_j^bc)_k = -int over inflow boundary faces of g eta_k (Omega_j . n)."""
         if self.g == 0.0:
@@ -335,12 +376,17 @@ class Problem:
 
     # ---------------------------------------------------------- operators
     def sweep(self, j: int, rhs: np.ndarray, sig_t: np.ndarray | None = None) -> np.ndarray:
-        """psi_j = (D_j + Sigma_t)^{-1} rhs by one upwind block Gauss-Seidel pass (Sec. 3.1)."""
+        """psi_j = (D_j + Sigma_t)^{-1} rhs by one upwind block Gauss-Seidel pass (Sec. 3.1).  sig_t: per-cell
+        values replacing the problem's Sigma_t."""
+        if sig_t is None and self.St_blk is not None:
+            return _lib.sweep_dir_blk(self.nx, self.ny, self.nd, self.M[j], self.C[j], self.inflow[j], self.St_blk, rhs)
         st = self.sig_t if sig_t is None else sig_t
         return _lib.sweep_dir(self.nx, self.ny, self.nd, self.M[j], self.C[j], self.inflow[j], st, rhs)
 
     def apply_forward(self, j: int, x: np.ndarray, sig_t: np.ndarray | None = None) -> np.ndarray:
         """(D_j + Sigma_t) x for direction j (no inflow-boundary term)."""
+        if sig_t is None and self.St_blk is not None:
+            return _lib.apply_dir_blk(self.nx, self.ny, self.nd, self.M[j], self.C[j], self.inflow[j], self.St_blk, x)
         st = self.sig_t if sig_t is None else sig_t
         return _lib.apply_dir(self.nx, self.ny, self.nd, self.M[j], self.C[j], self.inflow[j], st, x)
 
@@ -352,7 +398,10 @@ class Problem:
         for iy in range(ny):
             for ix in range(nx):
                 c = iy * nx + ix
-                L[c * nd:(c + 1) * nd, c * nd:(c + 1) * nd] = self.M[j] + st[c] * np.eye(nd)
+                if sig_t is None and self.St_blk is not None:
+                    L[c * nd:(c + 1) * nd, c * nd:(c + 1) * nd] = self.M[j] + self.St_blk[c]
+                else:
+                    L[c * nd:(c + 1) * nd, c * nd:(c + 1) * nd] = self.M[j] + st[c] * np.eye(nd)
                 nbrs = (
                     (ix - 1, iy) if ix > 0 else None,
                     (ix + 1, iy) if ix < nx - 1 else None,
@@ -378,4 +427,25 @@ def with_params(p: Problem, sigma_s, sigma_a) -> Problem:
     q.sig_t = ss[p.region] + sa[p.region]
     q.sig_s_dof = np.repeat(q.sig_s, p.nd)
     q.sig_t_dof = np.repeat(q.sig_t, p.nd)
+    if p.mode_blocks is not None:
+        _set_blocks(q, ss, sa)
     return q
+
+
+def _varscat_profile(x, y):
+    """The variable-scattering profile (Sec. 5): r^4 (2 - r^2)^2 for r <= 1, 1 outside."""
+    r2 = x * x + y * y
+    return np.where(r2 <= 1.0, r2 * r2 * (2.0 - r2) ** 2, 1.0)
+
+
+def _set_blocks(p: Problem, ss, sa) -> None:
+    """Cell blocks Sigma_s = sum_m sigma_s,m F_m and Sigma_t = sum_m (sigma_s,m + sigma_a,m) F_m of the profiles
+    F_m; the per-cell scalars become the cell means (the (0, 0) entry: eta_0 is constant), which the DSA
+    diffusion operator takes."""
+    B = p.mode_blocks
+    p.Ss_blk = np.einsum("m,mckl->ckl", np.asarray(ss, dtype=np.float64), B)
+    p.St_blk = np.einsum("m,mckl->ckl", np.asarray(ss, dtype=np.float64) + np.asarray(sa, dtype=np.float64), B)
+    p.sig_s = p.Ss_blk[:, 0, 0].copy()
+    p.sig_t = p.St_blk[:, 0, 0].copy()
+    p.sig_s_dof = np.repeat(p.sig_s, p.nd)
+    p.sig_t_dof = np.repeat(p.sig_t, p.nd)

@@ -185,6 +185,6 @@ def source_iteration(p, n_iter: int, phi0: Optional[np.ndarray] = None):
     phi = np.zeros(p.ndof) if phi0 is None else phi0.copy()
     out = [phi]
     for _ in range(n_iter):
-        phi = T_apply(p, p.sig_s_dof * phi) + bt
+        phi = T_apply(p, p.Ss_apply(phi)) + bt
         out.append(phi)
     return out

@@ -69,10 +69,10 @@ def build_rom(p: Problem, U: np.ndarray) -> Rom:
     T_R = np.zeros((R, r, r))
     S_R = np.zeros((R, r, r))
     for reg in range(R):
-        chi = np.repeat((p.region == reg).astype(np.float64), p.nd)
+        # term reg of the affine split: the region's indicator, or the blocks of profile reg
         for j in range(p.ndir):
-            T_R[reg] += (U[:, j, :] * chi) @ U[:, j, :].T
-        S_R[reg] = P.T @ (chi[:, None] * W)
+            T_R[reg] += p.mode_apply(reg, U[:, j, :]) @ U[:, j, :].T
+        S_R[reg] = P.T @ p.mode_apply(reg, W.T).T
     return Rom(U, P, W, A_D, T_R, S_R)
 
 
@@ -95,7 +95,7 @@ def reduced_operator_direct(p: Problem, U: np.ndarray) -> np.ndarray:
     for j in range(p.ndir):
         LU_ = np.stack([p.apply_forward(j, U[c, j]) for c in range(r)])
         A += U[:, j, :] @ LU_.T
-    A -= P.T @ (p.sig_s_dof[:, None] * W)
+    A -= P.T @ np.stack([p.Ss_apply(W[:, k]) for k in range(r)], axis=1)
     return A
 
 
@@ -103,7 +103,7 @@ def romsad_apply(rom: Rom, p: Problem, v: np.ndarray, A_r: Optional[np.ndarray] 
     """z = M_ROM^{-1} v = v + W (U^T A U)^{-1} P^T Sigma_s v (eq. rom-sa-preconditioner)."""
     if A_r is None:
         A_r = reduced_operator(rom, p.sigma_s_region, p.sigma_a_region)
-    c = np.linalg.solve(A_r, rom.P.T @ (p.sig_s_dof * v))
+    c = np.linalg.solve(A_r, rom.P.T @ p.Ss_apply(v))
     return v + rom.W @ c
 
 
@@ -172,7 +172,7 @@ def xi_recurrence(phi: np.ndarray, first: dict, window: int) -> List[np.ndarray]
 
 def correction_snapshot(p: Problem, xi: np.ndarray) -> np.ndarray:
     """delta psi_j = (D_j + Sigma_t)^{-1} Sigma_s xi for every j; shape [N_Omega, N_DOF]."""
-    s = p.sig_s_dof * xi
+    s = p.Ss_apply(xi)
     return np.stack([p.sweep(j, s) for j in range(p.ndir)])
 
 
@@ -217,7 +217,7 @@ def greedy(p_template: Problem, sigma_s: np.ndarray, sigma_a: np.ndarray, window
     probs = [with_params(p_template, sigma_s[i], sigma_a[i]) for i in range(n_train)]
     # Step 1: b~_mu and eta_mu^(0) = Sigma_s r_mu^(0) with r^(0) = b~ (zero initial guess)
     bt = [rhs_btilde(q) for q in probs]
-    eta0 = [q.sig_s_dof * b for q, b in zip(probs, bt)]
+    eta0 = [q.Ss_apply(b) for q, b in zip(probs, bt)]
     k_idx = default_mu1(sigma_s, sigma_a) if mu1 is None else mu1
     sampled = [k_idx]
     cols: List[np.ndarray] = []
@@ -272,7 +272,7 @@ def rom_indicator(rom: Rom, q: Problem, eta0: np.ndarray) -> float:
     """max_j ||(D_j + Sigma_t) U_j c - Sigma_s W c - eta^(0)||_2 / ||eta^(0)||_2 (eq. rom-residual)."""
     c = galerkin_coefficients(rom, q, eta0)
     dphi = rom.W @ c
-    base = q.sig_s_dof * dphi + eta0
+    base = q.Ss_apply(dphi) + eta0
     worst = 0.0
     for j in range(q.ndir):
         dpsi_j = np.tensordot(c, rom.U[:, j, :], axes=(0, 0))

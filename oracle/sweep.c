@@ -124,3 +124,61 @@ int oracle_apply_dir(int nx, int ny, int nd, const double* M, const double* C, c
   }
   return 0;
 }
+
+/*
+ * The same two operators when Sigma_t is a full nd x nd block per cell (Sec. 2.3: (Sigma_t)_kl is the
+ * integral of sigma_t eta_k eta_l over the cell, which is not diagonal when sigma_t varies inside it).
+ * St holds the blocks row-major, cell after cell: St[(c*nd + k)*nd + l].
+ */
+int oracle_sweep_dir_blk(int nx, int ny, int nd, const double* M, const double* C, const int* inflow,
+                         const double* St, const double* rhs, double* psi) {
+  double A[64], b[8];
+  if (nd > 8) return 2;
+  int x_up = inflow[0] ? 1 : (inflow[1] ? -1 : 1);
+  int y_up = inflow[2] ? 1 : (inflow[3] ? -1 : 1);
+  for (int sy = 0; sy < ny; ++sy) {
+    int iy = y_up > 0 ? sy : ny - 1 - sy;
+    for (int sx = 0; sx < nx; ++sx) {
+      int ix = x_up > 0 ? sx : nx - 1 - sx;
+      int c = iy * nx + ix;
+      for (int k = 0; k < nd; ++k) b[k] = rhs[c * nd + k];
+      for (int f = 0; f < 4; ++f) {
+        if (!inflow[f]) continue;
+        int nb = neighbour(nx, ny, ix, iy, f);
+        if (nb < 0) continue;
+        const double* Cf = C + f * nd * nd;
+        for (int k = 0; k < nd; ++k) {
+          double s = 0.0;
+          for (int l = 0; l < nd; ++l) s += Cf[k * nd + l] * psi[nb * nd + l];
+          b[k] -= s;
+        }
+      }
+      for (int k = 0; k < nd * nd; ++k) A[k] = M[k] + St[(size_t)c * nd * nd + k];
+      if (dense_solve(nd, A, b)) return 1;
+      for (int k = 0; k < nd; ++k) psi[c * nd + k] = b[k];
+    }
+  }
+  return 0;
+}
+
+int oracle_apply_dir_blk(int nx, int ny, int nd, const double* M, const double* C, const int* inflow,
+                         const double* St, const double* x, double* w) {
+  for (int iy = 0; iy < ny; ++iy) {
+    for (int ix = 0; ix < nx; ++ix) {
+      int c = iy * nx + ix;
+      for (int k = 0; k < nd; ++k) {
+        double s = 0.0;
+        for (int l = 0; l < nd; ++l) s += (M[k * nd + l] + St[((size_t)c * nd + k) * nd + l]) * x[c * nd + l];
+        for (int f = 0; f < 4; ++f) {
+          if (!inflow[f]) continue;
+          int nb = neighbour(nx, ny, ix, iy, f);
+          if (nb < 0) continue;
+          const double* Cf = C + f * nd * nd;
+          for (int l = 0; l < nd; ++l) s += Cf[k * nd + l] * x[nb * nd + l];
+        }
+        w[c * nd + k] = s;
+      }
+    }
+  }
+  return 0;
+}

@@ -53,7 +53,15 @@ def rhs_btilde(p: Problem) -> np.ndarray:
 
 def Atilde_apply(p: Problem, z: np.ndarray) -> np.ndarray:
     """A~ z = z - T (Sigma_s z)."""
-    return z - T_apply(p, p.sig_s_dof * z)
+    return z - T_apply(p, p.Ss_apply(z))
+
+
+def _block_diag(blocks: np.ndarray) -> np.ndarray:
+    n, nd, _ = blocks.shape
+    out = np.zeros((n * nd, n * nd))
+    for c in range(n):
+        out[c * nd:(c + 1) * nd, c * nd:(c + 1) * nd] = blocks[c]
+    return out
 
 
 def dense_coupled_system(p: Problem):
@@ -65,7 +73,7 @@ def dense_coupled_system(p: Problem):
     n = p.ndof
     N = p.ndir * n
     A = np.zeros((N, N))
-    Ss = np.diag(p.sig_s_dof)
+    Ss = np.diag(p.sig_s_dof) if p.Ss_blk is None else _block_diag(p.Ss_blk)
     b = np.empty(N)
     for i in range(p.ndir):
         A[i * n:(i + 1) * n, i * n:(i + 1) * n] = p.dense_L(i)

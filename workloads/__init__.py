@@ -60,6 +60,10 @@ class ProblemSpec:
     sigma_a_range  uniform range of sigma_a per region.
     src_gauss  None, or (A, a, xc, yc): the source A exp(-a ((x-xc)^2 + (y-yc)^2)) replaces the box source.
     inflow_faces  domain faces that carry the inflow g: a subset of ("x-", "x+", "y-", "y+") (2D).
+    sigma_modes   None: sigma_s and sigma_a are constant on each of the R regions.  "variable_scattering":
+               the R = 2 entries are the coefficients of two cross-section profiles over the whole domain,
+               sigma(x, y) = c_0 f(x, y) + c_1 with f = r^4 (2 - r^2)^2 inside the unit disc and 1 outside
+               (r^2 = x^2 + y^2), so that Sigma is a full 4x4 block per cell (2D).
     """
 
     name: str
@@ -83,6 +87,7 @@ class ProblemSpec:
     n_train: int = 20
     src_gauss: Optional[Sequence[float]] = None
     inflow_faces: Sequence[str] = ("x-", "x+", "y-", "y+")
+    sigma_modes: Optional[str] = None
 
     @property
     def n_instances(self) -> int:
@@ -205,6 +210,21 @@ def param_inflow_params(mu_s: float):
     for r in _INNER:
         ss[r], sa[r] = mu_s, 0.0
     return ss, sa
+
+
+def variable_scattering() -> ProblemSpec:
+    """Variable-scattering problem (Sec. 5): [-1,1]^2, 80 x 80 cells, CL(30, 6), zero inflow, source
+    (10/pi) exp(-100 (x^2+y^2)), sigma_a = 0 and sigma_s = mu_s f + 0.1 with the profile f of sigma_modes,
+    mu_s in [49.9, 99.9]; 51 training points, window 2, eps_ROM 1e-9, relative residual 1e-11."""
+    return ProblemSpec("varscat_80", 2, [80], [80], (-1.0, 1.0, -1.0, 1.0), 6, 30, 2, 1,
+                       0.0, (0.0, 0.0, 0.0, 0.0), 0.0, (49.9, 99.9), (0.0, 0.0),
+                       restart=30, rtol=1e-11, rom_rank=32, window=2, n_train=51,
+                       src_gauss=(10.0 / np.pi, 100.0, 0.0, 0.0), sigma_modes="variable_scattering")
+
+
+def variable_scattering_params(mu_s: float):
+    """Mode coefficients (sigma_s [2], sigma_a [2]) of the variable-scattering problem: sigma_s = mu_s f + 0.1."""
+    return np.array([mu_s, 0.1]), np.zeros(2)
 
 
 def draw_box(n: int, lo: Sequence[float], hi: Sequence[float], seed: int) -> np.ndarray:
