@@ -96,7 +96,20 @@ typedef struct rte_problem_desc {
                               RTE_FACE_XLO | RTE_FACE_XHI | RTE_FACE_YLO | RTE_FACE_YHI (a 1D slab has
                               x- and x+ only); the other faces are vacuum (the paper's two-material
                               problem has inflow on the left face only, Sec. 5)              */
+    int sigma_modes;       /* RTE_SIGMA_REGIONS: sigma_s, sigma_a constant on each region (diagonal
+                              Sigma).  RTE_SIGMA_VARSCAT (2D, rx*ry = 2, every instance on the same
+                              mesh): the two entries per instance are coefficients c_0, c_1 of
+                              sigma(x, y) = c_0 f(x, y) + c_1 with f = r^4 (2 - r^2)^2 in the unit disc
+                              and 1 outside, the variable-scattering problem of Sec. 5.  Sigma_s and
+                              Sigma_t are then full 4x4 blocks per cell, (Sigma)_kl = int_T sigma eta_k
+                              eta_l (Sec. 2.3), integrated with 16 x 16 Gauss-Legendre points per cell.
+                              The DSA preconditioner takes the cell means of the cross sections.  Not
+                              available in this mode: double-float sweeps (the mixed solves' refinement
+                              residuals are FP64), the tensor-core ROM products, rte_apply_op_noalloc,
+                              the band sweep kernels (the warp-per-task kernel runs)            */
 } rte_problem_desc;
+#define RTE_SIGMA_REGIONS 0
+#define RTE_SIGMA_VARSCAT 1
 #define RTE_FACE_XLO 1
 #define RTE_FACE_XHI 2
 #define RTE_FACE_YLO 4

@@ -24,6 +24,7 @@ RTE_DSA_PARTIAL, RTE_DSA_LUMPED, RTE_DSA_FULL = 0, 1, 2
 RTE_DSA_KEEP_SETUP = 16
 RTE_MODE_FP64, RTE_MODE_MIXED, RTE_MODE_MIXED_F64KRYLOV = 0, 1, 2
 RTE_RESIDUAL_DF, RTE_RESIDUAL_FP64 = 0, 1
+RTE_SIGMA_REGIONS, RTE_SIGMA_VARSCAT = 0, 1
 
 _lib = None
 
@@ -41,7 +42,8 @@ class ProblemDesc(ctypes.Structure):
                 ("rx", ctypes.c_int), ("ry", ctypes.c_int),
                 ("sigma_s", ctypes.POINTER(ctypes.c_double)), ("sigma_a", ctypes.POINTER(ctypes.c_double)),
                 ("src_q", ctypes.c_double), ("src_box", ctypes.c_double * 4), ("inflow_g", ctypes.c_double),
-                ("src_kind", ctypes.c_int), ("src_gauss", ctypes.c_double * 4), ("inflow_faces", ctypes.c_int)]
+                ("src_kind", ctypes.c_int), ("src_gauss", ctypes.c_double * 4), ("inflow_faces", ctypes.c_int),
+                ("sigma_modes", ctypes.c_int)]
 
 
 class ProblemInfo(ctypes.Structure):
@@ -263,6 +265,10 @@ class Problem:
         bits = {"x-": 1, "x+": 2, "y-": 4, "y+": 8}
         mask = sum(bits[f] for f in set(faces))
         d.inflow_faces = 0 if mask == 15 else mask
+        modes = getattr(spec, "sigma_modes", None)
+        if modes not in (None, "variable_scattering"):
+            raise ValueError(f"unknown sigma_modes {modes!r}")
+        d.sigma_modes = RTE_SIGMA_VARSCAT if modes == "variable_scattering" else RTE_SIGMA_REGIONS
         h = ctypes.c_void_p()
         _check(lib.rte_problem_create(ctypes.byref(d), ctypes.byref(h)), "rte_problem_create")
         self.h = h

@@ -1047,8 +1047,11 @@ int dsa_prepare(rte_problem* p, int variant, cudaStream_t st) {
   const DsaConst k = dsa_constants(p, variant);
   int max_nc = 0;
   for (const DsaInst& d : w->di) max_nc = std::max(max_nc, d.nx * d.ny);
+  // cross-section profiles: the diffusion operator and its scattering source take the cell means (one "region"
+  // per cell)
   k_dsa_setup_cells<<<dim3((max_nc + kSetupThreads - 1) / kSetupThreads, p->B), kSetupThreads, 0, st>>>(
-      w->d_di.p, w->data.p, p->d_sig_s.p, p->d_sig_t.p, p->R, p->rx, p->ry, k);
+      w->d_di.p, w->data.p, p->cellsig ? p->d_sigc_s.p : p->d_sig_s.p, p->cellsig ? p->d_sigc_t.p : p->d_sig_t.p,
+      p->cellsig ? p->ncell : p->R, p->cellsig ? p->nx[0] : p->rx, p->cellsig ? p->ny[0] : p->ry, k);
   count_launch();
   k_dsa_setup_levels<<<p->B, kSetupThreads, 0, st>>>(w->d_di.p, w->data.p);
   count_launch();

@@ -56,19 +56,46 @@ __global__ void k_to_f32(float* y, const double* x, long long n) {
 }
 
 // base_mu[i] = sigma_s(i) (W c_mu)[i] + eta0_mu[i], eta0 = sigma_s b~; one instance per blockIdx.y
+// With cross-section profiles (F: the profile blocks, sigma_s = c_0 F + c_1 I per cell) the cell's Sigma_s block
+// multiplies the cell's four values of W c_mu + b~.
 __global__ void k_base(const double* W, int rmax, int r, const double* c, const double* bt, const InstInfo* inst,
-                       const double* sig_s, int R, int rx, int ry, int nd, double* base) {
+                       const double* sig_s, int R, int rx, int ry, int nd, const double* F, double* base) {
   const int b = blockIdx.y;
   const InstInfo in = inst[b];
   const int cx = in.nx / rx, cy = in.ny / ry;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < in.ndof; i += gridDim.x * blockDim.x) {
     const int cell = i / nd;
+    if (F) {
+      double x[4];
+      for (int l = 0; l < 4; ++l) {
+        const int il = 4 * cell + l;
+        double s = 0.0;
+        for (int k = 0; k < r; ++k) s += W[(size_t)il * rmax + k] * c[(size_t)b * 64 + k];
+        x[l] = s + bt[in.off + il];
+      }
+      const double* Fr = F + (size_t)cell * 16 + (i & 3) * 4;
+      base[in.off + i] = sig_s[(size_t)b * R] * (Fr[0] * x[0] + Fr[1] * x[1] + Fr[2] * x[2] + Fr[3] * x[3]) +
+                         sig_s[(size_t)b * R + 1] * x[i & 3];
+      continue;
+    }
     const int ix = cell % in.nx, iy = cell / in.nx;
     const double sg = sig_s[(size_t)b * R + (iy / cy) * rx + ix / cx];
     double s = 0.0;
     for (int k = 0; k < r; ++k) s += W[(size_t)i * rmax + k] * c[(size_t)b * 64 + k];
     base[in.off + i] = sg * (s + bt[in.off + i]);
   }
+}
+
+// (F x)_i for the profile blocks F with the dofs of a cell on four consecutive lanes (i = chunk * 256 + thread, so
+// i mod 4 = lane mod 4): gathers the cell's four x by shuffles; every lane of the warp calls it.  0 without F.
+__device__ __forceinline__ double profile_times(const double* F, int i, double x, bool ok) {
+  if (!F) return 0.0;
+  const int g = (threadIdx.x & 31) & ~3;
+  const double x0 = __shfl_sync(0xffffffffu, x, g), x1 = __shfl_sync(0xffffffffu, x, g + 1);
+  const double x2 = __shfl_sync(0xffffffffu, x, g + 2), x3 = __shfl_sync(0xffffffffu, x, g + 3);
+  if (!ok) return 0.0;
+  const double* Fr = F + (size_t)(i >> 2) * 16 + (i & 3) * 4;
+  return Fr[0] * x0 + Fr[1] * x1 + Fr[2] * x2 + Fr[3] * x3;
 }
 
 // Squared residual norms of eq. rom-residual, one partial per (mu, u, dof chunk):
@@ -78,7 +105,7 @@ __global__ void k_base(const double* W, int rmax, int r, const double* c, const 
 template <typename T, int MT>
 __global__ void k_indicator(const T* U, const T* Y, int nA, int N, int r, const double* c,
                             const double* base, const int* mus, int nmu, const double* sig_t, int R, int rx, int ry,
-                            int nx, int ny, int nd, double* part) {
+                            int nx, int ny, int nd, const double* F, double* part) {
   const int u = blockIdx.y;
   const int chunk = blockIdx.x;
   const int mt0 = blockIdx.z * MT;
@@ -112,9 +139,12 @@ __global__ void k_indicator(const T* U, const T* Y, int nA, int N, int r, const 
 #pragma unroll
   for (int m = 0; m < MT; ++m) {
     double e2 = 0.0;
+    const double fb = profile_times(F, i, (double)b[m], i < N);   // (F (U c))_i with profiles
     if (i < N && mt0 + m < nmu) {
       const int mu = mus[mt0 + m];
-      const double e = (double)a[m] + sig_t[(size_t)mu * R + reg] * (double)b[m] - base[(size_t)mu * N + i];
+      const double st = F ? sig_t[(size_t)mu * R + 1] : sig_t[(size_t)mu * R + reg];
+      double e = (double)a[m] + st * (double)b[m] - base[(size_t)mu * N + i];
+      if (F) e += sig_t[(size_t)mu * R] * fb;
       e2 = e * e;
     }
     for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
@@ -137,7 +167,7 @@ template <int RMAX, int MT>
 __global__ void __launch_bounds__(256) k_indicator_reg(const float* U, const float* Y, int nA, int N, int r,
                                                        const double* c, const double* base, const int* mus, int nmu,
                                                        const double* sig_t, int R, int rx, int ry, int nx, int ny,
-                                                       int nd, int nchunk, double* part) {
+                                                       int nd, const double* F, int nchunk, double* part) {
   const int u = blockIdx.x;
   const int chunk = blockIdx.y;
   const int i = chunk * 256 + threadIdx.x;
@@ -182,9 +212,12 @@ __global__ void __launch_bounds__(256) k_indicator_reg(const float* U, const flo
 #pragma unroll
     for (int m = 0; m < MT; ++m) {
       double e2 = 0.0;
+      const double fb = profile_times(F, i, (double)b[m], i < N);   // (F (U c))_i with profiles
       if (i < N && mt0 + m < nmu) {
         const int mu = mus[mt0 + m];
-        const double e = (double)a[m] + sig_t[(size_t)mu * R + reg] * (double)b[m] - base[(size_t)mu * N + i];
+        const double st = F ? sig_t[(size_t)mu * R + 1] : sig_t[(size_t)mu * R + reg];
+        double e = (double)a[m] + st * (double)b[m] - base[(size_t)mu * N + i];
+        if (F) e += sig_t[(size_t)mu * R] * fb;
         e2 = e * e;
       }
       for (int o = 16; o > 0; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
@@ -235,6 +268,7 @@ static int make_problem_like(const rte_problem* tmpl, int n, const double* ss, c
   std::memcpy(d.src_gauss, tmpl->src_gauss, sizeof(d.src_gauss));
   d.inflow_g = tmpl->inst[0].g;
   d.inflow_faces = tmpl->inflow_mask;
+  d.sigma_modes = tmpl->cellsig ? RTE_SIGMA_VARSCAT : RTE_SIGMA_REGIONS;
   return rte_problem_create(&d, out);
 }
 
@@ -268,7 +302,7 @@ static int greedy_impl(rte_problem* tmpl, int n_train, const double* tss, const 
     RTE_TRY(base.alloc((size_t)n_train * N));
     dim3 g((N + 255) / 256, n_train);
     k_base<<<g, 256, 0, st>>>(rom->W.p, rom->rmax, 0, zc.p, bt.p, tp.p->d_inst.p, tp.p->d_sig_s.p, R, tp.p->rx,
-                              tp.p->ry, tp.p->nd, base.p);
+                              tp.p->ry, tp.p->nd, tp.p->cellsig ? tp.p->d_F64.p : nullptr, base.p);
     count_launch();
     std::vector<double> h((size_t)n_train * N);
     RTE_CHECK_CUDA(cudaMemcpyAsync(h.data(), base.p, h.size() * 8, cudaMemcpyDeviceToHost, st));
@@ -406,19 +440,20 @@ static int greedy_impl(rte_problem* tmpl, int n_train, const double* tss, const 
     RTE_TRY(base.alloc((size_t)n_train * N));
     dim3 g((N + 255) / 256, n_train);
     k_base<<<g, 256, 0, st>>>(rom->W.p, rom->rmax, rom->r, cs.p, bt.p, tp.p->d_inst.p, tp.p->d_sig_s.p, R, tp.p->rx,
-                              tp.p->ry, tp.p->nd, base.p);
+                              tp.p->ry, tp.p->nd, tp.p->cellsig ? tp.p->d_F64.p : nullptr, base.p);
     count_launch();
     const int nchunk = (N + 255) / 256;
     constexpr int MT = 8;
     RTE_TRY(ipart.alloc((size_t)n_train * rom->nA * nchunk));
     dim3 gi(nchunk, rom->nA, (nmu + MT - 1) / MT);
+    const double* prof = tp.p->cellsig ? tp.p->d_F64.p : nullptr;
     if (o->indicator_f32) {
       // basis in registers, all parameters per block; RMAX the smallest of 8, 16, 32, 64 covering the rank
       dim3 gr(rom->nA, nchunk);
 #define RTE_IND_REG(RM)                                                                                         \
   k_indicator_reg<RM, MT><<<gr, 256, 0, st>>>(U32.p, Y32.p, rom->nA, N, rom->r, cs.p, base.p, d_mus.p, nmu,      \
                                               tp.p->d_sig_t.p, R, tp.p->rx, tp.p->ry, tp.p->nx[0], tp.p->ny[0],  \
-                                              tp.p->nd, nchunk, ipart.p)
+                                              tp.p->nd, prof, nchunk, ipart.p)
       if (rom->r <= 8) RTE_IND_REG(8);
       else if (rom->r <= 16) RTE_IND_REG(16);
       else if (rom->r <= 32) RTE_IND_REG(32);
@@ -427,7 +462,7 @@ static int greedy_impl(rte_problem* tmpl, int n_train, const double* tss, const 
     } else
       k_indicator<double, MT><<<gi, 256, 0, st>>>(rom->U.p, rom->Y.p, rom->nA, N, rom->r, cs.p, base.p, d_mus.p, nmu,
                                                   tp.p->d_sig_t.p, R, tp.p->rx, tp.p->ry, tp.p->nx[0], tp.p->ny[0],
-                                                  tp.p->nd, ipart.p);
+                                                  tp.p->nd, prof, ipart.p);
     count_launch();
     RTE_CHECK_CUDA(cudaGetLastError());
     std::vector<double> hp_((size_t)n_train * rom->nA * nchunk);

@@ -174,6 +174,17 @@ struct rte_problem {
   rte::DevBuf<double> d_tmp64;                // [ntot] temporaries
   rte::DevBuf<float> d_tmp32;                 // [2 ntot] FP32 input and output of the autotuner's timing
   rte::DevBuf<double> d_wq;                   // [ndir] quadrature weights (paper order)
+  // cross-section profiles (RTE_SIGMA_VARSCAT): full 4x4 blocks per cell; every instance on the same mesh of ncell
+  // cells, block (b, c) at [(b * ncell + c) * 16]
+  bool cellsig = false;
+  int ncell = 0;
+  std::vector<double> F;                      // [ncell][16] blocks of the profile f (int_T f eta_k eta_l)
+  rte::DevBuf<double> d_F64;                  // the same on the device
+  rte::DevBuf<double> d_sblk64, d_tblk64;     // [B][ncell][16] Sigma_s and Sigma_t blocks
+  rte::DevBuf<float> d_sblk32;                // Sigma_s blocks in FP32
+  rte::DevBuf<double> d_sigc_s, d_sigc_t;     // [B][ncell] cell means (the DSA's cross sections)
+  rte::DevBuf<double> d_linvc64;              // [B][nu][ncell][16] cell inverses (reflected frame of each direction)
+  rte::DevBuf<float> d_linvc32;
   std::shared_ptr<void> krylov_ws;            // FGMRES workspace (krylov.cu), grown on demand
   std::shared_ptr<void> dsa_ws;               // DSA multigrid workspace (dsa.cu), sized once
 };

@@ -179,9 +179,26 @@ __device__ __forceinline__ TV warp_sum_t(TV v) {
 // z = M_ROM^{-1} v = v + W (U^T A_mu U)^{-1} P^T Sigma_s v for instances with a ROM, z = v otherwise.
 // slot (null: none): instances with slot[b] = 1 take the reduced coefficients from slot_c [B][64]
 // instead of the reduced solve (the learned correction in the ROMSAD slot).
+// Sigma_s w at global dof gdof of this lane: sigma_s per dof, or with cross-section profiles the cell's 4x4
+// block times the cell's four values, gathered from the four consecutive lanes that hold them (a cell's dofs are
+// 4 c .. 4 c + 3 and the lanes map to consecutive dofs from a multiple of 4).  Every lane of the warp calls it.
+template <typename TV>
+__device__ __forceinline__ TV sigma_s_times(const TV* sig_dof, const TV* sblk, long long gdof, TV wi, bool ok) {
+  if (sblk) {
+    const int g = (threadIdx.x & 31) & ~3;
+    const TV x0 = __shfl_sync(0xffffffffu, wi, g), x1 = __shfl_sync(0xffffffffu, wi, g + 1);
+    const TV x2 = __shfl_sync(0xffffffffu, wi, g + 2), x3 = __shfl_sync(0xffffffffu, wi, g + 3);
+    if (!ok) return TV(0);
+    const TV* S = sblk + (gdof >> 2) * 16 + (gdof & 3) * 4;
+    return S[0] * x0 + S[1] * x1 + S[2] * x2 + S[3] * x3;
+  }
+  return ok ? sig_dof[gdof] * wi : TV(0);
+}
+
 template <typename TV>
 __global__ void __launch_bounds__(256) k_precond_coop(int B, const int2* items, int nitems, const InstInfo* inst,
                                                       const int* active, const RomInstDev* ri, const TV* sig_dof,
+                                                      const TV* sblk,
                                                       const TV* v, TV* z, TV* rpart, TV* rc, int nchunk,
                                                       const int* slot, const TV* slot_c) {
   namespace cg = cooperative_groups;
@@ -210,7 +227,8 @@ __global__ void __launch_bounds__(256) k_precond_coop(int B, const int2* items, 
     const int nrow = min(32, i1 - ib);
     TV acc0 = 0, acc1 = 0;
     if (nrow > 0) {
-      const TV svl = lane < nrow ? sig_dof[in.off + ib + lane] * v[in.off + ib + lane] : TV(0);
+      const TV vl = lane < nrow ? v[in.off + ib + lane] : TV(0);
+      const TV svl = sigma_s_times(sig_dof, sblk, in.off + ib + lane, vl, lane < nrow);
       const TV m0 = lane < R.r ? TV(1) : TV(0);
       const TV m1 = lane + 32 < R.r ? TV(1) : TV(0);
       const int c0 = min(lane, R.rmax - 1), c1 = min(lane + 32, R.rmax - 1);
@@ -320,6 +338,7 @@ struct ArnArgs {
   TV* rpart;            // [B][nchunk][64] chunk partials of P^T Sigma_s w
   const RomInstDev* ri;
   const TV* sig_dof;
+  const TV* sblk;       // cross-section profiles: Sigma_s blocks [cells][16] (null: sigma_s per dof)
   double* H;            // [B][m][m+1] column j: rotated Hessenberg column
   double* Hraw;         // unrotated copy (first-cycle record) or null
   double* w0;           // [B] ||w|| before orthogonalisation
@@ -557,7 +576,7 @@ __global__ void __launch_bounds__(256) k_arnoldi_coop(ArnArgs<TP, TV> A) {
     // projection partials P^T Sigma_s w for the next preconditioner apply
     const RomInstDev R = A.ri[b];
     if (A.rom_next && A.znext && R.has) {
-      wsh[threadIdx.x] = ok ? A.sig_dof[in.off + i] * wi : TV(0);
+      wsh[threadIdx.x] = sigma_s_times(A.sig_dof, A.sblk, in.off + i, wi, ok);
       __syncthreads();
       const TV* Pm = RomSel<TV>::P(R);
       const int ib = warp * 32;                       // chunk-local first row of this warp
@@ -1244,16 +1263,19 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
   TV* Zb;
   TV* rb;
   const TV* sig_dof;
+  const TV* sblk = nullptr;   // cross-section profiles: Sigma_s blocks per cell
   if constexpr (f64) {
     Vb = W.V.p;
     Zb = W.Z.p;
     rb = W.r.p;
     sig_dof = p->d_sig_dof.p;
+    if (p->cellsig) sblk = p->d_sblk64.p;
   } else {
     Vb = W.V32.p;
     Zb = W.Z32.p;
     rb = W.r32.p;
     sig_dof = p->d_sig_dof32.p;
+    if (p->cellsig) sblk = p->d_sblk32.p;
   }
   const int B = p->B, m = C.m;
   const long long ntot = p->ntot;
@@ -1367,6 +1389,7 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
             const int* act_p = W.active.p;
             const RomInstDev* ri_p = W.rominst.p;
             const TV* sd_p = sig_dof;
+            const TV* sb_p = sblk;
             const TV* v_p = vj;
             TV* rp_p = reinterpret_cast<TV*>(W.rpart.p);
             TV* rc_p = reinterpret_cast<TV*>(W.rc.p);
@@ -1377,7 +1400,7 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
               if constexpr (f64) slc_p = W.slot_c.p;
               else slc_p = W.slot_c32.p;
             }
-            void* args[] = {&Bv, &it_p, &nit, &inst_p, &act_p, &ri_p, &sd_p, &v_p, &zj, &rp_p, &rc_p, &nch, &sl_p,
+            void* args[] = {&Bv, &it_p, &nit, &inst_p, &act_p, &ri_p, &sd_p, &sb_p, &v_p, &zj, &rp_p, &rc_p, &nch, &sl_p,
                             &slc_p};
             RTE_CHECK_CUDA(cudaLaunchCooperativeKernel((const void*)k_precond_coop<TV>, dim3(W.grid_pre), dim3(256),
                                                        args, 0, s));
@@ -1448,6 +1471,7 @@ static int run_fgmres_t(SolveCtx& C, const TV* rhs, TV* x, bool zero_guess, cons
           A.rpart = reinterpret_cast<TV*>(W.rpart.p);
           A.ri = W.rominst.p;
           A.sig_dof = sig_dof;
+          A.sblk = sblk;
           A.H = W.H.p;
           A.Hraw = C.rec ? W.Hraw.p : nullptr;
           A.w0 = W.w0.p;
@@ -1659,6 +1683,10 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
   RTE_ARG(o->mode == RTE_MODE_FP64 || o->refine_residual == RTE_RESIDUAL_DF || o->refine_residual == RTE_RESIDUAL_FP64,
           "unknown refine_residual");
   RTE_ARG(o->rom_bf16 == 0 || o->rom_bf16 == 1, "rom_bf16 must be 0 or 1");
+  if (p->cellsig && o->rom_bf16) {
+    set_error("fgmres_solve: no tensor-core ROM products with cross-section profiles");
+    return RTE_ERR_UNSUPPORTED;
+  }
   const bool use_dsa = o->post_mode == RTE_POST_DSA;
   if (use_dsa) {
     RTE_ARG(o->dsa_variant == RTE_DSA_PARTIAL || o->dsa_variant == RTE_DSA_LUMPED || o->dsa_variant == RTE_DSA_FULL,
@@ -1890,7 +1918,7 @@ extern "C" int fgmres_solve(rte_problem_t p, const romsad_t* roms, const fgmres_
     // converge; the residual that certifies convergence is always an FP64 sweep: an instance whose
     // double-float residual meets rtol is re-checked in FP64 before it stops (ro64 marks which residuals
     // are FP64).  refine_residual = RTE_RESIDUAL_FP64 makes every residual FP64.
-    const bool res_df = o->refine_residual == RTE_RESIDUAL_DF;
+    const bool res_df = o->refine_residual == RTE_RESIDUAL_DF && !p->cellsig;   // no double-float sweep with profiles
     const dim3 vg = vec_grid(p);
     double* ro = ws->ro.p;
     std::vector<int> act(B, 1), esc(B, 0), ro64(B, 1);

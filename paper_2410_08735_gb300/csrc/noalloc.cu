@@ -61,6 +61,10 @@ using namespace rte;
 extern "C" int rte_apply_op_noalloc(rte_problem_t p, int dtype, const void* z, void* w, void* stream) {
   RTE_ARG(p && z && w, "null handle or pointer");
   RTE_ARG(dtype == RTE_F64 || dtype == RTE_F32, "dtype must be RTE_F64 or RTE_F32");
+  if (p->cellsig) {
+    set_error("rte_apply_op_noalloc: not available with cross-section profiles (RTE_SIGMA_VARSCAT)");
+    return RTE_ERR_UNSUPPORTED;
+  }
   const bool f64 = dtype == RTE_F64;
   // Directions per warp: the value the sweep autotuner picked for this precision (when rte_apply_op or a
   // solve has tuned it) if its scratch fits, else the smallest D whose scratch fits (the most warps in flight;

@@ -141,6 +141,87 @@ __global__ void k_linv(int B, int nu, int R, int dim, const InstInfo* inst, cons
   }
 }
 
+// Cell inverses with a full Sigma_t block per cell (cross-section profiles): thread (b, u, c) inverts
+// alpha K (x) I + beta I (x) K + R_u T_c R_u, the cell block in the frame reflected so that Omega_x, Omega_y > 0
+// (R_u flips the sign of the x-odd and y-odd Legendre modes: the reflection maps the block T_c to R_u T_c R_u).
+__global__ void k_linv_cell(int B, int nu, int ncell, const InstInfo* inst, const UDir* ud, const double* tblk,
+                            double* out64, float* out32) {
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)B * nu * ncell;
+  if (tid >= total) return;
+  const int c = (int)(tid % ncell);
+  const int u = (int)((tid / ncell) % nu);
+  const int b = (int)(tid / ((long long)ncell * nu));
+  const double s3 = 1.7320508075688772;
+  const double K[4] = {1.0, s3, -s3, 3.0};
+  const double al = ud[u].ax / inst[b].hx, be = ud[u].ay / inst[b].hy;
+  const double rs[4] = {1.0, (double)ud[u].sx, (double)ud[u].sy, (double)(ud[u].sx * ud[u].sy)};
+  const double* T = tblk + ((size_t)b * ncell + c) * 16;
+  double A[16], X[16];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      const int a = i & 1, bb = i >> 1, cc = j & 1, d = j >> 1;
+      double v = rs[i] * rs[j] * T[i * 4 + j];
+      if (bb == d) v += al * K[a * 2 + cc];
+      if (a == cc) v += be * K[bb * 2 + d];
+      A[i * 4 + j] = v;
+      X[i * 4 + j] = i == j ? 1.0 : 0.0;
+    }
+  for (int col = 0; col < 4; ++col) {   // Gauss-Jordan with partial pivoting
+    int piv = col;
+    double best = fabs(A[col * 4 + col]);
+    for (int i = col + 1; i < 4; ++i)
+      if (fabs(A[i * 4 + col]) > best) { best = fabs(A[i * 4 + col]); piv = i; }
+    if (piv != col)
+      for (int j = 0; j < 4; ++j) {
+        double t = A[col * 4 + j]; A[col * 4 + j] = A[piv * 4 + j]; A[piv * 4 + j] = t;
+        t = X[col * 4 + j]; X[col * 4 + j] = X[piv * 4 + j]; X[piv * 4 + j] = t;
+      }
+    const double inv = 1.0 / A[col * 4 + col];
+    for (int j = 0; j < 4; ++j) { A[col * 4 + j] *= inv; X[col * 4 + j] *= inv; }
+    for (int i = 0; i < 4; ++i) {
+      if (i == col) continue;
+      const double fct = A[i * 4 + col];
+      for (int j = 0; j < 4; ++j) { A[i * 4 + j] -= fct * A[col * 4 + j]; X[i * 4 + j] -= fct * X[col * 4 + j]; }
+    }
+  }
+  const size_t o = (size_t)tid * 16;
+  for (int i = 0; i < 16; ++i) {
+    out64[o + i] = X[i];
+    out32[o + i] = (float)X[i];
+  }
+}
+
+// The variable-scattering profile of Sec. 5: r^4 (2 - r^2)^2 inside the unit disc, 1 outside.
+static double varscat_profile(double x, double y) {
+  const double r2 = x * x + y * y;
+  return r2 <= 1.0 ? r2 * r2 * (2.0 - r2) * (2.0 - r2) : 1.0;
+}
+
+// Blocks F_c[k][l] = int_T f eta_k eta_l of the profile on the mesh of instance 0, by 16 x 16 Gauss-Legendre
+// points per cell.  With eta_k = 2 / sqrt(hx hy) p_a(xi) p_b(zeta) (k = a + 2 b, p_0 = sqrt(1/2),
+// p_1 = sqrt(3/2) xi) the Jacobian hx hy / 4 cancels the normalisation.
+static void profile_blocks(const rte_problem* p, std::vector<double>& F) {
+  std::vector<double> q, wq;
+  gauss_legendre(16, q, wq);
+  const InstInfo& in = p->inst[0];
+  F.assign((size_t)p->ncell * 16, 0.0);
+  const double s0 = std::sqrt(0.5), s1 = std::sqrt(1.5);
+  for (int iy = 0; iy < in.ny; ++iy)
+    for (int ix = 0; ix < in.nx; ++ix) {
+      double* Fc = &F[((size_t)iy * in.nx + ix) * 16];
+      for (int i = 0; i < 16; ++i)
+        for (int j = 0; j < 16; ++j) {
+          const double x = p->box[0] + (ix + 0.5 + 0.5 * q[i]) * in.hx;
+          const double y = p->box[2] + (iy + 0.5 + 0.5 * q[j]) * in.hy;
+          const double fw = varscat_profile(x, y) * wq[i] * wq[j];
+          const double e[4] = {s0 * s0, s1 * q[i] * s0, s0 * s1 * q[j], s1 * q[i] * s1 * q[j]};
+          for (int k = 0; k < 4; ++k)
+            for (int l = 0; l < 4; ++l) Fc[k * 4 + l] += fw * e[k] * e[l];
+        }
+    }
+}
+
 // sigma_s of the cell of every dof (instance-major scalar-vector layout)
 __global__ void k_sig_dof(const InstInfo* inst, int B, int R, int rx, int ry, int nd, const double* sig_s, double* out,
                           float* out32) {
@@ -196,6 +277,38 @@ int upload_params(rte_problem* p) {
     count_launch();
     RTE_CHECK_CUDA(cudaGetLastError());
   }
+  if (p->cellsig) {
+    // Sigma_s = c_s0 F + c_s1 I, Sigma_t = c_t0 F + c_t1 I per cell (c_t = c_s + c_a), their cell means (the (0, 0)
+    // entries: eta_0 is constant), then the cell inverses of every unique direction
+    const size_t nb = (size_t)p->B * p->ncell;
+    std::vector<double> S(nb * 16), T(nb * 16), ms(nb), mt(nb);
+    std::vector<float> S32(nb * 16);
+    for (int b = 0; b < p->B; ++b) {
+      const double cs0 = p->ss[2 * b], cs1 = p->ss[2 * b + 1];
+      const double ct0 = cs0 + p->sa[2 * b], ct1 = cs1 + p->sa[2 * b + 1];
+      for (int c = 0; c < p->ncell; ++c) {
+        const size_t o = ((size_t)b * p->ncell + c) * 16;
+        for (int k = 0; k < 16; ++k) {
+          const double f = p->F[(size_t)c * 16 + k], id = (k % 5 == 0) ? 1.0 : 0.0;
+          S[o + k] = cs0 * f + cs1 * id;
+          T[o + k] = ct0 * f + ct1 * id;
+          S32[o + k] = (float)S[o + k];
+        }
+        ms[(size_t)b * p->ncell + c] = S[o];
+        mt[(size_t)b * p->ncell + c] = T[o];
+      }
+    }
+    RTE_CHECK_CUDA(cudaMemcpy(p->d_sblk64.p, S.data(), S.size() * 8, cudaMemcpyHostToDevice));
+    RTE_CHECK_CUDA(cudaMemcpy(p->d_tblk64.p, T.data(), T.size() * 8, cudaMemcpyHostToDevice));
+    RTE_CHECK_CUDA(cudaMemcpy(p->d_sblk32.p, S32.data(), S32.size() * 4, cudaMemcpyHostToDevice));
+    RTE_CHECK_CUDA(cudaMemcpy(p->d_sigc_s.p, ms.data(), ms.size() * 8, cudaMemcpyHostToDevice));
+    RTE_CHECK_CUDA(cudaMemcpy(p->d_sigc_t.p, mt.data(), mt.size() * 8, cudaMemcpyHostToDevice));
+    const long long tot = (long long)p->B * p->nu * p->ncell;
+    k_linv_cell<<<(unsigned)((tot + 127) / 128), 128>>>(p->B, p->nu, p->ncell, p->d_inst.p, p->d_udir.p,
+                                                        p->d_tblk64.p, p->d_linvc64.p, p->d_linvc32.p);
+    count_launch();
+    RTE_CHECK_CUDA(cudaGetLastError());
+  }
   RTE_CHECK_CUDA(cudaDeviceSynchronize());
   return RTE_OK;
 }
@@ -237,6 +350,13 @@ static int create_impl(const rte_problem_desc* d, rte_problem* p) {
   RTE_ARG(d->dim == 2 || d->inflow_faces == 15 || (d->inflow_faces & 12) == 0,
           "a 1D slab has the faces x- and x+ only");
   p->inflow_mask = d->inflow_faces == 0 ? 15 : d->inflow_faces;
+  RTE_ARG(d->sigma_modes == RTE_SIGMA_REGIONS || d->sigma_modes == RTE_SIGMA_VARSCAT, "unknown sigma_modes");
+  p->cellsig = d->sigma_modes == RTE_SIGMA_VARSCAT;
+  if (p->cellsig) {
+    RTE_ARG(d->dim == 2 && d->rx * d->ry == 2, "RTE_SIGMA_VARSCAT is 2D with two coefficients (rx * ry = 2)");
+    for (int b = 1; b < d->n_instances; ++b)
+      RTE_ARG(d->nx[b] == d->nx[0] && d->ny[b] == d->ny[0], "RTE_SIGMA_VARSCAT needs every instance on one mesh");
+  }
   p->nx.resize(p->B);
   p->ny.resize(p->B);
   p->off.assign(p->B + 1, 0);
@@ -397,6 +517,20 @@ static int create_impl(const rte_problem_desc* d, rte_problem* p) {
   RTE_TRY(p->d_linv_df.alloc(2 * nl));
   RTE_TRY(p->d_active.alloc(p->B));
   RTE_TRY(p->d_wq.alloc(p->ndir));
+  if (p->cellsig) {
+    p->ncell = p->nx[0] * p->ny[0];
+    profile_blocks(p, p->F);
+    const size_t nb = (size_t)p->B * p->ncell;
+    RTE_TRY(p->d_F64.alloc((size_t)p->ncell * 16));
+    RTE_TRY(p->d_sblk64.alloc(nb * 16));
+    RTE_TRY(p->d_tblk64.alloc(nb * 16));
+    RTE_TRY(p->d_sblk32.alloc(nb * 16));
+    RTE_TRY(p->d_sigc_s.alloc(nb));
+    RTE_TRY(p->d_sigc_t.alloc(nb));
+    RTE_TRY(p->d_linvc64.alloc(nb * p->nu * 16));
+    RTE_TRY(p->d_linvc32.alloc(nb * p->nu * 16));
+    RTE_CHECK_CUDA(cudaMemcpy(p->d_F64.p, p->F.data(), p->F.size() * 8, cudaMemcpyHostToDevice));
+  }
   RTE_CHECK_CUDA(cudaMemcpy(p->d_inst.p, p->inst.data(), p->B * sizeof(InstInfo), cudaMemcpyHostToDevice));
   RTE_CHECK_CUDA(cudaMemcpy(p->d_udir.p, p->udir.data(), p->nu * sizeof(UDir), cudaMemcpyHostToDevice));
   RTE_CHECK_CUDA(cudaMemcpy(p->d_G.p, G.data(), p->ntot * 8, cudaMemcpyHostToDevice));

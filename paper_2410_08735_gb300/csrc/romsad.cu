@@ -115,6 +115,102 @@ __global__ void k_newcol_S(const double* P, const double* W, int rmax, int k, in
   }
 }
 
+// Cross-section profiles: the same dots with the affine terms (profile blocks F, identity) in place of regions.
+// grid (l = 0..k, term t = 0 (F) / 1 (I), a-chunks); term 0 gets t2 = sum_a mult_a sum_c U_a[k]_c^T F_c U_a[l]_c
+// and no A_D part, term 1 all three sums over every dof.
+__global__ void k_newcol_dots_cell(const double* U, const double* Y, int nA, int N, int k, const double* F,
+                                   const double* mult, int achunk, double* out) {
+  const int l = blockIdx.x, t = blockIdx.y, ac = blockIdx.z;
+  const int a0 = ac * achunk, a1 = min(nA, a0 + achunk);
+  const int ncell = N / 4;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  const double* Uk = U + (size_t)k * nA * N;
+  const double* Ul = U + (size_t)l * nA * N;
+  const double* Yk = Y + (size_t)k * nA * N;
+  const double* Yl = Y + (size_t)l * nA * N;
+  for (int a = a0; a < a1; ++a) {
+    const double m = mult[a];
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+    if (t == 1) {
+      for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        const size_t g = (size_t)a * N + i;
+        t0 += Uk[g] * Yl[g];
+        t1 += Ul[g] * Yk[g];
+        t2 += Uk[g] * Ul[g];
+      }
+    } else {
+      for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const double* uk = Uk + (size_t)a * N + 4 * c;
+        const double* ul = Ul + (size_t)a * N + 4 * c;
+        const double* Fc = F + (size_t)c * 16;
+        for (int r = 0; r < 4; ++r) t2 += uk[r] * (Fc[4 * r] * ul[0] + Fc[4 * r + 1] * ul[1] + Fc[4 * r + 2] * ul[2] +
+                                                   Fc[4 * r + 3] * ul[3]);
+      }
+    }
+    s0 += m * t0;
+    s1 += m * t1;
+    s2 += m * t2;
+  }
+  __shared__ double red[3][256];
+  red[0][threadIdx.x] = s0;
+  red[1][threadIdx.x] = s1;
+  red[2][threadIdx.x] = s2;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int q = 0; q < 3; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const size_t o = (((size_t)l * gridDim.y + t) * gridDim.z + ac) * 3;
+    out[o] = red[0][0];
+    out[o + 1] = red[1][0];
+    out[o + 2] = red[2][0];
+  }
+}
+
+// S_t[k][l] = P[:, k]^T F_t W[:, l] and S_t[l][k] with F_0 = the profile blocks, F_1 = I; grid (l, t)
+__global__ void k_newcol_S_cell(const double* P, const double* W, int rmax, int k, int N, const double* F,
+                                double* out) {
+  const int l = blockIdx.x, t = blockIdx.y;
+  double s0 = 0.0, s1 = 0.0;
+  for (int c = threadIdx.x; c < N / 4; c += blockDim.x) {
+    double pk[4], pl[4], wk[4], wl[4];
+    for (int r = 0; r < 4; ++r) {
+      const size_t i = (size_t)(4 * c + r) * rmax;
+      pk[r] = P[i + k];
+      pl[r] = P[i + l];
+      wk[r] = W[i + k];
+      wl[r] = W[i + l];
+    }
+    for (int r = 0; r < 4; ++r) {
+      double fwl = wl[r], fwk = wk[r];
+      if (t == 0) {
+        const double* Fr = F + (size_t)c * 16 + 4 * r;
+        fwl = Fr[0] * wl[0] + Fr[1] * wl[1] + Fr[2] * wl[2] + Fr[3] * wl[3];
+        fwk = Fr[0] * wk[0] + Fr[1] * wk[1] + Fr[2] * wk[2] + Fr[3] * wk[3];
+      }
+      s0 += pk[r] * fwl;
+      s1 += pl[r] * fwk;
+    }
+  }
+  __shared__ double red[2][256];
+  red[0][threadIdx.x] = s0;
+  red[1][threadIdx.x] = s1;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[((size_t)l * gridDim.y + t) * 2] = red[0][0];
+    out[((size_t)l * gridDim.y + t) * 2 + 1] = red[1][0];
+  }
+}
+
 static int grow_host(romsad* rom, int newr) {
   // host affine matrices are re-laid out for rank newr
   auto regrow = [&](std::vector<double>& M, int nmat) {
@@ -147,14 +243,25 @@ int rom_add_column(romsad* rom, DevBuf<double>& d_mult, DevBuf<double>& d_wA, cu
   DevBuf<double> d_out;
   RTE_TRY(d_out.alloc((size_t)(k + 1) * R * nac * 3 + (size_t)(k + 1) * R * 2));
   dim3 g1(k + 1, R, nac);
-  k_newcol_dots<<<g1, 256, 0, st>>>(rom->U.p, rom->Y.p, nA, N, k, rom->nx, rom->ny, rom->nd, rom->rx, rom->ry,
-                                    d_mult.p, achunk, d_out.p);
-  count_launch();
-  RTE_CHECK_CUDA(cudaGetLastError());
   double* d_s = d_out.p + (size_t)(k + 1) * R * nac * 3;
   dim3 g2(k + 1, R);
-  k_newcol_S<<<g2, 256, 0, st>>>(rom->P.p, rom->W.p, rom->rmax, k, rom->nx, rom->ny, rom->nd, rom->rx, rom->ry, d_s);
-  count_launch();
+  if (rom->sigma_modes) {
+    if (!rom->F.p || R != 2) {
+      set_error("ROM: cross-section profile blocks missing");
+      return RTE_ERR_INVALID_ARG;
+    }
+    k_newcol_dots_cell<<<g1, 256, 0, st>>>(rom->U.p, rom->Y.p, nA, N, k, rom->F.p, d_mult.p, achunk, d_out.p);
+    count_launch();
+    k_newcol_S_cell<<<g2, 256, 0, st>>>(rom->P.p, rom->W.p, rom->rmax, k, N, rom->F.p, d_s);
+    count_launch();
+  } else {
+    k_newcol_dots<<<g1, 256, 0, st>>>(rom->U.p, rom->Y.p, nA, N, k, rom->nx, rom->ny, rom->nd, rom->rx, rom->ry,
+                                      d_mult.p, achunk, d_out.p);
+    count_launch();
+    k_newcol_S<<<g2, 256, 0, st>>>(rom->P.p, rom->W.p, rom->rmax, k, rom->nx, rom->ny, rom->nd, rom->rx, rom->ry, d_s);
+    count_launch();
+  }
+  RTE_CHECK_CUDA(cudaGetLastError());
   RTE_CHECK_CUDA(cudaGetLastError());
   std::vector<double> h(d_out.n);
   RTE_CHECK_CUDA(cudaMemcpyAsync(h.data(), d_out.p, h.size() * 8, cudaMemcpyDeviceToHost, st));
@@ -200,6 +307,7 @@ int rom_check_mesh(const romsad* rom, const rte_problem* p, int b) {
   RTE_ARG(rom->dim == p->dim && rom->nx == p->nx[b] && rom->ny == p->ny[b] && rom->ndir == p->ndir &&
               rom->nu == p->nu && rom->R == p->R && rom->rx == p->rx && rom->ry == p->ry,
           "ROM mesh/quadrature/regions do not match the instance");
+  RTE_ARG(rom->sigma_modes == (p->cellsig ? 1 : 0), "ROM and instance differ in their cross-section form");
   for (int q = 0; q < 4; ++q) RTE_ARG(std::fabs(rom->box[q] - p->box[q]) < 1e-12, "ROM domain does not match");
   return RTE_OK;
 }
@@ -208,7 +316,7 @@ int rom_check_mesh(const romsad* rom, const rte_problem* p, int b) {
 // y[b][k] = sum_i P[i][k] sigma_s(i) v_b[i]; one block per listed instance, warp lanes over k.
 template <typename TP>
 __global__ void k_project(const TP* P, int rmax, int r, const InstInfo* inst, const int* list, const double* sig_s,
-                          int R, int rx, int ry, int nd, const double* v, double* y) {
+                          int R, int rx, int ry, int nd, const double* sblk, const double* v, double* y) {
   const int b = list[blockIdx.x];
   const InstInfo in = inst[b];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -218,7 +326,14 @@ __global__ void k_project(const TP* P, int rmax, int r, const InstInfo* inst, co
   for (int i = warp; i < in.ndof; i += nw) {
     const int c = i / nd;
     const int ix = c % in.nx, iy = c / in.nx;
-    const double sv = sig_s[(size_t)b * R + (iy / cy) * rx + ix / cx] * vb[i];
+    double sv;
+    if (sblk) {   // cross-section profiles: row (i mod 4) of the cell's Sigma_s block times the cell's values
+      const double* S = sblk + ((size_t)(in.off / 4) + c) * 16 + (i & 3) * 4;
+      const double* x = vb + 4 * c;
+      sv = S[0] * x[0] + S[1] * x[1] + S[2] * x[2] + S[3] * x[3];
+    } else {
+      sv = sig_s[(size_t)b * R + (iy / cy) * rx + ix / cx] * vb[i];
+    }
     if (lane < r) acc0 += (double)P[(size_t)i * rmax + lane] * sv;
     if (lane + 32 < r) acc1 += (double)P[(size_t)i * rmax + lane + 32] * sv;
   }
@@ -370,7 +485,8 @@ __global__ void k_rom_factor(const double* aff, int r, int R, const double* sig_
 // (sigma_s per dof precomputed); grid (nchunk, ninst); 8 warps stride over the chunk, lanes over k.
 template <typename TP>
 __global__ void k_project_part(const TP* P, int rmax, int r, const InstInfo* inst, const int* list, const int* active,
-                               const double* sig_dof, const double* v, int chunk, double* part) {
+                               const double* sig_dof, const double* sblk, const double* v, int chunk,
+                               double* part) {
   const int b = list[blockIdx.y];
   if (active && !active[b]) return;
   const InstInfo in = inst[b];
@@ -380,7 +496,14 @@ __global__ void k_project_part(const TP* P, int rmax, int r, const InstInfo* ins
   const double* vb = v + in.off;
   const double* sb = sig_dof + in.off;
   for (int i = i0 + warp; i < i1; i += nw) {
-    const double sv = sb[i] * vb[i];
+    double sv;
+    if (sblk) {   // cross-section profiles: row (i mod 4) of the cell's Sigma_s block times the cell's values
+      const double* S = sblk + ((size_t)(in.off + i) >> 2) * 16 + (i & 3) * 4;
+      const double* x = vb + (i & ~3);
+      sv = S[0] * x[0] + S[1] * x[1] + S[2] * x[2] + S[3] * x[3];
+    } else {
+      sv = sb[i] * vb[i];
+    }
     if (lane < r) acc0 += (double)P[(size_t)i * rmax + lane] * sv;
     if (lane + 32 < r) acc1 += (double)P[(size_t)i * rmax + lane + 32] * sv;
   }
@@ -464,10 +587,12 @@ int RomPlan::apply(rte_problem* p, const int* d_active, const double* v, double*
   dim3 gp(nchunk, n);
   if (f64)
     k_project_part<double><<<gp, 256, 0, st>>>(rom->P.p, rom->rmax, rom->r, p->d_inst.p, d_ids.p, d_active,
-                                               p->d_sig_dof.p, v, chunk, part.p);
+                                               p->d_sig_dof.p, p->cellsig ? p->d_sblk64.p : nullptr, v, chunk,
+                                               part.p);
   else
     k_project_part<float><<<gp, 256, 0, st>>>(rom->P32.p, rom->rmax, rom->r, p->d_inst.p, d_ids.p, d_active,
-                                              p->d_sig_dof.p, v, chunk, part.p);
+                                              p->d_sig_dof.p, p->cellsig ? p->d_sblk64.p : nullptr, v, chunk,
+                                              part.p);
   count_launch();
   k_rom_inv_apply<<<n, 64, 0, st>>>(part.p, nchunk, rom->r, lu.p, d_ids.p, d_active, c.p);
   count_launch();
@@ -505,7 +630,7 @@ int rom_project_list(romsad* rom, rte_problem* p, const int* d_list, int ninst, 
                      cudaStream_t st) {
   if (ninst == 0) return RTE_OK;
   k_project<double><<<ninst, 256, 0, st>>>(rom->P.p, rom->rmax, rom->r, p->d_inst.p, d_list, p->d_sig_s.p, p->R, p->rx,
-                                           p->ry, p->nd, v, y);
+                                           p->ry, p->nd, p->cellsig ? p->d_sblk64.p : nullptr, v, y);
   count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
   return RTE_OK;
@@ -541,6 +666,9 @@ void rom_init_geometry(romsad* rom, const rte_problem* p, int b) {
   rom->ry = p->ry;
   std::memcpy(rom->box, p->box, sizeof(rom->box));
   rom->N = (int)(p->off[b + 1] - p->off[b]);
+  rom->sigma_modes = p->cellsig ? 1 : 0;
+  if (p->cellsig && rom->F.alloc((size_t)p->ncell * 16) == RTE_OK)
+    cudaMemcpy(rom->F.p, p->d_F64.p, (size_t)p->ncell * 16 * 8, cudaMemcpyDeviceToDevice);
   rom->r = 0;
   rom->A_D.clear();
   rom->T_R.clear();
@@ -670,6 +798,10 @@ int romsad_apply(romsad_t rom, rte_problem_t p, int dtype, const void* v, void* 
   RomPlan plan;
   RTE_TRY(plan.build(rom, p, ids, st));
   if (dtype == RTE_F32) {
+    if (p->cellsig) {
+      set_error("romsad_apply: FP32 vectors run the tensor-core products, not available with cross-section profiles");
+      return RTE_ERR_UNSUPPORTED;
+    }
     RTE_TRY(rom_tc_plan_setup(plan, st));
     RTE_TRY(rom_tc_apply(plan, p, nullptr, (const float*)v, (float*)z, st));
   } else {
@@ -687,7 +819,8 @@ int romsad_save(romsad_t rom, const char* path) {
     return RTE_ERR_IO;
   }
   const char magic[8] = {'R', 'T', 'E', 'R', 'O', 'M', '1', 0};
-  int hdr[12] = {rom->dim, rom->nx, rom->ny, rom->nd, rom->ndir, rom->nu, rom->R, rom->rx, rom->ry, rom->N, rom->r, 0};
+  int hdr[12] = {rom->dim, rom->nx, rom->ny, rom->nd, rom->ndir, rom->nu, rom->R, rom->rx, rom->ry, rom->N, rom->r,
+                 rom->sigma_modes};
   std::vector<double> P((size_t)rom->N * rom->r), W((size_t)rom->N * rom->r);
   for (int k = 0; k < rom->r; ++k) {
     std::vector<double> col(rom->N);
@@ -726,7 +859,9 @@ int romsad_load(const char* path, romsad_t* out) {
   if (ok) {
     rom->dim = hdr[0]; rom->nx = hdr[1]; rom->ny = hdr[2]; rom->nd = hdr[3]; rom->ndir = hdr[4]; rom->nu = hdr[5];
     rom->R = hdr[6]; rom->rx = hdr[7]; rom->ry = hdr[8]; rom->N = hdr[9]; rom->r = hdr[10];
-    ok = rom->r >= 1 && rom->r <= 64 && rom->N > 0 && rom->R >= 1 && rom->R <= 4096;
+    rom->sigma_modes = hdr[11];
+    ok = rom->r >= 1 && rom->r <= 64 && rom->N > 0 && rom->R >= 1 && rom->R <= 4096 &&
+         (rom->sigma_modes == 0 || (rom->sigma_modes == 1 && rom->R == 2));
   }
   std::vector<double> P, W;
   if (ok) {

@@ -32,6 +32,10 @@ struct romsad {
   rte::DevBuf<double> d_aff;   // [(1 + 2R)][r][r] device copy: A_D, T_R..., S_R...
   rte_mlp* mlp = nullptr;      // learned warm start (not owned)
   rte::DevBuf<uint16_t> P16, W16;   // BF16 copies of P32, W32 for the tensor-core products (romsad_tc.cu)
+  // cross-section profiles (RTE_SIGMA_VARSCAT): the affine terms are the profile blocks F (term 0) and the identity
+  // (term 1) instead of region indicators; F is kept (device) while columns are added
+  int sigma_modes = 0;
+  rte::DevBuf<double> F;            // [ncell][16]
   int bf16_rank = 0;                // rank the BF16 copies were made at (0: none)
 };
 

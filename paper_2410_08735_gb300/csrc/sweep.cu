@@ -126,7 +126,7 @@ constexpr int prec_of() { return std::is_same<T, float>::value ? PREC_F32 : (std
     }                                                                                                  \
   } while (0)
 
-template <typename T, typename TI, int D, bool ANG>
+template <typename T, typename TI, int D, bool ANG, bool CELL = false>
 __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int wpb = blockDim.x >> 5;
@@ -138,15 +138,23 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
   const int nx = in.nx, ny = in.ny, R = a.R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* tab = reinterpret_cast<T*>(smem_raw) + (size_t)warp * a.smem_per_warp;
-  T* ybuf = tab + D * R * 16;
+  T* ybuf = tab + (CELL ? 0 : D * R * 16);
   T* sgs = ybuf + D * nx * 2;   // sigma_s per region
   // angular-output staging ring: per lane and direction the last 8 cells of its current row
   T* ring = ANG ? reinterpret_cast<T*>(smem_raw) + (size_t)wpb * a.smem_per_warp + ((size_t)warp * 32 + lane) * D * 32
                 : nullptr;
-  const T* linv = reinterpret_cast<const T*>(a.linv) + ((size_t)tk.b * a.nu + tk.u0) * R * 16;
-  for (int e = lane; e < D * R * 16; e += 32) tab[e] = linv[e];
-  if (a.sig_s)
-    for (int e = lane; e < R; e += 32) sgs[e] = reinterpret_cast<const T*>(a.sig_s)[(size_t)tk.b * R + e];
+  // cross-section profiles (CELL): cell inverses and Sigma_s blocks per cell, read from global memory; else the
+  // per-region inverses and sigma_s staged in shared memory
+  const long long ncell = (long long)nx * ny, cell0 = in.off / 4;
+  const T* linvc = CELL ? reinterpret_cast<const T*>(a.linv) + ((size_t)cell0 * a.nu + (size_t)tk.u0 * ncell) * 16
+                        : nullptr;
+  const T* sblk = CELL && a.sig_s ? reinterpret_cast<const T*>(a.sig_s) + (size_t)cell0 * 16 : nullptr;
+  if (!CELL) {
+    const T* linv = reinterpret_cast<const T*>(a.linv) + ((size_t)tk.b * a.nu + tk.u0) * R * 16;
+    for (int e = lane; e < D * R * 16; e += 32) tab[e] = linv[e];
+    if (a.sig_s)
+      for (int e = lane; e < R; e += 32) sgs[e] = reinterpret_cast<const T*>(a.sig_s)[(size_t)tk.b * R + e];
+  }
   T al[D], be[D], wg[D];
   const int sx = a.udir[tk.u0].sx, sy = a.udir[tk.u0].sy;
 #pragma unroll
@@ -299,7 +307,19 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
 #pragma unroll
         for (int d = 0; d < D; ++d) { tx0[d] = bndx; tx1[d] = (T)0; }
       }
-      if (sig_s) {
+      if (CELL && sig_s) {   // Sigma_s q with the cell's block (physical frame, before the reflection)
+        T m[16];
+        const T* S = sblk + (size_t)c * 16;
+        Vec4<T>::load(S, m[0], m[1], m[2], m[3]);
+        Vec4<T>::load(S + 4, m[4], m[5], m[6], m[7]);
+        Vec4<T>::load(S + 8, m[8], m[9], m[10], m[11]);
+        Vec4<T>::load(S + 12, m[12], m[13], m[14], m[15]);
+        const T q0v = s0v, q1v = s1, q2v = s2, q3v = s3;
+        s0v = m[0] * q0v + m[1] * q1v + m[2] * q2v + m[3] * q3v;
+        s1 = m[4] * q0v + m[5] * q1v + m[6] * q2v + m[7] * q3v;
+        s2 = m[8] * q0v + m[9] * q1v + m[10] * q2v + m[11] * q3v;
+        s3 = m[12] * q0v + m[13] * q1v + m[14] * q2v + m[15] * q3v;
+      } else if (sig_s) {
         const T sg = sgs[reg];
         s0v *= sg; s1 *= sg; s2 *= sg; s3 *= sg;
       }
@@ -314,7 +334,7 @@ __global__ void __launch_bounds__(128) k_sweep2d(SweepArgs a) {
         const T r1 = s1 - S3 * ax * tx0[d] + by * yi1[d];
         const T r2 = s2 + ax * tx1[d] - S3 * by * yi0[d];
         const T r3 = s3 - S3 * (ax * tx1[d] + by * yi1[d]);
-        const T* L = tab + (d * R + reg) * 16;
+        const T* L = CELL ? linvc + ((size_t)d * ncell + c) * 16 : tab + (d * R + reg) * 16;
         T l[16];
         Vec4<T>::load(L, l[0], l[1], l[2], l[3]);
         Vec4<T>::load(L + 4, l[4], l[5], l[6], l[7]);
@@ -1133,6 +1153,45 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
   const bool ang_throughput = ANG && throughput;
   const int tv = p->force_var >= 0 ? p->force_var
                                     : (p->pin_var >= 0 ? p->pin_var : p->tuned_var[prec_of<T>()][ANG ? 1 : 0]);
+  if (p->cellsig) {
+    // cross-section profiles: the warp-per-task kernel reads the cell inverses and Sigma_s blocks from global memory
+    if constexpr (std::is_same<T, dfloat>::value) {
+      set_error("sweep: no double-float sweep with cross-section profiles");
+      return RTE_ERR_UNSUPPORTED;
+    } else {
+      a.smem_per_warp = ((D * maxnx * 2 + 1) + 3) & ~3;
+      const size_t per_warp = (size_t)a.smem_per_warp * sizeof(T) + (ANG ? (size_t)32 * D * 32 * sizeof(T) : 0);
+      int wpb = 4;
+      while (wpb > 1 && per_warp * wpb > 96 * 1024) --wpb;
+      const size_t smem = per_warp * wpb;
+      if (smem > 227 * 1024) {
+        set_error("sweep: shared memory too large for this mesh");
+        return RTE_ERR_UNSUPPORTED;
+      }
+      const int blocks = (a.ntasks + wpb - 1) / wpb;
+#define RTE_CELL_CASE(DD)                                                                                   \
+  case DD: {                                                                                                \
+    auto kern = k_sweep2d<T, TI, DD, ANG, true>;                                                            \
+    static std::atomic<size_t> granted[kMaxDevices];                                                        \
+    RTE_TRY(grant_smem(kern, smem, granted));                                                               \
+    kern<<<blocks, wpb * 32, smem, st>>>(a);                                                                \
+    count_launch();                                                                                         \
+    break;                                                                                                  \
+  }
+      switch (D) {
+        RTE_CELL_CASE(1)
+        RTE_CELL_CASE(2)
+        RTE_CELL_CASE(4)
+        RTE_CELL_CASE(8)
+        default:
+          set_error("sweep: unsupported directions-per-warp");
+          return RTE_ERR_UNSUPPORTED;
+      }
+#undef RTE_CELL_CASE
+      RTE_CHECK_CUDA(cudaGetLastError());
+      return RTE_OK;
+    }
+  }
   if constexpr (!ANG) {
     if (tv == 2 && nbands <= 8) {
       // pipelined band kernel: persistent CTAs over runs of tasks
@@ -1235,14 +1294,23 @@ static int launch_sweep_t(rte_problem* p, int D, SweepArgs& a, cudaStream_t st) 
   return RTE_OK;
 }
 
+// Sigma_s of the fused scaling: per region, or the cell blocks of cross-section profiles
+static const void* sigma_s_arg(const rte_problem* p, bool f64) {
+  if (p->cellsig) return f64 ? (const void*)p->d_sblk64.p : (const void*)p->d_sblk32.p;
+  return f64 ? (const void*)p->d_sig_s.p : (const void*)p->d_sig_s32.p;
+}
+
 static void fill_args(rte_problem* p, SweepArgs& a, int prec) {
   std::memset(&a, 0, sizeof(a));
   a.inst = p->d_inst.p;
   a.udir = p->d_udir.p;
   a.tasks = p->d_tasks_by_D[p->tasks_D].p;
   a.ntasks = p->ntasks;
-  a.linv = prec == PREC_F64 ? (const void*)p->d_linv64.p
-                            : (prec == PREC_DF ? (const void*)p->d_linv_df.p : (const void*)p->d_linv32.p);
+  if (p->cellsig)
+    a.linv = prec == PREC_F64 ? (const void*)p->d_linvc64.p : (const void*)p->d_linvc32.p;
+  else
+    a.linv = prec == PREC_F64 ? (const void*)p->d_linv64.p
+                              : (prec == PREC_DF ? (const void*)p->d_linv_df.p : (const void*)p->d_linv32.p);
   a.inflow_mask = p->inflow_mask;
   a.tasks_per_inst = p->tasks_per_inst;
   a.ndir = p->ndir;
@@ -1290,6 +1358,7 @@ int autotune(rte_problem* p, int prec, bool ang, const void* src, void* psi, cud
   float best = 1e30f;
   int bestD = 0, bestV = -1;
   for (int var = 0; var < 3; ++var) {
+    if (p->cellsig && var != 1) continue;   // cross-section profiles: the warp-per-task kernel only
     if ((var == 0 || var == 2) && (maxny + 31) / 32 > 8) continue;
     if (var == 2 && ang) continue;   // the pipelined kernel has no angular output
     for (int D : {1, 2, 4, 8}) {
@@ -1342,9 +1411,10 @@ int prepare_sweeps(rte_problem* p) {
   RTE_TRY(p->d_xdf.ensure((size_t)2 * p->ntot));
   RTE_TRY(autotune(p, PREC_F32, false, nullptr, nullptr, 0, false, false));
   RTE_TRY(autotune(p, PREC_F64, false, nullptr, nullptr, 0, false, false));
-  RTE_TRY(autotune(p, PREC_DF, false, nullptr, nullptr, 0, false, false));
+  if (!p->cellsig) RTE_TRY(autotune(p, PREC_DF, false, nullptr, nullptr, 0, false, false));
   size_t bytes = 0;
   for (int prec : {PREC_F32, PREC_F64, PREC_DF}) {
+    if (p->cellsig && prec == PREC_DF) continue;
     RTE_TRY(ensure_tasks(p, pick_D(p, prec)));
     if (p->dim == 2) RTE_TRY(ensure_runs(p, pick_D(p, prec)));   // the pipelined kernel's runs, before any capture
     bytes = std::max(bytes, (size_t)p->tasks_per_inst * (size_t)p->ntot * (size_t)(prec == PREC_F32 ? 4 : 8));
@@ -1365,6 +1435,10 @@ int launch_T_df(rte_problem* p, int mode, const double* x, const double* bvec, d
                 cudaStream_t st) {
   if (mode != MODE_OP && mode != MODE_RES) {
     set_error("launch_T_df: only the operator and the residual run in double-float");
+    return RTE_ERR_UNSUPPORTED;
+  }
+  if (p->cellsig) {
+    set_error("launch_T_df: no double-float sweep with cross-section profiles");
     return RTE_ERR_UNSUPPORTED;
   }
   RTE_TRY(p->d_xdf.ensure((size_t)2 * p->ntot));
@@ -1403,7 +1477,7 @@ int launch_T(rte_problem* p, int mode, bool f64, const void* src, bool in_f64, c
   a.src = mode == MODE_RHS ? (const void*)p->d_G.p : src;
   bool src64 = mode == MODE_RHS ? true : in_f64;
   a.with_bc = mode == MODE_RHS ? 1 : 0;
-  a.sig_s = (mode == MODE_OP || mode == MODE_RES) ? (f64 ? (const void*)p->d_sig_s.p : (const void*)p->d_sig_s32.p)
+  a.sig_s = (mode == MODE_OP || mode == MODE_RES) ? (sigma_s_arg(p, f64))
                                                    : nullptr;
   a.partial = p->d_partial.p;
   a.active = d_active;
@@ -1449,7 +1523,7 @@ int launch_op_partials(rte_problem* p, bool f64, const void* z, bool in_f64, con
   SweepArgs a;
   fill_args(p, a, prec);
   a.src = z;
-  a.sig_s = f64 ? (const void*)p->d_sig_s.p : (const void*)p->d_sig_s32.p;
+  a.sig_s = sigma_s_arg(p, f64);
   a.partial = p->d_partial.p;
   a.active = d_active;
   if (f64) {
@@ -1466,6 +1540,10 @@ int launch_op_partials(rte_problem* p, bool f64, const void* z, bool in_f64, con
 // a valid directions-per-warp value; tasks holds ntasks entries in the layout of ensure_tasks.
 int launch_op_external(rte_problem* p, bool f64, const void* z, void* w, const SweepTask* tasks, int ntasks,
                        int tasks_per_inst, int D, void* partial, cudaStream_t st) {
+  if (p->cellsig) {
+    set_error("rte_apply_op_noalloc: not available with cross-section profiles");
+    return RTE_ERR_UNSUPPORTED;
+  }
   SweepArgs a;
   std::memset(&a, 0, sizeof(a));
   a.inst = p->d_inst.p;
@@ -1481,7 +1559,7 @@ int launch_op_external(rte_problem* p, bool f64, const void* z, void* w, const S
   a.rx = p->rx;
   a.ry = p->ry;
   a.src = z;
-  a.sig_s = f64 ? (const void*)p->d_sig_s.p : (const void*)p->d_sig_s32.p;
+  a.sig_s = sigma_s_arg(p, f64);
   a.partial = partial;
   if (f64) RTE_TRY((launch_sweep_t<double, double, false>(p, D, a, st)));
   else RTE_TRY((launch_sweep_t<float, float, false>(p, D, a, st)));
@@ -1515,7 +1593,7 @@ int launch_angular(rte_problem* p, bool f64, const void* src, int with_bc, void*
   a.partial = p->d_partial.p;
   a.psi = psi;
   a.psi_unique = unique_layout ? 1 : 0;
-  if (scale_sigma_s) a.sig_s = f64 ? (const void*)p->d_sig_s.p : (const void*)p->d_sig_s32.p;
+  if (scale_sigma_s) a.sig_s = sigma_s_arg(p, f64);
   if (f64) RTE_TRY((launch_sweep_t<double, double, true>(p, D, a, st)));
   else RTE_TRY((launch_sweep_t<float, float, true>(p, D, a, st)));
   return RTE_OK;
