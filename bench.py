@@ -312,8 +312,8 @@ def build_rom_and_mlp(RB, spec, cfg, args, n_train, rank_cap, restart, seed_net=
                      batch=min(64, n_train), lr=2e-3, bf16=True)
     RB.attach_mlp(rom, net)
     info = {"greedy_s": t_greedy, "total_s": time.perf_counter() - t0, "training_draws": n_train,
-            "rank": rep["rank"], "sampled": len(rep["sampled"]), "max_indicator_last": rep["max_indicator"][-1:]
-            if rep["max_indicator"] else [], "mlp_final_loss": loss}
+            "rank": rep["rank"], "sampled": len(rep["sampled"]),
+            "max_indicator_last": [x for x in rep["max_indicator"] if x == x][-1:], "mlp_final_loss": loss}
     return rom, net, tmpl, rep, (tr_ss, tr_sa), info
 
 
@@ -569,7 +569,7 @@ def measure_pincell(RB, torch, dev, stream, flush, args, n_test=10):
     phi = torch.zeros(prob.n_dof, dtype=torch.float64, device=dev)
     out = {"workload": f"pin-cell 80x80, CL(30, 6) = 180 directions, {n_test} test parameters in one batched call",
            "offline": {"greedy_s": t_off, "rank": rep["rank"], "sampled": len(rep["sampled"]),
-                       "max_indicator_last": rep["max_indicator"][-1:] if rep["max_indicator"] else []}}
+                       "max_indicator_last": [x for x in rep["max_indicator"] if x == x][-1:]}}
     legs = (("fgmres_romsad_fp64", [rom] * n_test, RB.RTE_MODE_FP64, 1e-11),
             ("gmres_dsa_fp64", None, RB.RTE_MODE_FP64, 1e-11),
             ("fgmres_romsad_mixed", [rom] * n_test, RB.RTE_MODE_MIXED, 1e-8),
@@ -622,7 +622,7 @@ def measure_varscat(RB, torch, dev, stream, flush, args, n_test=10):
     phi = torch.zeros(prob.n_dof, dtype=torch.float64, device=dev)
     out = {"workload": f"variable scattering 80x80, CL(30, 6), {n_test} test values of mu_s in one batched call",
            "offline": {"greedy_s": t_off, "rank": rep["rank"], "sampled": len(rep["sampled"]),
-                       "max_indicator_last": rep["max_indicator"][-1:] if rep["max_indicator"] else []}}
+                       "max_indicator_last": [x for x in rep["max_indicator"] if x == x][-1:]}}
     legs = (("fgmres_romsad_fp64", [rom] * n_test, RB.RTE_MODE_FP64, 1e-11),
             ("gmres_dsa_fp64", None, RB.RTE_MODE_FP64, 1e-11),
             ("fgmres_romsad_mixed", [rom] * n_test, RB.RTE_MODE_MIXED, 1e-8),

@@ -217,7 +217,9 @@ typedef struct romsad_greedy_opts {
 typedef struct romsad_report {
     int n_sampled;
     int* sampled;          /* caller array [max_greedy_iter] or NULL: training indices in order */
-    double* max_indicator; /* caller array [max_greedy_iter] or NULL                           */
+    double* max_indicator; /* caller array [max_greedy_iter] or NULL: entry i = the largest error
+                              indicator over the training set after sample i was added; NaN where
+                              it was not evaluated (the iteration cap ended the greedy first)   */
     int rank;
     double* labels;        /* caller array [n_train][max_rank] or NULL: Galerkin coefficients
                               c_mu of eq. greedy-rom on the final basis (MLP labels)           */

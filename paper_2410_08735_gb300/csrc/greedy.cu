@@ -490,7 +490,8 @@ static int greedy_impl(rte_problem* tmpl, int n_train, const double* tss, const 
     if (rep->sampled)
       for (size_t i = 0; i < sampled.size() && (int)i < o->max_greedy_iter; ++i) rep->sampled[i] = sampled[i];
     if (rep->max_indicator)
-      for (size_t i = 0; i < max_ind.size() && (int)i < o->max_greedy_iter; ++i) rep->max_indicator[i] = max_ind[i];
+      for (int i = 0; i < (int)sampled.size() && i < o->max_greedy_iter; ++i)
+        rep->max_indicator[i] = i < (int)max_ind.size() ? max_ind[i] : std::nan("");   // NaN: not evaluated
     rep->rank = rom->r;
     if (rep->labels && rom->r > 0) {
       // Galerkin coefficients of eq. greedy-rom on the final basis for every training parameter
