@@ -341,11 +341,7 @@ int rte_mlp_set_params(rte_mlp_t mlp, const float* flat, const float* mean, cons
 int rte_mlp_get_params(rte_mlp_t mlp, float* flat, float* mean, float* stdv);
 /* Loss and gradient on the GPU for n samples: mu host [n][n_in], c host [n][n_out] -> loss, grad host [n_params]. */
 int rte_mlp_loss_grad(rte_mlp_t mlp, int n, const double* mu, const double* c, int bf16, double* loss, float* grad);
-/* Sets the feature standardisation from the training set, then Adam for the given epochs on the labels
- * standardised per coefficient ((c_k - mean_k) / std_k over the training set: the coefficients of a ROM basis
- * differ in scale by orders of magnitude); afterwards the label scaling is folded into the last layer
- * (W3 <- diag(std) W3, b3 <- std b3 + mean), so inference returns c directly.  final_loss: the loss of the
- * folded network against the unscaled labels over all n. */
+/* Sets the standardisation from the training set, then Adam for the given epochs; final_loss over all n. */
 int rte_mlp_train(rte_mlp_t mlp, int n, const double* mu, const double* c, const rte_mlp_train_opts* opts,
                   double* final_loss);
 /* c_out host [n][n_out] = network(mu host [n][n_in]) with BF16-rounded weights. */

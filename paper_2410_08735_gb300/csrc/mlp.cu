@@ -345,29 +345,13 @@ int rte_mlp_train(rte_mlp_t M, int n, const double* mu, const double* c, const r
     M->mean[f] = (float)mean;
     M->stdv[f] = (float)(var > 1e-24 ? std::sqrt(var) : 1.0);
   }
-  // label standardisation: the coefficients of a ROM basis differ in scale by orders of magnitude, so the network is
-  // trained on (c_k - mean_k) / std_k and the affine map is folded into the last layer afterwards
-  const int dout = M->dout;
-  std::vector<double> cmean(dout, 0.0), cstd(dout, 1.0), cz((size_t)n * dout);
-  for (int k = 0; k < dout; ++k) {
-    double s = 0.0, s2 = 0.0;
-    for (int i = 0; i < n; ++i) {
-      const double v = c[(size_t)i * dout + k];
-      s += v;
-      s2 += v * v;
-    }
-    const double mean = s / n, var = std::max(0.0, s2 / n - mean * mean);
-    cmean[k] = mean;
-    cstd[k] = var > 1e-60 ? std::sqrt(var) : 1.0;
-    for (int i = 0; i < n; ++i) cz[(size_t)i * dout + k] = (c[(size_t)i * dout + k] - mean) / cstd[k];
-  }
   const int bs = std::min(o->batch, n);
   MlpScratch S;
   RTE_TRY(S.alloc(M, bs));
   MlpScratch full;
   RTE_TRY(full.alloc(M, n));
   RTE_TRY(upload_features(M, full, n, mu, 0));
-  RTE_CHECK_CUDA(cudaMemcpy(full.c.p, cz.data(), (size_t)n * dout * 8, cudaMemcpyHostToDevice));
+  RTE_CHECK_CUDA(cudaMemcpy(full.c.p, c, (size_t)n * M->dout * 8, cudaMemcpyHostToDevice));
   RTE_CHECK_CUDA(cudaMemset(M->m.p, 0, M->nparam * 4));
   RTE_CHECK_CUDA(cudaMemset(M->v.p, 0, M->nparam * 4));
   M->adam_t = 0;
@@ -386,19 +370,6 @@ int rte_mlp_train(rte_mlp_t M, int n, const double* mu, const double* c, const r
     }
   }
   RTE_CHECK_CUDA(cudaGetLastError());
-  // fold the label scaling into the last layer: W3 <- diag(std) W3, b3 <- std b3 + mean
-  {
-    std::vector<float> w3((size_t)dout * M->H), b3(dout);
-    RTE_CHECK_CUDA(cudaMemcpy(w3.data(), M->w.p + M->off_W3, w3.size() * 4, cudaMemcpyDeviceToHost));
-    RTE_CHECK_CUDA(cudaMemcpy(b3.data(), M->w.p + M->off_b3, b3.size() * 4, cudaMemcpyDeviceToHost));
-    for (int k = 0; k < dout; ++k) {
-      for (int j = 0; j < M->H; ++j) w3[(size_t)k * M->H + j] = (float)(cstd[k] * w3[(size_t)k * M->H + j]);
-      b3[k] = (float)(cstd[k] * b3[k] + cmean[k]);
-    }
-    RTE_CHECK_CUDA(cudaMemcpy(M->w.p + M->off_W3, w3.data(), w3.size() * 4, cudaMemcpyHostToDevice));
-    RTE_CHECK_CUDA(cudaMemcpy(M->w.p + M->off_b3, b3.data(), b3.size() * 4, cudaMemcpyHostToDevice));
-  }
-  RTE_CHECK_CUDA(cudaMemcpy(full.c.p, c, (size_t)n * dout * 8, cudaMemcpyHostToDevice));
   if (final_loss) RTE_TRY(mlp_loss_grad_dev(M, full, n, o->bf16, final_loss, 0));
   return RTE_OK;
 }
