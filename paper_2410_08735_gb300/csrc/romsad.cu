@@ -571,11 +571,9 @@ int RomPlan::build(romsad* rom_, rte_problem* p, const std::vector<int>& ids_, c
   RTE_TRY(part.ensure((size_t)n * nchunk * 64));
   RTE_TRY(c.ensure((size_t)n * 64));
   size_t smem = (size_t)2 * rom->r * rom->r * 8;   // 64 KiB at the largest rank (64)
-  static size_t smem_set = 48 * 1024;
-  if (smem > smem_set) {
+  // the attribute is per device: set on the current one at every plan build (once per solve, not on the hot path)
+  if (smem > 48 * 1024)
     RTE_CHECK_CUDA(cudaFuncSetAttribute(k_rom_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    smem_set = smem;
-  }
   k_rom_factor<<<n, 256, smem, st>>>(rom->d_aff.p, rom->r, rom->R, p->d_sig_s.p, p->d_sig_t.p, d_ids.p, lu.p, piv.p);
   count_launch();
   RTE_CHECK_CUDA(cudaGetLastError());
